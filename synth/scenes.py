@@ -1,0 +1,633 @@
+"""Scene generators: meshes, appearance, skeleton, ground truth, target frames.
+
+Every random draw comes from ``numpy.random.default_rng(seed)`` or, for the
+value-noise lattice, from the splitmix64 finaliser applied to lattice
+coordinates.  All geometry is produced in FP64 and handed out as FP32 arrays,
+which is the precision the library's upload calls take.
+
+Workloads (sizes follow the problem statement of the non-rigid stage,
+Sec. 3.4, at the scales of the synthetic configurations):
+
+* ``"tiny"``: closed capsule, 1,002 vertices / 2,000 triangles, 64 nodes, K=4,
+  128x128 image, f=150 px.
+* ``"body"``: articulated capsule body (10 capsules), 6,020 vertices /
+  12,000 triangles, 500 nodes, K=4, 1024x1024 image, 23-joint skeleton.
+* ``"stress"``: a body of about 100,000 vertices, 4,000 nodes, K=8, 2048x2048.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+from scipy import ndimage
+
+# ----------------------------------------------------------------------------
+# splitmix64 (Steele, Lea, Flood 2014) — used for the value-noise lattice
+# ----------------------------------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 output function applied element-wise to uint64 states."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(x, dtype=np.uint64) + _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _MIX1
+        z = (z ^ (z >> np.uint64(27))) * _MIX2
+        return z ^ (z >> np.uint64(31))
+
+
+def _lattice_value(ix, iy, iz, salt: int) -> np.ndarray:
+    """Uniform [0,1) value attached to an integer lattice point."""
+    with np.errstate(over="ignore"):
+        h = splitmix64(np.uint64(salt) * np.uint64(0x632BE59BD9B4E019))
+        h = splitmix64(h ^ ix.astype(np.int64).astype(np.uint64))
+        h = splitmix64(h ^ iy.astype(np.int64).astype(np.uint64))
+        h = splitmix64(h ^ iz.astype(np.int64).astype(np.uint64))
+    return (h >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# ----------------------------------------------------------------------------
+# Camera
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Camera:
+    """Static pinhole camera; camera space is world space (Sec. 3.2).
+
+    Pixel centres sit at integer coordinates; the principal point is the
+    image centre, (W-1)/2, (H-1)/2.  No distortion.
+    """
+
+    f: float
+    W: int
+    H: int
+
+    @property
+    def cx(self) -> float:
+        return (self.W - 1) * 0.5
+
+    @property
+    def cy(self) -> float:
+        return (self.H - 1) * 0.5
+
+
+# ----------------------------------------------------------------------------
+# Meshes
+# ----------------------------------------------------------------------------
+def _profile(radius: float, cyl_len: float, rings: int):
+    """(rho, y) of ``rings`` rings spaced evenly in arc length pole to pole."""
+    quarter = 0.5 * math.pi * radius
+    total = 2.0 * quarter + cyl_len
+    s = np.arange(1, rings + 1, dtype=np.float64) * (total / (rings + 1))
+    rho = np.empty(rings)
+    y = np.empty(rings)
+    for j, sj in enumerate(s):
+        if sj <= quarter:
+            phi = sj / radius
+            rho[j] = radius * math.sin(phi)
+            y[j] = -0.5 * cyl_len - radius * math.cos(phi)
+        elif sj <= quarter + cyl_len:
+            rho[j] = radius
+            y[j] = -0.5 * cyl_len + (sj - quarter)
+        else:
+            phi = (sj - quarter - cyl_len) / radius
+            rho[j] = radius * math.cos(phi)
+            y[j] = 0.5 * cyl_len + radius * math.sin(phi)
+    return rho, y, 0.5 * cyl_len + radius
+
+
+def capsule_mesh(radius: float, total_len: float, rings: int, segments: int):
+    """Closed capsule along +Y centred at the origin, outward-oriented.
+
+    Returns (V float64 (2+rings*segments, 3), F int64 (2*V-4, 3)).
+    ``total_len`` includes both hemispherical caps.
+    """
+    cyl = total_len - 2.0 * radius
+    assert cyl >= 0.0
+    rho, y, half = _profile(radius, cyl, rings)
+    ang = 2.0 * math.pi * np.arange(segments) / segments
+    ring_pts = np.stack(
+        [rho[:, None] * np.cos(ang)[None, :],
+         np.repeat(y[:, None], segments, axis=1),
+         rho[:, None] * np.sin(ang)[None, :]], axis=-1).reshape(-1, 3)
+    V = np.concatenate([[[0.0, -half, 0.0]], ring_pts, [[0.0, half, 0.0]]])
+    S = segments
+    top = 1 + rings * S
+    tris = []
+    for k in range(S):
+        tris.append((0, 1 + k, 1 + (k + 1) % S))
+    for j in range(rings - 1):
+        a0 = 1 + j * S
+        b0 = 1 + (j + 1) * S
+        for k in range(S):
+            k1 = (k + 1) % S
+            tris.append((a0 + k, b0 + k, b0 + k1))
+            tris.append((a0 + k, b0 + k1, a0 + k1))
+    last = 1 + (rings - 1) * S
+    for k in range(S):
+        tris.append((last + k, top, last + (k + 1) % S))
+    F = np.asarray(tris, dtype=np.int64)
+    # orient every triangle outward (normal away from the capsule axis segment)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    n = np.cross(b - a, c - a)
+    cen = (a + b + c) / 3.0
+    axis_pt = np.zeros_like(cen)
+    axis_pt[:, 1] = np.clip(cen[:, 1], -0.5 * cyl, 0.5 * cyl)
+    flip = np.einsum("ij,ij->i", n, cen - axis_pt) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return V, F
+
+
+def _frame_from_axis(d: np.ndarray) -> np.ndarray:
+    """Rotation taking +Y to unit direction d (columns: x', y'=d, z')."""
+    d = d / np.linalg.norm(d)
+    helper = np.array([0.0, 0.0, 1.0]) if abs(d[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    x = np.cross(d, helper)
+    x /= np.linalg.norm(x)
+    z = np.cross(x, d)
+    return np.stack([x, d, z], axis=1)
+
+
+# ----------------------------------------------------------------------------
+# Skeleton: 23 joints, 5 of them end sites; root 6 DOF + 17 ball joints x 3
+# ----------------------------------------------------------------------------
+SKELETON_NAMES = [
+    "pelvis", "spine", "chest", "neck", "head_top",
+    "l_clavicle", "l_shoulder", "l_elbow", "l_wrist", "l_hand_tip",
+    "r_clavicle", "r_shoulder", "r_elbow", "r_wrist", "r_hand_tip",
+    "l_hip", "l_knee", "l_ankle", "l_toe",
+    "r_hip", "r_knee", "r_ankle", "r_toe",
+]
+SKELETON_PARENTS = np.array(
+    [-1, 0, 1, 2, 3,
+     2, 5, 6, 7, 8,
+     2, 10, 11, 12, 13,
+     0, 15, 16, 17,
+     0, 19, 20, 21], dtype=np.int32)
+SKELETON_SITES = np.array([4, 9, 14, 18, 22])
+N_POSE_DOF = 57
+
+# Rest joint positions relative to the pelvis.  Camera convention: +Y points
+# down in the image, so the head is at negative Y.  T-pose, facing -Z.
+_REST_REL = np.array([
+    [0.00, 0.00, 0.00],    # pelvis
+    [0.00, -0.12, 0.00],   # spine
+    [0.00, -0.30, 0.00],   # chest
+    [0.00, -0.50, 0.00],   # neck
+    [0.00, -0.76, 0.00],   # head_top
+    [0.05, -0.46, 0.00],   # l_clavicle
+    [0.20, -0.46, 0.00],   # l_shoulder
+    [0.50, -0.46, 0.00],   # l_elbow
+    [0.76, -0.46, 0.00],   # l_wrist
+    [0.88, -0.46, 0.00],   # l_hand_tip
+    [-0.05, -0.46, 0.00],  # r_clavicle
+    [-0.20, -0.46, 0.00],  # r_shoulder
+    [-0.50, -0.46, 0.00],  # r_elbow
+    [-0.76, -0.46, 0.00],  # r_wrist
+    [-0.88, -0.46, 0.00],  # r_hand_tip
+    [0.10, 0.02, 0.00],    # l_hip
+    [0.10, 0.47, 0.00],    # l_knee
+    [0.10, 0.90, 0.00],    # l_ankle
+    [0.10, 0.95, -0.12],   # l_toe
+    [-0.10, 0.02, 0.00],   # r_hip
+    [-0.10, 0.47, 0.00],   # r_knee
+    [-0.10, 0.90, 0.00],   # r_ankle
+    [-0.10, 0.95, -0.12],  # r_toe
+])
+
+# capsule: (proximal joint, distal joint, radius, bones along the axis, skin(1)/cloth(0))
+# bones along the axis: list of (axial fraction where the bone starts, bone id)
+_CAPSULES = [
+    ("torso", 0, 3, 0.15, [(0.0, 0), (0.3, 1), (0.6, 2)], 0),
+    ("head", 3, 4, 0.10, [(0.0, 3)], 1),
+    ("l_upper_arm", 6, 7, 0.055, [(0.0, 6)], 0),
+    ("l_forearm", 7, 9, 0.045, [(0.0, 7), (0.7, 8)], 1),
+    ("r_upper_arm", 11, 12, 0.055, [(0.0, 11)], 0),
+    ("r_forearm", 12, 14, 0.045, [(0.0, 12), (0.7, 13)], 1),
+    ("l_thigh", 15, 16, 0.075, [(0.0, 15)], 0),
+    ("l_shin", 16, 18, 0.06, [(0.0, 16), (0.85, 17)], 1),
+    ("r_thigh", 19, 20, 0.075, [(0.0, 19)], 0),
+    ("r_shin", 20, 22, 0.06, [(0.0, 20), (0.85, 21)], 1),
+]
+
+
+def body_template(rings: int = 24, segments: int = 25,
+                  root=(0.0, -0.05, 3.0)):
+    """Articulated capsule body in its rest (T) pose, in world coordinates.
+
+    Returns a dict with V (N,3), F (T,3), per-vertex segment id, skin flag,
+    LBS binding (4 bones per vertex: ``skin_idx`` int, ``skin_w`` float, rows
+    summing to 1), rest joint positions ``joints_rest`` (23,3) and ``parents``.
+    """
+    root = np.asarray(root, dtype=np.float64)
+    joints = _REST_REL + root
+    Vs, Fs, seg, skin, sidx, sw = [], [], [], [], [], []
+    base = 0
+    for ci, (name, pa, pb, r, bones, is_skin) in enumerate(_CAPSULES):
+        A, B = joints[pa], joints[pb]
+        L = float(np.linalg.norm(B - A))
+        V, F = capsule_mesh(r, L + 2.0 * r, rings, segments)
+        R = _frame_from_axis(B - A)
+        Vw = (V @ R.T) + 0.5 * (A + B)
+        # axial coordinate in [0,1] from A to B (caps clamp)
+        t = np.clip(((Vw - A) @ (B - A)) / (L * L), 0.0, 1.0)
+        Vs.append(Vw)
+        Fs.append(F + base)
+        seg.append(np.full(len(Vw), ci, dtype=np.int32))
+        skin.append(np.full(len(Vw), is_skin, dtype=np.int32))
+        # LBS weights: own bone by axial fraction, blended across bone starts
+        # and into the parent bone near the proximal joint.
+        idx = np.zeros((len(Vw), 4), dtype=np.int32)
+        w = np.zeros((len(Vw), 4), dtype=np.float64)
+        starts = [b[0] for b in bones] + [1.0]
+        bone_ids = [b[1] for b in bones]
+        parent_bone = int(SKELETON_PARENTS[bone_ids[0]])
+        if parent_bone < 0:
+            parent_bone = bone_ids[0]
+        for vi in range(len(Vw)):
+            ti = t[vi]
+            k = 0
+            while k + 1 < len(bone_ids) and ti >= starts[k + 1]:
+                k += 1
+            own = bone_ids[k]
+            slots = [(own, 1.0)]
+            # blend with the next bone near its start
+            if k + 1 < len(bone_ids):
+                d = starts[k + 1] - ti
+                if d < 0.1:
+                    a = 0.5 * (1.0 - d / 0.1)
+                    slots = [(own, 1.0 - a), (bone_ids[k + 1], a)]
+            # blend with the previous bone (or parent) near this bone's start
+            prev = bone_ids[k - 1] if k > 0 else parent_bone
+            d = ti - starts[k]
+            if d < 0.1 and prev != own:
+                a = 0.5 * (1.0 - d / 0.1)
+                slots = [(b, ww * (1.0 - a)) for b, ww in slots] + [(prev, a)]
+            # fill to 4 slots (unused slots: own bone, weight 0)
+            while len(slots) < 4:
+                slots.append((own, 0.0))
+            for s, (b, ww) in enumerate(slots[:4]):
+                idx[vi, s] = b
+                w[vi, s] = ww
+        w /= w.sum(axis=1, keepdims=True)
+        sidx.append(idx)
+        sw.append(w)
+        base += len(Vw)
+    return dict(
+        V=np.concatenate(Vs), F=np.concatenate(Fs),
+        segment=np.concatenate(seg), skin=np.concatenate(skin),
+        skin_idx=np.concatenate(sidx), skin_w=np.concatenate(sw),
+        joints_rest=joints, parents=SKELETON_PARENTS.copy())
+
+
+# ----------------------------------------------------------------------------
+# Appearance and materials
+# ----------------------------------------------------------------------------
+def value_noise_albedo(V: np.ndarray, seed: int,
+                       freqs=(2.0, 4.0, 8.0), amps=(0.5, 0.25, 0.125)) -> np.ndarray:
+    """Per-vertex RGB from 3-octave value noise, rescaled to [0.1, 0.9].
+
+    Lattice values from splitmix64; trilinear interpolation with smoothstep
+    weights; octave frequencies in cycles per metre.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    out = np.zeros((len(V), 3))
+    for ch in range(3):
+        acc = np.zeros(len(V))
+        for o, (fr, am) in enumerate(zip(freqs, amps)):
+            p = V * fr
+            i0 = np.floor(p)
+            fr_ = p - i0
+            s = fr_ * fr_ * (3.0 - 2.0 * fr_)
+            i0 = i0.astype(np.int64)
+            val = np.zeros(len(V))
+            for dx in (0, 1):
+                wx = s[:, 0] if dx else 1.0 - s[:, 0]
+                for dy in (0, 1):
+                    wy = s[:, 1] if dy else 1.0 - s[:, 1]
+                    for dz in (0, 1):
+                        wz = s[:, 2] if dz else 1.0 - s[:, 2]
+                        lv = _lattice_value(i0[:, 0] + dx, i0[:, 1] + dy, i0[:, 2] + dz,
+                                            seed * 97 + o * 7 + ch)
+                        val += wx * wy * wz * lv
+            acc += am * val
+        lo, hi = acc.min(), acc.max()
+        out[:, ch] = 0.1 + 0.8 * (acc - lo) / max(hi - lo, 1e-12)
+    return out
+
+
+def half_split_material(V: np.ndarray, seed: int, skin=1.0, cloth=0.2) -> np.ndarray:
+    """Material weight 1.0 (skin) or 0.2 (cloth) by a seeded half-space."""
+    rng = np.random.default_rng(seed + 1000)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    c = V.mean(axis=0)
+    return np.where((V - c) @ u >= 0.0, skin, cloth)
+
+
+# ----------------------------------------------------------------------------
+# Rotations (FP64, for ground truth only)
+# ----------------------------------------------------------------------------
+def _rodrigues(aa: np.ndarray) -> np.ndarray:
+    aa = np.atleast_2d(aa)
+    th = np.linalg.norm(aa, axis=1)
+    out = np.tile(np.eye(3), (len(aa), 1, 1))
+    for i in range(len(aa)):
+        if th[i] < 1e-15:
+            continue
+        k = aa[i] / th[i]
+        Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        out[i] = np.eye(3) + math.sin(th[i]) * Kx + (1 - math.cos(th[i])) * (Kx @ Kx)
+    return out
+
+
+def smooth_deformation(V: np.ndarray, n_ctrl: int, sigma_rot: float,
+                       sigma_t: float, seed: int) -> Dict[str, np.ndarray]:
+    """Ground-truth non-rigid deformation on random control points.
+
+    ``n_ctrl`` control points are a seeded random subset of the vertices; each
+    gets a random rotation (axis-angle ~ N(0, sigma_rot) per axis) and
+    translation (~ N(0, sigma_t)).  The field is blended with normalised
+    Gaussian RBFs of width equal to the mean nearest-control-point spacing.
+    Returns the deformed vertices and the draws.
+    """
+    rng = np.random.default_rng(seed + 2000)
+    V = np.asarray(V, dtype=np.float64)
+    ids = np.sort(rng.choice(len(V), size=n_ctrl, replace=False))
+    c = V[ids]
+    aa = rng.normal(0.0, sigma_rot, size=(n_ctrl, 3))
+    tt = rng.normal(0.0, sigma_t, size=(n_ctrl, 3))
+    R = _rodrigues(aa)
+    d2c = ((c[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2c, np.inf)
+    rho = float(np.sqrt(d2c.min(axis=1)).mean()) if n_ctrl > 1 else 0.1
+    out = np.empty_like(V)
+    chunk = 8192
+    for s in range(0, len(V), chunk):
+        v = V[s:s + chunk]
+        d2 = ((v[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+        lw = -d2 / (2.0 * rho * rho)
+        lw -= lw.max(axis=1, keepdims=True)
+        phi = np.exp(lw)
+        phi /= phi.sum(axis=1, keepdims=True)
+        rel = v[:, None, :] - c[None, :, :]
+        moved = np.einsum("mij,nmj->nmi", R, rel) + c[None] + tt[None]
+        out[s:s + chunk] = np.einsum("nm,nmi->ni", phi, moved)
+    return dict(V=out, ctrl_ids=ids, aa=aa, t=tt, rho=rho)
+
+
+def pose_body(tpl: dict, root_R: np.ndarray, root_t: np.ndarray,
+              local_R: np.ndarray):
+    """Pose the rest body: global joint frames from local rotations, then
+    linear blend skinning of the rest vertices.  Returns (V_posed, joints)."""
+    J = tpl["joints_rest"]
+    par = tpl["parents"]
+    n = len(par)
+    G = np.zeros((n, 3, 3))
+    o = np.zeros((n, 3))
+    for j in range(n):
+        if par[j] < 0:
+            G[j] = root_R
+            o[j] = root_t
+        else:
+            p = par[j]
+            o[j] = o[p] + G[p] @ (J[j] - J[p])
+            G[j] = G[p] @ local_R[j]
+    V = tpl["V"]
+    out = np.zeros_like(V)
+    for s in range(4):
+        b = tpl["skin_idx"][:, s]
+        w = tpl["skin_w"][:, s]
+        moved = np.einsum("nij,nj->ni", G[b], V - J[b]) + o[b]
+        out += w[:, None] * moved
+    return out, o
+
+
+# ----------------------------------------------------------------------------
+# Rendering (FP64 floating-point coverage, perspective-correct colours)
+# ----------------------------------------------------------------------------
+def render(Vw: np.ndarray, F: np.ndarray, colors: np.ndarray, cam: Camera):
+    """Z-buffered rendering of a coloured mesh at pixel centres.
+
+    Coverage uses FP64 barycentrics (closed triangles); colours are
+    interpolated perspective-correctly.  Background is black.
+    Returns (rgb (H,W,3) float64, mask (H,W) bool).
+    """
+    Vw = np.asarray(Vw, dtype=np.float64)
+    X, Y, Z = Vw[:, 0], Vw[:, 1], Vw[:, 2]
+    ok = Z > 1e-3
+    Zs = np.where(ok, Z, 1.0)
+    u = cam.f * X / Zs + cam.cx
+    v = cam.f * Y / Zs + cam.cy
+    F = np.asarray(F, dtype=np.int64)
+    tri_ok = ok[F].all(axis=1)
+    Ft = F[tri_ok]
+    tu, tv, tz = u[Ft], v[Ft], Z[Ft]
+    x0 = np.clip(np.ceil(tu.min(1)), 0, cam.W - 1).astype(np.int64)
+    x1 = np.clip(np.floor(tu.max(1)), -1, cam.W - 1).astype(np.int64)
+    y0 = np.clip(np.ceil(tv.min(1)), 0, cam.H - 1).astype(np.int64)
+    y1 = np.clip(np.floor(tv.max(1)), -1, cam.H - 1).astype(np.int64)
+    bw = x1 - x0 + 1
+    bh = y1 - y0 + 1
+    keep = (bw > 0) & (bh > 0) & (tu.max(1) >= 0) & (tv.max(1) >= 0) \
+        & (tu.min(1) <= cam.W - 1) & (tv.min(1) <= cam.H - 1)
+    idx = np.nonzero(keep)[0]
+    order = idx[np.lexsort((bh[idx], bw[idx]))]
+    pix_all, z_all, col_all = [], [], []
+    chunk = 2048
+    for s in range(0, len(order), chunk):
+        ids = order[s:s + chunk]
+        mw, mh = int(bw[ids].max()), int(bh[ids].max())
+        gx = x0[ids, None, None] + np.arange(mw)[None, None, :]
+        gy = y0[ids, None, None] + np.arange(mh)[None, :, None]
+        gx = np.broadcast_to(gx, (len(ids), mh, mw))
+        gy = np.broadcast_to(gy, (len(ids), mh, mw))
+        inb = (gx <= x1[ids, None, None]) & (gy <= y1[ids, None, None])
+        ax, ay = tu[ids, 0, None, None], tv[ids, 0, None, None]
+        bx, by = tu[ids, 1, None, None], tv[ids, 1, None, None]
+        cx, cy = tu[ids, 2, None, None], tv[ids, 2, None, None]
+        area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+        w0 = (bx - gx) * (cy - gy) - (by - gy) * (cx - gx)
+        w1 = (cx - gx) * (ay - gy) - (cy - gy) * (ax - gx)
+        w2 = (ax - gx) * (by - gy) - (ay - gy) * (bx - gx)
+        nz = np.abs(area) > 1e-18
+        sa = np.where(nz, area, 1.0)
+        b0, b1, b2 = w0 / sa, w1 / sa, w2 / sa
+        inside = inb & nz & (b0 >= 0) & (b1 >= 0) & (b2 >= 0)
+        zi = tz[ids]
+        invz = b0 / zi[:, 0, None, None] + b1 / zi[:, 1, None, None] + b2 / zi[:, 2, None, None]
+        depth = 1.0 / np.where(inside, invz, 1.0)
+        cc = colors[Ft[ids]]  # (n,3 verts,3 ch)
+        col = (b0[..., None] * cc[:, None, None, 0, :] / zi[:, 0, None, None, None]
+               + b1[..., None] * cc[:, None, None, 1, :] / zi[:, 1, None, None, None]
+               + b2[..., None] * cc[:, None, None, 2, :] / zi[:, 2, None, None, None]) \
+            * depth[..., None]
+        m = inside
+        pix_all.append((gy[m] * cam.W + gx[m]))
+        z_all.append(depth[m])
+        col_all.append(col[m])
+    rgb = np.zeros((cam.H * cam.W, 3))
+    mask = np.zeros(cam.H * cam.W, dtype=bool)
+    if pix_all:
+        pix = np.concatenate(pix_all)
+        if len(pix):
+            z = np.concatenate(z_all)
+            col = np.concatenate(col_all)
+            o = np.lexsort((z, pix))
+            pix_s = pix[o]
+            first = np.ones(len(pix_s), dtype=bool)
+            first[1:] = pix_s[1:] != pix_s[:-1]
+            sel = o[first]
+            rgb[pix[sel]] = col[sel]
+            mask[pix[sel]] = True
+    return rgb.reshape(cam.H, cam.W, 3), mask.reshape(cam.H, cam.W)
+
+
+def contour_distance_transform(mask: np.ndarray) -> np.ndarray:
+    """Euclidean distance (pixels) from each pixel centre to the nearest
+    contour pixel: a foreground pixel with a 4-neighbour in the background or
+    on the image border.  Zero on contour pixels.  An empty mask gives zeros.
+    """
+    m = np.asarray(mask, dtype=bool)
+    pad = np.pad(m, 1, constant_values=False)
+    interior = pad[1:-1, 1:-1] & pad[:-2, 1:-1] & pad[2:, 1:-1] & pad[1:-1, :-2] & pad[1:-1, 2:]
+    contour = m & ~interior
+    if not contour.any():
+        return np.zeros(m.shape, dtype=np.float64)
+    return ndimage.distance_transform_edt(~contour)
+
+
+# ----------------------------------------------------------------------------
+# Scenes
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Scene:
+    """Everything one capture needs, as FP32/int32 arrays ready for upload."""
+
+    name: str
+    cam: Camera
+    V: np.ndarray          # (N,3) f32 rest template
+    F: np.ndarray          # (T,3) i32
+    albedo: np.ndarray     # (N,3) f32
+    material: np.ndarray   # (N,) f32
+    rgb: np.ndarray        # (H,W,3) f32 target frame
+    dt: np.ndarray         # (H,W) f32 silhouette distance transform
+    mask: np.ndarray       # (H,W) bool
+    n_nodes: int
+    K: int
+    n_gn: int
+    n_pcg: int
+    weights: tuple         # (w_photo, w_sil, w_arap)
+    V_gt: np.ndarray       # (N,3) f64 ground-truth surface
+    skeleton: Optional[dict] = None   # body scenes only
+    joints2d: Optional[np.ndarray] = None
+    joints3d: Optional[np.ndarray] = None
+    pose_init: Optional[np.ndarray] = None   # (57,) f32
+    n_gn_pose: int = 5
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return len(self.V)
+
+
+def _finish_frame(V_target, F, albedo, cam, rng, noise=0.01):
+    rgb, mask = render(V_target, F, albedo, cam)
+    rgb = rgb + rng.normal(0.0, noise, size=rgb.shape)
+    dt = contour_distance_transform(mask)
+    return rgb.astype(np.float32), dt.astype(np.float32), mask
+
+
+def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
+    """Build one seeded capture.
+
+    ``tiny``   capsule (1,002 v / 2,000 t), 64 nodes K=4, 128^2, f=150,
+               GT rotations sigma 0.05 rad, translations 0.01 m, 5 GN x 20 PCG.
+    ``body``   articulated body (6,020 v / 12,000 t), 500 nodes K=4, 1024^2,
+               f=1200, GT pose + non-rigid rotations sigma 0.1 rad,
+               2D joints with 2 px noise, 3D joints with 1 cm noise,
+               10 GN x 40 PCG after a 5-step pose fit.
+    ``stress`` body of ~100k vertices, 4,000 nodes, K=8, 2048^2, f=2400.
+    Keyword overrides: rings, segments, n_nodes, K, side, n_gn, n_pcg.
+    """
+    if name == "tiny":
+        seed = 0 if seed is None else seed
+        rng = np.random.default_rng(seed)
+        V, F = capsule_mesh(0.3, 1.0, over.get("rings", 40), over.get("segments", 25))
+        V = V + np.array([0.0, 0.0, 3.0])
+        side = over.get("side", 128)
+        cam = Camera(f=150.0 * side / 128.0, W=side, H=side)
+        V32 = V.astype(np.float32)
+        albedo = value_noise_albedo(V32.astype(np.float64), seed)
+        material = half_split_material(V32.astype(np.float64), seed)
+        n_nodes = over.get("n_nodes", 64)
+        gt = smooth_deformation(V32.astype(np.float64), n_nodes, 0.05, 0.01, seed)
+        rgb, dt, mask = _finish_frame(gt["V"], F, albedo, cam, rng)
+        return Scene("tiny", cam, V32, F.astype(np.int32), albedo.astype(np.float32),
+                     material.astype(np.float32), rgb, dt, mask, n_nodes,
+                     over.get("K", 4), over.get("n_gn", 5), over.get("n_pcg", 20),
+                     (1.0, 0.1, 10.0), gt["V"], meta=dict(seed=seed))
+    if name in ("body", "stress"):
+        stress = name == "stress"
+        seed = (1 if not stress else 4) if seed is None else seed
+        rng = np.random.default_rng(seed)
+        rings = over.get("rings", 24 if not stress else 100)
+        segs = over.get("segments", 25 if not stress else 100)
+        tpl = body_template(rings, segs)
+        V = tpl["V"]
+        F = tpl["F"]
+        side = over.get("side", 1024 if not stress else 2048)
+        cam = Camera(f=1200.0 * side / 1024.0, W=side, H=side)
+        V32 = V.astype(np.float32)
+        albedo = value_noise_albedo(V32.astype(np.float64), seed)
+        material = np.where(tpl["skin"] > 0, 1.0, 0.2)
+        n_nodes = over.get("n_nodes", 500 if not stress else 4000)
+        # ground-truth pose: small global rotation, joint rotations ~N(0, 0.2)
+        root_aa = rng.normal(0.0, 0.05, size=3)
+        root_t = tpl["joints_rest"][0] + rng.normal(0.0, 0.03, size=3)
+        local = _rodrigues(rng.normal(0.0, over.get("sigma_pose", 0.2), size=(23, 3)))
+        local[SKELETON_SITES] = np.eye(3)
+        local[0] = np.eye(3)
+        Vp, joints_gt = pose_body(dict(tpl, V=V32.astype(np.float64)),
+                                  _rodrigues(root_aa)[0], root_t, local)
+        gt = smooth_deformation(Vp, n_nodes, over.get("sigma_nonrigid", 0.1), 0.01, seed)
+        rgb, dt, mask = _finish_frame(gt["V"], F, albedo, cam, rng)
+        j3 = joints_gt + rng.normal(0.0, 0.01, size=joints_gt.shape)
+        u = cam.f * joints_gt[:, 0] / joints_gt[:, 2] + cam.cx
+        v = cam.f * joints_gt[:, 1] / joints_gt[:, 2] + cam.cy
+        j2 = np.stack([u, v], 1) + rng.normal(0.0, 2.0, size=(23, 2))
+        pose0 = np.zeros(N_POSE_DOF)
+        pose0[3:6] = root_t + rng.normal(0.0, 0.02, size=3)
+        skel = dict(parents=tpl["parents"], joints_rest=tpl["joints_rest"].astype(np.float32),
+                    skin_idx=tpl["skin_idx"].astype(np.int32),
+                    skin_w=tpl["skin_w"].astype(np.float32),
+                    segment=tpl["segment"])
+        return Scene(name, cam, V32, F.astype(np.int32), albedo.astype(np.float32),
+                     material.astype(np.float32), rgb, dt, mask, n_nodes,
+                     over.get("K", 4 if not stress else 8),
+                     over.get("n_gn", 10), over.get("n_pcg", 40), (1.0, 0.1, 10.0),
+                     gt["V"], skeleton=skel, joints2d=j2.astype(np.float32),
+                     joints3d=j3.astype(np.float32), pose_init=pose0.astype(np.float32),
+                     meta=dict(seed=seed, root_aa=root_aa, root_t=root_t,
+                               joints_gt=joints_gt, V_posed=Vp))
+    raise ValueError(f"unknown scene {name!r}")
+
+
+def make_batch(count: int = 64, seed: int = 2, n_min=2000, n_max=20000,
+               side_min=256, side_max=1024) -> List[Scene]:
+    """Uneven captures: vertices log-uniform in [n_min, n_max] (articulated
+    capsule bodies with a variable ring count), nodes = vertices / 12, square
+    images log-uniform in [side_min, side_max] rounded to a multiple of 32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(count):
+        n_target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        rings = max(4, int(round((n_target / 10.0 - 2.0) / 25.0)))
+        side = int(round(math.exp(rng.uniform(math.log(side_min), math.log(side_max))) / 32.0)) * 32
+        n_vert = 10 * (2 + rings * 25)
+        out.append(make_scene("body", seed=1000 + seed * 100 + c, rings=rings,
+                              segments=25, side=side, n_nodes=max(8, n_vert // 12)))
+    return out
