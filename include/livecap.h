@@ -1,0 +1,227 @@
+/*
+ * livecap.h — C ABI of the GB300 (sm_103a) Gauss-Newton hot path of LiveCap
+ * ("Real-time Human Performance Capture from Monocular Video", Habermann et
+ * al., arXiv 1810.02648).
+ *
+ * Conventions for every call
+ * --------------------------
+ *  - Every call returns an lc_status.  The first error is kept in the context
+ *    and its message is returned by lc_last_error(); later calls keep
+ *    returning their own status.  Device-side failures (a pivot <= 0 in the
+ *    pose Cholesky, a non-finite input) are reported through a status word
+ *    that the next synchronising call reads.
+ *  - Array arguments are plain pointers that may point to host memory or to
+ *    CUDA device memory of the context's device; the library tells them apart
+ *    with cudaPointerGetAttributes.  The caller owns every pointer it passes.
+ *    Uploads copy into library-owned device memory; read-backs copy out.
+ *    Shapes are given per argument; all arrays are dense, row-major, with no
+ *    padding.
+ *  - Work is enqueued on the context's stream (the one given to lc_create).
+ *    Calls that return data to host memory synchronise that stream;
+ *    calls that only enqueue device work return without waiting.
+ *  - Calls made in the wrong order return LC_ERR_STATE (for instance a solve
+ *    before a template, graph and frame exist).
+ *
+ * Geometry conventions: camera space is world space (Sec. 3.2 of the paper);
+ * pinhole projection u = f X/Z + cx, v = f Y/Z + cy with pixel centres on
+ * integer coordinates; images are H rows of W pixels.
+ */
+#ifndef LIVECAP_H
+#define LIVECAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lc_ctx lc_ctx;
+
+typedef enum {
+    LC_OK = 0,
+    LC_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad mesh) */
+    LC_ERR_STATE = -2,    /* call out of order */
+    LC_ERR_CUDA = -3,     /* CUDA runtime error (message in lc_last_error) */
+    LC_ERR_NUMERIC = -4,  /* non-positive pivot or non-finite value */
+    LC_ERR_TIMEOUT = -5,  /* a bounded device-side wait ran out */
+    LC_ERR_OOM = -6       /* device allocation failed */
+} lc_status;
+
+/* Solver settings.
+ * Non-rigid energy weights (Sec. 3.4, E_photo / E_silhouette, plus the
+ * embedded-graph ARAP regulariser) and fixed iteration counts of the
+ * Gauss-Newton / PCG solver (Sec. 4: no damping, fixed counts).  eps_vis is
+ * the depth tolerance of the visibility test in metres.  The lambda_* are the
+ * pose-stage weights of Sec. 3.3 (defaults from the paper's parameter list in
+ * Sec. 5: lambda_2D = 460, lambda_3D = 28, lambda_silhouette = 200). */
+typedef struct {
+    float w_photo;      /* default 1 */
+    float w_sil;        /* default 0.1 */
+    float w_arap;       /* default 10 */
+    int n_gn;           /* Gauss-Newton steps of the non-rigid stage, <= LC_MAX_GN */
+    int n_pcg;          /* PCG iterations per step */
+    float eps_vis;      /* default 1e-2 m */
+    float lambda_2d;
+    float lambda_3d;
+    float lambda_sil;
+    int n_gn_pose;      /* Gauss-Newton steps of the pose stage, default 5 */
+} lc_params;
+
+#define LC_MAX_GN 64
+
+/* Per-solve statistics (FP64 energies: sums of squared residuals). */
+typedef struct {
+    double e_photo, e_sil, e_arap, e_total;  /* after the last update */
+    double e_gn[LC_MAX_GN];                  /* total energy at each linearisation */
+    double step_norm[LC_MAX_GN];             /* ||delta|| of each step */
+    int pcg_iters[LC_MAX_GN];                /* PCG iterations actually run */
+    int n_gn_done;
+    int n_visible;                           /* |V| photometric vertices */
+    int n_boundary;                          /* |B| contour vertices */
+    int n_boundary_neg;                      /* contour vertices with b_i = -1 */
+    int pcg_breakdowns;                      /* steps whose PCG stopped on p^T A p <= 0 */
+} lc_solve_stats;
+
+/* Vertex flag bits returned by lc_read_visibility / lc_read_back. */
+#define LC_FLAG_VISIBLE 1u   /* vertex in V (depth test passed) */
+#define LC_FLAG_ONSIL 2u     /* vertex on a silhouette edge */
+#define LC_FLAG_INB 4u       /* vertex in the contour set B */
+#define LC_FLAG_BNEG 8u      /* b_i = -1 */
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * that all work of the context is enqueued on.  0 = the context creates and
+ * owns a non-blocking stream (the solve is captured as a CUDA graph, which
+ * the legacy default stream does not allow).  *out receives the context. */
+lc_status lc_create(lc_ctx **out, int device, void *cuda_stream);
+/* Free the context and all its device memory.  Null is accepted. */
+lc_status lc_destroy(lc_ctx *ctx);
+/* Message of the first error seen by the context ("" if none). */
+const char *lc_last_error(const lc_ctx *ctx);
+/* Fill *p with the defaults listed at lc_params. */
+lc_status lc_params_default(lc_params *p);
+/* Replace the solver settings.  n_gn in [1, LC_MAX_GN], n_pcg >= 1. */
+lc_status lc_set_params(lc_ctx *ctx, const lc_params *p);
+/* Static pinhole camera (Sec. 3.2): focal length and principal point in
+ * pixels, image size W x H (1 <= W, H <= 16384). */
+lc_status lc_set_camera(lc_ctx *ctx, float f, float cx, float cy, int W, int H);
+
+/* ---- template and graph --------------------------------------------------- */
+
+/* Template mesh V^hat (Sec. 3.1): V N x 3 positions (metres), tris F x 3
+ * vertex indices forming a closed or open 2-manifold (an edge shared by more
+ * than two triangles is rejected with LC_ERR_ARG), albedo N x 3 in [0,1]
+ * (per-vertex colours C), material N per-vertex non-rigidity weights
+ * (Tab. 1; averaged per edge, Sec. 3.1).  Resets graph, skeleton and pose. */
+lc_status lc_upload_template(lc_ctx *ctx, const float *V, int N, const int32_t *tris, int F,
+                             const float *albedo, const float *material);
+
+/* Build the embedded deformation graph on the device: n_nodes nodes by
+ * farthest-point sampling (start vertex 0, lowest index on ties), each vertex
+ * bound to its K nearest nodes (1 <= K <= 8, n_nodes >= K+1) with weights
+ * (1 - d/d_max)^2 normalised, d_max the distance to the (K+1)-th nearest
+ * node, and node edges to the 4 nearest other nodes (symmetrised) weighted by
+ * the mean of the two nodes' material weights.  Node parameters are reset to
+ * the identity. */
+lc_status lc_build_graph(lc_ctx *ctx, int n_nodes, int K);
+
+/* Copy the graph out.  node_vid n, bind_idx N x K, bind_w N x K,
+ * edge_off n+1 (CSR offsets of the directed edges by source node),
+ * edge_dst E, edge_s E.  Any pointer may be null to skip it; *n_edges (if
+ * not null) receives E.  Synchronises. */
+lc_status lc_read_graph(lc_ctx *ctx, int32_t *node_vid, int32_t *bind_idx, float *bind_w,
+                        int32_t *edge_off, int32_t *edge_dst, float *edge_s, int *n_edges);
+
+/* Node parameters: rotations node_R n x 9 (row-major 3x3) and translations
+ * node_t n x 3.  Both null = reset to the identity. */
+lc_status lc_set_node_params(lc_ctx *ctx, const float *node_R, const float *node_t);
+
+/* ---- frame ---------------------------------------------------------------- */
+
+/* One input frame (Sec. 3.2): rgb H x W x 3 in [0,1], dt H x W the Euclidean
+ * distance transform of the foreground silhouette in pixels, mask H x W
+ * foreground flags (non-zero = foreground).  joints2d (J x 2 pixels) and
+ * joints3d (J x 3 metres) are the pose stage's detections (Sec. 3.3); both
+ * may be null when no skeleton is used.  The images are repacked on the
+ * device into one float4 (r, g, b, dt) per pixel. */
+lc_status lc_upload_frame(lc_ctx *ctx, const float *rgb, const float *dt, const uint8_t *mask,
+                          const float *joints2d, const float *joints3d);
+
+/* ---- solve ---------------------------------------------------------------- */
+
+/* Non-rigid stage (Sec. 3.4 and Sec. 4): from the current node parameters,
+ * warp, find visibility / contour set / b_i once, then n_gn Gauss-Newton
+ * steps, each solving J^T J delta = -J^T F by n_pcg iterations of
+ * Jacobi-preconditioned CG from zero, then R_k <- Exp(d_omega_k) R_k,
+ * t_k += d_t_k.  The whole sequence runs as one captured CUDA graph.
+ * `stats` may be null; when given, the call synchronises and fills it. */
+lc_status lc_solve_nonrigid(lc_ctx *ctx, lc_solve_stats *stats);
+
+/* Read the result.  node_R n x 9, node_t n x 3, V_out N x 3 (warped
+ * vertices), flags N (LC_FLAG_* bits of the last visibility pass),
+ * pose N_DOF (pose parameters, see lc_upload_skeleton).  Null pointers are
+ * skipped.  Synchronises. */
+lc_status lc_read_back(lc_ctx *ctx, float *node_R, float *node_t, float *V_out, uint8_t *flags,
+                       float *pose);
+
+/* ---- inspection (each step of the solve, callable on its own) ------------- */
+
+/* Warp with the current node parameters and recompute visibility, contour set
+ * and b_i.  Enqueue only. */
+lc_status lc_compute_visibility(lc_ctx *ctx);
+
+/* zbuf H x W 64-bit keys (bits of the FP32 depth << 32 | triangle id; all
+ * ones = empty), flags N, uv N x 2 projected positions of the visibility
+ * pass.  Null pointers are skipped.  Synchronises. */
+lc_status lc_read_visibility(lc_ctx *ctx, uint64_t *zbuf, uint8_t *flags, float *uv);
+
+/* Linearise at the current node parameters (visibility must exist): warped
+ * vertices v_warp N x 3, projections uv N x 2, per-vertex residuals
+ * r_photo N x 3 (sqrt(w_p)(I - C), zero where inactive) and r_sil N
+ * (sqrt(w_s) DT), per-vertex normal blocks H N x 6 (h00 h01 h02 h11 h12 h22
+ * of A_i^T A_i, A_i = d r_i / d v'_i with the b_i sign) and e N x 3
+ * (A_i^T r_i), energy 3 (photo, sil, arap).  Null pointers are skipped.
+ * Synchronises. */
+lc_status lc_eval_linearization(lc_ctx *ctx, float *v_warp, float *uv, float *r_photo,
+                                float *r_sil, float *H, float *e, double *energy);
+
+/* At the current linearisation: rhs 6n = -J^T F and diag 6n = diag(J^T J),
+ * node-major (d_omega_x, d_omega_y, d_omega_z, d_t_x, d_t_y, d_t_z).
+ * Synchronises. */
+lc_status lc_eval_gradient(lc_ctx *ctx, float *rhs, float *diag);
+
+/* out 6n = J^T J p at the current linearisation, p 6n (same layout).
+ * Synchronises. */
+lc_status lc_apply_jtj(lc_ctx *ctx, const float *p, float *out);
+
+/* delta 6n = the PCG solution of J^T J delta = -J^T F at the current
+ * linearisation (n_pcg iterations); iters (nullable) receives the number of
+ * iterations run.  Node parameters are not changed.  Synchronises. */
+lc_status lc_solve_linear(lc_ctx *ctx, float *delta, int *iters);
+
+/* ---- skeletal pose stage (Sec. 3.3) --------------------------------------- */
+
+/* Kinematic skeleton: J joints with parents (parent[0] = -1 is the root,
+ * parents precede children), rest joint positions joints_rest J x 3, a DOF
+ * flag per joint (dof[j] = 1: ball joint with 3 Euler angles XYZ; 0: fixed
+ * end site; the root always has 6 DOF: left-multiplied rotation increment
+ * and translation), and the LBS binding skin_idx N x 4 / skin_w N x 4.
+ * The pose vector is [root axis-angle 3, root translation 3, 3 Euler angles
+ * per DOF joint in joint order]; N_DOF = 6 + 3 * (number of DOF joints
+ * excluding the root).  J <= 64. */
+lc_status lc_upload_skeleton(lc_ctx *ctx, int J, const int32_t *parents, const float *joints_rest,
+                             const uint8_t *dof, const int32_t *skin_idx, const float *skin_w);
+/* Set the pose vector (N_DOF values) the next pose solve starts from. */
+lc_status lc_set_pose(lc_ctx *ctx, const float *pose);
+/* Pose stage: n_gn_pose Gauss-Newton steps on the 2D joint, 3D joint and
+ * silhouette terms, dense normal equations solved by an FP64 Cholesky
+ * factorisation on the device.  Afterwards the skinned mesh becomes the rest
+ * geometry of the non-rigid stage.  `stats` may be null (else synchronises;
+ * e_gn / step_norm hold the pose stage's history). */
+lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIVECAP_H */

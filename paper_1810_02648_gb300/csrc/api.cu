@@ -1,0 +1,829 @@
+// C ABI of the livecap library: context, uploads, graph build, the captured
+// non-rigid solve and the inspection calls.  See include/livecap.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "lc_context.h"
+
+using namespace lc;
+
+// ---------------------------------------------------------------------------
+// error helpers
+// ---------------------------------------------------------------------------
+lc_status lc_ctx::fail(lc_status st, const char* fmt, ...) {
+    if (err.empty()) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+    }
+    return st;
+}
+
+lc_status lc_ctx::cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LC_OK;
+    return fail(e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* lc_ctx::alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cuda(e, "cudaMalloc");
+        return nullptr;
+    }
+    owned.push_back(p);
+    return p;
+}
+
+void lc_ctx::release(void* p) {
+    if (!p) return;
+    auto it = std::find(owned.begin(), owned.end(), p);
+    if (it != owned.end()) {
+        cudaFree(p);
+        owned.erase(it);
+    }
+}
+
+bool lc_ctx::is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lc_status lc_ctx::copy_to_host(void* dst, const void* src_dev, size_t bytes) {
+    lc_status s = cuda(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, stream), "copy out");
+    if (s != LC_OK) return s;
+    return cuda(cudaStreamSynchronize(stream), "synchronize");
+}
+
+// copy `bytes` from a host-or-device pointer into host memory
+lc_status lc_ctx::fetch(void* dst_host, const void* src_any, size_t bytes) {
+    if (bytes == 0) return LC_OK;
+    return copy_to_host(dst_host, src_any, bytes);
+}
+
+// write a host staging buffer to a host-or-device destination
+lc_status lc_ctx::deliver(void* dst_any, const void* src_host, size_t bytes) {
+    if (bytes == 0) return LC_OK;
+    lc_status s = cuda(cudaMemcpyAsync(dst_any, src_host, bytes, cudaMemcpyDefault, stream), "copy");
+    if (s != LC_OK) return s;
+    return cuda(cudaStreamSynchronize(stream), "synchronize");
+}
+
+lc_status lc_ctx::sync_desc() {
+    lc_status s = cuda(cudaMemcpyAsync(dC, &hC, sizeof(CapDesc), cudaMemcpyHostToDevice, stream), "descriptor");
+    if (s != LC_OK) return s;
+    // the host copy must stay unchanged until the copy is done
+    return cuda(cudaStreamSynchronize(stream), "synchronize");
+}
+
+void lc_ctx::drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" lc_status lc_params_default(lc_params* p) {
+    if (!p) return LC_ERR_ARG;
+    p->w_photo = 1.0f;
+    p->w_sil = 0.1f;
+    p->w_arap = 10.0f;
+    p->n_gn = 5;
+    p->n_pcg = 20;
+    p->eps_vis = 1e-2f;
+    p->lambda_2d = 460.0f;
+    p->lambda_3d = 28.0f;
+    p->lambda_sil = 200.0f;
+    p->n_gn_pose = 5;
+    return LC_OK;
+}
+
+extern "C" lc_status lc_create(lc_ctx** out, int device, void* cuda_stream) {
+    if (!out) return LC_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return LC_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LC_ERR_CUDA;
+    lc_ctx* c = new lc_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (!c->stream) {
+        // the solve is captured into a CUDA graph, which the legacy default
+        // stream does not allow: use a stream of our own
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return LC_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    lc_params_default(&c->params);
+    memset(&c->hC, 0, sizeof(CapDesc));
+    c->dC = (CapDesc*)c->alloc(sizeof(CapDesc));
+    c->hC.sc = (Scalars*)c->alloc(sizeof(Scalars));
+    c->hC.counters = (unsigned*)c->alloc(sizeof(unsigned) * CNT_N);
+    c->hC.hist = (double*)c->alloc(sizeof(double) * 2 * (LC_MAX_GN + 1));
+    c->hC.hist_iters = (int*)c->alloc(sizeof(int) * (LC_MAX_GN + 2));
+    if (!c->dC || !c->hC.sc || !c->hC.counters || !c->hC.hist || !c->hC.hist_iters) {
+        lc_destroy(c);
+        return LC_ERR_OOM;
+    }
+    cudaMemsetAsync(c->hC.sc, 0, sizeof(Scalars), c->stream);
+    cudaMemsetAsync(c->hC.counters, 0, sizeof(unsigned) * CNT_N, c->stream);
+    c->apply_params();
+    if (c->sync_desc() != LC_OK) {
+        lc_destroy(c);
+        return LC_ERR_CUDA;
+    }
+    *out = c;
+    return LC_OK;
+}
+
+extern "C" lc_status lc_destroy(lc_ctx* ctx) {
+    if (!ctx) return LC_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->drop_graph();
+    ctx->pose_release();
+    for (void* p : ctx->owned) cudaFree(p);
+    ctx->owned.clear();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LC_OK;
+}
+
+extern "C" const char* lc_last_error(const lc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void lc_ctx::apply_params() {
+    hC.w_photo = params.w_photo;
+    hC.w_sil = params.w_sil;
+    hC.w_arap = params.w_arap;
+    hC.eps_vis = params.eps_vis;
+}
+
+extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
+    if (!ctx || !p) return LC_ERR_ARG;
+    if (p->n_gn < 1 || p->n_gn > LC_MAX_GN || p->n_pcg < 1 || p->n_gn_pose < 1 || p->n_gn_pose > LC_MAX_GN ||
+        !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f))
+        return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
+    cudaSetDevice(ctx->device);
+    if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg) ctx->drop_graph();
+    ctx->params = *p;
+    ctx->apply_params();
+    return ctx->sync_desc();
+}
+
+extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int W, int H) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!(f > 0.f) || W < 1 || H < 1 || W > 16384 || H > 16384)
+        return ctx->fail(LC_ERR_ARG, "lc_set_camera: bad camera");
+    cudaSetDevice(ctx->device);
+    if (W != ctx->hC.W || H != ctx->hC.H) {
+        ctx->release((void*)ctx->hC.img);
+        ctx->release((void*)ctx->hC.mask);
+        ctx->release(ctx->hC.zbuf);
+        ctx->release(ctx->stage_rgb);
+        ctx->release(ctx->stage_dt);
+        ctx->release(ctx->stage_mask);
+        const size_t P = (size_t)W * H;
+        ctx->hC.img = (const float4*)ctx->alloc(sizeof(float4) * P);
+        ctx->hC.mask = (const uint8_t*)ctx->alloc(P);
+        ctx->hC.zbuf = (unsigned long long*)ctx->alloc(sizeof(unsigned long long) * P);
+        ctx->stage_rgb = (float*)ctx->alloc(sizeof(float) * 3 * P);
+        ctx->stage_dt = (float*)ctx->alloc(sizeof(float) * P);
+        ctx->stage_mask = (uint8_t*)ctx->alloc(P);
+        if (!ctx->hC.img || !ctx->hC.mask || !ctx->hC.zbuf || !ctx->stage_rgb || !ctx->stage_dt || !ctx->stage_mask)
+            return LC_ERR_OOM;
+        ctx->has_frame = false;
+        ctx->has_vis = false;
+        ctx->drop_graph();
+    }
+    ctx->hC.f = f;
+    ctx->hC.cx = cx;
+    ctx->hC.cy = cy;
+    ctx->hC.W = W;
+    ctx->hC.H = H;
+    ctx->has_camera = true;
+    return ctx->sync_desc();
+}
+
+// ---------------------------------------------------------------------------
+// template
+// ---------------------------------------------------------------------------
+template <typename T>
+static lc_status host_copy(lc_ctx* ctx, std::vector<T>& dst, const T* src, size_t count) {
+    dst.resize(count);
+    return ctx->fetch(dst.data(), src, sizeof(T) * count);
+}
+
+extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, const int32_t* tris, int F,
+                                        const float* albedo, const float* material) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!V || !tris || !albedo || !material || N < 1 || F < 1)
+        return ctx->fail(LC_ERR_ARG, "lc_upload_template: null array or empty mesh");
+    cudaSetDevice(ctx->device);
+    std::vector<float> hv, ha, hm;
+    std::vector<int32_t> ht;
+    lc_status s;
+    if ((s = host_copy(ctx, hv, V, (size_t)3 * N)) != LC_OK) return s;
+    if ((s = host_copy(ctx, ht, tris, (size_t)3 * F)) != LC_OK) return s;
+    if ((s = host_copy(ctx, ha, albedo, (size_t)3 * N)) != LC_OK) return s;
+    if ((s = host_copy(ctx, hm, material, (size_t)N)) != LC_OK) return s;
+    for (int i = 0; i < 3 * F; ++i)
+        if (ht[i] < 0 || ht[i] >= N) return ctx->fail(LC_ERR_ARG, "lc_upload_template: triangle index out of range");
+    for (int i = 0; i < 3 * N; ++i)
+        if (!std::isfinite(hv[i])) return ctx->fail(LC_ERR_ARG, "lc_upload_template: non-finite vertex");
+    // mesh topology: vertex -> triangle CSR (ascending ids) and edges with two triangles
+    std::vector<int> vt_off(N + 1, 0), vt_tri((size_t)3 * F);
+    for (int i = 0; i < 3 * F; ++i) vt_off[ht[i] + 1]++;
+    for (int i = 0; i < N; ++i) vt_off[i + 1] += vt_off[i];
+    {
+        std::vector<int> fill(vt_off.begin(), vt_off.end() - 1);
+        for (int t = 0; t < F; ++t)
+            for (int c = 0; c < 3; ++c) vt_tri[fill[ht[3 * t + c]]++] = t;   // t ascending per vertex
+    }
+    struct HalfEdge {
+        int lo, hi, t;
+    };
+    std::vector<HalfEdge> he((size_t)3 * F);
+    for (int t = 0; t < F; ++t)
+        for (int c = 0; c < 3; ++c) {
+            int a = ht[3 * t + c], b = ht[3 * t + (c + 1) % 3];
+            he[3 * t + c] = {std::min(a, b), std::max(a, b), t};
+        }
+    std::sort(he.begin(), he.end(), [](const HalfEdge& x, const HalfEdge& y) {
+        return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.t < y.t);
+    });
+    std::vector<int4> medges;
+    for (size_t i = 0; i < he.size();) {
+        size_t j = i;
+        while (j < he.size() && he[j].lo == he[i].lo && he[j].hi == he[i].hi) ++j;
+        if (j - i > 2) return ctx->fail(LC_ERR_ARG, "lc_upload_template: non-manifold edge (%d,%d)", he[i].lo, he[i].hi);
+        medges.push_back(make_int4(he[i].lo, he[i].hi, he[i].t, j - i == 2 ? he[i + 1].t : -1));
+        i = j;
+    }
+    // release the old template and everything built on it
+    ctx->free_template();
+    std::vector<float4> v4(N), a4(N);
+    std::vector<int4> t4(F);
+    for (int i = 0; i < N; ++i) {
+        v4[i] = make_float4(hv[3 * i], hv[3 * i + 1], hv[3 * i + 2], 0.f);
+        a4[i] = make_float4(ha[3 * i], ha[3 * i + 1], ha[3 * i + 2], 0.f);
+    }
+    for (int t = 0; t < F; ++t) t4[t] = make_int4(ht[3 * t], ht[3 * t + 1], ht[3 * t + 2], 0);
+    CapDesc& C = ctx->hC;
+    ctx->tpl = (float4*)ctx->alloc(sizeof(float4) * N);
+    ctx->base_buf = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.albedo = (const float4*)ctx->alloc(sizeof(float4) * N);
+    C.tris = (const int4*)ctx->alloc(sizeof(int4) * F);
+    C.vt_off = (const int*)ctx->alloc(sizeof(int) * (N + 1));
+    C.vt_tri = (const int*)ctx->alloc(sizeof(int) * 3 * F);
+    C.medges = (const int4*)ctx->alloc(sizeof(int4) * medges.size());
+    ctx->material = (float*)ctx->alloc(sizeof(float) * N);
+    C.flags = (uint32_t*)ctx->alloc(sizeof(uint32_t) * N);
+    C.vw = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.uv = (float2*)ctx->alloc(sizeof(float2) * N);
+    C.res = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.HA = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.HB = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.ev = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.q = (float4*)ctx->alloc(sizeof(float4) * N);
+    if (!ctx->err.empty()) return LC_ERR_OOM;
+    C.base = ctx->base_buf;
+    cudaStream_t st = ctx->stream;
+    if ((s = ctx->cuda(cudaMemcpyAsync(ctx->tpl, v4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(ctx->base_buf, v4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)C.albedo, a4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)C.tris, t4.data(), sizeof(int4) * F, cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)C.vt_off, vt_off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)C.vt_tri, vt_tri.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)C.medges, medges.data(), sizeof(int4) * medges.size(), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(ctx->material, hm.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st), "upload")))
+        return s;
+    C.N = N;
+    C.F = F;
+    C.n_medges = (int)medges.size();
+    C.vert_tiles = (N + kVertTile - 1) / kVertTile;
+    C.tri_tiles = (F + kTriTile - 1) / kTriTile;
+    C.medge_tiles = (C.n_medges + kEdgeTile - 1) / kEdgeTile;
+    ctx->ensure_partials();
+    ctx->has_template = true;
+    ctx->drop_graph();
+    return ctx->sync_desc();
+}
+
+void lc_ctx::ensure_partials() {
+    const int need = std::max({2 * hC.vert_tiles, hC.node_tiles, (hC.n + kVecThreads - 1) / kVecThreads, 64}) + 8;
+    if (need > part_cap) {
+        release(hC.part);
+        hC.part = (double*)alloc(sizeof(double) * need);
+        part_cap = need;
+    }
+}
+
+void lc_ctx::free_graph() {
+    void* bufs[] = {(void*)hC.node_vid, (void*)hC.bind_idx, (void*)hC.bind_w, (void*)hC.node_g, (void*)hC.ent_off,
+                    (void*)hC.ent, (void*)hC.edge_off, (void*)hC.edge_dst, (void*)hC.edge_s, hC.node_R, hC.node_t,
+                    hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2};
+    for (void* p : bufs) release(p);
+    hC.node_vid = nullptr; hC.bind_idx = nullptr; hC.bind_w = nullptr; hC.node_g = nullptr;
+    hC.ent_off = nullptr; hC.ent = nullptr; hC.edge_off = nullptr; hC.edge_dst = nullptr; hC.edge_s = nullptr;
+    hC.node_R = nullptr; hC.node_t = nullptr;
+    hC.b = hC.minv = hC.diag = hC.x = hC.r = hC.z = hC.p = hC.Ap = nullptr;
+    tmp_vec = tmp_vec2 = nullptr;
+    hC.n = 0;
+    hC.K = 0;
+    hC.E = 0;
+    hC.node_tiles = 0;
+    has_graph = false;
+    has_lin = false;
+    has_vis = false;
+}
+
+void lc_ctx::free_template() {
+    free_graph();
+    pose_release();
+    void* bufs[] = {tpl, base_buf, (void*)hC.albedo, (void*)hC.tris, (void*)hC.vt_off, (void*)hC.vt_tri,
+                    (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q};
+    for (void* p : bufs) release(p);
+    tpl = base_buf = nullptr;
+    material = nullptr;
+    hC.base = nullptr; hC.albedo = nullptr; hC.tris = nullptr; hC.vt_off = nullptr; hC.vt_tri = nullptr;
+    hC.medges = nullptr; hC.flags = nullptr; hC.vw = nullptr; hC.uv = nullptr; hC.res = nullptr;
+    hC.HA = hC.HB = hC.ev = hC.q = nullptr;
+    hC.N = hC.F = hC.n_medges = 0;
+    has_template = false;
+}
+
+// ---------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------
+extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_build_graph: no template");
+    CapDesc& C = ctx->hC;
+    if (K < 1 || K > kMaxK || n_nodes < K + 1 || n_nodes > C.N)
+        return ctx->fail(LC_ERR_ARG, "lc_build_graph: need 1 <= K <= %d and K+1 <= n_nodes <= N", kMaxK);
+    cudaSetDevice(ctx->device);
+    ctx->free_graph();
+    const int n = n_nodes, N = C.N;
+    cudaStream_t st = ctx->stream;
+    C.n = n;
+    C.K = K;
+    C.node_tiles = (n + kNodeTile - 1) / kNodeTile;
+    C.node_vid = (const int*)ctx->alloc(sizeof(int) * n);
+    C.bind_idx = (const int*)ctx->alloc(sizeof(int) * (size_t)N * K);
+    C.bind_w = (const float*)ctx->alloc(sizeof(float) * (size_t)N * K);
+    C.node_g = (const float4*)ctx->alloc(sizeof(float4) * n);
+    C.ent_off = (const int*)ctx->alloc(sizeof(int) * (n + 1));
+    C.ent = (const int2*)ctx->alloc(sizeof(int2) * (size_t)N * K);
+    C.edge_off = (const int*)ctx->alloc(sizeof(int) * (n + 1));
+    C.node_R = (float4*)ctx->alloc(sizeof(float4) * 3 * n);
+    C.node_t = (float4*)ctx->alloc(sizeof(float4) * n);
+    float4** vecs[] = {&C.b, &C.minv, &C.diag, &C.x, &C.r, &C.z, &C.p, &C.Ap, &ctx->tmp_vec, &ctx->tmp_vec2};
+    for (float4** v : vecs) *v = (float4*)ctx->alloc(sizeof(float4) * 2 * n);
+    GraphScratch gs;
+    std::vector<void*> scratch;
+    auto salloc = [&](size_t b) {
+        void* p = ctx->alloc(b);
+        scratch.push_back(p);
+        return p;
+    };
+    gs.dist = (double*)salloc(sizeof(double) * N);
+    gs.knn_e = (int*)salloc(sizeof(int) * n * kEdgeNN);
+    gs.extra_cnt = (int*)salloc(sizeof(int) * n);
+    gs.extra = (int*)salloc(sizeof(int) * (size_t)n * kMaxExtraEdges);
+    gs.deg = (int*)salloc(sizeof(int) * (n + 1));
+    gs.ent_cnt = (int*)salloc(sizeof(int) * (n + 1));
+    gs.ent_fill = (int*)salloc(sizeof(int) * n);
+    gs.status = (int*)salloc(sizeof(int));
+    auto cleanup = [&]() {
+        for (void* p : scratch) ctx->release(p);
+    };
+    if (!ctx->err.empty()) {
+        cleanup();
+        return LC_ERR_OOM;
+    }
+    cudaMemsetAsync(gs.status, 0, sizeof(int), st);
+    // nodes and bindings on the rest template
+    launch_fps(ctx->tpl, N, n, gs.dist, (int*)C.node_vid, st);
+    float4* G_tpl = (float4*)salloc(sizeof(float4) * n);
+    launch_gather_nodes(ctx->tpl, C.node_vid, n, G_tpl, st);
+    launch_bind(ctx->tpl, N, G_tpl, n, K, (int*)C.bind_idx, (float*)C.bind_w, st);
+    launch_node_edges_count(G_tpl, n, gs, st);
+    launch_exclusive_scan(gs.deg, (int*)C.edge_off, n + 1, st);
+    int E = 0, gstat = 0;
+    lc_status s;
+    if ((s = ctx->copy_to_host(&E, C.edge_off + n, sizeof(int))) != LC_OK ||
+        (s = ctx->copy_to_host(&gstat, gs.status, sizeof(int))) != LC_OK) {
+        cleanup();
+        return s;
+    }
+    if (gstat) {
+        cleanup();
+        return ctx->fail(LC_ERR_NUMERIC, "lc_build_graph: a node has more than %d incoming edges", kMaxExtraEdges);
+    }
+    C.E = E;
+    C.edge_dst = (const int*)ctx->alloc(sizeof(int) * std::max(E, 1));
+    C.edge_s = (const float*)ctx->alloc(sizeof(float) * std::max(E, 1));
+    launch_node_edges_fill(G_tpl, n, ctx->material, C.node_vid, gs, C.edge_off, (int*)C.edge_dst, (float*)C.edge_s, st);
+    launch_entries(C.bind_idx, C.bind_w, N, K, n, gs, (int*)C.ent_off, (int2*)C.ent, st);
+    // node positions of the current rest geometry
+    launch_gather_nodes(C.base, C.node_vid, n, (float4*)C.node_g, st);
+    launch_identity_params(C.node_R, C.node_t, n, st);
+    s = ctx->cuda(cudaStreamSynchronize(st), "graph build");
+    cleanup();
+    if (s != LC_OK) return s;
+    ctx->ensure_partials();
+    ctx->has_graph = true;
+    ctx->drop_graph();
+    return ctx->sync_desc();
+}
+
+extern "C" lc_status lc_read_graph(lc_ctx* ctx, int32_t* node_vid, int32_t* bind_idx, float* bind_w, int32_t* edge_off,
+                                   int32_t* edge_dst, float* edge_s, int* n_edges) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_graph) return ctx->fail(LC_ERR_STATE, "lc_read_graph: no graph");
+    cudaSetDevice(ctx->device);
+    const CapDesc& C = ctx->hC;
+    lc_status s = LC_OK;
+    struct Item {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    } items[] = {{node_vid, C.node_vid, sizeof(int) * C.n},
+                 {bind_idx, C.bind_idx, sizeof(int) * (size_t)C.N * C.K},
+                 {bind_w, C.bind_w, sizeof(float) * (size_t)C.N * C.K},
+                 {edge_off, C.edge_off, sizeof(int) * (C.n + 1)},
+                 {edge_dst, C.edge_dst, sizeof(int) * C.E},
+                 {edge_s, C.edge_s, sizeof(float) * C.E}};
+    for (auto& it : items)
+        if (it.dst && (s = ctx->cuda(cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDefault, ctx->stream), "copy out")))
+            return s;
+    if (n_edges) *n_edges = C.E;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+extern "C" lc_status lc_set_node_params(lc_ctx* ctx, const float* node_R, const float* node_t) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_graph) return ctx->fail(LC_ERR_STATE, "lc_set_node_params: no graph");
+    cudaSetDevice(ctx->device);
+    const int n = ctx->hC.n;
+    if (!node_R && !node_t) {
+        launch_identity_params(ctx->hC.node_R, ctx->hC.node_t, n, ctx->stream);
+        return ctx->cuda(cudaGetLastError(), "identity params");
+    }
+    if (!node_R || !node_t) return ctx->fail(LC_ERR_ARG, "lc_set_node_params: give both arrays or neither");
+    std::vector<float> R, t;
+    lc_status s;
+    if ((s = host_copy(ctx, R, node_R, (size_t)9 * n)) || (s = host_copy(ctx, t, node_t, (size_t)3 * n))) return s;
+    std::vector<float4> R4(3 * n), t4(n);
+    for (int k = 0; k < n; ++k) {
+        for (int j = 0; j < 3; ++j) R4[3 * k + j] = make_float4(R[9 * k + 3 * j], R[9 * k + 3 * j + 1], R[9 * k + 3 * j + 2], 0.f);
+        t4[k] = make_float4(t[3 * k], t[3 * k + 1], t[3 * k + 2], 0.f);
+    }
+    if ((s = ctx->cuda(cudaMemcpyAsync(ctx->hC.node_R, R4.data(), sizeof(float4) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(ctx->hC.node_t, t4.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, ctx->stream), "upload")))
+        return s;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+// ---------------------------------------------------------------------------
+// frame
+// ---------------------------------------------------------------------------
+extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float* dt, const uint8_t* mask,
+                                     const float* joints2d, const float* joints3d) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_camera) return ctx->fail(LC_ERR_STATE, "lc_upload_frame: no camera");
+    if (!rgb || !dt || !mask) return ctx->fail(LC_ERR_ARG, "lc_upload_frame: null image");
+    cudaSetDevice(ctx->device);
+    CapDesc& C = ctx->hC;
+    const size_t P = (size_t)C.W * C.H;
+    cudaStream_t st = ctx->stream;
+    const float* drgb = rgb;
+    const float* ddt = dt;
+    const uint8_t* dmask = mask;
+    lc_status s;
+    if (!lc_ctx::is_device_ptr(rgb)) {
+        if ((s = ctx->cuda(cudaMemcpyAsync(ctx->stage_rgb, rgb, sizeof(float) * 3 * P, cudaMemcpyDefault, st), "frame upload")))
+            return s;
+        drgb = ctx->stage_rgb;
+    }
+    if (!lc_ctx::is_device_ptr(dt)) {
+        if ((s = ctx->cuda(cudaMemcpyAsync(ctx->stage_dt, dt, sizeof(float) * P, cudaMemcpyDefault, st), "frame upload")))
+            return s;
+        ddt = ctx->stage_dt;
+    }
+    if (!lc_ctx::is_device_ptr(mask)) {
+        if ((s = ctx->cuda(cudaMemcpyAsync(ctx->stage_mask, mask, P, cudaMemcpyDefault, st), "frame upload"))) return s;
+        dmask = ctx->stage_mask;
+    }
+    launch_pack_frame(drgb, ddt, dmask, (float4*)C.img, (uint8_t*)C.mask, C.W, C.H, st);
+    if ((s = ctx->cuda(cudaGetLastError(), "pack frame"))) return s;
+    if ((s = ctx->pose_frame(joints2d, joints3d))) return s;
+    ctx->has_frame = true;
+    ctx->has_vis = false;
+    ctx->has_lin = false;
+    return LC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+void lc_ctx::enqueue_nonrigid() {
+    const CapDesc& C = hC;
+    cudaStream_t st = stream;
+    cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
+    cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
+    launch_warp(dC, C, st);
+    launch_visibility(dC, C, st);
+    for (int gn = 0; gn < params.n_gn; ++gn) {
+        if (gn > 0) launch_warp(dC, C, st);
+        launch_linearize(dC, C, gn, st);
+        launch_rhs(dC, C, gn, false, st);
+        launch_pcg_init(dC, C, st);
+        for (int it = 0; it < params.n_pcg; ++it) launch_pcg_iteration(dC, C, st);
+        launch_update(dC, C, gn, st);
+    }
+    launch_warp(dC, C, st);
+    launch_linearize(dC, C, params.n_gn, st);
+    launch_rhs(dC, C, params.n_gn, true, st);
+}
+
+lc_status lc_ctx::check_solve_state(const char* who) {
+    if (!has_template || !has_graph) return fail(LC_ERR_STATE, "%s: template and graph required", who);
+    if (!has_camera || !has_frame) return fail(LC_ERR_STATE, "%s: camera and frame required", who);
+    return LC_OK;
+}
+
+lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn) {
+    Scalars sc;
+    std::vector<double> hist(2 * (LC_MAX_GN + 1));
+    std::vector<int> it(LC_MAX_GN + 2);
+    lc_status s;
+    if ((s = copy_to_host(&sc, hC.sc, sizeof(Scalars))) || (s = copy_to_host(hist.data(), hC.hist, sizeof(double) * hist.size())) ||
+        (s = copy_to_host(it.data(), hC.hist_iters, sizeof(int) * it.size())))
+        return s;
+    memset(stats, 0, sizeof(*stats));
+    stats->e_photo = sc.e_lin[0];
+    stats->e_sil = sc.e_lin[1];
+    stats->e_arap = sc.e_lin[2];
+    stats->e_total = sc.e_lin[0] + sc.e_lin[1] + sc.e_lin[2];
+    for (int g = 0; g < n_gn; ++g) {
+        stats->e_gn[g] = hist[2 * g];
+        stats->step_norm[g] = hist[2 * g + 1];
+        stats->pcg_iters[g] = it[g];
+    }
+    stats->n_gn_done = n_gn;
+    stats->n_visible = sc.counts[0];
+    stats->n_boundary = sc.counts[1];
+    stats->n_boundary_neg = sc.counts[2];
+    stats->pcg_breakdowns = it[LC_MAX_GN + 1];
+    return LC_OK;
+}
+
+extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
+    if (!ctx) return LC_ERR_ARG;
+    lc_status s;
+    if ((s = ctx->check_solve_state("lc_solve_nonrigid"))) return s;
+    cudaSetDevice(ctx->device);
+    if (!ctx->gexec) {
+        cudaGraph_t g = nullptr;
+        if ((s = ctx->cuda(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
+        ctx->enqueue_nonrigid();
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if ((s = ctx->cuda(e, "end capture"))) return s;
+        e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if ((s = ctx->cuda(e, "graph instantiate"))) return s;
+    }
+    if ((s = ctx->cuda(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch"))) return s;
+    ctx->has_vis = true;
+    ctx->has_lin = true;
+    if (stats) return ctx->read_stats(stats, ctx->params.n_gn);
+    return LC_OK;
+}
+
+extern "C" lc_status lc_read_back(lc_ctx* ctx, float* node_R, float* node_t, float* V_out, uint8_t* flags, float* pose) {
+    if (!ctx) return LC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const CapDesc& C = ctx->hC;
+    lc_status s;
+    if ((node_R || node_t) && !ctx->has_graph) return ctx->fail(LC_ERR_STATE, "lc_read_back: no graph");
+    if ((V_out || flags) && !ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_read_back: no template");
+    if (node_R) {
+        std::vector<float4> R4(3 * C.n);
+        if ((s = ctx->copy_to_host(R4.data(), C.node_R, sizeof(float4) * 3 * C.n))) return s;
+        std::vector<float> R(9 * C.n);
+        for (int k = 0; k < C.n; ++k)
+            for (int j = 0; j < 3; ++j) {
+                R[9 * k + 3 * j] = R4[3 * k + j].x;
+                R[9 * k + 3 * j + 1] = R4[3 * k + j].y;
+                R[9 * k + 3 * j + 2] = R4[3 * k + j].z;
+            }
+        if ((s = ctx->deliver(node_R, R.data(), sizeof(float) * R.size()))) return s;
+    }
+    if (node_t) {
+        std::vector<float4> t4(C.n);
+        if ((s = ctx->copy_to_host(t4.data(), C.node_t, sizeof(float4) * C.n))) return s;
+        std::vector<float> t(3 * C.n);
+        for (int k = 0; k < C.n; ++k) {
+            t[3 * k] = t4[k].x;
+            t[3 * k + 1] = t4[k].y;
+            t[3 * k + 2] = t4[k].z;
+        }
+        if ((s = ctx->deliver(node_t, t.data(), sizeof(float) * t.size()))) return s;
+    }
+    if (V_out) {
+        std::vector<float4> v4(C.N);
+        if ((s = ctx->copy_to_host(v4.data(), C.vw, sizeof(float4) * C.N))) return s;
+        std::vector<float> v(3 * C.N);
+        for (int i = 0; i < C.N; ++i) {
+            v[3 * i] = v4[i].x;
+            v[3 * i + 1] = v4[i].y;
+            v[3 * i + 2] = v4[i].z;
+        }
+        if ((s = ctx->deliver(V_out, v.data(), sizeof(float) * v.size()))) return s;
+    }
+    if (flags) {
+        std::vector<uint32_t> f(C.N);
+        if ((s = ctx->copy_to_host(f.data(), C.flags, sizeof(uint32_t) * C.N))) return s;
+        std::vector<uint8_t> f8(C.N);
+        for (int i = 0; i < C.N; ++i) f8[i] = (uint8_t)f[i];
+        if ((s = ctx->deliver(flags, f8.data(), f8.size()))) return s;
+    }
+    if (pose && (s = ctx->pose_read(pose))) return s;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+// ---------------------------------------------------------------------------
+// inspection
+// ---------------------------------------------------------------------------
+extern "C" lc_status lc_compute_visibility(lc_ctx* ctx) {
+    if (!ctx) return LC_ERR_ARG;
+    lc_status s;
+    if ((s = ctx->check_solve_state("lc_compute_visibility"))) return s;
+    cudaSetDevice(ctx->device);
+    launch_warp(ctx->dC, ctx->hC, ctx->stream);
+    launch_visibility(ctx->dC, ctx->hC, ctx->stream);
+    ctx->has_vis = true;
+    ctx->has_lin = false;
+    return ctx->cuda(cudaGetLastError(), "visibility");
+}
+
+extern "C" lc_status lc_read_visibility(lc_ctx* ctx, uint64_t* zbuf, uint8_t* flags, float* uv) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_vis) return ctx->fail(LC_ERR_STATE, "lc_read_visibility: no visibility pass yet");
+    cudaSetDevice(ctx->device);
+    const CapDesc& C = ctx->hC;
+    lc_status s;
+    if (zbuf && (s = ctx->cuda(cudaMemcpyAsync(zbuf, C.zbuf, sizeof(uint64_t) * (size_t)C.W * C.H, cudaMemcpyDefault, ctx->stream), "copy out")))
+        return s;
+    if (uv && (s = ctx->cuda(cudaMemcpyAsync(uv, C.uv, sizeof(float2) * C.N, cudaMemcpyDefault, ctx->stream), "copy out")))
+        return s;
+    if (flags) {
+        std::vector<uint32_t> f(C.N);
+        if ((s = ctx->copy_to_host(f.data(), C.flags, sizeof(uint32_t) * C.N))) return s;
+        std::vector<uint8_t> f8(C.N);
+        for (int i = 0; i < C.N; ++i) f8[i] = (uint8_t)f[i];
+        if ((s = ctx->deliver(flags, f8.data(), f8.size()))) return s;
+    }
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+lc_status lc_ctx::linearize_now(bool with_rhs) {
+    launch_warp(dC, hC, stream);
+    launch_linearize(dC, hC, LC_MAX_GN, stream);
+    launch_rhs(dC, hC, LC_MAX_GN, !with_rhs, stream);
+    has_lin = true;
+    return cuda(cudaGetLastError(), "linearize");
+}
+
+extern "C" lc_status lc_eval_linearization(lc_ctx* ctx, float* v_warp, float* uv, float* r_photo, float* r_sil, float* H,
+                                           float* e, double* energy) {
+    if (!ctx) return LC_ERR_ARG;
+    lc_status s;
+    if ((s = ctx->check_solve_state("lc_eval_linearization"))) return s;
+    if (!ctx->has_vis) return ctx->fail(LC_ERR_STATE, "lc_eval_linearization: no visibility pass yet");
+    cudaSetDevice(ctx->device);
+    if ((s = ctx->linearize_now(true))) return s;
+    const CapDesc& C = ctx->hC;
+    const int N = C.N;
+    std::vector<float4> a(N), b(N);
+    std::vector<float> out;
+    auto emit = [&](float* dst, int width, auto fn) -> lc_status {
+        if (!dst) return LC_OK;
+        out.assign((size_t)N * width, 0.f);
+        for (int i = 0; i < N; ++i) fn(i, &out[(size_t)i * width]);
+        return ctx->deliver(dst, out.data(), sizeof(float) * out.size());
+    };
+    if (v_warp) {
+        if ((s = ctx->copy_to_host(a.data(), C.vw, sizeof(float4) * N))) return s;
+        if ((s = emit(v_warp, 3, [&](int i, float* o) { o[0] = a[i].x; o[1] = a[i].y; o[2] = a[i].z; }))) return s;
+    }
+    if (uv && (s = ctx->cuda(cudaMemcpyAsync(uv, C.uv, sizeof(float2) * N, cudaMemcpyDefault, ctx->stream), "copy out")))
+        return s;
+    if (r_photo || r_sil) {
+        if ((s = ctx->copy_to_host(a.data(), C.res, sizeof(float4) * N))) return s;
+        if ((s = emit(r_photo, 3, [&](int i, float* o) { o[0] = a[i].x; o[1] = a[i].y; o[2] = a[i].z; }))) return s;
+        if ((s = emit(r_sil, 1, [&](int i, float* o) { o[0] = a[i].w; }))) return s;
+    }
+    if (H) {
+        if ((s = ctx->copy_to_host(a.data(), C.HA, sizeof(float4) * N)) || (s = ctx->copy_to_host(b.data(), C.HB, sizeof(float4) * N)))
+            return s;
+        if ((s = emit(H, 6, [&](int i, float* o) {
+                 o[0] = a[i].x; o[1] = a[i].y; o[2] = a[i].z; o[3] = a[i].w; o[4] = b[i].x; o[5] = b[i].y;
+             })))
+            return s;
+    }
+    if (e) {
+        if ((s = ctx->copy_to_host(a.data(), C.ev, sizeof(float4) * N))) return s;
+        if ((s = emit(e, 3, [&](int i, float* o) { o[0] = a[i].x; o[1] = a[i].y; o[2] = a[i].z; }))) return s;
+    }
+    if (energy) {
+        Scalars sc;
+        if ((s = ctx->copy_to_host(&sc, C.sc, sizeof(Scalars)))) return s;
+        double en[3] = {sc.e_lin[0], sc.e_lin[1], sc.e_lin[2]};
+        if ((s = ctx->deliver(energy, en, sizeof(en)))) return s;
+    }
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+lc_status lc_ctx::vec_out(float* dst, const float4* src) {
+    if (!dst) return LC_OK;
+    const int n = hC.n;
+    launch_unpack_vec(src, tmp_out(), n, stream);
+    std::vector<float> h(6 * n);
+    lc_status s;
+    if ((s = copy_to_host(h.data(), tmp_out(), sizeof(float) * 6 * n))) return s;
+    return deliver(dst, h.data(), sizeof(float) * h.size());
+}
+
+float* lc_ctx::tmp_out() {
+    if (!tmp6 || tmp6_cap < 6 * hC.n) {
+        release(tmp6);
+        tmp6 = (float*)alloc(sizeof(float) * 6 * std::max(hC.n, 1));
+        tmp6_cap = 6 * hC.n;
+    }
+    return tmp6;
+}
+
+extern "C" lc_status lc_eval_gradient(lc_ctx* ctx, float* rhs, float* diag) {
+    if (!ctx) return LC_ERR_ARG;
+    lc_status s;
+    if ((s = ctx->check_solve_state("lc_eval_gradient"))) return s;
+    if (!ctx->has_vis) return ctx->fail(LC_ERR_STATE, "lc_eval_gradient: no visibility pass yet");
+    cudaSetDevice(ctx->device);
+    if ((s = ctx->linearize_now(true))) return s;
+    if ((s = ctx->vec_out(rhs, ctx->hC.b))) return s;
+    return ctx->vec_out(diag, ctx->hC.diag);
+}
+
+extern "C" lc_status lc_apply_jtj(lc_ctx* ctx, const float* p, float* out) {
+    if (!ctx || !p || !out) return LC_ERR_ARG;
+    if (!ctx->has_lin) return ctx->fail(LC_ERR_STATE, "lc_apply_jtj: no linearisation (call lc_eval_linearization)");
+    cudaSetDevice(ctx->device);
+    const int n = ctx->hC.n;
+    std::vector<float> hp;
+    lc_status s;
+    if ((s = host_copy(ctx, hp, p, (size_t)6 * n))) return s;
+    if ((s = ctx->cuda(cudaMemcpyAsync(ctx->tmp_out(), hp.data(), sizeof(float) * 6 * n, cudaMemcpyHostToDevice, ctx->stream), "upload")))
+        return s;
+    launch_pack_vec(ctx->tmp_out(), ctx->tmp_vec, n, ctx->stream);
+    launch_jtj(ctx->dC, ctx->hC, ctx->tmp_vec, ctx->tmp_vec2, false, ctx->stream);
+    if ((s = ctx->cuda(cudaGetLastError(), "jtj"))) return s;
+    return ctx->vec_out(out, ctx->tmp_vec2);
+}
+
+extern "C" lc_status lc_solve_linear(lc_ctx* ctx, float* delta, int* iters) {
+    if (!ctx || !delta) return LC_ERR_ARG;
+    if (!ctx->has_lin) return ctx->fail(LC_ERR_STATE, "lc_solve_linear: no linearisation (call lc_eval_linearization)");
+    cudaSetDevice(ctx->device);
+    launch_pcg_init(ctx->dC, ctx->hC, ctx->stream);
+    for (int it = 0; it < ctx->params.n_pcg; ++it) launch_pcg_iteration(ctx->dC, ctx->hC, ctx->stream);
+    lc_status s;
+    if ((s = ctx->cuda(cudaGetLastError(), "pcg"))) return s;
+    if ((s = ctx->vec_out(delta, ctx->hC.x))) return s;
+    if (iters) {
+        Scalars sc;
+        if ((s = ctx->copy_to_host(&sc, ctx->hC.sc, sizeof(Scalars)))) return s;
+        *iters = sc.iters;
+    }
+    return LC_OK;
+}

@@ -1,0 +1,278 @@
+// Frame preparation, embedded-graph warp + projection, and the once-per-frame
+// visibility / contour pass.
+//
+// Visibility comes from depth buffering (Sec. 3.4, photometric term), the
+// contour set B and the directions b_i from Sec. 3.3 (silhouette term, the
+// n^T z < 0 rule for model points inside the image silhouette).  These are
+// integer decisions taken in exact integer arithmetic plus a fixed sequence
+// of FP32 operations (intrinsics: every operation rounded once, nothing
+// contracted), so the result is reproducible bit for bit:
+//   snapping: 1/256 px fixed point, round half to even; int64 edge functions
+//   with a top-left tie rule, both windings; FP32 perspective-correct depth
+//   1 / ((b0/z0 + b1/z1) + b2/z2); key = bits(depth) << 32 | triangle id,
+//   resolved with a 64-bit atomicMin.
+#include <cstddef>
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+// ---------------------------------------------------------------------------
+// Frame packing: (r, g, b) + dt -> float4 per pixel; mask copied.
+// ---------------------------------------------------------------------------
+__global__ void pack_frame_kernel(const float* __restrict__ rgb, const float* __restrict__ dt,
+                                  const uint8_t* __restrict__ mask_in, float4* __restrict__ img,
+                                  uint8_t* __restrict__ mask, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    img[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], dt[p]);
+    mask[p] = mask_in[p] ? 1 : 0;
+}
+
+void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in, float4* img, uint8_t* mask,
+                       int W, int H, cudaStream_t st) {
+    const int P = W * H;
+    pack_frame_kernel<<<(P + 255) / 256, 256, 0, st>>>(rgb, dt, mask_in, img, mask, P);
+}
+
+// ---------------------------------------------------------------------------
+// Warp + project: v'_i = v_i + sum_s w_is ((R_k - I)(v_i - g_k) + t_k).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVertTile) warp_kernel(const CapDesc* __restrict__ caps,
+                                                          const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int i = tile * kVertTile + threadIdx.x;
+    if (i >= C.N) return;
+    const float4 v = C.base[i];
+    const int K = C.K;
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    for (int s = 0; s < K; ++s) {
+        const int k = C.bind_idx[(size_t)i * K + s];
+        const float w = C.bind_w[(size_t)i * K + s];
+        const float4 g = C.node_g[k];
+        const float4 r0 = C.node_R[3 * k], r1 = C.node_R[3 * k + 1], r2 = C.node_R[3 * k + 2];
+        const float4 t = C.node_t[k];
+        const float ax = v.x - g.x, ay = v.y - g.y, az = v.z - g.z;
+        const float mx = (r0.x - 1.f) * ax + r0.y * ay + r0.z * az + t.x;
+        const float my = r1.x * ax + (r1.y - 1.f) * ay + r1.z * az + t.y;
+        const float mz = r2.x * ax + r2.y * ay + (r2.z - 1.f) * az + t.z;
+        dx += w * mx;
+        dy += w * my;
+        dz += w * mz;
+    }
+    const float X = v.x + dx, Y = v.y + dy, Z = v.z + dz;
+    const bool ok = valid_depth(Z);
+    C.vw[i] = make_float4(X, Y, Z, ok ? 1.f : 0.f);
+    C.uv[i] = ok ? project_exact(C.f, C.cx, C.cy, X, Y, Z) : make_float2(0.f, 0.f);
+}
+
+void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+    warp_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Rasteriser
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool snap(float x, long long& out) {
+    if (!(fabsf(x) < 1048576.0f)) return false;
+    out = __float2ll_rn(xmul(x, 256.0f));
+    return true;
+}
+
+__device__ __forceinline__ bool vertex_snap(const CapDesc& C, int i, long long& sx, long long& sy) {
+    const float4 v = C.vw[i];
+    if (!(v.w > 0.f)) return false;
+    const float2 uv = C.uv[i];
+    return snap(uv.x, sx) && snap(uv.y, sy);
+}
+
+__device__ __forceinline__ bool owns(long long ex, long long ey) { return ey < 0 || (ey == 0 && ex > 0); }
+
+__device__ __forceinline__ long long ceil256(long long a) { return a >= 0 ? (a + 255) / 256 : -((-a) / 256); }
+__device__ __forceinline__ long long floor256(long long a) { return a >= 0 ? a / 256 : -((-a + 255) / 256); }
+
+__global__ void __launch_bounds__(kTriTile) raster_kernel(const CapDesc* __restrict__ caps,
+                                                           const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int t = tile * kTriTile + threadIdx.x;
+    if (t >= C.F) return;
+    const int4 tri = C.tris[t];
+    long long ax, ay, bx, by, qx, qy;
+    if (!vertex_snap(C, tri.x, ax, ay) || !vertex_snap(C, tri.y, bx, by) || !vertex_snap(C, tri.z, qx, qy))
+        return;
+    const long long area = (bx - ax) * (qy - ay) - (by - ay) * (qx - ax);
+    if (area == 0) return;
+    const long long sg = area > 0 ? 1 : -1;
+    long long px0 = ceil256(min(ax, min(bx, qx))), px1 = floor256(max(ax, max(bx, qx)));
+    long long py0 = ceil256(min(ay, min(by, qy))), py1 = floor256(max(ay, max(by, qy)));
+    px0 = max(px0, 0LL);
+    py0 = max(py0, 0LL);
+    px1 = min(px1, (long long)C.W - 1);
+    py1 = min(py1, (long long)C.H - 1);
+    if (px0 > px1 || py0 > py1) return;
+    const bool oA = owns(sg * (qx - bx), sg * (qy - by));
+    const bool oB = owns(sg * (ax - qx), sg * (ay - qy));
+    const bool oC = owns(sg * (bx - ax), sg * (by - ay));
+    const float za = C.vw[tri.x].z, zb = C.vw[tri.y].z, zc = C.vw[tri.z].z;
+    const float farea = (float)(sg * area);
+    for (long long py = py0; py <= py1; ++py) {
+        const long long Py = py * 256;
+        for (long long px = px0; px <= px1; ++px) {
+            const long long Px = px * 256;
+            const long long wA = sg * ((qx - bx) * (Py - by) - (qy - by) * (Px - bx));
+            const long long wB = sg * ((ax - qx) * (Py - qy) - (ay - qy) * (Px - qx));
+            const long long wC = sg * ((bx - ax) * (Py - ay) - (by - ay) * (Px - ax));
+            if (wA < 0 || wB < 0 || wC < 0) continue;
+            if ((wA == 0 && !oA) || (wB == 0 && !oB) || (wC == 0 && !oC)) continue;
+            const float b0 = xdiv(__ll2float_rn(wA), farea);
+            const float b1 = xdiv(__ll2float_rn(wB), farea);
+            const float b2 = xdiv(__ll2float_rn(wC), farea);
+            const float s01 = xadd(xdiv(b0, za), xdiv(b1, zb));
+            const float depth = xdiv(1.0f, xadd(s01, xdiv(b2, zc)));
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned)t;
+            atomicMin(&C.zbuf[py * C.W + px], key);
+        }
+    }
+}
+
+// per-vertex depth test; also resets the vertex flags
+__global__ void __launch_bounds__(kVertTile) vis_kernel(const CapDesc* __restrict__ caps,
+                                                         const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int i = tile * kVertTile + threadIdx.x;
+    if (i >= C.N) return;
+    uint32_t fl = 0;
+    long long sx, sy;
+    if (vertex_snap(C, i, sx, sy)) {
+        const float2 uv = C.uv[i];
+        if (in_image(uv, C.W, C.H)) {
+            const long long px = __float2ll_rn(uv.x), py = __float2ll_rn(uv.y);
+            const unsigned long long key = C.zbuf[py * C.W + px];
+            bool vis = true;
+            if (key != ~0ULL) {
+                const float depth = __uint_as_float((unsigned)(key >> 32));
+                vis = C.vw[i].z <= xadd(depth, C.eps_vis);
+            }
+            if (vis) fl |= LC_VIS_BIT;
+        }
+    }
+    C.flags[i] = fl;
+}
+
+__device__ __forceinline__ bool front_facing(const CapDesc& C, int t) {
+    const int4 tri = C.tris[t];
+    long long ax, ay, bx, by, qx, qy;
+    if (!vertex_snap(C, tri.x, ax, ay) || !vertex_snap(C, tri.y, bx, by) || !vertex_snap(C, tri.z, qx, qy))
+        return false;
+    return (bx - ax) * (qy - ay) - (by - ay) * (qx - ax) > 0;
+}
+
+__global__ void __launch_bounds__(kEdgeTile) silhouette_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int e = tile * kEdgeTile + threadIdx.x;
+    if (e >= C.n_medges) return;
+    const int4 me = C.medges[e];
+    const bool sil = me.w < 0 ? true : (front_facing(C, me.z) != front_facing(C, me.w));
+    if (sil) {
+        atomicOr(&C.flags[me.x], LC_ONSIL_BIT);
+        atomicOr(&C.flags[me.y], LC_ONSIL_BIT);
+    }
+}
+
+__device__ __forceinline__ float xlerp(float a, float b, float t) { return xadd(a, xmul(t, xsub(b, a))); }
+
+__device__ __forceinline__ float dt_at(const CapDesc& C, int x, int y) { return C.img[(size_t)y * C.W + x].w; }
+
+__device__ __forceinline__ float dt_grad_x(const CapDesc& C, int x, int y) {
+    const int W = C.W;
+    if (W < 2) return 0.f;
+    if (x == 0) return xsub(dt_at(C, 1, y), dt_at(C, 0, y));
+    if (x == W - 1) return xsub(dt_at(C, W - 1, y), dt_at(C, W - 2, y));
+    return xmul(xsub(dt_at(C, x + 1, y), dt_at(C, x - 1, y)), 0.5f);
+}
+
+__device__ __forceinline__ float dt_grad_y(const CapDesc& C, int x, int y) {
+    const int H = C.H;
+    if (H < 2) return 0.f;
+    if (y == 0) return xsub(dt_at(C, x, 1), dt_at(C, x, 0));
+    if (y == H - 1) return xsub(dt_at(C, x, H - 1), dt_at(C, x, H - 2));
+    return xmul(xsub(dt_at(C, x, y + 1), dt_at(C, x, y - 1)), 0.5f);
+}
+
+// contour set B and b_i for visible vertices on a silhouette edge
+__global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __restrict__ caps,
+                                                             const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int i = tile * kVertTile + threadIdx.x;
+    int cnt[3] = {0, 0, 0};
+    if (i < C.N) {
+        uint32_t fl = C.flags[i];
+        if (fl & LC_VIS_BIT) cnt[0] = 1;
+        if ((fl & LC_VIS_BIT) && (fl & LC_ONSIL_BIT)) {
+            fl |= LC_INB_BIT;
+            cnt[1] = 1;
+            // area-weighted normal: incident triangles in ascending id order
+            float nx = 0.f, ny = 0.f, nz = 0.f;
+            for (int j = C.vt_off[i]; j < C.vt_off[i + 1]; ++j) {
+                const int4 tri = C.tris[C.vt_tri[j]];
+                const float4 A = C.vw[tri.x], B = C.vw[tri.y], Q = C.vw[tri.z];
+                const float e1x = xsub(B.x, A.x), e1y = xsub(B.y, A.y), e1z = xsub(B.z, A.z);
+                const float e2x = xsub(Q.x, A.x), e2y = xsub(Q.y, A.y), e2z = xsub(Q.z, A.z);
+                nx = xadd(nx, xsub(xmul(e1y, e2z), xmul(e1z, e2y)));
+                ny = xadd(ny, xsub(xmul(e1z, e2x), xmul(e1x, e2z)));
+                nz = xadd(nz, xsub(xmul(e1x, e2y), xmul(e1y, e2x)));
+            }
+            const float4 v = C.vw[i];
+            const float mx = xsub(nx, xmul(xdiv(v.x, v.z), nz));
+            const float my = xsub(ny, xmul(xdiv(v.y, v.z), nz));
+            const float2 uv = C.uv[i];
+            const int x0 = (int)floorf(uv.x), y0 = (int)floorf(uv.y);
+            const float fx = xsub(uv.x, (float)x0), fy = xsub(uv.y, (float)y0);
+            const int x1 = x0 + 1 < C.W ? x0 + 1 : C.W - 1;
+            const int y1 = y0 + 1 < C.H ? y0 + 1 : C.H - 1;
+            const float gx = xlerp(xlerp(dt_grad_x(C, x0, y0), dt_grad_x(C, x1, y0), fx),
+                                   xlerp(dt_grad_x(C, x0, y1), dt_grad_x(C, x1, y1), fx), fy);
+            const float gy = xlerp(xlerp(dt_grad_y(C, x0, y0), dt_grad_y(C, x1, y0), fx),
+                                   xlerp(dt_grad_y(C, x0, y1), dt_grad_y(C, x1, y1), fx), fy);
+            const float d = xadd(xmul(mx, gx), xmul(my, gy));
+            const long long px = __float2ll_rn(uv.x), py = __float2ll_rn(uv.y);
+            const bool inside = C.mask[py * C.W + px] != 0;
+            if (inside && d > 0.f) {
+                fl |= LC_BNEG_BIT;
+                cnt[2] = 1;
+            }
+            C.flags[i] = fl;
+        }
+    }
+    // vertex counts for the statistics (integer block sums)
+    __shared__ int sh[3];
+    if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (int j = 0; j < 3; ++j)
+        if (cnt[j]) atomicAdd(&sh[j], 1);
+    __syncthreads();
+    if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&C.sc->counts[threadIdx.x], sh[threadIdx.x]);
+}
+
+void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+    cudaMemsetAsync(hC.zbuf, 0xff, sizeof(unsigned long long) * (size_t)hC.W * hC.H, st);
+    cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, counts), 0, sizeof(int) * 3, st);
+    if (hC.tri_tiles) raster_kernel<<<hC.tri_tiles, kTriTile, 0, st>>>(dC, nullptr);
+    vis_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
+    if (hC.medge_tiles) silhouette_kernel<<<hC.medge_tiles, kEdgeTile, 0, st>>>(dC, nullptr);
+    contour_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
+}
+
+}  // namespace lc

@@ -1,0 +1,64 @@
+// Host-side context of the livecap library (one capture).
+#pragma once
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "lc_internal.cuh"
+
+struct PoseState;
+
+struct lc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;      // created by lc_create (caller passed 0)
+    std::string err;
+    lc_params params{};
+    lc::CapDesc hC{};             // host copy of the descriptor
+    lc::CapDesc* dC = nullptr;    // device copy
+    std::vector<void*> owned;     // every device allocation of this context
+    cudaGraphExec_t gexec = nullptr;
+    bool has_camera = false, has_template = false, has_graph = false, has_frame = false;
+    bool has_vis = false, has_lin = false;
+    // template
+    float4* tpl = nullptr;        // rest template V^hat
+    float4* base_buf = nullptr;   // rest geometry of the non-rigid stage (template or skinned mesh)
+    float* material = nullptr;
+    // frame staging for host inputs
+    float* stage_rgb = nullptr;
+    float* stage_dt = nullptr;
+    uint8_t* stage_mask = nullptr;
+    // scratch node vectors
+    float4* tmp_vec = nullptr;
+    float4* tmp_vec2 = nullptr;
+    float* tmp6 = nullptr;
+    int tmp6_cap = 0;
+    int part_cap = 0;
+    PoseState* pose = nullptr;
+
+    lc_status fail(lc_status st, const char* fmt, ...);
+    lc_status cuda(cudaError_t e, const char* what);
+    void* alloc(size_t bytes);
+    void release(void* p);
+    static bool is_device_ptr(const void* p);
+    lc_status copy_to_host(void* dst, const void* src_dev, size_t bytes);
+    lc_status fetch(void* dst_host, const void* src_any, size_t bytes);
+    lc_status deliver(void* dst_any, const void* src_host, size_t bytes);
+    lc_status sync_desc();
+    void drop_graph();
+    void apply_params();
+    void ensure_partials();
+    void free_graph();
+    void free_template();
+    void enqueue_nonrigid();
+    lc_status check_solve_state(const char* who);
+    lc_status read_stats(lc_solve_stats* stats, int n_gn);
+    lc_status linearize_now(bool with_rhs);
+    lc_status vec_out(float* dst, const float4* src);
+    float* tmp_out();
+    // pose stage (pose_api.cu)
+    void pose_release();
+    lc_status pose_frame(const float* joints2d, const float* joints3d);
+    lc_status pose_read(float* pose_out);
+};

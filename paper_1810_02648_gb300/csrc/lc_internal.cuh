@@ -1,0 +1,245 @@
+// Internal device-side declarations of the livecap library.
+//
+// One capture (template + graph + frame + solver state) is described by a
+// CapDesc that lives in device memory.  Every kernel takes the descriptor
+// array and an optional work list of (capture, tile) items, so the same
+// kernels serve one capture (work list null: capture 0, tile = blockIdx.x)
+// and many captures of uneven size in one launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/livecap.h"
+
+namespace lc {
+
+constexpr int kVertTile = 256;      // vertices per vertex tile (one per thread)
+constexpr int kNodeWarps = 8;       // warps (= nodes) per node tile
+constexpr int kNodeTile = kNodeWarps;
+constexpr int kTriTile = 128;       // triangles per raster tile
+constexpr int kEdgeTile = 256;      // mesh edges per tile
+constexpr int kMaxK = 8;            // nodes per vertex
+constexpr int kEdgeNN = 4;          // node-graph neighbours before symmetrising
+constexpr int kMaxExtraEdges = 60;  // symmetrised extra in-edges per node
+constexpr int kVecThreads = 256;    // nodes per PCG vector tile
+
+constexpr uint32_t LC_VIS_BIT = LC_FLAG_VISIBLE;
+constexpr uint32_t LC_ONSIL_BIT = LC_FLAG_ONSIL;
+constexpr uint32_t LC_INB_BIT = LC_FLAG_INB;
+constexpr uint32_t LC_BNEG_BIT = LC_FLAG_BNEG;
+
+// Per-capture reduction scalars (FP64; PCG dots and energies).
+struct Scalars {
+    double rz;         // r^T z of the current iteration
+    double rz_new;
+    double beta;
+    double pAp;
+    double e_lin[3];   // photo, sil, arap at the current linearisation
+    double step2;      // ||delta||^2 of the last step
+    int stop;          // PCG stopped (breakdown or exact convergence)
+    int breakdown;     // last PCG stopped on p^T A p <= 0
+    int iters;         // PCG iterations run in the current solve
+    int status;        // device error word (0 = ok)
+    int counts[3];     // visible, contour, contour with b = -1
+};
+
+// Reduction counters: the last tile of a capture to finish a phase reduces
+// the per-tile partials in a fixed order (deterministic, no float atomics).
+enum Counter { CNT_ENERGY = 0, CNT_ARAP, CNT_DOT, CNT_DOT2, CNT_STEP, CNT_COUNTS, CNT_N };
+
+struct CapDesc {
+    // sizes
+    int N, F, n, K, E, W, H, n_medges;
+    int vert_tiles, node_tiles, tri_tiles, medge_tiles;
+    float f, cx, cy;
+    float w_photo, w_sil, w_arap, eps_vis;
+    // template (rest geometry of this stage) and mesh topology
+    const float4* base;      // N (x, y, z, 0)
+    const float4* albedo;    // N (r, g, b, 0)
+    const int4* tris;        // F (a, b, c, 0)
+    const int* vt_off;       // N+1 vertex -> triangle CSR (triangle ids ascending)
+    const int* vt_tri;
+    const int4* medges;      // mesh edges (v0, v1, t0, t1), t1 = -1 on a border
+    // graph
+    const int* node_vid;     // n
+    const int* bind_idx;     // N*K
+    const float* bind_w;     // N*K
+    const float4* node_g;    // n (g, 0)
+    const int* ent_off;      // n+1 node -> (vertex, weight) CSR, vertex ascending
+    const int2* ent;         // (vertex, __float_as_int(weight))
+    const int* edge_off;     // n+1 node edges by source
+    const int* edge_dst;
+    const float* edge_s;
+    // node parameters
+    float4* node_R;          // 3n rows (R_j0, R_j1, R_j2, 0)
+    float4* node_t;          // n (t, 0)
+    // frame
+    const float4* img;       // H*W (r, g, b, dt)
+    const uint8_t* mask;     // H*W
+    // per-frame decisions
+    unsigned long long* zbuf;  // H*W
+    uint32_t* flags;         // N
+    // linearisation
+    float4* vw;              // N warped (x, y, z, valid)
+    float2* uv;              // N
+    float4* res;             // N (r_photo xyz, r_sil)
+    float4* HA;              // N (h00, h01, h02, h11)
+    float4* HB;              // N (h12, h22, 0, 0)
+    float4* ev;              // N (e0, e1, e2, active)
+    // PCG state: node vectors as two float4 per node (omega, t)
+    float4* b;               // -J^T F
+    float4* minv;            // Jacobi inverse diagonal
+    float4* diag;            // diag(J^T J)
+    float4* x;
+    float4* r;
+    float4* z;
+    float4* p;
+    float4* Ap;
+    float4* q;               // per-vertex H_i dv_i scratch (N)
+    // reductions
+    double* part;            // per-tile partials of the running reduction
+    unsigned* counters;      // CNT_N
+    Scalars* sc;
+    double* hist;            // 2 * (LC_MAX_GN + 1): [2 gn] energy, [2 gn + 1] step norm
+    int* hist_iters;         // LC_MAX_GN + 2: PCG iterations per step, [LC_MAX_GN + 1] breakdowns
+};
+
+struct WorkItem {
+    int cap;
+    int tile;
+};
+
+__device__ __forceinline__ void decode(const WorkItem* items, int& cap, int& tile) {
+    if (items) {
+        WorkItem w = items[blockIdx.x];
+        cap = w.cap;
+        tile = w.tile;
+    } else {
+        cap = 0;
+        tile = blockIdx.x;
+    }
+}
+
+// ---- exact FP32 helpers (each operation rounded once, no contraction) -----
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float xdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Projection with the specified operation order: u = (f*X)/Z + cx.
+__device__ __forceinline__ float2 project_exact(float f, float cx, float cy, float X, float Y, float Z) {
+    return make_float2(xadd(xdiv(xmul(f, X), Z), cx), xadd(xdiv(xmul(f, Y), Z), cy));
+}
+
+__device__ __forceinline__ bool valid_depth(float Z) { return Z > 1e-3f; }
+
+__device__ __forceinline__ bool in_image(float2 uv, int W, int H) {
+    return uv.x >= 0.0f && uv.x <= (float)(W - 1) && uv.y >= 0.0f && uv.y <= (float)(H - 1);
+}
+
+// ---- FP64 block reduction helpers -----------------------------------------
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sumf(float (&v)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+}
+
+// Block-wide sum of NV doubles in a fixed order; result valid in thread 0.
+template <int NV, int NWARPS>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
+    warp_sum<NV>(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[w][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < NWARPS; ++i) s += sh[i][j];
+            v[j] = s;
+        }
+    }
+}
+
+// Write this tile's partials; returns true in thread 0 of the block that
+// finished last for this capture and counter (it then sums in tile order).
+template <int NV>
+__device__ __forceinline__ bool publish_partial(const CapDesc& C, int counter, int tile, int ntiles,
+                                                const double (&v)[NV], double* part_base) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) part_base[tile * NV + j] = v[j];
+        __threadfence();
+        unsigned done = atomicAdd(&C.counters[counter], 1u);
+        last = (done == (unsigned)ntiles - 1u);
+        if (last) {
+            __threadfence();
+            C.counters[counter] = 0u;   // re-arm for the next launch
+        }
+    }
+    __syncthreads();
+    return last;
+}
+
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double* part_base, int ntiles, double (&out)[NV]) {
+    // called by a single thread, fixed order
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j] = 0.0;
+    for (int t = 0; t < ntiles; ++t)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] += __ldcg(&part_base[t * NV + j]);
+}
+
+// ---- kernel launchers (frame_kernels.cu, solver_kernels.cu, graph_kernels.cu)
+void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in, float4* img,
+                       uint8_t* mask, int W, int H, cudaStream_t st);
+void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
+void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
+void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
+void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_pcg_iteration(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
+void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
+void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);
+
+// graph construction
+struct GraphScratch {
+    double* dist;       // N
+    int* knn_e;         // n * kEdgeNN
+    int* extra_cnt;     // n
+    int* extra;         // n * kMaxExtraEdges
+    int* deg;           // n
+    int* ent_cnt;       // n
+    int* ent_fill;      // n
+    int* status;        // 1
+};
+void launch_fps(const float4* V, int N, int n, double* dist, int* node_vid, cudaStream_t st);
+void launch_bind(const float4* V, int N, const float4* G, int n, int K, int* idx, float* w, cudaStream_t st);
+void launch_node_edges_count(const float4* G, int n, GraphScratch& s, cudaStream_t st);
+void launch_node_edges_fill(const float4* G, int n, const float* material, const int* node_vid,
+                            const GraphScratch& s, const int* edge_off, int* edge_dst, float* edge_s,
+                            cudaStream_t st);
+void launch_entries(const int* idx, const float* w, int N, int K, int n, GraphScratch& s,
+                    int* ent_off, int2* ent, cudaStream_t st);
+void launch_exclusive_scan(const int* in, int* out, int n, cudaStream_t st);
+void launch_gather_nodes(const float4* base, const int* node_vid, int n, float4* G, cudaStream_t st);
+void launch_identity_params(float4* R, float4* t, int n, cudaStream_t st);
+
+}  // namespace lc

@@ -1,0 +1,533 @@
+// Gauss-Newton / PCG kernels of the non-rigid stage (Sec. 3.4 energy,
+// Sec. 4 solver: normal equations J^T J delta = -J^T F, Jacobi-preconditioned
+// CG with a fixed iteration count, no damping).
+//
+// The Jacobian is never stored.  Per vertex i the residual rows r_i
+// (3 photometric rows if i is visible, 1 silhouette row if i is in B) depend
+// on the node parameters only through the warped position v'_i, so the
+// linearisation keeps A_i = d r_i / d v'_i folded into H_i = A_i^T A_i (3x3)
+// and e_i = A_i^T r_i.  With a_is = R_k (v_i - g_k) and the left rotation
+// increment, d v'_i / d(omega_k, t_k) = w_is [-[a_is]x, I], so
+//   (J^T F)_k   = sum_(i,s) w_is [a_is x e_i ; e_i]                 + ARAP
+//   (J^T J p)_k = sum_(i,s) w_is [a_is x q_i ; q_i],  q_i = H_i dv_i + ARAP
+// with dv_i = sum_s w_is (p_omega,k x a_is + p_t,k).  Per-node sums are
+// warp-segmented gathers over the node -> (vertex, weight) CSR (one warp per
+// node, shuffle reductions), so there are no floating-point atomics and every
+// result is deterministic.  Dot products and energies accumulate in FP64 and
+// are reduced per capture by the last tile to finish, in tile order.
+#include "lc_internal.cuh"
+
+namespace lc {
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+struct Rot {
+    float3 r0, r1, r2;
+};
+__device__ __forceinline__ Rot load_R(const float4* R, int k) {
+    const float4 a = R[3 * k], b = R[3 * k + 1], c = R[3 * k + 2];
+    return {make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), make_float3(c.x, c.y, c.z)};
+}
+__device__ __forceinline__ float3 mul(const Rot& R, float3 v) { return make_float3(dot3(R.r0, v), dot3(R.r1, v), dot3(R.r2, v)); }
+
+// H stored as (h00, h01, h02, h11) + (h12, h22)
+__device__ __forceinline__ float3 mulH(float4 A, float4 B, float3 v) {
+    return make_float3(A.x * v.x + A.y * v.y + A.z * v.z, A.y * v.x + A.w * v.y + B.x * v.z,
+                       A.z * v.x + B.x * v.y + B.y * v.z);
+}
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
+    return make_float4(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z), a.w + t * (b.w - a.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+
+__device__ __forceinline__ float4 pix(const CapDesc& C, int x, int y) { return __ldg(&C.img[(size_t)y * C.W + x]); }
+
+// central difference (one-sided at the border) of all four channels
+__device__ __forceinline__ float4 grad_x(const CapDesc& C, int x, int y) {
+    if (C.W < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x == 0) return sub4(pix(C, 1, y), pix(C, 0, y));
+    if (x == C.W - 1) return sub4(pix(C, C.W - 1, y), pix(C, C.W - 2, y));
+    return scale4(sub4(pix(C, x + 1, y), pix(C, x - 1, y)), 0.5f);
+}
+__device__ __forceinline__ float4 grad_y(const CapDesc& C, int x, int y) {
+    if (C.H < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (y == 0) return sub4(pix(C, x, 1), pix(C, x, 0));
+    if (y == C.H - 1) return sub4(pix(C, x, C.H - 1), pix(C, x, C.H - 2));
+    return scale4(sub4(pix(C, x, y + 1), pix(C, x, y - 1)), 0.5f);
+}
+
+// ---------------------------------------------------------------------------
+// Linearisation: residuals, H_i, e_i and the data energy.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __restrict__ caps,
+                                                               const WorkItem* __restrict__ items, int slot) {
+    __shared__ double sh[kVertTile / 32][2];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int i = tile * kVertTile + threadIdx.x;
+    double en[2] = {0.0, 0.0};
+    if (i < C.N) {
+        const uint32_t fl = C.flags[i];
+        const float4 v = C.vw[i];
+        const float2 uv = C.uv[i];
+        const bool ok = v.w > 0.f && in_image(uv, C.W, C.H);
+        const bool ph = ok && (fl & LC_VIS_BIT);
+        const bool si = ok && (fl & LC_INB_BIT);
+        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+        float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        if (ph || si) {
+            const int x0 = (int)floorf(uv.x), y0 = (int)floorf(uv.y);
+            const float fx = uv.x - (float)x0, fy = uv.y - (float)y0;
+            const int x1 = min(x0 + 1, C.W - 1), y1 = min(y0 + 1, C.H - 1);
+            const float4 I = lerp4(lerp4(pix(C, x0, y0), pix(C, x1, y0), fx),
+                                   lerp4(pix(C, x0, y1), pix(C, x1, y1), fx), fy);
+            const float4 Gx = lerp4(lerp4(grad_x(C, x0, y0), grad_x(C, x1, y0), fx),
+                                    lerp4(grad_x(C, x0, y1), grad_x(C, x1, y1), fx), fy);
+            const float4 Gy = lerp4(lerp4(grad_y(C, x0, y0), grad_y(C, x1, y0), fx),
+                                    lerp4(grad_y(C, x0, y1), grad_y(C, x1, y1), fx), fy);
+            const float iz = 1.0f / v.z;
+            const float fz = C.f * iz;
+            const float px = -fz * v.x * iz, py = -fz * v.y * iz;   // d pi / dZ terms
+            auto add_row = [&](float gx, float gy, float s, float r) {
+                const float a0 = s * gx * fz, a1 = s * gy * fz, a2 = s * (gx * px + gy * py);
+                h00 += a0 * a0; h01 += a0 * a1; h02 += a0 * a2;
+                h11 += a1 * a1; h12 += a1 * a2; h22 += a2 * a2;
+                e0 += a0 * r; e1 += a1 * r; e2 += a2 * r;
+            };
+            if (ph) {
+                const float sw = sqrtf(C.w_photo);
+                const float4 alb = C.albedo[i];
+                res.x = sw * (I.x - alb.x);
+                res.y = sw * (I.y - alb.y);
+                res.z = sw * (I.z - alb.z);
+                add_row(Gx.x, Gy.x, sw, res.x);
+                add_row(Gx.y, Gy.y, sw, res.y);
+                add_row(Gx.z, Gy.z, sw, res.z);
+                en[0] = (double)res.x * res.x + (double)res.y * res.y + (double)res.z * res.z;
+            }
+            if (si) {
+                const float sw = sqrtf(C.w_sil);
+                res.w = sw * I.w;
+                const float bs = (fl & LC_BNEG_BIT) ? -sw : sw;
+                add_row(Gx.w, Gy.w, bs, res.w);
+                en[1] = (double)res.w * res.w;
+            }
+        }
+        C.res[i] = res;
+        C.HA[i] = make_float4(h00, h01, h02, h11);
+        C.HB[i] = make_float4(h12, h22, 0.f, 0.f);
+        C.ev[i] = make_float4(e0, e1, e2, (ph || si) ? 1.f : 0.f);
+    }
+    block_sum<2, kVertTile / 32>(en, sh);
+    if (publish_partial<2>(C, CNT_ENERGY, tile, C.vert_tiles, en, C.part)) {
+        double tot[2];
+        sum_partials<2>(C.part, C.vert_tiles, tot);
+        C.sc->e_lin[0] = tot[0];
+        C.sc->e_lin[1] = tot[1];
+    }
+    (void)slot;
+}
+
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st) {
+    linearize_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, gn_slot);
+}
+
+// ---------------------------------------------------------------------------
+// -J^T F, diag(J^T J) and the ARAP energy (warp per node).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __restrict__ caps,
+                                                               const WorkItem* __restrict__ items, int slot,
+                                                               int energy_only) {
+    __shared__ double sh[kNodeWarps][1];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = tile * kNodeTile + w;
+    double en[1] = {0.0};
+    if (k < C.n) {
+        const Rot R = load_R(C.node_R, k);
+        const float3 g = f3(C.node_g[k]), t = f3(C.node_t[k]);
+        float acc[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) acc[j] = 0.f;
+        if (!energy_only) {
+            for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
+                const int2 en2 = C.ent[j];
+                const int i = en2.x;
+                const float wi = __int_as_float(en2.y);
+                const float4 e4 = C.ev[i];
+                if (e4.w == 0.f) continue;
+                const float3 a = mul(R, f3(C.base[i]) - g);
+                const float3 e = f3(e4);
+                const float3 c = cross3(a, e);
+                acc[0] += wi * c.x; acc[1] += wi * c.y; acc[2] += wi * c.z;
+                acc[3] += wi * e.x; acc[4] += wi * e.y; acc[5] += wi * e.z;
+                const float4 HA = C.HA[i], HB = C.HB[i];
+                // columns of [a]x: a x e_x, a x e_y, a x e_z
+                const float3 c0 = make_float3(0.f, a.z, -a.y), c1 = make_float3(-a.z, 0.f, a.x),
+                             c2 = make_float3(a.y, -a.x, 0.f);
+                const float w2 = wi * wi;
+                acc[6] += w2 * dot3(c0, mulH(HA, HB, c0));
+                acc[7] += w2 * dot3(c1, mulH(HA, HB, c1));
+                acc[8] += w2 * dot3(c2, mulH(HA, HB, c2));
+                acc[9] += w2 * HA.x; acc[10] += w2 * HA.w; acc[11] += w2 * HB.y;
+            }
+        }
+        double arap = 0.0;
+        for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
+            const int l = C.edge_dst[j];
+            const float c = C.w_arap * C.edge_s[j];
+            const float3 gl = f3(C.node_g[l]), tl = f3(C.node_t[l]);
+            const float3 b = mul(R, gl - g);
+            const float3 d = b + g + t - gl - tl;
+            arap += (double)c * (double)dot3(d, d);
+            if (energy_only) continue;
+            const float3 bd = cross3(b, d);
+            acc[0] += c * bd.x; acc[1] += c * bd.y; acc[2] += c * bd.z;
+            acc[3] += c * d.x; acc[4] += c * d.y; acc[5] += c * d.z;
+            const float bb = dot3(b, b);
+            acc[6] += c * (bb - b.x * b.x); acc[7] += c * (bb - b.y * b.y); acc[8] += c * (bb - b.z * b.z);
+            // in-edge (l, k): residual R_l (g_k - g_l) + g_l + t_l - g_k - t_k, d/d t_k = -I
+            const Rot Rl = load_R(C.node_R, l);
+            const float3 dl = mul(Rl, g - gl) + gl + tl - g - t;
+            acc[3] -= c * dl.x; acc[4] -= c * dl.y; acc[5] -= c * dl.z;
+            acc[9] += 2.f * c; acc[10] += 2.f * c; acc[11] += 2.f * c;
+        }
+        if (!energy_only) {
+            warp_sumf<12>(acc);
+            if (lane == 0) {
+                C.b[2 * k] = make_float4(-acc[0], -acc[1], -acc[2], 0.f);
+                C.b[2 * k + 1] = make_float4(-acc[3], -acc[4], -acc[5], 0.f);
+                float m[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) m[j] = acc[6 + j] > 0.f ? 1.0f / acc[6 + j] : 0.f;
+                C.minv[2 * k] = make_float4(m[0], m[1], m[2], 0.f);
+                C.minv[2 * k + 1] = make_float4(m[3], m[4], m[5], 0.f);
+                C.diag[2 * k] = make_float4(acc[6], acc[7], acc[8], 0.f);
+                C.diag[2 * k + 1] = make_float4(acc[9], acc[10], acc[11], 0.f);
+            }
+        }
+        en[0] = arap;
+    }
+    block_sum<1, kNodeWarps>(en, sh);
+    if (publish_partial<1>(C, CNT_ARAP, tile, C.node_tiles, en, C.part)) {
+        double tot[1];
+        sum_partials<1>(C.part, C.node_tiles, tot);
+        Scalars* sc = C.sc;
+        sc->e_lin[2] = tot[0];
+        C.hist[2 * slot] = sc->e_lin[0] + sc->e_lin[1] + tot[0];
+    }
+}
+
+void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st) {
+    rhs_kernel<<<hC.node_tiles, kNodeWarps * 32, 0, st>>>(dC, nullptr, slot, energy_only ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// J^T J p: vertex phase (q_i = H_i dv_i), node phase (gather + ARAP).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items,
+                                                                const float4* __restrict__ p, int check_stop) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    if (check_stop && C.sc->stop) return;
+    const int i = tile * kVertTile + threadIdx.x;
+    if (i >= C.N) return;
+    const float4 e4 = C.ev[i];
+    if (e4.w == 0.f) {
+        C.q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float3 v = f3(C.base[i]);
+    const int K = C.K;
+    float3 dv = make_float3(0.f, 0.f, 0.f);
+    for (int s = 0; s < K; ++s) {
+        const int k = C.bind_idx[(size_t)i * K + s];
+        const float w = C.bind_w[(size_t)i * K + s];
+        const Rot R = load_R(C.node_R, k);
+        const float3 a = mul(R, v - f3(C.node_g[k]));
+        const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
+        dv = dv + w * (cross3(pw, a) + pt);
+    }
+    const float3 q = mulH(C.HA[i], C.HB[i], dv);
+    C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
+}
+
+__global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
+                                                                    const WorkItem* __restrict__ items,
+                                                                    const float4* __restrict__ p,
+                                                                    float4* __restrict__ out, int dot) {
+    __shared__ double sh[kNodeWarps][1];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    if (dot && C.sc->stop) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = tile * kNodeTile + w;
+    double pap[1] = {0.0};
+    if (k < C.n) {
+        const Rot R = load_R(C.node_R, k);
+        const float3 g = f3(C.node_g[k]);
+        const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
+            const int2 en2 = C.ent[j];
+            const float4 q4 = C.q[en2.x];
+            if (q4.w == 0.f) continue;
+            const float wi = __int_as_float(en2.y);
+            const float3 a = mul(R, f3(C.base[en2.x]) - g);
+            const float3 q = f3(q4);
+            const float3 c = cross3(a, q);
+            acc[0] += wi * c.x; acc[1] += wi * c.y; acc[2] += wi * c.z;
+            acc[3] += wi * q.x; acc[4] += wi * q.y; acc[5] += wi * q.z;
+        }
+        for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
+            const int l = C.edge_dst[j];
+            const float c = C.w_arap * C.edge_s[j];
+            const float3 gl = f3(C.node_g[l]);
+            const float3 plw = f3(p[2 * l]), plt = f3(p[2 * l + 1]);
+            const float3 b = mul(R, gl - g);
+            const float3 D = cross3(pw, b) + pt - plt;
+            const float3 bD = cross3(b, D);
+            acc[0] += c * bD.x; acc[1] += c * bD.y; acc[2] += c * bD.z;
+            acc[3] += c * D.x; acc[4] += c * D.y; acc[5] += c * D.z;
+            const Rot Rl = load_R(C.node_R, l);
+            const float3 bl = mul(Rl, g - gl);
+            const float3 Dl = cross3(plw, bl) + plt - pt;
+            acc[3] -= c * Dl.x; acc[4] -= c * Dl.y; acc[5] -= c * Dl.z;
+        }
+        warp_sumf<6>(acc);
+        if (lane == 0) {
+            out[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
+            out[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+            pap[0] = (double)pw.x * acc[0] + (double)pw.y * acc[1] + (double)pw.z * acc[2] +
+                     (double)pt.x * acc[3] + (double)pt.y * acc[4] + (double)pt.z * acc[5];
+        }
+    }
+    if (!dot) return;
+    block_sum<1, kNodeWarps>(pap, sh);
+    if (publish_partial<1>(C, CNT_DOT, tile, C.node_tiles, pap, C.part)) {
+        double tot[1];
+        sum_partials<1>(C.part, C.node_tiles, tot);
+        Scalars* sc = C.sc;
+        sc->pAp = tot[0];
+        if (!(tot[0] > 0.0)) {
+            sc->stop = 1;
+            sc->breakdown = 1;
+        }
+    }
+}
+
+void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st) {
+    jtj_vertex_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, p, dot ? 1 : 0);
+    jtj_node_kernel<<<hC.node_tiles, kNodeWarps * 32, 0, st>>>(dC, nullptr, p, out, dot ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// PCG vector kernels (node-parallel, 2 float4 per node, FP64 dots).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dot4(float4 a, float4 b) {
+    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+}
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
+    return make_float4(y.x + a * x.x, y.y + a * x.y, y.z + a * x.z, y.w + a * x.w);
+}
+
+__global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items) {
+    __shared__ double sh[kVecThreads / 32][1];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int k = tile * kVecThreads + threadIdx.x;
+    double rz[1] = {0.0};
+    if (k < C.n) {
+        for (int h = 0; h < 2; ++h) {
+            const float4 b = C.b[2 * k + h];
+            const float4 z = mul4(C.minv[2 * k + h], b);
+            C.x[2 * k + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            C.r[2 * k + h] = b;
+            C.z[2 * k + h] = z;
+            C.p[2 * k + h] = z;
+            rz[0] += dot4(b, z);
+        }
+    }
+    const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
+    block_sum<1, kVecThreads / 32>(rz, sh);
+    if (publish_partial<1>(C, CNT_DOT2, tile, ntiles, rz, C.part)) {
+        double tot[1];
+        sum_partials<1>(C.part, ntiles, tot);
+        Scalars* sc = C.sc;
+        sc->rz = tot[0];
+        sc->stop = tot[0] == 0.0 ? 1 : 0;
+        sc->breakdown = 0;
+        sc->iters = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items) {
+    __shared__ double sh[kVecThreads / 32][1];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    Scalars* sc = C.sc;
+    if (sc->stop) return;
+    const float alpha = (float)(sc->rz / sc->pAp);
+    const int k = tile * kVecThreads + threadIdx.x;
+    double rz[1] = {0.0};
+    if (k < C.n) {
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * k + h;
+            const float4 p = C.p[j];
+            C.x[j] = axpy4(alpha, p, C.x[j]);
+            const float4 r = axpy4(-alpha, C.Ap[j], C.r[j]);
+            const float4 z = mul4(C.minv[j], r);
+            C.r[j] = r;
+            C.z[j] = z;
+            rz[0] += dot4(r, z);
+        }
+    }
+    const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
+    block_sum<1, kVecThreads / 32>(rz, sh);
+    if (publish_partial<1>(C, CNT_DOT2, tile, ntiles, rz, C.part)) {
+        double tot[1];
+        sum_partials<1>(C.part, ntiles, tot);
+        sc->iters += 1;
+        sc->rz_new = tot[0];
+        if (tot[0] == 0.0) {
+            sc->stop = 1;
+        } else {
+            // every other tile has read rz already (it finished before this one)
+            sc->beta = tot[0] / sc->rz;
+            sc->rz = tot[0];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __restrict__ caps,
+                                                               const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    Scalars* sc = C.sc;
+    if (sc->stop) return;
+    const float beta = (float)sc->beta;
+    const int k = tile * kVecThreads + threadIdx.x;
+    if (k < C.n) {
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * k + h;
+            C.p[j] = axpy4(beta, C.p[j], C.z[j]);
+        }
+    }
+}
+
+void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+    pcg_init_kernel<<<(hC.n + kVecThreads - 1) / kVecThreads, kVecThreads, 0, st>>>(dC, nullptr);
+}
+
+void launch_pcg_iteration(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+    const int vb = (hC.n + kVecThreads - 1) / kVecThreads;
+    launch_jtj(dC, hC, hC.p, hC.Ap, true, st);
+    pcg_step_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
+    pcg_dir_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Parameter update: R_k <- Exp(d_omega_k) R_k, t_k += d_t_k.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __restrict__ caps,
+                                                              const WorkItem* __restrict__ items, int slot) {
+    __shared__ double sh[kVecThreads / 32][1];
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int k = tile * kVecThreads + threadIdx.x;
+    double s2[1] = {0.0};
+    if (k < C.n) {
+        const float4 xw = C.x[2 * k], xt = C.x[2 * k + 1];
+        s2[0] = dot4(xw, xw) + dot4(xt, xt);
+        const float th2 = xw.x * xw.x + xw.y * xw.y + xw.z * xw.z;
+        const float th = sqrtf(th2);
+        float A, B;
+        if (th < 1e-4f) {
+            A = 1.f - th2 * (1.f / 6.f);
+            B = 0.5f - th2 * (1.f / 24.f);
+        } else {
+            const float sh2 = sinf(0.5f * th);
+            A = sinf(th) / th;
+            B = 2.f * sh2 * sh2 / th2;
+        }
+        // E = I + A [w]x + B [w]x^2
+        const float wx = xw.x, wy = xw.y, wz = xw.z;
+        const float E00 = 1.f - B * (wy * wy + wz * wz), E11 = 1.f - B * (wx * wx + wz * wz),
+                    E22 = 1.f - B * (wx * wx + wy * wy);
+        const float E01 = -A * wz + B * wx * wy, E10 = A * wz + B * wx * wy;
+        const float E02 = A * wy + B * wx * wz, E20 = -A * wy + B * wx * wz;
+        const float E12 = -A * wx + B * wy * wz, E21 = A * wx + B * wy * wz;
+        const float4 r0 = C.node_R[3 * k], r1 = C.node_R[3 * k + 1], r2 = C.node_R[3 * k + 2];
+        C.node_R[3 * k] = make_float4(E00 * r0.x + E01 * r1.x + E02 * r2.x, E00 * r0.y + E01 * r1.y + E02 * r2.y,
+                                      E00 * r0.z + E01 * r1.z + E02 * r2.z, 0.f);
+        C.node_R[3 * k + 1] = make_float4(E10 * r0.x + E11 * r1.x + E12 * r2.x, E10 * r0.y + E11 * r1.y + E12 * r2.y,
+                                          E10 * r0.z + E11 * r1.z + E12 * r2.z, 0.f);
+        C.node_R[3 * k + 2] = make_float4(E20 * r0.x + E21 * r1.x + E22 * r2.x, E20 * r0.y + E21 * r1.y + E22 * r2.y,
+                                          E20 * r0.z + E21 * r1.z + E22 * r2.z, 0.f);
+        const float4 t = C.node_t[k];
+        C.node_t[k] = make_float4(t.x + xt.x, t.y + xt.y, t.z + xt.z, 0.f);
+    }
+    const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
+    block_sum<1, kVecThreads / 32>(s2, sh);
+    if (publish_partial<1>(C, CNT_STEP, tile, ntiles, s2, C.part)) {
+        double tot[1];
+        sum_partials<1>(C.part, ntiles, tot);
+        Scalars* sc = C.sc;
+        sc->step2 = tot[0];
+        C.hist[2 * slot + 1] = sqrt(tot[0]);
+        C.hist_iters[slot] = sc->iters;
+        C.hist_iters[LC_MAX_GN + 1] += sc->breakdown;
+    }
+}
+
+void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st) {
+    update_kernel<<<(hC.n + kVecThreads - 1) / kVecThreads, kVecThreads, 0, st>>>(dC, nullptr, gn_slot);
+}
+
+// ---------------------------------------------------------------------------
+// 6n <-> two float4 per node
+// ---------------------------------------------------------------------------
+__global__ void pack_vec_kernel(const float* __restrict__ in, float4* __restrict__ out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[2 * k] = make_float4(in[6 * k], in[6 * k + 1], in[6 * k + 2], 0.f);
+    out[2 * k + 1] = make_float4(in[6 * k + 3], in[6 * k + 4], in[6 * k + 5], 0.f);
+}
+__global__ void unpack_vec_kernel(const float4* __restrict__ in, float* __restrict__ out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 a = in[2 * k], b = in[2 * k + 1];
+    out[6 * k] = a.x; out[6 * k + 1] = a.y; out[6 * k + 2] = a.z;
+    out[6 * k + 3] = b.x; out[6 * k + 4] = b.y; out[6 * k + 5] = b.z;
+}
+void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st) {
+    pack_vec_kernel<<<(n + 127) / 128, 128, 0, st>>>(in6, out, n);
+}
+void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st) {
+    unpack_vec_kernel<<<(n + 127) / 128, 128, 0, st>>>(in, out6, n);
+}
+
+}  // namespace lc

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of the livecap C ABI (include/livecap.h).
+
+Argument marshalling only: every computation runs in the CUDA library.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+device memory); they must be C-contiguous with the dtype the C call takes.
+Outputs default to freshly allocated numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LC_OK, LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_NUMERIC, LC_ERR_TIMEOUT, LC_ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+LC_MAX_GN = 64
+FLAG_VISIBLE, FLAG_ONSIL, FLAG_INB, FLAG_BNEG = 1, 2, 4, 8
+
+
+class lc_params(ctypes.Structure):
+    _fields_ = [("w_photo", ctypes.c_float), ("w_sil", ctypes.c_float), ("w_arap", ctypes.c_float),
+                ("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("eps_vis", ctypes.c_float),
+                ("lambda_2d", ctypes.c_float), ("lambda_3d", ctypes.c_float), ("lambda_sil", ctypes.c_float),
+                ("n_gn_pose", ctypes.c_int)]
+
+
+class lc_solve_stats(ctypes.Structure):
+    _fields_ = [("e_photo", ctypes.c_double), ("e_sil", ctypes.c_double), ("e_arap", ctypes.c_double),
+                ("e_total", ctypes.c_double), ("e_gn", ctypes.c_double * LC_MAX_GN),
+                ("step_norm", ctypes.c_double * LC_MAX_GN), ("pcg_iters", ctypes.c_int * LC_MAX_GN),
+                ("n_gn_done", ctypes.c_int), ("n_visible", ctypes.c_int), ("n_boundary", ctypes.c_int),
+                ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int)]
+
+    def to_dict(self) -> dict:
+        g = self.n_gn_done
+        return dict(e_photo=self.e_photo, e_sil=self.e_sil, e_arap=self.e_arap, e_total=self.e_total,
+                    e_gn=list(self.e_gn[:g]), step_norm=list(self.step_norm[:g]),
+                    pcg_iters=list(self.pcg_iters[:g]), n_visible=self.n_visible,
+                    n_boundary=self.n_boundary, n_boundary_neg=self.n_boundary_neg,
+                    pcg_breakdowns=self.pcg_breakdowns)
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "lc_create": [ctypes.POINTER(_P), ctypes.c_int, _P],
+    "lc_destroy": [_P],
+    "lc_last_error": [_P],
+    "lc_params_default": [ctypes.POINTER(lc_params)],
+    "lc_set_params": [_P, ctypes.POINTER(lc_params)],
+    "lc_set_camera": [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int],
+    "lc_upload_template": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P],
+    "lc_build_graph": [_P, ctypes.c_int, ctypes.c_int],
+    "lc_read_graph": [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)],
+    "lc_set_node_params": [_P, _P, _P],
+    "lc_upload_frame": [_P, _P, _P, _P, _P, _P],
+    "lc_solve_nonrigid": [_P, ctypes.POINTER(lc_solve_stats)],
+    "lc_read_back": [_P, _P, _P, _P, _P, _P],
+    "lc_compute_visibility": [_P],
+    "lc_read_visibility": [_P, _P, _P, _P],
+    "lc_eval_linearization": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "lc_eval_gradient": [_P, _P, _P],
+    "lc_apply_jtj": [_P, _P, _P],
+    "lc_solve_linear": [_P, _P, ctypes.POINTER(ctypes.c_int)],
+    "lc_upload_skeleton": [_P, ctypes.c_int, _P, _P, _P, _P, _P],
+    "lc_set_pose": [_P, _P],
+    "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblivecap.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"livecap library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "lc_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class LivecapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"livecap status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(a) -> Optional[int]:
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _arr(a, dtype):
+    """numpy arrays are converted to a contiguous copy of `dtype`; torch
+    tensors must already have the matching dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+class Context:
+    """One capture: template, graph, frame and solver state on one GPU."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load()
+        h = _P()
+        st = 0
+        if stream is not None:
+            st = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.lc_create(ctypes.byref(h), device, st), None)
+        self.h = h
+        self.N = self.n = self.K = 0
+        self.W = self.H = 0
+        self.n_dof = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st: int, h=0):
+        if st != LC_OK:
+            msg = "" if h is None else self._lib.lc_last_error(self.h if h == 0 else h).decode()
+            raise LivecapError(st, msg)
+
+    # ---- setup
+    def params(self) -> lc_params:
+        p = lc_params()
+        self._lib.lc_params_default(ctypes.byref(p))
+        return p
+
+    def set_params(self, **kw):
+        p = self.params() if not hasattr(self, "_params") else self._params
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._check(self._lib.lc_set_params(self.h, ctypes.byref(p)))
+        self._params = p
+
+    def set_camera(self, f, cx, cy, W, H):
+        self._check(self._lib.lc_set_camera(self.h, float(f), float(cx), float(cy), int(W), int(H)))
+        self.W, self.H = int(W), int(H)
+
+    def upload_template(self, V, tris, albedo, material):
+        V = _arr(V, np.float32)
+        tris = _arr(tris, np.int32)
+        albedo = _arr(albedo, np.float32)
+        material = _arr(material, np.float32)
+        N, F = len(V), len(tris)
+        self._check(self._lib.lc_upload_template(self.h, _ptr(V), N, _ptr(tris), F, _ptr(albedo), _ptr(material)))
+        self.N = N
+
+    def build_graph(self, n_nodes: int, K: int):
+        self._check(self._lib.lc_build_graph(self.h, int(n_nodes), int(K)))
+        self.n, self.K = int(n_nodes), int(K)
+
+    def read_graph(self) -> dict:
+        ne = ctypes.c_int(0)
+        self._check(self._lib.lc_read_graph(self.h, None, None, None, None, None, None, ctypes.byref(ne)))
+        E = ne.value
+        out = dict(node_vid=np.zeros(self.n, np.int32), bind_idx=np.zeros((self.N, self.K), np.int32),
+                   bind_w=np.zeros((self.N, self.K), np.float32), edge_off=np.zeros(self.n + 1, np.int32),
+                   edge_dst=np.zeros(E, np.int32), edge_s=np.zeros(E, np.float32))
+        self._check(self._lib.lc_read_graph(self.h, *(_ptr(out[k]) for k in
+                                                       ("node_vid", "bind_idx", "bind_w", "edge_off",
+                                                        "edge_dst", "edge_s")), None))
+        return out
+
+    def set_node_params(self, R=None, t=None):
+        R = _arr(R, np.float32)
+        t = _arr(t, np.float32)
+        self._check(self._lib.lc_set_node_params(self.h, _ptr(R), _ptr(t)))
+
+    def upload_frame(self, rgb, dt, mask, joints2d=None, joints3d=None):
+        rgb = _arr(rgb, np.float32)
+        dt = _arr(dt, np.float32)
+        mask = _arr(mask, np.uint8)
+        j2 = _arr(joints2d, np.float32)
+        j3 = _arr(joints3d, np.float32)
+        self._check(self._lib.lc_upload_frame(self.h, _ptr(rgb), _ptr(dt), _ptr(mask), _ptr(j2), _ptr(j3)))
+
+    # ---- solve
+    def solve_nonrigid(self, stats: bool = True):
+        if not stats:
+            self._check(self._lib.lc_solve_nonrigid(self.h, None))
+            return None
+        s = lc_solve_stats()
+        self._check(self._lib.lc_solve_nonrigid(self.h, ctypes.byref(s)))
+        return s.to_dict()
+
+    def read_back(self, R=True, t=True, V=True, flags=True, pose=False):
+        out = {}
+        if R:
+            out["R"] = np.zeros((self.n, 3, 3), np.float32)
+        if t:
+            out["t"] = np.zeros((self.n, 3), np.float32)
+        if V:
+            out["V"] = np.zeros((self.N, 3), np.float32)
+        if flags:
+            out["flags"] = np.zeros(self.N, np.uint8)
+        if pose:
+            out["pose"] = np.zeros(self.n_dof, np.float32)
+        self._check(self._lib.lc_read_back(self.h, _ptr(out.get("R")), _ptr(out.get("t")), _ptr(out.get("V")),
+                                           _ptr(out.get("flags")), _ptr(out.get("pose"))))
+        return out
+
+    # ---- inspection
+    def compute_visibility(self):
+        self._check(self._lib.lc_compute_visibility(self.h))
+
+    def read_visibility(self) -> dict:
+        out = dict(zbuf=np.zeros((self.H, self.W), np.uint64), flags=np.zeros(self.N, np.uint8),
+                   uv=np.zeros((self.N, 2), np.float32))
+        self._check(self._lib.lc_read_visibility(self.h, _ptr(out["zbuf"]), _ptr(out["flags"]), _ptr(out["uv"])))
+        return out
+
+    def eval_linearization(self) -> dict:
+        N = self.N
+        out = dict(v=np.zeros((N, 3), np.float32), uv=np.zeros((N, 2), np.float32),
+                   r_photo=np.zeros((N, 3), np.float32), r_sil=np.zeros(N, np.float32),
+                   H=np.zeros((N, 6), np.float32), e=np.zeros((N, 3), np.float32), energy=np.zeros(3))
+        self._check(self._lib.lc_eval_linearization(self.h, *(_ptr(out[k]) for k in
+                                                               ("v", "uv", "r_photo", "r_sil", "H", "e",
+                                                                "energy"))))
+        return out
+
+    def eval_gradient(self):
+        rhs = np.zeros(6 * self.n, np.float32)
+        diag = np.zeros(6 * self.n, np.float32)
+        self._check(self._lib.lc_eval_gradient(self.h, _ptr(rhs), _ptr(diag)))
+        return rhs, diag
+
+    def apply_jtj(self, p):
+        p = _arr(p, np.float32)
+        out = np.zeros(6 * self.n, np.float32)
+        self._check(self._lib.lc_apply_jtj(self.h, _ptr(p), _ptr(out)))
+        return out
+
+    def solve_linear(self):
+        d = np.zeros(6 * self.n, np.float32)
+        it = ctypes.c_int(0)
+        self._check(self._lib.lc_solve_linear(self.h, _ptr(d), ctypes.byref(it)))
+        return d, it.value
+
+    # ---- pose stage
+    def upload_skeleton(self, parents, joints_rest, dof, skin_idx, skin_w):
+        parents = _arr(parents, np.int32)
+        joints_rest = _arr(joints_rest, np.float32)
+        dof = _arr(dof, np.uint8)
+        skin_idx = _arr(skin_idx, np.int32)
+        skin_w = _arr(skin_w, np.float32)
+        J = len(parents)
+        self._check(self._lib.lc_upload_skeleton(self.h, J, _ptr(parents), _ptr(joints_rest), _ptr(dof),
+                                                 _ptr(skin_idx), _ptr(skin_w)))
+        self.n_dof = 6 + 3 * int(np.count_nonzero(np.asarray(dof)[1:]))
+
+    def set_pose(self, pose):
+        pose = _arr(pose, np.float32)
+        self._check(self._lib.lc_set_pose(self.h, _ptr(pose)))
+
+    def solve_pose(self, stats: bool = True):
+        if not stats:
+            self._check(self._lib.lc_solve_pose(self.h, None))
+            return None
+        s = lc_solve_stats()
+        self._check(self._lib.lc_solve_pose(self.h, ctypes.byref(s)))
+        return s.to_dict()
+
+
+def setup_scene(ctx: Context, scene, with_frame: bool = True):
+    """Upload a ``synth.Scene`` (template, camera, graph, weights, frame)."""
+    wp, ws, wa = scene.weights
+    ctx.set_params(w_photo=wp, w_sil=ws, w_arap=wa, n_gn=scene.n_gn, n_pcg=scene.n_pcg)
+    ctx.set_camera(scene.cam.f, scene.cam.cx, scene.cam.cy, scene.cam.W, scene.cam.H)
+    ctx.upload_template(scene.V, scene.F, scene.albedo, scene.material)
+    ctx.build_graph(scene.n_nodes, scene.K)
+    if with_frame:
+        ctx.upload_frame(scene.rgb, scene.dt, scene.mask.astype(np.uint8), scene.joints2d, scene.joints3d)

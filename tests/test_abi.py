@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every declared entry point
+(CPU: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lc_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1810_02648_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_all_declared_symbols_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_1810_02648_gb300 import livecap
+    assert set(_declared()) <= set(livecap._SIGS)
+
+
+def test_no_device_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1810_02648_gb300 import Context, LivecapError
+    with pytest.raises(LivecapError):
+        Context(0)
+
+
+def test_params_default(lib):
+    from paper_1810_02648_gb300 import livecap
+    livecap.load()
+    p = livecap.lc_params()
+    assert livecap.load().lc_params_default(ctypes.byref(p)) == 0
+    # pose-stage weights from the paper's parameter list (Sec. 5)
+    assert (p.lambda_2d, p.lambda_3d, p.lambda_sil) == (460.0, 28.0, 200.0)
+    assert (p.n_gn, p.n_pcg) == (5, 20)

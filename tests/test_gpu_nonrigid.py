@@ -1,0 +1,260 @@
+"""GPU parity of the non-rigid stage against the FP64 oracle.
+
+Integer work (node sampling, binding indices, node edges, z-buffer keys,
+visibility / contour / b_i flags, projections used for the decisions) must
+be bit-exact.  Floating-point tolerances (FP32 kernels vs FP64 oracle):
+
+* per residual, at identical FP32 inputs of the residual kernel:
+  |r_gpu - r_ref| <= 1e-5 * max(|r_ref|, full scale of the term), the full
+  scale being sqrt(w) times one image unit (one colour unit for photometric
+  rows, one pixel for silhouette rows);
+* per-vertex normal blocks H_i, e_i: 1e-5 of the block's largest entry;
+* J^T F, diag(J^T J), J^T J p per node vector: 1e-4 of the vector's largest
+  entry (FP32 accumulation over the node's ~50-200 vertex terms plus the
+  FP32-vs-FP64 warp, ~1e-7 relative per term);
+* end to end: final energy relative difference <= 1e-4, vertex positions
+  within 1e-4 x the template's bounding-box diagonal.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import (graph_from_gpu, oracle_problem, oracle_vertex_blocks, random_params, report,
+                         set_flags, vec6)
+from oracle import graph as ograph
+from oracle import nonrigid as onr
+from oracle import visibility as ovis
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(scene, **params):
+    from paper_1810_02648_gb300 import Context, setup_scene
+    ctx = Context(0)
+    setup_scene(ctx, scene)
+    if params:
+        ctx.set_params(**params)
+    return ctx
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.make_scene("tiny")
+
+
+@pytest.fixture(scope="module")
+def body():
+    return synth.make_scene("body")
+
+
+def _ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
+    V, F = synth.capsule_mesh(0.3, 1.0, rings, segs)
+    V = V + np.array([shift, 0.0, 3.0])
+    cam = synth.Camera(f=150.0 * side / 128.0, W=side, H=side + 7)
+    alb = synth.value_noise_albedo(V, seed)
+    mat = synth.half_split_material(V, seed)
+    gt = synth.smooth_deformation(V, min(n_nodes, len(V)), 0.05, 0.01, seed)
+    rgb, mask = synth.render(gt["V"], F, alb, cam)
+    rng = np.random.default_rng(seed)
+    rgb = (rgb + rng.normal(0, 0.01, rgb.shape)).astype(np.float32)
+    dt = synth.contour_distance_transform(mask).astype(np.float32)
+    return synth.Scene("ragged", cam, V.astype(np.float32), F.astype(np.int32), alb.astype(np.float32),
+                       mat.astype(np.float32), rgb, dt, mask, n_nodes, K, 4, 15, (1.0, 0.1, 10.0), gt["V"])
+
+
+# ---------------------------------------------------------------------------
+# graph construction (integer work bit-exact)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["tiny", "ragged_k3", "ragged_k8", "min_nodes", "body"])
+def test_graph_matches_oracle(case, tiny, body):
+    scene = {"tiny": tiny, "body": body}.get(case)
+    if case == "ragged_k3":
+        scene = _ragged_scene(13, 11, 37, 3)
+    elif case == "ragged_k8":
+        scene = _ragged_scene(17, 9, 50, 8)
+    elif case == "min_nodes":
+        scene = _ragged_scene(6, 7, 5, 4)
+    ctx = _ctx(scene)
+    g = ctx.read_graph()
+    ref = ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
+    assert np.array_equal(g["node_vid"], ref["node_vid"])
+    assert np.array_equal(g["bind_idx"], ref["bind_idx"])
+    assert np.array_equal(g["bind_w"], ref["bind_w"].astype(np.float32)) or \
+        np.abs(g["bind_w"] - ref["bind_w"]).max() <= 2.5e-7
+    from gpu_helpers import csr_edges
+    assert np.array_equal(csr_edges(g), ref["edges"])
+    assert np.allclose(g["edge_s"], ref["edge_s"], rtol=1e-7, atol=0)
+    report(f"graph_{case}", w_maxdiff=np.abs(g["bind_w"] - ref["bind_w"]).max(), E=len(ref["edges"]))
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# visibility / contour / b_i (bit-exact) and the warp
+# ---------------------------------------------------------------------------
+def _vis_case(scene, params_seed, tag):
+    ctx = _ctx(scene)
+    n = scene.n_nodes
+    if params_seed is not None:
+        R, t = random_params(n, params_seed)
+        ctx.set_node_params(R.reshape(n, 9), t)
+    ctx.compute_visibility()
+    vis = ctx.read_visibility()
+    lin = ctx.eval_linearization()
+    ref = ovis.visibility(lin["v"], scene.F, scene.cam.f, scene.cam.cx, scene.cam.cy, scene.cam.W, scene.cam.H,
+                          scene.dt, scene.mask.astype(np.uint8))
+    assert np.array_equal(vis["uv"], ref["uv"])
+    assert np.array_equal(vis["zbuf"], ref["zbuf"])
+    assert np.array_equal(vis["flags"], ref["flags"])
+    # warp vs FP64 oracle at the same parameters
+    g = ctx.read_graph()
+    P = oracle_problem(scene, g)
+    if params_seed is None:
+        Rr, tr = onr.identity_params(n)
+    else:
+        Rr, tr = R.astype(np.float64), t.astype(np.float64)
+    vref = onr.warp(P, Rr, tr)
+    dv = np.abs(lin["v"] - vref).max()
+    report(f"vis_{tag}", n_vis=int((vis["flags"] & 1).sum()), n_B=int((vis["flags"] & 4).sum()),
+           n_bneg=int((vis["flags"] & 8).sum()), warp_maxdiff=dv)
+    if params_seed is None:
+        assert np.array_equal(lin["v"], P.base.astype(np.float32))
+    assert dv <= 4e-6 * np.abs(vref).max()
+    assert (vis["flags"] & 1).sum() > 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("params_seed", [None, 1])
+def test_visibility_bit_exact_tiny(tiny, params_seed):
+    _vis_case(tiny, params_seed, f"tiny_{params_seed}")
+
+
+def test_visibility_bit_exact_body(body):
+    _vis_case(body, 2, "body")
+
+
+def test_visibility_partially_outside():
+    _vis_case(_ragged_scene(20, 16, 40, 4, side=80, shift=0.45), 3, "outside")
+
+
+# ---------------------------------------------------------------------------
+# per-kernel floating-point parity at identical inputs
+# ---------------------------------------------------------------------------
+def _lin_case(scene, seed, tag):
+    ctx = _ctx(scene)
+    n = scene.n_nodes
+    R, t = random_params(n, seed)
+    ctx.set_node_params(R.reshape(n, 9), t)
+    ctx.compute_visibility()
+    lin = ctx.eval_linearization()
+    g = ctx.read_graph()
+    flags = ctx.read_visibility()["flags"]
+    P = oracle_problem(scene, g, flags)
+    ref = oracle_vertex_blocks(P, lin["v"], lin["uv"])
+    sp = np.sqrt(P.w_photo)
+    ss = np.sqrt(P.w_sil)
+    d_ph = np.abs(lin["r_photo"] - ref["r_photo"]) / np.maximum(np.abs(ref["r_photo"]), sp)
+    d_si = np.abs(lin["r_sil"] - ref["r_sil"]) / np.maximum(np.abs(ref["r_sil"]), ss)
+    scale = np.maximum(np.abs(ref["H"]).max(1), 1e-30)
+    d_H = (np.abs(lin["H"] - ref["H"]).max(1) / scale)
+    escale = np.maximum(np.abs(ref["e"]).max(1), np.sqrt(scale) * sp)
+    d_e = np.abs(lin["e"] - ref["e"]).max(1) / escale
+    # energies at the GPU's inputs
+    e_ref = np.array([(ref["r_photo"] ** 2).sum(), (ref["r_sil"] ** 2).sum(),
+                      (onr.arap_residuals(P, R.astype(np.float64), t.astype(np.float64)) ** 2).sum()])
+    d_en = np.abs(lin["energy"] - e_ref) / np.maximum(e_ref, 1e-12)
+    report(f"lin_{tag}", r_photo=d_ph.max(), r_sil=d_si.max(), H=d_H.max(), e=d_e.max(),
+           energy=d_en.max(), n_photo=int(ref["photo_on"].sum()), n_sil=int(ref["sil_on"].sum()))
+    assert d_ph.max() <= 1e-5 and d_si.max() <= 1e-5
+    assert d_H.max() <= 1e-5 and d_e.max() <= 1e-5
+    assert d_en.max() <= 1e-5
+
+    # J^T F, diag, J^T J p against the oracle's assembled J at the same parameters
+    rhs, diag = ctx.eval_gradient()
+    Rr, tr = R.astype(np.float64), t.astype(np.float64)
+    F, J = onr.linearise(P, Rr, tr)
+    JT = J.T.tocsr()
+    rhs_ref = -(JT @ F)
+    diag_ref = np.asarray((JT.multiply(JT)).sum(1)).ravel()
+    rng = np.random.default_rng(seed + 100)
+    p = rng.normal(size=6 * n).astype(np.float32)
+    Ap = ctx.apply_jtj(p)
+    Ap_ref = JT @ (J @ p.astype(np.float64))
+    d_rhs = np.abs(vec6(rhs) - rhs_ref).max() / np.abs(rhs_ref).max()
+    d_diag = np.abs(vec6(diag) - diag_ref).max() / np.abs(diag_ref).max()
+    d_Ap = np.abs(vec6(Ap) - Ap_ref).max() / np.abs(Ap_ref).max()
+    report(f"normal_eq_{tag}", rhs=d_rhs, diag=d_diag, jtjp=d_Ap)
+    assert d_rhs <= 1e-4 and d_diag <= 1e-4 and d_Ap <= 1e-4
+
+    # PCG: the GPU's n_pcg-step solution vs the oracle's on J^T J from the oracle
+    delta, iters = ctx.solve_linear()
+    A = (JT @ J).tocsr()
+    dref, info = onr.pcg(A, rhs_ref, scene.n_pcg)
+    d_pcg = np.linalg.norm(vec6(delta) - dref) / np.linalg.norm(dref)
+    report(f"pcg_{tag}", rel=d_pcg, iters=iters, iters_ref=info["iters"])
+    assert iters == info["iters"]
+    assert d_pcg <= 1e-3
+    ctx.close()
+
+
+def test_linearization_tiny(tiny):
+    _lin_case(tiny, 11, "tiny")
+
+
+def test_linearization_body(body):
+    _lin_case(body, 12, "body")
+
+
+def test_linearization_ragged():
+    _lin_case(_ragged_scene(13, 11, 37, 3, side=70, shift=0.3), 13, "ragged")
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+def _e2e(scene, tag, base32=None):
+    ctx = _ctx(scene)
+    stats = ctx.solve_nonrigid()
+    out = ctx.read_back()
+    g = ctx.read_graph()
+    ref = onr.solve_scene(scene, graph=graph_from_gpu(g), base32=base32)
+    e_gpu, e_ref = stats["e_total"], ref["e1"]["total"]
+    rel = abs(e_gpu - e_ref) / abs(e_ref)
+    diag = np.linalg.norm(scene.V.max(0) - scene.V.min(0))
+    dv = np.abs(out["V"].astype(np.float64) - ref["v"]).max()
+    P = ref["problem"]
+    f_ref = (P.vis.astype(np.uint8) * 1) | (P.inB.astype(np.uint8) * 4) | ((P.bsign < 0).astype(np.uint8) * 8)
+    e_hist = np.array(stats["e_gn"])
+    e_hist_ref = np.array([h["energy"] for h in ref["hist"]])
+    report(f"e2e_{tag}", e_gpu=e_gpu, e_ref=e_ref, rel=rel, dv=dv, dv_over_diag=dv / diag,
+           hist_rel=np.abs(e_hist - e_hist_ref).max() / e_hist_ref.max(),
+           n_vis=stats["n_visible"], n_B=stats["n_boundary"])
+    assert np.array_equal(out["flags"] & 13, f_ref)
+    assert stats["n_visible"] == int(P.vis.sum()) and stats["n_boundary"] == int(P.inB.sum())
+    assert rel <= 1e-4
+    assert dv <= 1e-4 * diag
+    # a second solve from the result is deterministic: replaying the same
+    # graph from the same state gives bit-identical output
+    ctx.set_node_params(None, None)
+    stats2 = ctx.solve_nonrigid()
+    out2 = ctx.read_back()
+    assert stats2["e_total"] == e_gpu and np.array_equal(out2["V"], out["V"])
+    ctx.close()
+    return stats
+
+
+def test_end_to_end_tiny(tiny):
+    _e2e(tiny, "tiny")
+
+
+def test_end_to_end_ragged():
+    _e2e(_ragged_scene(15, 13, 41, 4, side=90, shift=0.2), "ragged")
+
+
+def test_empty_frame(tiny):
+    """No foreground: DT and mask are zero, the image is black."""
+    s = synth.make_scene("tiny")
+    s.rgb = np.zeros_like(s.rgb)
+    s.dt = np.zeros_like(s.dt)
+    s.mask = np.zeros_like(s.mask)
+    stats = _e2e(s, "empty")
+    assert stats["n_boundary_neg"] == 0
