@@ -86,3 +86,58 @@ def oracle_vertex_blocks(P, v32, uv32):
         e[isl] += A[:, 0, :] * r_sil[isl, None]
     H6 = np.stack([H[:, 0, 0], H[:, 0, 1], H[:, 0, 2], H[:, 1, 1], H[:, 1, 2], H[:, 2, 2]], 1)
     return dict(r_photo=r_photo, r_sil=r_sil, H=H6, e=e, photo_on=ph, sil_on=si)
+
+
+def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None):
+    """Spread of the oracle's end-to-end result when its CG vectors and
+    matrix-vector products are rounded to FP32 with a random tie-break
+    perturbation of one unit roundoff (seeded).  This measures how far any
+    FP32 execution of the same algorithm may land from the FP64 result: CG
+    amplifies rounding along the system's ill-conditioned (depth) directions.
+    Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
+    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
+    orig = onr.pcg
+    dE, dV = 0.0, 0.0
+    u = 2.0 ** -24
+    for seed in range(n_runs):
+        rng = np.random.default_rng(1000 + seed)
+
+        def r32(x):
+            return (x * (1.0 + u * rng.standard_normal(x.shape))).astype(np.float32).astype(np.float64)
+
+        def pcg32(A, b, n):
+            d = np.asarray(A.diagonal(), dtype=np.float64)
+            minv = r32(np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0))
+            x = np.zeros_like(b)
+            r = r32(b)
+            z = r32(minv * r)
+            p = z.copy()
+            rz = float(r @ z)
+            info = dict(iters=0, breakdown=False, rz=[rz])
+            if rz == 0.0:
+                return x, info
+            for it in range(n):
+                Ap = r32(A @ p)
+                pAp = float(p @ Ap)
+                if not pAp > 0.0:
+                    info["breakdown"] = True
+                    break
+                al = np.float32(rz / pAp)
+                x = r32(x + al * p)
+                r = r32(r - al * Ap)
+                z = r32(minv * r)
+                rzn = float(r @ z)
+                info["iters"] = it + 1
+                if rzn == 0.0:
+                    break
+                p = r32(z + np.float32(rzn / rz) * p)
+                rz = rzn
+            return x, info
+        onr.pcg = pcg32
+        try:
+            o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
+        finally:
+            onr.pcg = orig
+        dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
+        dV = max(dV, float(np.abs(o["v"] - ref["v"]).max()))
+    return ref, dE, dV
