@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the LiveCap Gauss-Newton hot path on GB300.
+
+Metric: GN-solve frames/s (higher is better) on the full-body workload
+(articulated capsule body, 6,020 vertices / 12,000 triangles, 500 graph nodes,
+K = 4, 1024x1024 frame, 10 Gauss-Newton x 40 PCG iterations), plus the
+matrix-free J^T J p kernel's achieved bandwidth against the measured HBM
+peak.  Inputs are seeded synthetic frames (``synth``); every step solves one
+frame whose data already sits in device memory; L2 is flushed (a 256 MiB
+write, outside the timed events) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent capture per GPU (replicas, weak scaling, no
+collective in the data path); launched by torch.distributed.run.
+``--impl reference`` times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GN-solve frames/s at equal final energy; J^TJp HBM GB/s vs GB300 peak"
+UNIT = "frames/s"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["body", "tiny", "stress"], default="body")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(scene, stages):
+    return {"workload": f"{scene.name}: {scene.N} vertices / {len(scene.F)} triangles, "
+                        f"{scene.n_nodes} nodes K={scene.K}, {scene.cam.W}x{scene.cam.H} frame, "
+                        f"{stages}, {scene.n_gn} GN x {scene.n_pcg} PCG",
+            "vertices": int(scene.N), "triangles": int(len(scene.F)), "nodes": int(scene.n_nodes),
+            "K": int(scene.K), "image": [int(scene.cam.W), int(scene.cam.H)],
+            "gn_iters": int(scene.n_gn), "pcg_iters": int(scene.n_pcg),
+            "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    name, seed, seconds = args
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    import synth
+    from oracle import nonrigid as onr
+    from oracle import graph as ograph
+    scene = synth.make_scene(name, seed=seed)
+    g = ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        onr.solve_scene(scene, graph=g)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(name, seconds):
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(name, 100 + c, seconds) for c in range(cores)])
+    frames = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": frames / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{frames} non-rigid frame solves of the {name} workload by the FP64 oracle, "
+                      f"one single-threaded process per core for ~{seconds:.0f} s"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    import synth
+    from oracle import nonrigid as onr
+    from oracle import graph as ograph
+    scene = synth.make_scene(a.workload)
+    g = ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
+    for _ in range(a.warmup):
+        onr.solve_scene(scene, graph=g)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        onr.solve_scene(scene, graph=g)
+    dt = time.perf_counter() - t0
+    v = a.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(scene, "non-rigid stage"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{a.steps} frame solves, one single-threaded process"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def jtj_algorithmic_bytes(scene, n_active, n_edges):
+    """Minimal bytes one J^T J p must move: per active vertex its K node
+    indices and weights, rest position and H_i (8K + 12 + 24 bytes); per node
+    R, g and p read (72 B) and the result written (24 B); per directed edge
+    two indices and a weight (12 B)."""
+    return (8 * scene.K + 36) * n_active + 96 * scene.n_nodes + 12 * n_edges
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1810_02648_gb300 import Context, setup_scene
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    cpu_base = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        # spawn the oracle pool before the first GPU call
+        cpu_base = cpu_baseline(a.workload, a.cpu_seconds)
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    scene = synth.make_scene(a.workload, seed=None if rank == 0 else 1000 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream=stream)
+    setup_scene(ctx, scene)
+    stages = "non-rigid stage"
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        # each frame starts from the identity deformation (device-side reset)
+        ctx.set_node_params(None, None)
+        ctx.solve_nonrigid(stats=False)
+
+    for _ in range(a.warmup):
+        step()
+    stats = ctx.solve_nonrigid(stats=True)
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * a.steps / (total_ms / 1e3)
+
+    # per-phase device time (event chain in the captured solve), same workload
+    ctx.set_profiling(True)
+    n_prof = min(a.steps, 20)
+    for _ in range(n_prof):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    prof = ctx.read_profile()
+    ctx.set_profiling(False)
+    g = ctx.read_graph()
+    E = len(g["edge_dst"])
+    n_active = stats["n_visible"]
+    jtj_ms, jtj_n = prof["jtj"]
+    jtj_bytes = jtj_algorithmic_bytes(scene, n_active, E)
+    peak, peak_kind = measured_peaks()
+    achieved = jtj_bytes / (jtj_ms / jtj_n * 1e-3) / 1e9 if jtj_n else None
+
+    # end to end through the C ABI: pinned host frame in, result out
+    rgb = torch.from_numpy(np.ascontiguousarray(scene.rgb)).pin_memory()
+    dtm = torch.from_numpy(np.ascontiguousarray(scene.dt)).pin_memory()
+    msk = torch.from_numpy(scene.mask.astype(np.uint8)).pin_memory()
+    outR = torch.empty((scene.n_nodes, 9), dtype=torch.float32).pin_memory()
+    outT = torch.empty((scene.n_nodes, 3), dtype=torch.float32).pin_memory()
+    outV = torch.empty((scene.N, 3), dtype=torch.float32).pin_memory()
+    lib = ctx._lib
+    from paper_1810_02648_gb300.livecap import _ptr
+    n_e2e = max(10, a.steps // 2)
+
+    def e2e_step():
+        ctx._check(lib.lc_upload_frame(ctx.h, _ptr(rgb), _ptr(dtm), _ptr(msk), None, None))
+        ctx._check(lib.lc_set_node_params(ctx.h, None, None))
+        ctx._check(lib.lc_solve_nonrigid(ctx.h, None))
+        ctx._check(lib.lc_read_back(ctx.h, _ptr(outR), _ptr(outT), _ptr(outV), None, None))
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    h2d = rgb.numel() * 4 + dtm.numel() * 4 + msk.numel()
+    d2h = (outR.numel() + outT.numel() + outV.numel()) * 4
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    phases = {k: {"ms_per_frame": v[0] / n_prof, "segments_per_frame": v[1] / n_prof}
+              for k, v in prof.items() if v[1]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(scene, stages),
+        "clocks": clk.summary(),
+        "e2e": {"value": world * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": (int(stats["n_kernels"]) + 1) * a.steps,
+        "roofline": {"kernel": "jtj (matrix-free J^T J p: vertex + node phase)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": jtj_bytes,
+                     "avg_launch_us": 1e3 * jtj_ms / jtj_n if jtj_n else None,
+                     "note": "working set is L2-resident at this size; per-launch time is latency-bound"},
+        "phases": phases,
+        "solve": {"e_total": stats["e_total"], "n_visible": stats["n_visible"],
+                  "n_boundary": stats["n_boundary"], "kernels_per_frame": stats["n_kernels"]},
+        "cpu_baseline": cpu_base,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -80,6 +80,7 @@ typedef struct {
     int n_boundary;                          /* |B| contour vertices */
     int n_boundary_neg;                      /* contour vertices with b_i = -1 */
     int pcg_breakdowns;                      /* steps whose PCG stopped on p^T A p <= 0 */
+    int n_kernels;                           /* kernel launches in one solve (captured graph) */
 } lc_solve_stats;
 
 /* Vertex flag bits returned by lc_read_visibility / lc_read_back. */
@@ -220,6 +221,32 @@ lc_status lc_set_pose(lc_ctx *ctx, const float *pose);
  * geometry of the non-rigid stage.  `stats` may be null (else synchronises;
  * e_gn / step_norm hold the pose stage's history). */
 lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
+
+/* ---- profiling ------------------------------------------------------------ */
+
+/* Phases of the non-rigid solve, for lc_read_profile. */
+#define LC_PH_WARP 0      /* warp + projection */
+#define LC_PH_VIS 1       /* z-buffer, visibility, contour set, b_i */
+#define LC_PH_LIN 2       /* residuals and per-vertex normal blocks */
+#define LC_PH_RHS 3       /* -J^T F, Jacobi diagonal, ARAP energy */
+#define LC_PH_PCG_INIT 4  /* PCG start vectors */
+#define LC_PH_JTJ 5       /* matrix-free J^T J p */
+#define LC_PH_PCG_VEC 6   /* PCG vector updates and FP64 dots */
+#define LC_PH_UPDATE 7    /* rotation / translation update */
+#define LC_PH_POSE 8      /* pose stage (whole) */
+#define LC_N_PHASES 9
+
+/* Profiling on (1) or off (0).  When on, the captured solves record a chain
+ * of CUDA events on the context stream between consecutive phases, so each
+ * phase's device time of the last solve can be read with lc_read_profile.
+ * The event nodes add a little launch overhead; keep it off for throughput
+ * runs.  Changing it re-captures the solve. */
+lc_status lc_set_profiling(lc_ctx *ctx, int on);
+/* Device time in milliseconds (ms[LC_N_PHASES]) and number of timed
+ * segments (count[LC_N_PHASES], nullable) per phase of the last solves since
+ * profiling was switched on or last read; reading resets the sums.
+ * Synchronises. */
+lc_status lc_read_profile(lc_ctx *ctx, double *ms, int *count);
 
 #ifdef __cplusplus
 }

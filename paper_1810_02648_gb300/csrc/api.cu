@@ -161,6 +161,8 @@ extern "C" lc_status lc_destroy(lc_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     ctx->drop_graph();
     ctx->pose_release();
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
     for (void* p : ctx->owned) cudaFree(p);
     ctx->owned.clear();
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -546,24 +548,96 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
 // ---------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------
+void lc_ctx::mark(int phase) {
+    if (!profiling) return;
+    if (prof_used == (int)prof_ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        prof_ev.push_back(e);
+        prof_phase.push_back(-1);
+    }
+    prof_phase[prof_used] = phase;
+    // external: a real event-record node in the captured graph (a plain record
+    // during capture only expresses a dependency)
+    cudaEventRecordWithFlags(prof_ev[prof_used], stream, cudaEventRecordExternal);
+    ++prof_used;
+}
+
+void lc_ctx::mark_end() { mark(-1); }
+
+lc_status lc_ctx::accumulate_profile() {
+    if (!profiling || prof_used < 2) return LC_OK;
+    lc_status s = cuda(cudaStreamSynchronize(stream), "synchronize");
+    if (s) return s;
+    for (int j = 0; j + 1 < prof_used; ++j) {
+        if (prof_phase[j] < 0) continue;
+        float ms = 0.f;
+        if ((s = cuda(cudaEventElapsedTime(&ms, prof_ev[j], prof_ev[j + 1]), "event time"))) return s;
+        prof_ms[prof_phase[j]] += ms;
+        prof_cnt[prof_phase[j]] += 1;
+    }
+    return LC_OK;
+}
+
 void lc_ctx::enqueue_nonrigid() {
     const CapDesc& C = hC;
     cudaStream_t st = stream;
+    prof_used = 0;
     cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
+    mark(LC_PH_WARP);
     launch_warp(dC, C, st);
+    mark(LC_PH_VIS);
     launch_visibility(dC, C, st);
     for (int gn = 0; gn < params.n_gn; ++gn) {
-        if (gn > 0) launch_warp(dC, C, st);
+        if (gn > 0) {
+            mark(LC_PH_WARP);
+            launch_warp(dC, C, st);
+        }
+        mark(LC_PH_LIN);
         launch_linearize(dC, C, gn, st);
+        mark(LC_PH_RHS);
         launch_rhs(dC, C, gn, false, st);
+        mark(LC_PH_PCG_INIT);
         launch_pcg_init(dC, C, st);
-        for (int it = 0; it < params.n_pcg; ++it) launch_pcg_iteration(dC, C, st);
+        for (int it = 0; it < params.n_pcg; ++it) {
+            mark(LC_PH_JTJ);
+            launch_jtj(dC, C, C.p, C.Ap, true, st);
+            mark(LC_PH_PCG_VEC);
+            launch_pcg_vectors(dC, C, st);
+        }
+        mark(LC_PH_UPDATE);
         launch_update(dC, C, gn, st);
     }
+    mark(LC_PH_WARP);
     launch_warp(dC, C, st);
+    mark(LC_PH_LIN);
     launch_linearize(dC, C, params.n_gn, st);
+    mark(LC_PH_RHS);
     launch_rhs(dC, C, params.n_gn, true, st);
+    mark_end();
+}
+
+lc_status lc_ctx::capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)()) {
+    cudaGraph_t g = nullptr;
+    lc_status s;
+    if ((s = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
+    (this->*enqueue)();
+    cudaError_t e = cudaStreamEndCapture(stream, &g);
+    if ((s = cuda(e, "end capture"))) return s;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    *n_kernels = k;
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return cuda(e, "graph instantiate");
 }
 
 lc_status lc_ctx::check_solve_state(const char* who) {
@@ -603,20 +677,43 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     lc_status s;
     if ((s = ctx->check_solve_state("lc_solve_nonrigid"))) return s;
     cudaSetDevice(ctx->device);
-    if (!ctx->gexec) {
-        cudaGraph_t g = nullptr;
-        if ((s = ctx->cuda(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
-        ctx->enqueue_nonrigid();
-        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-        if ((s = ctx->cuda(e, "end capture"))) return s;
-        e = cudaGraphInstantiate(&ctx->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if ((s = ctx->cuda(e, "graph instantiate"))) return s;
-    }
+    if (!ctx->gexec && (s = ctx->capture(&ctx->gexec, &ctx->graph_kernels, &lc_ctx::enqueue_nonrigid))) return s;
     if ((s = ctx->cuda(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch"))) return s;
+    if ((s = ctx->accumulate_profile())) return s;
     ctx->has_vis = true;
     ctx->has_lin = true;
-    if (stats) return ctx->read_stats(stats, ctx->params.n_gn);
+    if (stats) {
+        if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
+        stats->n_kernels = ctx->graph_kernels;
+    }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_set_profiling(lc_ctx* ctx, int on) {
+    if (!ctx) return LC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if ((on != 0) != ctx->profiling) {
+        ctx->profiling = on != 0;
+        ctx->drop_graph();
+        ctx->pose_drop_graph();
+    }
+    for (int j = 0; j < LC_N_PHASES; ++j) {
+        ctx->prof_ms[j] = 0.0;
+        ctx->prof_cnt[j] = 0;
+    }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_read_profile(lc_ctx* ctx, double* ms, int* count) {
+    if (!ctx || !ms) return LC_ERR_ARG;
+    lc_status s = ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+    if (s) return s;
+    for (int j = 0; j < LC_N_PHASES; ++j) {
+        ms[j] = ctx->prof_ms[j];
+        if (count) count[j] = ctx->prof_cnt[j];
+        ctx->prof_ms[j] = 0.0;
+        ctx->prof_cnt[j] = 0;
+    }
     return LC_OK;
 }
 
@@ -816,7 +913,10 @@ extern "C" lc_status lc_solve_linear(lc_ctx* ctx, float* delta, int* iters) {
     if (!ctx->has_lin) return ctx->fail(LC_ERR_STATE, "lc_solve_linear: no linearisation (call lc_eval_linearization)");
     cudaSetDevice(ctx->device);
     launch_pcg_init(ctx->dC, ctx->hC, ctx->stream);
-    for (int it = 0; it < ctx->params.n_pcg; ++it) launch_pcg_iteration(ctx->dC, ctx->hC, ctx->stream);
+    for (int it = 0; it < ctx->params.n_pcg; ++it) {
+        launch_jtj(ctx->dC, ctx->hC, ctx->hC.p, ctx->hC.Ap, true, ctx->stream);
+        launch_pcg_vectors(ctx->dC, ctx->hC, ctx->stream);
+    }
     lc_status s;
     if ((s = ctx->cuda(cudaGetLastError(), "pcg"))) return s;
     if ((s = ctx->vec_out(delta, ctx->hC.x))) return s;

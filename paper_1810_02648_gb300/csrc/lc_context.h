@@ -19,6 +19,7 @@ struct lc_ctx {
     lc::CapDesc* dC = nullptr;    // device copy
     std::vector<void*> owned;     // every device allocation of this context
     cudaGraphExec_t gexec = nullptr;
+    int graph_kernels = 0;        // kernel nodes in the captured non-rigid solve
     bool has_camera = false, has_template = false, has_graph = false, has_frame = false;
     bool has_vis = false, has_lin = false;
     // template
@@ -36,6 +37,16 @@ struct lc_ctx {
     int tmp6_cap = 0;
     int part_cap = 0;
     PoseState* pose = nullptr;
+    // profiling: an event chain recorded between phases of the captured solve
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_phase;   // phase of the segment starting at event j
+    int prof_used = 0;
+    double prof_ms[LC_N_PHASES] = {0};
+    int prof_cnt[LC_N_PHASES] = {0};
+    void mark(int phase);          // record the next event of the chain (capture time)
+    void mark_end();
+    lc_status accumulate_profile();
 
     lc_status fail(lc_status st, const char* fmt, ...);
     lc_status cuda(cudaError_t e, const char* what);
@@ -54,11 +65,13 @@ struct lc_ctx {
     void enqueue_nonrigid();
     lc_status check_solve_state(const char* who);
     lc_status read_stats(lc_solve_stats* stats, int n_gn);
+    lc_status capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)());
     lc_status linearize_now(bool with_rhs);
     lc_status vec_out(float* dst, const float4* src);
     float* tmp_out();
     // pose stage (pose_api.cu)
     void pose_release();
+    void pose_drop_graph();
     lc_status pose_frame(const float* joints2d, const float* joints3d);
     lc_status pose_read(float* pose_out);
 };

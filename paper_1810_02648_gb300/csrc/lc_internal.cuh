@@ -214,7 +214,7 @@ void launch_linearize(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStr
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
-void launch_pcg_iteration(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
 void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
 void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);

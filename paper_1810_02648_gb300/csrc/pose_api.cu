@@ -8,6 +8,8 @@ void lc_ctx::pose_release() {
     pose = nullptr;
 }
 
+void lc_ctx::pose_drop_graph() {}
+
 lc_status lc_ctx::pose_frame(const float* joints2d, const float* joints3d) {
     (void)joints2d;
     (void)joints3d;

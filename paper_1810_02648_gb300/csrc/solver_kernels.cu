@@ -441,9 +441,8 @@ void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     pcg_init_kernel<<<(hC.n + kVecThreads - 1) / kVecThreads, kVecThreads, 0, st>>>(dC, nullptr);
 }
 
-void launch_pcg_iteration(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     const int vb = (hC.n + kVecThreads - 1) / kVecThreads;
-    launch_jtj(dC, hC, hC.p, hC.Ap, true, st);
     pcg_step_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
     pcg_dir_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
 }

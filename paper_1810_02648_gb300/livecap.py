@@ -32,7 +32,8 @@ class lc_solve_stats(ctypes.Structure):
                 ("e_total", ctypes.c_double), ("e_gn", ctypes.c_double * LC_MAX_GN),
                 ("step_norm", ctypes.c_double * LC_MAX_GN), ("pcg_iters", ctypes.c_int * LC_MAX_GN),
                 ("n_gn_done", ctypes.c_int), ("n_visible", ctypes.c_int), ("n_boundary", ctypes.c_int),
-                ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int)]
+                ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int),
+                ("n_kernels", ctypes.c_int)]
 
     def to_dict(self) -> dict:
         g = self.n_gn_done
@@ -40,7 +41,7 @@ class lc_solve_stats(ctypes.Structure):
                     e_gn=list(self.e_gn[:g]), step_norm=list(self.step_norm[:g]),
                     pcg_iters=list(self.pcg_iters[:g]), n_visible=self.n_visible,
                     n_boundary=self.n_boundary, n_boundary_neg=self.n_boundary_neg,
-                    pcg_breakdowns=self.pcg_breakdowns)
+                    pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels)
 
 
 _P = ctypes.c_void_p
@@ -67,7 +68,10 @@ _SIGS = {
     "lc_upload_skeleton": [_P, ctypes.c_int, _P, _P, _P, _P, _P],
     "lc_set_pose": [_P, _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
+    "lc_set_profiling": [_P, ctypes.c_int],
+    "lc_read_profile": [_P, _P, _P],
 }
+PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose"]
 
 _lib = None
 
@@ -280,6 +284,16 @@ class Context:
         it = ctypes.c_int(0)
         self._check(self._lib.lc_solve_linear(self.h, _ptr(d), ctypes.byref(it)))
         return d, it.value
+
+    # ---- profiling
+    def set_profiling(self, on: bool):
+        self._check(self._lib.lc_set_profiling(self.h, 1 if on else 0))
+
+    def read_profile(self) -> dict:
+        ms = np.zeros(len(PHASES), np.float64)
+        cnt = np.zeros(len(PHASES), np.int32)
+        self._check(self._lib.lc_read_profile(self.h, _ptr(ms), _ptr(cnt)))
+        return {name: (float(ms[j]), int(cnt[j])) for j, name in enumerate(PHASES)}
 
     # ---- pose stage
     def upload_skeleton(self, parents, joints_rest, dof, skin_idx, skin_w):
