@@ -248,6 +248,36 @@ lc_status lc_set_profiling(lc_ctx *ctx, int on);
  * Synchronises. */
 lc_status lc_read_profile(lc_ctx *ctx, double *ms, int *count);
 
+/* ---- visibility without device allocation --------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need visibility: code running
+ * inside another framework's memory pool that forbids outside allocations,
+ * a real-time process whose device memory is reserved up front, or a plugin
+ * that may not grow its host application's footprint.
+ *
+ * Per-vertex visibility of warped vertices V_warp (N x 3, metres) of the
+ * mesh tris (F x 3) under the pinhole camera (f, cx, cy, W x H), with depth
+ * tolerance eps_vis: visible[i] = 1 or 0, bit-identical to the
+ * LC_FLAG_VISIBLE bit of lc_compute_visibility for the same positions.
+ * V_warp, tris and visible must be device memory of the current device;
+ * work is enqueued on cuda_stream (a cudaStream_t, 0 = legacy default) and
+ * the call returns without waiting.  Triangles naming a vertex outside
+ * [0, N) are skipped.
+ *
+ * No device memory is allocated, on any path: the z-buffer scratch is a
+ * static device array of LC_NOALLOC_MAX_PIXELS 64-bit entries (8 MiB) that
+ * every GPU which loads this library holds until the process exits.  W * H
+ * above LC_NOALLOC_MAX_PIXELS returns LC_ERR_ARG; host (non-device)
+ * pointers return LC_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, which may load the module):
+ * make that first call outside any stream capture.  All calls share the
+ * scratch, each clearing what it uses first; calls that overlap on the GPU
+ * race on it, so serialise them (one stream, or explicit ordering). */
+#define LC_NOALLOC_MAX_PIXELS (1024 * 1024)
+lc_status lc_visibility_noalloc(const float *V_warp, int N, const int32_t *tris, int F, float f, float cx,
+                                float cy, int W, int H, float eps_vis, uint8_t *visible, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ _SIGS = {
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_set_profiling": [_P, ctypes.c_int],
     "lc_read_profile": [_P, _P, _P],
+    "lc_visibility_noalloc": [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_float, _P, _P],
 }
 PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose"]
 
