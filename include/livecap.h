@@ -65,6 +65,10 @@ typedef struct {
     float lambda_3d;
     float lambda_sil;
     int n_gn_pose;      /* Gauss-Newton steps of the pose stage, default 5 */
+    int pcg_kernel;     /* 0 (default): one cluster-persistent kernel runs all PCG
+                           iterations of a Gauss-Newton step when the capture's
+                           per-CTA data fits in shared memory; 1: one launch per
+                           PCG phase (J^T J p, vector updates) */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -81,6 +85,7 @@ typedef struct {
     int n_boundary_neg;                      /* contour vertices with b_i = -1 */
     int pcg_breakdowns;                      /* steps whose PCG stopped on p^T A p <= 0 */
     int n_kernels;                           /* kernel launches in one solve (captured graph) */
+    int pcg_cluster_size;                    /* CTAs per cluster of the persistent PCG, 0 = per-phase kernels */
 } lc_solve_stats;
 
 /* Vertex flag bits returned by lc_read_visibility / lc_read_back. */
@@ -234,7 +239,8 @@ lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
 #define LC_PH_PCG_VEC 6   /* PCG vector updates and FP64 dots */
 #define LC_PH_UPDATE 7    /* rotation / translation update */
 #define LC_PH_POSE 8      /* pose stage (whole) */
-#define LC_N_PHASES 9
+#define LC_PH_PCG 9       /* cluster-persistent PCG (all iterations of one step) */
+#define LC_N_PHASES 10
 
 /* Profiling on (1) or off (0).  When on, the captured solves record a chain
  * of CUDA events on the context stream between consecutive phases, so each

@@ -109,6 +109,7 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->lambda_3d = 28.0f;
     p->lambda_sil = 200.0f;
     p->n_gn_pose = 5;
+    p->pcg_kernel = 0;
     return LC_OK;
 }
 
@@ -185,7 +186,9 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
-    if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg) ctx->drop_graph();
+    if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
+    if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel)
+        ctx->drop_graph();
     ctx->params = *p;
     ctx->apply_params();
     return ctx->sync_desc();
@@ -349,6 +352,7 @@ void lc_ctx::free_graph() {
     hC.node_R = nullptr; hC.node_t = nullptr;
     hC.b = hC.minv = hC.diag = hC.x = hC.r = hC.z = hC.p = hC.Ap = nullptr;
     tmp_vec = tmp_vec2 = nullptr;
+    pcg_plan_ok = false;
     hC.n = 0;
     hC.K = 0;
     hC.E = 0;
@@ -452,6 +456,14 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     s = ctx->cuda(cudaStreamSynchronize(st), "graph build");
     cleanup();
     if (s != LC_OK) return s;
+    {
+        std::vector<int> eo(n + 1), go(n + 1);
+        if ((s = ctx->copy_to_host(eo.data(), C.ent_off, sizeof(int) * (n + 1))) ||
+            (s = ctx->copy_to_host(go.data(), C.edge_off, sizeof(int) * (n + 1))))
+            return s;
+        ctx->pcg_plan_ok = plan_pcg_cluster(n, K, eo.data(), go.data(), &ctx->pcg_plan);
+        cudaGetLastError();
+    }
     ctx->ensure_partials();
     ctx->has_graph = true;
     ctx->drop_graph();
@@ -579,6 +591,22 @@ lc_status lc_ctx::accumulate_profile() {
     return LC_OK;
 }
 
+void lc_ctx::enqueue_pcg() {
+    if (use_cluster_pcg()) {
+        mark(LC_PH_PCG);
+        launch_pcg_cluster(dC, pcg_plan, hC.K, params.n_pcg, stream);
+        return;
+    }
+    mark(LC_PH_PCG_INIT);
+    launch_pcg_init(dC, hC, stream);
+    for (int it = 0; it < params.n_pcg; ++it) {
+        mark(LC_PH_JTJ);
+        launch_jtj(dC, hC, hC.p, hC.Ap, true, stream);
+        mark(LC_PH_PCG_VEC);
+        launch_pcg_vectors(dC, hC, stream);
+    }
+}
+
 void lc_ctx::enqueue_nonrigid() {
     const CapDesc& C = hC;
     cudaStream_t st = stream;
@@ -598,14 +626,7 @@ void lc_ctx::enqueue_nonrigid() {
         launch_linearize(dC, C, gn, st);
         mark(LC_PH_RHS);
         launch_rhs(dC, C, gn, false, st);
-        mark(LC_PH_PCG_INIT);
-        launch_pcg_init(dC, C, st);
-        for (int it = 0; it < params.n_pcg; ++it) {
-            mark(LC_PH_JTJ);
-            launch_jtj(dC, C, C.p, C.Ap, true, st);
-            mark(LC_PH_PCG_VEC);
-            launch_pcg_vectors(dC, C, st);
-        }
+        enqueue_pcg();
         mark(LC_PH_UPDATE);
         launch_update(dC, C, gn, st);
     }
@@ -685,6 +706,7 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     if (stats) {
         if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
         stats->n_kernels = ctx->graph_kernels;
+        stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
     }
     return LC_OK;
 }
@@ -912,11 +934,10 @@ extern "C" lc_status lc_solve_linear(lc_ctx* ctx, float* delta, int* iters) {
     if (!ctx || !delta) return LC_ERR_ARG;
     if (!ctx->has_lin) return ctx->fail(LC_ERR_STATE, "lc_solve_linear: no linearisation (call lc_eval_linearization)");
     cudaSetDevice(ctx->device);
-    launch_pcg_init(ctx->dC, ctx->hC, ctx->stream);
-    for (int it = 0; it < ctx->params.n_pcg; ++it) {
-        launch_jtj(ctx->dC, ctx->hC, ctx->hC.p, ctx->hC.Ap, true, ctx->stream);
-        launch_pcg_vectors(ctx->dC, ctx->hC, ctx->stream);
-    }
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    ctx->enqueue_pcg();
+    ctx->profiling = prof;
     lc_status s;
     if ((s = ctx->cuda(cudaGetLastError(), "pcg"))) return s;
     if ((s = ctx->vec_out(delta, ctx->hC.x))) return s;

@@ -36,6 +36,10 @@ struct lc_ctx {
     float* tmp6 = nullptr;
     int tmp6_cap = 0;
     int part_cap = 0;
+    lc::PcgPlan pcg_plan{};
+    bool pcg_plan_ok = false;     // the cluster-persistent PCG fits this capture
+    bool use_cluster_pcg() const { return pcg_plan_ok && params.pcg_kernel == 0; }
+    void enqueue_pcg();
     PoseState* pose = nullptr;
     // profiling: an event chain recorded between phases of the captured solve
     bool profiling = false;

@@ -10,7 +10,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/livecap.h"
+#include "livecap.h"
 
 namespace lc {
 
@@ -218,6 +218,17 @@ void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
 void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
 void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);
+
+// cluster-persistent PCG (pcg_cluster.cu)
+struct PcgPlan {
+    int cl;          // CTAs per cluster
+    int cap_e;       // CSR-entry capacity per CTA
+    int cap_d;       // node-edge capacity per CTA
+    int cap_n;       // owned-node capacity per CTA
+    size_t smem;     // dynamic shared memory bytes
+};
+bool plan_pcg_cluster(int n, int K, const int* ent_off_host, const int* edge_off_host, PcgPlan* out);
+cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st);
 
 // graph construction
 struct GraphScratch {

@@ -191,7 +191,11 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
             const float c = C.w_arap * C.edge_s[j];
             const float3 gl = f3(C.node_g[l]), tl = f3(C.node_t[l]);
             const float3 b = mul(R, gl - g);
-            const float3 d = b + g + t - gl - tl;
+            // R_k (g_l - g_k) + g_k + t_k - g_l - t_l, evaluated as
+            // (R_k - I)(g_l - g_k) + t_k - t_l: the same value, exactly zero
+            // for the identity parameters
+            const float3 dg = gl - g;
+            const float3 d = (b - dg) + t - tl;
             arap += (double)c * (double)dot3(d, d);
             if (energy_only) continue;
             const float3 bd = cross3(b, d);
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
             acc[6] += c * (bb - b.x * b.x); acc[7] += c * (bb - b.y * b.y); acc[8] += c * (bb - b.z * b.z);
             // in-edge (l, k): residual R_l (g_k - g_l) + g_l + t_l - g_k - t_k, d/d t_k = -I
             const Rot Rl = load_R(C.node_R, l);
-            const float3 dl = mul(Rl, g - gl) + gl + tl - g - t;
+            const float3 dl = (mul(Rl, g - gl) - (g - gl)) + tl - t;
             acc[3] -= c * dl.x; acc[4] -= c * dl.y; acc[5] -= c * dl.z;
             acc[9] += 2.f * c; acc[10] += 2.f * c; acc[11] += 2.f * c;
         }

@@ -24,7 +24,7 @@ class lc_params(ctypes.Structure):
     _fields_ = [("w_photo", ctypes.c_float), ("w_sil", ctypes.c_float), ("w_arap", ctypes.c_float),
                 ("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("eps_vis", ctypes.c_float),
                 ("lambda_2d", ctypes.c_float), ("lambda_3d", ctypes.c_float), ("lambda_sil", ctypes.c_float),
-                ("n_gn_pose", ctypes.c_int)]
+                ("n_gn_pose", ctypes.c_int), ("pcg_kernel", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -33,7 +33,7 @@ class lc_solve_stats(ctypes.Structure):
                 ("step_norm", ctypes.c_double * LC_MAX_GN), ("pcg_iters", ctypes.c_int * LC_MAX_GN),
                 ("n_gn_done", ctypes.c_int), ("n_visible", ctypes.c_int), ("n_boundary", ctypes.c_int),
                 ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int),
-                ("n_kernels", ctypes.c_int)]
+                ("n_kernels", ctypes.c_int), ("pcg_cluster_size", ctypes.c_int)]
 
     def to_dict(self) -> dict:
         g = self.n_gn_done
@@ -41,7 +41,8 @@ class lc_solve_stats(ctypes.Structure):
                     e_gn=list(self.e_gn[:g]), step_norm=list(self.step_norm[:g]),
                     pcg_iters=list(self.pcg_iters[:g]), n_visible=self.n_visible,
                     n_boundary=self.n_boundary, n_boundary_neg=self.n_boundary_neg,
-                    pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels)
+                    pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels,
+                    pcg_cluster_size=self.pcg_cluster_size)
 
 
 _P = ctypes.c_void_p
@@ -73,7 +74,7 @@ _SIGS = {
     "lc_visibility_noalloc": [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_int, ctypes.c_int, ctypes.c_float, _P, _P],
 }
-PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose"]
+PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose", "pcg"]
 
 _lib = None
 

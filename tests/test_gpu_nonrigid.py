@@ -143,8 +143,8 @@ def test_visibility_partially_outside():
 # ---------------------------------------------------------------------------
 # per-kernel floating-point parity at identical inputs
 # ---------------------------------------------------------------------------
-def _lin_case(scene, seed, tag):
-    ctx = _ctx(scene)
+def _lin_case(scene, seed, tag, pcg_kernel=0):
+    ctx = _ctx(scene, pcg_kernel=pcg_kernel)
     n = scene.n_nodes
     R, t = random_params(n, seed)
     ctx.set_node_params(R.reshape(n, 9), t)
@@ -211,12 +211,14 @@ def _lin_case(scene, seed, tag):
     ctx.close()
 
 
-def test_linearization_tiny(tiny):
-    _lin_case(tiny, 11, "tiny")
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
+def test_linearization_tiny(tiny, pcg_kernel):
+    _lin_case(tiny, 11, f"tiny_k{pcg_kernel}", pcg_kernel)
 
 
-def test_linearization_body(body):
-    _lin_case(body, 12, "body")
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
+def test_linearization_body(body, pcg_kernel):
+    _lin_case(body, 12, f"body_k{pcg_kernel}", pcg_kernel)
 
 
 def test_linearization_ragged():
@@ -226,7 +228,7 @@ def test_linearization_ragged():
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------
-def _e2e(scene, tag, base32=None, n_pcg=None, strict=True):
+def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
     """Full solve on the GPU vs the oracle from the same graph.
 
     strict: final energy within 1e-4 (relative) and vertices within 1e-4 of
@@ -235,7 +237,7 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True):
     result under FP32 rounding of its CG (``fp32_rounding_band``), or the
     strict bound if larger."""
     from gpu_helpers import fp32_rounding_band
-    ctx = _ctx(scene)
+    ctx = _ctx(scene, pcg_kernel=pcg_kernel)
     if n_pcg is not None:
         ctx.set_params(n_pcg=n_pcg)
     stats = ctx.solve_nonrigid()
@@ -251,7 +253,13 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True):
     f_ref = (P.vis.astype(np.uint8) * 1) | (P.inB.astype(np.uint8) * 4) | ((P.bsign < 0).astype(np.uint8) * 8)
     e_hist = np.array(stats["e_gn"])
     e_hist_ref = np.array([h["energy"] for h in ref["hist"]])
+    if pcg_kernel == 0:
+        assert stats["pcg_cluster_size"] in (8, 16)
+    else:
+        assert stats["pcg_cluster_size"] == 0
+    assert stats["pcg_iters"] == [h["pcg_iters"] for h in ref["hist"]]
     report(f"e2e_{tag}", e_gpu=e_gpu, e_ref=e_ref, rel=rel, dv=dv, dv_over_diag=dv / diag,
+           cluster=stats["pcg_cluster_size"],
            band_E_rel=band_E / abs(e_ref), band_V=band_V,
            hist_rel=np.abs(e_hist - e_hist_ref).max() / e_hist_ref.max(),
            n_vis=stats["n_visible"], n_B=stats["n_boundary"])
@@ -272,12 +280,14 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True):
     return stats
 
 
-def test_end_to_end_tiny_strict(tiny):
-    _e2e(tiny, "tiny_pcg3", n_pcg=3)
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
+def test_end_to_end_tiny_strict(tiny, pcg_kernel):
+    _e2e(tiny, f"tiny_pcg3_k{pcg_kernel}", n_pcg=3, pcg_kernel=pcg_kernel)
 
 
-def test_end_to_end_tiny(tiny):
-    _e2e(tiny, "tiny", strict=False)
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
+def test_end_to_end_tiny(tiny, pcg_kernel):
+    _e2e(tiny, f"tiny_k{pcg_kernel}", strict=False, pcg_kernel=pcg_kernel)
 
 
 def test_end_to_end_ragged_strict():
