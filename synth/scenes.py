@@ -344,6 +344,18 @@ def _rodrigues(aa: np.ndarray) -> np.ndarray:
     return out
 
 
+def _euler_xyz(a: np.ndarray) -> np.ndarray:
+    """Rx(a0) Ry(a1) Rz(a2) per row (the pose convention of the skeleton)."""
+    out = np.empty((len(a), 3, 3))
+    for i, (x, y, z) in enumerate(a):
+        cx, sx, cy, sy, cz, sz = math.cos(x), math.sin(x), math.cos(y), math.sin(y), math.cos(z), math.sin(z)
+        Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+        Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+        Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+        out[i] = Rx @ Ry @ Rz
+    return out
+
+
 def smooth_deformation(V: np.ndarray, n_ctrl: int, sigma_rot: float,
                        sigma_t: float, seed: int) -> Dict[str, np.ndarray]:
     """Ground-truth non-rigid deformation on random control points.
@@ -585,12 +597,16 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
         albedo = value_noise_albedo(V32.astype(np.float64), seed)
         material = np.where(tpl["skin"] > 0, 1.0, 0.2)
         n_nodes = over.get("n_nodes", 500 if not stress else 4000)
-        # ground-truth pose: small global rotation, joint rotations ~N(0, 0.2)
+        # ground-truth pose: small global rotation, Euler XYZ joint angles
+        # ~N(0, 0.2); the frame starts from the ground truth perturbed by
+        # N(0, 0.05) rad per angle and N(0, 2 cm) at the root, like a pose
+        # extrapolated from the previous two frames
         root_aa = rng.normal(0.0, 0.05, size=3)
         root_t = tpl["joints_rest"][0] + rng.normal(0.0, 0.03, size=3)
-        local = _rodrigues(rng.normal(0.0, over.get("sigma_pose", 0.2), size=(23, 3)))
-        local[SKELETON_SITES] = np.eye(3)
-        local[0] = np.eye(3)
+        angles = rng.normal(0.0, over.get("sigma_pose", 0.2), size=(23, 3))
+        angles[SKELETON_SITES] = 0.0
+        angles[0] = 0.0
+        local = _euler_xyz(angles)
         Vp, joints_gt = pose_body(dict(tpl, V=V32.astype(np.float64)),
                                   _rodrigues(root_aa)[0], root_t, local)
         gt = smooth_deformation(Vp, n_nodes, over.get("sigma_nonrigid", 0.1), 0.01, seed)
@@ -599,8 +615,12 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
         u = cam.f * joints_gt[:, 0] / joints_gt[:, 2] + cam.cx
         v = cam.f * joints_gt[:, 1] / joints_gt[:, 2] + cam.cy
         j2 = np.stack([u, v], 1) + rng.normal(0.0, 2.0, size=(23, 2))
-        pose0 = np.zeros(N_POSE_DOF)
-        pose0[3:6] = root_t + rng.normal(0.0, 0.02, size=3)
+        dof_joints = [j for j in range(1, 23) if j not in set(SKELETON_SITES.tolist())]
+        pose_gt = np.concatenate([root_aa, root_t] + [angles[j] for j in dof_joints])
+        pose0 = pose_gt.copy()
+        pose0[:3] += rng.normal(0.0, 0.02, size=3)
+        pose0[3:6] += rng.normal(0.0, 0.02, size=3)
+        pose0[6:] += rng.normal(0.0, over.get("sigma_init", 0.05), size=len(pose0) - 6)
         skel = dict(parents=tpl["parents"], joints_rest=tpl["joints_rest"].astype(np.float32),
                     skin_idx=tpl["skin_idx"].astype(np.int32),
                     skin_w=tpl["skin_w"].astype(np.float32),
@@ -611,7 +631,7 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
                      over.get("n_gn", 10), over.get("n_pcg", 40), (1.0, 0.1, 10.0),
                      gt["V"], skeleton=skel, joints2d=j2.astype(np.float32),
                      joints3d=j3.astype(np.float32), pose_init=pose0.astype(np.float32),
-                     meta=dict(seed=seed, root_aa=root_aa, root_t=root_t,
+                     meta=dict(seed=seed, root_aa=root_aa, root_t=root_t, pose_gt=pose_gt,
                                joints_gt=joints_gt, V_posed=Vp))
     raise ValueError(f"unknown scene {name!r}")
 

@@ -1,0 +1,135 @@
+"""Pins for the pose-stage oracle (CPU).
+
+* Euler convention vs SciPy's intrinsic XYZ rotations.
+* Rest pose skins to the template; a global root motion moves every joint
+  and vertex rigidly (closed form).
+* Finite-difference Jacobian with an affine distance-transform stand-in
+  (bilinear sampling and central differences exact), b_i signs folded in.
+* Cholesky solve vs numpy.linalg.solve; a non-positive pivot raises.
+* Noise-free detections generated at a known pose are recovered.
+"""
+import copy
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import synth
+from oracle import nonrigid as nr
+from oracle import pose as op
+
+
+@pytest.fixture(scope="module")
+def body():
+    return synth.make_scene("body")
+
+
+def test_euler_matches_scipy():
+    a = np.random.default_rng(0).normal(scale=0.7, size=(20, 3))
+    ref = Rotation.from_euler("XYZ", a).as_matrix()
+    assert np.abs(op.euler_xyz(a) - ref).max() < 1e-14
+
+
+def test_rest_pose_and_rigid_root(body):
+    pb = op.problem_from_scene(body)
+    sk = pb.sk
+    rest = np.zeros(sk.n_dof)
+    rest[3:6] = sk.joints_rest[0]
+    R, t, ang = op.split_pose(sk, rest)
+    G, o = op.forward_kinematics(sk, R, t, ang)
+    _, VS = op.skin(sk, pb.V, G, o)
+    # the skinning weights are FP32: sum_s w_is = 1 only to within rounding
+    wtol = 2.0 * np.abs(sk.skin_w.sum(1) - 1.0).max() * np.abs(pb.V).max() + 1e-13
+    assert np.abs(o - sk.joints_rest).max() < 1e-15
+    assert np.abs(VS - pb.V).max() <= wtol
+    Rg = nr.so3_exp(np.array([0.2, -0.3, 0.1]))[0]
+    tg = np.array([0.05, -0.02, 0.1])
+    moved = rest.copy()
+    moved[:3] = nr.so3_log(Rg)[0]
+    moved[3:6] = Rg @ sk.joints_rest[0] + tg
+    R, t, ang = op.split_pose(sk, moved)
+    G, o = op.forward_kinematics(sk, R, t, ang)
+    _, VS2 = op.skin(sk, pb.V, G, o)
+    assert np.abs(o - (sk.joints_rest @ Rg.T + tg)).max() < 1e-12
+    assert np.abs(VS2 - (pb.V @ Rg.T + tg)).max() <= wtol + 1e-12
+
+
+def _affine_dt(pb):
+    Q = copy.copy(pb)
+    yy, xx = np.mgrid[:pb.H, :pb.W].astype(np.float64)
+    Q.dt = 3.0 + 0.02 * xx - 0.015 * yy
+    Q._gdt = None
+    return Q
+
+
+def test_jacobian_fd(body):
+    pb = _affine_dt(op.problem_from_scene(body))
+    pose0 = np.asarray(body.pose_init, dtype=np.float64)
+    op.frame_decisions(op.problem_from_scene(body), pose0)
+    dec = op.problem_from_scene(body)
+    op.frame_decisions(dec, pose0)
+    pb.inB, pb.bsign = dec.inB, dec.bsign
+    rng = np.random.default_rng(3)
+    pose = pose0.copy()
+    pose[6:] += rng.normal(scale=0.05, size=len(pose) - 6)
+    F, J = op.residuals_and_jacobian(pb, pose)
+    h = 1e-6
+    Jfd = np.zeros_like(J)
+    for d in range(J.shape[1]):
+        e = np.zeros(J.shape[1])
+        e[d] = h
+        Fp, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, e))
+        Fm, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, -e))
+        assert len(Fp) == len(F) == len(Fm)
+        Jfd[:, d] = (Fp - Fm) / (2 * h)
+    # silhouette rows carry b_i
+    R, t, ang = op.split_pose(pb.sk, pose)
+    G, o = op.forward_kinematics(pb.sk, R, t, ang)
+    _, VS = op.skin(pb.sk, pb.V, G, o)
+    _, _, _, okj, _ = op._proj(pb, o)
+    _, _, _, _, inimg = op._proj(pb, VS)
+    sel = np.nonzero(pb.inB & inimg)[0]
+    r0 = 2 * int(okj.sum()) + 3 * len(o)
+    Jfd[r0:r0 + len(sel)] *= pb.bsign[sel][:, None]
+    assert len(sel) > 50
+    err = np.abs(J - Jfd).max() / np.abs(Jfd).max()
+    assert err < 1e-6, err
+
+
+def test_cholesky():
+    rng = np.random.default_rng(1)
+    M = rng.normal(size=(57, 57))
+    A = M @ M.T + 57 * np.eye(57)
+    b = rng.normal(size=57)
+    assert np.allclose(op.cholesky_solve(A, b), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    with pytest.raises(np.linalg.LinAlgError):
+        op.cholesky_solve(-np.eye(3), np.ones(3))
+
+
+def test_noise_free_recovery(body):
+    pb = op.problem_from_scene(body, lam_prior=1e-6)
+    pb.lam_sil = 0.0
+    # 3D residuals weighted as if in millimetres: with metres the 3D term is
+    # too weak to rule out depth-flipped limb poses that match the 2D joints
+    pb.lam_3d = 28.0e6
+    gt = body.meta["pose_gt"]
+    R, t, ang = op.split_pose(pb.sk, gt)
+    G, o = op.forward_kinematics(pb.sk, R, t, ang)
+    pb.j3d = o.copy()
+    pb.j2d = np.stack([pb.f * o[:, 0] / o[:, 2] + pb.cx, pb.f * o[:, 1] / o[:, 2] + pb.cy], 1)
+    pose, hist = op.gauss_newton(pb, np.asarray(body.pose_init, dtype=np.float64), 25)
+    R, t, ang = op.split_pose(pb.sk, pose)
+    G2, o2 = op.forward_kinematics(pb.sk, R, t, ang)
+    assert np.abs(o2 - o).max() < 1e-6
+    assert hist[-1]["energy"] < 1e-9 * hist[0]["energy"]
+
+
+def test_pose_stage_improves_joints(body):
+    out = op.solve_scene(body)
+    pb = out["problem"]
+    R, t, ang = op.split_pose(pb.sk, np.asarray(body.pose_init, dtype=np.float64))
+    _, o0 = op.forward_kinematics(pb.sk, R, t, ang)
+    e_init = np.linalg.norm(o0 - body.meta["joints_gt"], axis=1).mean()
+    e_fin = np.linalg.norm(out["joints"] - body.meta["joints_gt"], axis=1).mean()
+    assert out["e1"] < out["e0"]
+    assert e_fin < 1.5 * e_init
