@@ -21,8 +21,12 @@ What it computes (paper references are to sections and equations):
   gradients are central differences (one-sided at the border) sampled
   bilinearly.  Vertices with Z <= 1e-3 or a projection outside
   [0,W-1] x [0,H-1] contribute no residual at that linearisation.
-* Visibility V, contour set B and directions b_i are fixed per frame (Sec. 3.3
-  and 3.4); they come from the exact-arithmetic module ``visibility``.
+* Visibility V and the contour set B are fixed per frame (Sec. 3.3 and 3.4);
+  the direction b_i of each contour vertex is re-evaluated at every
+  linearisation from the current surface (its normal and the DT gradient at
+  its projection), so that a vertex which crossed the medial axis follows the
+  contour it now faces.  Both come from the exact-arithmetic module
+  ``visibility``.
 * The silhouette residual is r_i = sqrt(w_s) I_DT(pi(v'_i)); its Jacobian row
   is multiplied by b_i, so b_i = -1 reverses the row's pull along the DT
   gradient (Sec. 3.3, the two silhouette cases) while J^T J stays PSD.
@@ -104,6 +108,7 @@ class Problem:
     vis: Optional[np.ndarray] = None     # (N,) bool
     inB: Optional[np.ndarray] = None     # (N,) bool
     bsign: Optional[np.ndarray] = None   # (N,) +-1
+    tris: Optional[np.ndarray] = None    # (T,3): when set, b_i follows the current surface
 
     @property
     def n(self) -> int:
@@ -246,6 +251,16 @@ def energy(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     return e
 
 
+def update_directions(P: Problem, R: np.ndarray, t: np.ndarray):
+    """b_i of the frame's contour set at the current FP32 surface."""
+    if P.tris is None or P.inB is None:
+        return
+    from . import visibility as _vis
+    v32 = warp(P, R, t).astype(np.float32)
+    neg = _vis.directions(v32, P.tris, P.f, P.cx, P.cy, P.W, P.H, P.dt.astype(np.float32), P.mask, P.inB)
+    P.bsign = np.where(neg, -1.0, 1.0)
+
+
 def linearise(P: Problem, R: np.ndarray, t: np.ndarray):
     """Stacked residual vector F and its Jacobian J (sparse, FP64).
 
@@ -255,6 +270,7 @@ def linearise(P: Problem, R: np.ndarray, t: np.ndarray):
     """
     n = P.n
     K = P.bind_idx.shape[1]
+    update_directions(P, R, t)
     vr = vertex_residuals(P, R, t)
     v, u, w = vr["v"], vr["u"], vr["w"]
     (gxI, gyI), (gxD, gyD) = P.grads()
@@ -409,7 +425,7 @@ def problem_from_scene(scene, graph: dict, base32: Optional[np.ndarray] = None) 
         edges=graph["edges"], edge_s=np.asarray(graph["edge_s"], dtype=np.float32),
         f=float(np.float32(scene.cam.f)), cx=float(np.float32(scene.cam.cx)),
         cy=float(np.float32(scene.cam.cy)), W=scene.cam.W, H=scene.cam.H,
-        rgb=scene.rgb, dt=scene.dt, mask=scene.mask, w_photo=wp, w_sil=ws, w_arap=wa)
+        rgb=scene.rgb, dt=scene.dt, mask=scene.mask, tris=np.asarray(scene.F, dtype=np.int32), w_photo=wp, w_sil=ws, w_arap=wa)
 
 
 def solve_scene(scene, graph: Optional[dict] = None, base32=None, n_gn=None, n_pcg=None):

@@ -28,8 +28,9 @@ Readings:
   the role of the paper's temporal term in angle space.
 * The silhouette weight is divided by |B| so that the term does not grow
   with the mesh resolution (the paper gives no units for its weights).
-* Contour set B and b_i come from the skinned mesh at the frame's initial
-  pose (once per frame, Sec. 3.3), through the exact visibility module.
+* The contour set B comes from the skinned mesh at the frame's initial pose
+  (once per frame, Sec. 3.3); b_i is re-evaluated on the current skinned
+  surface at every linearisation.  Both through the exact visibility module.
 * The normal equations are solved by a Cholesky factorisation (FP64).
 """
 from __future__ import annotations
@@ -244,6 +245,13 @@ def residuals_and_jacobian(pb: PoseProblem, pose: np.ndarray):
     rows.append(s3 * Jo.reshape(-1, sk.n_dof))
     if pb.inB is not None and pb.inB.any():
         P, VS = skin(sk, pb.V, G, o)
+        # b_i follows the current skinned surface (the contour set B does not);
+        # with no triangles given the caller's b_i stay fixed
+        if pb.tris is not None:
+            from . import visibility as _vis
+            neg = _vis.directions(VS.astype(np.float32), pb.tris, pb.f, pb.cx, pb.cy, pb.W, pb.H,
+                                  pb.dt.astype(np.float32), pb.mask, pb.inB)
+            pb.bsign = np.where(neg, -1.0, 1.0)
         uu, vv, DD, okv, inimg = _proj(pb, VS)
         sel = np.nonzero(pb.inB & inimg)[0]
         if len(sel):

@@ -23,7 +23,11 @@
  *               v in [0,H-1], and (pixel empty or Z <= depth(p) + eps).
  *  contour      mesh edge is a silhouette edge iff its two triangles differ in
  *               (snapped int64 area > 0); an edge with one triangle always is.
- *               B = visible vertices on a silhouette edge.
+ *               B = visible vertices on a silhouette edge whose pixel p lies
+ *               on the model's projected outline: some pixel of the 3x3
+ *               block around p is outside the image or not covered by any
+ *               triangle (internal occluding contours are not part of the
+ *               model silhouette).
  *  direction    n_i = sum over incident triangles, increasing id, of
  *               cross(B-A, C-A) (component order x,y,z; each product rounded,
  *               then the difference).  m = (nx - (X/Z)*nz, ny - (Y/Z)*nz).
@@ -75,6 +79,74 @@ static float grad_y(const float *D, int W, int H, int x, int y) {
 
 /* owned zero set of an edge under the top-left rule */
 static int owns(int64_t ex, int64_t ey) { return ey < 0 || (ey == 0 && ex > 0); }
+
+/* area-weighted vertex normals, incident triangles in increasing id order */
+static void vertex_normals(const float *V, const int32_t *F, int T, int N, float *nrm) {
+    for (int i = 0; i < 3 * N; ++i) nrm[i] = 0.0f;
+    for (int t = 0; t < T; ++t) {
+        int ia = F[3 * t], ib = F[3 * t + 1], ic = F[3 * t + 2];
+        float e1x = V[3 * ib] - V[3 * ia], e1y = V[3 * ib + 1] - V[3 * ia + 1], e1z = V[3 * ib + 2] - V[3 * ia + 2];
+        float e2x = V[3 * ic] - V[3 * ia], e2y = V[3 * ic + 1] - V[3 * ia + 1], e2z = V[3 * ic + 2] - V[3 * ia + 2];
+        float p1, p2;
+        p1 = e1y * e2z; p2 = e1z * e2y; float cxv = p1 - p2;
+        p1 = e1z * e2x; p2 = e1x * e2z; float cyv = p1 - p2;
+        p1 = e1x * e2y; p2 = e1y * e2x; float czv = p1 - p2;
+        int vv[3] = {ia, ib, ic};
+        for (int k = 0; k < 3; ++k) {
+            nrm[3 * vv[k]] = nrm[3 * vv[k]] + cxv;
+            nrm[3 * vv[k] + 1] = nrm[3 * vv[k] + 1] + cyv;
+            nrm[3 * vv[k] + 2] = nrm[3 * vv[k] + 2] + czv;
+        }
+    }
+}
+
+/* b_i = -1 rule for vertex i (projection uv must be valid and in the image):
+ * returns 1 iff the foreground mask is set at rint(uv) and d > 0 */
+static int direction_neg(const float *V, const int32_t *F, int T, const float *nrm, const float *uv, int W, int H,
+                         const float *DT, const uint8_t *mask, int i) {
+    (void)F; (void)T;
+    float X = V[3 * i], Y = V[3 * i + 1], Z = V[3 * i + 2];
+    float xz = X / Z, yz = Y / Z;
+    float t1 = xz * nrm[3 * i + 2]; float mx = nrm[3 * i] - t1;
+    float t2 = yz * nrm[3 * i + 2]; float my = nrm[3 * i + 1] - t2;
+    float u = uv[2 * i], v = uv[2 * i + 1];
+    int x0 = (int)floorf(u), y0 = (int)floorf(v);
+    float fx = u - (float)x0, fy = v - (float)y0;
+    int x1 = x0 + 1 < W ? x0 + 1 : W - 1;
+    int y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+    float gx = lerpf(lerpf(grad_x(DT, W, x0, y0), grad_x(DT, W, x1, y0), fx),
+                     lerpf(grad_x(DT, W, x0, y1), grad_x(DT, W, x1, y1), fx), fy);
+    float gy = lerpf(lerpf(grad_y(DT, W, H, x0, y0), grad_y(DT, W, H, x1, y0), fx),
+                     lerpf(grad_y(DT, W, H, x0, y1), grad_y(DT, W, H, x1, y1), fx), fy);
+    float q1 = mx * gx; float q2 = my * gy; float d = q1 + q2;
+    int64_t px = (int64_t)rintf(u), py = (int64_t)rintf(v);
+    int inside = mask[py * W + px] != 0;
+    return inside && d > 0.0f;
+}
+
+/* Directions b_i of the vertices flagged in `sel` at the surface V (the
+ * contour set B stays that of the frame; b_i follows the current surface):
+ * bneg[i] = 1 iff b_i = -1.  Vertices whose projection is invalid or
+ * outside the image get 0 (they carry no residual). */
+void oracle_directions(const float *V, int N, const int32_t *F, int T, float f, float cx, float cy, int W, int H,
+                       const float *DT, const uint8_t *mask, const uint8_t *sel, uint8_t *bneg) {
+    float *nrm = (float *)malloc(sizeof(float) * 3 * (size_t)(N > 0 ? N : 1));
+    float *uv = (float *)malloc(sizeof(float) * 2 * (size_t)(N > 0 ? N : 1));
+    vertex_normals(V, F, T, N, nrm);
+    for (int i = 0; i < N; ++i) {
+        bneg[i] = 0;
+        if (!sel[i]) continue;
+        float X = V[3 * i], Y = V[3 * i + 1], Z = V[3 * i + 2];
+        if (!(Z > 1e-3f)) continue;
+        float a = f * X; float b = a / Z; float u = b + cx;
+        float c = f * Y; float d = c / Z; float v = d + cy;
+        uv[2 * i] = u; uv[2 * i + 1] = v;
+        if (!(u >= 0.0f && u <= (float)(W - 1) && v >= 0.0f && v <= (float)(H - 1))) continue;
+        bneg[i] = (uint8_t)direction_neg(V, F, T, nrm, uv, W, H, DT, mask, i);
+    }
+    free(nrm);
+    free(uv);
+}
 
 /*
  * V: N*3 FP32 warped positions.  F: T*3 triangles.  E: NE*4 mesh edges
@@ -195,43 +267,22 @@ void oracle_visibility(const float *V, int N, const int32_t *F, int T,
         int sil = (t1 < 0) ? 1 : (front[0] != front[1]);
         if (sil) { flags[v0] |= FLAG_ONSIL; flags[v1] |= FLAG_ONSIL; }
     }
-    /* normals for B */
-    for (int i = 0; i < 3 * N; ++i) nrm[i] = 0.0f;
-    for (int t = 0; t < T; ++t) {
-        int ia = F[3 * t], ib = F[3 * t + 1], ic = F[3 * t + 2];
-        float e1x = V[3 * ib] - V[3 * ia], e1y = V[3 * ib + 1] - V[3 * ia + 1], e1z = V[3 * ib + 2] - V[3 * ia + 2];
-        float e2x = V[3 * ic] - V[3 * ia], e2y = V[3 * ic + 1] - V[3 * ia + 1], e2z = V[3 * ic + 2] - V[3 * ia + 2];
-        float p1, p2;
-        p1 = e1y * e2z; p2 = e1z * e2y; float cxv = p1 - p2;
-        p1 = e1z * e2x; p2 = e1x * e2z; float cyv = p1 - p2;
-        p1 = e1x * e2y; p2 = e1y * e2x; float czv = p1 - p2;
-        int vv[3] = {ia, ib, ic};
-        for (int k = 0; k < 3; ++k) {
-            nrm[3 * vv[k]] = nrm[3 * vv[k]] + cxv;
-            nrm[3 * vv[k] + 1] = nrm[3 * vv[k] + 1] + cyv;
-            nrm[3 * vv[k] + 2] = nrm[3 * vv[k] + 2] + czv;
-        }
-    }
+    vertex_normals(V, F, T, N, nrm);
     for (int i = 0; i < N; ++i) {
         if (!((flags[i] & FLAG_VISIBLE) && (flags[i] & FLAG_ONSIL))) continue;
+        {
+            int64_t px = (int64_t)rintf(uv[2 * i]), py = (int64_t)rintf(uv[2 * i + 1]);
+            int outline = 0;
+            for (int dy = -1; dy <= 1 && !outline; ++dy)
+                for (int dx = -1; dx <= 1 && !outline; ++dx) {
+                    int64_t qx = px + dx, qy = py + dy;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) outline = 1;
+                    else if (zbuf[qy * W + qx] == ~(uint64_t)0) outline = 1;
+                }
+            if (!outline) continue;
+        }
         flags[i] |= FLAG_INB;
-        float X = V[3 * i], Y = V[3 * i + 1], Z = V[3 * i + 2];
-        float xz = X / Z, yz = Y / Z;
-        float t1 = xz * nrm[3 * i + 2]; float mx = nrm[3 * i] - t1;
-        float t2 = yz * nrm[3 * i + 2]; float my = nrm[3 * i + 1] - t2;
-        float u = uv[2 * i], v = uv[2 * i + 1];
-        int x0 = (int)floorf(u), y0 = (int)floorf(v);
-        float fx = u - (float)x0, fy = v - (float)y0;
-        int x1 = x0 + 1 < W ? x0 + 1 : W - 1;
-        int y1 = y0 + 1 < H ? y0 + 1 : H - 1;
-        float gx = lerpf(lerpf(grad_x(DT, W, x0, y0), grad_x(DT, W, x1, y0), fx),
-                         lerpf(grad_x(DT, W, x0, y1), grad_x(DT, W, x1, y1), fx), fy);
-        float gy = lerpf(lerpf(grad_y(DT, W, H, x0, y0), grad_y(DT, W, H, x1, y0), fx),
-                         lerpf(grad_y(DT, W, H, x0, y1), grad_y(DT, W, H, x1, y1), fx), fy);
-        float q1 = mx * gx; float q2 = my * gy; float d = q1 + q2;
-        int64_t px = (int64_t)rintf(u), py = (int64_t)rintf(v);
-        int inside = mask[py * W + px] != 0;
-        if (inside && d > 0.0f) flags[i] |= FLAG_BNEG;
+        if (direction_neg(V, F, T, nrm, uv, W, H, DT, mask, i)) flags[i] |= FLAG_BNEG;
     }
     free(S);
     free(ok);

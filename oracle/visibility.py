@@ -40,6 +40,9 @@ def _load():
                                            ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_int, ctypes.c_int, P, P, ctypes.c_float, P, P, P]
         _lib.oracle_visibility.restype = None
+        _lib.oracle_directions.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_int, ctypes.c_int, P, P, P, P]
+        _lib.oracle_directions.restype = None
     return _lib
 
 
@@ -91,3 +94,19 @@ def visibility(Vwarp32, F, cam_f, cam_cx, cam_cy, W, H, DT, mask, eps=1e-2, edge
                           M.ctypes.data, float(np.float32(eps)), uv.ctypes.data, zbuf.ctypes.data,
                           flags.ctypes.data)
     return dict(uv=uv, zbuf=zbuf, flags=flags)
+
+
+def directions(Vwarp32, F, cam_f, cam_cx, cam_cy, W, H, DT, mask, sel):
+    """b_i = -1 flags (bool) of the selected vertices at the FP32 surface
+    Vwarp32 (the direction rule re-evaluated on the current surface)."""
+    lib = _load()
+    V = np.ascontiguousarray(Vwarp32, dtype=np.float32)
+    Fi = np.ascontiguousarray(F, dtype=np.int32)
+    D = np.ascontiguousarray(DT, dtype=np.float32)
+    M = np.ascontiguousarray(mask, dtype=np.uint8)
+    S = np.ascontiguousarray(sel, dtype=np.uint8)
+    out = np.zeros(len(V), dtype=np.uint8)
+    lib.oracle_directions(V.ctypes.data, len(V), Fi.ctypes.data, len(Fi), float(np.float32(cam_f)),
+                          float(np.float32(cam_cx)), float(np.float32(cam_cy)), int(W), int(H), D.ctypes.data,
+                          M.ctypes.data, S.ctypes.data, out.ctypes.data)
+    return out != 0

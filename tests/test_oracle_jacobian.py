@@ -101,6 +101,7 @@ def test_normal_equations_rhs_is_gradient(tiny_problem):
     """-J^T F is minus half the gradient of E on affine images (b_i = +1)."""
     P = _affine_problem(tiny_problem)
     P.bsign = np.ones_like(P.bsign)
+    P.tris = None          # keep b_i = +1 (no direction update)
     R, t = _params(P, 4)
     A, b, F, J = nr.normal_equations(P, R, t)
     vr = nr.vertex_residuals(P, R, t)
