@@ -65,6 +65,10 @@ typedef struct {
     float lambda_3d;
     float lambda_sil;
     int n_gn_pose;      /* Gauss-Newton steps of the pose stage, default 5 */
+    float lambda_prior; /* pose stage: weight of (theta - theta_start)^2 on the
+                           Euler angles, default 1e4 (keeps the 57x57 system
+                           positive definite: bone twists that move no joint and
+                           no silhouette are otherwise undetermined) */
     int pcg_kernel;     /* 0 (default): one cluster-persistent kernel runs all PCG
                            iterations of a Gauss-Newton step when the capture's
                            per-CTA data fits in shared memory; 1: one launch per
@@ -157,15 +161,17 @@ lc_status lc_upload_frame(lc_ctx *ctx, const float *rgb, const float *dt, const 
 /* ---- solve ---------------------------------------------------------------- */
 
 /* Non-rigid stage (Sec. 3.4 and Sec. 4): from the current node parameters,
- * warp, find visibility / contour set / b_i once, then n_gn Gauss-Newton
- * steps, each solving J^T J delta = -J^T F by n_pcg iterations of
+ * warp, find visibility and the contour set B once per frame, then n_gn
+ * Gauss-Newton steps, each re-deciding b_i for B on the current surface and
+ * solving J^T J delta = -J^T F by n_pcg iterations of
  * Jacobi-preconditioned CG from zero, then R_k <- Exp(d_omega_k) R_k,
  * t_k += d_t_k.  The whole sequence runs as one captured CUDA graph.
  * `stats` may be null; when given, the call synchronises and fills it. */
 lc_status lc_solve_nonrigid(lc_ctx *ctx, lc_solve_stats *stats);
 
 /* Read the result.  node_R n x 9, node_t n x 3, V_out N x 3 (warped
- * vertices), flags N (LC_FLAG_* bits of the last visibility pass),
+ * vertices), flags N (LC_FLAG_* bits of the last visibility pass; BNEG as
+ * last decided, at the final linearisation point),
  * pose N_DOF (pose parameters, see lc_upload_skeleton).  Null pointers are
  * skipped.  Synchronises. */
 lc_status lc_read_back(lc_ctx *ctx, float *node_R, float *node_t, float *V_out, uint8_t *flags,
@@ -179,10 +185,13 @@ lc_status lc_compute_visibility(lc_ctx *ctx);
 
 /* zbuf H x W 64-bit keys (bits of the FP32 depth << 32 | triangle id; all
  * ones = empty), flags N, uv N x 2 projected positions of the visibility
- * pass.  Null pointers are skipped.  Synchronises. */
+ * pass.  After lc_solve_pose: the pose stage's decisions (z-buffer,
+ * visibility and B at its starting pose; BNEG and uv at its final pose).
+ * Null pointers are skipped.  Synchronises. */
 lc_status lc_read_visibility(lc_ctx *ctx, uint64_t *zbuf, uint8_t *flags, float *uv);
 
-/* Linearise at the current node parameters (visibility must exist): warped
+/* Linearise at the current node parameters (visibility must exist; b_i of
+ * the contour set is re-decided here, as in every Gauss-Newton step): warped
  * vertices v_warp N x 3, projections uv N x 2, per-vertex residuals
  * r_photo N x 3 (sqrt(w_p)(I - C), zero where inactive) and r_sil N
  * (sqrt(w_s) DT), per-vertex normal blocks H N x 6 (h00 h01 h02 h11 h12 h22
@@ -220,12 +229,24 @@ lc_status lc_upload_skeleton(lc_ctx *ctx, int J, const int32_t *parents, const f
                              const uint8_t *dof, const int32_t *skin_idx, const float *skin_w);
 /* Set the pose vector (N_DOF values) the next pose solve starts from. */
 lc_status lc_set_pose(lc_ctx *ctx, const float *pose);
-/* Pose stage: n_gn_pose Gauss-Newton steps on the 2D joint, 3D joint and
- * silhouette terms, dense normal equations solved by an FP64 Cholesky
- * factorisation on the device.  Afterwards the skinned mesh becomes the rest
- * geometry of the non-rigid stage.  `stats` may be null (else synchronises;
- * e_gn / step_norm hold the pose stage's history). */
+/* Pose stage (Sec. 3.3; Sec. 4 pose estimation): from the current pose,
+ * skin the template (linear blend skinning), take the contour set B of the
+ * skinned mesh once, then n_gn_pose Gauss-Newton steps (each re-deciding b_i
+ * on the current skinned surface) on
+ *   lambda_2d |pi(o_j) - P2D_j|^2 + lambda_3d |o_j - P3D_j|^2
+ *   + lambda_sil / |B| sum_B DT(pi(V_i))^2 + lambda_prior |theta - theta_start|^2
+ * with a dense FP32 Jacobian, FP32 J^T J and an FP64 Cholesky solve on the
+ * device (a non-positive pivot returns LC_ERR_NUMERIC when stats are read).
+ * Afterwards the skinned mesh becomes the rest geometry of the non-rigid
+ * stage and the graph nodes move with it.  `stats` may be null (else the
+ * call synchronises; e_gn / step_norm hold the history, e_total the final
+ * energy, n_boundary |B|). */
 lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
+/* Inspection: at the current pose, recompute B and b_i and export the pose
+ * normal equations: V_skinned N x 3 (FP32 skinned template), A n_dof x n_dof
+ * (J^T J + prior), g n_dof (-J^T F - prior gradient), energy 1.  Null
+ * pointers are skipped.  Synchronises. */
+lc_status lc_eval_pose(lc_ctx *ctx, float *V_skinned, double *A, double *g, double *energy);
 
 /* ---- profiling ------------------------------------------------------------ */
 

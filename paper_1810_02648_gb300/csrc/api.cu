@@ -109,6 +109,7 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->lambda_3d = 28.0f;
     p->lambda_sil = 200.0f;
     p->n_gn_pose = 5;
+    p->lambda_prior = 1e4f;
     p->pcg_kernel = 0;
     return LC_OK;
 }
@@ -183,12 +184,14 @@ void lc_ctx::apply_params() {
 extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
     if (!ctx || !p) return LC_ERR_ARG;
     if (p->n_gn < 1 || p->n_gn > LC_MAX_GN || p->n_pcg < 1 || p->n_gn_pose < 1 || p->n_gn_pose > LC_MAX_GN ||
-        !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f))
+        !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f) ||
+        !(p->lambda_2d >= 0.f) || !(p->lambda_3d >= 0.f) || !(p->lambda_sil >= 0.f) || !(p->lambda_prior >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel)
         ctx->drop_graph();
+    if (p->n_gn_pose != ctx->params.n_gn_pose) ctx->pose_drop_graph();
     ctx->params = *p;
     ctx->apply_params();
     return ctx->sync_desc();
@@ -467,6 +470,7 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     ctx->ensure_partials();
     ctx->has_graph = true;
     ctx->drop_graph();
+    ctx->pose_drop_graph();   // the pose solve moves the graph nodes
     return ctx->sync_desc();
 }
 
@@ -623,7 +627,7 @@ void lc_ctx::enqueue_nonrigid() {
             launch_warp(dC, C, st);
         }
         mark(LC_PH_LIN);
-        launch_linearize(dC, C, gn, st);
+        launch_linearize(dC, C, true, st);
         mark(LC_PH_RHS);
         launch_rhs(dC, C, gn, false, st);
         enqueue_pcg();
@@ -633,7 +637,7 @@ void lc_ctx::enqueue_nonrigid() {
     mark(LC_PH_WARP);
     launch_warp(dC, C, st);
     mark(LC_PH_LIN);
-    launch_linearize(dC, C, params.n_gn, st);
+    launch_linearize(dC, C, false, st);
     mark(LC_PH_RHS);
     launch_rhs(dC, C, params.n_gn, true, st);
     mark_end();
@@ -828,7 +832,7 @@ extern "C" lc_status lc_read_visibility(lc_ctx* ctx, uint64_t* zbuf, uint8_t* fl
 
 lc_status lc_ctx::linearize_now(bool with_rhs) {
     launch_warp(dC, hC, stream);
-    launch_linearize(dC, hC, LC_MAX_GN, stream);
+    launch_linearize(dC, hC, true, stream);
     launch_rhs(dC, hC, LC_MAX_GN, !with_rhs, stream);
     has_lin = true;
     return cuda(cudaGetLastError(), "linearize");

@@ -189,27 +189,8 @@ __global__ void __launch_bounds__(kEdgeTile) silhouette_kernel(const CapDesc* __
     }
 }
 
-__device__ __forceinline__ float xlerp(float a, float b, float t) { return xadd(a, xmul(t, xsub(b, a))); }
-
-__device__ __forceinline__ float dt_at(const CapDesc& C, int x, int y) { return C.img[(size_t)y * C.W + x].w; }
-
-__device__ __forceinline__ float dt_grad_x(const CapDesc& C, int x, int y) {
-    const int W = C.W;
-    if (W < 2) return 0.f;
-    if (x == 0) return xsub(dt_at(C, 1, y), dt_at(C, 0, y));
-    if (x == W - 1) return xsub(dt_at(C, W - 1, y), dt_at(C, W - 2, y));
-    return xmul(xsub(dt_at(C, x + 1, y), dt_at(C, x - 1, y)), 0.5f);
-}
-
-__device__ __forceinline__ float dt_grad_y(const CapDesc& C, int x, int y) {
-    const int H = C.H;
-    if (H < 2) return 0.f;
-    if (y == 0) return xsub(dt_at(C, x, 1), dt_at(C, x, 0));
-    if (y == H - 1) return xsub(dt_at(C, x, H - 1), dt_at(C, x, H - 2));
-    return xmul(xsub(dt_at(C, x, y + 1), dt_at(C, x, y - 1)), 0.5f);
-}
-
-// contour set B and b_i for visible vertices on a silhouette edge
+// contour set B (visible vertices on a silhouette edge and on the model's
+// projected outline) and the directions b_i
 __global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __restrict__ caps,
                                                              const WorkItem* __restrict__ items) {
     int cap, tile;
@@ -221,39 +202,26 @@ __global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __res
         uint32_t fl = C.flags[i];
         if (fl & LC_VIS_BIT) cnt[0] = 1;
         if ((fl & LC_VIS_BIT) && (fl & LC_ONSIL_BIT)) {
-            fl |= LC_INB_BIT;
-            cnt[1] = 1;
-            // area-weighted normal: incident triangles in ascending id order
-            float nx = 0.f, ny = 0.f, nz = 0.f;
-            for (int j = C.vt_off[i]; j < C.vt_off[i + 1]; ++j) {
-                const int4 tri = C.tris[C.vt_tri[j]];
-                const float4 A = C.vw[tri.x], B = C.vw[tri.y], Q = C.vw[tri.z];
-                const float e1x = xsub(B.x, A.x), e1y = xsub(B.y, A.y), e1z = xsub(B.z, A.z);
-                const float e2x = xsub(Q.x, A.x), e2y = xsub(Q.y, A.y), e2z = xsub(Q.z, A.z);
-                nx = xadd(nx, xsub(xmul(e1y, e2z), xmul(e1z, e2y)));
-                ny = xadd(ny, xsub(xmul(e1z, e2x), xmul(e1x, e2z)));
-                nz = xadd(nz, xsub(xmul(e1x, e2y), xmul(e1y, e2x)));
-            }
-            const float4 v = C.vw[i];
-            const float mx = xsub(nx, xmul(xdiv(v.x, v.z), nz));
-            const float my = xsub(ny, xmul(xdiv(v.y, v.z), nz));
+            // only vertices on the model's projected outline: some pixel of
+            // the 3x3 block around rint(uv) is outside the image or uncovered
             const float2 uv = C.uv[i];
-            const int x0 = (int)floorf(uv.x), y0 = (int)floorf(uv.y);
-            const float fx = xsub(uv.x, (float)x0), fy = xsub(uv.y, (float)y0);
-            const int x1 = x0 + 1 < C.W ? x0 + 1 : C.W - 1;
-            const int y1 = y0 + 1 < C.H ? y0 + 1 : C.H - 1;
-            const float gx = xlerp(xlerp(dt_grad_x(C, x0, y0), dt_grad_x(C, x1, y0), fx),
-                                   xlerp(dt_grad_x(C, x0, y1), dt_grad_x(C, x1, y1), fx), fy);
-            const float gy = xlerp(xlerp(dt_grad_y(C, x0, y0), dt_grad_y(C, x1, y0), fx),
-                                   xlerp(dt_grad_y(C, x0, y1), dt_grad_y(C, x1, y1), fx), fy);
-            const float d = xadd(xmul(mx, gx), xmul(my, gy));
             const long long px = __float2ll_rn(uv.x), py = __float2ll_rn(uv.y);
-            const bool inside = C.mask[py * C.W + px] != 0;
-            if (inside && d > 0.f) {
-                fl |= LC_BNEG_BIT;
-                cnt[2] = 1;
+            bool outline = false;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const long long qx = px + dx, qy = py + dy;
+                    if (qx < 0 || qy < 0 || qx >= C.W || qy >= C.H) outline = true;
+                    else if (C.zbuf[qy * C.W + qx] == ~0ULL) outline = true;
+                }
+            if (outline) {
+                fl |= LC_INB_BIT;
+                cnt[1] = 1;
+                if (direction_neg(C, i)) {
+                    fl |= LC_BNEG_BIT;
+                    cnt[2] = 1;
+                }
+                C.flags[i] = fl;
             }
-            C.flags[i] = fl;
         }
     }
     // vertex counts for the statistics (integer block sums)

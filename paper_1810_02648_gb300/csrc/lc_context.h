@@ -74,6 +74,7 @@ struct lc_ctx {
     lc_status vec_out(float* dst, const float4* src);
     float* tmp_out();
     // pose stage (pose_api.cu)
+    void enqueue_pose();
     void pose_release();
     void pose_drop_graph();
     lc_status pose_frame(const float* joints2d, const float* joints3d);

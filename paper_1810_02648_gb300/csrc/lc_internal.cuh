@@ -138,6 +138,61 @@ __device__ __forceinline__ bool in_image(float2 uv, int W, int H) {
     return uv.x >= 0.0f && uv.x <= (float)(W - 1) && uv.y >= 0.0f && uv.y <= (float)(H - 1);
 }
 
+// ---- exact direction rule b_i (shared by the contour pass, the non-rigid
+// linearisation and the pose stage) ------------------------------------------
+__device__ __forceinline__ float xlerp(float a, float b, float t) { return xadd(a, xmul(t, xsub(b, a))); }
+
+__device__ __forceinline__ float dt_px(const float4* img, int W, int x, int y) { return img[(size_t)y * W + x].w; }
+
+__device__ __forceinline__ float dt_grad_x_exact(const float4* img, int W, int x, int y) {
+    if (W < 2) return 0.f;
+    if (x == 0) return xsub(dt_px(img, W, 1, y), dt_px(img, W, 0, y));
+    if (x == W - 1) return xsub(dt_px(img, W, W - 1, y), dt_px(img, W, W - 2, y));
+    return xmul(xsub(dt_px(img, W, x + 1, y), dt_px(img, W, x - 1, y)), 0.5f);
+}
+
+__device__ __forceinline__ float dt_grad_y_exact(const float4* img, int W, int H, int x, int y) {
+    if (H < 2) return 0.f;
+    if (y == 0) return xsub(dt_px(img, W, x, 1), dt_px(img, W, x, 0));
+    if (y == H - 1) return xsub(dt_px(img, W, x, H - 1), dt_px(img, W, x, H - 2));
+    return xmul(xsub(dt_px(img, W, x, y + 1), dt_px(img, W, x, y - 1)), 0.5f);
+}
+
+// b_i = -1 iff the model point projects inside the image silhouette (mask at
+// rint(uv)) and its projected area-weighted normal m opposes z = -grad DT,
+// i.e. m . grad DT > 0 (Sec. 3.3).  Normal: incident triangles in ascending id
+// order, every FP32 operation rounded once.  The vertex must be valid and its
+// projection inside the image.
+__device__ __forceinline__ bool direction_neg(const CapDesc& C, int i) {
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    for (int j = C.vt_off[i]; j < C.vt_off[i + 1]; ++j) {
+        const int4 tri = C.tris[C.vt_tri[j]];
+        const float4 A = C.vw[tri.x], B = C.vw[tri.y], Q = C.vw[tri.z];
+        const float e1x = xsub(B.x, A.x), e1y = xsub(B.y, A.y), e1z = xsub(B.z, A.z);
+        const float e2x = xsub(Q.x, A.x), e2y = xsub(Q.y, A.y), e2z = xsub(Q.z, A.z);
+        nx = xadd(nx, xsub(xmul(e1y, e2z), xmul(e1z, e2y)));
+        ny = xadd(ny, xsub(xmul(e1z, e2x), xmul(e1x, e2z)));
+        nz = xadd(nz, xsub(xmul(e1x, e2y), xmul(e1y, e2x)));
+    }
+    const float4 v = C.vw[i];
+    const float mx = xsub(nx, xmul(xdiv(v.x, v.z), nz));
+    const float my = xsub(ny, xmul(xdiv(v.y, v.z), nz));
+    const float2 uv = C.uv[i];
+    const int x0 = (int)floorf(uv.x), y0 = (int)floorf(uv.y);
+    const float fx = xsub(uv.x, (float)x0), fy = xsub(uv.y, (float)y0);
+    const int x1 = x0 + 1 < C.W ? x0 + 1 : C.W - 1;
+    const int y1 = y0 + 1 < C.H ? y0 + 1 : C.H - 1;
+    const float gx = xlerp(xlerp(dt_grad_x_exact(C.img, C.W, x0, y0), dt_grad_x_exact(C.img, C.W, x1, y0), fx),
+                           xlerp(dt_grad_x_exact(C.img, C.W, x0, y1), dt_grad_x_exact(C.img, C.W, x1, y1), fx), fy);
+    const float gy = xlerp(xlerp(dt_grad_y_exact(C.img, C.W, C.H, x0, y0), dt_grad_y_exact(C.img, C.W, C.H, x1, y0), fx),
+                           xlerp(dt_grad_y_exact(C.img, C.W, C.H, x0, y1), dt_grad_y_exact(C.img, C.W, C.H, x1, y1), fx),
+                           fy);
+    const float d = xadd(xmul(mx, gx), xmul(my, gy));
+    const long long px = __float2ll_rn(uv.x), py = __float2ll_rn(uv.y);
+    const bool inside = C.mask[py * C.W + px] != 0;
+    return inside && d > 0.f;
+}
+
 // ---- FP64 block reduction helpers -----------------------------------------
 template <int NV>
 __device__ __forceinline__ void warp_sum(double (&v)[NV]) {
@@ -210,7 +265,7 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
                        uint8_t* mask, int W, int H, cudaStream_t st);
 void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
-void launch_linearize(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);

@@ -69,7 +69,7 @@ __device__ __forceinline__ float4 grad_y(const CapDesc& C, int x, int y) {
 // Linearisation: residuals, H_i, e_i and the data energy.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __restrict__ caps,
-                                                               const WorkItem* __restrict__ items, int slot) {
+                                                               const WorkItem* __restrict__ items, int update_b) {
     __shared__ double sh[kVertTile / 32][2];
     int cap, tile;
     decode(items, cap, tile);
@@ -77,12 +77,18 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     const int i = tile * kVertTile + threadIdx.x;
     double en[2] = {0.0, 0.0};
     if (i < C.N) {
-        const uint32_t fl = C.flags[i];
+        uint32_t fl = C.flags[i];
         const float4 v = C.vw[i];
         const float2 uv = C.uv[i];
         const bool ok = v.w > 0.f && in_image(uv, C.W, C.H);
         const bool ph = ok && (fl & LC_VIS_BIT);
         const bool si = ok && (fl & LC_INB_BIT);
+        if (update_b && si) {
+            // b_i follows the current surface; the contour set stays the frame's
+            const uint32_t nf = direction_neg(C, i) ? (fl | LC_BNEG_BIT) : (fl & ~LC_BNEG_BIT);
+            if (nf != fl) C.flags[i] = nf;
+            fl = nf;
+        }
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
@@ -136,11 +142,10 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         C.sc->e_lin[0] = tot[0];
         C.sc->e_lin[1] = tot[1];
     }
-    (void)slot;
 }
 
-void launch_linearize(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st) {
-    linearize_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, gn_slot);
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st) {
+    linearize_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, update_b ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------

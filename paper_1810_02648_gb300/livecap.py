@@ -24,7 +24,7 @@ class lc_params(ctypes.Structure):
     _fields_ = [("w_photo", ctypes.c_float), ("w_sil", ctypes.c_float), ("w_arap", ctypes.c_float),
                 ("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("eps_vis", ctypes.c_float),
                 ("lambda_2d", ctypes.c_float), ("lambda_3d", ctypes.c_float), ("lambda_sil", ctypes.c_float),
-                ("n_gn_pose", ctypes.c_int), ("pcg_kernel", ctypes.c_int)]
+                ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -69,6 +69,7 @@ _SIGS = {
     "lc_upload_skeleton": [_P, ctypes.c_int, _P, _P, _P, _P, _P],
     "lc_set_pose": [_P, _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
+    "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
     "lc_read_profile": [_P, _P, _P],
     "lc_visibility_noalloc": [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -314,6 +315,13 @@ class Context:
         pose = _arr(pose, np.float32)
         self._check(self._lib.lc_set_pose(self.h, _ptr(pose)))
 
+    def eval_pose(self) -> dict:
+        nd = self.n_dof
+        out = dict(V=np.zeros((self.N, 3), np.float32), A=np.zeros((nd, nd)), g=np.zeros(nd), energy=np.zeros(1))
+        self._check(self._lib.lc_eval_pose(self.h, _ptr(out["V"]), _ptr(out["A"]), _ptr(out["g"]),
+                                           _ptr(out["energy"])))
+        return out
+
     def solve_pose(self, stats: bool = True):
         if not stats:
             self._check(self._lib.lc_solve_pose(self.h, None))
@@ -324,11 +332,20 @@ class Context:
 
 
 def setup_scene(ctx: Context, scene, with_frame: bool = True):
-    """Upload a ``synth.Scene`` (template, camera, graph, weights, frame)."""
+    """Upload a ``synth.Scene`` (template, camera, graph, weights, frame, and
+    for body scenes the skeleton and start pose)."""
     wp, ws, wa = scene.weights
-    ctx.set_params(w_photo=wp, w_sil=ws, w_arap=wa, n_gn=scene.n_gn, n_pcg=scene.n_pcg)
+    ctx.set_params(w_photo=wp, w_sil=ws, w_arap=wa, n_gn=scene.n_gn, n_pcg=scene.n_pcg,
+                   n_gn_pose=scene.n_gn_pose)
     ctx.set_camera(scene.cam.f, scene.cam.cx, scene.cam.cy, scene.cam.W, scene.cam.H)
     ctx.upload_template(scene.V, scene.F, scene.albedo, scene.material)
     ctx.build_graph(scene.n_nodes, scene.K)
+    if scene.skeleton is not None:
+        sk = scene.skeleton
+        from synth.scenes import SKELETON_SITES
+        dof = np.ones(len(sk["parents"]), np.uint8)
+        dof[SKELETON_SITES] = 0
+        ctx.upload_skeleton(sk["parents"], sk["joints_rest"], dof, sk["skin_idx"], sk["skin_w"])
+        ctx.set_pose(scene.pose_init)
     if with_frame:
         ctx.upload_frame(scene.rgb, scene.dt, scene.mask.astype(np.uint8), scene.joints2d, scene.joints3d)

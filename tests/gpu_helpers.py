@@ -44,6 +44,20 @@ def set_flags(P, flags):
     P.bsign = np.where((flags & ovis.FLAG_BNEG) != 0, -1.0, 1.0)
 
 
+def check_frame_flags(flags, P):
+    """Final flags of a GPU solve against the oracle's problem: visibility and
+    the contour set (decided once per frame on identical vertices) bit-exact;
+    b_i, re-decided at every linearisation on each side's own iterate, may
+    differ where m . grad DT is within rounding of zero on the two iterates:
+    at most max(2, 1% of |B|) vertices.  Returns the mismatch count."""
+    assert np.array_equal((flags & ovis.FLAG_VISIBLE) != 0, P.vis)
+    assert np.array_equal((flags & ovis.FLAG_INB) != 0, P.inB)
+    neg = (flags & ovis.FLAG_BNEG) != 0
+    nb = int(((neg != (P.bsign < 0)) & P.inB).sum())
+    assert nb <= max(2, P.inB.sum() // 100)
+    return nb
+
+
 def random_params(n, seed, rot=0.05, trans=0.005):
     rng = np.random.default_rng(seed)
     R = onr.so3_exp(rng.normal(scale=rot, size=(n, 3))).astype(np.float32)
@@ -88,56 +102,103 @@ def oracle_vertex_blocks(P, v32, uv32):
     return dict(r_photo=r_photo, r_sil=r_sil, H=H6, e=e, photo_on=ph, sil_on=si)
 
 
+def _r32(rng):
+    """FP32 rounding with a random tie-break perturbation of one unit roundoff."""
+    u = 2.0 ** -24
+
+    def r32(x):
+        x = np.asarray(x, dtype=np.float64)
+        return (x * (1.0 + u * rng.standard_normal(x.shape))).astype(np.float32).astype(np.float64)
+    return r32
+
+
+def pcg32(A, b, n, r32):
+    """The oracle's Jacobi-PCG with every vector and matrix-vector product
+    rounded by ``r32`` (one FP32 execution of the same algorithm)."""
+    d = np.asarray(A.diagonal(), dtype=np.float64)
+    minv = r32(np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0))
+    x = np.zeros_like(b)
+    r = r32(b)
+    z = r32(minv * r)
+    p = z.copy()
+    rz = float(r @ z)
+    info = dict(iters=0, breakdown=False, rz=[rz])
+    if rz == 0.0:
+        return x, info
+    for it in range(n):
+        Ap = r32(A @ p)
+        pAp = float(p @ Ap)
+        if not pAp > 0.0:
+            info["breakdown"] = True
+            break
+        al = np.float32(rz / pAp)
+        x = r32(x + al * p)
+        r = r32(r - al * Ap)
+        z = r32(minv * r)
+        rzn = float(r @ z)
+        info["iters"] = it + 1
+        if rzn == 0.0:
+            break
+        p = r32(z + np.float32(rzn / rz) * p)
+        rz = rzn
+    return x, info
+
+
 def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None):
-    """Spread of the oracle's end-to-end result when its CG vectors and
-    matrix-vector products are rounded to FP32 with a random tie-break
-    perturbation of one unit roundoff (seeded).  This measures how far any
-    FP32 execution of the same algorithm may land from the FP64 result: CG
-    amplifies rounding along the system's ill-conditioned (depth) directions.
+    """Spread of the oracle's end-to-end result under FP32 rounding, with a
+    random tie-break perturbation of one unit roundoff (seeded), of what an
+    FP32 execution rounds: the node parameters after every update, the warped
+    vertices, the residuals and Jacobian entries, and the CG vectors and
+    matrix-vector products.  This measures how far any FP32 execution of the
+    same algorithm may land from the FP64 result: CG amplifies rounding along
+    the system's ill-conditioned (depth) directions, and a projection within
+    rounding of a pixel boundary takes the other cell of the piecewise
+    bilinear image and DT gradients.
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
     ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
-    orig = onr.pcg
+    orig = (onr.pcg, onr.linearise, onr.apply_update, onr.warp)
     dE, dV = 0.0, 0.0
-    u = 2.0 ** -24
     for seed in range(n_runs):
-        rng = np.random.default_rng(1000 + seed)
+        r32 = _r32(np.random.default_rng(1000 + seed))
 
-        def r32(x):
-            return (x * (1.0 + u * rng.standard_normal(x.shape))).astype(np.float32).astype(np.float64)
+        def lin32(P, R, t):
+            F, J = orig[1](P, R, t)
+            J = J.tocsr(copy=True)
+            J.data = r32(J.data)
+            return r32(F), J
 
-        def pcg32(A, b, n):
-            d = np.asarray(A.diagonal(), dtype=np.float64)
-            minv = r32(np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0))
-            x = np.zeros_like(b)
-            r = r32(b)
-            z = r32(minv * r)
-            p = z.copy()
-            rz = float(r @ z)
-            info = dict(iters=0, breakdown=False, rz=[rz])
-            if rz == 0.0:
-                return x, info
-            for it in range(n):
-                Ap = r32(A @ p)
-                pAp = float(p @ Ap)
-                if not pAp > 0.0:
-                    info["breakdown"] = True
-                    break
-                al = np.float32(rz / pAp)
-                x = r32(x + al * p)
-                r = r32(r - al * Ap)
-                z = r32(minv * r)
-                rzn = float(r @ z)
-                info["iters"] = it + 1
-                if rzn == 0.0:
-                    break
-                p = r32(z + np.float32(rzn / rz) * p)
-                rz = rzn
-            return x, info
-        onr.pcg = pcg32
+        def upd32(R, t, delta):
+            R1, t1 = orig[2](R, t, delta)
+            return r32(R1), r32(t1)
+
+        onr.pcg = lambda A, b, n: pcg32(A, b, n, r32)
+        onr.linearise = lin32
+        onr.apply_update = upd32
+        def warp32(P, R, t):
+            # an FP32 warp is exact where the displacement is exactly zero
+            v = orig[3](P, R, t)
+            return np.where(v != P.base, r32(v), v)
+
+        onr.warp = warp32
         try:
             o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
         finally:
-            onr.pcg = orig
+            onr.pcg, onr.linearise, onr.apply_update, onr.warp = orig
         dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
         dV = max(dV, float(np.abs(o["v"] - ref["v"]).max()))
     return ref, dE, dV
+
+
+def q_band(A, b, n, n_runs=3):
+    """Spread of the quadratic model q(d) = d^T A d / 2 - b^T d at the n-step
+    PCG iterate over FP32 executions (``pcg32``), relative to the FP64
+    iterate's q.  Returns (FP64 iterate, its info, max relative spread)."""
+    from oracle.nonrigid import pcg
+    dref, info = pcg(A, b, n)
+    q = lambda d: 0.5 * d @ (A @ d) - b @ d  # noqa: E731
+    q0 = q(dref)
+    spread = 0.0
+    for seed in range(n_runs):
+        d, _ = pcg32(A, b, n, _r32(np.random.default_rng(2000 + seed)))
+        spread = max(spread, abs(q(d) - q0) / abs(q0))
+    return dref, info, spread
