@@ -227,15 +227,21 @@ lc_status lc_solve_linear(lc_ctx *ctx, float *delta, int *iters);
  * excluding the root).  J <= 64. */
 lc_status lc_upload_skeleton(lc_ctx *ctx, int J, const int32_t *parents, const float *joints_rest,
                              const uint8_t *dof, const int32_t *skin_idx, const float *skin_w);
-/* Set the pose vector (N_DOF values) the next pose solve starts from. */
+/* Set the pose vector (N_DOF values) the next pose solve starts from.
+ * Synchronises. */
 lc_status lc_set_pose(lc_ctx *ctx, const float *pose);
+/* Restart from the pose last given to lc_set_pose (the rest pose if none):
+ * a device-side copy, enqueue only, so a frame can be re-solved from the same
+ * start without a host round trip. */
+lc_status lc_reset_pose(lc_ctx *ctx);
 /* Pose stage (Sec. 3.3; Sec. 4 pose estimation): from the current pose,
  * skin the template (linear blend skinning), take the contour set B of the
  * skinned mesh once, then n_gn_pose Gauss-Newton steps (each re-deciding b_i
  * on the current skinned surface) on
  *   lambda_2d |pi(o_j) - P2D_j|^2 + lambda_3d |o_j - P3D_j|^2
  *   + lambda_sil / |B| sum_B DT(pi(V_i))^2 + lambda_prior |theta - theta_start|^2
- * with a dense FP32 Jacobian, FP32 J^T J and an FP64 Cholesky solve on the
+ * with a dense FP32 Jacobian, FP32 J^T J and an FP64 square-root-free
+ * Cholesky (L D L^T) solve on the
  * device (a non-positive pivot returns LC_ERR_NUMERIC when stats are read).
  * Afterwards the skinned mesh becomes the rest geometry of the non-rigid
  * stage and the graph nodes move with it.  `stats` may be null (else the

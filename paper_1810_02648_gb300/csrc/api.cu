@@ -581,11 +581,11 @@ void lc_ctx::mark(int phase) {
 
 void lc_ctx::mark_end() { mark(-1); }
 
-lc_status lc_ctx::accumulate_profile() {
-    if (!profiling || prof_used < 2) return LC_OK;
+lc_status lc_ctx::accumulate_profile(const ProfRange& r) {
+    if (!profiling || r.end - r.begin < 2) return LC_OK;
     lc_status s = cuda(cudaStreamSynchronize(stream), "synchronize");
     if (s) return s;
-    for (int j = 0; j + 1 < prof_used; ++j) {
+    for (int j = r.begin; j + 1 < r.end; ++j) {
         if (prof_phase[j] < 0) continue;
         float ms = 0.f;
         if ((s = cuda(cudaEventElapsedTime(&ms, prof_ev[j], prof_ev[j + 1]), "event time"))) return s;
@@ -614,7 +614,7 @@ void lc_ctx::enqueue_pcg() {
 void lc_ctx::enqueue_nonrigid() {
     const CapDesc& C = hC;
     cudaStream_t st = stream;
-    prof_used = 0;
+    prof_nonrigid.begin = prof_used;
     cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
     mark(LC_PH_WARP);
@@ -641,6 +641,7 @@ void lc_ctx::enqueue_nonrigid() {
     mark(LC_PH_RHS);
     launch_rhs(dC, C, params.n_gn, true, st);
     mark_end();
+    prof_nonrigid.end = prof_used;
 }
 
 lc_status lc_ctx::capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)()) {
@@ -704,7 +705,7 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     cudaSetDevice(ctx->device);
     if (!ctx->gexec && (s = ctx->capture(&ctx->gexec, &ctx->graph_kernels, &lc_ctx::enqueue_nonrigid))) return s;
     if ((s = ctx->cuda(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch"))) return s;
-    if ((s = ctx->accumulate_profile())) return s;
+    if ((s = ctx->accumulate_profile(ctx->prof_nonrigid))) return s;
     ctx->has_vis = true;
     ctx->has_lin = true;
     if (stats) {
@@ -722,6 +723,8 @@ extern "C" lc_status lc_set_profiling(lc_ctx* ctx, int on) {
         ctx->profiling = on != 0;
         ctx->drop_graph();
         ctx->pose_drop_graph();
+        ctx->prof_used = 0;
+        ctx->prof_nonrigid = ctx->prof_pose = lc_ctx::ProfRange{};
     }
     for (int j = 0; j < LC_N_PHASES; ++j) {
         ctx->prof_ms[j] = 0.0;

@@ -45,12 +45,15 @@ struct lc_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_phase;   // phase of the segment starting at event j
-    int prof_used = 0;
+    int prof_used = 0;             // events handed out since profiling was switched on
+    struct ProfRange {
+        int begin = 0, end = 0;    // the events one captured graph records
+    } prof_nonrigid, prof_pose;
     double prof_ms[LC_N_PHASES] = {0};
     int prof_cnt[LC_N_PHASES] = {0};
     void mark(int phase);          // record the next event of the chain (capture time)
     void mark_end();
-    lc_status accumulate_profile();
+    lc_status accumulate_profile(const ProfRange& r);
 
     lc_status fail(lc_status st, const char* fmt, ...);
     lc_status cuda(cudaError_t e, const char* what);

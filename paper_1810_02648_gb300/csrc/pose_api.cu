@@ -1,4 +1,5 @@
 // Skeletal pose stage (Sec. 3.3): entry points, state and the captured solve.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -16,6 +17,7 @@ struct PoseState {
     int graph_kernels = 0;
     int graph_n_gn = 0;
     bool has_pose = false;
+    float* pose_set = nullptr;      // kMaxDof + 9: the pose last given to lc_set_pose, then its root rotation
 };
 
 static void rodrigues(const double* w, double* R) {
@@ -65,8 +67,9 @@ void lc_ctx::pose_release() {
     pose_drop_graph();
     void* bufs[] = {(void*)pose->h.parents, (void*)pose->h.rest, (void*)pose->h.col, (void*)pose->h.anc,
                     (void*)pose->h.skin_idx, (void*)pose->h.skin_w, (void*)pose->h.j2d, (void*)pose->h.j3d,
-                    pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.F, pose->h.Jm, pose->h.blist,
-                    pose->h.bcount, pose->h.hist, pose->h.expA, pose->h.status, pose->d};
+                    (void*)pose->h.level, (void*)pose->h.pairs, pose->h.fk, pose->h.part,
+                    pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.blist,
+                    pose->h.bcount, pose->h.hist, pose->h.expA, pose->h.status, pose->d, pose->pose_set};
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
@@ -167,6 +170,16 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     std::vector<unsigned long long> anc(J, 0ULL);
     for (int j = 0; j < J; ++j)
         for (int a = j; a >= 0; a = par[a]) anc[j] |= 1ULL << a;
+    std::vector<int> level(J, 0);
+    int n_levels = 1;
+    for (int j = 1; j < J; ++j) {
+        level[j] = level[par[j]] + 1;
+        n_levels = std::max(n_levels, level[j] + 1);
+    }
+    std::vector<unsigned short> pairs;
+    for (int a = 0; a <= nd; ++a)
+        for (int b = a; b <= nd; ++b) pairs.push_back((unsigned short)(a << 8 | b));
+    if (cudaError_t e = pose_kernels_init(nd)) return ctx->cuda(e, "pose kernel attributes");
     ctx->pose_release();
     ctx->pose = new PoseState();
     PoseState& S = *ctx->pose;
@@ -174,8 +187,12 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     PoseDesc& P = S.h;
     P.J = J;
     P.n_dof = nd;
-    P.max_rows = 5 * J + N;
+    P.n_levels = n_levels;
     P.parents = (const int*)ctx->alloc(sizeof(int) * J);
+    P.level = (const int*)ctx->alloc(sizeof(int) * J);
+    P.pairs = (const unsigned short*)ctx->alloc(sizeof(unsigned short) * pairs.size());
+    P.fk = (PoseFk*)ctx->alloc(sizeof(PoseFk));
+    P.part = (float*)ctx->alloc(sizeof(float) * pairs.size() * (size_t)pose_system_ctas(J, N));
     P.rest = (const float4*)ctx->alloc(sizeof(float4) * J);
     P.col = (const int*)ctx->alloc(sizeof(int) * J);
     P.anc = (const unsigned long long*)ctx->alloc(sizeof(unsigned long long) * J);
@@ -187,14 +204,13 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     P.pose = (float*)ctx->alloc(sizeof(float) * kMaxDof);
     P.pose_start = (float*)ctx->alloc(sizeof(float) * kMaxDof);
     P.Rroot = (float*)ctx->alloc(sizeof(float) * 9);
-    P.F = (float*)ctx->alloc(sizeof(float) * P.max_rows);
-    P.Jm = (float*)ctx->alloc(sizeof(float) * (size_t)nd * P.max_rows);
     P.blist = (int*)ctx->alloc(sizeof(int) * N);
     P.bcount = (int*)ctx->alloc(sizeof(int));
     P.hist = (double*)ctx->alloc(sizeof(double) * 2 * (LC_MAX_GN + 1));
     P.expA = (double*)ctx->alloc(sizeof(double) * nd * (nd + 1));
     P.status = (int*)ctx->alloc(sizeof(int));
     S.d = (PoseDesc*)ctx->alloc(sizeof(PoseDesc));
+    S.pose_set = (float*)ctx->alloc(sizeof(float) * (kMaxDof + 9));
     if (!ctx->err.empty()) return LC_ERR_OOM;
     std::vector<float4> r4(J), w4(N);
     std::vector<int4> i4(N);
@@ -215,10 +231,13 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
         const void* src;
         size_t bytes;
     } ups[] = {{P.parents, par.data(), sizeof(int) * J},     {P.rest, r4.data(), sizeof(float4) * J},
+               {P.level, level.data(), sizeof(int) * J},
+               {P.pairs, pairs.data(), sizeof(unsigned short) * pairs.size()},
                {P.col, col.data(), sizeof(int) * J},         {P.anc, anc.data(), sizeof(unsigned long long) * J},
                {P.skin_idx, i4.data(), sizeof(int4) * N},    {P.skin_w, w4.data(), sizeof(float4) * N},
                {P.pose, p0.data(), sizeof(float) * kMaxDof}, {P.pose_start, p0.data(), sizeof(float) * kMaxDof},
-               {P.Rroot, I3, sizeof(I3)}};
+               {P.Rroot, I3, sizeof(I3)},                    {S.pose_set, p0.data(), sizeof(float) * kMaxDof},
+               {S.pose_set + kMaxDof, I3, sizeof(I3)}};
     for (auto& u : ups)
         if ((s = ctx->cuda(cudaMemcpyAsync((void*)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st), "skeleton upload")))
             return s;
@@ -245,33 +264,60 @@ extern "C" lc_status lc_set_pose(lc_ctx* ctx, const float* pose) {
     if ((s = ctx->cuda(cudaMemcpyAsync(ctx->pose->h.pose, p.data(), sizeof(float) * nd, cudaMemcpyHostToDevice, ctx->stream),
                        "pose upload")) ||
         (s = ctx->cuda(cudaMemcpyAsync(ctx->pose->h.Rroot, Rf, sizeof(Rf), cudaMemcpyHostToDevice, ctx->stream),
+                       "pose upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(ctx->pose->pose_set, ctx->pose->h.pose, sizeof(float) * nd,
+                                       cudaMemcpyDeviceToDevice, ctx->stream),
+                       "pose upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(ctx->pose->pose_set + kMaxDof, Rf, sizeof(Rf), cudaMemcpyHostToDevice,
+                                       ctx->stream),
                        "pose upload")))
         return s;
     return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+extern "C" lc_status lc_reset_pose(lc_ctx* ctx) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_reset_pose: no skeleton");
+    cudaSetDevice(ctx->device);
+    PoseState& S = *ctx->pose;
+    lc_status s;
+    if ((s = ctx->cuda(cudaMemcpyAsync(S.h.pose, S.pose_set, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice,
+                                       ctx->stream),
+                       "pose reset")) ||
+        (s = ctx->cuda(cudaMemcpyAsync(S.h.Rroot, S.pose_set + kMaxDof, sizeof(float) * 9, cudaMemcpyDeviceToDevice,
+                                       ctx->stream),
+                       "pose reset")))
+        return s;
+    return LC_OK;
 }
 
 void lc_ctx::enqueue_pose() {
     PoseState& S = *pose;
     const PoseDesc& P = S.h;
     cudaStream_t st = stream;
+    prof_pose.begin = prof_used;
     mark(LC_PH_POSE);
     cudaMemsetAsync(P.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemcpyAsync(P.pose_start, P.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
+    launch_pose_fk(S.d, st);
     launch_pose_skin(dC, hC, S.d, nullptr, 0, st);
     launch_visibility(dC, hC, st);
     launch_pose_blist(dC, S.d, st);
+    // step 0 linearises at the start pose, whose b_i the contour pass just
+    // decided on the same vertices; later steps re-decide them
     for (int g = 0; g < params.n_gn_pose; ++g) {
-        launch_pose_dirs(dC, hC, S.d, st);
-        launch_pose_rows(dC, hC, S.d, P.J, st);
+        if (g > 0) launch_pose_dirs(dC, hC, S.d, st);
+        launch_pose_system(dC, hC, S.d, P.J, P.n_dof, st);
         launch_pose_solve(S.d, g, 0, st);
     }
     launch_pose_dirs(dC, hC, S.d, st);
-    launch_pose_rows(dC, hC, S.d, P.J, st);
+    launch_pose_system(dC, hC, S.d, P.J, P.n_dof, st);
     launch_pose_solve(S.d, params.n_gn_pose, 1, st);
     // the skinned mesh becomes the rest geometry of the non-rigid stage
     launch_pose_skin(dC, hC, S.d, base_buf, 1, st);
     if (has_graph) launch_gather_nodes(base_buf, hC.node_vid, hC.n, (float4*)hC.node_g, st);
     mark_end();
+    prof_pose.end = prof_used;
 }
 
 extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
@@ -289,7 +335,7 @@ extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
         S.graph_n_gn = ctx->params.n_gn_pose;
     }
     if ((s = ctx->cuda(cudaGraphLaunch(S.gexec, ctx->stream), "graph launch"))) return s;
-    if ((s = ctx->accumulate_profile())) return s;
+    if ((s = ctx->accumulate_profile(ctx->prof_pose))) return s;
     // the visibility state now holds the pose stage's frame decisions
     // (z-buffer, visibility and B at the starting pose; b_i and uv at the final)
     ctx->has_vis = true;
@@ -332,11 +378,11 @@ extern "C" lc_status lc_eval_pose(lc_ctx* ctx, float* V_skinned, double* A, doub
     cudaStream_t st = ctx->stream;
     // contour set at the current pose, then the system at the current pose
     cudaMemcpyAsync(S.h.pose_start, S.h.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
+    launch_pose_fk(S.d, st);
     launch_pose_skin(ctx->dC, ctx->hC, S.d, nullptr, 0, st);
     launch_visibility(ctx->dC, ctx->hC, st);
     launch_pose_blist(ctx->dC, S.d, st);
-    launch_pose_dirs(ctx->dC, ctx->hC, S.d, st);
-    launch_pose_rows(ctx->dC, ctx->hC, S.d, S.h.J, st);
+    launch_pose_system(ctx->dC, ctx->hC, S.d, S.h.J, S.h.n_dof, st);
     launch_pose_solve(S.d, LC_MAX_GN, 2, st);
     if ((s = ctx->cuda(cudaGetLastError(), "pose eval"))) return s;
     ctx->has_vis = true;

@@ -7,12 +7,23 @@ namespace lc {
 
 constexpr int kMaxJoints = 64;
 constexpr int kMaxDof = 63;    // 6 root DOF + 3 per ball joint (up to 19 ball joints)
+constexpr int kSysItems = 64;  // residual items (joints / contour vertices) per row CTA
+constexpr int kSysThreads = 256;
+
+// kinematics of every joint at the current pose
+struct PoseFk {
+    float G[kMaxJoints][9];    // world rotation
+    float o[kMaxJoints][3];    // world position
+    float U[kMaxJoints][9];    // world Euler axes (x, y, z columns) of a DOF joint
+};
 
 struct PoseDesc {
-    int J, n_dof, max_rows;
+    int J, n_dof, n_levels;
     int has_j2d, has_j3d;
     float lam_2d, lam_3d, lam_sil, lam_prior;
     const int* parents;               // J
+    const int* level;                 // J: depth in the tree (root 0)
+    const unsigned short* pairs;      // (n_dof + 1)(n_dof + 2) / 2: a << 8 | b, column pairs a <= b of [J | F]
     const float4* rest;               // J rest joint positions
     const int* col;                   // J: first pose column of a ball joint, -1 otherwise
     const unsigned long long* anc;    // J: bit a set iff a is j or an ancestor of j
@@ -24,8 +35,8 @@ struct PoseDesc {
     float* pose;                      // n_dof ([0:3] unused on the device)
     float* pose_start;                // n_dof: the frame's start pose (angle prior)
     float* Rroot;                     // 9
-    float* F;                         // max_rows
-    float* Jm;                        // n_dof x max_rows, column-major
+    PoseFk* fk;                       // kinematics at the current pose
+    float* part;                      // row CTAs x pairs: FP32 partial pair sums
     int* blist;                       // N contour vertices
     int* bcount;
     double* hist;                     // 2 (LC_MAX_GN + 1): energy, step norm
@@ -36,10 +47,16 @@ struct PoseDesc {
 void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* out_base, int mode,
                       cudaStream_t st);
 void launch_pose_blist(const CapDesc* dC, const PoseDesc* dP, cudaStream_t st);
+// forward kinematics of the current pose into P.fk
+void launch_pose_fk(const PoseDesc* dP, cudaStream_t st);
 // re-skins the mesh into C.vw / C.uv and re-evaluates b_i of the contour set
 void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, cudaStream_t st);
-void launch_pose_rows(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, cudaStream_t st);
-// mode 0: solve and update, 1: energy only, 2: export A | g into expA
+// residual rows -> partial pair sums (P.part)
+cudaError_t pose_kernels_init(int n_dof);
+int pose_system_ctas(int J, int N);
+void launch_pose_system(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, int n_dof,
+                        cudaStream_t st);
+// mode 0: solve, update and the next kinematics; 1: energy only; 2: export A | g into expA
 void launch_pose_solve(const PoseDesc* dP, int slot, int mode, cudaStream_t st);
 
 }  // namespace lc

@@ -15,21 +15,17 @@
 //     root t -> I, Euler axis u of an ancestor-or-self joint j of b ->
 //     u x (P - o_j), with u_a = G_p e_x, u_b = G_p Rx e_y, u_c = G_p Rx Ry e_z.
 //
-// The dense Jacobian (rows x n_dof, FP32, column-major) is reduced to J^T J
-// and J^T F in FP32 by one CTA staging row chunks in shared memory, and the
-// normal equations are solved by an FP64 Cholesky factorisation in shared
-// memory (pivot <= 0 sets a status word) - no host round trip.
+// Per Gauss-Newton step: forward kinematics once (one CTA, joints of a tree
+// level in parallel) into a global table; skinning and b_i of the contour
+// set; the residual rows built in shared memory by a grid of CTAs, each
+// reducing its rows to FP32 partial sums of the pairs of [J | F] columns; one
+// CTA summing the partials in a fixed order into the FP64 normal equations,
+// factorising them by Cholesky (pivot <= 0 sets a status word), updating the
+// pose and computing the next forward kinematics - no host round trip.
 #include "lc_internal.cuh"
 #include "pose_internal.h"
 
 namespace lc {
-
-// forward kinematics of the whole skeleton into shared memory (thread 0)
-struct FkSmem {
-    float G[kMaxJoints][9];
-    float o[kMaxJoints][3];
-    float U[kMaxJoints][9];   // three world axes (rows) per DOF joint
-};
 
 __device__ __forceinline__ void mat3mul(const float* A, const float* B, float* C) {
 #pragma unroll
@@ -38,49 +34,73 @@ __device__ __forceinline__ void mat3mul(const float* A, const float* B, float* C
         for (int c = 0; c < 3; ++c) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
 }
 
-__device__ void forward_kinematics(const PoseDesc& P, FkSmem& fk) {
-    if (threadIdx.x != 0) return;
+// Forward kinematics of the whole skeleton at the current pose into fk, by
+// the calling CTA: thread j handles joint j, one tree level at a time (the
+// parent's frame is final before its children read it).  Every thread of
+// the CTA must call this (it synchronises).
+__device__ void forward_kinematics(const PoseDesc& P, PoseFk& fk) {
+    const int j = threadIdx.x;
     const float* pose = P.pose;
-    for (int j = 0; j < P.J; ++j) {
-        const int p = P.parents[j];
-        if (p < 0) {
+    for (int lvl = 0; lvl < P.n_levels; ++lvl) {
+        if (j < P.J && P.level[j] == lvl) {
+            const int p = P.parents[j];
+            if (p < 0) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) fk.G[j][q] = P.Rroot[q];
-            fk.o[j][0] = pose[3];
-            fk.o[j][1] = pose[4];
-            fk.o[j][2] = pose[5];
-            continue;
+                for (int q = 0; q < 9; ++q) fk.G[j][q] = P.Rroot[q];
+                fk.o[j][0] = pose[3];
+                fk.o[j][1] = pose[4];
+                fk.o[j][2] = pose[5];
+            } else {
+                const float4 rj = P.rest[j], rp = P.rest[p];
+                const float d[3] = {rj.x - rp.x, rj.y - rp.y, rj.z - rp.z};
+                float Gp[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) Gp[q] = fk.G[p][q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    fk.o[j][r] = fk.o[p][r] + Gp[3 * r] * d[0] + Gp[3 * r + 1] * d[1] + Gp[3 * r + 2] * d[2];
+                const int c = P.col[j];
+                if (c < 0) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) fk.G[j][q] = Gp[q];
+                } else {
+                    float sa, ca, sb, cb, sc, cc;
+                    sincosf(pose[c], &sa, &ca);
+                    sincosf(pose[c + 1], &sb, &cb);
+                    sincosf(pose[c + 2], &sc, &cc);
+                    const float Rx[9] = {1.f, 0.f, 0.f, 0.f, ca, -sa, 0.f, sa, ca};
+                    const float Ry[9] = {cb, 0.f, sb, 0.f, 1.f, 0.f, -sb, 0.f, cb};
+                    const float Rz[9] = {cc, -sc, 0.f, sc, cc, 0.f, 0.f, 0.f, 1.f};
+                    float GRx[9], GRxRy[9], G[9];
+                    mat3mul(Gp, Rx, GRx);
+                    mat3mul(GRx, Ry, GRxRy);
+                    mat3mul(GRxRy, Rz, G);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) fk.G[j][q] = G[q];
+                    // axes: G_p e_x, G_p Rx e_y, G_p Rx Ry e_z (columns)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        fk.U[j][r] = Gp[3 * r];
+                        fk.U[j][3 + r] = GRx[3 * r + 1];
+                        fk.U[j][6 + r] = GRxRy[3 * r + 2];
+                    }
+                }
+            }
         }
-        const float4 rj = P.rest[j], rp = P.rest[p];
-        const float d[3] = {rj.x - rp.x, rj.y - rp.y, rj.z - rp.z};
-        const float* Gp = fk.G[p];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) fk.o[j][r] = fk.o[p][r] + Gp[3 * r] * d[0] + Gp[3 * r + 1] * d[1] + Gp[3 * r + 2] * d[2];
-        const int c = P.col[j];
-        if (c < 0) {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) fk.G[j][q] = Gp[q];
-            continue;
-        }
-        float sa, ca, sb, cb, sc, cc;
-        sincosf(pose[c], &sa, &ca);
-        sincosf(pose[c + 1], &sb, &cb);
-        sincosf(pose[c + 2], &sc, &cc);
-        const float Rx[9] = {1.f, 0.f, 0.f, 0.f, ca, -sa, 0.f, sa, ca};
-        const float Ry[9] = {cb, 0.f, sb, 0.f, 1.f, 0.f, -sb, 0.f, cb};
-        const float Rz[9] = {cc, -sc, 0.f, sc, cc, 0.f, 0.f, 0.f, 1.f};
-        float GRx[9], GRxRy[9];
-        mat3mul(Gp, Rx, GRx);
-        mat3mul(GRx, Ry, GRxRy);
-        mat3mul(GRxRy, Rz, fk.G[j]);
-        // axes: G_p e_x, G_p Rx e_y, G_p Rx Ry e_z (columns)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            fk.U[j][r] = Gp[3 * r];
-            fk.U[j][3 + r] = GRx[3 * r + 1];
-            fk.U[j][6 + r] = GRxRy[3 * r + 2];
-        }
+        __syncthreads();
     }
+}
+
+// the global kinematics table -> shared memory (G and o; U when asked)
+__device__ __forceinline__ void load_fk(const PoseDesc& P, PoseFk& fk, bool axes) {
+    const int J = P.J;
+    const float* gG = &P.fk->G[0][0];
+    const float* go = &P.fk->o[0][0];
+    const float* gU = &P.fk->U[0][0];
+    for (int q = threadIdx.x; q < 9 * J; q += blockDim.x) (&fk.G[0][0])[q] = gG[q];
+    for (int q = threadIdx.x; q < 3 * J; q += blockDim.x) (&fk.o[0][0])[q] = go[q];
+    if (axes)
+        for (int q = threadIdx.x; q < 9 * J; q += blockDim.x) (&fk.U[0][0])[q] = gU[q];
 }
 
 __device__ __forceinline__ void cross3f(const float* a, const float* b, float* c) {
@@ -90,7 +110,7 @@ __device__ __forceinline__ void cross3f(const float* a, const float* b, float* c
 }
 
 // Adds w * coef . dP/dtheta (P riding on bone b) into row[0..n_dof).
-__device__ __forceinline__ void add_point_row(const PoseDesc& P, const FkSmem& fk, const float* pt, int b,
+__device__ __forceinline__ void add_point_row(const PoseDesc& P, const PoseFk& fk, const float* pt, int b,
                                               const float* coef, float w, float* row) {
     const float t[3] = {P.pose[3], P.pose[4], P.pose[5]};
     const float rel[3] = {pt[0] - t[0], pt[1] - t[1], pt[2] - t[2]};
@@ -151,10 +171,10 @@ __device__ __forceinline__ float4 dt_sample(const CapDesc& C, float u, float v, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) pose_skin_kernel(const CapDesc* __restrict__ caps, const PoseDesc* __restrict__ pd,
                                                         float4* __restrict__ out_base, int mode) {
-    __shared__ FkSmem fk;
+    __shared__ PoseFk fk;
     const CapDesc& C = caps[0];
     const PoseDesc& P = *pd;
-    forward_kinematics(P, fk);
+    load_fk(P, fk, false);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.N) return;
@@ -227,182 +247,161 @@ __global__ void __launch_bounds__(256) pose_dirs_kernel(const CapDesc* __restric
 }
 
 // ---------------------------------------------------------------------------
-// residual rows and dense Jacobian rows (column-major, ld = max_rows)
-// thread t < J: 2D rows of joint t; t < 2J: 3D rows; then one row per
-// contour vertex
+// forward kinematics of the current pose into the global table (one CTA)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) pose_rows_kernel(const CapDesc* __restrict__ caps, const PoseDesc* __restrict__ pd) {
-    __shared__ FkSmem fk;
-    const CapDesc& C = caps[0];
+__global__ void __launch_bounds__(64) pose_fk_kernel(const PoseDesc* __restrict__ pd) {
+    __shared__ PoseFk fk;
     const PoseDesc& P = *pd;
     forward_kinematics(P, fk);
-    __syncthreads();
-    const int J = P.J, nd = P.n_dof, ld = P.max_rows;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int q = threadIdx.x; q < (int)(sizeof(PoseFk) / sizeof(float)); q += blockDim.x)
+        (&P.fk->G[0][0])[q] = (&fk.G[0][0])[q];
+}
+
+// ---------------------------------------------------------------------------
+// residual rows and their FP32 pair sums.  Items: t < J the 2 rows of 2D
+// joint t, t < 2J the 3 rows of 3D joint t - J, then one row per contour
+// vertex; CTA c takes items [c kSysItems, (c + 1) kSysItems), builds their
+// rows [J | F] in shared memory (stride na | 1, odd: conflict-free) and
+// writes sum_rows a_r b_r for every column pair a <= b of [J | F].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pose_row_of(int t, int J) {
+    return t < J ? 2 * t : (t < 2 * J ? 2 * J + 3 * (t - J) : 5 * J + (t - 2 * J));
+}
+
+__global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc* __restrict__ caps,
+                                                                  const PoseDesc* __restrict__ pd) {
+    extern __shared__ float sR[];
+    __shared__ PoseFk fk;
+    const CapDesc& C = caps[0];
+    const PoseDesc& P = *pd;
+    const int J = P.J, nd = P.n_dof, na = nd + 1, stride = na | 1;
     const int nB = *P.bcount;
-    if (t >= 2 * J + nB) return;
-    float row[3][kMaxDof];
-    if (t < J) {
-        // 2D joint rows
-        const int j = t;
-        const float X = fk.o[j][0], Y = fk.o[j][1], Z = fk.o[j][2];
-        const float s2 = sqrtf(P.lam_2d);
-        const bool ok = P.has_j2d && Z > 1e-3f;
-        float r0 = 0.f, r1 = 0.f;
-        for (int c = 0; c < nd; ++c) row[0][c] = row[1][c] = 0.f;
-        if (ok) {
-            const float iz = 1.f / Z, fz = C.f * iz;
-            r0 = s2 * (fz * X + C.cx - P.j2d[j].x);
-            r1 = s2 * (fz * Y + C.cy - P.j2d[j].y);
-            const float cu[3] = {s2 * fz, 0.f, -s2 * fz * X * iz};
-            const float cv[3] = {0.f, s2 * fz, -s2 * fz * Y * iz};
-            add_point_row(P, fk, fk.o[j], j, cu, 1.f, row[0]);
-            add_point_row(P, fk, fk.o[j], j, cv, 1.f, row[1]);
-        }
-        P.F[2 * j] = r0;
-        P.F[2 * j + 1] = r1;
-        for (int c = 0; c < nd; ++c) {
-            P.Jm[(size_t)c * ld + 2 * j] = row[0][c];
-            P.Jm[(size_t)c * ld + 2 * j + 1] = row[1][c];
-        }
-    } else if (t < 2 * J) {
-        const int j = t - J;
-        const float s3 = P.has_j3d ? sqrtf(P.lam_3d) : 0.f;
-        for (int k = 0; k < 3; ++k) {
-            for (int c = 0; c < nd; ++c) row[k][c] = 0.f;
-            const float coef[3] = {k == 0 ? s3 : 0.f, k == 1 ? s3 : 0.f, k == 2 ? s3 : 0.f};
-            if (s3 > 0.f) add_point_row(P, fk, fk.o[j], j, coef, 1.f, row[k]);
-        }
-        const float4 p3 = P.j3d[j];
-        const float tgt[3] = {p3.x, p3.y, p3.z};
-        for (int k = 0; k < 3; ++k) {
-            const int r = 2 * J + 3 * j + k;
-            P.F[r] = s3 * (fk.o[j][k] - tgt[k]);
-            for (int c = 0; c < nd; ++c) P.Jm[(size_t)c * ld + r] = row[k][c];
-        }
-    } else {
-        const int i = P.blist[t - 2 * J];
-        const int r = 5 * J + (t - 2 * J);
-        const float4 v = P.tpl[i];
-        const int4 bi = P.skin_idx[i];
-        const float4 bw = P.skin_w[i];
-        const int bones[4] = {bi.x, bi.y, bi.z, bi.w};
-        const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
-        float Pt[4][3];
-        float X = 0.f, Y = 0.f, Z = 0.f;
+    const int nitems = 2 * J + nB;
+    const int t0 = blockIdx.x * kSysItems;
+    if (t0 >= nitems) return;                       // uniform over the CTA
+    const int t1 = min(nitems, t0 + kSysItems);
+    const int r0 = pose_row_of(t0, J), nr = pose_row_of(t1, J) - r0;
+    const int tid = threadIdx.x;
+    load_fk(P, fk, true);
+    for (int q = tid; q < nr * stride; q += kSysThreads) sR[q] = 0.f;
+    __syncthreads();
+    const int t = t0 + tid;
+    if (tid < kSysItems && t < t1) {
+        float* row0 = &sR[(pose_row_of(t, J) - r0) * stride];
+        if (t < J) {
+            // 2D joint rows
+            const int j = t;
+            const float X = fk.o[j][0], Y = fk.o[j][1], Z = fk.o[j][2];
+            const float s2 = sqrtf(P.lam_2d);
+            if (P.has_j2d && Z > 1e-3f) {
+                const float iz = 1.f / Z, fz = C.f * iz;
+                row0[nd] = s2 * (fz * X + C.cx - P.j2d[j].x);
+                row0[stride + nd] = s2 * (fz * Y + C.cy - P.j2d[j].y);
+                const float cu[3] = {s2 * fz, 0.f, -s2 * fz * X * iz};
+                const float cv[3] = {0.f, s2 * fz, -s2 * fz * Y * iz};
+                add_point_row(P, fk, fk.o[j], j, cu, 1.f, row0);
+                add_point_row(P, fk, fk.o[j], j, cv, 1.f, row0 + stride);
+            }
+        } else if (t < 2 * J) {
+            // 3D joint rows
+            const int j = t - J;
+            const float s3 = P.has_j3d ? sqrtf(P.lam_3d) : 0.f;
+            const float4 p3 = P.j3d[j];
+            const float tgt[3] = {p3.x, p3.y, p3.z};
+            for (int k = 0; k < 3; ++k) {
+                float* row = row0 + k * stride;
+                const float coef[3] = {k == 0 ? s3 : 0.f, k == 1 ? s3 : 0.f, k == 2 ? s3 : 0.f};
+                if (s3 > 0.f) add_point_row(P, fk, fk.o[j], j, coef, 1.f, row);
+                row[nd] = s3 * (fk.o[j][k] - tgt[k]);
+            }
+        } else {
+            // silhouette row of a contour vertex
+            const int i = P.blist[t - 2 * J];
+            const float4 v = P.tpl[i];
+            const int4 bi = P.skin_idx[i];
+            const float4 bw = P.skin_w[i];
+            const int bones[4] = {bi.x, bi.y, bi.z, bi.w};
+            const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
+            float Pt[4][3];
+            float X = 0.f, Y = 0.f, Z = 0.f;
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int b = bones[s];
-            const float4 rb = P.rest[b];
-            const float d0 = v.x - rb.x, d1 = v.y - rb.y, d2 = v.z - rb.z;
-            const float* G = fk.G[b];
-            Pt[s][0] = G[0] * d0 + G[1] * d1 + G[2] * d2 + fk.o[b][0];
-            Pt[s][1] = G[3] * d0 + G[4] * d1 + G[5] * d2 + fk.o[b][1];
-            Pt[s][2] = G[6] * d0 + G[7] * d1 + G[8] * d2 + fk.o[b][2];
-            X += ws[s] * Pt[s][0];
-            Y += ws[s] * Pt[s][1];
-            Z += ws[s] * Pt[s][2];
-        }
-        for (int c = 0; c < nd; ++c) row[0][c] = 0.f;
-        float res = 0.f;
-        const float2 uv = project_exact(C.f, C.cx, C.cy, X, Y, Z);
-        if (valid_depth(Z) && in_image(uv, C.W, C.H)) {
-            float gx, gy;
-            const float d = dt_sample(C, uv.x, uv.y, gx, gy).x;
-            const float ss = sqrtf(P.lam_sil / (float)max(nB, 1));
-            res = ss * d;
-            const float bs = (C.flags[i] & LC_BNEG_BIT) ? -ss : ss;
-            const float iz = 1.f / Z, fz = C.f * iz;
-            const float coef[3] = {bs * gx * fz, bs * gy * fz, -bs * fz * iz * (gx * X + gy * Y)};
+            for (int s = 0; s < 4; ++s) {
+                const int b = bones[s];
+                const float4 rb = P.rest[b];
+                const float d0 = v.x - rb.x, d1 = v.y - rb.y, d2 = v.z - rb.z;
+                const float* G = fk.G[b];
+                Pt[s][0] = G[0] * d0 + G[1] * d1 + G[2] * d2 + fk.o[b][0];
+                Pt[s][1] = G[3] * d0 + G[4] * d1 + G[5] * d2 + fk.o[b][1];
+                Pt[s][2] = G[6] * d0 + G[7] * d1 + G[8] * d2 + fk.o[b][2];
+                X += ws[s] * Pt[s][0];
+                Y += ws[s] * Pt[s][1];
+                Z += ws[s] * Pt[s][2];
+            }
+            const float2 uv = project_exact(C.f, C.cx, C.cy, X, Y, Z);
+            if (valid_depth(Z) && in_image(uv, C.W, C.H)) {
+                float gx, gy;
+                const float d = dt_sample(C, uv.x, uv.y, gx, gy).x;
+                const float ss = sqrtf(P.lam_sil / (float)max(nB, 1));
+                row0[nd] = ss * d;
+                const float bs = (C.flags[i] & LC_BNEG_BIT) ? -ss : ss;
+                const float iz = 1.f / Z, fz = C.f * iz;
+                const float coef[3] = {bs * gx * fz, bs * gy * fz, -bs * fz * iz * (gx * X + gy * Y)};
 #pragma unroll
-            for (int s = 0; s < 4; ++s) add_point_row(P, fk, Pt[s], bones[s], coef, ws[s], row[0]);
+                for (int s = 0; s < 4; ++s) add_point_row(P, fk, Pt[s], bones[s], coef, ws[s], row0);
+            }
         }
-        P.F[r] = res;
-        for (int c = 0; c < nd; ++c) P.Jm[(size_t)c * ld + r] = row[0][c];
+    }
+    __syncthreads();
+    const int npairs = na * (na + 1) / 2;
+    float* out = P.part + (size_t)blockIdx.x * npairs;
+    for (int p = tid; p < npairs; p += kSysThreads) {
+        const unsigned pr = P.pairs[p];
+        const int a = (int)(pr >> 8), b = (int)(pr & 255u);
+        float acc = 0.f;
+        for (int r = 0; r < nr; ++r) acc += sR[r * stride + a] * sR[r * stride + b];
+        out[p] = acc;
     }
 }
 
 // ---------------------------------------------------------------------------
-// normal equations + FP64 Cholesky + update (one CTA)
+// normal equations + FP64 Cholesky + update + next kinematics (one CTA)
+// mode 0: solve and update, 1: energy only, 2: export A | g into expA
 // ---------------------------------------------------------------------------
 constexpr int kSolveThreads = 1024;
-constexpr int kChunkRows = 32;
 
 __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDesc* __restrict__ pd, int slot,
                                                                   int mode) {
-    __shared__ float sJ[(kMaxDof + 1) * kChunkRows];
     __shared__ double A[kMaxDof][kMaxDof + 1];
-    __shared__ double x[kMaxDof];
-    __shared__ unsigned char pa[(kMaxDof + 1) * (kMaxDof + 2) / 2], pb[(kMaxDof + 1) * (kMaxDof + 2) / 2];
+    __shared__ double invd[kMaxDof];
+    __shared__ double y[kMaxDof];
+    __shared__ PoseFk fk;
     __shared__ float s_ftf;
-    __shared__ double s_inv;
     __shared__ int s_bad;
     const PoseDesc& P = *pd;
-    const int nd = P.n_dof, ld = P.max_rows;
-    const int nrows = 5 * P.J + *P.bcount;
-    const int tid = threadIdx.x;
-    const int na = nd + 1;                          // augmented with F
+    const int nd = P.n_dof, na = nd + 1;
     const int npairs = na * (na + 1) / 2;
-    if (tid == 0) {
-        int p = 0;
-        for (int a = 0; a < na; ++a)
-            for (int b = a; b < na; ++b) {
-                pa[p] = (unsigned char)a;
-                pb[p] = (unsigned char)b;
-                ++p;
-            }
-        s_bad = 0;
-    }
-    __syncthreads();
-    // pairs (a <= b) of the augmented matrix [J | F]: FP32 dot products over
-    // the rows, in a fixed order
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-    for (int r0 = 0; r0 < nrows; r0 += kChunkRows) {
-        const int rn = min(kChunkRows, nrows - r0);
-        for (int q = tid; q < na * kChunkRows; q += kSolveThreads) {
-            const int c = q / kChunkRows, r = q % kChunkRows;
-            float v = 0.f;
-            if (r < rn) v = c < nd ? P.Jm[(size_t)c * ld + r0 + r] : P.F[r0 + r];
-            sJ[c * kChunkRows + r] = v;
-        }
-        __syncthreads();
-        if (tid < npairs) {
-            const float* ca = &sJ[pa[tid] * kChunkRows];
-            const float* cb = &sJ[pb[tid] * kChunkRows];
-            for (int r = 0; r < rn; ++r) acc0 += ca[r] * cb[r];
-        }
-        if (tid + kSolveThreads < npairs) {
-            const float* ca = &sJ[pa[tid + kSolveThreads] * kChunkRows];
-            const float* cb = &sJ[pb[tid + kSolveThreads] * kChunkRows];
-            for (int r = 0; r < rn; ++r) acc1 += ca[r] * cb[r];
-        }
-        if (tid + 2 * kSolveThreads < npairs) {
-            const float* ca = &sJ[pa[tid + 2 * kSolveThreads] * kChunkRows];
-            const float* cb = &sJ[pb[tid + 2 * kSolveThreads] * kChunkRows];
-            for (int r = 0; r < rn; ++r) acc2 += ca[r] * cb[r];
-        }
-        __syncthreads();
-    }
-    // scatter into the FP64 system: A (nd x nd) and g = -J^T F in column nd
-    auto put = [&](int p, float v) {
-        if (p >= npairs) return;
-        const int a = pa[p], b = pb[p];
+    const int nact = (2 * P.J + *P.bcount + kSysItems - 1) / kSysItems;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    // partial pair sums of the row CTAs, added in CTA order
+    for (int p = tid; p < npairs; p += kSolveThreads) {
+        float v = 0.f;
+        for (int c = 0; c < nact; ++c) v += P.part[(size_t)c * npairs + p];
+        const unsigned pr = P.pairs[p];
+        const int a = (int)(pr >> 8), b = (int)(pr & 255u);
         if (b < nd) {
             A[a][b] = (double)v;
             A[b][a] = (double)v;
         } else if (a < nd) {
-            A[a][nd] = -(double)v;
+            A[a][nd] = -(double)v;          // g = -J^T F
         } else {
-            s_ftf = v;   // F^T F
+            s_ftf = v;                      // F^T F
         }
-    };
-    put(tid, acc0);
-    put(tid + kSolveThreads, acc1);
-    put(tid + 2 * kSolveThreads, acc2);
+    }
     __syncthreads();
     // angle prior: lprior (theta - theta_start) on the Euler DOF
-    double prior_e = 0.0;
     if (tid == 0) {
+        double prior_e = 0.0;
         for (int c = 6; c < nd; ++c) {
             const double dv = (double)P.pose[c] - (double)P.pose_start[c];
             A[c][c] += (double)P.lam_prior;
@@ -417,41 +416,48 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         for (int q = tid; q < nd * (nd + 1); q += kSolveThreads) P.expA[q] = A[q / (nd + 1)][q % (nd + 1)];
         return;
     }
-    // Cholesky, lower triangle in place (FP64)
+    // Square-root-free Cholesky A = L D L^T (FP64) of the matrix augmented
+    // with g: after pivot k the trailing block holds the Schur complement and
+    // column nd the forward-substituted right-hand side.  GB300's FP64 units
+    // have a long latency, so the per-pivot chain is kept short: 1 / d_k from
+    // an FP32 seed refined by two Newton steps y <- y (2 - d y), and one
+    // fused update per entry.
     for (int k = 0; k < nd; ++k) {
         if (tid == 0) {
             const double d = A[k][k];
             if (!(d > 0.0)) s_bad = 1;
-            A[k][k] = d > 0.0 ? sqrt(d) : 1.0;
-            s_inv = 1.0 / A[k][k];
+            double r;
+            const float fd = (float)d;
+            if (fd > 1e-30f && fd < 1e30f) {
+                r = (double)(1.0f / fd);
+                r = r * fma(-d, r, 2.0);
+                r = r * fma(-d, r, 2.0);
+            } else {
+                r = d > 0.0 ? 1.0 / d : 0.0;
+            }
+            invd[k] = r;
         }
         __syncthreads();
-        const double inv = s_inv;
-        for (int i = k + 1 + tid; i < nd; i += kSolveThreads) A[i][k] *= inv;
-        __syncthreads();
+        const double dinv = invd[k];
         const int m = nd - k - 1;
-        for (int q = tid; q < m * m; q += kSolveThreads) {
-            const int i = k + 1 + q / m, j = k + 1 + q % m;
-            if (j <= i) A[i][j] -= A[i][k] * A[j][k];
+        // entries (i, j), k < j <= i < nd, and (i, nd), k < i < nd
+        for (int q = tid; q < m * (m + 1); q += kSolveThreads) {
+            const int i = k + 1 + q / (m + 1), jj = q % (m + 1);
+            const int j = jj < m ? k + 1 + jj : nd;
+            if (j <= i || j == nd) {
+                const double w = (j < nd ? A[j][k] : A[k][nd]) * dinv;
+                A[i][j] = fma(-A[i][k], w, A[i][j]);
+            }
         }
         __syncthreads();
     }
-    // forward / back substitution by one warp
+    // x = L^-T D^-1 y, column by column in one warp (L_ik = A_ik / d_k)
     if (tid < 32) {
-        for (int i = 0; i < nd; ++i) {
-            double s = 0.0;
-            for (int j = tid; j < i; j += 32) s += A[i][j] * x[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (tid == 0) x[i] = (A[i][nd] - s) / A[i][i];
-            __syncwarp();
-        }
-        for (int i = nd - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int j = i + 1 + tid; j < nd; j += 32) s += A[j][i] * x[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (tid == 0) x[i] = (x[i] - s) / A[i][i];
+        for (int i = tid; i < nd; i += 32) y[i] = A[i][nd] * invd[i];
+        __syncwarp();
+        for (int k = nd - 1; k >= 0; --k) {
+            const double xk = y[k];
+            for (int i = tid; i < k; i += 32) y[i] = fma(-A[k][i] * invd[i], xk, y[i]);
             __syncwarp();
         }
     }
@@ -460,32 +466,38 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         if (s_bad) {
             *P.status = 1;
             P.hist[2 * slot + 1] = 0.0;
-            return;
-        }
-        double n2 = 0.0;
-        for (int c = 0; c < nd; ++c) n2 += x[c] * x[c];
-        P.hist[2 * slot + 1] = sqrt(n2);
-        for (int c = 3; c < nd; ++c) P.pose[c] += (float)x[c];
-        // R <- Exp(d_omega) R (Rodrigues, FP32)
-        const float wx = (float)x[0], wy = (float)x[1], wz = (float)x[2];
-        const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
-        float Af, Bf;
-        if (th < 1e-4f) {
-            Af = 1.f - th2 / 6.f;
-            Bf = 0.5f - th2 / 24.f;
         } else {
-            const float sh = sinf(0.5f * th);
-            Af = sinf(th) / th;
-            Bf = 2.f * sh * sh / th2;
+            double n2 = 0.0;
+            for (int c = 0; c < nd; ++c) n2 += y[c] * y[c];
+            P.hist[2 * slot + 1] = sqrt(n2);
+            for (int c = 3; c < nd; ++c) P.pose[c] += (float)y[c];
+            // R <- Exp(d_omega) R (Rodrigues, FP32)
+            const float wx = (float)y[0], wy = (float)y[1], wz = (float)y[2];
+            const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
+            float Af, Bf;
+            if (th < 1e-4f) {
+                Af = 1.f - th2 / 6.f;
+                Bf = 0.5f - th2 / 24.f;
+            } else {
+                const float sh = sinf(0.5f * th);
+                Af = sinf(th) / th;
+                Bf = 2.f * sh * sh / th2;
+            }
+            const float E[9] = {1.f - Bf * (wy * wy + wz * wz), -Af * wz + Bf * wx * wy, Af * wy + Bf * wx * wz,
+                                Af * wz + Bf * wx * wy, 1.f - Bf * (wx * wx + wz * wz), -Af * wx + Bf * wy * wz,
+                                -Af * wy + Bf * wx * wz, Af * wx + Bf * wy * wz, 1.f - Bf * (wx * wx + wy * wy)};
+            float R[9], Rn[9];
+            for (int q = 0; q < 9; ++q) R[q] = P.Rroot[q];
+            mat3mul(E, R, Rn);
+            for (int q = 0; q < 9; ++q) P.Rroot[q] = Rn[q];
         }
-        const float E[9] = {1.f - Bf * (wy * wy + wz * wz), -Af * wz + Bf * wx * wy, Af * wy + Bf * wx * wz,
-                            Af * wz + Bf * wx * wy, 1.f - Bf * (wx * wx + wz * wz), -Af * wx + Bf * wy * wz,
-                            -Af * wy + Bf * wx * wz, Af * wx + Bf * wy * wz, 1.f - Bf * (wx * wx + wy * wy)};
-        float R[9], Rn[9];
-        for (int q = 0; q < 9; ++q) R[q] = P.Rroot[q];
-        mat3mul(E, R, Rn);
-        for (int q = 0; q < 9; ++q) P.Rroot[q] = Rn[q];
     }
+    __threadfence_block();
+    __syncthreads();
+    // kinematics of the new pose for the next step's kernels
+    forward_kinematics(P, fk);
+    for (int q = tid; q < (int)(sizeof(PoseFk) / sizeof(float)); q += kSolveThreads)
+        (&P.fk->G[0][0])[q] = (&fk.G[0][0])[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -493,6 +505,7 @@ void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, 
                       cudaStream_t st) {
     pose_skin_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP, out_base, mode);
 }
+void launch_pose_fk(const PoseDesc* dP, cudaStream_t st) { pose_fk_kernel<<<1, 64, 0, st>>>(dP); }
 void launch_pose_blist(const CapDesc* dC, const PoseDesc* dP, cudaStream_t st) {
     pose_blist_kernel<<<1, 1024, 0, st>>>(dC, dP);
 }
@@ -500,9 +513,15 @@ void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, 
     pose_skin_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP, nullptr, 0);
     pose_dirs_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP);
 }
-void launch_pose_rows(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, cudaStream_t st) {
-    const int maxt = 2 * J + hC.N;
-    pose_rows_kernel<<<(maxt + 255) / 256, 256, 0, st>>>(dC, dP);
+size_t pose_system_smem(int n_dof) { return sizeof(float) * 3 * kSysItems * ((n_dof + 1) | 1); }
+cudaError_t pose_kernels_init(int n_dof) {
+    return cudaFuncSetAttribute(pose_system_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pose_system_smem(n_dof));
+}
+int pose_system_ctas(int J, int N) { return (2 * J + N + kSysItems - 1) / kSysItems; }
+void launch_pose_system(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, int n_dof,
+                        cudaStream_t st) {
+    pose_system_kernel<<<pose_system_ctas(J, hC.N), kSysThreads, pose_system_smem(n_dof), st>>>(dC, dP);
 }
 void launch_pose_solve(const PoseDesc* dP, int slot, int mode, cudaStream_t st) {
     pose_solve_kernel<<<1, kSolveThreads, 0, st>>>(dP, slot, mode);

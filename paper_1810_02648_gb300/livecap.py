@@ -68,6 +68,7 @@ _SIGS = {
     "lc_solve_linear": [_P, _P, ctypes.POINTER(ctypes.c_int)],
     "lc_upload_skeleton": [_P, ctypes.c_int, _P, _P, _P, _P, _P],
     "lc_set_pose": [_P, _P],
+    "lc_reset_pose": [_P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
@@ -314,6 +315,10 @@ class Context:
     def set_pose(self, pose):
         pose = _arr(pose, np.float32)
         self._check(self._lib.lc_set_pose(self.h, _ptr(pose)))
+
+    def reset_pose(self):
+        """Restart from the pose last given to set_pose (device-side, no sync)."""
+        self._check(self._lib.lc_reset_pose(self.h))
 
     def eval_pose(self) -> dict:
         nd = self.n_dof
