@@ -118,8 +118,8 @@ def _vis_case(scene, params_seed, tag):
         Rr, tr = R.astype(np.float64), t.astype(np.float64)
     vref = onr.warp(P, Rr, tr)
     dv = np.abs(lin["v"] - vref).max()
-    report(f"vis_{tag}", n_vis=int((vis["flags"] & 1).sum()), n_B=int((vis["flags"] & 4).sum()),
-           n_bneg=int((vis["flags"] & 8).sum()), warp_maxdiff=dv)
+    report(f"vis_{tag}", n_vis=int(((vis["flags"] & 1) != 0).sum()), n_B=int(((vis["flags"] & 4) != 0).sum()),
+           n_bneg=int(((vis["flags"] & 8) != 0).sum()), warp_maxdiff=dv)
     if params_seed is None:
         assert np.array_equal(lin["v"], P.base.astype(np.float32))
     assert dv <= 4e-6 * np.abs(vref).max()
