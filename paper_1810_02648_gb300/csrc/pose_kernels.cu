@@ -367,13 +367,22 @@ __global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc*
 // normal equations + FP64 Cholesky + update + next kinematics (one CTA)
 // mode 0: solve and update, 1: energy only, 2: export A | g into expA
 // ---------------------------------------------------------------------------
-constexpr int kSolveThreads = 1024;
+constexpr int kSolveThreads = 512;
+
+// FP64 sum over a warp (lane 0 holds the result), fixed tree order
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDesc* __restrict__ pd, int slot,
                                                                   int mode) {
     __shared__ double A[kMaxDof][kMaxDof + 1];
     __shared__ double invd[kMaxDof];
+    __shared__ double w[kMaxDof + 1];
     __shared__ double y[kMaxDof];
+    __shared__ double prior_t[kMaxDof];
     __shared__ PoseFk fk;
     __shared__ float s_ftf;
     __shared__ int s_bad;
@@ -399,18 +408,24 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         }
     }
     __syncthreads();
-    // angle prior: lprior (theta - theta_start) on the Euler DOF
-    if (tid == 0) {
-        double prior_e = 0.0;
-        for (int c = 6; c < nd; ++c) {
-            const double dv = (double)P.pose[c] - (double)P.pose_start[c];
-            A[c][c] += (double)P.lam_prior;
-            A[c][nd] -= (double)P.lam_prior * dv;
-            prior_e += (double)P.lam_prior * dv * dv;
+    // angle prior lprior (theta - theta_start) on the Euler DOF, one DOF per thread
+    if (tid < nd) {
+        double e = 0.0;
+        if (tid >= 6) {
+            const double dv = (double)P.pose[tid] - (double)P.pose_start[tid];
+            A[tid][tid] += (double)P.lam_prior;
+            A[tid][nd] -= (double)P.lam_prior * dv;
+            e = (double)P.lam_prior * dv * dv;
         }
-        P.hist[2 * slot] = (double)s_ftf + prior_e;
+        prior_t[tid] = e;
     }
     __syncthreads();
+    if (tid < 32) {
+        double e = 0.0;
+        for (int c = tid; c < nd; c += 32) e += prior_t[c];
+        e = warp_sum_f64(e);
+        if (tid == 0) P.hist[2 * slot] = (double)s_ftf + e;
+    }
     if (mode == 1) return;
     if (mode == 2) {
         for (int q = tid; q < nd * (nd + 1); q += kSolveThreads) P.expA[q] = A[q / (nd + 1)][q % (nd + 1)];
@@ -418,10 +433,11 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     }
     // Square-root-free Cholesky A = L D L^T (FP64) of the matrix augmented
     // with g: after pivot k the trailing block holds the Schur complement and
-    // column nd the forward-substituted right-hand side.  GB300's FP64 units
-    // have a long latency, so the per-pivot chain is kept short: 1 / d_k from
-    // an FP32 seed refined by two Newton steps y <- y (2 - d y), and one
-    // fused update per entry.
+    // column nd the forward-substituted right-hand side.  GB300's FP64 pipe
+    // has a long latency and a low rate per SM, so per pivot: 1 / d_k from an
+    // FP32 seed refined by two Newton steps y <- y (2 - d y) (no division),
+    // the pivot row scaled once (w_j = A_jk / d_k), then one FMA per entry
+    // of the trailing lower triangle and column nd.
     for (int k = 0; k < nd; ++k) {
         if (tid == 0) {
             const double d = A[k][k];
@@ -438,15 +454,18 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
             invd[k] = r;
         }
         __syncthreads();
-        const double dinv = invd[k];
         const int m = nd - k - 1;
+        if (tid <= m) {
+            const int j = tid < m ? k + 1 + tid : nd;
+            w[tid] = (j < nd ? A[j][k] : A[k][nd]) * invd[k];
+        }
+        __syncthreads();
         // entries (i, j), k < j <= i < nd, and (i, nd), k < i < nd
         for (int q = tid; q < m * (m + 1); q += kSolveThreads) {
-            const int i = k + 1 + q / (m + 1), jj = q % (m + 1);
-            const int j = jj < m ? k + 1 + jj : nd;
-            if (j <= i || j == nd) {
-                const double w = (j < nd ? A[j][k] : A[k][nd]) * dinv;
-                A[i][j] = fma(-A[i][k], w, A[i][j]);
+            const int ii = q / (m + 1), jj = q - ii * (m + 1);
+            if (jj <= ii || jj == m) {
+                const int i = k + 1 + ii, j = jj < m ? k + 1 + jj : nd;
+                A[i][j] = fma(-A[i][k], w[jj], A[i][j]);
             }
         }
         __syncthreads();
@@ -460,36 +479,36 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
             for (int i = tid; i < k; i += 32) y[i] = fma(-A[k][i] * invd[i], xk, y[i]);
             __syncwarp();
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (s_bad) {
-            *P.status = 1;
-            P.hist[2 * slot + 1] = 0.0;
-        } else {
-            double n2 = 0.0;
-            for (int c = 0; c < nd; ++c) n2 += y[c] * y[c];
-            P.hist[2 * slot + 1] = sqrt(n2);
-            for (int c = 3; c < nd; ++c) P.pose[c] += (float)y[c];
-            // R <- Exp(d_omega) R (Rodrigues, FP32)
-            const float wx = (float)y[0], wy = (float)y[1], wz = (float)y[2];
-            const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
-            float Af, Bf;
-            if (th < 1e-4f) {
-                Af = 1.f - th2 / 6.f;
-                Bf = 0.5f - th2 / 24.f;
+        double n2 = 0.0;
+        for (int c = tid; c < nd; c += 32) n2 += y[c] * y[c];
+        n2 = warp_sum_f64(n2);
+        if (tid == 0) {
+            if (s_bad) {
+                *P.status = 1;
+                P.hist[2 * slot + 1] = 0.0;
             } else {
-                const float sh = sinf(0.5f * th);
-                Af = sinf(th) / th;
-                Bf = 2.f * sh * sh / th2;
+                P.hist[2 * slot + 1] = sqrt(n2);
+                for (int c = 3; c < nd; ++c) P.pose[c] += (float)y[c];
+                // R <- Exp(d_omega) R (Rodrigues, FP32)
+                const float wx = (float)y[0], wy = (float)y[1], wz = (float)y[2];
+                const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
+                float Af, Bf;
+                if (th < 1e-4f) {
+                    Af = 1.f - th2 / 6.f;
+                    Bf = 0.5f - th2 / 24.f;
+                } else {
+                    const float sh = sinf(0.5f * th);
+                    Af = sinf(th) / th;
+                    Bf = 2.f * sh * sh / th2;
+                }
+                const float E[9] = {1.f - Bf * (wy * wy + wz * wz), -Af * wz + Bf * wx * wy, Af * wy + Bf * wx * wz,
+                                    Af * wz + Bf * wx * wy, 1.f - Bf * (wx * wx + wz * wz), -Af * wx + Bf * wy * wz,
+                                    -Af * wy + Bf * wx * wz, Af * wx + Bf * wy * wz, 1.f - Bf * (wx * wx + wy * wy)};
+                float R[9], Rn[9];
+                for (int q = 0; q < 9; ++q) R[q] = P.Rroot[q];
+                mat3mul(E, R, Rn);
+                for (int q = 0; q < 9; ++q) P.Rroot[q] = Rn[q];
             }
-            const float E[9] = {1.f - Bf * (wy * wy + wz * wz), -Af * wz + Bf * wx * wy, Af * wy + Bf * wx * wz,
-                                Af * wz + Bf * wx * wy, 1.f - Bf * (wx * wx + wz * wz), -Af * wx + Bf * wy * wz,
-                                -Af * wy + Bf * wx * wz, Af * wx + Bf * wy * wz, 1.f - Bf * (wx * wx + wy * wy)};
-            float R[9], Rn[9];
-            for (int q = 0; q < 9; ++q) R[q] = P.Rroot[q];
-            mat3mul(E, R, Rn);
-            for (int q = 0; q < 9; ++q) P.Rroot[q] = Rn[q];
         }
     }
     __threadfence_block();
