@@ -93,48 +93,82 @@ __device__ __forceinline__ bool owns(long long ex, long long ey) { return ey < 0
 __device__ __forceinline__ long long ceil256(long long a) { return a >= 0 ? (a + 255) / 256 : -((-a) / 256); }
 __device__ __forceinline__ long long floor256(long long a) { return a >= 0 ? a / 256 : -((-a + 255) / 256); }
 
+// Triangle setup shared by a warp: each thread sets up one triangle, then
+// the warp rasterises its 32 triangles one after the other, the lanes taking
+// the pixels of the bounding box in turn (a warp's time is the sum of its
+// triangles' box areas / 32 instead of the largest box).
+struct TriSetup {
+    long long ax, ay, bx, by, qx, qy;
+    int px0, py0, w, npix;   // box origin, width, pixel count (0: nothing to draw)
+    float za, zb, zc, farea;
+    int sg, own, t, pad;
+};
+
 __global__ void __launch_bounds__(kTriTile) raster_kernel(const CapDesc* __restrict__ caps,
                                                            const WorkItem* __restrict__ items) {
+    __shared__ TriSetup su[kTriTile];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     const int t = tile * kTriTile + threadIdx.x;
-    if (t >= C.F) return;
-    const int4 tri = C.tris[t];
-    long long ax, ay, bx, by, qx, qy;
-    if (!vertex_snap(C, tri.x, ax, ay) || !vertex_snap(C, tri.y, bx, by) || !vertex_snap(C, tri.z, qx, qy))
-        return;
-    const long long area = (bx - ax) * (qy - ay) - (by - ay) * (qx - ax);
-    if (area == 0) return;
-    const long long sg = area > 0 ? 1 : -1;
-    long long px0 = ceil256(min(ax, min(bx, qx))), px1 = floor256(max(ax, max(bx, qx)));
-    long long py0 = ceil256(min(ay, min(by, qy))), py1 = floor256(max(ay, max(by, qy)));
-    px0 = max(px0, 0LL);
-    py0 = max(py0, 0LL);
-    px1 = min(px1, (long long)C.W - 1);
-    py1 = min(py1, (long long)C.H - 1);
-    if (px0 > px1 || py0 > py1) return;
-    const bool oA = owns(sg * (qx - bx), sg * (qy - by));
-    const bool oB = owns(sg * (ax - qx), sg * (ay - qy));
-    const bool oC = owns(sg * (bx - ax), sg * (by - ay));
-    const float za = C.vw[tri.x].z, zb = C.vw[tri.y].z, zc = C.vw[tri.z].z;
-    const float farea = (float)(sg * area);
-    for (long long py = py0; py <= py1; ++py) {
-        const long long Py = py * 256;
-        for (long long px = px0; px <= px1; ++px) {
-            const long long Px = px * 256;
+    TriSetup& S = su[threadIdx.x];
+    S.npix = 0;
+    if (t < C.F) {
+        const int4 tri = C.tris[t];
+        long long ax, ay, bx, by, qx, qy;
+        if (vertex_snap(C, tri.x, ax, ay) && vertex_snap(C, tri.y, bx, by) && vertex_snap(C, tri.z, qx, qy)) {
+            const long long area = (bx - ax) * (qy - ay) - (by - ay) * (qx - ax);
+            if (area != 0) {
+                const long long sg = area > 0 ? 1 : -1;
+                long long px0 = ceil256(min(ax, min(bx, qx))), px1 = floor256(max(ax, max(bx, qx)));
+                long long py0 = ceil256(min(ay, min(by, qy))), py1 = floor256(max(ay, max(by, qy)));
+                px0 = max(px0, 0LL);
+                py0 = max(py0, 0LL);
+                px1 = min(px1, (long long)C.W - 1);
+                py1 = min(py1, (long long)C.H - 1);
+                if (px0 <= px1 && py0 <= py1) {
+                    S.ax = ax; S.ay = ay; S.bx = bx; S.by = by; S.qx = qx; S.qy = qy;
+                    S.px0 = (int)px0;
+                    S.py0 = (int)py0;
+                    S.w = (int)(px1 - px0 + 1);
+                    S.npix = S.w * (int)(py1 - py0 + 1);
+                    S.own = (owns(sg * (qx - bx), sg * (qy - by)) ? 1 : 0) | (owns(sg * (ax - qx), sg * (ay - qy)) ? 2 : 0) |
+                            (owns(sg * (bx - ax), sg * (by - ay)) ? 4 : 0);
+                    S.za = C.vw[tri.x].z;
+                    S.zb = C.vw[tri.y].z;
+                    S.zc = C.vw[tri.z].z;
+                    S.farea = (float)(sg * area);
+                    S.sg = (int)sg;
+                    S.t = t;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    for (int src = 0; src < 32; ++src) {
+        const TriSetup& T = su[wbase + src];
+        const int npix = T.npix;
+        if (npix == 0) continue;
+        const long long ax = T.ax, ay = T.ay, bx = T.bx, by = T.by, qx = T.qx, qy = T.qy;
+        const long long sg = T.sg;
+        const bool oA = T.own & 1, oB = T.own & 2, oC = T.own & 4;
+        for (int q = lane; q < npix; q += 32) {
+            const int ry = q / T.w;
+            const long long px = T.px0 + (q - ry * T.w), py = T.py0 + ry;
+            const long long Px = px * 256, Py = py * 256;
             const long long wA = sg * ((qx - bx) * (Py - by) - (qy - by) * (Px - bx));
             const long long wB = sg * ((ax - qx) * (Py - qy) - (ay - qy) * (Px - qx));
             const long long wC = sg * ((bx - ax) * (Py - ay) - (by - ay) * (Px - ax));
             if (wA < 0 || wB < 0 || wC < 0) continue;
             if ((wA == 0 && !oA) || (wB == 0 && !oB) || (wC == 0 && !oC)) continue;
-            const float b0 = xdiv(__ll2float_rn(wA), farea);
-            const float b1 = xdiv(__ll2float_rn(wB), farea);
-            const float b2 = xdiv(__ll2float_rn(wC), farea);
-            const float s01 = xadd(xdiv(b0, za), xdiv(b1, zb));
-            const float depth = xdiv(1.0f, xadd(s01, xdiv(b2, zc)));
+            const float b0 = xdiv(__ll2float_rn(wA), T.farea);
+            const float b1 = xdiv(__ll2float_rn(wB), T.farea);
+            const float b2 = xdiv(__ll2float_rn(wC), T.farea);
+            const float s01 = xadd(xdiv(b0, T.za), xdiv(b1, T.zb));
+            const float depth = xdiv(1.0f, xadd(s01, xdiv(b2, T.zc)));
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned)t;
+                ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned)T.t;
             atomicMin(&C.zbuf[py * C.W + px], key);
         }
     }
