@@ -254,6 +254,47 @@ lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
  * pointers are skipped.  Synchronises. */
 lc_status lc_eval_pose(lc_ctx *ctx, float *V_skinned, double *A, double *g, double *energy);
 
+/* ---- batches: many captures per launch (Sec. 4 solver, batched) ---------- */
+
+/* A batch solves the non-rigid stage of several contexts together: one
+ * launch per phase for all captures (their work lists concatenated), the
+ * whole Gauss-Newton / PCG loop captured as one CUDA graph on the batch's own
+ * stream.  Every member keeps its own buffers and reductions, so each
+ * capture's result equals its single-context lc_solve_nonrigid with the same
+ * PCG kernel and cluster size.  Members must be on one device, fully set up
+ * (template, graph, camera, frame) and agree in n_gn and n_pcg.  Frames and
+ * node parameters may change between solves (a member whose buffers were
+ * reallocated makes the next solve rebuild the plan).  The pose stage is not
+ * batched: run lc_solve_pose per context first. */
+typedef struct lc_batch lc_batch;
+
+/* PCG strategy of a batch: */
+#define LC_BATCH_PCG_AUTO 0           /* each capture as on its own (smallest cluster that fits) */
+#define LC_BATCH_PCG_CLUSTER8 1       /* 8-CTA clusters where they fit, else per-iteration kernels */
+#define LC_BATCH_PCG_CLUSTER16 2      /* 16-CTA clusters where they fit, else per-iteration kernels */
+#define LC_BATCH_PCG_PER_ITERATION 3  /* per-iteration kernels for every capture */
+
+/* ctxs: count >= 1 context handles (the caller keeps ownership; they must
+ * outlive the batch).  LC_ERR_STATE if a member is not ready, LC_ERR_ARG if
+ * they differ in device, n_gn or n_pcg (message in the first context). */
+lc_status lc_batch_create(lc_batch **out, lc_ctx *const *ctxs, int count);
+lc_status lc_batch_destroy(lc_batch *batch);
+const char *lc_batch_last_error(const lc_batch *batch);
+/* Choose the PCG strategy (LC_BATCH_PCG_*); rebuilds the work lists.
+ * Synchronises. */
+lc_status lc_batch_set_pcg_mode(lc_batch *batch, int mode);
+/* One non-rigid solve of every member (from the identity deformation when
+ * from_identity != 0, else from each member's current node parameters).
+ * The solve waits for work already enqueued on the members' streams, and
+ * their later calls wait for the solve.  Enqueue only when stats is null;
+ * else synchronises and fills stats[i] for member i (caller order). */
+lc_status lc_batch_solve(lc_batch *batch, int from_identity, lc_solve_stats *stats);
+/* Autotuner: times `reps` solves (from the identity) under each PCG strategy
+ * on the members' current frames, keeps the fastest and returns it in
+ * *mode_out; ms_out (nullable, 4 entries indexed by LC_BATCH_PCG_*) receives
+ * the mean milliseconds per solve of each.  Synchronises. */
+lc_status lc_batch_autotune(lc_batch *batch, int reps, int *mode_out, float *ms_out);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Phases of the non-rigid solve, for lc_read_profile. */

@@ -1,0 +1,450 @@
+// Batched non-rigid stage: many captures of uneven mesh and image size solved
+// together, one launch per phase for all of them, the whole Gauss-Newton /
+// PCG loop captured as one CUDA graph.
+//
+// Every kernel of the single-capture path already takes a descriptor array
+// and a (capture, tile) work list; the batch concatenates the captures' tile
+// lists per tile family.  The PCG runs as the cluster-persistent kernel, one
+// cluster per capture, for groups of captures (same K) whose common plan fits
+// in shared memory; the rest use the per-iteration kernels over their own
+// work lists.  Each capture keeps its own buffers, reductions and counters
+// (its context's), so a capture's arithmetic does not depend on the others:
+// its result is bit-identical to its single-capture solve with the same PCG
+// kernel and cluster size.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "lc_context.h"
+
+using namespace lc;
+
+namespace lc {
+
+constexpr int kPixTile = 2048;   // z-buffer pixels cleared per block (256 threads x 8)
+
+// Frame reset of every capture: z-buffer cleared, visibility counters and
+// the per-step history zeroed (tile 0 of each capture).
+__global__ void __launch_bounds__(256) batch_reset_kernel(const CapDesc* __restrict__ caps,
+                                                          const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const size_t P = (size_t)C.W * C.H;
+    const size_t p0 = (size_t)tile * kPixTile;
+    for (int j = threadIdx.x; j < kPixTile; j += blockDim.x) {
+        const size_t p = p0 + j;
+        if (p < P) C.zbuf[p] = ~0ULL;
+    }
+    if (tile == 0) {
+        for (int j = threadIdx.x; j < 2 * (LC_MAX_GN + 1); j += blockDim.x) C.hist[j] = 0.0;
+        for (int j = threadIdx.x; j < LC_MAX_GN + 2; j += blockDim.x) C.hist_iters[j] = 0;
+        if (threadIdx.x < 3) C.sc->counts[threadIdx.x] = 0;
+    }
+}
+
+// Node parameters of every capture back to the identity.
+__global__ void __launch_bounds__(kVecThreads) batch_identity_kernel(const CapDesc* __restrict__ caps,
+                                                                     const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    const int k = tile * kVecThreads + threadIdx.x;
+    if (k >= C.n) return;
+    C.node_R[3 * k + 0] = make_float4(1.f, 0.f, 0.f, 0.f);
+    C.node_R[3 * k + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
+    C.node_R[3 * k + 2] = make_float4(0.f, 0.f, 1.f, 0.f);
+    C.node_t[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+}  // namespace lc
+
+struct BatchGroup {
+    int first = 0, count = 0;   // slots in the batch's descriptor array
+    int K = 0;
+    PcgPlan plan{};
+};
+
+struct lc_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<lc_ctx*> ctxs;        // in caller order
+    std::vector<int> slot_of;         // caller index -> descriptor slot
+    std::vector<int> ctx_of;          // descriptor slot -> caller index
+    std::vector<CapDesc> snap;        // descriptors as uploaded (slot order)
+    CapDesc* dC = nullptr;
+    WorkItem* items = nullptr;        // all work lists, one allocation
+    Tiles all, multi;                 // every capture / captures on the per-iteration PCG
+    const WorkItem* pix_items = nullptr;
+    int pix_blocks = 0;
+    std::vector<BatchGroup> groups;   // captures on the cluster PCG
+    int mode = LC_BATCH_PCG_AUTO;
+    int n_gn = 0, n_pcg = 0;
+    cudaGraphExec_t gexec = nullptr;
+    bool gexec_identity = false;
+    std::vector<cudaEvent_t> ev;      // per member: its stream's work before the solve
+    cudaEvent_t done = nullptr;       // the batch solve, awaited by every member's stream
+    int graph_kernels = 0;
+    std::string err;
+
+    lc_status fail(lc_status st, const char* msg) {
+        err = msg;
+        return st;
+    }
+    void free_plan() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        if (items) cudaFree(items);
+        items = nullptr;
+        if (dC) cudaFree(dC);
+        dC = nullptr;
+    }
+    lc_status build();
+    void enqueue(bool from_identity);
+};
+
+// Descriptor order, work lists and PCG groups for the current mode.
+lc_status lc_batch::build() {
+    free_plan();
+    const int count = (int)ctxs.size();
+    // cluster-PCG candidates: the mode's cluster size must fit the capture
+    // on its own; grouped by K, ascending node count, greedily while the
+    // common plan fits
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<int> cl_of(count, 0);
+    std::vector<std::vector<int>> eo(count), go(count);
+    for (int i = 0; i < count; ++i) {
+        lc_ctx* c = ctxs[i];
+        int cl = 0;
+        if (mode == LC_BATCH_PCG_AUTO && c->use_cluster_pcg()) cl = c->pcg_plan.cl;
+        if (mode == LC_BATCH_PCG_CLUSTER8 || mode == LC_BATCH_PCG_CLUSTER16) {
+            const int want = mode == LC_BATCH_PCG_CLUSTER8 ? 8 : 16;
+            const int n = c->hC.n;
+            eo[i].resize(n + 1);
+            go[i].resize(n + 1);
+            cudaMemcpy(eo[i].data(), c->hC.ent_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
+            cudaMemcpy(go[i].data(), c->hC.edge_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
+            const int* e0 = eo[i].data();
+            const int* g0 = go[i].data();
+            PcgPlan pl;
+            if (plan_pcg_cluster_group(want, &n, c->hC.K, &e0, &g0, 1, &pl)) cl = want;
+        }
+        cl_of[i] = cl;
+        if (cl && eo[i].empty()) {
+            const int n = c->hC.n;
+            eo[i].resize(n + 1);
+            go[i].resize(n + 1);
+            cudaMemcpy(eo[i].data(), c->hC.ent_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
+            cudaMemcpy(go[i].data(), c->hC.edge_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(LC_ERR_CUDA, "lc_batch: reading the graphs");
+    // slot order: cluster captures by (cl, K, n), then the rest
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const bool ca = cl_of[a] != 0, cb = cl_of[b] != 0;
+        if (ca != cb) return ca;
+        if (cl_of[a] != cl_of[b]) return cl_of[a] < cl_of[b];
+        if (ctxs[a]->hC.K != ctxs[b]->hC.K) return ctxs[a]->hC.K < ctxs[b]->hC.K;
+        return ctxs[a]->hC.n < ctxs[b]->hC.n;
+    });
+    groups.clear();
+    int s = 0;
+    while (s < count && cl_of[order[s]]) {
+        BatchGroup g;
+        g.first = s;
+        g.K = ctxs[order[s]]->hC.K;
+        const int cl = cl_of[order[s]];
+        std::vector<int> ns;
+        std::vector<const int*> es, gs;
+        int e = s;
+        PcgPlan best{};
+        while (e < count && cl_of[order[e]] == cl && ctxs[order[e]]->hC.K == g.K) {
+            const int i = order[e];
+            ns.push_back(ctxs[i]->hC.n);
+            es.push_back(eo[i].data());
+            gs.push_back(go[i].data());
+            PcgPlan pl;
+            if (!plan_pcg_cluster_group(cl, ns.data(), g.K, es.data(), gs.data(), (int)ns.size(), &pl)) {
+                ns.pop_back();
+                break;
+            }
+            best = pl;
+            ++e;
+        }
+        if (e == s) break;   // cannot happen for a capture that fits alone; the rest go per-iteration
+        g.count = e - s;
+        g.plan = best;
+        groups.push_back(g);
+        s = e;
+    }
+    const int first_multi = s;
+    slot_of.assign(count, 0);
+    ctx_of.assign(count, 0);
+    snap.resize(count);
+    for (int j = 0; j < count; ++j) {
+        ctx_of[j] = order[j];
+        slot_of[order[j]] = j;
+        snap[j] = ctxs[order[j]]->hC;
+    }
+    // work lists
+    std::vector<WorkItem> w;
+    struct Fam {
+        size_t off;
+        int n;
+    };
+    auto family = [&](int lo, int hi, auto tiles_of) {
+        Fam f{w.size(), 0};
+        for (int j = lo; j < hi; ++j) {
+            const int t = tiles_of(snap[j]);
+            for (int q = 0; q < t; ++q) w.push_back({j, q});
+            f.n += t;
+        }
+        return f;
+    };
+    auto vert = [](const CapDesc& C) { return C.vert_tiles; };
+    auto tri = [](const CapDesc& C) { return C.tri_tiles; };
+    auto medge = [](const CapDesc& C) { return C.medge_tiles; };
+    auto node = [](const CapDesc& C) { return C.node_tiles; };
+    auto vec = [](const CapDesc& C) { return (C.n + kVecThreads - 1) / kVecThreads; };
+    auto pix = [](const CapDesc& C) { return (int)(((size_t)C.W * C.H + kPixTile - 1) / kPixTile); };
+    const Fam fa[6] = {family(0, count, vert), family(0, count, tri), family(0, count, medge),
+                       family(0, count, node), family(0, count, vec), family(0, count, pix)};
+    const Fam fm[3] = {family(first_multi, count, vert), family(first_multi, count, node),
+                       family(first_multi, count, vec)};
+    if (cudaMalloc(&items, sizeof(WorkItem) * std::max<size_t>(w.size(), 1)) != cudaSuccess ||
+        cudaMalloc(&dC, sizeof(CapDesc) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LC_ERR_OOM, "lc_batch: device memory");
+    }
+    cudaMemcpy(items, w.data(), sizeof(WorkItem) * w.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(dC, snap.data(), sizeof(CapDesc) * count, cudaMemcpyHostToDevice);
+    auto at = [&](const Fam& f) { return f.n ? items + f.off : nullptr; };
+    all = Tiles{};
+    all.vert = fa[0].n, all.vert_items = at(fa[0]);
+    all.tri = fa[1].n, all.tri_items = at(fa[1]);
+    all.medge = fa[2].n, all.medge_items = at(fa[2]);
+    all.node = fa[3].n, all.node_items = at(fa[3]);
+    all.vec = fa[4].n, all.vec_items = at(fa[4]);
+    pix_blocks = fa[5].n, pix_items = at(fa[5]);
+    multi = Tiles{};
+    multi.vert = fm[0].n, multi.vert_items = at(fm[0]);
+    multi.node = fm[1].n, multi.node_items = at(fm[1]);
+    multi.vec = fm[2].n, multi.vec_items = at(fm[2]);
+    if (cudaGetLastError() != cudaSuccess) return fail(LC_ERR_CUDA, "lc_batch: uploading the work lists");
+    return LC_OK;
+}
+
+void lc_batch::enqueue(bool from_identity) {
+    cudaStream_t st = stream;
+    if (from_identity && all.vec) batch_identity_kernel<<<all.vec, kVecThreads, 0, st>>>(dC, all.vec_items);
+    if (pix_blocks) batch_reset_kernel<<<pix_blocks, 256, 0, st>>>(dC, pix_items);
+    launch_warp(dC, all, st);
+    launch_visibility_kernels(dC, all, st);
+    for (int gn = 0; gn < n_gn; ++gn) {
+        if (gn > 0) launch_warp(dC, all, st);
+        launch_linearize(dC, all, true, st);
+        launch_rhs(dC, all, gn, false, st);
+        for (const BatchGroup& g : groups)
+            launch_pcg_cluster(dC + g.first, g.plan, g.K, n_pcg, st, g.count);
+        if (multi.vec) {
+            launch_pcg_init(dC, multi, st);
+            for (int it = 0; it < n_pcg; ++it) {
+                launch_jtj(dC, multi, nullptr, nullptr, true, st);
+                launch_pcg_vectors(dC, multi, st);
+            }
+        }
+        launch_update(dC, all, gn, st);
+    }
+    launch_warp(dC, all, st);
+    launch_linearize(dC, all, false, st);
+    launch_rhs(dC, all, n_gn, true, st);
+}
+
+static lc_status batch_check(lc_batch* b) {
+    for (lc_ctx* c : b->ctxs) {
+        if (!c->has_template || !c->has_graph || !c->has_camera || !c->has_frame)
+            return b->fail(LC_ERR_STATE, "lc_batch: every context needs template, graph, camera and frame");
+        if (c->device != b->device) return b->fail(LC_ERR_ARG, "lc_batch: contexts on different devices");
+        if (c->params.n_gn != b->n_gn || c->params.n_pcg != b->n_pcg)
+            return b->fail(LC_ERR_ARG, "lc_batch: contexts differ in n_gn / n_pcg");
+    }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_batch_create(lc_batch** out, lc_ctx* const* ctxs, int count) {
+    if (!out || !ctxs || count < 1) return LC_ERR_ARG;
+    *out = nullptr;
+    auto* b = new lc_batch();
+    b->ctxs.assign(ctxs, ctxs + count);
+    for (lc_ctx* c : b->ctxs)
+        if (!c) {
+            delete b;
+            return LC_ERR_ARG;
+        }
+    b->device = ctxs[0]->device;
+    b->n_gn = ctxs[0]->params.n_gn;
+    b->n_pcg = ctxs[0]->params.n_pcg;
+    lc_status s;
+    if ((s = batch_check(b))) {
+        // keep the message reachable through the first context
+        ctxs[0]->fail(s, "%s", b->err.c_str());
+        delete b;
+        return s;
+    }
+    cudaSetDevice(b->device);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return LC_ERR_CUDA;
+    }
+    // the members' own work must be finished before the batch uses their buffers
+    for (lc_ctx* c : b->ctxs) cudaStreamSynchronize(c->stream);
+    b->ev.resize(count);
+    for (auto& e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if ((s = b->build())) {
+        ctxs[0]->fail(s, "%s", b->err.c_str());
+        lc_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return LC_OK;
+}
+
+extern "C" lc_status lc_batch_destroy(lc_batch* b) {
+    if (!b) return LC_ERR_ARG;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->free_plan();
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LC_OK;
+}
+
+extern "C" const char* lc_batch_last_error(const lc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" lc_status lc_batch_set_pcg_mode(lc_batch* b, int mode) {
+    if (!b) return LC_ERR_ARG;
+    if (mode < LC_BATCH_PCG_AUTO || mode > LC_BATCH_PCG_PER_ITERATION)
+        return b->fail(LC_ERR_ARG, "lc_batch_set_pcg_mode: unknown mode");
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->mode = mode;
+    return b->build();
+}
+
+extern "C" lc_status lc_batch_solve(lc_batch* b, int from_identity, lc_solve_stats* stats) {
+    if (!b) return LC_ERR_ARG;
+    cudaSetDevice(b->device);
+    lc_status s;
+    if ((s = batch_check(b))) return s;
+    // a member whose buffers or sizes changed since the plan was built
+    bool changed = false;
+    for (size_t j = 0; j < b->snap.size(); ++j)
+        if (memcmp(&b->snap[j], &b->ctxs[b->ctx_of[j]]->hC, sizeof(CapDesc)) != 0) changed = true;
+    if (changed && (s = b->build())) return s;
+    if (b->gexec && b->gexec_identity != (from_identity != 0)) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if (!b->gexec) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return b->fail(LC_ERR_CUDA, "lc_batch_solve: begin capture");
+        b->enqueue(from_identity != 0);
+        if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess || !g) {
+            cudaGetLastError();
+            return b->fail(LC_ERR_CUDA, "lc_batch_solve: capture failed");
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int k = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nd, &ty);
+            if (ty == cudaGraphNodeTypeKernel) ++k;
+        }
+        b->graph_kernels = k;
+        const cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->gexec = nullptr;
+            return b->fail(LC_ERR_CUDA, "lc_batch_solve: graph instantiation");
+        }
+        b->gexec_identity = from_identity != 0;
+    }
+    // order with the members' own streams: the solve waits for their pending
+    // work (uploads, parameter changes), and their later calls wait for it
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        cudaEventRecord(b->ev[i], b->ctxs[i]->stream);
+        cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+    }
+    if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return b->fail(LC_ERR_CUDA, "lc_batch_solve: graph launch");
+    }
+    cudaEventRecord(b->done, b->stream);
+    for (lc_ctx* c : b->ctxs) cudaStreamWaitEvent(c->stream, b->done, 0);
+    if (!stats) return LC_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return b->fail(LC_ERR_CUDA, "lc_batch_solve: execution failed");
+    }
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        lc_ctx* c = b->ctxs[i];
+        if ((s = c->read_stats(&stats[i], b->n_gn))) return b->fail(s, "lc_batch_solve: reading statistics");
+        stats[i].n_kernels = b->graph_kernels;
+        int cl = 0;
+        const int slot = b->slot_of[i];
+        for (const BatchGroup& g : b->groups)
+            if (slot >= g.first && slot < g.first + g.count) cl = g.plan.cl;
+        stats[i].pcg_cluster_size = cl;
+    }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_batch_autotune(lc_batch* b, int reps, int* mode_out, float* ms_out) {
+    if (!b || reps < 1) return LC_ERR_ARG;
+    cudaSetDevice(b->device);
+    const int modes[4] = {LC_BATCH_PCG_AUTO, LC_BATCH_PCG_CLUSTER8, LC_BATCH_PCG_CLUSTER16,
+                          LC_BATCH_PCG_PER_ITERATION};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    float best_ms = 0.f;
+    lc_status s = LC_OK;
+    for (int m : modes) {
+        if ((s = lc_batch_set_pcg_mode(b, m))) break;
+        // warm up (capture + one run), then time reps solves from the identity
+        if ((s = lc_batch_solve(b, 1, nullptr))) break;
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps; ++r)
+            if ((s = lc_batch_solve(b, 1, nullptr))) break;
+        if (s) break;
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms_out) ms_out[m] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = m;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if (mode_out) *mode_out = best;
+    return lc_batch_set_pcg_mode(b, best);
+}

@@ -68,9 +68,10 @@ __global__ void __launch_bounds__(kVertTile) warp_kernel(const CapDesc* __restri
     C.uv[i] = ok ? project_exact(C.f, C.cx, C.cy, X, Y, Z) : make_float2(0.f, 0.f);
 }
 
-void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
-    warp_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
+void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
+    warp_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
 }
+void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_warp(dC, single_tiles(hC), st); }
 
 // ---------------------------------------------------------------------------
 // Rasteriser
@@ -268,13 +269,19 @@ __global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __res
     if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&C.sc->counts[threadIdx.x], sh[threadIdx.x]);
 }
 
+// raster, depth test, silhouette edges, contour set (the z-buffers must be
+// cleared and the visibility counters zeroed before)
+void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
+    if (T.tri) raster_kernel<<<T.tri, kTriTile, 0, st>>>(dC, T.tri_items);
+    vis_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
+    if (T.medge) silhouette_kernel<<<T.medge, kEdgeTile, 0, st>>>(dC, T.medge_items);
+    contour_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
+}
+
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     cudaMemsetAsync(hC.zbuf, 0xff, sizeof(unsigned long long) * (size_t)hC.W * hC.H, st);
     cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, counts), 0, sizeof(int) * 3, st);
-    if (hC.tri_tiles) raster_kernel<<<hC.tri_tiles, kTriTile, 0, st>>>(dC, nullptr);
-    vis_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
-    if (hC.medge_tiles) silhouette_kernel<<<hC.medge_tiles, kEdgeTile, 0, st>>>(dC, nullptr);
-    contour_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr);
+    launch_visibility_kernels(dC, single_tiles(hC), st);
 }
 
 }  // namespace lc

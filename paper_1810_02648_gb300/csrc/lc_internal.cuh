@@ -260,17 +260,49 @@ __device__ __forceinline__ void sum_partials(const double* part_base, int ntiles
         for (int j = 0; j < NV; ++j) out[j] += __ldcg(&part_base[t * NV + j]);
 }
 
+// ---- launch shapes --------------------------------------------------------
+// Blocks of each tile family and their (capture, tile) work lists.  A null
+// list means one capture (capture 0, tile = blockIdx.x); a batch of
+// captures passes concatenated lists, so the same kernels serve both.
+struct Tiles {
+    int vert = 0, tri = 0, medge = 0, node = 0, vec = 0;
+    const WorkItem* vert_items = nullptr;
+    const WorkItem* tri_items = nullptr;
+    const WorkItem* medge_items = nullptr;
+    const WorkItem* node_items = nullptr;
+    const WorkItem* vec_items = nullptr;
+};
+
+inline Tiles single_tiles(const CapDesc& C) {
+    Tiles t;
+    t.vert = C.vert_tiles;
+    t.tri = C.tri_tiles;
+    t.medge = C.medge_tiles;
+    t.node = C.node_tiles;
+    t.vec = (C.n + kVecThreads - 1) / kVecThreads;
+    return t;
+}
+
 // ---- kernel launchers (frame_kernels.cu, solver_kernels.cu, graph_kernels.cu)
 void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in, float4* img,
                        uint8_t* mask, int W, int H, cudaStream_t st);
 void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st);
+void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
+void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, cudaStream_t st);
+// p / out null: each capture's own p and Ap
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_pcg_vectors(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
+void launch_update(const CapDesc* dC, const Tiles& T, int gn_slot, cudaStream_t st);
 void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
 void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);
 
@@ -283,7 +315,12 @@ struct PcgPlan {
     size_t smem;     // dynamic shared memory bytes
 };
 bool plan_pcg_cluster(int n, int K, const int* ent_off_host, const int* edge_off_host, PcgPlan* out);
-cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st);
+// one cluster per capture: captures 0 .. ncap-1 of dC, all fitting the plan
+cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st, int ncap = 1);
+// a plan that fits every capture of a group (same K): per-CTA capacities are
+// the maxima over the captures, shared memory sized for the largest n
+bool plan_pcg_cluster_group(int cl, const int* n, int K, const int* const* ent_off_host,
+                            const int* const* edge_off_host, int count, PcgPlan* out);
 
 // graph construction
 struct GraphScratch {

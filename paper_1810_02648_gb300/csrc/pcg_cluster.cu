@@ -474,53 +474,88 @@ static PcgKernel pcg_kernel_for(int K) {
     return pcg_cluster_kernel<0>;
 }
 
+// The device can run the kernel for K with this plan (shared memory opt-in,
+// non-portable cluster size, at least one resident cluster).
+static int max_dynamic_smem();
+
+static bool accept_plan(int K, const PcgPlan& pl) {
+    const PcgKernel kern = pcg_kernel_for(K);
+    // the attribute caps every later launch of this kernel (other contexts and
+    // batches included), so it is raised to the device limit, never lowered
+    if (pl.smem > (size_t)max_dynamic_smem() ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem()) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (pl.cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.cl);
+    cfg.blockDim = dim3(kPcgThreads);
+    cfg.dynamicSmemBytes = pl.smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = pl.cl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+static int max_dynamic_smem() {
+    int dev = 0, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return max_optin - 1024;   // the kernel's own __shared__ arrays (< 1 KB)
+}
+
 // Choose the cluster size: the smallest of {8, 16} whose per-CTA staging fits
 // in shared memory and that the device can schedule.  Returns false if none
 // (the multi-kernel PCG is used then).
 bool plan_pcg_cluster(int n, int K, const int* ent_off_host, const int* edge_off_host, PcgPlan* out) {
-    int dev = 0, max_optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int static_smem = 1024;   // the kernel's own __shared__ arrays (< 1 KB)
+    const int max_smem = max_dynamic_smem();
     for (int cl : {8, 16}) {
         PcgPlan pl;
-        if (!try_plan(cl, n, K, ent_off_host, edge_off_host, max_optin - static_smem, pl)) continue;
-        const PcgKernel kern = pcg_kernel_for(K);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                          cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cl);
-        cfg.blockDim = dim3(kPcgThreads);
-        cfg.dynamicSmemBytes = pl.smem;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = cl;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!try_plan(cl, n, K, ent_off_host, edge_off_host, max_smem, pl)) continue;
+        if (!accept_plan(K, pl)) continue;
         *out = pl;
         return true;
     }
     return false;
 }
 
-cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st) {
+bool plan_pcg_cluster_group(int cl, const int* n, int K, const int* const* ent_off_host,
+                            const int* const* edge_off_host, int count, PcgPlan* out) {
+    int cap_e = 1, cap_d = 1, cap_n = 1, nmax = 1;
+    for (int c = 0; c < count; ++c) {
+        if (n[c] < cl || n[c] > 65535) return false;
+        nmax = std::max(nmax, n[c]);
+        for (int r = 0; r < cl; ++r) {
+            const int lo = part_lo(ent_off_host[c], n[c], cl, r), hi = part_lo(ent_off_host[c], n[c], cl, r + 1);
+            cap_e = std::max(cap_e, ent_off_host[c][hi] - ent_off_host[c][lo]);
+            cap_d = std::max(cap_d, edge_off_host[c][hi] - edge_off_host[c][lo]);
+            cap_n = std::max(cap_n, hi - lo);
+        }
+    }
+    const Smem L = smem_layout(nmax, K, cap_e, cap_d, cap_n);
+    if (L.total > (size_t)max_dynamic_smem()) return false;
+    const PcgPlan pl = {cl, cap_e, cap_d, cap_n, L.total};
+    if (!accept_plan(K, pl)) return false;
+    *out = pl;
+    return true;
+}
+
+cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st, int ncap) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pl.cl);
+    cfg.gridDim = dim3(pl.cl * ncap);
     cfg.blockDim = dim3(kPcgThreads);
     cfg.dynamicSmemBytes = pl.smem;
     cfg.stream = st;

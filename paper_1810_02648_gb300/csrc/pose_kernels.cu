@@ -534,8 +534,10 @@ void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, 
 }
 size_t pose_system_smem(int n_dof) { return sizeof(float) * 3 * kSysItems * ((n_dof + 1) | 1); }
 cudaError_t pose_kernels_init(int n_dof) {
+    // sized for the largest skeleton, so no context lowers it below another's need
+    (void)n_dof;
     return cudaFuncSetAttribute(pose_system_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pose_system_smem(n_dof));
+                                (int)pose_system_smem(kMaxDof));
 }
 int pose_system_ctas(int J, int N) { return (2 * J + N + kSysItems - 1) / kSysItems; }
 void launch_pose_system(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, int n_dof,

@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     }
 }
 
+void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st) {
+    linearize_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, update_b ? 1 : 0);
+}
 void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st) {
-    linearize_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, update_b ? 1 : 0);
+    launch_linearize(dC, single_tiles(hC), update_b, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,8 +243,11 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
     }
 }
 
+void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, cudaStream_t st) {
+    rhs_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, slot, energy_only ? 1 : 0);
+}
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st) {
-    rhs_kernel<<<hC.node_tiles, kNodeWarps * 32, 0, st>>>(dC, nullptr, slot, energy_only ? 1 : 0);
+    launch_rhs(dC, single_tiles(hC), slot, energy_only, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -249,11 +255,12 @@ void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items,
-                                                                const float4* __restrict__ p, int check_stop) {
+                                                                const float4* __restrict__ p_in, int check_stop) {
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (check_stop && C.sc->stop) return;
+    const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's PCG direction
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
     const float4 e4 = C.ev[i];
@@ -278,13 +285,15 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
 
 __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
                                                                     const WorkItem* __restrict__ items,
-                                                                    const float4* __restrict__ p,
-                                                                    float4* __restrict__ out, int dot) {
+                                                                    const float4* __restrict__ p_in,
+                                                                    float4* __restrict__ out_in, int dot) {
     __shared__ double sh[kNodeWarps][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (dot && C.sc->stop) return;
+    const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's p and Ap
+    float4* __restrict__ out = out_in ? out_in : C.Ap;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = tile * kNodeTile + w;
     double pap[1] = {0.0};
@@ -341,9 +350,12 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     }
 }
 
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st) {
+    jtj_vertex_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+    jtj_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, p, out, dot ? 1 : 0);
+}
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st) {
-    jtj_vertex_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, nullptr, p, dot ? 1 : 0);
-    jtj_node_kernel<<<hC.node_tiles, kNodeWarps * 32, 0, st>>>(dC, nullptr, p, out, dot ? 1 : 0);
+    launch_jtj(dC, single_tiles(hC), p, out, dot, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,14 +458,17 @@ __global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __r
     }
 }
 
-void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
-    pcg_init_kernel<<<(hC.n + kVecThreads - 1) / kVecThreads, kVecThreads, 0, st>>>(dC, nullptr);
+void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
+    pcg_init_kernel<<<T.vec, kVecThreads, 0, st>>>(dC, T.vec_items);
 }
+void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_pcg_init(dC, single_tiles(hC), st); }
 
+void launch_pcg_vectors(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
+    pcg_step_kernel<<<T.vec, kVecThreads, 0, st>>>(dC, T.vec_items);
+    pcg_dir_kernel<<<T.vec, kVecThreads, 0, st>>>(dC, T.vec_items);
+}
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
-    const int vb = (hC.n + kVecThreads - 1) / kVecThreads;
-    pcg_step_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
-    pcg_dir_kernel<<<vb, kVecThreads, 0, st>>>(dC, nullptr);
+    launch_pcg_vectors(dC, single_tiles(hC), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,8 +526,11 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
     }
 }
 
+void launch_update(const CapDesc* dC, const Tiles& T, int gn_slot, cudaStream_t st) {
+    update_kernel<<<T.vec, kVecThreads, 0, st>>>(dC, T.vec_items, gn_slot);
+}
 void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st) {
-    update_kernel<<<(hC.n + kVecThreads - 1) / kVecThreads, kVecThreads, 0, st>>>(dC, nullptr, gn_slot);
+    launch_update(dC, single_tiles(hC), gn_slot, st);
 }
 
 // ---------------------------------------------------------------------------

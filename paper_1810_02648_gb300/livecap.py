@@ -69,6 +69,12 @@ _SIGS = {
     "lc_upload_skeleton": [_P, ctypes.c_int, _P, _P, _P, _P, _P],
     "lc_set_pose": [_P, _P],
     "lc_reset_pose": [_P],
+    "lc_batch_create": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int],
+    "lc_batch_destroy": [_P],
+    "lc_batch_last_error": [_P],
+    "lc_batch_set_pcg_mode": [_P, ctypes.c_int],
+    "lc_batch_solve": [_P, ctypes.c_int, ctypes.POINTER(lc_solve_stats)],
+    "lc_batch_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
@@ -99,7 +105,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "lc_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name in ("lc_last_error", "lc_batch_last_error") else ctypes.c_int
     _lib = lib
     return lib
 
@@ -334,6 +340,56 @@ class Context:
         s = lc_solve_stats()
         self._check(self._lib.lc_solve_pose(self.h, ctypes.byref(s)))
         return s.to_dict()
+
+
+BATCH_PCG_AUTO, BATCH_PCG_CLUSTER8, BATCH_PCG_CLUSTER16, BATCH_PCG_PER_ITERATION = 0, 1, 2, 3
+
+
+class Batch:
+    """Several contexts solved together (lc_batch_*): one launch per phase
+    for all captures, the whole non-rigid loop in one CUDA graph."""
+
+    def __init__(self, contexts):
+        self._lib = load()
+        self.contexts = list(contexts)
+        arr = (_P * len(self.contexts))(*[c.h for c in self.contexts])
+        h = _P()
+        st = self._lib.lc_batch_create(ctypes.byref(h), arr, len(self.contexts))
+        if st != LC_OK:
+            raise LivecapError(st, self._lib.lc_last_error(self.contexts[0].h).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != LC_OK:
+            raise LivecapError(st, self._lib.lc_batch_last_error(self.h).decode())
+
+    def set_pcg_mode(self, mode: int):
+        self._check(self._lib.lc_batch_set_pcg_mode(self.h, int(mode)))
+
+    def solve(self, from_identity: bool = True, stats: bool = True):
+        if not stats:
+            self._check(self._lib.lc_batch_solve(self.h, int(from_identity), None))
+            return None
+        arr = (lc_solve_stats * len(self.contexts))()
+        self._check(self._lib.lc_batch_solve(self.h, int(from_identity), arr))
+        return [a.to_dict() for a in arr]
+
+    def autotune(self, reps: int = 3):
+        mode = ctypes.c_int(-1)
+        ms = np.zeros(4, np.float32)
+        self._check(self._lib.lc_batch_autotune(self.h, int(reps), ctypes.byref(mode), _ptr(ms)))
+        return mode.value, ms
 
 
 def setup_scene(ctx: Context, scene, with_frame: bool = True):

@@ -202,3 +202,21 @@ def q_band(A, b, n, n_runs=3):
         d, _ = pcg32(A, b, n, _r32(np.random.default_rng(2000 + seed)))
         spread = max(spread, abs(q(d) - q0) / abs(q0))
     return dref, info, spread
+
+
+def ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
+    """A capsule capture with odd sizes (rings, segments, nodes, K, a
+    non-square image, optionally shifted so it leaves the image)."""
+    import synth
+    V, F = synth.capsule_mesh(0.3, 1.0, rings, segs)
+    V = V + np.array([shift, 0.0, 3.0])
+    cam = synth.Camera(f=150.0 * side / 128.0, W=side, H=side + 7)
+    alb = synth.value_noise_albedo(V, seed)
+    mat = synth.half_split_material(V, seed)
+    gt = synth.smooth_deformation(V, min(n_nodes, len(V)), 0.05, 0.01, seed)
+    rgb, mask = synth.render(gt["V"], F, alb, cam)
+    rng = np.random.default_rng(seed)
+    rgb = (rgb + rng.normal(0, 0.01, rgb.shape)).astype(np.float32)
+    dt = synth.contour_distance_transform(mask).astype(np.float32)
+    return synth.Scene("ragged", cam, V.astype(np.float32), F.astype(np.int32), alb.astype(np.float32),
+                       mat.astype(np.float32), rgb, dt, mask, n_nodes, K, 4, 15, (1.0, 0.1, 10.0), gt["V"])

@@ -1,0 +1,134 @@
+"""Batched captures (lc_batch_*): uneven meshes, node counts, K and images
+solved together in one launch per phase.
+
+Each capture keeps its own buffers and reductions, so under the same PCG
+strategy its batched result must equal its own single-context solve bit for
+bit (node parameters, vertices, flags, energies, iteration counts).  That,
+plus the single-context parity against the oracle, carries the oracle parity
+over to the batch; one member is also compared with the oracle directly.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import graph_from_gpu, ragged_scene, report
+
+pytestmark = pytest.mark.gpu
+
+N_GN, N_PCG = 3, 10
+
+
+def _scenes():
+    out = [synth.make_scene("tiny"),
+           ragged_scene(13, 11, 37, 3),                   # K = 3, odd image
+           ragged_scene(17, 9, 50, 8, side=80, shift=0.45),   # K = 8, leaves the image
+           ragged_scene(6, 7, 5, 4)]                      # 5 nodes: too few for a cluster
+    out += synth.make_batch(count=3, seed=7, n_min=2000, n_max=4000, side_min=256, side_max=384)
+    return out
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    return _scenes()
+
+
+def _contexts(scenes, pcg_kernel):
+    from paper_1810_02648_gb300 import Context, setup_scene
+    ctxs = []
+    for sc in scenes:
+        c = Context(0)
+        setup_scene(c, sc)
+        c.set_params(n_gn=N_GN, n_pcg=N_PCG, pcg_kernel=pcg_kernel)
+        ctxs.append(c)
+    return ctxs
+
+
+def _single(ctxs):
+    res = []
+    for c in ctxs:
+        c.set_node_params(None, None)
+        st = c.solve_nonrigid()
+        res.append((st, c.read_back()))
+    return res
+
+
+def _same(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in ("R", "t", "V", "flags"))
+
+
+@pytest.mark.parametrize("mode,pcg_kernel", [(0, 0), (3, 1)])
+def test_batch_equals_single_solves(scenes, mode, pcg_kernel):
+    from paper_1810_02648_gb300 import Batch
+    ctxs = _contexts(scenes, pcg_kernel)
+    ref = _single(ctxs)
+    b = Batch(ctxs)
+    b.set_pcg_mode(mode)
+    stats = b.solve(from_identity=True)
+    clusters = []
+    for i, c in enumerate(ctxs):
+        out = c.read_back()
+        st_ref, out_ref = ref[i]
+        assert _same(out, out_ref), f"capture {i}"
+        assert stats[i]["e_total"] == st_ref["e_total"]
+        assert stats[i]["e_gn"] == st_ref["e_gn"] and stats[i]["pcg_iters"] == st_ref["pcg_iters"]
+        assert stats[i]["n_visible"] == st_ref["n_visible"] and stats[i]["n_boundary"] == st_ref["n_boundary"]
+        assert stats[i]["pcg_cluster_size"] == st_ref["pcg_cluster_size"]
+        clusters.append(stats[i]["pcg_cluster_size"])
+    if mode == 0:
+        assert any(clusters) and not all(clusters)   # both PCG paths in one batch
+    # a second solve from the identity repeats the first exactly
+    b.solve(from_identity=True, stats=False)
+    for i, c in enumerate(ctxs):
+        assert _same(c.read_back(), ref[i][1])
+    report(f"batch_mode{mode}", captures=len(ctxs), cluster_sizes=clusters, kernels=stats[0]["n_kernels"])
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_member_matches_oracle(scenes):
+    """One batch member (3 PCG iterations, outside CG's FP32-sensitive regime)
+    against the oracle to the strict bound."""
+    from paper_1810_02648_gb300 import Batch
+    from oracle import nonrigid as onr
+    ctxs = _contexts(scenes[:3], 0)
+    for c in ctxs:
+        c.set_params(n_pcg=3)
+    b = Batch(ctxs)
+    stats = b.solve(from_identity=True)
+    sc, c = scenes[1], ctxs[1]
+    ref = onr.solve_scene(sc, graph=graph_from_gpu(c.read_graph()), n_gn=N_GN, n_pcg=3)
+    out = c.read_back()
+    rel = abs(stats[1]["e_total"] - ref["e1"]["total"]) / ref["e1"]["total"]
+    diag = np.linalg.norm(sc.V.max(0) - sc.V.min(0))
+    dv = np.abs(out["V"] - ref["v"]).max()
+    report("batch_member_oracle", rel=rel, dv_over_diag=dv / diag)
+    assert rel <= 1e-4 and dv <= 1e-4 * diag
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_autotune_and_errors(scenes):
+    from paper_1810_02648_gb300 import Batch, Context, LivecapError
+    ctxs = _contexts(scenes[:4], 0)
+    b = Batch(ctxs)
+    mode, ms = b.autotune(reps=2)
+    assert mode in (0, 1, 2, 3) and np.all(ms > 0)
+    assert ms[mode] == ms.min()
+    stats = b.solve(from_identity=True)
+    assert all(np.isfinite(s["e_total"]) for s in stats)
+    report("batch_autotune", mode=mode, ms=[float(x) for x in ms])
+    with pytest.raises(LivecapError):
+        b.set_pcg_mode(7)
+    b.close()
+    # members must agree in n_gn / n_pcg, and be set up
+    ctxs[1].set_params(n_pcg=N_PCG + 1)
+    with pytest.raises(LivecapError):
+        Batch(ctxs)
+    bare = Context(0)
+    with pytest.raises(LivecapError):
+        Batch([ctxs[0], bare])
+    bare.close()
+    for c in ctxs:
+        c.close()

@@ -24,7 +24,7 @@ import pytest
 
 import synth
 from gpu_helpers import (check_frame_flags, graph_from_gpu, oracle_problem, oracle_vertex_blocks,
-                         random_params, report, set_flags, vec6)
+                         ragged_scene, random_params, report, set_flags, vec6)
 from oracle import graph as ograph
 from oracle import nonrigid as onr
 from oracle import visibility as ovis
@@ -51,19 +51,7 @@ def body():
     return synth.make_scene("body")
 
 
-def _ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
-    V, F = synth.capsule_mesh(0.3, 1.0, rings, segs)
-    V = V + np.array([shift, 0.0, 3.0])
-    cam = synth.Camera(f=150.0 * side / 128.0, W=side, H=side + 7)
-    alb = synth.value_noise_albedo(V, seed)
-    mat = synth.half_split_material(V, seed)
-    gt = synth.smooth_deformation(V, min(n_nodes, len(V)), 0.05, 0.01, seed)
-    rgb, mask = synth.render(gt["V"], F, alb, cam)
-    rng = np.random.default_rng(seed)
-    rgb = (rgb + rng.normal(0, 0.01, rgb.shape)).astype(np.float32)
-    dt = synth.contour_distance_transform(mask).astype(np.float32)
-    return synth.Scene("ragged", cam, V.astype(np.float32), F.astype(np.int32), alb.astype(np.float32),
-                       mat.astype(np.float32), rgb, dt, mask, n_nodes, K, 4, 15, (1.0, 0.1, 10.0), gt["V"])
+_ragged_scene = ragged_scene
 
 
 # ---------------------------------------------------------------------------
