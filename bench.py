@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["body", "tiny", "stress"], default="body")
+    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch"], default="body")
+    ap.add_argument("--batch-count", type=int, default=64, help="captures of the batch workload")
+    ap.add_argument("--pcg-mode", type=int, default=-1, help="batch PCG strategy (-1: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -406,10 +408,138 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# batched captures (uneven sizes, one launch per phase)
+# ---------------------------------------------------------------------------
+def _batch_member(spec):
+    sys.path.insert(0, ROOT)
+    import synth
+    return synth.make_batch_member(spec)
+
+
+def _oracle_batch_worker(spec):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    import synth
+    from oracle import graph as ograph
+    from oracle import nonrigid as onr
+    sc = synth.make_batch_member(spec)
+    g = ograph.build_graph(sc.V, sc.material, sc.n_nodes, sc.K)
+    t0 = time.perf_counter()
+    onr.solve_scene(sc, graph=g)
+    return time.perf_counter() - t0
+
+
+def batch_cpu_baseline(specs):
+    """The oracle's non-rigid solve of the batch's first captures, one
+    single-threaded process per core (one capture each); frames/s = captures
+    solved / the longest solve (they run at the same time)."""
+    cores = min(os.cpu_count() or 1, len(specs))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        secs = pool.map(_oracle_batch_worker, specs[:cores])
+    return {"value": cores / max(secs), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the non-rigid solves of the batch's first {cores} captures by the FP64 oracle, one "
+                      f"single-threaded process per core (scene generation and graph build not timed)"}
+
+
+def run_batch(a):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1810_02648_gb300 import Batch, Context, setup_scene
+
+    specs = synth.batch_specs(a.batch_count)
+    cpu_base = None
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        scenes = pool.map(_batch_member, specs)
+    if not a.no_cpu_baseline:
+        cpu_base = batch_cpu_baseline(specs)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctxs = []
+    for sc in scenes:
+        c = Context(0)
+        setup_scene(c, sc)
+        ctxs.append(c)
+    batch = Batch(ctxs)
+    if a.pcg_mode < 0:
+        mode, mode_ms = batch.autotune(reps=2)
+    else:
+        mode, mode_ms = a.pcg_mode, []
+        batch.set_pcg_mode(mode)
+    ext = torch.cuda.ExternalStream(batch.stream_handle, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(a.warmup):
+        batch.solve(True, stats=False)
+    stats = batch.solve(True, stats=True)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    with ClockSampler(0) as clk:
+        for k in range(a.steps):
+            with torch.cuda.stream(ext):
+                flush.zero_()
+            starts[k].record(ext)
+            batch.solve(True, stats=False)
+            ends[k].record(ext)
+        torch.cuda.synchronize(dev)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    count = len(ctxs)
+    value = count * a.steps / (total_ms / 1e3)
+    # the metric kernel alone over all captures, L2 flushed before each call
+    reps = 20
+    j0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    j1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for r in range(reps):
+        with torch.cuda.stream(ext):
+            flush.zero_()
+        j0[r].record(ext)
+        batch.apply_jtj()
+        j1[r].record(ext)
+    torch.cuda.synchronize(dev)
+    jtj_ms = sum(s.elapsed_time(e) for s, e in zip(j0, j1)) / reps
+    jtj_bytes = 0
+    verts = 0
+    for c, sc, st in zip(ctxs, scenes, stats):
+        E = len(c.read_graph()["edge_dst"])
+        jtj_bytes += jtj_algorithmic_bytes(sc, st["n_visible"], E)
+        verts += sc.N
+    peak, peak_kind = measured_peaks()
+    achieved = jtj_bytes / (jtj_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch: {count} uneven captures ({verts} vertices in total, 2k-20k each, "
+                               f"nodes = vertices/12, K=4, 256-1024 px images), non-rigid stage "
+                               f"{scenes[0].n_gn} GN x {scenes[0].n_pcg} PCG, one launch per phase",
+                   "captures": count, "vertices_total": int(verts),
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "pcg_mode": int(mode), "autotune_ms": [float(x) for x in mode_ms]},
+        "clocks": clk.summary(),
+        "gpu_launches": int(stats[0]["n_kernels"]) * a.steps,
+        "roofline": {"kernel": "jtj_vertex_kernel + jtj_node_kernel over all captures (one J^T J p each)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": jtj_bytes,
+                     "avg_launch_us": 1e3 * jtj_ms, "l2": "flushed before each timed call"},
+        "solve": {"e_total_sum": float(sum(s["e_total"] for s in stats)),
+                  "cluster_sizes": sorted(set(int(s["pcg_cluster_size"]) for s in stats))},
+        "cpu_baseline": cpu_base,
+    }
+    print(json.dumps(line))
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)
 

@@ -294,6 +294,13 @@ lc_status lc_batch_solve(lc_batch *batch, int from_identity, lc_solve_stats *sta
  * *mode_out; ms_out (nullable, 4 entries indexed by LC_BATCH_PCG_*) receives
  * the mean milliseconds per solve of each.  Synchronises. */
 lc_status lc_batch_autotune(lc_batch *batch, int reps, int *mode_out, float *ms_out);
+/* The batch's CUDA stream (a cudaStream_t), for ordering and timing. */
+void *lc_batch_stream(const lc_batch *batch);
+/* One matrix-free J^T J p of every member in one launch pair (vertex phase,
+ * node phase), at each member's current linearisation with p = its PCG
+ * direction, result into its A p buffer: the metric kernel on its own, for
+ * measurement.  Requires a previous lc_batch_solve.  Enqueue only. */
+lc_status lc_batch_apply_jtj(lc_batch *batch);
 
 /* ---- profiling ------------------------------------------------------------ */
 

@@ -84,6 +84,7 @@ struct lc_batch {
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
     bool gexec_identity = false;
+    bool solved = false;              // a solve has run: linearisations and directions exist
     std::vector<cudaEvent_t> ev;      // per member: its stream's work before the solve
     cudaEvent_t done = nullptr;       // the batch solve, awaited by every member's stream
     int graph_kernels = 0;
@@ -394,6 +395,7 @@ extern "C" lc_status lc_batch_solve(lc_batch* b, int from_identity, lc_solve_sta
     }
     cudaEventRecord(b->done, b->stream);
     for (lc_ctx* c : b->ctxs) cudaStreamWaitEvent(c->stream, b->done, 0);
+    b->solved = true;
     if (!stats) return LC_OK;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -447,4 +449,15 @@ extern "C" lc_status lc_batch_autotune(lc_batch* b, int reps, int* mode_out, flo
     if (s) return s;
     if (mode_out) *mode_out = best;
     return lc_batch_set_pcg_mode(b, best);
+}
+
+extern "C" void* lc_batch_stream(const lc_batch* b) { return b ? (void*)b->stream : nullptr; }
+
+extern "C" lc_status lc_batch_apply_jtj(lc_batch* b) {
+    if (!b) return LC_ERR_ARG;
+    if (!b->solved) return b->fail(LC_ERR_STATE, "lc_batch_apply_jtj: no batch solve yet");
+    cudaSetDevice(b->device);
+    launch_jtj(b->dC, b->all, nullptr, nullptr, false, b->stream);
+    if (cudaGetLastError() != cudaSuccess) return b->fail(LC_ERR_CUDA, "lc_batch_apply_jtj: launch");
+    return LC_OK;
 }

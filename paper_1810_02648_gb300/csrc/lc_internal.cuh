@@ -229,8 +229,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
     }
 }
 
-// Write this tile's partials; returns true in thread 0 of the block that
-// finished last for this capture and counter (it then sums in tile order).
+// Write this tile's partials; returns true (in every thread) in the block
+// that finished last for this capture and counter.
 template <int NV>
 __device__ __forceinline__ bool publish_partial(const CapDesc& C, int counter, int tile, int ntiles,
                                                 const double (&v)[NV], double* part_base) {
@@ -250,14 +250,33 @@ __device__ __forceinline__ bool publish_partial(const CapDesc& C, int counter, i
     return last;
 }
 
+// Sum of the ntiles partials by one warp, in a fixed order (lane l adds
+// tiles l, l + 32, ...; then a fixed shuffle tree); every lane gets the
+// total.  FP64 has a long latency on GB300, so the chain is kept short.
 template <int NV>
-__device__ __forceinline__ void sum_partials(const double* part_base, int ntiles, double (&out)[NV]) {
-    // called by a single thread, fixed order
+__device__ __forceinline__ void sum_partials_warp(const double* part_base, int ntiles, double (&out)[NV]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NV; ++j) out[j] = 0.0;
-    for (int t = 0; t < ntiles; ++t)
+    for (int t = lane; t < ntiles; t += 32)
 #pragma unroll
         for (int j = 0; j < NV; ++j) out[j] += __ldcg(&part_base[t * NV + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] += __shfl_xor_sync(0xffffffffu, out[j], o);
+}
+
+// publish_partial + in the last block: warp 0 sums all tiles, thread 0 runs
+// fin(total) (the capture's scalar update, exactly once).
+template <int NV, typename Fin>
+__device__ __forceinline__ void reduce_partials(const CapDesc& C, int counter, int tile, int ntiles,
+                                                const double (&v)[NV], Fin&& fin) {
+    if (!publish_partial<NV>(C, counter, tile, ntiles, v, C.part)) return;
+    if (threadIdx.x >= 32) return;
+    double tot[NV];
+    sum_partials_warp<NV>(C.part, ntiles, tot);
+    if (threadIdx.x == 0) fin(tot);
 }
 
 // ---- launch shapes --------------------------------------------------------

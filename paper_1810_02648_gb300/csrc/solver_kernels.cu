@@ -136,12 +136,10 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         C.ev[i] = make_float4(e0, e1, e2, (ph || si) ? 1.f : 0.f);
     }
     block_sum<2, kVertTile / 32>(en, sh);
-    if (publish_partial<2>(C, CNT_ENERGY, tile, C.vert_tiles, en, C.part)) {
-        double tot[2];
-        sum_partials<2>(C.part, C.vert_tiles, tot);
+    reduce_partials<2>(C, CNT_ENERGY, tile, C.vert_tiles, en, [&](const double (&tot)[2]) {
         C.sc->e_lin[0] = tot[0];
         C.sc->e_lin[1] = tot[1];
-    }
+    });
 }
 
 void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st) {
@@ -234,13 +232,11 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
         en[0] = arap;
     }
     block_sum<1, kNodeWarps>(en, sh);
-    if (publish_partial<1>(C, CNT_ARAP, tile, C.node_tiles, en, C.part)) {
-        double tot[1];
-        sum_partials<1>(C.part, C.node_tiles, tot);
+    reduce_partials<1>(C, CNT_ARAP, tile, C.node_tiles, en, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->e_lin[2] = tot[0];
         C.hist[2 * slot] = sc->e_lin[0] + sc->e_lin[1] + tot[0];
-    }
+    });
 }
 
 void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, cudaStream_t st) {
@@ -332,22 +328,22 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
         if (lane == 0) {
             out[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
             out[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+        }
+        if (dot && lane == 0) {
             pap[0] = (double)pw.x * acc[0] + (double)pw.y * acc[1] + (double)pw.z * acc[2] +
                      (double)pt.x * acc[3] + (double)pt.y * acc[4] + (double)pt.z * acc[5];
         }
     }
     if (!dot) return;
     block_sum<1, kNodeWarps>(pap, sh);
-    if (publish_partial<1>(C, CNT_DOT, tile, C.node_tiles, pap, C.part)) {
-        double tot[1];
-        sum_partials<1>(C.part, C.node_tiles, tot);
+    reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, pap, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->pAp = tot[0];
         if (!(tot[0] > 0.0)) {
             sc->stop = 1;
             sc->breakdown = 1;
         }
-    }
+    });
 }
 
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st) {
@@ -390,15 +386,13 @@ __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
     block_sum<1, kVecThreads / 32>(rz, sh);
-    if (publish_partial<1>(C, CNT_DOT2, tile, ntiles, rz, C.part)) {
-        double tot[1];
-        sum_partials<1>(C.part, ntiles, tot);
+    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->rz = tot[0];
         sc->stop = tot[0] == 0.0 ? 1 : 0;
         sc->breakdown = 0;
         sc->iters = 0;
-    }
+    });
 }
 
 __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __restrict__ caps,
@@ -426,9 +420,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
     block_sum<1, kVecThreads / 32>(rz, sh);
-    if (publish_partial<1>(C, CNT_DOT2, tile, ntiles, rz, C.part)) {
-        double tot[1];
-        sum_partials<1>(C.part, ntiles, tot);
+    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
         sc->iters += 1;
         sc->rz_new = tot[0];
         if (tot[0] == 0.0) {
@@ -438,7 +430,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __
             sc->beta = tot[0] / sc->rz;
             sc->rz = tot[0];
         }
-    }
+    });
 }
 
 __global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __restrict__ caps,
@@ -515,15 +507,13 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
     block_sum<1, kVecThreads / 32>(s2, sh);
-    if (publish_partial<1>(C, CNT_STEP, tile, ntiles, s2, C.part)) {
-        double tot[1];
-        sum_partials<1>(C.part, ntiles, tot);
+    reduce_partials<1>(C, CNT_STEP, tile, ntiles, s2, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->step2 = tot[0];
         C.hist[2 * slot + 1] = sqrt(tot[0]);
         C.hist_iters[slot] = sc->iters;
         C.hist_iters[LC_MAX_GN + 1] += sc->breakdown;
-    }
+    });
 }
 
 void launch_update(const CapDesc* dC, const Tiles& T, int gn_slot, cudaStream_t st) {

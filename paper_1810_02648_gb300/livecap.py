@@ -75,6 +75,8 @@ _SIGS = {
     "lc_batch_set_pcg_mode": [_P, ctypes.c_int],
     "lc_batch_solve": [_P, ctypes.c_int, ctypes.POINTER(lc_solve_stats)],
     "lc_batch_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P],
+    "lc_batch_stream": [_P],
+    "lc_batch_apply_jtj": [_P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
@@ -106,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_char_p if name in ("lc_last_error", "lc_batch_last_error") else ctypes.c_int
+        if name == "lc_batch_stream":
+            fn.restype = _P
     _lib = lib
     return lib
 
@@ -384,6 +388,15 @@ class Batch:
         arr = (lc_solve_stats * len(self.contexts))()
         self._check(self._lib.lc_batch_solve(self.h, int(from_identity), arr))
         return [a.to_dict() for a in arr]
+
+    @property
+    def stream_handle(self) -> int:
+        """The batch's cudaStream_t as an integer."""
+        return self._lib.lc_batch_stream(self.h) or 0
+
+    def apply_jtj(self):
+        """Enqueue one J^T J p of every member (measurement entry)."""
+        self._check(self._lib.lc_batch_apply_jtj(self.h))
 
     def autotune(self, reps: int = 3):
         mode = ctypes.c_int(-1)

@@ -23,6 +23,8 @@ from .scenes import (  # noqa: F401
     contour_distance_transform,
     make_scene,
     make_batch,
+    make_batch_member,
+    batch_specs,
     SKELETON_PARENTS,
     SKELETON_NAMES,
     N_POSE_DOF,

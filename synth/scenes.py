@@ -636,11 +636,11 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
     raise ValueError(f"unknown scene {name!r}")
 
 
-def make_batch(count: int = 64, seed: int = 2, n_min=2000, n_max=20000,
-               side_min=256, side_max=1024) -> List[Scene]:
-    """Uneven captures: vertices log-uniform in [n_min, n_max] (articulated
-    capsule bodies with a variable ring count), nodes = vertices / 12, square
-    images log-uniform in [side_min, side_max] rounded to a multiple of 32."""
+def batch_specs(count: int = 64, seed: int = 2, n_min=2000, n_max=20000, side_min=256, side_max=1024):
+    """Per-capture (scene seed, rings, image side, nodes) of an uneven batch:
+    vertices log-uniform in [n_min, n_max] (articulated capsule bodies with a
+    variable ring count), nodes = vertices / 12, square images log-uniform in
+    [side_min, side_max] rounded to a multiple of 32."""
     rng = np.random.default_rng(seed)
     out = []
     for c in range(count):
@@ -648,6 +648,16 @@ def make_batch(count: int = 64, seed: int = 2, n_min=2000, n_max=20000,
         rings = max(4, int(round((n_target / 10.0 - 2.0) / 25.0)))
         side = int(round(math.exp(rng.uniform(math.log(side_min), math.log(side_max))) / 32.0)) * 32
         n_vert = 10 * (2 + rings * 25)
-        out.append(make_scene("body", seed=1000 + seed * 100 + c, rings=rings,
-                              segments=25, side=side, n_nodes=max(8, n_vert // 12)))
+        out.append((1000 + seed * 100 + c, rings, side, max(8, n_vert // 12)))
     return out
+
+
+def make_batch_member(spec) -> Scene:
+    scene_seed, rings, side, n_nodes = spec
+    return make_scene("body", seed=scene_seed, rings=rings, segments=25, side=side, n_nodes=n_nodes)
+
+
+def make_batch(count: int = 64, seed: int = 2, n_min=2000, n_max=20000,
+               side_min=256, side_max=1024) -> List[Scene]:
+    """Uneven captures (``batch_specs``), generated one after the other."""
+    return [make_batch_member(sp) for sp in batch_specs(count, seed, n_min, n_max, side_min, side_max)]
