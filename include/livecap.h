@@ -73,6 +73,11 @@ typedef struct {
                            iterations of a Gauss-Newton step when the capture's
                            per-CTA data fits in shared memory; 1: one launch per
                            PCG phase (J^T J p, vector updates) */
+    float target_energy; /* 0 (default): run all n_gn steps.  > 0: the non-rigid
+                           solve stops at the first step whose linearisation
+                           energy is <= target_energy (the remaining steps are
+                           skipped on the device; stats.n_gn_done counts the
+                           updates made) */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -301,6 +306,70 @@ void *lc_batch_stream(const lc_batch *batch);
  * direction, result into its A p buffer: the metric kernel on its own, for
  * measurement.  Requires a previous lc_batch_solve.  Enqueue only. */
 lc_status lc_batch_apply_jtj(lc_batch *batch);
+
+/* ---- learned warm start (the project's addition to the paper's solver) ---- */
+
+/* The paper starts each frame's non-rigid solve from the previous frame's
+ * result (Sec. 3.4, Sec. 4).  A small network predicts every graph node's
+ * update (d_omega, d_t) from features pooled at that start, so that the
+ * Gauss-Newton iteration starts closer; the prediction is kept only if the
+ * energy at the predicted parameters does not exceed the energy at the start.
+ *
+ * Network: x = (f - mu) / sigma (per feature), h1 = relu(x W1 + b1),
+ * h2 = relu(h1 W2 + b2), y = h2 W3 + b3, sizes 64 -> 256 -> 256 -> 6;
+ * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
+ * master parameters.  Parameter vector (LC_MLP_PARAMS floats): W1 row-major
+ * 64 x 256, b1 256, W2 256 x 256, b2 256, W3 256 x 6, b3 6.  Loss over M
+ * rows: (1/M) sum ||y - t||^2.
+ *
+ * Node features (64 per node), at the current node parameters, pooled over
+ * the node's bound vertices with their binding weights w (W = sum w; a
+ * pooled value is 0 when W = 0) from the linearisation there:
+ *   0-2 Log(R_k)   3-5 t_k   6-11 -(J^T F)_k   12-17 diag(J^T J)_k
+ *   18-23 (-(J^T F)_k) / (diag_k + 1e-6 max(diag_k))
+ *   24-26 sum w r_photo / W   27-29 sum w |r_photo| / W
+ *   30 sum w r_sil / W   31 sum w r_sil^2 / W
+ *   32-34 sum w e / W   35-37 sum w |e| / W   (e = A_i^T r_i)
+ *   38-43 sum w H / W   (H = A_i^T A_i: h00 h01 h02 h11 h12 h22)
+ *   44 sum w [visible] / W   45 sum w [in B] / W   46 sum w [b = -1] / W   47 W
+ *   48-50 g_k   51-56 u_k: the node's motion over the last frame (lc_record_motion)
+ *   57-62 mean u_l over the node's graph neighbours   63 1 */
+#define LC_MLP_PARAMS 83974
+typedef struct lc_mlp lc_mlp;
+
+/* params (LC_MLP_PARAMS, null = zeros), mu / sigma (64 each, null = 0 / 1;
+ * sigma <= 0 is treated as 1): host or device. */
+lc_status lc_mlp_create(lc_mlp **out, int device, const float *params, const float *mu, const float *sigma);
+lc_status lc_mlp_destroy(lc_mlp *mlp);
+const char *lc_mlp_last_error(const lc_mlp *mlp);
+/* Current FP32 parameters (LC_MLP_PARAMS).  Synchronises. */
+lc_status lc_mlp_get_params(lc_mlp *mlp, float *params);
+/* Y (M x 6) for raw features F (M x 64).  Synchronises. */
+lc_status lc_mlp_forward(lc_mlp *mlp, const float *F, int M, float *Y);
+/* Loss and its gradient (LC_MLP_PARAMS, nullable) for features F (M x 64)
+ * and targets T (M x 6).  Synchronises. */
+lc_status lc_mlp_gradient(lc_mlp *mlp, const float *F, const float *T, int M, float *grad, double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * rows idx[0..B) (host or device) of the device arrays F (rows x 64) and
+ * T (rows x 6).  Enqueue only unless loss (nullable) is requested. */
+lc_status lc_mlp_train_step(lc_mlp *mlp, const float *F, const float *T, const int *idx, int B, float lr,
+                            double *loss);
+
+/* Features (n x 64) at the current node parameters and the frame decisions
+ * of the last visibility pass.  Synchronises. */
+lc_status lc_node_features(lc_ctx *ctx, float *F);
+/* Record the motion of every node since the previous call (or since the
+ * graph was built): u_k = (Log(R_k R_prev,k^T), t_k - t_prev,k).  Call once
+ * per frame after its solve.  Enqueue only. */
+lc_status lc_record_motion(lc_ctx *ctx);
+/* Warm start at the current node parameters (normally the previous frame's
+ * result): visibility, linearisation and features there; the network's
+ * update applied to every node (R <- Exp(d_omega) R, t += d_t); kept iff
+ * the energy at the predicted parameters (same frame decisions) is <= the
+ * energy at the start, else the start parameters are restored - all on the
+ * device.  accepted (nullable) receives 1/0 and energies (nullable, 2) the
+ * two energies; either makes the call synchronise. */
+lc_status lc_warm_start(lc_ctx *ctx, lc_mlp *mlp, int *accepted, double *energies);
 
 /* ---- profiling ------------------------------------------------------------ */
 

@@ -179,13 +179,15 @@ void lc_ctx::apply_params() {
     hC.w_sil = params.w_sil;
     hC.w_arap = params.w_arap;
     hC.eps_vis = params.eps_vis;
+    hC.target_energy = params.target_energy;
 }
 
 extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
     if (!ctx || !p) return LC_ERR_ARG;
     if (p->n_gn < 1 || p->n_gn > LC_MAX_GN || p->n_pcg < 1 || p->n_gn_pose < 1 || p->n_gn_pose > LC_MAX_GN ||
         !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f) ||
-        !(p->lambda_2d >= 0.f) || !(p->lambda_3d >= 0.f) || !(p->lambda_sil >= 0.f) || !(p->lambda_prior >= 0.f))
+        !(p->lambda_2d >= 0.f) || !(p->lambda_3d >= 0.f) || !(p->lambda_sil >= 0.f) || !(p->lambda_prior >= 0.f) ||
+        !(p->target_energy >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
@@ -346,6 +348,7 @@ void lc_ctx::ensure_partials() {
 }
 
 void lc_ctx::free_graph() {
+    warm_release();
     void* bufs[] = {(void*)hC.node_vid, (void*)hC.bind_idx, (void*)hC.bind_w, (void*)hC.node_g, (void*)hC.ent_off,
                     (void*)hC.ent, (void*)hC.edge_off, (void*)hC.edge_dst, (void*)hC.edge_s, hC.node_R, hC.node_t,
                     hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2};
@@ -617,6 +620,7 @@ void lc_ctx::enqueue_nonrigid() {
     prof_nonrigid.begin = prof_used;
     cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
+    cudaMemsetAsync((char*)C.sc + offsetof(Scalars, gn_stop), 0, 2 * sizeof(int), st);
     mark(LC_PH_WARP);
     launch_warp(dC, C, st);
     mark(LC_PH_VIS);
@@ -624,7 +628,7 @@ void lc_ctx::enqueue_nonrigid() {
     for (int gn = 0; gn < params.n_gn; ++gn) {
         if (gn > 0) {
             mark(LC_PH_WARP);
-            launch_warp(dC, C, st);
+            launch_warp(dC, C, st, true);
         }
         mark(LC_PH_LIN);
         launch_linearize(dC, C, true, st);
@@ -690,7 +694,7 @@ lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn) {
         stats->step_norm[g] = hist[2 * g + 1];
         stats->pcg_iters[g] = it[g];
     }
-    stats->n_gn_done = n_gn;
+    stats->n_gn_done = sc.gn_done;
     stats->n_visible = sc.counts[0];
     stats->n_boundary = sc.counts[1];
     stats->n_boundary_neg = sc.counts[2];
@@ -834,6 +838,7 @@ extern "C" lc_status lc_read_visibility(lc_ctx* ctx, uint64_t* zbuf, uint8_t* fl
 }
 
 lc_status lc_ctx::linearize_now(bool with_rhs) {
+    cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, gn_stop), 0, sizeof(int), stream);
     launch_warp(dC, hC, stream);
     launch_linearize(dC, hC, true, stream);
     launch_rhs(dC, hC, LC_MAX_GN, !with_rhs, stream);
@@ -943,6 +948,7 @@ extern "C" lc_status lc_solve_linear(lc_ctx* ctx, float* delta, int* iters) {
     cudaSetDevice(ctx->device);
     const bool prof = ctx->profiling;
     ctx->profiling = false;
+    cudaMemsetAsync((char*)ctx->hC.sc + offsetof(Scalars, gn_stop), 0, sizeof(int), ctx->stream);
     ctx->enqueue_pcg();
     ctx->profiling = prof;
     lc_status s;

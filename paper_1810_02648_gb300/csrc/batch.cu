@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(256) batch_reset_kernel(const CapDesc* __restr
         for (int j = threadIdx.x; j < 2 * (LC_MAX_GN + 1); j += blockDim.x) C.hist[j] = 0.0;
         for (int j = threadIdx.x; j < LC_MAX_GN + 2; j += blockDim.x) C.hist_iters[j] = 0;
         if (threadIdx.x < 3) C.sc->counts[threadIdx.x] = 0;
+        if (threadIdx.x == 0) {
+            C.sc->gn_stop = 0;
+            C.sc->gn_done = 0;
+        }
     }
 }
 
@@ -245,7 +249,7 @@ void lc_batch::enqueue(bool from_identity) {
     launch_warp(dC, all, st);
     launch_visibility_kernels(dC, all, st);
     for (int gn = 0; gn < n_gn; ++gn) {
-        if (gn > 0) launch_warp(dC, all, st);
+        if (gn > 0) launch_warp(dC, all, st, true);
         launch_linearize(dC, all, true, st);
         launch_rhs(dC, all, gn, false, st);
         for (const BatchGroup& g : groups)

@@ -39,10 +39,11 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
 // Warp + project: v'_i = v_i + sum_s w_is ((R_k - I)(v_i - g_k) + t_k).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) warp_kernel(const CapDesc* __restrict__ caps,
-                                                          const WorkItem* __restrict__ items) {
+                                                          const WorkItem* __restrict__ items, int gated) {
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (gated && C.sc->gn_stop) return;
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
     const float4 v = C.base[i];
@@ -68,10 +69,12 @@ __global__ void __launch_bounds__(kVertTile) warp_kernel(const CapDesc* __restri
     C.uv[i] = ok ? project_exact(C.f, C.cx, C.cy, X, Y, Z) : make_float2(0.f, 0.f);
 }
 
-void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
-    warp_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
+void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st, bool gated) {
+    warp_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, gated ? 1 : 0);
 }
-void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_warp(dC, single_tiles(hC), st); }
+void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st, bool gated) {
+    launch_warp(dC, single_tiles(hC), st, gated);
+}
 
 // ---------------------------------------------------------------------------
 // Rasteriser

@@ -8,6 +8,7 @@
 #include "lc_internal.cuh"
 
 struct PoseState;
+struct WarmState;
 
 struct lc_ctx {
     int device = 0;
@@ -41,6 +42,8 @@ struct lc_ctx {
     bool use_cluster_pcg() const { return pcg_plan_ok && params.pcg_kernel == 0; }
     void enqueue_pcg();
     PoseState* pose = nullptr;
+    WarmState* warm = nullptr;    // learned warm start (warmstart.cu)
+    void warm_release();
     // profiling: an event chain recorded between phases of the captured solve
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;

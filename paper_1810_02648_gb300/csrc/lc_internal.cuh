@@ -42,6 +42,8 @@ struct Scalars {
     int iters;         // PCG iterations run in the current solve
     int status;        // device error word (0 = ok)
     int counts[3];     // visible, contour, contour with b = -1
+    int gn_stop;       // the solve reached its target energy: later GN steps are skipped
+    int gn_done;       // GN updates made in the current solve
 };
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
@@ -54,6 +56,7 @@ struct CapDesc {
     int vert_tiles, node_tiles, tri_tiles, medge_tiles;
     float f, cx, cy;
     float w_photo, w_sil, w_arap, eps_vis;
+    float target_energy;   // > 0: stop the GN loop once the energy is <= this
     // template (rest geometry of this stage) and mesh topology
     const float4* base;      // N (x, y, z, 0)
     const float4* albedo;    // N (r, g, b, 0)
@@ -305,8 +308,9 @@ inline Tiles single_tiles(const CapDesc& C) {
 // ---- kernel launchers (frame_kernels.cu, solver_kernels.cu, graph_kernels.cu)
 void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in, float4* img,
                        uint8_t* mask, int W, int H, cudaStream_t st);
-void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
-void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st);
+void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st, bool gated = false);
+// gated: skipped for captures whose GN loop has stopped (steps after the first)
+void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st, bool gated = false);
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st);

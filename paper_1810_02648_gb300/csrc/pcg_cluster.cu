@@ -186,6 +186,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     const int rank = (int)cluster.block_rank();
     const int cap = blockIdx.x / cl;   // one cluster per capture
     const CapDesc& C = caps[cap];
+    // the solve reached its target energy: every CTA of the cluster leaves
+    // before any distributed shared memory access
+    if (C.sc->gn_stop) return;
     const int n = C.n, K = C.K;
     const int lo = part_lo(C.ent_off, n, cl, rank), hi = part_lo(C.ent_off, n, cl, rank + 1);
     const int nown = hi - lo;

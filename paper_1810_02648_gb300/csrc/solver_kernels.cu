@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (update_b && C.sc->gn_stop) return;   // a GN step after the solve reached its target
     const int i = tile * kVertTile + threadIdx.x;
     double en[2] = {0.0, 0.0};
     if (i < C.N) {
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (!energy_only && C.sc->gn_stop) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = tile * kNodeTile + w;
     double en[1] = {0.0};
@@ -235,7 +237,9 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
     reduce_partials<1>(C, CNT_ARAP, tile, C.node_tiles, en, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->e_lin[2] = tot[0];
-        C.hist[2 * slot] = sc->e_lin[0] + sc->e_lin[1] + tot[0];
+        const double E = sc->e_lin[0] + sc->e_lin[1] + tot[0];
+        C.hist[2 * slot] = E;
+        if (!energy_only && C.target_energy > 0.f && E <= (double)C.target_energy) sc->gn_stop = 1;
     });
 }
 
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
-    if (check_stop && C.sc->stop) return;
+    if (check_stop && (C.sc->stop || C.sc->gn_stop)) return;
     const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's PCG direction
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
-    if (dot && C.sc->stop) return;
+    if (dot && (C.sc->stop || C.sc->gn_stop)) return;
     const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's p and Ap
     float4* __restrict__ out = out_in ? out_in : C.Ap;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -371,6 +375,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
     double rz[1] = {0.0};
     if (k < C.n) {
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
-    if (sc->stop) return;
+    if (sc->stop || sc->gn_stop) return;
     const float alpha = (float)(sc->rz / sc->pAp);
     const int k = tile * kVecThreads + threadIdx.x;
     double rz[1] = {0.0};
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __r
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
-    if (sc->stop) return;
+    if (sc->stop || sc->gn_stop) return;
     const float beta = (float)sc->beta;
     const int k = tile * kVecThreads + threadIdx.x;
     if (k < C.n) {
@@ -472,6 +477,7 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
     double s2[1] = {0.0};
     if (k < C.n) {
@@ -513,6 +519,7 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
         C.hist[2 * slot + 1] = sqrt(tot[0]);
         C.hist_iters[slot] = sc->iters;
         C.hist_iters[LC_MAX_GN + 1] += sc->breakdown;
+        sc->gn_done = slot + 1;
     });
 }
 

@@ -24,7 +24,8 @@ class lc_params(ctypes.Structure):
     _fields_ = [("w_photo", ctypes.c_float), ("w_sil", ctypes.c_float), ("w_arap", ctypes.c_float),
                 ("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("eps_vis", ctypes.c_float),
                 ("lambda_2d", ctypes.c_float), ("lambda_3d", ctypes.c_float), ("lambda_sil", ctypes.c_float),
-                ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int)]
+                ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int),
+                ("target_energy", ctypes.c_float)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -42,7 +43,8 @@ class lc_solve_stats(ctypes.Structure):
                     pcg_iters=list(self.pcg_iters[:g]), n_visible=self.n_visible,
                     n_boundary=self.n_boundary, n_boundary_neg=self.n_boundary_neg,
                     pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels,
-                    pcg_cluster_size=self.pcg_cluster_size)
+                    pcg_cluster_size=self.pcg_cluster_size, n_gn_done=g,
+                    e_gn_all=list(self.e_gn))
 
 
 _P = ctypes.c_void_p
@@ -77,6 +79,16 @@ _SIGS = {
     "lc_batch_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P],
     "lc_batch_stream": [_P],
     "lc_batch_apply_jtj": [_P],
+    "lc_mlp_create": [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P],
+    "lc_mlp_destroy": [_P],
+    "lc_mlp_last_error": [_P],
+    "lc_mlp_get_params": [_P, _P],
+    "lc_mlp_forward": [_P, _P, ctypes.c_int, _P],
+    "lc_mlp_gradient": [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)],
+    "lc_mlp_train_step": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
+    "lc_node_features": [_P, _P],
+    "lc_record_motion": [_P],
+    "lc_warm_start": [_P, _P, ctypes.POINTER(ctypes.c_int), _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
@@ -107,7 +119,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name in ("lc_last_error", "lc_batch_last_error") else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name in ("lc_last_error", "lc_batch_last_error", "lc_mlp_last_error") \
+            else ctypes.c_int
         if name == "lc_batch_stream":
             fn.restype = _P
     _lib = lib
@@ -262,6 +275,24 @@ class Context:
                                            _ptr(out.get("flags")), _ptr(out.get("pose"))))
         return out
 
+    # ---- learned warm start
+    def node_features(self) -> np.ndarray:
+        F = np.zeros((self.n, 64), np.float32)
+        self._check(self._lib.lc_node_features(self.h, _ptr(F)))
+        return F
+
+    def record_motion(self):
+        self._check(self._lib.lc_record_motion(self.h))
+
+    def warm_start(self, mlp, sync: bool = True):
+        if not sync:
+            self._check(self._lib.lc_warm_start(self.h, mlp.h, None, None))
+            return None
+        acc = ctypes.c_int(0)
+        e = np.zeros(2, np.float64)
+        self._check(self._lib.lc_warm_start(self.h, mlp.h, ctypes.byref(acc), _ptr(e)))
+        return bool(acc.value), e
+
     # ---- inspection
     def compute_visibility(self):
         self._check(self._lib.lc_compute_visibility(self.h))
@@ -344,6 +375,65 @@ class Context:
         s = lc_solve_stats()
         self._check(self._lib.lc_solve_pose(self.h, ctypes.byref(s)))
         return s.to_dict()
+
+
+MLP_PARAMS = 83974
+
+
+class MLP:
+    """The warm-start network (lc_mlp_*): 64 -> 256 -> 256 -> 6, BF16 tensor-core
+    kernels, FP32 master parameters, Adam."""
+
+    def __init__(self, device: int = 0, params=None, mu=None, sigma=None):
+        self._lib = load()
+        self.device = device
+        self._keep = [_arr(params, np.float32), _arr(mu, np.float32), _arr(sigma, np.float32)]
+        h = _P()
+        st = self._lib.lc_mlp_create(ctypes.byref(h), device, *[_ptr(a) for a in self._keep])
+        if st != LC_OK:
+            raise LivecapError(st, "lc_mlp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != LC_OK:
+            raise LivecapError(st, self._lib.lc_mlp_last_error(self.h).decode())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, np.float32)
+        self._check(self._lib.lc_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def forward(self, F) -> np.ndarray:
+        F = _arr(F, np.float32)
+        Y = np.zeros((F.shape[0], 6), np.float32)
+        self._check(self._lib.lc_mlp_forward(self.h, _ptr(F), F.shape[0], _ptr(Y)))
+        return Y
+
+    def gradient(self, F, T):
+        F, T = _arr(F, np.float32), _arr(T, np.float32)
+        g = np.zeros(MLP_PARAMS, np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(self._lib.lc_mlp_gradient(self.h, _ptr(F), _ptr(T), F.shape[0], _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, F_dev, T_dev, idx, lr: float, want_loss: bool = False):
+        """One Adam step on rows idx of device arrays F_dev (rows x 64), T_dev (rows x 6)."""
+        idx = _arr(idx, np.int32)
+        loss = ctypes.c_double(0.0)
+        self._check(self._lib.lc_mlp_train_step(self.h, _ptr(F_dev), _ptr(T_dev), _ptr(idx), len(idx),
+                                                float(lr), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
 
 
 BATCH_PCG_AUTO, BATCH_PCG_CLUSTER8, BATCH_PCG_CLUSTER16, BATCH_PCG_PER_ITERATION = 0, 1, 2, 3
