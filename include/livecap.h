@@ -173,6 +173,8 @@ lc_status lc_upload_frame(lc_ctx *ctx, const float *rgb, const float *dt, const 
  * t_k += d_t_k.  The whole sequence runs as one captured CUDA graph.
  * `stats` may be null; when given, the call synchronises and fills it. */
 lc_status lc_solve_nonrigid(lc_ctx *ctx, lc_solve_stats *stats);
+/* Statistics of the last lc_solve_nonrigid (as its `stats`).  Synchronises. */
+lc_status lc_read_stats(lc_ctx *ctx, lc_solve_stats *stats);
 
 /* Read the result.  node_R n x 9, node_t n x 3, V_out N x 3 (warped
  * vertices), flags N (LC_FLAG_* bits of the last visibility pass; BNEG as
@@ -367,8 +369,11 @@ lc_status lc_record_motion(lc_ctx *ctx);
  * update applied to every node (R <- Exp(d_omega) R, t += d_t); kept iff
  * the energy at the predicted parameters (same frame decisions) is <= the
  * energy at the start, else the start parameters are restored - all on the
- * device.  accepted (nullable) receives 1/0 and energies (nullable, 2) the
- * two energies; either makes the call synchronise. */
+ * device.  The next lc_solve_nonrigid keeps the frame decisions taken at
+ * the start (visibility and the contour set are not recomputed at the
+ * predicted parameters), so its energies compare with those of a solve from
+ * the start.  accepted (nullable) receives 1/0 and energies (nullable, 2)
+ * the two energies; either makes the call synchronise. */
 lc_status lc_warm_start(lc_ctx *ctx, lc_mlp *mlp, int *accepted, double *energies);
 
 /* ---- profiling ------------------------------------------------------------ */

@@ -644,6 +644,7 @@ void lc_ctx::enqueue_nonrigid() {
     launch_linearize(dC, C, false, st);
     mark(LC_PH_RHS);
     launch_rhs(dC, C, params.n_gn, true, st);
+    launch_vis_unfreeze(dC, st);
     mark_end();
     prof_nonrigid.end = prof_used;
 }
@@ -717,6 +718,17 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
         stats->n_kernels = ctx->graph_kernels;
         stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
     }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_read_stats(lc_ctx* ctx, lc_solve_stats* stats) {
+    if (!ctx || !stats) return LC_ERR_ARG;
+    if (!ctx->gexec) return ctx->fail(LC_ERR_STATE, "lc_read_stats: no non-rigid solve yet");
+    cudaSetDevice(ctx->device);
+    lc_status s;
+    if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
+    stats->n_kernels = ctx->graph_kernels;
+    stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
     return LC_OK;
 }
 
@@ -811,6 +823,7 @@ extern "C" lc_status lc_compute_visibility(lc_ctx* ctx) {
     if ((s = ctx->check_solve_state("lc_compute_visibility"))) return s;
     cudaSetDevice(ctx->device);
     launch_warp(ctx->dC, ctx->hC, ctx->stream);
+    launch_vis_unfreeze(ctx->dC, ctx->stream);
     launch_visibility(ctx->dC, ctx->hC, ctx->stream);
     ctx->has_vis = true;
     ctx->has_lin = false;

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) batch_reset_kernel(const CapDesc* __restr
         if (threadIdx.x == 0) {
             C.sc->gn_stop = 0;
             C.sc->gn_done = 0;
+            C.sc->vis_frozen = 0;
         }
     }
 }

@@ -1,3 +1,4 @@
+#include <algorithm>
 // Frame preparation, embedded-graph warp + projection, and the once-per-frame
 // visibility / contour pass.
 //
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kTriTile) raster_kernel(const CapDesc* __restr
     const int t = tile * kTriTile + threadIdx.x;
     TriSetup& S = su[threadIdx.x];
     S.npix = 0;
-    if (t < C.F) {
+    if (t < C.F && !C.sc->vis_frozen) {
         const int4 tri = C.tris[t];
         long long ax, ay, bx, by, qx, qy;
         if (vertex_snap(C, tri.x, ax, ay) && vertex_snap(C, tri.y, bx, by) && vertex_snap(C, tri.z, qx, qy)) {
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(kVertTile) vis_kernel(const CapDesc* __restric
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (C.sc->vis_frozen) return;   // the frame decisions were kept from the start
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
     uint32_t fl = 0;
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(kEdgeTile) silhouette_kernel(const CapDesc* __
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (C.sc->vis_frozen) return;   // the frame decisions were kept from the start
     const int e = tile * kEdgeTile + threadIdx.x;
     if (e >= C.n_medges) return;
     const int4 me = C.medges[e];
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __res
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    if (C.sc->vis_frozen) return;   // the frame decisions were kept from the start
     const int i = tile * kVertTile + threadIdx.x;
     int cnt[3] = {0, 0, 0};
     if (i < C.N) {
@@ -281,10 +285,26 @@ void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t s
     contour_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
 }
 
+// z-buffer cleared and visibility counters zeroed, unless the capture's
+// frame decisions are frozen
+__global__ void __launch_bounds__(256) vis_clear_kernel(const CapDesc* __restrict__ caps) {
+    const CapDesc& C = caps[0];
+    if (C.sc->vis_frozen) return;
+    const size_t P = (size_t)C.W * C.H;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x)
+        C.zbuf[p] = ~0ULL;
+    if (blockIdx.x == 0 && threadIdx.x < 3) C.sc->counts[threadIdx.x] = 0;
+}
+
+__global__ void vis_unfreeze_kernel(const CapDesc* __restrict__ caps) { caps[0].sc->vis_frozen = 0; }
+
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
-    cudaMemsetAsync(hC.zbuf, 0xff, sizeof(unsigned long long) * (size_t)hC.W * hC.H, st);
-    cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, counts), 0, sizeof(int) * 3, st);
+    const size_t P = (size_t)hC.W * hC.H;
+    const int blocks = (int)std::min<size_t>((P + 255) / 256, 2048);
+    vis_clear_kernel<<<blocks, 256, 0, st>>>(dC);
     launch_visibility_kernels(dC, single_tiles(hC), st);
 }
+
+void launch_vis_unfreeze(const CapDesc* dC, cudaStream_t st) { vis_unfreeze_kernel<<<1, 1, 0, st>>>(dC); }
 
 }  // namespace lc

@@ -43,7 +43,8 @@ struct Scalars {
     int status;        // device error word (0 = ok)
     int counts[3];     // visible, contour, contour with b = -1
     int gn_stop;       // the solve reached its target energy: later GN steps are skipped
-    int gn_done;       // GN updates made in the current solve
+    int gn_done;       // GN updates made in the current solve (gn_stop, gn_done are reset together)
+    int vis_frozen;    // keep the frame decisions (V, B) of the start for the next solve
 };
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
@@ -313,6 +314,8 @@ void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st, bool gat
 void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st, bool gated = false);
 void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st);
+// the next visibility pass runs again (clears vis_frozen)
+void launch_vis_unfreeze(const CapDesc* dC, cudaStream_t st);
 void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st);
 void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);

@@ -301,6 +301,7 @@ void lc_ctx::enqueue_pose() {
     cudaMemcpyAsync(P.pose_start, P.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
     launch_pose_fk(S.d, st);
     launch_pose_skin(dC, hC, S.d, nullptr, 0, st);
+    launch_vis_unfreeze(dC, st);
     launch_visibility(dC, hC, st);
     launch_pose_blist(dC, S.d, st);
     // step 0 linearises at the start pose, whose b_i the contour pass just
@@ -380,6 +381,7 @@ extern "C" lc_status lc_eval_pose(lc_ctx* ctx, float* V_skinned, double* A, doub
     cudaMemcpyAsync(S.h.pose_start, S.h.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
     launch_pose_fk(S.d, st);
     launch_pose_skin(ctx->dC, ctx->hC, S.d, nullptr, 0, st);
+    launch_vis_unfreeze(ctx->dC, st);
     launch_visibility(ctx->dC, ctx->hC, st);
     launch_pose_blist(ctx->dC, S.d, st);
     launch_pose_system(ctx->dC, ctx->hC, S.d, S.h.J, S.h.n_dof, st);

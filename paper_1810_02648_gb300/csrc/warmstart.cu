@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -377,7 +378,10 @@ __global__ void accept_kernel(const CapDesc* __restrict__ caps, const double* __
     const CapDesc& C = caps[0];
     const bool keep = e[1] <= e[0];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) *accepted = keep ? 1 : 0;
+    if (k == 0) {
+        *accepted = keep ? 1 : 0;
+        C.sc->vis_frozen = 1;   // the next solve keeps the frame decisions of the start
+    }
     if (keep || k >= C.n) return;
     C.node_R[3 * k] = R0[3 * k];
     C.node_R[3 * k + 1] = R0[3 * k + 1];
@@ -420,7 +424,11 @@ __global__ void identity_rows_kernel(float4* __restrict__ R, float4* __restrict_
 // ---------------------------------------------------------------------------
 // the network object
 // ---------------------------------------------------------------------------
+static std::atomic<unsigned long long> g_mlp_uid{0};   // creation counter (host)
+
 struct lc_mlp {
+    unsigned long long uid = 0;   // unique per network; gen bumps when scratch moves
+    unsigned long long gen = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -482,6 +490,7 @@ struct lc_mlp {
             return fail(LC_ERR_OOM, "lc_mlp: device memory");
         }
         cap = M;
+        ++gen;
         return LC_OK;
     }
     void refresh_weights(cudaStream_t st) { weights_bf16_kernel<<<(kDH * kDH + 255) / 256, 256, 0, st>>>(theta, W1, W2, W3); }
@@ -530,6 +539,10 @@ struct WarmState {
     float4* t0 = nullptr;
     double* e = nullptr;       // energies at the start and at the prediction
     int* accepted = nullptr;
+    // the warm-start sequence captured as one CUDA graph, for this network
+    // and its scratch buffers
+    cudaGraphExec_t gexec = nullptr;
+    unsigned long long g_uid = 0, g_gen = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -556,6 +569,7 @@ extern "C" lc_status lc_mlp_create(lc_mlp** out, int device, const float* params
     if (!out) return LC_ERR_ARG;
     *out = nullptr;
     auto* m = new lc_mlp();
+    m->uid = ++g_mlp_uid;
     m->device = device;
     if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -677,6 +691,7 @@ extern "C" lc_status lc_mlp_train_step(lc_mlp* m, const float* F, const float* T
 // ---------------------------------------------------------------------------
 void lc_ctx::warm_release() {
     if (!warm) return;
+    if (warm->gexec) cudaGraphExecDestroy(warm->gexec);
     for (void* p : {(void*)warm->F, (void*)warm->Yp, (void*)warm->motion, (void*)warm->Rprev, (void*)warm->tprev,
                     (void*)warm->R0, (void*)warm->t0, (void*)warm->e, (void*)warm->accepted})
         release(p);
@@ -739,28 +754,20 @@ extern "C" lc_status lc_record_motion(lc_ctx* ctx) {
     return ctx->cuda(cudaGetLastError(), "record motion");
 }
 
-extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double* energies) {
-    if (!ctx || !m) return LC_ERR_ARG;
-    lc_status s;
-    if ((s = ctx->check_solve_state("lc_warm_start"))) return s;
-    if (m->device != ctx->device) return ctx->fail(LC_ERR_ARG, "lc_warm_start: network on another device");
-    cudaSetDevice(ctx->device);
-    if ((s = warm_ensure(ctx))) return s;
-    const int n = ctx->hC.n;
-    if ((s = m->ensure(n))) return ctx->fail(s, "lc_warm_start: network scratch");
+// the warm-start sequence on the context's stream (captured once per network)
+static void enqueue_warm(lc_ctx* ctx, lc_mlp* m) {
     WarmState& w = *ctx->warm;
+    const int n = ctx->hC.n;
     cudaStream_t st = ctx->stream;
-    // the network's previous work (training) before its buffers are reused here
-    cudaEvent_t ev;
-    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    cudaEventRecord(ev, m->stream);
-    cudaStreamWaitEvent(st, ev, 0);
-    cudaEventDestroy(ev);
     // frame decisions and linearisation at the start, its energy and features
     launch_warp(ctx->dC, ctx->hC, st);
+    launch_vis_unfreeze(ctx->dC, st);
     launch_visibility(ctx->dC, ctx->hC, st);
-    ctx->has_vis = true;
-    if ((s = warm_features(ctx))) return s;
+    cudaMemsetAsync((char*)ctx->hC.sc + offsetof(Scalars, gn_stop), 0, sizeof(int), st);
+    launch_warp(ctx->dC, ctx->hC, st);
+    launch_linearize(ctx->dC, ctx->hC, true, st);
+    launch_rhs(ctx->dC, ctx->hC, LC_MAX_GN, false, st);
+    node_features_kernel<<<(n + 7) / 8, 256, 0, st>>>(ctx->dC, w.motion, w.F);
     energy_copy_kernel<<<1, 1, 0, st>>>(ctx->dC, w.e);
     // prediction
     normalise_kernel<<<(unsigned)(((size_t)n * kDIn + 255) / 256), 256, 0, st>>>(w.F, m->mu, m->sigma, m->X, n);
@@ -772,6 +779,46 @@ extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double
     launch_rhs(ctx->dC, ctx->hC, LC_MAX_GN, true, st);
     energy_copy_kernel<<<1, 1, 0, st>>>(ctx->dC, w.e + 1);
     accept_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctx->dC, w.e, w.R0, w.t0, w.accepted);
+}
+
+extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double* energies) {
+    if (!ctx || !m) return LC_ERR_ARG;
+    lc_status s;
+    if ((s = ctx->check_solve_state("lc_warm_start"))) return s;
+    if (m->device != ctx->device) return ctx->fail(LC_ERR_ARG, "lc_warm_start: network on another device");
+    cudaSetDevice(ctx->device);
+    if ((s = warm_ensure(ctx))) return s;
+    const int n = ctx->hC.n;
+    if ((s = m->ensure(n))) return ctx->fail(s, "lc_warm_start: network scratch");
+    WarmState& w = *ctx->warm;
+    cudaStream_t st = ctx->stream;
+    if (w.gexec && (w.g_uid != m->uid || w.g_gen != m->gen)) {
+        cudaGraphExecDestroy(w.gexec);
+        w.gexec = nullptr;
+    }
+    if (!w.gexec) {
+        cudaGraph_t g = nullptr;
+        if ((s = ctx->cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
+        enqueue_warm(ctx, m);
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if ((s = ctx->cuda(e, "end capture"))) return s;
+        const cudaError_t e2 = cudaGraphInstantiate(&w.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if ((s = ctx->cuda(e2, "warm-start graph"))) {
+            w.gexec = nullptr;
+            return s;
+        }
+        w.g_uid = m->uid;
+        w.g_gen = m->gen;
+    }
+    // the network's previous work (training) before its buffers are reused here
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, m->stream);
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    if ((s = ctx->cuda(cudaGraphLaunch(w.gexec, st), "warm-start graph launch"))) return s;
+    ctx->has_vis = true;
     ctx->has_lin = false;
     // the network's later work waits for this use of its buffers
     cudaEvent_t ev2;
@@ -779,7 +826,6 @@ extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double
     cudaEventRecord(ev2, st);
     cudaStreamWaitEvent(m->stream, ev2, 0);
     cudaEventDestroy(ev2);
-    if ((s = ctx->cuda(cudaGetLastError(), "warm start"))) return s;
     if (!accepted && !energies) return LC_OK;
     if (accepted && (s = ctx->copy_to_host(accepted, w.accepted, sizeof(int)))) return s;
     if (energies && (s = ctx->copy_to_host(energies, w.e, 2 * sizeof(double)))) return s;

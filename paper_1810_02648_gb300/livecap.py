@@ -87,6 +87,7 @@ _SIGS = {
     "lc_mlp_gradient": [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)],
     "lc_mlp_train_step": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
     "lc_node_features": [_P, _P],
+    "lc_read_stats": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_record_motion": [_P],
     "lc_warm_start": [_P, _P, ctypes.POINTER(ctypes.c_int), _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
@@ -258,6 +259,12 @@ class Context:
         s = lc_solve_stats()
         self._check(self._lib.lc_solve_nonrigid(self.h, ctypes.byref(s)))
         return s.to_dict()
+
+    def read_stats(self) -> dict:
+        """Statistics of the last non-rigid solve."""
+        st = lc_solve_stats()
+        self._check(self._lib.lc_read_stats(self.h, ctypes.byref(st)))
+        return st.to_dict()
 
     def read_back(self, R=True, t=True, V=True, flags=True, pose=False):
         out = {}

@@ -19,6 +19,9 @@ from .scenes import (  # noqa: F401
     value_noise_albedo,
     half_split_material,
     smooth_deformation,
+    rbf_field,
+    ar1_sequence,
+    render_frame,
     render,
     contour_distance_transform,
     make_scene,

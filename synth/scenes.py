@@ -356,6 +356,36 @@ def _euler_xyz(a: np.ndarray) -> np.ndarray:
     return out
 
 
+def _rbf_width(c: np.ndarray) -> float:
+    n_ctrl = len(c)
+    if n_ctrl < 2:
+        return 0.1
+    d2c = ((c[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2c, np.inf)
+    return float(np.sqrt(d2c.min(axis=1)).mean())
+
+
+def rbf_field(V: np.ndarray, ctrl: np.ndarray, aa: np.ndarray, tt: np.ndarray, rho: float) -> np.ndarray:
+    """Blend of the control points' rigid motions (rotation ``aa`` about the
+    control point, then translation ``tt``) with normalised Gaussian RBFs of
+    width ``rho``: the generator's own smooth deformation model."""
+    V = np.asarray(V, dtype=np.float64)
+    R = _rodrigues(aa)
+    out = np.empty_like(V)
+    chunk = 8192
+    for s in range(0, len(V), chunk):
+        v = V[s:s + chunk]
+        d2 = ((v[:, None, :] - ctrl[None, :, :]) ** 2).sum(-1)
+        lw = -d2 / (2.0 * rho * rho)
+        lw -= lw.max(axis=1, keepdims=True)
+        phi = np.exp(lw)
+        phi /= phi.sum(axis=1, keepdims=True)
+        rel = v[:, None, :] - ctrl[None, :, :]
+        moved = np.einsum("mij,nmj->nmi", R, rel) + ctrl[None] + tt[None]
+        out[s:s + chunk] = np.einsum("nm,nmi->ni", phi, moved)
+    return out
+
+
 def smooth_deformation(V: np.ndarray, n_ctrl: int, sigma_rot: float,
                        sigma_t: float, seed: int) -> Dict[str, np.ndarray]:
     """Ground-truth non-rigid deformation on random control points.
@@ -372,23 +402,36 @@ def smooth_deformation(V: np.ndarray, n_ctrl: int, sigma_rot: float,
     c = V[ids]
     aa = rng.normal(0.0, sigma_rot, size=(n_ctrl, 3))
     tt = rng.normal(0.0, sigma_t, size=(n_ctrl, 3))
-    R = _rodrigues(aa)
-    d2c = ((c[:, None, :] - c[None, :, :]) ** 2).sum(-1)
-    np.fill_diagonal(d2c, np.inf)
-    rho = float(np.sqrt(d2c.min(axis=1)).mean()) if n_ctrl > 1 else 0.1
-    out = np.empty_like(V)
-    chunk = 8192
-    for s in range(0, len(V), chunk):
-        v = V[s:s + chunk]
-        d2 = ((v[:, None, :] - c[None, :, :]) ** 2).sum(-1)
-        lw = -d2 / (2.0 * rho * rho)
-        lw -= lw.max(axis=1, keepdims=True)
-        phi = np.exp(lw)
-        phi /= phi.sum(axis=1, keepdims=True)
-        rel = v[:, None, :] - c[None, :, :]
-        moved = np.einsum("mij,nmj->nmi", R, rel) + c[None] + tt[None]
-        out[s:s + chunk] = np.einsum("nm,nmi->ni", phi, moved)
-    return dict(V=out, ctrl_ids=ids, aa=aa, t=tt, rho=rho)
+    rho = _rbf_width(c)
+    return dict(V=rbf_field(V, c, aa, tt, rho), ctrl_ids=ids, aa=aa, t=tt, rho=rho)
+
+
+def ar1_sequence(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma_t: float,
+                 seed: int, rho_ar: float = 0.9) -> List[np.ndarray]:
+    """Deformed vertex positions of a sequence whose control-point rotations
+    and translations follow AR(1): x_t = rho x_{t-1} + sqrt(1 - rho^2) sigma
+    eps_t, started from the stationary distribution."""
+    rng = np.random.default_rng(seed + 3000)
+    V = np.asarray(V, dtype=np.float64)
+    ids = np.sort(rng.choice(len(V), size=n_ctrl, replace=False))
+    c = V[ids]
+    rho = _rbf_width(c)
+    aa = rng.normal(0.0, sigma_rot, size=(n_ctrl, 3))
+    tt = rng.normal(0.0, sigma_t, size=(n_ctrl, 3))
+    k = math.sqrt(1.0 - rho_ar * rho_ar)
+    out = []
+    for _ in range(n_frames):
+        out.append(rbf_field(V, c, aa, tt, rho))
+        aa = rho_ar * aa + k * rng.normal(0.0, sigma_rot, size=aa.shape)
+        tt = rho_ar * tt + k * rng.normal(0.0, sigma_t, size=tt.shape)
+    return out
+
+
+def render_frame(V_target: np.ndarray, F: np.ndarray, albedo: np.ndarray, cam: Camera, seed: int,
+                 noise: float = 0.01):
+    """(rgb, dt, mask) of a target frame: rendering + N(0, noise) + the
+    silhouette's contour distance transform."""
+    return _finish_frame(V_target, F, albedo, cam, np.random.default_rng(seed), noise)
 
 
 def pose_body(tpl: dict, root_R: np.ndarray, root_t: np.ndarray,

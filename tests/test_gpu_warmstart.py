@@ -225,3 +225,75 @@ def test_solve_stops_at_target_energy():
     ctx.set_node_params(None, None)
     assert ctx.solve_nonrigid()["e_total"] == full["e_total"]
     ctx.close()
+
+
+def _render_seq(args):
+    import synth as _synth
+    s, n_frames = args
+    scene = _synth.make_scene("tiny")
+    Vs = _synth.ar1_sequence(scene.V, n_frames, 64, 0.05, 0.01, seed=s)
+    return [_synth.render_frame(v, scene.F, scene.albedo, scene.cam, seed=10000 * s + i) for i, v in enumerate(Vs)]
+
+
+def _tiny_sequences(seeds, n_frames):
+    import multiprocessing as mp
+    import os
+    with mp.get_context("spawn").Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+        return pool.map(_render_seq, [(s, n_frames) for s in seeds])
+
+
+def _restart(ctx):
+    ctx.set_node_params(None, None)
+    ctx.record_motion()
+    ctx.record_motion()          # motion zero: the previous state is the identity too
+
+
+def test_learned_warm_start_gain():
+    """Train on tracked AR(1) sequences of the capsule (control-point motion
+    rho 0.9), evaluate on a held-out sequence: the warm-started solve (up to
+    twice the plain step budget, stopping at the plain final energy within
+    1e-4) must reach that energy in nearly every frame with fewer
+    Gauss-Newton steps on average; the frames/s gain (device time of warm
+    start + solve vs the plain solve) is reported."""
+    import torch
+    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import warmstart as ws
+    tiny = synth.make_scene("tiny")
+    seqs = _tiny_sequences(list(range(1, 41)) + [999], 41)
+    train_seqs, eval_seq = seqs[:-1], seqs[-1]
+    sp, sw = torch.cuda.Stream(), torch.cuda.Stream()
+    plain = Context(0, stream=sp)
+    setup_scene(plain, tiny)
+    Fs, Ts = [], []
+    for seq in train_seqs:
+        _restart(plain)
+        F, T, _ = ws.collect(plain, seq)
+        Fs.append(F[1:])                    # the first frame starts from the identity
+        Ts.append(T[1:])
+    pred, losses = ws.train(np.concatenate(Fs), np.concatenate(Ts), steps=4000, batch=2048, lr=1e-3,
+                            seed=0, log_every=500)
+    warm = Context(0, stream=sw)
+    setup_scene(warm, tiny)
+    warm.set_params(n_gn=2 * tiny.n_gn)
+    for c in (plain, warm):
+        _restart(c)
+    ws.collect(plain, eval_seq[:1])         # the first frame, plain from the identity
+    r0 = plain.read_back(V=False, flags=False)
+    warm.set_node_params(r0["R"].reshape(-1, 9), r0["t"])
+    warm.record_motion()
+    res = ws.evaluate(plain, warm, pred, eval_seq[1:], (sp, sw))
+    steps_plain = np.mean([r["steps_plain"] for r in res])
+    reached = np.mean([r["reached"] for r in res])
+    steps_reached = [r["steps_warm"] for r in res if r["reached"]]
+    gain = np.sum([r["plain_ms"] for r in res]) / np.sum([r["warm_ms"] for r in res])
+    report("warm_start_gain_tiny", loss_first=losses[0][1], loss_last=losses[-1][1], steps_plain=steps_plain,
+           steps_warm_mean=np.mean([r["steps_warm"] for r in res]),
+           steps_warm_median_reached=float(np.median(steps_reached)), reached=reached,
+           frames_per_s_gain=gain, frames=len(res), rows=int(sum(len(f) for f in Fs) * tiny.n_nodes),
+           plain_ms=np.mean([r["plain_ms"] for r in res]), warm_ms=np.mean([r["warm_ms"] for r in res]))
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    assert reached >= 0.75
+    assert np.median(steps_reached) < steps_plain
+    pred.close()
+    plain.close()
+    warm.close()
