@@ -432,9 +432,20 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
         cleanup();
         return LC_ERR_OOM;
     }
+    constexpr int kFpsMaxCtas = 4096;
+    double* fps_val = (double*)salloc(sizeof(double) * 2 * kFpsMaxCtas);
+    int* fps_idx = (int*)salloc(sizeof(int) * 2 * kFpsMaxCtas);
+    if (!ctx->err.empty()) {
+        cleanup();
+        return LC_ERR_OOM;
+    }
     cudaMemsetAsync(gs.status, 0, sizeof(int), st);
     // nodes and bindings on the rest template
-    launch_fps(ctx->tpl, N, n, gs.dist, (int*)C.node_vid, st);
+    if (!launch_fps(ctx->tpl, N, n, gs.dist, (int*)C.node_vid, fps_val, fps_idx, kFpsMaxCtas, st)) {
+        cudaGetLastError();
+        cleanup();
+        return ctx->fail(LC_ERR_CUDA, "lc_build_graph: cooperative launch of the node sampling failed");
+    }
     float4* G_tpl = (float4*)salloc(sizeof(float4) * n);
     launch_gather_nodes(ctx->tpl, C.node_vid, n, G_tpl, st);
     launch_bind(ctx->tpl, N, G_tpl, n, K, (int*)C.bind_idx, (float*)C.bind_w, st);

@@ -10,7 +10,13 @@
 // the FP32 coordinates as (dx*dx + dy*dy) + dz*dz with every operation
 // rounded separately, ties broken by the lower index, so any implementation
 // following that recipe selects the same nodes and neighbours.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
 #include "lc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lc {
 
@@ -22,22 +28,47 @@ __device__ __forceinline__ double d2_exact(float4 a, float4 b) {
 }
 
 // ---------------------------------------------------------------------------
-// Farthest-point sampling: one CTA of 1024 threads iterates over the nodes.
+// Farthest-point sampling, cooperative over the whole GPU: each CTA owns a
+// contiguous range of vertices and their running minimum distance; per node
+// every CTA publishes its farthest vertex (largest distance, lowest index on
+// ties), one grid barrier, and every CTA reduces the partials in the same
+// way, so all agree on the next node.  GB300's FP64 rate per SM is low, so
+// the exact FP64 distance work is spread over every SM.
 // ---------------------------------------------------------------------------
-constexpr int kFpsThreads = 1024;
+constexpr int kFpsThreads = 256;
+
+__device__ __forceinline__ void argmax_merge(double& bd, int& bi, double od, int oi) {
+    if (od > bd || (od == bd && oi < bi)) {
+        bd = od;
+        bi = oi;
+    }
+}
+
+__device__ __forceinline__ void warp_argmax(double& bd, int& bi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(bd, bi, od, oi);
+    }
+}
 
 __global__ void __launch_bounds__(kFpsThreads) fps_kernel(const float4* __restrict__ V, int N, int n,
-                                                           double* __restrict__ dist, int* __restrict__ node_vid) {
-    __shared__ double sd[32];
-    __shared__ int si[32];
+                                                           double* __restrict__ dist, int* __restrict__ node_vid,
+                                                           double* __restrict__ pval, int* __restrict__ pidx) {
+    __shared__ double sd[kFpsThreads / 32];
+    __shared__ int si[kFpsThreads / 32];
     __shared__ int chosen;
+    cg::grid_group grid = cg::this_grid();
+    const int G = gridDim.x, b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lo = (int)((long long)N * b / G), hi = (int)((long long)N * (b + 1) / G);
     float4 q = V[0];
-    if (threadIdx.x == 0) node_vid[0] = 0;
-    for (int it = 1; it <= n; ++it) {
+    if (b == 0 && threadIdx.x == 0) node_vid[0] = 0;
+    for (int it = 1; it < n; ++it) {
         double bd = -1.0;
         int bi = 0x7fffffff;
-        for (int i = threadIdx.x; i < N; i += kFpsThreads) {
+        for (int i = lo + threadIdx.x; i < hi; i += kFpsThreads) {
             double d = d2_exact(V[i], q);
             if (it > 1) d = fmin(d, dist[i]);
             dist[i] = d;
@@ -46,36 +77,27 @@ __global__ void __launch_bounds__(kFpsThreads) fps_kernel(const float4* __restri
                 bi = i;
             }
         }
-        if (it == n) break;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double od = __shfl_xor_sync(0xffffffffu, bd, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (od > bd || (od == bd && oi < bi)) {
-                bd = od;
-                bi = oi;
-            }
-        }
+        warp_argmax(bd, bi);
         if (lane == 0) {
             sd[wid] = bd;
             si[wid] = bi;
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kFpsThreads / 32; ++w) argmax_merge(bd, bi, sd[w], si[w]);
+            pval[(it & 1) * G + b] = bd;
+            pidx[(it & 1) * G + b] = bi;
+        }
+        grid.sync();
         if (wid == 0) {
-            bd = sd[lane];
-            bi = si[lane];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double od = __shfl_xor_sync(0xffffffffu, bd, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (od > bd || (od == bd && oi < bi)) {
-                    bd = od;
-                    bi = oi;
-                }
-            }
+            bd = -1.0;
+            bi = 0x7fffffff;
+            for (int c = lane; c < G; c += 32) argmax_merge(bd, bi, __ldcg(&pval[(it & 1) * G + c]),
+                                                            __ldcg(&pidx[(it & 1) * G + c]));
+            warp_argmax(bd, bi);
             if (lane == 0) {
                 chosen = bi;
-                node_vid[it] = bi;
+                if (b == 0) node_vid[it] = bi;
             }
         }
         __syncthreads();
@@ -83,8 +105,18 @@ __global__ void __launch_bounds__(kFpsThreads) fps_kernel(const float4* __restri
     }
 }
 
-void launch_fps(const float4* V, int N, int n, double* dist, int* node_vid, cudaStream_t st) {
-    fps_kernel<<<1, kFpsThreads, 0, st>>>(V, N, n, dist, node_vid);
+// Returns false if the cooperative launch is not possible (the caller then
+// reports an error).
+bool launch_fps(const float4* V, int N, int n, double* dist, int* node_vid, double* pval, int* pidx, int max_ctas,
+                cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fps_kernel, kFpsThreads, 0);
+    int G = std::min({sms * std::max(per_sm, 1), (N + kFpsThreads - 1) / kFpsThreads, max_ctas});
+    G = std::max(G, 1);
+    void* args[] = {(void*)&V, (void*)&N, (void*)&n, (void*)&dist, (void*)&node_vid, (void*)&pval, (void*)&pidx};
+    return cudaLaunchCooperativeKernel((const void*)fps_kernel, dim3(G), dim3(kFpsThreads), args, 0, st) == cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

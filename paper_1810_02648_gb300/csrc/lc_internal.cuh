@@ -359,7 +359,10 @@ struct GraphScratch {
     int* ent_fill;      // n
     int* status;        // 1
 };
-void launch_fps(const float4* V, int N, int n, double* dist, int* node_vid, cudaStream_t st);
+// farthest-point sampling as one cooperative launch over the GPU (at most
+// max_ctas CTAs; pval / pidx hold 2 * max_ctas partials); false if the launch failed
+bool launch_fps(const float4* V, int N, int n, double* dist, int* node_vid, double* pval, int* pidx, int max_ctas,
+                cudaStream_t st);
 void launch_bind(const float4* V, int N, const float4* G, int n, int K, int* idx, float* w, cudaStream_t st);
 void launch_node_edges_count(const float4* G, int n, GraphScratch& s, cudaStream_t st);
 void launch_node_edges_fill(const float4* G, int n, const float* material, const int* node_vid,

@@ -131,7 +131,7 @@ def test_visibility_partially_outside():
 # ---------------------------------------------------------------------------
 # per-kernel floating-point parity at identical inputs
 # ---------------------------------------------------------------------------
-def _lin_case(scene, seed, tag, pcg_kernel=0):
+def _lin_case(scene, seed, tag, pcg_kernel=0, pcg_counts=None):
     ctx = _ctx(scene, pcg_kernel=pcg_kernel)
     n = scene.n_nodes
     R, t = random_params(n, seed)
@@ -188,7 +188,8 @@ def _lin_case(scene, seed, tag, pcg_kernel=0):
     # amplification sets in) within 1e-5 and 1e-4.
     A = (JT @ J).tocsr()
     q = lambda d: 0.5 * d @ (A @ d) - rhs_ref @ d  # noqa: E731
-    for n_pcg, tol in ((1, 1e-5), (3, 1e-4), (scene.n_pcg, 5e-2)):
+    counts = pcg_counts or ((1, 1e-5), (3, 1e-4), (scene.n_pcg, 5e-2))
+    for n_pcg, tol in counts:
         ctx.set_params(n_pcg=n_pcg)
         delta, iters = ctx.solve_linear()
         dref, info = onr.pcg(A, rhs_ref, n_pcg)
