@@ -351,11 +351,13 @@ void lc_ctx::free_graph() {
     warm_release();
     void* bufs[] = {(void*)hC.node_vid, (void*)hC.bind_idx, (void*)hC.bind_w, (void*)hC.node_g, (void*)hC.ent_off,
                     (void*)hC.ent, (void*)hC.edge_off, (void*)hC.edge_dst, (void*)hC.edge_s, hC.node_R, hC.node_t,
+                    hC.vA, hC.eA, hC.dB,
                     hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2};
     for (void* p : bufs) release(p);
     hC.node_vid = nullptr; hC.bind_idx = nullptr; hC.bind_w = nullptr; hC.node_g = nullptr;
     hC.ent_off = nullptr; hC.ent = nullptr; hC.edge_off = nullptr; hC.edge_dst = nullptr; hC.edge_s = nullptr;
     hC.node_R = nullptr; hC.node_t = nullptr;
+    hC.vA = hC.eA = hC.dB = nullptr;
     hC.b = hC.minv = hC.diag = hC.x = hC.r = hC.z = hC.p = hC.Ap = nullptr;
     tmp_vec = tmp_vec2 = nullptr;
     pcg_plan_ok = false;
@@ -465,6 +467,9 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     C.E = E;
     C.edge_dst = (const int*)ctx->alloc(sizeof(int) * std::max(E, 1));
     C.edge_s = (const float*)ctx->alloc(sizeof(float) * std::max(E, 1));
+    C.vA = (float4*)ctx->alloc(sizeof(float4) * (size_t)N * K);
+    C.eA = (float4*)ctx->alloc(sizeof(float4) * (size_t)N * K);
+    C.dB = (float4*)ctx->alloc(sizeof(float4) * 2 * (size_t)std::max(E, 1));
     launch_node_edges_fill(G_tpl, n, ctx->material, C.node_vid, gs, C.edge_off, (int*)C.edge_dst, (float*)C.edge_s, st);
     launch_entries(C.bind_idx, C.bind_w, N, K, n, gs, (int*)C.ent_off, (int2*)C.ent, st);
     // node positions of the current rest geometry
@@ -616,6 +621,7 @@ void lc_ctx::enqueue_pcg() {
         return;
     }
     mark(LC_PH_PCG_INIT);
+    launch_jtj_stage(dC, hC, stream);
     launch_pcg_init(dC, hC, stream);
     for (int it = 0; it < params.n_pcg; ++it) {
         mark(LC_PH_JTJ);
@@ -961,6 +967,7 @@ extern "C" lc_status lc_apply_jtj(lc_ctx* ctx, const float* p, float* out) {
     if ((s = ctx->cuda(cudaMemcpyAsync(ctx->tmp_out(), hp.data(), sizeof(float) * 6 * n, cudaMemcpyHostToDevice, ctx->stream), "upload")))
         return s;
     launch_pack_vec(ctx->tmp_out(), ctx->tmp_vec, n, ctx->stream);
+    launch_jtj_stage(ctx->dC, ctx->hC, ctx->stream);
     launch_jtj(ctx->dC, ctx->hC, ctx->tmp_vec, ctx->tmp_vec2, false, ctx->stream);
     if ((s = ctx->cuda(cudaGetLastError(), "jtj"))) return s;
     return ctx->vec_out(out, ctx->tmp_vec2);

@@ -256,6 +256,7 @@ void lc_batch::enqueue(bool from_identity) {
         for (const BatchGroup& g : groups)
             launch_pcg_cluster(dC + g.first, g.plan, g.K, n_pcg, st, g.count);
         if (multi.vec) {
+            launch_jtj_stage(dC, multi, st);
             launch_pcg_init(dC, multi, st);
             for (int it = 0; it < n_pcg; ++it) {
                 launch_jtj(dC, multi, nullptr, nullptr, true, st);
@@ -462,6 +463,7 @@ extern "C" lc_status lc_batch_apply_jtj(lc_batch* b) {
     if (!b) return LC_ERR_ARG;
     if (!b->solved) return b->fail(LC_ERR_STATE, "lc_batch_apply_jtj: no batch solve yet");
     cudaSetDevice(b->device);
+    launch_jtj_stage(b->dC, b->all, b->stream);
     launch_jtj(b->dC, b->all, nullptr, nullptr, false, b->stream);
     if (cudaGetLastError() != cudaSuccess) return b->fail(LC_ERR_CUDA, "lc_batch_apply_jtj: launch");
     return LC_OK;

@@ -101,6 +101,10 @@ struct CapDesc {
     float4* p;
     float4* Ap;
     float4* q;               // per-vertex H_i dv_i scratch (N)
+    // operands of the per-iteration J^T J p, staged once per linearisation
+    float4* vA;              // N*K: (R_k (v_i - g_k), w_is) per binding, 0 weight for inactive vertices
+    float4* eA;              // N*K: the same per node -> vertex CSR entry
+    float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)
     // reductions
     double* part;            // per-tile partials of the running reduction
     unsigned* counters;      // CNT_N
@@ -320,6 +324,10 @@ void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaS
 void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, cudaStream_t st);
+// rotated offsets of bindings, entries and edges for the per-iteration J^T J p
+// (once per linearisation; node parameters and activity must be current)
+void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 // p / out null: each capture's own p and Ap
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st);

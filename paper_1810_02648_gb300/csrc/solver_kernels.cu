@@ -252,7 +252,65 @@ void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only
 
 // ---------------------------------------------------------------------------
 // J^T J p: vertex phase (q_i = H_i dv_i), node phase (gather + ARAP).
+//
+// The rotated offsets a_is = R_k (v_i - g_k) of every binding, of every node
+// -> vertex entry, and of every node edge do not change during the PCG, so
+// they are staged once per linearisation (the kernels below); the PCG's
+// J^T J p then reads them coalesced instead of gathering node rotations and
+// positions, and skips inactive vertices without touching them.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVertTile) jtj_stage_vertex_kernel(const CapDesc* __restrict__ caps,
+                                                                      const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    if (C.sc->gn_stop) return;
+    const int i = tile * kVertTile + threadIdx.x;
+    if (i >= C.N) return;
+    const bool active = C.ev[i].w != 0.f;
+    const float3 v = f3(C.base[i]);
+    const int K = C.K;
+    for (int s = 0; s < K; ++s) {
+        const size_t e = (size_t)i * K + s;
+        const int k = C.bind_idx[e];
+        const float3 a = mul(load_R(C.node_R, k), v - f3(C.node_g[k]));
+        C.vA[e] = make_float4(a.x, a.y, a.z, active ? C.bind_w[e] : 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const CapDesc* __restrict__ caps,
+                                                                          const WorkItem* __restrict__ items) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    if (C.sc->gn_stop) return;
+    const int lane = threadIdx.x & 31;
+    const int k = tile * kNodeTile + (threadIdx.x >> 5);
+    if (k >= C.n) return;
+    const Rot R = load_R(C.node_R, k);
+    const float3 g = f3(C.node_g[k]);
+    for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
+        const int2 en = C.ent[j];
+        const bool active = C.ev[en.x].w != 0.f;
+        const float3 a = mul(R, f3(C.base[en.x]) - g);
+        C.eA[j] = make_float4(a.x, a.y, a.z, active ? __int_as_float(en.y) : 0.f);
+    }
+    for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
+        const int l = C.edge_dst[j];
+        const float3 gl = f3(C.node_g[l]);
+        const float3 b = mul(R, gl - g);
+        const float3 bl = mul(load_R(C.node_R, l), g - gl);
+        C.dB[2 * j] = make_float4(b.x, b.y, b.z, C.w_arap * C.edge_s[j]);
+        C.dB[2 * j + 1] = make_float4(bl.x, bl.y, bl.z, 0.f);
+    }
+}
+
+void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
+    jtj_stage_vertex_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
+    jtj_stage_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items);
+}
+void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_jtj_stage(dC, single_tiles(hC), st); }
+
 __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items,
                                                                 const float4* __restrict__ p_in, int check_stop) {
@@ -263,21 +321,15 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
     const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's PCG direction
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
-    const float4 e4 = C.ev[i];
-    if (e4.w == 0.f) {
-        C.q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    const float3 v = f3(C.base[i]);
     const int K = C.K;
+    const float4* __restrict__ A = C.vA + (size_t)i * K;
+    if (A[0].w == 0.f) return;   // inactive vertex: no entry of the node phase reads its q
     float3 dv = make_float3(0.f, 0.f, 0.f);
     for (int s = 0; s < K; ++s) {
+        const float4 a = A[s];
         const int k = C.bind_idx[(size_t)i * K + s];
-        const float w = C.bind_w[(size_t)i * K + s];
-        const Rot R = load_R(C.node_R, k);
-        const float3 a = mul(R, v - f3(C.node_g[k]));
         const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
-        dv = dv + w * (cross3(pw, a) + pt);
+        dv = dv + a.w * (cross3(pw, f3(a)) + pt);
     }
     const float3 q = mulH(C.HA[i], C.HB[i], dv);
     C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
@@ -298,34 +350,26 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     const int k = tile * kNodeTile + w;
     double pap[1] = {0.0};
     if (k < C.n) {
-        const Rot R = load_R(C.node_R, k);
-        const float3 g = f3(C.node_g[k]);
         const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
-            const int2 en2 = C.ent[j];
-            const float4 q4 = C.q[en2.x];
-            if (q4.w == 0.f) continue;
-            const float wi = __int_as_float(en2.y);
-            const float3 a = mul(R, f3(C.base[en2.x]) - g);
-            const float3 q = f3(q4);
-            const float3 c = cross3(a, q);
-            acc[0] += wi * c.x; acc[1] += wi * c.y; acc[2] += wi * c.z;
-            acc[3] += wi * q.x; acc[4] += wi * q.y; acc[5] += wi * q.z;
+            const float4 a = C.eA[j];
+            if (a.w == 0.f) continue;
+            const float3 q = f3(C.q[C.ent[j].x]);
+            const float3 c = cross3(f3(a), q);
+            acc[0] += a.w * c.x; acc[1] += a.w * c.y; acc[2] += a.w * c.z;
+            acc[3] += a.w * q.x; acc[4] += a.w * q.y; acc[5] += a.w * q.z;
         }
         for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
             const int l = C.edge_dst[j];
-            const float c = C.w_arap * C.edge_s[j];
-            const float3 gl = f3(C.node_g[l]);
+            const float4 bk = C.dB[2 * j], bl = C.dB[2 * j + 1];
+            const float c = bk.w;
             const float3 plw = f3(p[2 * l]), plt = f3(p[2 * l + 1]);
-            const float3 b = mul(R, gl - g);
-            const float3 D = cross3(pw, b) + pt - plt;
-            const float3 bD = cross3(b, D);
+            const float3 D = cross3(pw, f3(bk)) + pt - plt;
+            const float3 bD = cross3(f3(bk), D);
             acc[0] += c * bD.x; acc[1] += c * bD.y; acc[2] += c * bD.z;
             acc[3] += c * D.x; acc[4] += c * D.y; acc[5] += c * D.z;
-            const Rot Rl = load_R(C.node_R, l);
-            const float3 bl = mul(Rl, g - gl);
-            const float3 Dl = cross3(plw, bl) + plt - pt;
+            const float3 Dl = cross3(plw, f3(bl)) + plt - pt;
             acc[3] -= c * Dl.x; acc[4] -= c * Dl.y; acc[5] -= c * Dl.z;
         }
         warp_sumf<6>(acc);
