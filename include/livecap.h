@@ -306,8 +306,10 @@ void *lc_batch_stream(const lc_batch *batch);
 /* One matrix-free J^T J p of every member in one launch pair (vertex phase,
  * node phase), at each member's current linearisation with p = its PCG
  * direction, result into its A p buffer: the metric kernel on its own, for
- * measurement.  Requires a previous lc_batch_solve.  Enqueue only. */
-lc_status lc_batch_apply_jtj(lc_batch *batch);
+ * measurement.  stage != 0 first recomputes the rotated offsets it reads
+ * (once per linearisation in a solve); stage == 0 reuses them.  Requires a
+ * previous lc_batch_solve.  Enqueue only. */
+lc_status lc_batch_apply_jtj(lc_batch *batch, int stage);
 
 /* ---- learned warm start (the project's addition to the paper's solver) ---- */
 

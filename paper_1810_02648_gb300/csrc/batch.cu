@@ -459,11 +459,11 @@ extern "C" lc_status lc_batch_autotune(lc_batch* b, int reps, int* mode_out, flo
 
 extern "C" void* lc_batch_stream(const lc_batch* b) { return b ? (void*)b->stream : nullptr; }
 
-extern "C" lc_status lc_batch_apply_jtj(lc_batch* b) {
+extern "C" lc_status lc_batch_apply_jtj(lc_batch* b, int stage) {
     if (!b) return LC_ERR_ARG;
     if (!b->solved) return b->fail(LC_ERR_STATE, "lc_batch_apply_jtj: no batch solve yet");
     cudaSetDevice(b->device);
-    launch_jtj_stage(b->dC, b->all, b->stream);
+    if (stage) launch_jtj_stage(b->dC, b->all, b->stream);
     launch_jtj(b->dC, b->all, nullptr, nullptr, false, b->stream);
     if (cudaGetLastError() != cudaSuccess) return b->fail(LC_ERR_CUDA, "lc_batch_apply_jtj: launch");
     return LC_OK;

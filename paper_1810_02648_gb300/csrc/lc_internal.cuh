@@ -330,7 +330,9 @@ void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 // p / out null: each capture's own p and Ap
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
-void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st);
+// K: the captures' common K selects an unrolled vertex phase (0: any K)
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st,
+                int K = 0);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);

@@ -311,6 +311,32 @@ void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
 }
 void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_jtj_stage(dC, single_tiles(hC), st); }
 
+template <int KT>
+__device__ __forceinline__ float3 vertex_dv(const float4* __restrict__ A, const int* __restrict__ idx,
+                                            const float4* __restrict__ p, int K) {
+    // all K (offset, node) pairs loaded before the p gathers, so the loads of
+    // the slots are in flight together
+    constexpr int KM = KT > 0 ? KT : kMaxK;
+    const int kk = KT > 0 ? KT : K;
+    float4 a[KM];
+    int k[KM];
+#pragma unroll
+    for (int s = 0; s < KM; ++s)
+        if (s < kk) {
+            a[s] = A[s];
+            k[s] = idx[s];
+        }
+    float3 dv = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < KM; ++s)
+        if (s < kk) {
+            const float3 pw = f3(p[2 * k[s]]), pt = f3(p[2 * k[s] + 1]);
+            dv = dv + a[s].w * (cross3(pw, f3(a[s])) + pt);
+        }
+    return dv;
+}
+
+template <int KT>
 __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items,
                                                                 const float4* __restrict__ p_in, int check_stop) {
@@ -324,13 +350,7 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
     const int K = C.K;
     const float4* __restrict__ A = C.vA + (size_t)i * K;
     if (A[0].w == 0.f) return;   // inactive vertex: no entry of the node phase reads its q
-    float3 dv = make_float3(0.f, 0.f, 0.f);
-    for (int s = 0; s < K; ++s) {
-        const float4 a = A[s];
-        const int k = C.bind_idx[(size_t)i * K + s];
-        const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
-        dv = dv + a.w * (cross3(pw, f3(a)) + pt);
-    }
+    const float3 dv = vertex_dv<KT>(A, C.bind_idx + (size_t)i * K, p, K);
     const float3 q = mulH(C.HA[i], C.HB[i], dv);
     C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
 }
@@ -352,13 +372,30 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     if (k < C.n) {
         const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
-            const float4 a = C.eA[j];
-            if (a.w == 0.f) continue;
-            const float3 q = f3(C.q[C.ent[j].x]);
-            const float3 c = cross3(f3(a), q);
-            acc[0] += a.w * c.x; acc[1] += a.w * c.y; acc[2] += a.w * c.z;
-            acc[3] += a.w * q.x; acc[4] += a.w * q.y; acc[5] += a.w * q.z;
+        // four rounds of the node's entries at a time: their loads are issued
+        // together before any result is used
+        constexpr int U = 4;
+        const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
+        for (int jb = e0 + lane; jb < e1; jb += 32 * U) {
+            float4 a[U];
+            int vi[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = jb + 32 * u;
+                a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                vi[u] = j < e1 ? C.ent[j].x : 0;
+            }
+            float4 q4[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) q4[u] = a[u].w != 0.f ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float3 q = f3(q4[u]);
+                const float3 c = cross3(f3(a[u]), q);
+                const float wv = a[u].w;
+                acc[0] += wv * c.x; acc[1] += wv * c.y; acc[2] += wv * c.z;
+                acc[3] += wv * q.x; acc[4] += wv * q.y; acc[5] += wv * q.z;
+            }
         }
         for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
             const int l = C.edge_dst[j];
@@ -394,12 +431,17 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     });
 }
 
-void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st) {
-    jtj_vertex_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st, int K) {
+    if (K == 4)
+        jtj_vertex_kernel<4><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+    else if (K == 8)
+        jtj_vertex_kernel<8><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+    else
+        jtj_vertex_kernel<0><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
     jtj_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, p, out, dot ? 1 : 0);
 }
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st) {
-    launch_jtj(dC, single_tiles(hC), p, out, dot, st);
+    launch_jtj(dC, single_tiles(hC), p, out, dot, st, hC.K);
 }
 
 // ---------------------------------------------------------------------------

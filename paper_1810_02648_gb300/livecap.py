@@ -78,7 +78,7 @@ _SIGS = {
     "lc_batch_solve": [_P, ctypes.c_int, ctypes.POINTER(lc_solve_stats)],
     "lc_batch_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P],
     "lc_batch_stream": [_P],
-    "lc_batch_apply_jtj": [_P],
+    "lc_batch_apply_jtj": [_P, ctypes.c_int],
     "lc_mlp_create": [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P],
     "lc_mlp_destroy": [_P],
     "lc_mlp_last_error": [_P],
@@ -491,9 +491,10 @@ class Batch:
         """The batch's cudaStream_t as an integer."""
         return self._lib.lc_batch_stream(self.h) or 0
 
-    def apply_jtj(self):
-        """Enqueue one J^T J p of every member (measurement entry)."""
-        self._check(self._lib.lc_batch_apply_jtj(self.h))
+    def apply_jtj(self, stage: bool = False):
+        """Enqueue one J^T J p of every member (measurement entry); stage
+        recomputes the operands it reads first."""
+        self._check(self._lib.lc_batch_apply_jtj(self.h, int(stage)))
 
     def autotune(self, reps: int = 3):
         mode = ctypes.c_int(-1)
