@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch"], default="body")
+    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch", "warmstart"], default="body")
+    ap.add_argument("--ws-train-seqs", type=int, default=24, help="warm start: training sequences")
+    ap.add_argument("--ws-frames", type=int, default=21, help="warm start: frames per sequence")
     ap.add_argument("--batch-count", type=int, default=64, help="captures of the batch workload")
     ap.add_argument("--pcg-mode", type=int, default=-1, help="batch PCG strategy (-1: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample length")
@@ -537,12 +539,99 @@ def run_batch(a):
         c.close()
 
 
+# ---------------------------------------------------------------------------
+# learned warm start on tracked sequences of the body capture
+# ---------------------------------------------------------------------------
+def _ws_sequence(args):
+    seed, n_frames = args
+    sys.path.insert(0, ROOT)
+    import synth
+    sc = synth.make_scene("body")
+    Vs = synth.ar1_sequence(sc.V, n_frames, sc.n_nodes, 0.05, 0.01, seed=seed)
+    return [synth.render_frame(v, sc.F, sc.albedo, sc.cam, seed=100000 + 1000 * seed + i) for i, v in enumerate(Vs)]
+
+
+def run_warmstart(a):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import warmstart as ws
+
+    seeds = list(range(1, a.ws_train_seqs + 1)) + [9999]
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        seqs = pool.map(_ws_sequence, [(s, a.ws_frames) for s in seeds])
+    train_seqs, eval_seq = seqs[:-1], seqs[-1]
+    sc = synth.make_scene("body")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sp, sw = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    plain = Context(0, stream=sp)
+    setup_scene(plain, sc)
+    t0 = time.perf_counter()
+    Fs, Ts = [], []
+    for seq in train_seqs:
+        plain.set_node_params(None, None)
+        plain.record_motion()
+        plain.record_motion()
+        F, T, _ = ws.collect(plain, seq)
+        Fs.append(F[1:])
+        Ts.append(T[1:])
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pred, losses = ws.train(np.concatenate(Fs), np.concatenate(Ts), steps=4000, batch=4096, lr=1e-3, seed=0,
+                            log_every=1000)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    warm = Context(0, stream=sw)
+    setup_scene(warm, sc)
+    warm.set_params(n_gn=2 * sc.n_gn)
+    for c in (plain, warm):
+        c.set_node_params(None, None)
+        c.record_motion()
+        c.record_motion()
+    ws.collect(plain, eval_seq[:1])
+    r0 = plain.read_back(V=False, flags=False)
+    warm.set_node_params(r0["R"].reshape(-1, 9), r0["t"])
+    warm.record_motion()
+    res = ws.evaluate(plain, warm, pred, eval_seq[1:], (sp, sw))
+    plain_ms = float(np.sum([r["plain_ms"] for r in res]))
+    warm_ms = float(np.sum([r["warm_ms"] for r in res]))
+    reached = [r for r in res if r["reached"]]
+    value = len(res) / (warm_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(res), "warmup": 1,
+        "ms_per_step": warm_ms / len(res), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 solver, bf16 network", "data": "synthetic",
+        "config": {"workload": f"warm start: body capture ({sc.N} vertices, {sc.n_nodes} nodes, K={sc.K}, "
+                               f"{sc.cam.W}x{sc.cam.H}), AR(1) sequences (rho 0.9, 0.05 rad / 1 cm), "
+                               f"plain {sc.n_gn} GN x {sc.n_pcg} PCG from the previous frame vs warm start + GN "
+                               f"until the plain final energy (1e-4), budget {2 * sc.n_gn} steps",
+                   "train_sequences": len(train_seqs), "frames_per_sequence": a.ws_frames,
+                   "train_rows": int(sum(len(f) for f in Fs) * sc.n_nodes), "adam_steps": 4000},
+        "warm_start": {"plain_frames_per_s": len(res) / (plain_ms / 1e3), "gain": plain_ms / warm_ms,
+                       "reached_fraction": len(reached) / len(res),
+                       "steps_plain": float(np.mean([r["steps_plain"] for r in res])),
+                       "steps_warm_median_reached": float(np.median([r["steps_warm"] for r in reached]))
+                       if reached else None,
+                       "loss_first": losses[0][1], "loss_last": losses[-1][1],
+                       "collect_s": t_collect, "train_s": t_train},
+    }
+    print(json.dumps(line))
+    pred.close()
+    plain.close()
+    warm.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "warmstart":
+        run_warmstart(a)
     else:
         run_ours(a)
 
