@@ -45,6 +45,7 @@ struct Scalars {
     int gn_stop;       // the solve reached its target energy: later GN steps are skipped
     int gn_done;       // GN updates made in the current solve (gn_stop, gn_done are reset together)
     int vis_frozen;    // keep the frame decisions (V, B) of the start for the next solve
+    float alpha, beta_f;   // PCG step lengths in FP32 (FP64 sums divided in FP32)
 };
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
@@ -233,6 +234,33 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV]) {
             double s = 0.0;
             for (int i = 0; i < NWARPS; ++i) s += sh[i][j];
             v[j] = s;
+        }
+    }
+}
+
+// Block-wide sum of NV per-thread FP32 values: FP32 inside the block (fixed
+// shuffle tree, then the warps' sums in warp order by thread 0), returned in
+// FP64 in thread 0 for the FP64 sum across tiles.  Per-thread FP64 work is
+// avoided: GB300 runs FP64 at ~1.7 lane-operations per clock per SM.
+template <int NV, int NWARPS>
+__device__ __forceinline__ void block_sum_f(float (&v)[NV], double (&out)[NV], float (*sh)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[w][j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j] = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float s = 0.f;
+            for (int i = 0; i < NWARPS; ++i) s += sh[i][j];
+            out[j] = (double)s;
         }
     }
 }

@@ -70,13 +70,13 @@ __device__ __forceinline__ float4 grad_y(const CapDesc& C, int x, int y) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __restrict__ caps,
                                                                const WorkItem* __restrict__ items, int update_b) {
-    __shared__ double sh[kVertTile / 32][2];
+    __shared__ float sh[kVertTile / 32][2];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (update_b && C.sc->gn_stop) return;   // a GN step after the solve reached its target
     const int i = tile * kVertTile + threadIdx.x;
-    double en[2] = {0.0, 0.0};
+    float enf[2] = {0.f, 0.f};
     if (i < C.N) {
         uint32_t fl = C.flags[i];
         const float4 v = C.vw[i];
@@ -121,14 +121,14 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
                 add_row(Gx.x, Gy.x, sw, res.x);
                 add_row(Gx.y, Gy.y, sw, res.y);
                 add_row(Gx.z, Gy.z, sw, res.z);
-                en[0] = (double)res.x * res.x + (double)res.y * res.y + (double)res.z * res.z;
+                enf[0] = res.x * res.x + res.y * res.y + res.z * res.z;
             }
             if (si) {
                 const float sw = sqrtf(C.w_sil);
                 res.w = sw * I.w;
                 const float bs = (fl & LC_BNEG_BIT) ? -sw : sw;
                 add_row(Gx.w, Gy.w, bs, res.w);
-                en[1] = (double)res.w * res.w;
+                enf[1] = res.w * res.w;
             }
         }
         C.res[i] = res;
@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         C.HB[i] = make_float4(h12, h22, 0.f, 0.f);
         C.ev[i] = make_float4(e0, e1, e2, (ph || si) ? 1.f : 0.f);
     }
-    block_sum<2, kVertTile / 32>(en, sh);
+    double en[2];
+    block_sum_f<2, kVertTile / 32>(enf, en, sh);
     reduce_partials<2>(C, CNT_ENERGY, tile, C.vert_tiles, en, [&](const double (&tot)[2]) {
         C.sc->e_lin[0] = tot[0];
         C.sc->e_lin[1] = tot[1];
@@ -156,14 +157,14 @@ void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaS
 __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __restrict__ caps,
                                                                const WorkItem* __restrict__ items, int slot,
                                                                int energy_only) {
-    __shared__ double sh[kNodeWarps][1];
+    __shared__ float sh[kNodeWarps][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (!energy_only && C.sc->gn_stop) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = tile * kNodeTile + w;
-    double en[1] = {0.0};
+    float enf[1] = {0.f};
     if (k < C.n) {
         const Rot R = load_R(C.node_R, k);
         const float3 g = f3(C.node_g[k]), t = f3(C.node_t[k]);
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
                 acc[9] += w2 * HA.x; acc[10] += w2 * HA.w; acc[11] += w2 * HB.y;
             }
         }
-        double arap = 0.0;
+        float arap = 0.f;
         for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
             const int l = C.edge_dst[j];
             const float c = C.w_arap * C.edge_s[j];
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
             // for the identity parameters
             const float3 dg = gl - g;
             const float3 d = (b - dg) + t - tl;
-            arap += (double)c * (double)dot3(d, d);
+            arap += c * dot3(d, d);
             if (energy_only) continue;
             const float3 bd = cross3(b, d);
             acc[0] += c * bd.x; acc[1] += c * bd.y; acc[2] += c * bd.z;
@@ -231,9 +232,10 @@ __global__ void __launch_bounds__(kNodeWarps * 32) rhs_kernel(const CapDesc* __r
                 C.diag[2 * k + 1] = make_float4(acc[9], acc[10], acc[11], 0.f);
             }
         }
-        en[0] = arap;
+        enf[0] = arap;
     }
-    block_sum<1, kNodeWarps>(en, sh);
+    double en[1];
+    block_sum_f<1, kNodeWarps>(enf, en, sh);
     reduce_partials<1>(C, CNT_ARAP, tile, C.node_tiles, en, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->e_lin[2] = tot[0];
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
                                                                     const WorkItem* __restrict__ items,
                                                                     const float4* __restrict__ p_in,
                                                                     float4* __restrict__ out_in, int dot) {
-    __shared__ double sh[kNodeWarps][1];
+    __shared__ float sh[kNodeWarps][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     float4* __restrict__ out = out_in ? out_in : C.Ap;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = tile * kNodeTile + w;
-    double pap[1] = {0.0};
+    float papf[1] = {0.f};
     if (k < C.n) {
         const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -414,19 +416,20 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
             out[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
             out[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
         }
-        if (dot && lane == 0) {
-            pap[0] = (double)pw.x * acc[0] + (double)pw.y * acc[1] + (double)pw.z * acc[2] +
-                     (double)pt.x * acc[3] + (double)pt.y * acc[4] + (double)pt.z * acc[5];
-        }
+        if (dot && lane == 0)
+            papf[0] = pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
     }
     if (!dot) return;
-    block_sum<1, kNodeWarps>(pap, sh);
+    double pap[1];
+    block_sum_f<1, kNodeWarps>(papf, pap, sh);
     reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, pap, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->pAp = tot[0];
         if (!(tot[0] > 0.0)) {
             sc->stop = 1;
             sc->breakdown = 1;
+        } else {
+            sc->alpha = __fdiv_rn((float)sc->rz, (float)tot[0]);
         }
     });
 }
@@ -447,9 +450,7 @@ void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* o
 // ---------------------------------------------------------------------------
 // PCG vector kernels (node-parallel, 2 float4 per node, FP64 dots).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dot4(float4 a, float4 b) {
-    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
-}
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
 __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
     return make_float4(y.x + a * x.x, y.y + a * x.y, y.z + a * x.z, y.w + a * x.w);
@@ -457,13 +458,13 @@ __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
 
 __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items) {
-    __shared__ double sh[kVecThreads / 32][1];
+    __shared__ float sh[kVecThreads / 32][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
-    double rz[1] = {0.0};
+    float rzf[1] = {0.f};
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
             const float4 b = C.b[2 * k + h];
@@ -472,11 +473,12 @@ __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __
             C.r[2 * k + h] = b;
             C.z[2 * k + h] = z;
             C.p[2 * k + h] = z;
-            rz[0] += dot4(b, z);
+            rzf[0] += dot4(b, z);
         }
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    block_sum<1, kVecThreads / 32>(rz, sh);
+    double rz[1];
+    block_sum_f<1, kVecThreads / 32>(rzf, rz, sh);
     reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->rz = tot[0];
@@ -488,15 +490,15 @@ __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __
 
 __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items) {
-    __shared__ double sh[kVecThreads / 32][1];
+    __shared__ float sh[kVecThreads / 32][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
     if (sc->stop || sc->gn_stop) return;
-    const float alpha = (float)(sc->rz / sc->pAp);
+    const float alpha = sc->alpha;
     const int k = tile * kVecThreads + threadIdx.x;
-    double rz[1] = {0.0};
+    float rzf[1] = {0.f};
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * k + h;
@@ -506,19 +508,21 @@ __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __
             const float4 z = mul4(C.minv[j], r);
             C.r[j] = r;
             C.z[j] = z;
-            rz[0] += dot4(r, z);
+            rzf[0] += dot4(r, z);
         }
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    block_sum<1, kVecThreads / 32>(rz, sh);
+    double rz[1];
+    block_sum_f<1, kVecThreads / 32>(rzf, rz, sh);
     reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
         sc->iters += 1;
         sc->rz_new = tot[0];
         if (tot[0] == 0.0) {
             sc->stop = 1;
         } else {
-            // every other tile has read rz already (it finished before this one)
+            // every other tile has read its inputs already (it finished before this one)
             sc->beta = tot[0] / sc->rz;
+            sc->beta_f = __fdiv_rn((float)tot[0], (float)sc->rz);
             sc->rz = tot[0];
         }
     });
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __r
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
     if (sc->stop || sc->gn_stop) return;
-    const float beta = (float)sc->beta;
+    const float beta = sc->beta_f;
     const int k = tile * kVecThreads + threadIdx.x;
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
@@ -559,16 +563,16 @@ void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __restrict__ caps,
                                                               const WorkItem* __restrict__ items, int slot) {
-    __shared__ double sh[kVecThreads / 32][1];
+    __shared__ float sh[kVecThreads / 32][1];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
-    double s2[1] = {0.0};
+    float s2f[1] = {0.f};
     if (k < C.n) {
         const float4 xw = C.x[2 * k], xt = C.x[2 * k + 1];
-        s2[0] = dot4(xw, xw) + dot4(xt, xt);
+        s2f[0] = dot4(xw, xw) + dot4(xt, xt);
         const float th2 = xw.x * xw.x + xw.y * xw.y + xw.z * xw.z;
         const float th = sqrtf(th2);
         float A, B;
@@ -598,7 +602,8 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
         C.node_t[k] = make_float4(t.x + xt.x, t.y + xt.y, t.z + xt.z, 0.f);
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    block_sum<1, kVecThreads / 32>(s2, sh);
+    double s2[1];
+    block_sum_f<1, kVecThreads / 32>(s2f, s2, sh);
     reduce_partials<1>(C, CNT_STEP, tile, ntiles, s2, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->step2 = tot[0];
