@@ -71,8 +71,12 @@ typedef struct {
                            no silhouette are otherwise undetermined) */
     int pcg_kernel;     /* 0 (default): one cluster-persistent kernel runs all PCG
                            iterations of a Gauss-Newton step when the capture's
-                           per-CTA data fits in shared memory; 1: one launch per
-                           PCG phase (J^T J p, vector updates) */
+                           per-CTA data fits in shared memory, else one launch
+                           per PCG phase; 1: one launch per PCG phase (J^T J p,
+                           vector updates); 2: one grid-persistent cooperative
+                           kernel over the GPU (four grid barriers per
+                           iteration: slower than 1 on GB300, kept for
+                           comparison) */
     float target_energy; /* 0 (default): run all n_gn steps.  > 0: the non-rigid
                            solve stops at the first step whose linearisation
                            energy is <= target_energy (the remaining steps are
@@ -276,10 +280,11 @@ lc_status lc_eval_pose(lc_ctx *ctx, float *V_skinned, double *A, double *g, doub
 typedef struct lc_batch lc_batch;
 
 /* PCG strategy of a batch: */
-#define LC_BATCH_PCG_AUTO 0           /* each capture as on its own (smallest cluster that fits) */
+#define LC_BATCH_PCG_AUTO 0           /* each capture as on its own (smallest cluster that fits,
+                                         else the batched per-iteration kernels) */
 #define LC_BATCH_PCG_CLUSTER8 1       /* 8-CTA clusters where they fit, else per-iteration kernels */
 #define LC_BATCH_PCG_CLUSTER16 2      /* 16-CTA clusters where they fit, else per-iteration kernels */
-#define LC_BATCH_PCG_PER_ITERATION 3  /* per-iteration kernels for every capture */
+#define LC_BATCH_PCG_PER_ITERATION 3  /* per-iteration kernels for every capture, batched */
 
 /* ctxs: count >= 1 context handles (the caller keeps ownership; they must
  * outlive the batch).  LC_ERR_STATE if a member is not ready, LC_ERR_ARG if

@@ -142,7 +142,11 @@ extern "C" lc_status lc_create(lc_ctx** out, int device, void* cuda_stream) {
     c->hC.counters = (unsigned*)c->alloc(sizeof(unsigned) * CNT_N);
     c->hC.hist = (double*)c->alloc(sizeof(double) * 2 * (LC_MAX_GN + 1));
     c->hC.hist_iters = (int*)c->alloc(sizeof(int) * (LC_MAX_GN + 2));
-    if (!c->dC || !c->hC.sc || !c->hC.counters || !c->hC.hist || !c->hC.hist_iters) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    c->grid_pcg_ok = coop != 0;
+    c->grid_part = (float*)c->alloc(sizeof(float) * 2 * std::max(pcg_grid_max_ctas(), 1));
+    if (!c->dC || !c->hC.sc || !c->hC.counters || !c->hC.hist || !c->hC.hist_iters || !c->grid_part) {
         lc_destroy(c);
         return LC_ERR_OOM;
     }
@@ -190,7 +194,7 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->target_energy >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
-    if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
+    if (p->pcg_kernel < 0 || p->pcg_kernel > 2) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0, 1 or 2");
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel)
         ctx->drop_graph();
     if (p->n_gn_pose != ctx->params.n_gn_pose) ctx->pose_drop_graph();
@@ -618,6 +622,12 @@ void lc_ctx::enqueue_pcg() {
     if (use_cluster_pcg()) {
         mark(LC_PH_PCG);
         launch_pcg_cluster(dC, pcg_plan, hC.K, params.n_pcg, stream);
+        return;
+    }
+    if (use_grid_pcg()) {
+        mark(LC_PH_PCG);
+        launch_jtj_stage(dC, hC, stream);
+        launch_pcg_grid(dC, hC.K, params.n_pcg, grid_part, stream);
         return;
     }
     mark(LC_PH_PCG_INIT);

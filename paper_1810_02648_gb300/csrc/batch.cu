@@ -86,6 +86,8 @@ struct lc_batch {
     int pix_blocks = 0;
     std::vector<BatchGroup> groups;   // captures on the cluster PCG
     int mode = LC_BATCH_PCG_AUTO;
+    int first_multi = 0;              // first slot on the per-iteration / grid PCG
+    bool grid_multi = false;          // the non-cluster members all use the grid-persistent PCG
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
     bool gexec_identity = false;
@@ -186,7 +188,9 @@ lc_status lc_batch::build() {
         groups.push_back(g);
         s = e;
     }
-    const int first_multi = s;
+    first_multi = s;
+    grid_multi = mode != LC_BATCH_PCG_PER_ITERATION && first_multi < count;
+    for (int j = first_multi; j < count; ++j) grid_multi = grid_multi && ctxs[order[j]]->use_grid_pcg();
     slot_of.assign(count, 0);
     ctx_of.assign(count, 0);
     snap.resize(count);
@@ -257,10 +261,16 @@ void lc_batch::enqueue(bool from_identity) {
             launch_pcg_cluster(dC + g.first, g.plan, g.K, n_pcg, st, g.count);
         if (multi.vec) {
             launch_jtj_stage(dC, multi, st);
-            launch_pcg_init(dC, multi, st);
-            for (int it = 0; it < n_pcg; ++it) {
-                launch_jtj(dC, multi, nullptr, nullptr, true, st);
-                launch_pcg_vectors(dC, multi, st);
+            if (!grid_multi) {
+                launch_pcg_init(dC, multi, st);
+                for (int it = 0; it < n_pcg; ++it) {
+                    launch_jtj(dC, multi, nullptr, nullptr, true, st);
+                    launch_pcg_vectors(dC, multi, st);
+                }
+            } else {
+                // members that asked for the grid-persistent PCG (pcg_kernel 2), one at a time
+                for (int j = first_multi; j < (int)snap.size(); ++j)
+                    launch_pcg_grid(dC + j, snap[j].K, n_pcg, ctxs[ctx_of[j]]->grid_part, st);
             }
         }
         launch_update(dC, all, gn, st);

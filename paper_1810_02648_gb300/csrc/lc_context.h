@@ -40,6 +40,9 @@ struct lc_ctx {
     lc::PcgPlan pcg_plan{};
     bool pcg_plan_ok = false;     // the cluster-persistent PCG fits this capture
     bool use_cluster_pcg() const { return pcg_plan_ok && params.pcg_kernel == 0; }
+    float* grid_part = nullptr;   // partial sums of the grid-persistent PCG
+    bool grid_pcg_ok = false;     // the device supports cooperative launches
+    bool use_grid_pcg() const { return grid_pcg_ok && params.pcg_kernel == 2; }
     void enqueue_pcg();
     PoseState* pose = nullptr;
     WarmState* warm = nullptr;    // learned warm start (warmstart.cu)

@@ -379,6 +379,10 @@ struct PcgPlan {
     size_t smem;     // dynamic shared memory bytes
 };
 bool plan_pcg_cluster(int n, int K, const int* ent_off_host, const int* edge_off_host, PcgPlan* out);
+// grid-persistent PCG of capture 0 of dC (cooperative launch over the GPU);
+// part holds 2 * pcg_grid_max_ctas() floats
+int pcg_grid_max_ctas();
+cudaError_t launch_pcg_grid(const CapDesc* dC, int K, int n_pcg, float* part, cudaStream_t st);
 // one cluster per capture: captures 0 .. ncap-1 of dC, all fitting the plan
 cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st, int ncap = 1);
 // a plan that fits every capture of a group (same K): per-CTA capacities are

@@ -15,7 +15,13 @@
 // node, shuffle reductions), so there are no floating-point atomics and every
 // result is deterministic.  Dot products and energies accumulate in FP64 and
 // are reduced per capture by the last tile to finish, in tile order.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
 #include "lc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lc {
 
@@ -556,6 +562,240 @@ void launch_pcg_vectors(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
 }
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     launch_pcg_vectors(dC, single_tiles(hC), st);
+}
+
+// ---------------------------------------------------------------------------
+// Grid-persistent PCG: all n_pcg iterations of one Gauss-Newton step in one
+// cooperative launch over the whole GPU, for captures whose data does not fit
+// a cluster's shared memory.  Per iteration: the vertex phase (q_i), a grid
+// barrier, the node phase (A p and the CTA's p.Ap partial), a barrier, every
+// CTA sums the partials in the same fixed order (FP64 across CTAs) for
+// alpha, the vector phase (x, r, z and the r.z partial), a barrier, beta the
+// same way, p = z + beta p, a barrier.  Operands are the staged rotated
+// offsets (jtj_stage_*); vectors live in global memory (L2).
+// ---------------------------------------------------------------------------
+constexpr int kGridThreads = 256;
+
+__device__ __forceinline__ double grid_total(const float* __restrict__ part, int G) {
+    // warp 0: lanes add CTAs lane, lane + 32, ... then a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int c = lane; c < G; c += 32) v += (double)__ldcg(&part[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float block_total_f32(float v, float* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kGridThreads / 32; ++i) t += sh[i];
+    return t;   // thread 0
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kGridThreads) pcg_grid_kernel(const CapDesc* __restrict__ caps, int n_pcg,
+                                                                 float* __restrict__ part) {
+    __shared__ float sh[kGridThreads / 32];
+    __shared__ float s_scal[2];   // alpha / beta of this iteration (thread 0 -> block)
+    __shared__ int s_stop;
+    cg::grid_group grid = cg::this_grid();
+    const CapDesc& C = caps[0];
+    if (C.sc->gn_stop) return;   // uniform: read before any barrier
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int gtid = b * kGridThreads + tid, gthreads = G * kGridThreads;
+    const int lane = tid & 31, gwarp = gtid >> 5, gwarps = gthreads >> 5;
+    const int n = C.n, N = C.N, K = C.K;
+    float* partA = part;        // G: p.Ap partials
+    float* partB = part + G;    // G: r.z partials
+    // x = 0, r = b, z = M^-1 r, p = z; r.z
+    float rz_p = 0.f;
+    for (int j = gtid; j < 2 * n; j += gthreads) {
+        const float4 bb = C.b[j], mi = C.minv[j];
+        const float4 z = make_float4(mi.x * bb.x, mi.y * bb.y, mi.z * bb.z, 0.f);
+        C.x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        C.r[j] = bb;
+        C.z[j] = z;
+        C.p[j] = z;
+        rz_p += bb.x * z.x + bb.y * z.y + bb.z * z.z;
+    }
+    {
+        const float t = block_total_f32(rz_p, sh);
+        if (tid == 0) partB[b] = t;
+    }
+    grid.sync();
+    double rz = 0.0;
+    if (tid < 32) rz = grid_total(partB, G);
+    if (tid == 0) s_stop = rz == 0.0 ? 1 : 0;
+    __syncthreads();
+    rz = __shfl_sync(0xffffffffu, rz, 0);
+    int iters = 0, breakdown = 0;
+    int stop = s_stop;
+    for (int it = 0; it < n_pcg && !stop; ++it) {
+        // vertex phase: q_i = H_i dv_i for the active vertices
+        for (int i = gtid; i < N; i += gthreads) {
+            const float4* __restrict__ A = C.vA + (size_t)i * K;
+            if (A[0].w == 0.f) continue;
+            const float3 dv = vertex_dv<KT>(A, C.bind_idx + (size_t)i * K, C.p, K);
+            const float3 q = mulH(C.HA[i], C.HB[i], dv);
+            C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
+        }
+        grid.sync();
+        // node phase: (J^T J p)_k, warp per node; p.Ap partial of the CTA
+        float pap = 0.f;
+        for (int k = gwarp; k < n; k += gwarps) {
+            const float3 pw = f3(C.p[2 * k]), pt = f3(C.p[2 * k + 1]);
+            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            constexpr int U = 4;
+            const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
+            for (int jb = e0 + lane; jb < e1; jb += 32 * U) {
+                float4 a[U];
+                int vi[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = jb + 32 * u;
+                    a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    vi[u] = j < e1 ? C.ent[j].x : 0;
+                }
+                float4 q4[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) q4[u] = a[u].w != 0.f ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float3 q = f3(q4[u]);
+                    const float3 c = cross3(f3(a[u]), q);
+                    const float wv = a[u].w;
+                    acc[0] += wv * c.x; acc[1] += wv * c.y; acc[2] += wv * c.z;
+                    acc[3] += wv * q.x; acc[4] += wv * q.y; acc[5] += wv * q.z;
+                }
+            }
+            for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
+                const int l = C.edge_dst[j];
+                const float4 bk = C.dB[2 * j], bl = C.dB[2 * j + 1];
+                const float c = bk.w;
+                const float3 plw = f3(C.p[2 * l]), plt = f3(C.p[2 * l + 1]);
+                const float3 D = cross3(pw, f3(bk)) + pt - plt;
+                const float3 bD = cross3(f3(bk), D);
+                acc[0] += c * bD.x; acc[1] += c * bD.y; acc[2] += c * bD.z;
+                acc[3] += c * D.x; acc[4] += c * D.y; acc[5] += c * D.z;
+                const float3 Dl = cross3(plw, f3(bl)) + plt - pt;
+                acc[3] -= c * Dl.x; acc[4] -= c * Dl.y; acc[5] -= c * Dl.z;
+            }
+            warp_sumf<6>(acc);
+            if (lane == 0) {
+                C.Ap[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                C.Ap[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+                pap += pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
+            }
+        }
+        {
+            const float t = block_total_f32(pap, sh);
+            if (tid == 0) partA[b] = t;
+        }
+        grid.sync();
+        if (tid < 32) {
+            const double pAp = grid_total(partA, G);
+            if (tid == 0) {
+                if (!(pAp > 0.0)) {
+                    s_stop = 1;
+                } else {
+                    // the step length is applied in FP32: the FP64 sums are divided in FP32
+                    s_scal[0] = __fdiv_rn((float)rz, (float)pAp);
+                    s_stop = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) {
+            stop = 1;
+            breakdown = 1;
+            break;
+        }
+        const float alpha = s_scal[0];
+        // vector phase: x, r, z; r.z partial
+        float rzp = 0.f;
+        for (int j = gtid; j < 2 * n; j += gthreads) {
+            const float4 pp = C.p[j], ap = C.Ap[j], mi = C.minv[j];
+            float4 x = C.x[j], r = C.r[j];
+            x.x += alpha * pp.x; x.y += alpha * pp.y; x.z += alpha * pp.z;
+            r.x -= alpha * ap.x; r.y -= alpha * ap.y; r.z -= alpha * ap.z;
+            const float4 z = make_float4(mi.x * r.x, mi.y * r.y, mi.z * r.z, 0.f);
+            C.x[j] = x;
+            C.r[j] = r;
+            C.z[j] = z;
+            rzp += r.x * z.x + r.y * z.y + r.z * z.z;
+        }
+        {
+            const float t = block_total_f32(rzp, sh);
+            if (tid == 0) partB[b] = t;
+        }
+        grid.sync();
+        ++iters;
+        double rz_new = 0.0;
+        if (tid < 32) {
+            rz_new = grid_total(partB, G);
+            if (tid == 0) {
+                if (rz_new == 0.0) {
+                    s_stop = 1;
+                } else {
+                    s_scal[1] = __fdiv_rn((float)rz_new, (float)rz);
+                    s_stop = 0;
+                }
+            }
+        }
+        __syncthreads();
+        rz = rz_new;   // meaningful in warp 0; only thread 0 reports it
+        if (s_stop) {
+            stop = 1;
+            break;
+        }
+        const float beta = s_scal[1];
+        for (int j = gtid; j < 2 * n; j += gthreads) {
+            const float4 pp = C.p[j], z = C.z[j];
+            C.p[j] = make_float4(z.x + beta * pp.x, z.y + beta * pp.y, z.z + beta * pp.z, 0.f);
+        }
+        grid.sync();
+    }
+    if (b == 0 && tid == 0) {
+        Scalars* sc = C.sc;
+        sc->iters = iters;
+        sc->breakdown = breakdown;
+        sc->stop = stop;
+        sc->rz = rz;
+    }
+}
+
+static int pcg_grid_ctas(const void* kern) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGridThreads, 0);
+    return std::max(1, std::min(2, per_sm) * sms);
+}
+
+int pcg_grid_max_ctas() { return pcg_grid_ctas((const void*)pcg_grid_kernel<0>); }
+
+cudaError_t launch_pcg_grid(const CapDesc* dC, int K, int n_pcg, float* part, cudaStream_t st) {
+    const void* kern = K == 4 ? (const void*)pcg_grid_kernel<4>
+                               : (K == 8 ? (const void*)pcg_grid_kernel<8> : (const void*)pcg_grid_kernel<0>);
+    const int G = pcg_grid_ctas(kern);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kGridThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if (K == 4) return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<4>, dC, n_pcg, part);
+    if (K == 8) return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<8>, dC, n_pcg, part);
+    return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<0>, dC, n_pcg, part);
 }
 
 // ---------------------------------------------------------------------------

@@ -201,12 +201,12 @@ def _lin_case(scene, seed, tag, pcg_kernel=0, pcg_counts=None):
     ctx.close()
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1])
+@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
 def test_linearization_tiny(tiny, pcg_kernel):
     _lin_case(tiny, 11, f"tiny_k{pcg_kernel}", pcg_kernel)
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1])
+@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
 def test_linearization_body(body, pcg_kernel):
     _lin_case(body, 12, f"body_k{pcg_kernel}", pcg_kernel)
 
@@ -270,12 +270,12 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
     return stats
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1])
+@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
 def test_end_to_end_tiny_strict(tiny, pcg_kernel):
     _e2e(tiny, f"tiny_pcg3_k{pcg_kernel}", n_pcg=3, pcg_kernel=pcg_kernel)
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1])
+@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
 def test_end_to_end_tiny(tiny, pcg_kernel):
     _e2e(tiny, f"tiny_k{pcg_kernel}", strict=False, pcg_kernel=pcg_kernel)
 
