@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 The paper starts each frame's non-rigid solve from the previous frame's
 result (Sec. 3.4, Sec. 4).  The project adds a small network that predicts
 each graph node's update so that Gauss-Newton starts closer; plain GN stays
-the judge (a prediction that raises the energy is rejected).  This module is
+the arbiter (a prediction that raises the energy is rejected).  This module is
 the reference the BF16 kernels are checked against.
 
 Network (64 -> 256 -> 256 -> 6, 83,974 parameters), on normalised inputs

@@ -4,7 +4,7 @@
 //
 // The paper starts each frame from the previous frame's result; the network
 // predicts each node's update (d_omega, d_t) from features pooled at that
-// start so that Gauss-Newton starts closer.  Plain GN stays the judge: the
+// start so that Gauss-Newton starts closer.  Plain GN stays the arbiter: the
 // prediction is kept only if the energy at the predicted parameters does not
 // exceed the energy at the start (decided on the device).
 //
