@@ -21,6 +21,9 @@ visibility  the integer / FP32-exact decisions: z-buffer visibility, the
 pose        the skeletal stage-1 fit (Sec. 3.3): forward kinematics, linear
             blend skinning, 2D / 3D joint and silhouette residuals, dense
             normal equations solved by a Cholesky factorisation.
+surface     the paper's own per-vertex formulation of the non-rigid stage
+            (unknowns V; E_smooth, E_edge, E_velocity, E_acceleration beside
+            the data terms), its sparse Jacobian and Gauss-Newton, in FP64.
 mlp         the learned per-node warm start network in FP64 (forward,
             backward, Adam), the reference for the BF16 kernels.
 """

@@ -558,6 +558,14 @@ def contour_distance_transform(mask: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Scenes
 # ----------------------------------------------------------------------------
+# Weights of the per-vertex surface stage.  The paper's values (w_photo 1e4,
+# w_silhouette 600, w_smooth 10, w_edge 30, w_velocity 0.25, w_acceleration
+# 0.1) read with positions in millimetres; the regularisers are rescaled by
+# 1e6 for metres and all weights by 1e-4 so that w_photo = 1 as in the graph
+# stage, whose silhouette weight 0.1 is kept.
+SURFACE_WEIGHTS = (1.0, 0.1, 1.0e3, 3.0e3, 25.0, 10.0)
+
+
 @dataclasses.dataclass
 class Scene:
     """Everything one capture needs, as FP32/int32 arrays ready for upload."""
@@ -582,6 +590,11 @@ class Scene:
     joints3d: Optional[np.ndarray] = None
     pose_init: Optional[np.ndarray] = None   # (57,) f32
     n_gn_pose: int = 5
+    # per-vertex surface stage: (w_photo, w_sil, w_smooth, w_edge, w_velocity,
+    # w_acceleration) and its Gauss-Newton / PCG counts
+    surface_weights: tuple = SURFACE_WEIGHTS
+    n_gn_surface: int = 3
+    n_pcg_surface: int = 4
     meta: dict = dataclasses.field(default_factory=dict)
 
     @property
