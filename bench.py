@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch", "warmstart"], default="body")
+    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch", "warmstart", "surface",
+                                           "surface-stress"], default="body",
+                    help="surface*: the per-vertex surface stage (the paper's own unknowns) in place of the "
+                         "embedded graph, on the body / stress capture")
     ap.add_argument("--ws-train-seqs", type=int, default=24, help="warm start: training sequences")
     ap.add_argument("--ws-frames", type=int, default=21, help="warm start: frames per sequence")
     ap.add_argument("--batch-count", type=int, default=64, help="captures of the batch workload")
@@ -54,36 +57,59 @@ def parse():
     return ap.parse_args()
 
 
-def stages_of(scene):
+def is_surface(workload):
+    return workload.startswith("surface")
+
+
+def scene_name(workload):
+    """Capture of a workload: the surface workloads run on the body / stress
+    captures."""
+    return {"surface": "body", "surface-stress": "stress"}.get(workload, workload)
+
+
+def stages_of(scene, surface=False):
+    stage2 = "per-vertex surface stage" if surface else "non-rigid stage"
     if scene.skeleton is not None:
         return (f"pose stage ({len(scene.skeleton['parents'])} joints, {len(scene.pose_init)} DOF, "
-                f"{scene.n_gn_pose} GN) + non-rigid stage")
-    return "non-rigid stage"
+                f"{scene.n_gn_pose} GN) + {stage2}")
+    return stage2
 
 
-def workload_config(scene):
-    cfg = {"workload": f"{scene.name}: {scene.N} vertices / {len(scene.F)} triangles, "
-                       f"{scene.n_nodes} nodes K={scene.K}, {scene.cam.W}x{scene.cam.H} frame, "
-                       f"{stages_of(scene)}, {scene.n_gn} GN x {scene.n_pcg} PCG",
-           "vertices": int(scene.N), "triangles": int(len(scene.F)), "nodes": int(scene.n_nodes),
-           "K": int(scene.K), "image": [int(scene.cam.W), int(scene.cam.H)],
-           "gn_iters": int(scene.n_gn), "pcg_iters": int(scene.n_pcg),
-           "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
+def workload_config(scene, surface=False):
+    if surface:
+        wl = (f"surface ({scene.name} capture): {scene.N} vertices / {len(scene.F)} triangles, "
+              f"{scene.cam.W}x{scene.cam.H} frame, {stages_of(scene, True)}, {scene.n_gn_surface} GN x "
+              f"{scene.n_pcg_surface} PCG over the vertex positions, displacement warping and temporal terms")
+        cfg = {"workload": wl, "vertices": int(scene.N), "triangles": int(len(scene.F)),
+               "image": [int(scene.cam.W), int(scene.cam.H)], "gn_iters": int(scene.n_gn_surface),
+               "pcg_iters": int(scene.n_pcg_surface), "surface_weights": list(scene.surface_weights)}
+    else:
+        cfg = {"workload": f"{scene.name}: {scene.N} vertices / {len(scene.F)} triangles, "
+                           f"{scene.n_nodes} nodes K={scene.K}, {scene.cam.W}x{scene.cam.H} frame, "
+                           f"{stages_of(scene)}, {scene.n_gn} GN x {scene.n_pcg} PCG",
+               "vertices": int(scene.N), "triangles": int(len(scene.F)), "nodes": int(scene.n_nodes),
+               "K": int(scene.K), "image": [int(scene.cam.W), int(scene.cam.H)],
+               "gn_iters": int(scene.n_gn), "pcg_iters": int(scene.n_pcg)}
+    cfg["l2"] = "flushed between timed steps (256 MiB write outside the timed events)"
     if scene.skeleton is not None:
         cfg.update(pose_dof=int(len(scene.pose_init)), pose_gn_iters=int(scene.n_gn_pose))
     return cfg
 
 
-def oracle_frame(scene, g):
+def oracle_frame(scene, g, surface=False):
     """One frame through the oracle: the pose stage from the scene's start
     pose, then the non-rigid stage on the skinned mesh (graph g built once on
-    the template, its nodes following the skinned mesh)."""
+    the template, its nodes following the skinned mesh), or the per-vertex
+    surface stage from the skinned mesh."""
     import numpy as np
     from oracle import nonrigid as onr
     base = None
     if scene.skeleton is not None:
         from oracle import pose as op
         base = op.solve_scene(scene)["VS"].astype(np.float32)
+    if surface:
+        from oracle import surface as osf
+        return osf.solve_scene(scene, base32=base)
     return onr.solve_scene(scene, graph=g, base32=base)
 
 
@@ -91,18 +117,19 @@ def oracle_frame(scene, g):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 def _oracle_worker(args):
-    name, seed, seconds = args
+    workload, seed, seconds = args
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     sys.path.insert(0, ROOT)
     import synth
     from oracle import graph as ograph
-    scene = synth.make_scene(name, seed=seed)
-    g = ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
+    scene = synth.make_scene(scene_name(workload), seed=seed)
+    surface = is_surface(workload)
+    g = None if surface else ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
     t0 = time.perf_counter()
     n = 0
     while True:
-        oracle_frame(scene, g)
+        oracle_frame(scene, g, surface)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
@@ -117,13 +144,13 @@ def cpu_baseline(name, seconds):
     frames = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
     return {"value": frames / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{frames} frame solves ({stages_of(synth_scene(name))}) of the {name} workload by the "
-                      f"FP64 oracle, one single-threaded process per core for ~{seconds:.0f} s"}
+            "sample": f"{frames} frame solves ({stages_of(synth_scene(name), is_surface(name))}) of the {name} "
+                      f"workload by the FP64 oracle, one single-threaded process per core for ~{seconds:.0f} s"}
 
 
-def synth_scene(name):
+def synth_scene(workload):
     import synth
-    return synth.make_scene(name)
+    return synth.make_scene(scene_name(workload))
 
 
 def run_reference(a):
@@ -134,19 +161,20 @@ def run_reference(a):
         os.environ.setdefault(k, "1")
     import synth
     from oracle import graph as ograph
-    scene = synth.make_scene(a.workload)
-    g = ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
+    scene = synth.make_scene(scene_name(a.workload))
+    surface = is_surface(a.workload)
+    g = None if surface else ograph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
     for _ in range(a.warmup):
-        oracle_frame(scene, g)
+        oracle_frame(scene, g, surface)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        oracle_frame(scene, g)
+        oracle_frame(scene, g, surface)
     dt = time.perf_counter() - t0
     v = a.steps / dt
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": workload_config(scene),
+            "impl": "reference", "config": workload_config(scene, surface),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{a.steps} frame solves, one single-threaded process"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -219,6 +247,24 @@ def jtj_algorithmic_bytes(scene, n_active, n_edges):
     return (8 * scene.K + 36) * n_active + 96 * scene.n_nodes + 12 * n_edges
 
 
+def surface_jtj_algorithmic_bytes(N, n_adj):
+    """Minimal bytes of one fused surface J^T J p (direction update included):
+    per vertex z and the previous direction read, H_i read, the new direction
+    and A p written (12 + 12 + 24 + 12 + 12 bytes); per ordered one-ring pair
+    the neighbour index, the staged edge direction and smoothness weight
+    (4 + 12 + 4 bytes)."""
+    return 72 * N + 20 * n_adj
+
+
+def one_ring_pairs(F):
+    """Ordered one-ring pairs of a triangle mesh (twice its unique edges)."""
+    import numpy as np
+    F = np.asarray(F, dtype=np.int64)
+    e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    e.sort(axis=1)
+    return 2 * len(np.unique(e, axis=0))
+
+
 def pcg_vector_bytes(n):
     """PCG vector traffic per iteration if streamed: p read twice, Ap, x, r,
     z, M^-1 read, x, r, z, p written (24 B per node each)."""
@@ -256,7 +302,8 @@ def run_ours(a):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    scene = synth.make_scene(a.workload, seed=None if rank == 0 else 1000 + rank)
+    surface = is_surface(a.workload)
+    scene = synth.make_scene(scene_name(a.workload), seed=None if rank == 0 else 1000 + rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream=stream)
     setup_scene(ctx, scene)
@@ -264,13 +311,20 @@ def run_ours(a):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        # every frame starts from the same pose and the identity deformation
-        # (device-side resets, no host round trip)
+        # every frame starts from the same pose (device-side reset, no host
+        # round trip); the graph stage from the identity deformation, the
+        # surface stage from the skinned mesh plus the warped displacement of
+        # the previous frame, which it then records with its history
         if has_pose:
             ctx.reset_pose()
             ctx.solve_pose(stats=False)
-        ctx.set_node_params(None, None)
-        ctx.solve_nonrigid(stats=False)
+        if surface:
+            ctx.surface_start()
+            ctx.solve_surface(stats=False)
+            ctx.surface_advance()
+        else:
+            ctx.set_node_params(None, None)
+            ctx.solve_nonrigid(stats=False)
 
     for _ in range(a.warmup):
         step()
@@ -278,8 +332,13 @@ def run_ours(a):
     if has_pose:
         ctx.reset_pose()
         pose_stats = ctx.solve_pose(stats=True)
+    if surface:
+        ctx.surface_start()
+        stats = ctx.solve_surface(stats=True)
+        ctx.surface_advance()
+    else:
         ctx.set_node_params(None, None)
-    stats = ctx.solve_nonrigid(stats=True)
+        stats = ctx.solve_nonrigid(stats=True)
     torch.cuda.synchronize(dev)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -314,14 +373,21 @@ def run_ours(a):
         step()
     prof = ctx.read_profile()
     ctx.set_profiling(False)
-    g = ctx.read_graph()
-    E = len(g["edge_dst"])
-    n_active = stats["n_visible"]
-    jtj_bytes = jtj_algorithmic_bytes(scene, n_active, E)
     peak, peak_kind = measured_peaks()
+    if surface:
+        jtj_bytes = surface_jtj_algorithmic_bytes(scene.N, one_ring_pairs(scene.F))
+    else:
+        g = ctx.read_graph()
+        E = len(g["edge_dst"])
+        n_active = stats["n_visible"]
+        jtj_bytes = jtj_algorithmic_bytes(scene, n_active, E)
     # dominant kernel: the cluster-persistent PCG when it is used, else the
-    # per-iteration J^T J p pair
-    if prof["pcg"][1]:
+    # per-iteration J^T J p pair (the fused J^T J p of the surface stage)
+    if surface:
+        k_ms, k_n = prof["jtj"]
+        k_bytes = jtj_bytes
+        k_name = "surface_jtj_kernel (fused direction update + one-ring J^T J p + p.Ap)"
+    elif prof["pcg"][1]:
         k_ms, k_n = prof["pcg"]
         k_bytes = scene.n_pcg * (jtj_bytes + pcg_vector_bytes(scene.n_nodes))
         k_name = "pcg_cluster_kernel (all PCG iterations of one GN step; J^T J p + vectors)"
@@ -353,6 +419,14 @@ def run_ours(a):
         if has_pose:
             ctx._check(lib.lc_reset_pose(ctx.h))
             ctx._check(lib.lc_solve_pose(ctx.h, None))
+        if surface:
+            ctx._check(lib.lc_surface_start(ctx.h))
+            ctx._check(lib.lc_solve_surface(ctx.h, None))
+            ctx._check(lib.lc_surface_advance(ctx.h))
+            ctx._check(lib.lc_read_surface(ctx.h, _ptr(outV), None))
+            if has_pose:
+                ctx._check(lib.lc_read_back(ctx.h, None, None, None, None, _ptr(outP)))
+            return
         ctx._check(lib.lc_set_node_params(ctx.h, None, None))
         ctx._check(lib.lc_solve_nonrigid(ctx.h, None))
         ctx._check(lib.lc_read_back(ctx.h, _ptr(outR), _ptr(outT), _ptr(outV), None,
@@ -367,7 +441,7 @@ def run_ours(a):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     h2d = rgb.numel() * 4 + dtm.numel() * 4 + msk.numel() + ((j2.numel() + j3.numel()) * 4 if has_pose else 0)
-    d2h = (outR.numel() + outT.numel() + outV.numel() + (outP.numel() if has_pose else 0)) * 4
+    d2h = ((0 if surface else outR.numel() + outT.numel()) + outV.numel() + (outP.numel() if has_pose else 0)) * 4
 
     if rank != 0:
         ctx.close()
@@ -376,17 +450,21 @@ def run_ours(a):
         return
     phases = {k: {"ms_per_frame": v[0] / n_prof, "segments_per_frame": v[1] / n_prof}
               for k, v in prof.items() if v[1]}
+    extra_kernels = (5 if has_pose else 3) if surface else 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(scene),
+        "config": workload_config(scene, surface),
         "clocks": clk.summary(),
         "e2e": {"value": world * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         # per frame: the captured non-rigid solve, the identity reset kernel
+        # (surface stage: start and advance, 2 + 3 kernels with a skeleton,
+        # 1 + 2 without)
         # and, with a skeleton, the captured pose solve
-        "gpu_launches": (int(stats["n_kernels"]) + 1 + (int(pose_stats["n_kernels"]) if has_pose else 0)) * a.steps,
+        "gpu_launches": (int(stats["n_kernels"]) + extra_kernels
+                         + (int(pose_stats["n_kernels"]) if has_pose else 0)) * a.steps,
         "roofline": {"kernel": k_name, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
@@ -394,7 +472,10 @@ def run_ours(a):
                      "algorithmic_bytes_per_launch": k_bytes,
                      "jtjp_algorithmic_bytes": jtj_bytes,
                      "avg_launch_us": 1e3 * k_ms / k_n if k_n else None,
-                     "note": ("the capture's working set (~0.3 MB per J^T J p) stays on chip / in L2 across the "
+                     "note": (f"the capture's working set ({jtj_bytes / 1e6:.2f} MB per J^T J p) stays in L2 across "
+                              "the PCG iterations; one CTA per 256 vertices, so the small capture fills few SMs and "
+                              "the kernel is latency-bound") if surface else
+                             ("the capture's working set (~0.3 MB per J^T J p) stays on chip / in L2 across the "
                               "PCG iterations and the kernel is latency-bound (cluster barriers, FP64 reductions), "
                               "so the HBM fraction is low by construction") if prof["pcg"][1] else
                              ("per-iteration J^T J p (the capture does not fit a cluster): the operands stay in "
@@ -402,7 +483,7 @@ def run_ours(a):
         "phases": phases,
         "solve": {"e_total": stats["e_total"], "n_visible": stats["n_visible"],
                   "n_boundary": stats["n_boundary"], "kernels_per_frame": stats["n_kernels"]
-                  + 1 + (pose_stats["n_kernels"] if has_pose else 0),
+                  + extra_kernels + (pose_stats["n_kernels"] if has_pose else 0),
                   "pose_e_total": pose_stats["e_total"] if has_pose else None},
         "cpu_baseline": cpu_base,
     }

@@ -81,7 +81,17 @@ typedef struct {
                            solve stops at the first step whose linearisation
                            energy is <= target_energy (the remaining steps are
                            skipped on the device; stats.n_gn_done counts the
-                           updates made) */
+                           updates made; the surface stage too) */
+    /* per-vertex surface stage (lc_solve_surface), Sec. 3.4 regularisers.
+     * The paper's weights (w_smooth 10, w_edge 30, w_velocity 0.25,
+     * w_acceleration 0.1 beside w_photo 1e4) read with positions in
+     * millimetres, rescaled to metres and to w_photo = 1: */
+    float w_smooth;       /* default 1e3 */
+    float w_edge;         /* default 3e3 */
+    float w_velocity;     /* default 25 */
+    float w_acceleration; /* default 10 */
+    int n_gn_surface;     /* Gauss-Newton steps, default 3 (Sec. 4), <= LC_MAX_GN */
+    int n_pcg_surface;    /* PCG iterations per step, default 4 (Sec. 4) */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -99,6 +109,7 @@ typedef struct {
     int pcg_breakdowns;                      /* steps whose PCG stopped on p^T A p <= 0 */
     int n_kernels;                           /* kernel launches in one solve (captured graph) */
     int pcg_cluster_size;                    /* CTAs per cluster of the persistent PCG, 0 = per-phase kernels */
+    double e_smooth, e_edge, e_velocity, e_acceleration;  /* surface stage terms (0 after a graph solve) */
 } lc_solve_stats;
 
 /* Vertex flag bits returned by lc_read_visibility / lc_read_back. */
@@ -155,6 +166,12 @@ lc_status lc_read_graph(lc_ctx *ctx, int32_t *node_vid, int32_t *bind_idx, float
 /* Node parameters: rotations node_R n x 9 (row-major 3x3) and translations
  * node_t n x 3.  Both null = reset to the identity. */
 lc_status lc_set_node_params(lc_ctx *ctx, const float *node_R, const float *node_t);
+
+/* Rest geometry V^S (N x 3) of the non-rigid stages: the skinned mesh of a
+ * pose estimate made outside the library (lc_solve_pose sets it from its own
+ * fit).  The graph nodes move with it (g_k = V^S of the node's vertex);
+ * V^S = NULL restores the template. */
+lc_status lc_set_rest_geometry(lc_ctx *ctx, const float *V_S);
 
 /* ---- frame ---------------------------------------------------------------- */
 
@@ -382,6 +399,67 @@ lc_status lc_record_motion(lc_ctx *ctx);
  * the start.  accepted (nullable) receives 1/0 and energies (nullable, 2)
  * the two energies; either makes the call synchronise. */
 lc_status lc_warm_start(lc_ctx *ctx, lc_mlp *mlp, int *accepted, double *energies);
+
+/* ---- per-vertex surface stage (the paper's own non-rigid unknowns) ---------
+ *
+ * Sec. 3.4 poses the non-rigid stage over the vertex positions V (N x 3):
+ *   E(V) = E_photo + E_silhouette + E_smooth + E_edge + E_velocity + E_acceleration
+ *   E_smooth       = w_smooth sum_i sum_{j in N_i} s_ij/|N_i| ||(V_i - V_j) - (V^S_i - V^S_j)||^2
+ *   E_edge         = w_edge   sum_i sum_{j in N_i} s_ij/|N_i| (||V_i - V_j|| - ||Vh_i - Vh_j||)^2
+ *   E_velocity     = w_velocity     sum_i ||V_i - V^{t-1}_i||^2
+ *   E_acceleration = w_acceleration sum_i ||V_i - 2 V^{t-1}_i + V^{t-2}_i||^2
+ * N_i is the one-ring of vertex i (vertices sharing a mesh edge), s_ij the
+ * mean of the two vertices' material weights (Sec. 3.1), V^S the stage's rest
+ * geometry (the skinned mesh after lc_solve_pose, else the template), Vh the
+ * template.  The data terms are the graph stage's (same visibility, contour
+ * set and b_i rules) evaluated at V_i.  Sec. 4: Gauss-Newton, n_gn_surface
+ * steps of n_pcg_surface Jacobi-PCG iterations from 0, one thread per vertex
+ * block row gathering its one-ring (no atomics), V <- V + delta.
+ * Temporal history: none -> both temporal terms off; one previous frame ->
+ * V^{t-2} = V^{t-1}.  The surface state exists once a template is uploaded;
+ * the surface calls need no graph.  A new template clears the history. */
+
+/* The current surface V (N x 3 floats): the unknowns and the start of the
+ * next lc_solve_surface. */
+lc_status lc_set_surface(lc_ctx *ctx, const float *V);
+/* Start of a frame (Sec. 3.4, displacement warping): V <- V^S + d^S, where
+ * d^S is the displacement recorded by the last lc_surface_advance carried
+ * from that frame's pose to the current one: d^S_i = Q_i dh_i with dh_i the
+ * recorded rest-pose displacement and Q_i the rotation of the dual-quaternion
+ * blend of vertex i's bone rotations (skinning weights of lc_upload_skeleton;
+ * Q_i = I without a skeleton).  Without a recorded displacement V <- V^S.
+ * Enqueued, no synchronisation. */
+lc_status lc_surface_start(lc_ctx *ctx);
+/* Temporal history V^{t-1}, V^{t-2} (N x 3 each).  V_prev = NULL clears the
+ * history; V_prev2 = NULL sets V^{t-2} = V^{t-1}. */
+lc_status lc_surface_history(lc_ctx *ctx, const float *V_prev, const float *V_prev2);
+/* End of a frame: V^{t-2} <- V^{t-1}, V^{t-1} <- V, and the rest-pose
+ * displacement dh_i = Q_i^T (V_i - V^S_i) is recorded for lc_surface_start.
+ * Enqueued, no synchronisation. */
+lc_status lc_surface_advance(lc_ctx *ctx);
+/* One frame of the surface stage from the current V: frame decisions (V, B,
+ * b_i) at the start, n_gn_surface Gauss-Newton steps, final energy.  Needs
+ * template, camera and frame.  Captured once as a CUDA graph.  stats
+ * (nullable; filling it synchronises): e_photo, e_sil and the four
+ * regulariser energies after the last update, e_total their sum, e_gn the
+ * total at each linearisation; e_arap = 0. */
+lc_status lc_solve_surface(lc_ctx *ctx, lc_solve_stats *stats);
+/* Surface read-back (synchronises): V (N x 3, nullable), flags (N, nullable:
+ * LC_FLAG_* of the last frame decisions). */
+lc_status lc_read_surface(lc_ctx *ctx, float *V, uint8_t *flags);
+
+/* Inspection (each synchronises).  lc_surface_visibility: the frame
+ * decisions at the current V (lc_read_visibility returns them).
+ * lc_surface_linearize: at the current V with those decisions (b_i
+ * re-evaluated), rhs = -J^T F (N x 3), diag = diag(J^T J) (N x 3) and
+ * energies[6] = photo, silhouette, smooth, edge, velocity, acceleration;
+ * any output may be NULL.  lc_surface_apply_jtj: out = J^T J p (N x 3) at
+ * that linearisation.  lc_surface_solve_linear: n_pcg_surface Jacobi-PCG
+ * iterations on it from 0 (delta N x 3, iters = iterations run). */
+lc_status lc_surface_visibility(lc_ctx *ctx);
+lc_status lc_surface_linearize(lc_ctx *ctx, float *rhs, float *diag, double *energies);
+lc_status lc_surface_apply_jtj(lc_ctx *ctx, const float *p, float *out);
+lc_status lc_surface_solve_linear(lc_ctx *ctx, float *delta, int *iters);
 
 /* ---- profiling ------------------------------------------------------------ */
 

@@ -277,6 +277,40 @@ def gauss_newton(P: SurfaceProblem, V: np.ndarray, n_gn: int, n_pcg: int):
 
 
 # ----------------------------------------------------------------------------
+# Displacement warping (Sec. 3.4)
+# ----------------------------------------------------------------------------
+def blend_rotations(G: np.ndarray, skin_idx: np.ndarray, skin_w: np.ndarray) -> np.ndarray:
+    """Per-vertex rotation of the dual-quaternion blend of the bone
+    rotations G (J,3,3) with the skinning weights (N,S): the bones'
+    quaternions, each sign-aligned with the quaternion of the vertex's first
+    bone, summed with the weights and normalised (the rotation part of dual
+    quaternion skinning).  Returns (N,3,3); the identity where the sum is 0."""
+    from scipy.spatial.transform import Rotation
+    q = Rotation.from_matrix(np.asarray(G, dtype=np.float64)).as_quat()      # (J,4) x, y, z, w
+    idx = np.asarray(skin_idx, dtype=np.int64)
+    w = np.asarray(skin_w, dtype=np.float64)
+    qs = q[idx]                                                               # (N,S,4)
+    sign = np.where(np.einsum("nsk,nk->ns", qs, qs[:, 0]) < 0.0, -1.0, 1.0)
+    blend = np.einsum("ns,nsk->nk", w * sign, qs)
+    norm = np.linalg.norm(blend, axis=1)
+    out = np.tile(np.eye(3), (len(blend), 1, 1))
+    ok = norm > 0.0
+    if ok.any():
+        out[ok] = Rotation.from_quat(blend[ok] / norm[ok, None]).as_matrix()
+    return out
+
+
+def record_displacement(V: np.ndarray, VS: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """Rest-pose displacement dh_i = Q_i^T (V_i - V^S_i)."""
+    return np.einsum("nji,nj->ni", Q, np.asarray(V, np.float64) - np.asarray(VS, np.float64))
+
+
+def warped_start(VS: np.ndarray, Q: np.ndarray, dh: np.ndarray) -> np.ndarray:
+    """Start of the next frame: V_i = V^S_i + Q_i dh_i."""
+    return np.asarray(VS, np.float64) + np.einsum("nij,nj->ni", Q, dh)
+
+
+# ----------------------------------------------------------------------------
 # Assembling a problem from scene data
 # ----------------------------------------------------------------------------
 def problem_from_scene(scene, base32: Optional[np.ndarray] = None, weights=None,

@@ -92,6 +92,8 @@ lc_status lc_ctx::sync_desc() {
 void lc_ctx::drop_graph() {
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
+    if (surf_gexec) cudaGraphExecDestroy(surf_gexec);
+    surf_gexec = nullptr;
 }
 
 // ---------------------------------------------------------------------------
@@ -99,6 +101,7 @@ void lc_ctx::drop_graph() {
 // ---------------------------------------------------------------------------
 extern "C" lc_status lc_params_default(lc_params* p) {
     if (!p) return LC_ERR_ARG;
+    memset(p, 0, sizeof(*p));
     p->w_photo = 1.0f;
     p->w_sil = 0.1f;
     p->w_arap = 10.0f;
@@ -111,6 +114,13 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->n_gn_pose = 5;
     p->lambda_prior = 1e4f;
     p->pcg_kernel = 0;
+    p->target_energy = 0.0f;
+    p->w_smooth = 1.0e3f;
+    p->w_edge = 3.0e3f;
+    p->w_velocity = 25.0f;
+    p->w_acceleration = 10.0f;
+    p->n_gn_surface = 3;
+    p->n_pcg_surface = 4;
     return LC_OK;
 }
 
@@ -184,6 +194,7 @@ void lc_ctx::apply_params() {
     hC.w_arap = params.w_arap;
     hC.eps_vis = params.eps_vis;
     hC.target_energy = params.target_energy;
+    surface_weights();
 }
 
 extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
@@ -191,11 +202,13 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
     if (p->n_gn < 1 || p->n_gn > LC_MAX_GN || p->n_pcg < 1 || p->n_gn_pose < 1 || p->n_gn_pose > LC_MAX_GN ||
         !(p->w_photo >= 0.f) || !(p->w_sil >= 0.f) || !(p->w_arap >= 0.f) || !(p->eps_vis >= 0.f) ||
         !(p->lambda_2d >= 0.f) || !(p->lambda_3d >= 0.f) || !(p->lambda_sil >= 0.f) || !(p->lambda_prior >= 0.f) ||
-        !(p->target_energy >= 0.f))
+        !(p->target_energy >= 0.f) || p->n_gn_surface < 1 || p->n_gn_surface > LC_MAX_GN || p->n_pcg_surface < 1 ||
+        !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 2) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0, 1 or 2");
-    if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel)
+    if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
+        p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
     if (p->n_gn_pose != ctx->params.n_gn_pose) ctx->pose_drop_graph();
     ctx->params = *p;
@@ -336,6 +349,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
     C.vert_tiles = (N + kVertTile - 1) / kVertTile;
     C.tri_tiles = (F + kTriTile - 1) / kTriTile;
     C.medge_tiles = (C.n_medges + kEdgeTile - 1) / kEdgeTile;
+    if ((s = ctx->surface_setup(hv.data(), hm.data(), medges))) return s;
     ctx->ensure_partials();
     ctx->has_template = true;
     ctx->drop_graph();
@@ -343,7 +357,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
 }
 
 void lc_ctx::ensure_partials() {
-    const int need = std::max({2 * hC.vert_tiles, hC.node_tiles, (hC.n + kVecThreads - 1) / kVecThreads, 64}) + 8;
+    const int need = std::max({4 * hC.vert_tiles, hC.node_tiles, (hC.n + kVecThreads - 1) / kVecThreads, 64}) + 8;
     if (need > part_cap) {
         release(hC.part);
         hC.part = (double*)alloc(sizeof(double) * need);
@@ -377,6 +391,7 @@ void lc_ctx::free_graph() {
 void lc_ctx::free_template() {
     free_graph();
     pose_release();
+    surface_release();
     void* bufs[] = {tpl, base_buf, (void*)hC.albedo, (void*)hC.tris, (void*)hC.vt_off, (void*)hC.vt_tri,
                     (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q};
     for (void* p : bufs) release(p);
@@ -545,6 +560,35 @@ extern "C" lc_status lc_set_node_params(lc_ctx* ctx, const float* node_R, const 
     return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
 }
 
+extern "C" lc_status lc_set_rest_geometry(lc_ctx* ctx, const float* V_S) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_set_rest_geometry: no template");
+    cudaSetDevice(ctx->device);
+    CapDesc& C = ctx->hC;
+    const int N = C.N;
+    lc_status s;
+    if (!V_S) {
+        s = ctx->cuda(cudaMemcpyAsync(ctx->base_buf, ctx->tpl, sizeof(float4) * N, cudaMemcpyDeviceToDevice, ctx->stream),
+                      "copy");
+    } else {
+        std::vector<float> h;
+        if ((s = host_copy(ctx, h, V_S, (size_t)3 * N))) return s;
+        std::vector<float4> v4(N);
+        for (int i = 0; i < N; ++i) {
+            if (!std::isfinite(h[3 * i]) || !std::isfinite(h[3 * i + 1]) || !std::isfinite(h[3 * i + 2]))
+                return ctx->fail(LC_ERR_ARG, "lc_set_rest_geometry: non-finite vertex");
+            v4[i] = make_float4(h[3 * i], h[3 * i + 1], h[3 * i + 2], 0.f);
+        }
+        s = ctx->cuda(cudaMemcpyAsync(ctx->base_buf, v4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, ctx->stream),
+                      "upload");
+    }
+    if (s) return s;
+    if (ctx->has_graph) launch_gather_nodes(ctx->base_buf, C.node_vid, C.n, (float4*)C.node_g, ctx->stream);
+    ctx->has_lin = false;
+    ctx->surf_has_lin = false;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
 // ---------------------------------------------------------------------------
 // frame
 // ---------------------------------------------------------------------------
@@ -704,7 +748,7 @@ lc_status lc_ctx::check_solve_state(const char* who) {
     return LC_OK;
 }
 
-lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn) {
+lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn, bool surface) {
     Scalars sc;
     std::vector<double> hist(2 * (LC_MAX_GN + 1));
     std::vector<int> it(LC_MAX_GN + 2);
@@ -717,6 +761,14 @@ lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn) {
     stats->e_sil = sc.e_lin[1];
     stats->e_arap = sc.e_lin[2];
     stats->e_total = sc.e_lin[0] + sc.e_lin[1] + sc.e_lin[2];
+    if (surface) {
+        stats->e_arap = 0.0;
+        stats->e_smooth = sc.e_reg[0];
+        stats->e_edge = sc.e_reg[1];
+        stats->e_velocity = sc.e_reg[2];
+        stats->e_acceleration = sc.e_reg[3];
+        stats->e_total = sc.e_lin[0] + sc.e_lin[1] + sc.e_reg[0] + sc.e_reg[1] + sc.e_reg[2] + sc.e_reg[3];
+    }
     for (int g = 0; g < n_gn; ++g) {
         stats->e_gn[g] = hist[2 * g];
         stats->step_norm[g] = hist[2 * g + 1];
@@ -740,6 +792,8 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     if ((s = ctx->accumulate_profile(ctx->prof_nonrigid))) return s;
     ctx->has_vis = true;
     ctx->has_lin = true;
+    ctx->surf_has_lin = false;
+    ctx->last_surface = false;
     if (stats) {
         if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
         stats->n_kernels = ctx->graph_kernels;
@@ -750,9 +804,16 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
 
 extern "C" lc_status lc_read_stats(lc_ctx* ctx, lc_solve_stats* stats) {
     if (!ctx || !stats) return LC_ERR_ARG;
-    if (!ctx->gexec) return ctx->fail(LC_ERR_STATE, "lc_read_stats: no non-rigid solve yet");
+    if (ctx->last_surface ? !ctx->surf_gexec : !ctx->gexec)
+        return ctx->fail(LC_ERR_STATE, "lc_read_stats: no non-rigid solve yet");
     cudaSetDevice(ctx->device);
     lc_status s;
+    if (ctx->last_surface) {
+        if ((s = ctx->read_stats(stats, ctx->params.n_gn_surface, true))) return s;
+        stats->n_kernels = ctx->surf_graph_kernels;
+        stats->pcg_cluster_size = 0;
+        return LC_OK;
+    }
     if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
     stats->n_kernels = ctx->graph_kernels;
     stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
@@ -767,7 +828,7 @@ extern "C" lc_status lc_set_profiling(lc_ctx* ctx, int on) {
         ctx->drop_graph();
         ctx->pose_drop_graph();
         ctx->prof_used = 0;
-        ctx->prof_nonrigid = ctx->prof_pose = lc_ctx::ProfRange{};
+        ctx->prof_nonrigid = ctx->prof_pose = ctx->prof_surface = lc_ctx::ProfRange{};
     }
     for (int j = 0; j < LC_N_PHASES; ++j) {
         ctx->prof_ms[j] = 0.0;

@@ -9,6 +9,9 @@
 
 struct PoseState;
 struct WarmState;
+namespace lc {
+struct PoseDesc;
+}
 
 struct lc_ctx {
     int device = 0;
@@ -54,7 +57,7 @@ struct lc_ctx {
     int prof_used = 0;             // events handed out since profiling was switched on
     struct ProfRange {
         int begin = 0, end = 0;    // the events one captured graph records
-    } prof_nonrigid, prof_pose;
+    } prof_nonrigid, prof_pose, prof_surface;
     double prof_ms[LC_N_PHASES] = {0};
     int prof_cnt[LC_N_PHASES] = {0};
     void mark(int phase);          // record the next event of the chain (capture time)
@@ -77,12 +80,26 @@ struct lc_ctx {
     void free_template();
     void enqueue_nonrigid();
     lc_status check_solve_state(const char* who);
-    lc_status read_stats(lc_solve_stats* stats, int n_gn);
+    lc_status read_stats(lc_solve_stats* stats, int n_gn, bool surface = false);
     lc_status capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)());
     lc_status linearize_now(bool with_rhs);
     lc_status vec_out(float* dst, const float4* src);
     float* tmp_out();
+    // per-vertex surface stage (surface.cu)
+    cudaGraphExec_t surf_gexec = nullptr;
+    int surf_graph_kernels = 0;
+    int surf_hist = 0;             // temporal history frames held (0, 1, 2)
+    bool surf_has_disp = false;    // a rest-pose displacement was recorded
+    bool surf_has_lin = false;     // the surface operands match the current V
+    bool last_surface = false;     // the last solve was the surface stage (lc_read_stats)
+    float4* surf_diag = nullptr;   // N: diag(J^T J) for lc_surface_linearize
+    lc_status surface_setup(const float* V, const float* material, const std::vector<int4>& medges);
+    void surface_release();
+    void surface_weights();
+    void enqueue_surface();
+    lc_status check_surface_state(const char* who);
     // pose stage (pose_api.cu)
+    const lc::PoseDesc* pose_desc() const;   // device descriptor, null without a skeleton
     void enqueue_pose();
     void pose_release();
     void pose_drop_graph();

@@ -46,6 +46,7 @@ struct Scalars {
     int gn_done;       // GN updates made in the current solve (gn_stop, gn_done are reset together)
     int vis_frozen;    // keep the frame decisions (V, B) of the start for the next solve
     float alpha, beta_f;   // PCG step lengths in FP32 (FP64 sums divided in FP32)
+    double e_reg[4];       // surface stage: smooth, edge, velocity, acceleration
 };
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
@@ -106,6 +107,25 @@ struct CapDesc {
     float4* vA;              // N*K: (R_k (v_i - g_k), w_is) per binding, 0 weight for inactive vertices
     float4* eA;              // N*K: the same per node -> vertex CSR entry
     float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)
+    // per-vertex surface stage (unknowns V)
+    int n_adj;               // directed one-ring pairs
+    float w_smooth, w_edge;
+    float w_vel, w_acc;      // 0 without temporal history
+    const int* adj_off;      // N+1 one-ring CSR, neighbours ascending
+    const int* adj_dst;      // n_adj
+    const float4* adj_geo;   // n_adj: (s_ij/|N_i|, s_ij (1/|N_i| + 1/|N_j|), |Vh_i - Vh_j|, 0)
+    float4* adj_m;           // n_adj, per linearisation: (sqrt(w_edge c_ij) n_ij, w_smooth c_ij)
+    float4* sV;              // N current surface (x, y, z, 0)
+    float4* sH1;             // N V^{t-1}
+    float4* sH2;             // N V^{t-2}
+    float4* sD;              // N rest-pose displacement of the last advanced frame
+    float4* sb;              // N -J^T F
+    float4* sminv;           // N Jacobi inverse diagonal
+    float4* sx;
+    float4* sr;
+    float4* sz;
+    float4* sp[2];           // search directions of even / odd PCG iterations
+    float4* sAp;
     // reductions
     double* part;            // per-tile partials of the running reduction
     unsigned* counters;      // CNT_N
@@ -369,6 +389,17 @@ void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream
 void launch_update(const CapDesc* dC, const Tiles& T, int gn_slot, cudaStream_t st);
 void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
 void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);
+
+// per-vertex surface stage (surface.cu)
+void launch_surface_project(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+// diag_out (nullable): diag(J^T J) per vertex; energy_only: energies only
+void launch_surface_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, float4* diag_out,
+                        cudaStream_t st);
+// it: PCG iteration (-1: plain product of p into out with no dot)
+void launch_surface_jtj(const CapDesc* dC, const CapDesc& hC, int it, const float4* p, float4* out, cudaStream_t st);
+void launch_surface_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+void launch_surface_pcg_step(const CapDesc* dC, const CapDesc& hC, int it, cudaStream_t st);
+void launch_surface_update(const CapDesc* dC, const CapDesc& hC, int slot, cudaStream_t st);
 
 // cluster-persistent PCG (pcg_cluster.cu)
 struct PcgPlan {

@@ -55,6 +55,8 @@ static void rot_log(const double* R, double* w) {
     for (int k = 0; k < 3; ++k) w[k] = f * v[k];
 }
 
+const PoseDesc* lc_ctx::pose_desc() const { return pose && pose->has_pose ? pose->d : nullptr; }
+
 void lc_ctx::pose_drop_graph() {
     if (pose && pose->gexec) {
         cudaGraphExecDestroy(pose->gexec);

@@ -51,6 +51,9 @@ void launch_pose_blist(const CapDesc* dC, const PoseDesc* dP, cudaStream_t st);
 void launch_pose_fk(const PoseDesc* dP, cudaStream_t st);
 // re-skins the mesh into C.vw / C.uv and re-evaluates b_i of the contour set
 void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, cudaStream_t st);
+// displacement warping of the surface stage (dP null: no skeleton, Q_i = I);
+// mode 0 records sD from sV, mode 1 sets sV from sD
+void launch_surface_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int mode, cudaStream_t st);
 // residual rows -> partial pair sums (P.part)
 cudaError_t pose_kernels_init(int n_dof);
 int pose_system_ctas(int J, int N);

@@ -520,11 +520,89 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Displacement warping of the surface stage (Sec. 3.4): the rotation Q_i of
+// the dual-quaternion blend of vertex i's bone rotations (its skinning
+// weights; quaternions sign-aligned with the first slot's bone, summed and
+// normalised).  mode 0 records the rest-pose displacement
+// sD_i = Q_i^T (V_i - V^S_i); mode 1 starts the surface at
+// V_i = V^S_i + Q_i sD_i.  Without a skeleton (pd null) Q_i = I.
+// ---------------------------------------------------------------------------
+// unit quaternion (x, y, z, w) of a row-major rotation matrix, branching on
+// the largest of the trace and the diagonal (Shepperd, 1978)
+__device__ __forceinline__ float4 quat_of(const float* G) {
+    const float tr = G[0] + G[4] + G[8];
+    float4 q;
+    if (tr >= G[0] && tr >= G[4] && tr >= G[8]) {
+        const float w = 0.5f * sqrtf(fmaxf(1.f + tr, 0.f)), k = 0.25f / w;
+        q = make_float4((G[7] - G[5]) * k, (G[2] - G[6]) * k, (G[3] - G[1]) * k, w);
+    } else if (G[0] >= G[4] && G[0] >= G[8]) {
+        const float x = 0.5f * sqrtf(fmaxf(1.f + G[0] - G[4] - G[8], 0.f)), k = 0.25f / x;
+        q = make_float4(x, (G[1] + G[3]) * k, (G[2] + G[6]) * k, (G[7] - G[5]) * k);
+    } else if (G[4] >= G[8]) {
+        const float y = 0.5f * sqrtf(fmaxf(1.f - G[0] + G[4] - G[8], 0.f)), k = 0.25f / y;
+        q = make_float4((G[1] + G[3]) * k, y, (G[5] + G[7]) * k, (G[2] - G[6]) * k);
+    } else {
+        const float z = 0.5f * sqrtf(fmaxf(1.f - G[0] - G[4] + G[8], 0.f)), k = 0.25f / z;
+        q = make_float4((G[2] + G[6]) * k, (G[5] + G[7]) * k, z, (G[3] - G[1]) * k);
+    }
+    return q;
+}
+
+__global__ void __launch_bounds__(256) surface_warp_kernel(const CapDesc* __restrict__ caps,
+                                                           const PoseDesc* __restrict__ pd, int mode) {
+    __shared__ float4 qb[kMaxJoints];
+    const CapDesc& C = caps[0];
+    if (pd)
+        for (int b = threadIdx.x; b < pd->J; b += blockDim.x) qb[b] = quat_of(&pd->fk->G[b][0]);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C.N) return;
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    if (pd) {
+        const int4 bi = pd->skin_idx[i];
+        const float4 bw = pd->skin_w[i];
+        const int bones[4] = {bi.x, bi.y, bi.z, bi.w};
+        const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
+        const float4 q0 = qb[bones[0]];
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 q = qb[bones[k]];
+            const float w = (q.x * q0.x + q.y * q0.y + q.z * q0.z + q.w * q0.w) < 0.f ? -ws[k] : ws[k];
+            s.x += w * q.x; s.y += w * q.y; s.z += w * q.z; s.w += w * q.w;
+        }
+        const float n2 = s.x * s.x + s.y * s.y + s.z * s.z + s.w * s.w;
+        if (n2 > 0.f) {
+            const float inv = rsqrtf(n2);
+            const float x = s.x * inv, y = s.y * inv, z = s.z * inv, w = s.w * inv;
+            R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
+            R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
+            R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
+        }
+    }
+    const float4 S = C.base[i];
+    if (mode == 0) {
+        const float4 V = C.sV[i];
+        const float dx = V.x - S.x, dy = V.y - S.y, dz = V.z - S.z;
+        C.sD[i] = make_float4(R[0] * dx + R[3] * dy + R[6] * dz, R[1] * dx + R[4] * dy + R[7] * dz,
+                              R[2] * dx + R[5] * dy + R[8] * dz, 0.f);
+    } else {
+        const float4 d = C.sD[i];
+        C.sV[i] = make_float4(S.x + (R[0] * d.x + R[1] * d.y + R[2] * d.z), S.y + (R[3] * d.x + R[4] * d.y + R[5] * d.z),
+                              S.z + (R[6] * d.x + R[7] * d.y + R[8] * d.z), 0.f);
+    }
+}
+
 void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* out_base, int mode,
                       cudaStream_t st) {
     pose_skin_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP, out_base, mode);
 }
 void launch_pose_fk(const PoseDesc* dP, cudaStream_t st) { pose_fk_kernel<<<1, 64, 0, st>>>(dP); }
+void launch_surface_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int mode, cudaStream_t st) {
+    if (dP) pose_fk_kernel<<<1, 64, 0, st>>>(dP);   // kinematics of the current pose
+    surface_warp_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP, mode);
+}
 void launch_pose_blist(const CapDesc* dC, const PoseDesc* dP, cudaStream_t st) {
     pose_blist_kernel<<<1, 1024, 0, st>>>(dC, dP);
 }

@@ -25,7 +25,9 @@ class lc_params(ctypes.Structure):
                 ("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("eps_vis", ctypes.c_float),
                 ("lambda_2d", ctypes.c_float), ("lambda_3d", ctypes.c_float), ("lambda_sil", ctypes.c_float),
                 ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int),
-                ("target_energy", ctypes.c_float)]
+                ("target_energy", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_edge", ctypes.c_float),
+                ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
+                ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -34,7 +36,9 @@ class lc_solve_stats(ctypes.Structure):
                 ("step_norm", ctypes.c_double * LC_MAX_GN), ("pcg_iters", ctypes.c_int * LC_MAX_GN),
                 ("n_gn_done", ctypes.c_int), ("n_visible", ctypes.c_int), ("n_boundary", ctypes.c_int),
                 ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int),
-                ("n_kernels", ctypes.c_int), ("pcg_cluster_size", ctypes.c_int)]
+                ("n_kernels", ctypes.c_int), ("pcg_cluster_size", ctypes.c_int),
+                ("e_smooth", ctypes.c_double), ("e_edge", ctypes.c_double), ("e_velocity", ctypes.c_double),
+                ("e_acceleration", ctypes.c_double)]
 
     def to_dict(self) -> dict:
         g = self.n_gn_done
@@ -44,7 +48,8 @@ class lc_solve_stats(ctypes.Structure):
                     n_boundary=self.n_boundary, n_boundary_neg=self.n_boundary_neg,
                     pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels,
                     pcg_cluster_size=self.pcg_cluster_size, n_gn_done=g,
-                    e_gn_all=list(self.e_gn))
+                    e_gn_all=list(self.e_gn), e_smooth=self.e_smooth, e_edge=self.e_edge,
+                    e_velocity=self.e_velocity, e_acceleration=self.e_acceleration)
 
 
 _P = ctypes.c_void_p
@@ -94,6 +99,17 @@ _SIGS = {
     "lc_eval_pose": [_P, _P, _P, _P, _P],
     "lc_set_profiling": [_P, ctypes.c_int],
     "lc_read_profile": [_P, _P, _P],
+    "lc_set_rest_geometry": [_P, _P],
+    "lc_set_surface": [_P, _P],
+    "lc_surface_start": [_P],
+    "lc_surface_history": [_P, _P, _P],
+    "lc_surface_advance": [_P],
+    "lc_solve_surface": [_P, ctypes.POINTER(lc_solve_stats)],
+    "lc_read_surface": [_P, _P, _P],
+    "lc_surface_visibility": [_P],
+    "lc_surface_linearize": [_P, _P, _P, _P],
+    "lc_surface_apply_jtj": [_P, _P, _P],
+    "lc_surface_solve_linear": [_P, _P, ctypes.POINTER(ctypes.c_int)],
     "lc_visibility_noalloc": [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_int, ctypes.c_int, ctypes.c_float, _P, _P],
 }
@@ -243,6 +259,10 @@ class Context:
         t = _arr(t, np.float32)
         self._check(self._lib.lc_set_node_params(self.h, _ptr(R), _ptr(t)))
 
+    def set_rest_geometry(self, V_S=None):
+        V_S = _arr(V_S, np.float32)
+        self._check(self._lib.lc_set_rest_geometry(self.h, _ptr(V_S)))
+
     def upload_frame(self, rgb, dt, mask, joints2d=None, joints3d=None):
         rgb = _arr(rgb, np.float32)
         dt = _arr(dt, np.float32)
@@ -336,6 +356,58 @@ class Context:
         d = np.zeros(6 * self.n, np.float32)
         it = ctypes.c_int(0)
         self._check(self._lib.lc_solve_linear(self.h, _ptr(d), ctypes.byref(it)))
+        return d, it.value
+
+    # ---- per-vertex surface stage
+    def set_surface(self, V):
+        V = _arr(V, np.float32)
+        self._check(self._lib.lc_set_surface(self.h, _ptr(V)))
+
+    def surface_start(self):
+        self._check(self._lib.lc_surface_start(self.h))
+
+    def surface_history(self, V_prev=None, V_prev2=None):
+        V_prev = _arr(V_prev, np.float32)
+        V_prev2 = _arr(V_prev2, np.float32)
+        self._check(self._lib.lc_surface_history(self.h, _ptr(V_prev), _ptr(V_prev2)))
+
+    def surface_advance(self):
+        self._check(self._lib.lc_surface_advance(self.h))
+
+    def solve_surface(self, stats: bool = True):
+        if not stats:
+            self._check(self._lib.lc_solve_surface(self.h, None))
+            return None
+        s = lc_solve_stats()
+        self._check(self._lib.lc_solve_surface(self.h, ctypes.byref(s)))
+        return s.to_dict()
+
+    def read_surface(self, flags: bool = False):
+        V = np.zeros((self.N, 3), np.float32)
+        f = np.zeros(self.N, np.uint8) if flags else None
+        self._check(self._lib.lc_read_surface(self.h, _ptr(V), _ptr(f)))
+        return (V, f) if flags else V
+
+    def surface_visibility(self):
+        self._check(self._lib.lc_surface_visibility(self.h))
+
+    def surface_linearize(self) -> dict:
+        out = dict(rhs=np.zeros((self.N, 3), np.float32), diag=np.zeros((self.N, 3), np.float32),
+                   energy=np.zeros(6))
+        self._check(self._lib.lc_surface_linearize(self.h, _ptr(out["rhs"]), _ptr(out["diag"]),
+                                                   _ptr(out["energy"])))
+        return out
+
+    def surface_apply_jtj(self, p):
+        p = _arr(p, np.float32)
+        out = np.zeros((self.N, 3), np.float32)
+        self._check(self._lib.lc_surface_apply_jtj(self.h, _ptr(p), _ptr(out)))
+        return out
+
+    def surface_solve_linear(self):
+        d = np.zeros((self.N, 3), np.float32)
+        it = ctypes.c_int(0)
+        self._check(self._lib.lc_surface_solve_linear(self.h, _ptr(d), ctypes.byref(it)))
         return d, it.value
 
     # ---- profiling
@@ -507,8 +579,10 @@ def setup_scene(ctx: Context, scene, with_frame: bool = True):
     """Upload a ``synth.Scene`` (template, camera, graph, weights, frame, and
     for body scenes the skeleton and start pose)."""
     wp, ws, wa = scene.weights
+    _, _, wsm, wed, wv, wac = scene.surface_weights
     ctx.set_params(w_photo=wp, w_sil=ws, w_arap=wa, n_gn=scene.n_gn, n_pcg=scene.n_pcg,
-                   n_gn_pose=scene.n_gn_pose)
+                   n_gn_pose=scene.n_gn_pose, w_smooth=wsm, w_edge=wed, w_velocity=wv, w_acceleration=wac,
+                   n_gn_surface=scene.n_gn_surface, n_pcg_surface=scene.n_pcg_surface)
     ctx.set_camera(scene.cam.f, scene.cam.cx, scene.cam.cy, scene.cam.W, scene.cam.H)
     ctx.upload_template(scene.V, scene.F, scene.albedo, scene.material)
     ctx.build_graph(scene.n_nodes, scene.K)

@@ -220,3 +220,47 @@ def ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
     dt = synth.contour_distance_transform(mask).astype(np.float32)
     return synth.Scene("ragged", cam, V.astype(np.float32), F.astype(np.int32), alb.astype(np.float32),
                        mat.astype(np.float32), rgb, dt, mask, n_nodes, K, 4, 15, (1.0, 0.1, 10.0), gt["V"])
+
+
+def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n_gn=None, n_pcg=None,
+                          n_runs=3):
+    """``fp32_rounding_band`` for the per-vertex surface stage: the spread of
+    the oracle's result when its Jacobian entries, residuals, CG vectors and
+    products and the vertex positions after every update are rounded to FP32
+    with a random tie-break of one unit roundoff.
+    Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
+    from oracle import surface as osf
+    kw = dict(base32=base32, V0=V0, n_gn=n_gn, n_pcg=n_pcg, prev1=prev1, prev2=prev2)
+    ref = osf.solve_scene(scene, **kw)
+    orig_pcg, orig_lin, orig_gn = onr.pcg, osf.linearise, osf.gauss_newton
+    dE, dV = 0.0, 0.0
+    for seed in range(n_runs):
+        r32 = _r32(np.random.default_rng(3000 + seed))
+
+        def lin32(P, V, directions=True):
+            F, J = orig_lin(P, V, directions)
+            J = J.tocsr(copy=True)
+            J.data = r32(J.data)
+            return r32(F), J
+
+        def gn32(P, V, n_gn, n_pcg):
+            V = np.asarray(V, dtype=np.float64).copy()
+            hist = []
+            for _ in range(n_gn):
+                A, b, F, _ = osf.normal_equations(P, V)
+                delta, info = onr.pcg(A, b, n_pcg)
+                hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta)),
+                                 pcg_iters=info["iters"], breakdown=info["breakdown"]))
+                V = r32(V + delta.reshape(-1, 3))
+            return V, hist
+
+        onr.pcg = lambda A, b, n: pcg32(A, b, n, r32)
+        osf.linearise = lin32
+        osf.gauss_newton = gn32
+        try:
+            o = osf.solve_scene(scene, **kw)
+        finally:
+            onr.pcg, osf.linearise, osf.gauss_newton = orig_pcg, orig_lin, orig_gn
+        dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
+        dV = max(dV, float(np.abs(o["V"] - ref["V"]).max()))
+    return ref, dE, dV

@@ -55,3 +55,8 @@ def test_params_default(lib):
     # pose-stage weights from the paper's parameter list (Sec. 5)
     assert (p.lambda_2d, p.lambda_3d, p.lambda_sil) == (460.0, 28.0, 200.0)
     assert (p.n_gn, p.n_pcg) == (5, 20)
+    # surface stage: Sec. 4 counts (3 Gauss-Newton x 4 PCG) and the weights
+    # of Sec. 5 read in millimetres, rescaled to metres and w_photo = 1
+    assert (p.n_gn_surface, p.n_pcg_surface) == (3, 4)
+    assert (p.w_smooth, p.w_edge, p.w_velocity, p.w_acceleration) == (1e3, 3e3, 25.0, 10.0)
+    assert p.target_energy == 0.0

@@ -10,7 +10,10 @@
   exact there), every block separately, and a planted mistake failing it;
 * with only the quadratic terms (smooth, velocity, acceleration) one
   Gauss-Newton step solved to convergence lands on the minimiser of the
-  weighted graph Laplacian system built by scipy.sparse.csgraph.
+  weighted graph Laplacian system built by scipy.sparse.csgraph;
+* displacement warping: the blended rotation reduces to the bone's own for
+  one bone, commutes with a global rotation, is the half-way rotation for
+  two opposite bones, and a same-pose round trip returns the surface.
 """
 import copy
 
@@ -212,3 +215,57 @@ def test_quadratic_terms_reach_the_laplacian_minimiser():
     e_star = sf.energy(P, Vstar)["total"]
     for k in range(3):
         assert sf.energy(P, Vstar + rng.normal(scale=1e-4, size=Vstar.shape))["total"] > e_star
+
+
+def _random_rotations(n, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return nr.so3_exp(rng.normal(scale=scale, size=(n, 3)))
+
+
+def test_blend_rotations_special_cases():
+    G = _random_rotations(6, 7)
+    rng = np.random.default_rng(8)
+    idx = rng.integers(0, 6, size=(50, 4))
+    w = rng.uniform(0.0, 1.0, size=(50, 4))
+    w /= w.sum(1, keepdims=True)
+    # one bone with all the weight: that bone's rotation
+    w1 = np.zeros((50, 4))
+    w1[:, 0] = 1.0
+    assert np.allclose(sf.blend_rotations(G, idx, w1), G[idx[:, 0]], atol=1e-12)
+    # every slot on bones with the same rotation: that rotation
+    Gs = np.tile(G[2], (6, 1, 1))
+    assert np.allclose(sf.blend_rotations(Gs, idx, w), np.tile(G[2], (50, 1, 1)), atol=1e-12)
+    # a rotation applied to every bone rotates the blend: blend(R G) = R blend(G)
+    R = _random_rotations(1, 9)[0]
+    Q = sf.blend_rotations(G, idx, w)
+    assert np.allclose(sf.blend_rotations(R @ G, idx, w), R @ Q, atol=1e-12)
+    # the result is a rotation; zero weights give the identity
+    assert np.allclose(np.einsum("nji,njk->nik", Q, Q), np.eye(3), atol=1e-12)
+    assert np.allclose(np.linalg.det(Q), 1.0)
+    assert np.allclose(sf.blend_rotations(G, idx, np.zeros((50, 4))), np.eye(3))
+    # two bones at +-theta about one axis, equal weights: the identity
+    # (the half-way rotation), and with weights (a, 1 - a) a rotation by
+    # an angle strictly between the two
+    axis = np.array([0.0, 0.0, 1.0])
+    G2 = nr.so3_exp(np.stack([0.6 * axis, -0.6 * axis]))
+    Qh = sf.blend_rotations(G2, np.array([[0, 1, 0, 0]]), np.array([[0.5, 0.5, 0.0, 0.0]]))
+    assert np.allclose(Qh[0], np.eye(3), atol=1e-12)
+
+
+def test_displacement_warping_round_trip():
+    rng = np.random.default_rng(10)
+    G = _random_rotations(5, 11)
+    idx = rng.integers(0, 5, size=(40, 4))
+    w = rng.uniform(size=(40, 4))
+    w /= w.sum(1, keepdims=True)
+    Q = sf.blend_rotations(G, idx, w)
+    VS = rng.normal(size=(40, 3))
+    V = VS + rng.normal(scale=0.01, size=(40, 3))
+    dh = sf.record_displacement(V, VS, Q)
+    # same pose: the surface comes back exactly
+    assert np.allclose(sf.warped_start(VS, Q, dh), V, atol=1e-14)
+    # lengths are preserved; a global extra rotation R rotates every displacement
+    assert np.allclose(np.linalg.norm(dh, axis=1), np.linalg.norm(V - VS, axis=1))
+    R = _random_rotations(1, 12)[0]
+    Q2 = sf.blend_rotations(R @ G, idx, w)
+    assert np.allclose(sf.warped_start(VS, Q2, dh) - VS, (V - VS) @ R.T, atol=1e-12)
