@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     __shared__ double A[kMaxDof][kMaxDof + 1];
     __shared__ double invd[kMaxDof];
     __shared__ double w[kMaxDof + 1];
+    __shared__ double colbuf[2][kMaxDof + 1];
     __shared__ double y[kMaxDof];
     __shared__ double prior_t[kMaxDof];
     __shared__ PoseFk fk;
@@ -432,51 +433,82 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         return;
     }
     // Square-root-free Cholesky A = L D L^T (FP64) of the matrix augmented
-    // with g: after pivot k the trailing block holds the Schur complement and
-    // column nd the forward-substituted right-hand side.  GB300's FP64 pipe
-    // has a long latency and a low rate per SM, so per pivot: 1 / d_k from an
-    // FP32 seed refined by two Newton steps y <- y (2 - d y) (no division),
-    // the pivot row scaled once (w_j = A_jk / d_k), then one FMA per entry
-    // of the trailing lower triangle and column nd.
+    // with g, right-looking: after pivot k the trailing block holds the Schur
+    // complement and column nd the forward-substituted right-hand side.
+    // GB300's FP64 pipe has a long latency and a low rate per SM, so the
+    // entries of the packed lower triangle (and of column nd) live in
+    // registers, round-robin over the threads; the owners publish column k
+    // (and A[k][nd]) to shared memory as soon as it is final.  Per pivot:
+    // every thread forms 1/d_k itself (FP32 seed, two Newton steps
+    // y <- y (2 - d y), no division), the row multipliers
+    // w_i = A_ik / d_k are formed once (they are L's column k), then one FMA
+    // per trailing entry.  Two block barriers per pivot.
+    constexpr int kEnt = (kMaxDof * (kMaxDof + 1) / 2 + kMaxDof + kSolveThreads - 1) / kSolveThreads;
+    const int ntri = nd * (nd + 1) / 2;
+    double ra[kEnt];
+    int ri[kEnt], rj[kEnt];
+#pragma unroll
+    for (int e = 0; e < kEnt; ++e) {
+        const int q = tid + e * kSolveThreads;
+        int i = -1, j = -1;
+        if (q < ntri) {
+            i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+            while (i * (i + 1) / 2 > q) --i;
+            while ((i + 1) * (i + 2) / 2 <= q) ++i;
+            j = q - i * (i + 1) / 2;
+        } else if (q < ntri + nd) {
+            i = q - ntri;
+            j = nd;
+        }
+        ri[e] = i;
+        rj[e] = j;
+        ra[e] = i >= 0 ? A[i][j] : 0.0;
+        if (j == 0) colbuf[0][i] = ra[e];           // column 0 and A[0][nd]
+        if (j == nd && i == 0) colbuf[0][nd] = ra[e];
+    }
     for (int k = 0; k < nd; ++k) {
+        __syncthreads();   // column k published; pivot k-1's updates and reads done
+        const double* col = colbuf[k & 1];
+        const double d = col[k];
+        double r;
+        const float fd = (float)d;
+        if (fd > 1e-30f && fd < 1e30f) {
+            r = (double)(1.0f / fd);
+            r = r * fma(-d, r, 2.0);
+            r = r * fma(-d, r, 2.0);
+        } else {
+            r = d > 0.0 ? 1.0 / d : 0.0;
+        }
+        const int m = nd - k - 1;
+        if (tid <= m) {
+            // L_ik (rows k+1 .. nd-1) and y_k = A[k][nd] / d_k
+            const double wv = (tid < m ? col[k + 1 + tid] : col[nd]) * r;
+            w[tid] = wv;
+            if (tid < m) A[k + 1 + tid][k] = wv;
+            else y[k] = wv;
+        }
         if (tid == 0) {
-            const double d = A[k][k];
             if (!(d > 0.0)) s_bad = 1;
-            double r;
-            const float fd = (float)d;
-            if (fd > 1e-30f && fd < 1e30f) {
-                r = (double)(1.0f / fd);
-                r = r * fma(-d, r, 2.0);
-                r = r * fma(-d, r, 2.0);
-            } else {
-                r = d > 0.0 ? 1.0 / d : 0.0;
-            }
             invd[k] = r;
         }
         __syncthreads();
-        const int m = nd - k - 1;
-        if (tid <= m) {
-            const int j = tid < m ? k + 1 + tid : nd;
-            w[tid] = (j < nd ? A[j][k] : A[k][nd]) * invd[k];
-        }
-        __syncthreads();
-        // entries (i, j), k < j <= i < nd, and (i, nd), k < i < nd
-        for (int q = tid; q < m * (m + 1); q += kSolveThreads) {
-            const int ii = q / (m + 1), jj = q - ii * (m + 1);
-            if (jj <= ii || jj == m) {
-                const int i = k + 1 + ii, j = jj < m ? k + 1 + jj : nd;
-                A[i][j] = fma(-A[i][k], w[jj], A[i][j]);
+        double* nxt = colbuf[(k + 1) & 1];
+#pragma unroll
+        for (int e = 0; e < kEnt; ++e) {
+            const int i = ri[e], j = rj[e];
+            if (i > k && (j == nd || j > k)) {
+                ra[e] = fma(-w[i - k - 1], col[j == nd ? nd : j], ra[e]);
+                if (j == k + 1) nxt[i] = ra[e];
+                else if (j == nd && i == k + 1) nxt[nd] = ra[e];
             }
         }
-        __syncthreads();
     }
-    // x = L^-T D^-1 y, column by column in one warp (L_ik = A_ik / d_k)
+    __syncthreads();
+    // x = L^-T y, column by column in one warp (L stored below the diagonal of A)
     if (tid < 32) {
-        for (int i = tid; i < nd; i += 32) y[i] = A[i][nd] * invd[i];
-        __syncwarp();
         for (int k = nd - 1; k >= 0; --k) {
             const double xk = y[k];
-            for (int i = tid; i < k; i += 32) y[i] = fma(-A[k][i] * invd[i], xk, y[i]);
+            for (int i = tid; i < k; i += 32) y[i] = fma(-A[k][i], xk, y[i]);
             __syncwarp();
         }
         double n2 = 0.0;

@@ -76,29 +76,46 @@ __global__ void __launch_bounds__(kVertTile) surface_rhs_kernel(const CapDesc* _
             g = xyz(e4);
             dg = make_float3(HA.x, HA.w, HB.y);
         }
+        constexpr int U = 4;
         const int p0 = C.adj_off[i], p1 = C.adj_off[i + 1];
-        for (int p = p0; p < p1; ++p) {
-            const int j = C.adj_dst[p];
-            const float4 geo = C.adj_geo[p];
-            const float3 Vj = xyz(C.sV[j]);
-            const float3 rs = sub3(Di, sub3(Vj, xyz(C.base[j])));
-            const float3 d = sub3(Vi, Vj);
-            const float len = sqrtf(dot3f(d, d));
-            const float er = len - geo.z;
-            en[0] += C.w_smooth * geo.x * dot3f(rs, rs);
-            en[1] += C.w_edge * geo.x * er * er;
-            if (energy_only) continue;
-            const float csm = C.w_smooth * geo.y, ce = C.w_edge * geo.y;
-            const float inv = len > 0.f ? 1.0f / len : 0.f;
-            const float3 n = make_float3(d.x * inv, d.y * inv, d.z * inv);
-            g.x += csm * rs.x + ce * er * n.x;
-            g.y += csm * rs.y + ce * er * n.y;
-            g.z += csm * rs.z + ce * er * n.z;
-            dg.x += csm + ce * n.x * n.x;
-            dg.y += csm + ce * n.y * n.y;
-            dg.z += csm + ce * n.z * n.z;
-            const float sce = sqrtf(ce);
-            C.adj_m[p] = make_float4(sce * n.x, sce * n.y, sce * n.z, csm);
+        for (int pb = p0; pb < p1; pb += U) {
+            int jj[U];
+            float4 gg[U], vj4[U], sj4[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                jj[u] = pb + u < p1 ? C.adj_dst[pb + u] : i;
+                gg[u] = pb + u < p1 ? C.adj_geo[pb + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                vj4[u] = C.sV[jj[u]];
+                sj4[u] = C.base[jj[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (pb + u >= p1) break;
+                const int p = pb + u;
+                const float4 geo = gg[u];
+                const float3 Vj = xyz(vj4[u]);
+                const float3 rs = sub3(Di, sub3(Vj, xyz(sj4[u])));
+                const float3 d = sub3(Vi, Vj);
+                const float len = sqrtf(dot3f(d, d));
+                const float er = len - geo.z;
+                en[0] += C.w_smooth * geo.x * dot3f(rs, rs);
+                en[1] += C.w_edge * geo.x * er * er;
+                if (energy_only) continue;
+                const float csm = C.w_smooth * geo.y, ce = C.w_edge * geo.y;
+                const float inv = len > 0.f ? 1.0f / len : 0.f;
+                const float3 n = make_float3(d.x * inv, d.y * inv, d.z * inv);
+                g.x += csm * rs.x + ce * er * n.x;
+                g.y += csm * rs.y + ce * er * n.y;
+                g.z += csm * rs.z + ce * er * n.z;
+                dg.x += csm + ce * n.x * n.x;
+                dg.y += csm + ce * n.y * n.y;
+                dg.z += csm + ce * n.z * n.z;
+                const float sce = sqrtf(ce);
+                C.adj_m[p] = make_float4(sce * n.x, sce * n.y, sce * n.z, csm);
+            }
         }
         if (C.w_vel > 0.f || C.w_acc > 0.f) {
             const float3 P1 = xyz(C.sH1[i]), P2 = xyz(C.sH2[i]);
@@ -153,16 +170,31 @@ __global__ void __launch_bounds__(kVertTile) surface_jtj_kernel(const CapDesc* _
         float3 q = make_float3(HA.x * pi.x + HA.y * pi.y + HA.z * pi.z + wt * pi.x,
                                HA.y * pi.x + HA.w * pi.y + HB.x * pi.z + wt * pi.y,
                                HA.z * pi.x + HB.x * pi.y + HB.y * pi.z + wt * pi.z);
+        // the one-ring in rounds of U pairs: a round's index and operand
+        // loads are issued together before any is used (a padding slot points
+        // at the vertex itself with a zero operand and adds nothing)
+        constexpr int U = 4;
         const int p0 = C.adj_off[i], p1 = C.adj_off[i + 1];
-        for (int p = p0; p < p1; ++p) {
-            const int j = C.adj_dst[p];
-            const float4 m = C.adj_m[p];
-            const float3 pj = pcg ? direction(C, it, beta, j) : xyz(p_in[j]);
-            const float3 dp = sub3(pi, pj);
-            const float s = m.x * dp.x + m.y * dp.y + m.z * dp.z;
-            q.x += m.w * dp.x + s * m.x;
-            q.y += m.w * dp.y + s * m.y;
-            q.z += m.w * dp.z + s * m.z;
+        for (int pb = p0; pb < p1; pb += U) {
+            int jj[U];
+            float4 m[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = pb + u < p1;
+                jj[u] = ok ? C.adj_dst[pb + u] : i;
+                m[u] = ok ? C.adj_m[pb + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float3 pj[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) pj[u] = pcg ? direction(C, it, beta, jj[u]) : xyz(p_in[jj[u]]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float3 dp = sub3(pi, pj[u]);
+                const float s = m[u].x * dp.x + m[u].y * dp.y + m[u].z * dp.z;
+                q.x += m[u].w * dp.x + s * m[u].x;
+                q.y += m[u].w * dp.y + s * m[u].y;
+                q.z += m[u].w * dp.z + s * m[u].z;
+            }
         }
         if (pcg) {
             if (it > 0) C.sp[it & 1][i] = make_float4(pi.x, pi.y, pi.z, 0.f);
