@@ -472,9 +472,12 @@ lc_status lc_surface_solve_linear(lc_ctx *ctx, float *delta, int *iters);
 #define LC_PH_JTJ 5       /* matrix-free J^T J p */
 #define LC_PH_PCG_VEC 6   /* PCG vector updates and FP64 dots */
 #define LC_PH_UPDATE 7    /* rotation / translation update */
-#define LC_PH_POSE 8      /* pose stage (whole) */
+#define LC_PH_POSE 8      /* pose stage: the rest (start-pose copy, final skinning into V^S) */
 #define LC_PH_PCG 9       /* cluster-persistent PCG (all iterations of one step) */
-#define LC_N_PHASES 10
+#define LC_PH_POSE_VIS 10   /* pose stage: kinematics, skinning, visibility and contour set at the start */
+#define LC_PH_POSE_SYS 11   /* pose stage: skinning, b_i and the residual rows reduced to J^T J (per step) */
+#define LC_PH_POSE_SOLVE 12 /* pose stage: FP64 normal equations, L D L^T solve, update (per step) */
+#define LC_N_PHASES 13
 
 /* Profiling on (1) or off (0).  When on, the captured solves record a chain
  * of CUDA events on the context stream between consecutive phases, so each

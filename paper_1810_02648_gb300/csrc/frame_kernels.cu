@@ -109,16 +109,25 @@ struct TriSetup {
     int sg, own, t, pad;
 };
 
-__global__ void __launch_bounds__(kTriTile) raster_kernel(const CapDesc* __restrict__ caps,
-                                                           const WorkItem* __restrict__ items) {
+// A warp rasterises kTriPerWarp triangles: each is set up by one lane, then
+// the warp's lanes take the pixels of its bounding box in turn.  Few triangles
+// per warp keep many warps in flight (the per-pixel work is a chain of int64
+// edge functions and exact divisions).
+constexpr int kTriPerWarp = 8;
+constexpr int kRasterThreads = kTriTile / kTriPerWarp * 32;
+
+__global__ void __launch_bounds__(kRasterThreads) raster_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items) {
     __shared__ TriSetup su[kTriTile];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
-    const int t = tile * kTriTile + threadIdx.x;
-    TriSetup& S = su[threadIdx.x];
-    S.npix = 0;
-    if (t < C.F && !C.sc->vis_frozen) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = warp * kTriPerWarp + lane;
+    const int t = tile * kTriTile + slot;
+    TriSetup& S = su[lane < kTriPerWarp ? slot : 0];
+    if (lane < kTriPerWarp) S.npix = 0;
+    if (lane < kTriPerWarp && t < C.F && !C.sc->vis_frozen) {
         const int4 tri = C.tris[t];
         long long ax, ay, bx, by, qx, qy;
         if (vertex_snap(C, tri.x, ax, ay) && vertex_snap(C, tri.y, bx, by) && vertex_snap(C, tri.z, qx, qy)) {
@@ -150,9 +159,8 @@ __global__ void __launch_bounds__(kTriTile) raster_kernel(const CapDesc* __restr
         }
     }
     __syncwarp();
-    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    for (int src = 0; src < 32; ++src) {
-        const TriSetup& T = su[wbase + src];
+    for (int src = 0; src < kTriPerWarp; ++src) {
+        const TriSetup& T = su[warp * kTriPerWarp + src];
         const int npix = T.npix;
         if (npix == 0) continue;
         const long long ax = T.ax, ay = T.ay, bx = T.bx, by = T.by, qx = T.qx, qy = T.qy;
@@ -279,7 +287,7 @@ __global__ void __launch_bounds__(kVertTile) contour_kernel(const CapDesc* __res
 // raster, depth test, silhouette edges, contour set (the z-buffers must be
 // cleared and the visibility counters zeroed before)
 void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
-    if (T.tri) raster_kernel<<<T.tri, kTriTile, 0, st>>>(dC, T.tri_items);
+    if (T.tri) raster_kernel<<<T.tri, kRasterThreads, 0, st>>>(dC, T.tri_items);
     vis_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);
     if (T.medge) silhouette_kernel<<<T.medge, kEdgeTile, 0, st>>>(dC, T.medge_items);
     contour_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items);

@@ -301,6 +301,7 @@ void lc_ctx::enqueue_pose() {
     mark(LC_PH_POSE);
     cudaMemsetAsync(P.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemcpyAsync(P.pose_start, P.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
+    mark(LC_PH_POSE_VIS);
     launch_pose_fk(S.d, st);
     launch_pose_skin(dC, hC, S.d, nullptr, 0, st);
     launch_vis_unfreeze(dC, st);
@@ -309,14 +310,19 @@ void lc_ctx::enqueue_pose() {
     // step 0 linearises at the start pose, whose b_i the contour pass just
     // decided on the same vertices; later steps re-decide them
     for (int g = 0; g < params.n_gn_pose; ++g) {
+        mark(LC_PH_POSE_SYS);
         if (g > 0) launch_pose_dirs(dC, hC, S.d, st);
         launch_pose_system(dC, hC, S.d, P.J, P.n_dof, st);
+        mark(LC_PH_POSE_SOLVE);
         launch_pose_solve(S.d, g, 0, st);
     }
+    mark(LC_PH_POSE_SYS);
     launch_pose_dirs(dC, hC, S.d, st);
     launch_pose_system(dC, hC, S.d, P.J, P.n_dof, st);
+    mark(LC_PH_POSE_SOLVE);
     launch_pose_solve(S.d, params.n_gn_pose, 1, st);
     // the skinned mesh becomes the rest geometry of the non-rigid stage
+    mark(LC_PH_POSE);
     launch_pose_skin(dC, hC, S.d, base_buf, 1, st);
     if (has_graph) launch_gather_nodes(base_buf, hC.node_vid, hC.n, (float4*)hC.node_g, st);
     mark_end();

@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     __shared__ double A[kMaxDof][kMaxDof + 1];
     __shared__ double invd[kMaxDof];
     __shared__ double w[kMaxDof + 1];
-    __shared__ double colbuf[2][kMaxDof + 1];
+    __shared__ double colk[kMaxDof + 1];
     __shared__ double y[kMaxDof];
     __shared__ double prior_t[kMaxDof];
     __shared__ PoseFk fk;
@@ -433,77 +433,60 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         return;
     }
     // Square-root-free Cholesky A = L D L^T (FP64) of the matrix augmented
-    // with g, right-looking: after pivot k the trailing block holds the Schur
-    // complement and column nd the forward-substituted right-hand side.
-    // GB300's FP64 pipe has a long latency and a low rate per SM, so the
-    // entries of the packed lower triangle (and of column nd) live in
-    // registers, round-robin over the threads; the owners publish column k
-    // (and A[k][nd]) to shared memory as soon as it is final.  Per pivot:
-    // every thread forms 1/d_k itself (FP32 seed, two Newton steps
-    // y <- y (2 - d y), no division), the row multipliers
-    // w_i = A_ik / d_k are formed once (they are L's column k), then one FMA
-    // per trailing entry.  Two block barriers per pivot.
-    constexpr int kEnt = (kMaxDof * (kMaxDof + 1) / 2 + kMaxDof + kSolveThreads - 1) / kSolveThreads;
-    const int ntri = nd * (nd + 1) / 2;
-    double ra[kEnt];
-    int ri[kEnt], rj[kEnt];
-#pragma unroll
-    for (int e = 0; e < kEnt; ++e) {
-        const int q = tid + e * kSolveThreads;
-        int i = -1, j = -1;
-        if (q < ntri) {
-            i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-            while (i * (i + 1) / 2 > q) --i;
-            while ((i + 1) * (i + 2) / 2 <= q) ++i;
-            j = q - i * (i + 1) / 2;
-        } else if (q < ntri + nd) {
-            i = q - ntri;
-            j = nd;
-        }
-        ri[e] = i;
-        rj[e] = j;
-        ra[e] = i >= 0 ? A[i][j] : 0.0;
-        if (j == 0) colbuf[0][i] = ra[e];           // column 0 and A[0][nd]
-        if (j == nd && i == 0) colbuf[0][nd] = ra[e];
-    }
+    // with g, right-looking: after pivot k the trailing lower triangle holds
+    // the Schur complement and column nd the forward-substituted right-hand
+    // side.  GB300's FP64 pipe is slow per warp instruction, so per pivot:
+    // warp 0 alone forms 1/d_k (FP32 seed refined by two Newton steps
+    // y <- y (2 - d y), no division) and the multipliers w_i = A_ik / d_k
+    // (L's column k, stored in place; the unscaled column kept in colk); one
+    // block barrier; then the trailing lower triangle and column nd, packed
+    // densely over all threads so that every FP64 warp instruction carries
+    // 32 useful FMAs; one block barrier.
     for (int k = 0; k < nd; ++k) {
-        __syncthreads();   // column k published; pivot k-1's updates and reads done
-        const double* col = colbuf[k & 1];
-        const double d = col[k];
-        double r;
-        const float fd = (float)d;
-        if (fd > 1e-30f && fd < 1e30f) {
-            r = (double)(1.0f / fd);
-            r = r * fma(-d, r, 2.0);
-            r = r * fma(-d, r, 2.0);
-        } else {
-            r = d > 0.0 ? 1.0 / d : 0.0;
-        }
         const int m = nd - k - 1;
-        if (tid <= m) {
-            // L_ik (rows k+1 .. nd-1) and y_k = A[k][nd] / d_k
-            const double wv = (tid < m ? col[k + 1 + tid] : col[nd]) * r;
-            w[tid] = wv;
-            if (tid < m) A[k + 1 + tid][k] = wv;
-            else y[k] = wv;
-        }
-        if (tid == 0) {
-            if (!(d > 0.0)) s_bad = 1;
-            invd[k] = r;
-        }
-        __syncthreads();
-        double* nxt = colbuf[(k + 1) & 1];
-#pragma unroll
-        for (int e = 0; e < kEnt; ++e) {
-            const int i = ri[e], j = rj[e];
-            if (i > k && (j == nd || j > k)) {
-                ra[e] = fma(-w[i - k - 1], col[j == nd ? nd : j], ra[e]);
-                if (j == k + 1) nxt[i] = ra[e];
-                else if (j == nd && i == k + 1) nxt[nd] = ra[e];
+        if (tid < 32) {
+            const double d = A[k][k];
+            double r;
+            const float fd = (float)d;
+            if (fd > 1e-30f && fd < 1e30f) {
+                r = (double)__frcp_rn(fd);
+                r = r * fma(-d, r, 2.0);
+                r = r * fma(-d, r, 2.0);
+            } else {
+                r = d > 0.0 ? 1.0 / d : 0.0;
+            }
+            for (int t = tid; t <= m; t += 32) {
+                const double c = t < m ? A[k + 1 + t][k] : A[k][nd];
+                colk[t] = c;
+                const double wv = c * r;
+                w[t] = wv;
+                if (t < m) A[k + 1 + t][k] = wv;
+                else y[k] = wv;
+            }
+            if (tid == 0) {
+                if (!(d > 0.0)) s_bad = 1;
+                invd[k] = r;
             }
         }
+        __syncthreads();
+        const int tri = m * (m + 1) / 2;
+        for (int q = tid; q < tri + m; q += kSolveThreads) {
+            if (q < tri) {
+                // packed row-major trailing triangle: q -> (ii, jj), jj <= ii
+                int ii = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+                while (ii * (ii + 1) / 2 > q) --ii;
+                while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+                const int jj = q - ii * (ii + 1) / 2;
+                double& a = A[k + 1 + ii][k + 1 + jj];
+                a = fma(-w[ii], colk[jj], a);
+            } else {
+                const int ii = q - tri;
+                double& a = A[k + 1 + ii][nd];
+                a = fma(-w[ii], colk[m], a);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // x = L^-T y, column by column in one warp (L stored below the diagonal of A)
     if (tid < 32) {
         for (int k = nd - 1; k >= 0; --k) {

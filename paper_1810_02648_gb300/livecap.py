@@ -113,7 +113,8 @@ _SIGS = {
     "lc_visibility_noalloc": [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_int, ctypes.c_int, ctypes.c_float, _P, _P],
 }
-PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose", "pcg"]
+PHASES = ["warp", "visibility", "linearize", "rhs", "pcg_init", "jtj", "pcg_vec", "update", "pose", "pcg",
+          "pose_vis", "pose_system", "pose_solve"]
 
 _lib = None
 
