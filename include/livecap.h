@@ -92,6 +92,10 @@ typedef struct {
     float w_acceleration; /* default 10 */
     int n_gn_surface;     /* Gauss-Newton steps, default 3 (Sec. 4), <= LC_MAX_GN */
     int n_pcg_surface;    /* PCG iterations per step, default 4 (Sec. 4) */
+    int pose_solver;      /* pose stage normal equations: 0 (default) mixed precision
+                             (FP32 inverse by a symmetric sweep, FP64 residuals,
+                             iterative refinement to 1e-10; the FP64 L D L^T when
+                             that does not converge); 1: always the FP64 L D L^T */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -101,7 +105,9 @@ typedef struct {
     double e_photo, e_sil, e_arap, e_total;  /* after the last update */
     double e_gn[LC_MAX_GN];                  /* total energy at each linearisation */
     double step_norm[LC_MAX_GN];             /* ||delta|| of each step */
-    int pcg_iters[LC_MAX_GN];                /* PCG iterations actually run */
+    int pcg_iters[LC_MAX_GN];                /* PCG iterations actually run (pose stage: rounds of
+                                                the mixed-precision refinement of each step's
+                                                solve, -1 where the FP64 factorisation ran) */
     int n_gn_done;
     int n_visible;                           /* |V| photometric vertices */
     int n_boundary;                          /* |B| contour vertices */

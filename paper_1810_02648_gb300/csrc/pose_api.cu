@@ -71,7 +71,8 @@ void lc_ctx::pose_release() {
                     (void*)pose->h.skin_idx, (void*)pose->h.skin_w, (void*)pose->h.j2d, (void*)pose->h.j3d,
                     (void*)pose->h.level, (void*)pose->h.pairs, pose->h.fk, pose->h.part,
                     pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.blist,
-                    pose->h.bcount, pose->h.hist, pose->h.expA, pose->h.status, pose->d, pose->pose_set};
+                    pose->h.bcount, pose->h.hist, pose->h.info, pose->h.expA, pose->h.status, pose->d,
+                    pose->pose_set};
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
@@ -137,6 +138,7 @@ static void apply_pose_params(lc_ctx* ctx) {
     P.lam_3d = ctx->params.lambda_3d;
     P.lam_sil = ctx->params.lambda_sil;
     P.lam_prior = ctx->params.lambda_prior;
+    P.solver = ctx->params.pose_solver;
 }
 
 extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* parents, const float* joints_rest,
@@ -209,6 +211,7 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     P.blist = (int*)ctx->alloc(sizeof(int) * N);
     P.bcount = (int*)ctx->alloc(sizeof(int));
     P.hist = (double*)ctx->alloc(sizeof(double) * 2 * (LC_MAX_GN + 1));
+    P.info = (int*)ctx->alloc(sizeof(int) * (LC_MAX_GN + 1));
     P.expA = (double*)ctx->alloc(sizeof(double) * nd * (nd + 1));
     P.status = (int*)ctx->alloc(sizeof(int));
     S.d = (PoseDesc*)ctx->alloc(sizeof(PoseDesc));
@@ -300,6 +303,7 @@ void lc_ctx::enqueue_pose() {
     prof_pose.begin = prof_used;
     mark(LC_PH_POSE);
     cudaMemsetAsync(P.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
+    cudaMemsetAsync(P.info, 0, sizeof(int) * (LC_MAX_GN + 1), st);
     cudaMemcpyAsync(P.pose_start, P.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
     mark(LC_PH_POSE_VIS);
     launch_pose_fk(S.d, st);
@@ -351,8 +355,10 @@ extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
     ctx->has_lin = false;
     if (stats) {
         std::vector<double> hist(2 * (LC_MAX_GN + 1));
+        std::vector<int> info(LC_MAX_GN + 1);
         int status = 0, nb = 0;
         if ((s = ctx->copy_to_host(hist.data(), S.h.hist, sizeof(double) * hist.size())) ||
+            (s = ctx->copy_to_host(info.data(), S.h.info, sizeof(int) * info.size())) ||
             (s = ctx->copy_to_host(&status, S.h.status, sizeof(int))) ||
             (s = ctx->copy_to_host(&nb, S.h.bcount, sizeof(int))))
             return s;
@@ -361,6 +367,7 @@ extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
         for (int k = 0; k < g; ++k) {
             stats->e_gn[k] = hist[2 * k];
             stats->step_norm[k] = hist[2 * k + 1];
+            stats->pcg_iters[k] = info[k];
         }
         stats->e_total = hist[2 * g];
         stats->n_gn_done = g;

@@ -21,6 +21,7 @@ struct PoseDesc {
     int J, n_dof, n_levels;
     int has_j2d, has_j3d;
     float lam_2d, lam_3d, lam_sil, lam_prior;
+    int solver;                       // 0: mixed-precision refinement, 1: FP64 L D L^T
     const int* parents;               // J
     const int* level;                 // J: depth in the tree (root 0)
     const unsigned short* pairs;      // (n_dof + 1)(n_dof + 2) / 2: a << 8 | b, column pairs a <= b of [J | F]
@@ -40,6 +41,7 @@ struct PoseDesc {
     int* blist;                       // N contour vertices
     int* bcount;
     double* hist;                     // 2 (LC_MAX_GN + 1): energy, step norm
+    int* info;                        // LC_MAX_GN + 1: refinement rounds of each step's solve (-1: FP64 factorisation)
     double* expA;                     // n_dof x (n_dof + 1) exported system (inspection)
     int* status;                      // 1: non-positive Cholesky pivot
 };

@@ -376,34 +376,112 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
+constexpr int kTri = kMaxDof * (kMaxDof + 1) / 2;   // packed lower triangle of the normal matrix
+constexpr int kGs = kMaxDof + 2;                     // FP32 inverse row stride (odd: conflict-free columns)
+constexpr int kSeg = 8;                              // partial dot products per row of the FP64 residual
+constexpr int kMaxRefine = 12;
+
+__device__ __forceinline__ int tri_at(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// FP64 right-looking square-root-free Cholesky (L D L^T) of the packed lower
+// triangle Ap with right-hand side g, in place; y <- D^-1 L^-1 g, L scaled
+// below the diagonal.  The robust path, taken when the mixed-precision solve
+// does not converge.  Per pivot warp 0 forms 1/d_k (FP32 seed, two Newton
+// steps) and the multipliers; then the trailing triangle densely over the CTA.
+__device__ void ldlt_f64(double* Ap, double* g, double* colk, double* w, double* y, int nd, int tid, int* bad) {
+    for (int k = 0; k < nd; ++k) {
+        const int m = nd - k - 1;
+        if (tid < 32) {
+            const double d = Ap[tri_at(k, k)];
+            double r;
+            const float fd = (float)d;
+            if (fd > 1e-30f && fd < 1e30f) {
+                r = (double)(1.0f / fd);
+                r = r * fma(-d, r, 2.0);
+                r = r * fma(-d, r, 2.0);
+            } else {
+                r = d > 0.0 ? 1.0 / d : 0.0;
+            }
+            for (int t = tid; t <= m; t += 32) {
+                const double c = t < m ? Ap[tri_at(k + 1 + t, k)] : g[k];
+                colk[t] = c;
+                const double wv = c * r;
+                w[t] = wv;
+                if (t < m) Ap[tri_at(k + 1 + t, k)] = wv;
+                else y[k] = wv;
+            }
+            if (tid == 0 && !(d > 0.0)) *bad = 1;
+        }
+        __syncthreads();
+        const int tri = m * (m + 1) / 2;
+        for (int q = tid; q < tri + m; q += kSolveThreads) {
+            if (q < tri) {
+                int ii = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+                while (ii * (ii + 1) / 2 > q) --ii;
+                while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+                const int jj = q - ii * (ii + 1) / 2;
+                double& a = Ap[tri_at(k + 1 + ii, k + 1 + jj)];
+                a = fma(-w[ii], colk[jj], a);
+            } else {
+                const int ii = q - tri;
+                g[k + 1 + ii] = fma(-w[ii], colk[m], g[k + 1 + ii]);
+            }
+        }
+        __syncthreads();
+    }
+    // x = L^-T y in one warp
+    if (tid < 32) {
+        for (int k = nd - 1; k >= 0; --k) {
+            const double xk = y[k];
+            for (int i = tid; i < k; i += 32) y[i] = fma(-Ap[tri_at(k, i)], xk, y[i]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDesc* __restrict__ pd, int slot,
                                                                   int mode) {
-    __shared__ double A[kMaxDof][kMaxDof + 1];
-    __shared__ double invd[kMaxDof];
+    __shared__ double Ap[kTri];               // FP64 normal matrix, packed lower triangle
+    __shared__ double g[kMaxDof];             // -J^T F (+ prior)
+    __shared__ double x[kMaxDof];             // solution
+    __shared__ double rs[kMaxDof];            // residual g - A x
+    __shared__ double part4[kMaxDof * kSeg];  // residual partial sums
     __shared__ double w[kMaxDof + 1];
     __shared__ double colk[kMaxDof + 1];
-    __shared__ double y[kMaxDof];
     __shared__ double prior_t[kMaxDof];
+    __shared__ float Gf[kMaxDof * kGs];       // FP32 inverse (Gauss-Jordan, in place)
+    __shared__ float colb[2][kMaxDof], rf[kMaxDof], redc[4], redx[4];
     __shared__ PoseFk fk;
     __shared__ float s_ftf;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_fail, s_conv, s_rounds;
     const PoseDesc& P = *pd;
     const int nd = P.n_dof, na = nd + 1;
     const int npairs = na * (na + 1) / 2;
     const int nact = (2 * P.J + *P.bcount + kSysItems - 1) / kSysItems;
     const int tid = threadIdx.x;
-    if (tid == 0) s_bad = 0;
-    // partial pair sums of the row CTAs, added in CTA order
+    if (tid == 0) {
+        s_bad = 0;
+        s_fail = 0;
+    }
+    // partial pair sums of the row CTAs, added in CTA order; the loads of a
+    // round of 8 CTAs are issued together before any is added
     for (int p = tid; p < npairs; p += kSolveThreads) {
         float v = 0.f;
-        for (int c = 0; c < nact; ++c) v += P.part[(size_t)c * npairs + p];
+        for (int c0 = 0; c0 < nact; c0 += 8) {
+            float pv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) pv[u] = c0 + u < nact ? __ldcg(&P.part[(size_t)(c0 + u) * npairs + p]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < nact) v += pv[u];
+        }
         const unsigned pr = P.pairs[p];
         const int a = (int)(pr >> 8), b = (int)(pr & 255u);
         if (b < nd) {
-            A[a][b] = (double)v;
-            A[b][a] = (double)v;
+            Ap[tri_at(b, a)] = (double)v;
         } else if (a < nd) {
-            A[a][nd] = -(double)v;          // g = -J^T F
+            g[a] = -(double)v;              // g = -J^T F
         } else {
             s_ftf = v;                      // F^T F
         }
@@ -414,8 +492,8 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         double e = 0.0;
         if (tid >= 6) {
             const double dv = (double)P.pose[tid] - (double)P.pose_start[tid];
-            A[tid][tid] += (double)P.lam_prior;
-            A[tid][nd] -= (double)P.lam_prior * dv;
+            Ap[tri_at(tid, tid)] += (double)P.lam_prior;
+            g[tid] -= (double)P.lam_prior * dv;
             e = (double)P.lam_prior * dv * dv;
         }
         prior_t[tid] = e;
@@ -429,71 +507,171 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     }
     if (mode == 1) return;
     if (mode == 2) {
-        for (int q = tid; q < nd * (nd + 1); q += kSolveThreads) P.expA[q] = A[q / (nd + 1)][q % (nd + 1)];
+        for (int q = tid; q < nd * (nd + 1); q += kSolveThreads) {
+            const int i = q / (nd + 1), j = q % (nd + 1);
+            P.expA[q] = j < nd ? Ap[tri_at(i, j)] : g[i];
+        }
         return;
     }
-    // Square-root-free Cholesky A = L D L^T (FP64) of the matrix augmented
-    // with g, right-looking: after pivot k the trailing lower triangle holds
-    // the Schur complement and column nd the forward-substituted right-hand
-    // side.  GB300's FP64 pipe is slow per warp instruction, so per pivot:
-    // warp 0 alone forms 1/d_k (FP32 seed refined by two Newton steps
-    // y <- y (2 - d y), no division) and the multipliers w_i = A_ik / d_k
-    // (L's column k, stored in place; the unscaled column kept in colk); one
-    // block barrier; then the trailing lower triangle and column nd, packed
-    // densely over all threads so that every FP64 warp instruction carries
-    // 32 useful FMAs; one block barrier.
-    for (int k = 0; k < nd; ++k) {
-        const int m = nd - k - 1;
-        if (tid < 32) {
-            const double d = A[k][k];
-            double r;
-            const float fd = (float)d;
-            if (fd > 1e-30f && fd < 1e30f) {
-                r = (double)__frcp_rn(fd);
-                r = r * fma(-d, r, 2.0);
-                r = r * fma(-d, r, 2.0);
-            } else {
-                r = d > 0.0 ? 1.0 / d : 0.0;
+    // Solve A x = g to FP64 accuracy.  GB300's FP64 pipe is slow per warp
+    // instruction and the 57 pivots of a factorisation form a serial chain,
+    // so the factorisation runs in FP32 and FP64 only enters the residual
+    // (mixed-precision iterative refinement):
+    //   Gf = A^-1 in FP32 by in-place Gauss-Jordan (A is positive definite:
+    //        no pivoting; two block barriers per pivot);
+    //   x = 0, r = g; repeat  x += Gf r (FP32 product), r = g - A x (FP64)
+    //   until the correction is below 1e-10 of x (the FP64 residual's floor
+    //   is ~cond(A) 1e-16).
+    // A non-positive or non-finite FP32 pivot, or no convergence in
+    // kMaxRefine rounds, falls back to the FP64 L D L^T of the same system.
+    // Symmetric sweep (Gauss-Jordan for a symmetric matrix, lower triangle
+    // only): per pivot k with d = a_kk and the old column c,
+    //   a_ij -= c_i c_j / d (i, j != k),  a_ik = c_i / d,  a_kk = -1 / d;
+    // after all pivots the triangle holds -A^-1.  Each thread keeps its
+    // entries of the packed triangle in registers (round-robin); the owners
+    // publish column k + 1 (double-buffered), so one block barrier per pivot;
+    // every thread forms 1 / d itself (FP32).
+    constexpr int kPer = (kTri + kSolveThreads - 1) / kSolveThreads;
+    const int ntri = nd * (nd + 1) / 2;
+    float ga[kPer];
+    int gi[kPer], gj[kPer];
+#pragma unroll
+    for (int sI = 0; sI < kPer; ++sI) {
+        const int e = tid + kSolveThreads * sI;
+        int i = -1, j = -1;
+        if (e < ntri) {
+            i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while (i * (i + 1) / 2 > e) --i;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            j = e - i * (i + 1) / 2;
+        }
+        gi[sI] = i;
+        gj[sI] = j;
+        ga[sI] = e < ntri ? (float)Ap[e] : 0.f;
+        if (j == 0) colb[0][i] = ga[sI];
+    }
+    bool ok32 = P.solver == 0;
+    for (int k = 0; ok32 && k < nd; ++k) {
+        __syncthreads();
+        const float* c = colb[k & 1];
+        float* cn = colb[(k + 1) & 1];
+        const float d = c[k];
+        if (!(d > 0.f) || !(d < 3.0e38f)) {
+            ok32 = false;                            // uniform: every thread read the same pivot
+            break;
+        }
+        const float r = __frcp_rn(d);
+#pragma unroll
+        for (int sI = 0; sI < kPer; ++sI) {
+            const int i = gi[sI], j = gj[sI];
+            if (i >= 0) {
+                float a = ga[sI];
+                if (i == k) a = j == k ? -r : c[j] * r;
+                else if (j == k) a = c[i] * r;
+                else a = fmaf(-c[i] * r, c[j], a);
+                ga[sI] = a;
+                if (j == k + 1) cn[i] = a;
+                if (i == k + 1) cn[j] = a;
             }
-            for (int t = tid; t <= m; t += 32) {
-                const double c = t < m ? A[k + 1 + t][k] : A[k][nd];
-                colk[t] = c;
-                const double wv = c * r;
-                w[t] = wv;
-                if (t < m) A[k + 1 + t][k] = wv;
-                else y[k] = wv;
+        }
+    }
+    if (ok32) {
+#pragma unroll
+        for (int sI = 0; sI < kPer; ++sI) {
+            const int i = gi[sI], j = gj[sI];
+            if (i >= 0) {
+                Gf[i * kGs + j] = -ga[sI];
+                Gf[j * kGs + i] = -ga[sI];
             }
-            if (tid == 0) {
-                if (!(d > 0.0)) s_bad = 1;
-                invd[k] = r;
-            }
+        }
+    }
+    __syncthreads();
+    if (ok32) {
+        if (tid < nd) {
+            x[tid] = 0.0;
+            rs[tid] = g[tid];
         }
         __syncthreads();
-        const int tri = m * (m + 1) / 2;
-        for (int q = tid; q < tri + m; q += kSolveThreads) {
-            if (q < tri) {
-                // packed row-major trailing triangle: q -> (ii, jj), jj <= ii
-                int ii = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-                while (ii * (ii + 1) / 2 > q) --ii;
-                while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-                const int jj = q - ii * (ii + 1) / 2;
-                double& a = A[k + 1 + ii][k + 1 + jj];
-                a = fma(-w[ii], colk[jj], a);
-            } else {
-                const int ii = q - tri;
-                double& a = A[k + 1 + ii][nd];
-                a = fma(-w[ii], colk[m], a);
+        double cm_prev = 0.0;   // thread 0: the last correction
+        for (int it = 0; it < kMaxRefine; ++it) {
+            // correction c = Gf r (FP32), x += c; the largest |c| and |x|
+            if (tid < nd) rf[tid] = (float)rs[tid];
+            __syncthreads();
+            if (tid < 2 * 64) {
+                // two threads per row, the halves added in a fixed order
+                const int i = tid >> 1, h = tid & 1;
+                float c = 0.f;
+                if (i < nd)
+                    for (int j = h; j < nd; j += 2) c = fmaf(Gf[i * kGs + j], rf[j], c);
+                c += __shfl_xor_sync(0xffffffffu, c, 1);
+                float cmax = 0.f, xmax = 0.f;          // magnitudes for the stopping test
+                if (i < nd && h == 0) {
+                    const double xn = x[i] + (double)c;
+                    x[i] = xn;
+                    cmax = fabsf(c);
+                    xmax = fabsf((float)xn);
+                    if (!(cmax < 3.0e38f) || !(xmax < 3.0e38f)) s_fail = 1;   // non-finite (read after the barrier)
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+                }
+                if ((tid & 31) == 0) {
+                    redc[tid >> 5] = cmax;
+                    redx[tid >> 5] = xmax;
+                }
             }
+            __syncthreads();
+            if (tid == 0) {
+                // converged: the correction is below 1e-10 of x; or the
+                // corrections stopped shrinking (the FP64 residual's rounding
+                // floor, ~n cond(A) 1e-16) at <= 1e-6 of x; a stall above
+                // that is a failure (the FP32 inverse does not contract)
+                const double cm = fmaxf(fmaxf(redc[0], redc[1]), fmaxf(redc[2], redc[3]));
+                const double xm = fmaxf(fmaxf(redx[0], redx[1]), fmaxf(redx[2], redx[3]));
+                int conv = cm <= 1e-10 * xm ? 1 : 0;
+                if (!conv && it > 0 && cm > 0.5 * cm_prev) {
+                    if (cm <= 1e-6 * xm) conv = 1;
+                    else s_fail = 1;
+                }
+                s_conv = conv;
+                s_rounds = it + 1;
+                cm_prev = cm;
+            }
+            __syncthreads();
+            if (s_conv || s_fail) break;
+            // r = g - A x in FP64: kSeg partial products per row, then one sum per row
+            if (tid < nd * kSeg) {
+                const int i = tid / kSeg, sg = tid - i * kSeg;
+                const int j0 = sg * ((nd + kSeg - 1) / kSeg), j1 = min(nd, j0 + (nd + kSeg - 1) / kSeg);
+                double acc = 0.0;
+                for (int j = j0; j < j1; ++j) acc = fma(Ap[tri_at(i, j)], x[j], acc);
+                part4[tid] = acc;
+            }
+            __syncthreads();
+            if (tid < nd) {
+                double a = 0.0;
+                for (int sg = 0; sg < kSeg; ++sg) a += part4[tid * kSeg + sg];
+                rs[tid] = g[tid] - a;
+            }
+            __syncthreads();
         }
+        if (tid == 0 && !s_conv) s_fail = 1;
         __syncthreads();
     }
-    // x = L^-T y, column by column in one warp (L stored below the diagonal of A)
+    double* y = rs;     // the solution handed to the update: x, or the fallback's
+    const bool fallback = !ok32 || s_fail;
+    if (fallback) {
+        ldlt_f64(Ap, g, colk, w, rs, nd, tid, &s_bad);
+    } else if (tid < nd) {
+        rs[tid] = x[tid];
+    }
+    if (tid == 0) P.info[slot] = fallback ? -1 : s_rounds;
+    __syncthreads();
+    // the pose update: one DOF per thread; the root rotation and the step
+    // norm by thread 0
+    if (!s_bad && tid >= 3 && tid < nd) P.pose[tid] += (float)y[tid];
     if (tid < 32) {
-        for (int k = nd - 1; k >= 0; --k) {
-            const double xk = y[k];
-            for (int i = tid; i < k; i += 32) y[i] = fma(-A[k][i], xk, y[i]);
-            __syncwarp();
-        }
         double n2 = 0.0;
         for (int c = tid; c < nd; c += 32) n2 += y[c] * y[c];
         n2 = warp_sum_f64(n2);
@@ -503,7 +681,6 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
                 P.hist[2 * slot + 1] = 0.0;
             } else {
                 P.hist[2 * slot + 1] = sqrt(n2);
-                for (int c = 3; c < nd; ++c) P.pose[c] += (float)y[c];
                 // R <- Exp(d_omega) R (Rodrigues, FP32)
                 const float wx = (float)y[0], wy = (float)y[1], wz = (float)y[2];
                 const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);

@@ -27,7 +27,7 @@ class lc_params(ctypes.Structure):
                 ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int),
                 ("target_energy", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_edge", ctypes.c_float),
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
-                ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int)]
+                ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):

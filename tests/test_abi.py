@@ -59,4 +59,4 @@ def test_params_default(lib):
     # of Sec. 5 read in millimetres, rescaled to metres and w_photo = 1
     assert (p.n_gn_surface, p.n_pcg_surface) == (3, 4)
     assert (p.w_smooth, p.w_edge, p.w_velocity, p.w_acceleration) == (1e3, 3e3, 25.0, 10.0)
-    assert p.target_energy == 0.0
+    assert p.target_energy == 0.0 and p.pose_solver == 0

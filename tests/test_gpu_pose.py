@@ -92,7 +92,11 @@ def test_pose_solve_matches_oracle(body):
     dh = np.abs(np.array(st["e_gn"]) - [h["energy"] for h in hist]).max() / hist[0]["energy"]
     gt = body.meta["joints_gt"]
     report("pose_solve", dj=dj, de=de, dh=dh, e_gpu=st["e_total"], e_ref=e_ref,
-           jerr_gpu=np.linalg.norm(o_gpu - gt, axis=1).mean(), jerr_ref=np.linalg.norm(o_ref - gt, axis=1).mean())
+           jerr_gpu=np.linalg.norm(o_gpu - gt, axis=1).mean(), jerr_ref=np.linalg.norm(o_ref - gt, axis=1).mean(),
+           refine_rounds=max(st["pcg_iters"]))
+    # every step's normal equations were solved by the mixed-precision
+    # refinement (FP32 inverse, FP64 residuals), not by its FP64 fallback
+    assert all(1 <= r <= 12 for r in st["pcg_iters"]), st["pcg_iters"]
     assert st["n_boundary"] == int(pb.inB.sum())
     assert dj <= 2e-3          # metres; the joints are well determined
     assert de <= 1e-2 and dh <= 1e-3
@@ -220,3 +224,51 @@ def test_pose_numeric_error_is_reported(body):
         ctx.solve_pose()
     assert ei.value.status == -4
     ctx.close()
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_pose_solver_paths_agree(body, solver):
+    """The mixed-precision solve (default) and the FP64 L D L^T (pose_solver
+    1) give the same poses up to FP32 rounding of the update, both matching
+    the oracle's Cholesky steps."""
+    ctx = _ctx(body, pose_solver=solver)
+    st = ctx.solve_pose()
+    pose = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    ref = _ctx(body, pose_solver=1 - solver)
+    ref.solve_pose()
+    pose_other = ref.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    report(f"pose_solver_{solver}", rounds=max(st["pcg_iters"]), dpose=np.abs(pose - pose_other).max())
+    if solver == 1:
+        assert st["pcg_iters"] == [-1] * body.n_gn_pose
+    else:
+        assert all(1 <= r <= 12 for r in st["pcg_iters"])
+    assert np.abs(pose - pose_other).max() <= 1e-5
+    ctx.close()
+    ref.close()
+
+
+def test_pose_solve_ill_conditioned(body):
+    """A nearly singular system (a weak angle prior leaves the bone twists
+    almost free; condition number ~3e8), solved by either path.  Along the
+    near-null directions the step is set by rounding in the FP32-accumulated
+    J^T J (~1e-7 relative, amplified by the condition number), so it is not
+    compared with the oracle's step; what a solver must deliver is checked
+    instead: the step satisfies the normal equations the kernel assembled
+    (exported at the same pose), relative residual <= 1e-4 (the step is read
+    back through the FP32 pose, ~1e-7 relative per component)."""
+    lam = 1e-2
+    for solver in (0, 1):
+        ctx = _ctx(body, lambda_prior=lam, n_gn_pose=1, pose_solver=solver)
+        ev = ctx.eval_pose()
+        st = ctx.solve_pose()
+        pose1 = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"].astype(np.float64)
+        pose0 = np.asarray(body.pose_init, dtype=np.float32).astype(np.float64)
+        R0 = onr.so3_exp(pose0[None, :3])[0]
+        R1 = onr.so3_exp(pose1[None, :3])[0]
+        delta = np.concatenate([onr.so3_log(R1 @ R0.T)[0], pose1[3:] - pose0[3:]])
+        res = np.abs(ev["A"] @ delta - ev["g"]).max() / np.abs(ev["g"]).max()
+        report(f"pose_ill_conditioned_{solver}", rounds=st["pcg_iters"][0], residual=res, step=np.abs(delta).max())
+        assert st["pcg_iters"][0] == -1 if solver == 1 else st["pcg_iters"][0] in [-1] + list(range(1, 13))
+        assert np.isfinite(pose1).all()
+        assert res <= 1e-4
+        ctx.close()
