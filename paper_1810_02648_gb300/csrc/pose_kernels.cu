@@ -20,8 +20,10 @@
 // set; the residual rows built in shared memory by a grid of CTAs, each
 // reducing its rows to FP32 partial sums of the pairs of [J | F] columns; one
 // CTA summing the partials in a fixed order into the FP64 normal equations,
-// factorising them by Cholesky (pivot <= 0 sets a status word), updating the
-// pose and computing the next forward kinematics - no host round trip.
+// solving them to FP64 accuracy (an FP32 inverse refined with FP64
+// residuals, or an FP64 L D L^T whose pivot <= 0 sets a status word),
+// updating the pose and computing the next forward kinematics - no host round
+// trip.
 #include "lc_internal.cuh"
 #include "pose_internal.h"
 
@@ -39,11 +41,48 @@ __device__ __forceinline__ void mat3mul(const float* A, const float* B, float* C
 // parent's frame is final before its children read it).  Every thread of
 // the CTA must call this (it synchronises).
 __device__ void forward_kinematics(const PoseDesc& P, PoseFk& fk) {
+    // the joint's local rotation L = Rx(a) Ry(b) Rz(c) and its Euler axes in
+    // the parent frame (e_x, Rx e_y, Rx Ry e_z) first, for every joint at once;
+    // then the tree level by level: G_j = G_p L, U_j = G_p [axes],
+    // o_j = o_p + G_p (J_j - J_p)
     const int j = threadIdx.x;
     const float* pose = P.pose;
+    float L[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float Ax[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};   // columns: the three axes
+    int p = -1, lvl_j = -1, c = -1;
+    float d[3] = {0.f, 0.f, 0.f};
+    if (j < P.J) {
+        p = P.parents[j];
+        lvl_j = P.level[j];
+        c = P.col[j];
+        if (p >= 0) {
+            const float4 rj = P.rest[j], rp = P.rest[p];
+            d[0] = rj.x - rp.x;
+            d[1] = rj.y - rp.y;
+            d[2] = rj.z - rp.z;
+        }
+        if (p >= 0 && c >= 0) {
+            float sa, ca, sb, cb, sc, cc;
+            sincosf(pose[c], &sa, &ca);
+            sincosf(pose[c + 1], &sb, &cb);
+            sincosf(pose[c + 2], &sc, &cc);
+            const float Rx[9] = {1.f, 0.f, 0.f, 0.f, ca, -sa, 0.f, sa, ca};
+            const float Ry[9] = {cb, 0.f, sb, 0.f, 1.f, 0.f, -sb, 0.f, cb};
+            const float Rz[9] = {cc, -sc, 0.f, sc, cc, 0.f, 0.f, 0.f, 1.f};
+            float RxRy[9];
+            mat3mul(Rx, Ry, RxRy);
+            mat3mul(RxRy, Rz, L);
+            // axes as columns: e_x, Rx e_y, Rx Ry e_z
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                Ax[3 * r] = r == 0 ? 1.f : 0.f;
+                Ax[3 * r + 1] = Rx[3 * r + 1];
+                Ax[3 * r + 2] = RxRy[3 * r + 2];
+            }
+        }
+    }
     for (int lvl = 0; lvl < P.n_levels; ++lvl) {
-        if (j < P.J && P.level[j] == lvl) {
-            const int p = P.parents[j];
+        if (lvl_j == lvl) {
             if (p < 0) {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) fk.G[j][q] = P.Rroot[q];
@@ -51,40 +90,30 @@ __device__ void forward_kinematics(const PoseDesc& P, PoseFk& fk) {
                 fk.o[j][1] = pose[4];
                 fk.o[j][2] = pose[5];
             } else {
-                const float4 rj = P.rest[j], rp = P.rest[p];
-                const float d[3] = {rj.x - rp.x, rj.y - rp.y, rj.z - rp.z};
                 float Gp[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) Gp[q] = fk.G[p][q];
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
                     fk.o[j][r] = fk.o[p][r] + Gp[3 * r] * d[0] + Gp[3 * r + 1] * d[1] + Gp[3 * r + 2] * d[2];
-                const int c = P.col[j];
+                float G[9];
                 if (c < 0) {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) fk.G[j][q] = Gp[q];
+                    for (int q = 0; q < 9; ++q) G[q] = Gp[q];
                 } else {
-                    float sa, ca, sb, cb, sc, cc;
-                    sincosf(pose[c], &sa, &ca);
-                    sincosf(pose[c + 1], &sb, &cb);
-                    sincosf(pose[c + 2], &sc, &cc);
-                    const float Rx[9] = {1.f, 0.f, 0.f, 0.f, ca, -sa, 0.f, sa, ca};
-                    const float Ry[9] = {cb, 0.f, sb, 0.f, 1.f, 0.f, -sb, 0.f, cb};
-                    const float Rz[9] = {cc, -sc, 0.f, sc, cc, 0.f, 0.f, 0.f, 1.f};
-                    float GRx[9], GRxRy[9], G[9];
-                    mat3mul(Gp, Rx, GRx);
-                    mat3mul(GRx, Ry, GRxRy);
-                    mat3mul(GRxRy, Rz, G);
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) fk.G[j][q] = G[q];
-                    // axes: G_p e_x, G_p Rx e_y, G_p Rx Ry e_z (columns)
+                    mat3mul(Gp, L, G);
+                    float U[9];
+                    mat3mul(Gp, Ax, U);
+                    // fk.U[j]: rows x, y, z of each axis: U[j][3 a + r] = (G_p axis_a)_r
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
-                        fk.U[j][r] = Gp[3 * r];
-                        fk.U[j][3 + r] = GRx[3 * r + 1];
-                        fk.U[j][6 + r] = GRxRy[3 * r + 2];
+                        fk.U[j][r] = U[3 * r];
+                        fk.U[j][3 + r] = U[3 * r + 1];
+                        fk.U[j][6 + r] = U[3 * r + 2];
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) fk.G[j][q] = G[q];
             }
         }
         __syncthreads();
@@ -451,10 +480,10 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     __shared__ double colk[kMaxDof + 1];
     __shared__ double prior_t[kMaxDof];
     __shared__ float Gf[kMaxDof * kGs];       // FP32 inverse (Gauss-Jordan, in place)
-    __shared__ float colb[2][kMaxDof], rf[kMaxDof], redc[4], redx[4];
+    __shared__ float colb[2][kMaxDof + 1], rf[kMaxDof], redc[4], redx[4];
     __shared__ PoseFk fk;
     __shared__ float s_ftf;
-    __shared__ int s_bad, s_fail, s_conv, s_rounds;
+    __shared__ int s_bad, s_fail, s_conv, s_rounds, s_ok32;
     const PoseDesc& P = *pd;
     const int nd = P.n_dof, na = nd + 1;
     const int npairs = na * (na + 1) / 2;
@@ -464,26 +493,40 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         s_bad = 0;
         s_fail = 0;
     }
-    // partial pair sums of the row CTAs, added in CTA order; the loads of a
-    // round of 8 CTAs are issued together before any is added
-    for (int p = tid; p < npairs; p += kSolveThreads) {
-        float v = 0.f;
+    // partial pair sums of the row CTAs, added in CTA order.  A thread's
+    // pairs (up to 4) and a round of 8 CTAs: their 32 loads are issued
+    // together before any is added (one L2 latency per round)
+    constexpr int kPairsPer = 4;
+    for (int p0 = tid; p0 < npairs; p0 += kPairsPer * kSolveThreads) {
+        float v[kPairsPer] = {0.f, 0.f, 0.f, 0.f};
         for (int c0 = 0; c0 < nact; c0 += 8) {
-            float pv[8];
+            float pv[kPairsPer][8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) pv[u] = c0 + u < nact ? __ldcg(&P.part[(size_t)(c0 + u) * npairs + p]) : 0.f;
+            for (int h = 0; h < kPairsPer; ++h)
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < nact) v += pv[u];
+                for (int u = 0; u < 8; ++u) {
+                    const int pp = p0 + h * kSolveThreads;
+                    pv[h][u] = (c0 + u < nact && pp < npairs) ? __ldcg(&P.part[(size_t)(c0 + u) * npairs + pp]) : 0.f;
+                }
+#pragma unroll
+            for (int h = 0; h < kPairsPer; ++h)
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c0 + u < nact) v[h] += pv[h][u];
         }
-        const unsigned pr = P.pairs[p];
-        const int a = (int)(pr >> 8), b = (int)(pr & 255u);
-        if (b < nd) {
-            Ap[tri_at(b, a)] = (double)v;
-        } else if (a < nd) {
-            g[a] = -(double)v;              // g = -J^T F
-        } else {
-            s_ftf = v;                      // F^T F
+#pragma unroll
+        for (int h = 0; h < kPairsPer; ++h) {
+            const int pp = p0 + h * kSolveThreads;
+            if (pp >= npairs) break;
+            const unsigned pr = P.pairs[pp];
+            const int a = (int)(pr >> 8), b = (int)(pr & 255u);
+            if (b < nd) {
+                Ap[tri_at(b, a)] = (double)v[h];
+            } else if (a < nd) {
+                g[a] = -(double)v[h];           // g = -J^T F
+            } else {
+                s_ftf = v[h];                   // F^T F
+            }
         }
     }
     __syncthreads();
@@ -517,11 +560,11 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     // instruction and the 57 pivots of a factorisation form a serial chain,
     // so the factorisation runs in FP32 and FP64 only enters the residual
     // (mixed-precision iterative refinement):
-    //   Gf = A^-1 in FP32 by in-place Gauss-Jordan (A is positive definite:
-    //        no pivoting; two block barriers per pivot);
+    //   Gf = A^-1 in FP32 by a symmetric sweep (A is positive definite: no
+    //        pivoting);
     //   x = 0, r = g; repeat  x += Gf r (FP32 product), r = g - A x (FP64)
-    //   until the correction is below 1e-10 of x (the FP64 residual's floor
-    //   is ~cond(A) 1e-16).
+    //   until the correction (or its extrapolated successor) is below 1e-10
+    //   of x (the FP64 residual's floor is ~cond(A) 1e-16).
     // A non-positive or non-finite FP32 pivot, or no convergence in
     // kMaxRefine rounds, falls back to the FP64 L D L^T of the same system.
     // Symmetric sweep (Gauss-Jordan for a symmetric matrix, lower triangle
@@ -530,62 +573,67 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     // after all pivots the triangle holds -A^-1.  Each thread keeps its
     // entries of the packed triangle in registers (round-robin); the owners
     // publish column k + 1 (double-buffered), so one block barrier per pivot;
-    // every thread forms 1 / d itself (FP32).
+    // every thread forms 1 / d itself (FP32).  The per-entry update is
+    // branch-free (selects, and a publish store that lands in a spare slot
+    // when the entry is not in column k + 1), so a thread's entries
+    // interleave.
     constexpr int kPer = (kTri + kSolveThreads - 1) / kSolveThreads;
-    const int ntri = nd * (nd + 1) / 2;
-    float ga[kPer];
-    int gi[kPer], gj[kPer];
-#pragma unroll
-    for (int sI = 0; sI < kPer; ++sI) {
-        const int e = tid + kSolveThreads * sI;
-        int i = -1, j = -1;
-        if (e < ntri) {
-            i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-            while (i * (i + 1) / 2 > e) --i;
-            while ((i + 1) * (i + 2) / 2 <= e) ++i;
-            j = e - i * (i + 1) / 2;
-        }
-        gi[sI] = i;
-        gj[sI] = j;
-        ga[sI] = e < ntri ? (float)Ap[e] : 0.f;
-        if (j == 0) colb[0][i] = ga[sI];
-    }
-    bool ok32 = P.solver == 0;
-    for (int k = 0; ok32 && k < nd; ++k) {
-        __syncthreads();
-        const float* c = colb[k & 1];
-        float* cn = colb[(k + 1) & 1];
-        const float d = c[k];
-        if (!(d > 0.f) || !(d < 3.0e38f)) {
-            ok32 = false;                            // uniform: every thread read the same pivot
-            break;
-        }
-        const float r = __frcp_rn(d);
+    constexpr int kSpare = kMaxDof;              // colb slot that absorbs non-publishing stores
+    {
+        const int ntri = nd * (nd + 1) / 2;
+        float ga[kPer];
+        int gi[kPer], gj[kPer];
 #pragma unroll
         for (int sI = 0; sI < kPer; ++sI) {
-            const int i = gi[sI], j = gj[sI];
-            if (i >= 0) {
-                float a = ga[sI];
-                if (i == k) a = j == k ? -r : c[j] * r;
-                else if (j == k) a = c[i] * r;
-                else a = fmaf(-c[i] * r, c[j], a);
+            const int e = tid + kSolveThreads * sI;
+            int i = kSpare, j = kSpare;              // padding entries: every access in the spare slot
+            if (e < ntri) {
+                i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while (i * (i + 1) / 2 > e) --i;
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                j = e - i * (i + 1) / 2;
+            }
+            gi[sI] = i;
+            gj[sI] = j;
+            ga[sI] = e < ntri ? (float)Ap[e] : 0.f;
+            if (e < ntri && j == 0) colb[0][i] = ga[sI];
+        }
+        bool ok = P.solver == 0;
+        for (int k = 0; ok && k < nd; ++k) {
+            __syncthreads();
+            const float* c = colb[k & 1];
+            float* cn = colb[(k + 1) & 1];
+            const float d = c[k];
+            if (!(d > 0.f) || !(d < 3.0e38f)) {
+                ok = false;                          // uniform: every thread read the same pivot
+                break;
+            }
+            const float r = __frcp_rn(d);
+#pragma unroll
+            for (int sI = 0; sI < kPer; ++sI) {
+                const int i = gi[sI], j = gj[sI];
+                const float ci = c[i], cj = c[j];
+                const float upd = fmaf(-ci * r, cj, ga[sI]);
+                const float rowk = j == k ? -r : cj * r;
+                const float a = i == k ? rowk : (j == k ? ci * r : upd);
                 ga[sI] = a;
-                if (j == k + 1) cn[i] = a;
-                if (i == k + 1) cn[j] = a;
+                cn[j == k + 1 ? i : (i == k + 1 ? j : kSpare)] = a;
             }
         }
-    }
-    if (ok32) {
+        if (tid == 0) s_ok32 = ok ? 1 : 0;
+        if (ok) {
 #pragma unroll
-        for (int sI = 0; sI < kPer; ++sI) {
-            const int i = gi[sI], j = gj[sI];
-            if (i >= 0) {
-                Gf[i * kGs + j] = -ga[sI];
-                Gf[j * kGs + i] = -ga[sI];
+            for (int sI = 0; sI < kPer; ++sI) {
+                const int i = gi[sI], j = gj[sI];
+                if (j < kSpare) {
+                    Gf[i * kGs + j] = -ga[sI];
+                    Gf[j * kGs + i] = -ga[sI];
+                }
             }
         }
     }
     __syncthreads();
+    const bool ok32 = s_ok32 != 0;
     if (ok32) {
         if (tid < nd) {
             x[tid] = 0.0;
@@ -623,13 +671,16 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
             }
             __syncthreads();
             if (tid == 0) {
-                // converged: the correction is below 1e-10 of x; or the
-                // corrections stopped shrinking (the FP64 residual's rounding
-                // floor, ~n cond(A) 1e-16) at <= 1e-6 of x; a stall above
-                // that is a failure (the FP32 inverse does not contract)
+                // converged: the correction is below 1e-10 of x, or the next
+                // one, extrapolated from the contraction of the last two
+                // (cm^2 / cm_prev), is; or the corrections stopped shrinking
+                // (the FP64 residual's rounding floor, ~n cond(A) 1e-16) at
+                // <= 1e-6 of x; a stall above that is a failure (the FP32
+                // inverse does not contract)
                 const double cm = fmaxf(fmaxf(redc[0], redc[1]), fmaxf(redc[2], redc[3]));
                 const double xm = fmaxf(fmaxf(redx[0], redx[1]), fmaxf(redx[2], redx[3]));
                 int conv = cm <= 1e-10 * xm ? 1 : 0;
+                if (!conv && it > 0 && cm < 0.5 * cm_prev && cm * cm <= 1e-10 * xm * cm_prev) conv = 1;
                 if (!conv && it > 0 && cm > 0.5 * cm_prev) {
                     if (cm <= 1e-6 * xm) conv = 1;
                     else s_fail = 1;
