@@ -256,6 +256,12 @@ def surface_jtj_algorithmic_bytes(N, n_adj):
     return 72 * N + 20 * n_adj
 
 
+def surface_vector_bytes(N):
+    """PCG vector traffic per iteration of the surface stage besides J^T J p:
+    p, x, A p, r, M^-1 read and x, r, z written (12 B per vertex each)."""
+    return 96 * N
+
+
 def one_ring_pairs(F):
     """Ordered one-ring pairs of a triangle mesh (twice its unique edges)."""
     import numpy as np
@@ -383,7 +389,12 @@ def run_ours(a):
         jtj_bytes = jtj_algorithmic_bytes(scene, n_active, E)
     # dominant kernel: the cluster-persistent PCG when it is used, else the
     # per-iteration J^T J p pair (the fused J^T J p of the surface stage)
-    if surface:
+    if surface and prof["pcg"][1]:
+        k_ms, k_n = prof["pcg"]
+        k_bytes = scene.n_pcg_surface * (jtj_bytes + surface_vector_bytes(scene.N)) + 72 * scene.N
+        k_name = ("surface_pcg_cluster_kernel (all PCG iterations of one GN step: fused direction update, "
+                  "one-ring J^T J p, vector updates, cluster reductions)")
+    elif surface:
         k_ms, k_n = prof["jtj"]
         k_bytes = jtj_bytes
         k_name = "surface_jtj_kernel (fused direction update + one-ring J^T J p + p.Ap)"
@@ -473,8 +484,8 @@ def run_ours(a):
                      "jtjp_algorithmic_bytes": jtj_bytes,
                      "avg_launch_us": 1e3 * k_ms / k_n if k_n else None,
                      "note": (f"the capture's working set ({jtj_bytes / 1e6:.2f} MB per J^T J p) stays in L2 across "
-                              "the PCG iterations; one CTA per 256 vertices, so the small capture fills few SMs and "
-                              "the kernel is latency-bound") if surface else
+                              "the PCG iterations; a few CTAs (one per 256-1024 vertices) and dependent one-ring "
+                              "gathers plus cluster reductions per iteration: latency-bound") if surface else
                              ("the capture's working set (~0.3 MB per J^T J p) stays on chip / in L2 across the "
                               "PCG iterations and the kernel is latency-bound (cluster barriers, FP64 reductions), "
                               "so the HBM fraction is low by construction") if prof["pcg"][1] else

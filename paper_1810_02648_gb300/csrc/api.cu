@@ -813,7 +813,7 @@ extern "C" lc_status lc_read_stats(lc_ctx* ctx, lc_solve_stats* stats) {
     if (ctx->last_surface) {
         if ((s = ctx->read_stats(stats, ctx->params.n_gn_surface, true))) return s;
         stats->n_kernels = ctx->surf_graph_kernels;
-        stats->pcg_cluster_size = 0;
+        stats->pcg_cluster_size = ctx->surf_cl > 0 && ctx->params.pcg_kernel == 0 ? ctx->surf_cl : 0;
         return LC_OK;
     }
     if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;

@@ -93,6 +93,8 @@ struct lc_ctx {
     bool surf_has_lin = false;     // the surface operands match the current V
     bool last_surface = false;     // the last solve was the surface stage (lc_read_stats)
     float4* surf_diag = nullptr;   // N: diag(J^T J) for lc_surface_linearize
+    int surf_cl = 0;               // cluster size of the surface cluster PCG (0: per-iteration kernels)
+    lc::SurfCluster surf_shape{0, 0};
     lc_status surface_setup(const float* V, const float* material, const std::vector<int4>& medges);
     void surface_release();
     void surface_weights();

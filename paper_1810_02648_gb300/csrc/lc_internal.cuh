@@ -400,6 +400,13 @@ void launch_surface_jtj(const CapDesc* dC, const CapDesc& hC, int it, const floa
 void launch_surface_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_surface_pcg_step(const CapDesc* dC, const CapDesc& hC, int it, cudaStream_t st);
 void launch_surface_update(const CapDesc* dC, const CapDesc& hC, int slot, cudaStream_t st);
+// all PCG iterations of one step in one cluster launch: cl CTAs of tpc
+// vertex tiles each (cl = 0: the capture is too large, per-iteration kernels)
+struct SurfCluster {
+    int cl, tpc;
+};
+SurfCluster plan_surface_cluster(int vert_tiles);
+cudaError_t launch_surface_pcg_cluster(const CapDesc* dC, SurfCluster shape, int n_pcg, cudaStream_t st);
 
 // cluster-persistent PCG (pcg_cluster.cu)
 struct PcgPlan {

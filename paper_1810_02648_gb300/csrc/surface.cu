@@ -21,8 +21,12 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "lc_context.h"
 #include "pose_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lc {
 
@@ -32,13 +36,84 @@ __device__ __forceinline__ float3 xyz(float4 a) { return make_float3(a.x, a.y, a
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3f(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// Loads of vectors another CTA of the same launch wrote (the cluster PCG):
+// through L2 (__ldcg); plain loads elsewhere.
+template <bool kL2>
+__device__ __forceinline__ float4 ldv(const float4* p) {
+    if (kL2) return __ldcg(p);
+    return *p;
+}
+
 // p of PCG iteration `it` at vertex j: iteration 0 reads the start direction
 // z; later iterations form p = z + beta p_prev on the fly (the direction
 // update is fused into the product), with one rounding order everywhere.
+template <bool kL2>
 __device__ __forceinline__ float3 direction(const CapDesc& C, int it, float beta, int j) {
-    if (it <= 0) return xyz(C.sp[0][j]);
-    const float4 z = C.sz[j], q = C.sp[(it - 1) & 1][j];
+    if (it <= 0) return xyz(ldv<kL2>(&C.sp[0][j]));
+    const float4 z = ldv<kL2>(&C.sz[j]), q = ldv<kL2>(&C.sp[(it - 1) & 1][j]);
     return make_float3(__fmaf_rn(beta, q.x, z.x), __fmaf_rn(beta, q.y, z.y), __fmaf_rn(beta, q.z, z.z));
+}
+
+// Block row i of J^T J applied to p (p_in, or with p_in null the PCG
+// direction of iteration it): returns p_i and (J^T J p)_i.  The one-ring in
+// rounds of U pairs: a round's index and operand loads are issued together
+// before any is used (a padding slot points at the vertex itself with a zero
+// operand and adds nothing).
+template <bool kL2>
+__device__ __forceinline__ void row_product(const CapDesc& C, int it, float beta, const float4* __restrict__ p_in,
+                                            int i, float3& pi, float3& q) {
+    const bool pcg = p_in == nullptr;
+    pi = pcg ? direction<kL2>(C, it, beta, i) : xyz(p_in[i]);
+    const float4 HA = C.HA[i], HB = C.HB[i];
+    const float wt = C.w_vel + C.w_acc;
+    q = make_float3(HA.x * pi.x + HA.y * pi.y + HA.z * pi.z + wt * pi.x,
+                    HA.y * pi.x + HA.w * pi.y + HB.x * pi.z + wt * pi.y,
+                    HA.z * pi.x + HB.x * pi.y + HB.y * pi.z + wt * pi.z);
+    constexpr int U = 4;
+    const int p0 = C.adj_off[i], p1 = C.adj_off[i + 1];
+    for (int pb = p0; pb < p1; pb += U) {
+        int jj[U];
+        float4 m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = pb + u < p1;
+            jj[u] = ok ? C.adj_dst[pb + u] : i;
+            m[u] = ok ? C.adj_m[pb + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float3 pj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) pj[u] = pcg ? direction<kL2>(C, it, beta, jj[u]) : xyz(p_in[jj[u]]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float3 dp = sub3(pi, pj[u]);
+            const float s = m[u].x * dp.x + m[u].y * dp.y + m[u].z * dp.z;
+            q.x += m[u].w * dp.x + s * m[u].x;
+            q.y += m[u].w * dp.y + s * m[u].y;
+            q.z += m[u].w * dp.z + s * m[u].z;
+        }
+    }
+}
+
+// PCG start at vertex i: x = 0, r = b, z = p = M^-1 b; returns r.z
+__device__ __forceinline__ float init_vertex(const CapDesc& C, int i) {
+    const float4 b = C.sb[i], m = C.sminv[i];
+    const float4 z = make_float4(m.x * b.x, m.y * b.y, m.z * b.z, 0.f);
+    C.sx[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    C.sr[i] = b;
+    C.sz[i] = z;
+    C.sp[0][i] = z;
+    return b.x * z.x + b.y * z.y + b.z * z.z;
+}
+
+// x += alpha p, r -= alpha A p, z = M^-1 r at vertex i; returns r.z
+__device__ __forceinline__ float step_vertex(const CapDesc& C, int it, float alpha, int i) {
+    const float4 p = C.sp[it & 1][i], x = C.sx[i], Ap = C.sAp[i], r0 = C.sr[i], m = C.sminv[i];
+    C.sx[i] = make_float4(x.x + alpha * p.x, x.y + alpha * p.y, x.z + alpha * p.z, 0.f);
+    const float4 r = make_float4(r0.x - alpha * Ap.x, r0.y - alpha * Ap.y, r0.z - alpha * Ap.z, 0.f);
+    const float4 z = make_float4(m.x * r.x, m.y * r.y, m.z * r.z, 0.f);
+    C.sr[i] = r;
+    C.sz[i] = z;
+    return r.x * z.x + r.y * z.y + r.z * z.z;
 }
 
 }  // namespace
@@ -164,38 +239,8 @@ __global__ void __launch_bounds__(kVertTile) surface_jtj_kernel(const CapDesc* _
     const int i = tile * kVertTile + threadIdx.x;
     float papf[1] = {0.f};
     if (i < C.N) {
-        const float3 pi = pcg ? direction(C, it, beta, i) : xyz(p_in[i]);
-        const float4 HA = C.HA[i], HB = C.HB[i];
-        const float wt = C.w_vel + C.w_acc;
-        float3 q = make_float3(HA.x * pi.x + HA.y * pi.y + HA.z * pi.z + wt * pi.x,
-                               HA.y * pi.x + HA.w * pi.y + HB.x * pi.z + wt * pi.y,
-                               HA.z * pi.x + HB.x * pi.y + HB.y * pi.z + wt * pi.z);
-        // the one-ring in rounds of U pairs: a round's index and operand
-        // loads are issued together before any is used (a padding slot points
-        // at the vertex itself with a zero operand and adds nothing)
-        constexpr int U = 4;
-        const int p0 = C.adj_off[i], p1 = C.adj_off[i + 1];
-        for (int pb = p0; pb < p1; pb += U) {
-            int jj[U];
-            float4 m[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = pb + u < p1;
-                jj[u] = ok ? C.adj_dst[pb + u] : i;
-                m[u] = ok ? C.adj_m[pb + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            float3 pj[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) pj[u] = pcg ? direction(C, it, beta, jj[u]) : xyz(p_in[jj[u]]);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float3 dp = sub3(pi, pj[u]);
-                const float s = m[u].x * dp.x + m[u].y * dp.y + m[u].z * dp.z;
-                q.x += m[u].w * dp.x + s * m[u].x;
-                q.y += m[u].w * dp.y + s * m[u].y;
-                q.z += m[u].w * dp.z + s * m[u].z;
-            }
-        }
+        float3 pi, q;
+        row_product<false>(C, it, beta, pcg ? nullptr : p_in, i, pi, q);
         if (pcg) {
             if (it > 0) C.sp[it & 1][i] = make_float4(pi.x, pi.y, pi.z, 0.f);
             C.sAp[i] = make_float4(q.x, q.y, q.z, 0.f);
@@ -226,15 +271,7 @@ __global__ void __launch_bounds__(kVertTile) surface_pcg_init_kernel(const CapDe
     const int tile = blockIdx.x;
     const int i = tile * kVertTile + threadIdx.x;
     float rzf[1] = {0.f};
-    if (i < C.N) {
-        const float4 b = C.sb[i], m = C.sminv[i];
-        const float4 z = make_float4(m.x * b.x, m.y * b.y, m.z * b.z, 0.f);
-        C.sx[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        C.sr[i] = b;
-        C.sz[i] = z;
-        C.sp[0][i] = z;
-        rzf[0] = b.x * z.x + b.y * z.y + b.z * z.z;
-    }
+    if (i < C.N) rzf[0] = init_vertex(C, i);
     double rz[1];
     block_sum_f<1, kVertTile / 32>(rzf, rz, sh);
     reduce_partials<1>(C, CNT_DOT2, tile, C.vert_tiles, rz, [&](const double (&tot)[1]) {
@@ -256,15 +293,7 @@ __global__ void __launch_bounds__(kVertTile) surface_pcg_step_kernel(const CapDe
     const int tile = blockIdx.x;
     const int i = tile * kVertTile + threadIdx.x;
     float rzf[1] = {0.f};
-    if (i < C.N) {
-        const float4 p = C.sp[it & 1][i], x = C.sx[i], Ap = C.sAp[i], r0 = C.sr[i], m = C.sminv[i];
-        C.sx[i] = make_float4(x.x + alpha * p.x, x.y + alpha * p.y, x.z + alpha * p.z, 0.f);
-        const float4 r = make_float4(r0.x - alpha * Ap.x, r0.y - alpha * Ap.y, r0.z - alpha * Ap.z, 0.f);
-        const float4 z = make_float4(m.x * r.x, m.y * r.y, m.z * r.z, 0.f);
-        C.sr[i] = r;
-        C.sz[i] = z;
-        rzf[0] = r.x * z.x + r.y * z.y + r.z * z.z;
-    }
+    if (i < C.N) rzf[0] = step_vertex(C, it, alpha, i);
     double rz[1];
     block_sum_f<1, kVertTile / 32>(rzf, rz, sh);
     reduce_partials<1>(C, CNT_DOT2, tile, C.vert_tiles, rz, [&](const double (&tot)[1]) {
@@ -278,6 +307,114 @@ __global__ void __launch_bounds__(kVertTile) surface_pcg_step_kernel(const CapDe
             sc->rz = tot[0];
         }
     });
+}
+
+// ---------------------------------------------------------------------------
+// Cluster-persistent PCG: all n_pcg iterations of one Gauss-Newton step in
+// one launch of a thread-block cluster (one CTA per SM).  A CTA holds tpc
+// consecutive vertex tiles of 256 threads (one vertex per thread), so the
+// whole capture is in flight at once.  Vectors stay in global memory (L2);
+// each dot product is reduced per tile exactly like the per-iteration
+// kernels (FP32 inside the tile, the tile's FP64 partial pushed through
+// distributed shared memory into every CTA, summed there in the same lane
+// order), so both paths give identical results; one cluster barrier per
+// reduction replaces a kernel boundary.
+// ---------------------------------------------------------------------------
+constexpr int kSurfClusterTiles = 64;   // vertex tiles a cluster PCG handles at most
+constexpr int kSurfTilesPerCta = 4;     // up to 1024 threads per CTA
+
+__device__ __forceinline__ double surf_cluster_reduce(cg::cluster_group& cluster, float v, int tile0, int cl,
+                                                      int ntiles, double* slots, float* s_warp, double* s_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // FP32 sum of each 256-thread tile in the order of block_sum_f: a fixed
+    // shuffle tree per warp, then the tile's 8 warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    constexpr int kW = kVertTile / 32;
+    if ((warp % kW) == 0) {
+        // the tile's first warp: lanes < cl push its partial into slot
+        // `tile` of every cluster CTA
+        const int g = warp / kW;
+        float t = 0.f;
+        for (int w = 0; w < kW; ++w) t += s_warp[g * kW + w];
+        const int tile = tile0 + g;
+        if (lane < cl && tile < ntiles) cluster.map_shared_rank(slots, lane)[tile] = (double)t;
+    }
+    cluster.sync();
+    if (warp == 0) {
+        // the order of sum_partials_warp: lane l adds tiles l, l + 32, ...,
+        // then a fixed shuffle tree
+        double d = 0.0;
+        for (int tl = lane; tl < ntiles; tl += 32) d += slots[tl];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) *s_tot = d;
+    }
+    __syncthreads();
+    return *s_tot;
+}
+
+__global__ void __launch_bounds__(kVertTile * kSurfTilesPerCta) surface_pcg_cluster_kernel(
+    const CapDesc* __restrict__ caps, int n_pcg) {
+    __shared__ double slots[2][kSurfClusterTiles];
+    __shared__ float s_warp[kSurfTilesPerCta * kVertTile / 32];
+    __shared__ double s_tot;
+    cg::cluster_group cluster = cg::this_cluster();
+    const CapDesc& C = caps[0];
+    if (C.sc->gn_stop) return;   // uniform over the cluster
+    const int rank = (int)cluster.block_rank(), cl = (int)cluster.num_blocks();
+    const int tpc = (int)blockDim.x / kVertTile;
+    const int ntiles = C.vert_tiles, N = C.N;
+    const int tile0 = rank * tpc;
+    const int i = tile0 * kVertTile + (int)threadIdx.x;   // this thread's vertex
+    const bool own = i < N;
+    int par = 0;
+    // start: x = 0, r = b, z = p = M^-1 b
+    double rz = surf_cluster_reduce(cluster, own ? init_vertex(C, i) : 0.f, tile0, cl, ntiles, slots[par], s_warp,
+                                    &s_tot);
+    par ^= 1;
+    int iters = 0, breakdown = 0;
+    bool stop = rz == 0.0;
+    float beta = 0.f;
+    for (int it = 0; it < n_pcg && !stop; ++it) {
+        // A p (the direction update fused in) and p.Ap
+        float v = 0.f;
+        if (own) {
+            float3 pi, q;
+            row_product<true>(C, it, beta, nullptr, i, pi, q);
+            if (it > 0) C.sp[it & 1][i] = make_float4(pi.x, pi.y, pi.z, 0.f);
+            C.sAp[i] = make_float4(q.x, q.y, q.z, 0.f);
+            v = pi.x * q.x + pi.y * q.y + pi.z * q.z;
+        }
+        const double pap = surf_cluster_reduce(cluster, v, tile0, cl, ntiles, slots[par], s_warp, &s_tot);
+        par ^= 1;
+        if (!(pap > 0.0)) {
+            breakdown = 1;
+            break;
+        }
+        const float alpha = __fdiv_rn((float)rz, (float)pap);
+        const double rzn = surf_cluster_reduce(cluster, own ? step_vertex(C, it, alpha, i) : 0.f, tile0, cl, ntiles,
+                                               slots[par], s_warp, &s_tot);
+        par ^= 1;
+        ++iters;
+        if (rzn == 0.0) {
+            stop = true;
+        } else {
+            beta = __fdiv_rn((float)rzn, (float)rz);
+            rz = rzn;
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        Scalars* sc = C.sc;
+        sc->iters = iters;
+        sc->breakdown = breakdown;
+        sc->stop = 1;
+        sc->rz = rz;
+    }
+    // no CTA may leave while another can still write into its partial slots
+    cluster.sync();
 }
 
 // V += delta, the new projections, ||delta||
@@ -337,6 +474,53 @@ void launch_surface_pcg_step(const CapDesc* dC, const CapDesc& hC, int it, cudaS
 void launch_surface_update(const CapDesc* dC, const CapDesc& hC, int slot, cudaStream_t st) {
     surface_update_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC, slot);
 }
+// Cluster shape for the cluster PCG of a capture with `tiles` vertex tiles:
+// tiles per CTA (1-4) and CTAs (<= 16, or <= 8 if the device does not
+// schedule 16); {0, 0} when the capture is too large.
+SurfCluster plan_surface_cluster(int tiles) {
+    if (tiles > kSurfClusterTiles) return {0, 0};
+    for (int clmax : {16, 8}) {
+        const int tpc = (tiles + clmax - 1) / clmax;
+        if (tpc > kSurfTilesPerCta) continue;
+        const int cl = (tiles + tpc - 1) / tpc;
+        if (cl > 8 && cudaFuncSetAttribute(surface_pcg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                           1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(tpc * kVertTile);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = cl;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, surface_pcg_cluster_kernel, &cfg) == cudaSuccess && n >= 1)
+            return {cl, tpc};
+        cudaGetLastError();
+    }
+    return {0, 0};
+}
+
+cudaError_t launch_surface_pcg_cluster(const CapDesc* dC, SurfCluster sc, int n_pcg, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sc.cl);
+    cfg.blockDim = dim3(sc.tpc * kVertTile);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = sc.cl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, surface_pcg_cluster_kernel, dC, n_pcg);
+}
+
 static void launch_surface_shift(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     surface_shift_kernel<<<hC.vert_tiles, kVertTile, 0, st>>>(dC);
 }
@@ -406,6 +590,8 @@ lc_status lc_ctx::surface_setup(const float* V, const float* mat, const std::vec
     surf_hist = 0;
     surf_has_disp = false;
     surf_has_lin = false;
+    surf_shape = plan_surface_cluster(C.vert_tiles);
+    surf_cl = surf_shape.cl;
     apply_params();
     return LC_OK;
 }
@@ -447,13 +633,18 @@ void lc_ctx::enqueue_surface() {
         launch_linearize(dC, C, true, st);
         mark(LC_PH_RHS);
         launch_surface_rhs(dC, C, gn, false, nullptr, st);
-        mark(LC_PH_PCG_INIT);
-        launch_surface_pcg_init(dC, C, st);
-        for (int it = 0; it < n_pcg; ++it) {
-            mark(LC_PH_JTJ);
-            launch_surface_jtj(dC, C, it, nullptr, nullptr, st);
-            mark(LC_PH_PCG_VEC);
-            launch_surface_pcg_step(dC, C, it, st);
+        if (surf_cl > 0 && params.pcg_kernel == 0) {
+            mark(LC_PH_PCG);
+            launch_surface_pcg_cluster(dC, surf_shape, n_pcg, st);
+        } else {
+            mark(LC_PH_PCG_INIT);
+            launch_surface_pcg_init(dC, C, st);
+            for (int it = 0; it < n_pcg; ++it) {
+                mark(LC_PH_JTJ);
+                launch_surface_jtj(dC, C, it, nullptr, nullptr, st);
+                mark(LC_PH_PCG_VEC);
+                launch_surface_pcg_step(dC, C, it, st);
+            }
         }
         mark(LC_PH_UPDATE);
         launch_surface_update(dC, C, gn, st);
@@ -599,7 +790,7 @@ extern "C" lc_status lc_solve_surface(lc_ctx* ctx, lc_solve_stats* stats) {
     if (stats) {
         if ((s = ctx->read_stats(stats, ctx->params.n_gn_surface, true))) return s;
         stats->n_kernels = ctx->surf_graph_kernels;
-        stats->pcg_cluster_size = 0;
+        stats->pcg_cluster_size = ctx->surf_cl > 0 && ctx->params.pcg_kernel == 0 ? ctx->surf_cl : 0;
     }
     return LC_OK;
 }
@@ -679,10 +870,14 @@ extern "C" lc_status lc_surface_solve_linear(lc_ctx* ctx, float* delta, int* ite
     const CapDesc& C = ctx->hC;
     cudaStream_t st = ctx->stream;
     cudaMemsetAsync((char*)C.sc + offsetof(Scalars, gn_stop), 0, 2 * sizeof(int), st);
-    launch_surface_pcg_init(ctx->dC, C, st);
-    for (int it = 0; it < ctx->params.n_pcg_surface; ++it) {
-        launch_surface_jtj(ctx->dC, C, it, nullptr, nullptr, st);
-        launch_surface_pcg_step(ctx->dC, C, it, st);
+    if (ctx->surf_cl > 0 && ctx->params.pcg_kernel == 0) {
+        launch_surface_pcg_cluster(ctx->dC, ctx->surf_shape, ctx->params.n_pcg_surface, st);
+    } else {
+        launch_surface_pcg_init(ctx->dC, C, st);
+        for (int it = 0; it < ctx->params.n_pcg_surface; ++it) {
+            launch_surface_jtj(ctx->dC, C, it, nullptr, nullptr, st);
+            launch_surface_pcg_step(ctx->dC, C, it, st);
+        }
     }
     lc_status s;
     if ((s = ctx->cuda(cudaStreamSynchronize(st), "lc_surface_solve_linear"))) return s;

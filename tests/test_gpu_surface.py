@@ -180,9 +180,9 @@ def test_surface_linearization_zero_length_edge(tiny):
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------
-def _e2e(scene, kind, tag, history=False, seed=3):
+def _e2e(scene, kind, tag, history=False, seed=3, pcg_kernel=0):
     V0, VS = _start(scene, kind, seed)
-    ctx = _ctx(scene)
+    ctx = _ctx(scene, pcg_kernel=pcg_kernel)
     if VS is not None:
         ctx.set_rest_geometry(VS)
     prev1 = prev2 = None
@@ -233,7 +233,30 @@ def test_surface_end_to_end_tiny(tiny):
 
 @pytest.mark.parametrize("history", [False, True])
 def test_surface_end_to_end_body(body, history):
-    _e2e(body, "posed", f"body_h{int(history)}", history=history)
+    st = _e2e(body, "posed", f"body_h{int(history)}", history=history)
+    assert 1 <= st["pcg_cluster_size"] <= 16
+
+
+@pytest.mark.parametrize("case", ["tiny", "body"])
+def test_surface_pcg_paths_bit_identical(case, tiny, body):
+    """The cluster-persistent PCG (default for captures of <= 64 vertex
+    tiles) reduces every dot product per tile in the order of the
+    per-iteration kernels (pcg_kernel 1): both solves give identical bits."""
+    scene, kind = _cases(tiny, body)[case]
+    V0, VS = _start(scene, kind, 5)
+    out = []
+    for k in (0, 1):
+        ctx = _ctx(scene, pcg_kernel=k)
+        if VS is not None:
+            ctx.set_rest_geometry(VS)
+        ctx.set_surface(V0)
+        st = ctx.solve_surface()
+        out.append((st, ctx.read_surface()))
+        ctx.close()
+    (s0, v0), (s1, v1) = out
+    assert 1 <= s0["pcg_cluster_size"] <= 16 and s1["pcg_cluster_size"] == 0
+    assert np.array_equal(v0, v1)
+    assert s0["e_total"] == s1["e_total"] and s0["e_gn"] == s1["e_gn"] and s0["pcg_iters"] == s1["pcg_iters"]
 
 
 def test_surface_end_to_end_ragged():
