@@ -6,6 +6,8 @@ Energy:
     E_pose = lambda_2D sum_j ||pi(o_j) - P2D_j||^2            (2D joints, pixels)
            + lambda_3D sum_j ||o_j - P3D_j||^2                (3D joints, metres)
            + lambda_sil/|B| sum_{i in B} I_DT(pi(V^S_i))^2     (silhouette, b_i sign)
+           + lambda_temporal sum_j w_j ||o_j - o_j^{t-1}||^2   (temporal stabilisation)
+           + lambda_anatomic sum_{Euler DOF} Psi(theta)        (joint angle limits)
            + lambda_prior sum_{Euler DOF} (theta - theta_init)^2
 over the pose vector [root axis-angle (3), root translation (3), Euler XYZ
 angles of every DOF joint (3 each)].
@@ -31,6 +33,15 @@ Readings:
 * The contour set B comes from the skinned mesh at the frame's initial pose
   (once per frame, Sec. 3.3); b_i is re-evaluated on the current skinned
   surface at every linearisation.  Both through the exact visibility module.
+* E_temporal (Sec. 3.3) compares the joints with the previous frame's; it
+  is off until a previous frame has been recorded.  E_anatomic's barrier
+  Psi(x) = (x - max)^2 above the limit, (min - x)^2 below, 0 inside, enters
+  Gauss-Newton as a residual sqrt(lambda)(theta - bound) on the DOFs outside
+  their limits at the linearisation point (no limits: off).
+* Frame start (Sec. 3.3): an explicit Euler step in angle space from the
+  last two frames, theta = 2 theta^{t-1} - theta^{t-2} for the Euler angles
+  and the root translation; the root rotation takes the same
+  constant-velocity step on SO(3), R = R^{t-1} (R^{t-2})^T R^{t-1}.
 * The normal equations are solved by a Cholesky factorisation (FP64).
 """
 from __future__ import annotations
@@ -190,6 +201,12 @@ class PoseProblem:
     lam_sil: float = 200.0
     lam_prior: float = 1e4
     pose_init: Optional[np.ndarray] = None
+    lam_temporal: float = 1.5
+    temporal_w: Optional[np.ndarray] = None    # (J,) per-joint weights, default 1
+    prev_joints: Optional[np.ndarray] = None   # (J,3) joints of the previous frame
+    lam_anatomic: float = 1e6
+    theta_min: Optional[np.ndarray] = None     # (n_dof,) limits, -inf / +inf where none
+    theta_max: Optional[np.ndarray] = None
     inB: Optional[np.ndarray] = None
     bsign: Optional[np.ndarray] = None
 
@@ -266,6 +283,24 @@ def residuals_and_jacobian(pb: PoseProblem, pose: np.ndarray):
                 Jv += sk.skin_w[sel, sl, None, None] * point_jacobian(sk, P[sel, sl], bones, t, o, U)
             Jr = np.einsum("mk,mkd->md", g, np.einsum("mkc,mcd->mkd", DD[sel], Jv))
             rows.append((ss * pb.bsign[sel])[:, None] * Jr)
+    if pb.prev_joints is not None and pb.lam_temporal > 0:
+        w = np.ones(Jn) if pb.temporal_w is None else np.asarray(pb.temporal_w, dtype=np.float64)
+        st = np.sqrt(pb.lam_temporal * w)
+        Fs.append((st[:, None] * (o - np.asarray(pb.prev_joints, dtype=np.float64))).ravel())
+        rows.append((st[:, None, None] * Jo).reshape(-1, sk.n_dof))
+    if pb.theta_min is not None and pb.lam_anatomic > 0:
+        th = np.asarray(pose, dtype=np.float64)
+        lo = np.asarray(pb.theta_min, dtype=np.float64)
+        hi = np.asarray(pb.theta_max, dtype=np.float64)
+        sa = np.sqrt(pb.lam_anatomic)
+        for c in range(6, sk.n_dof):
+            bound = hi[c] if th[c] > hi[c] else (lo[c] if th[c] < lo[c] else None)
+            if bound is None:
+                continue
+            Fs.append(np.array([sa * (th[c] - bound)]))
+            r = np.zeros(sk.n_dof)
+            r[c] = sa
+            rows.append(r[None])
     if pb.lam_prior > 0:
         sp = np.sqrt(pb.lam_prior)
         base = pb.pose_init if pb.pose_init is not None else np.zeros(sk.n_dof)
@@ -338,6 +373,20 @@ def gauss_newton(pb: PoseProblem, pose0, n_gn: int):
         hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta))))
         pose = apply_update(pb.sk, pose, delta)
     return pose, hist
+
+
+def extrapolate(pose1: np.ndarray, pose2: Optional[np.ndarray] = None) -> np.ndarray:
+    """Frame start from the last two poses (pose1 = t-1, pose2 = t-2): the
+    explicit Euler step of the reading above; pose1 itself without pose2."""
+    p1 = np.asarray(pose1, dtype=np.float64)
+    if pose2 is None:
+        return p1.copy()
+    p2 = np.asarray(pose2, dtype=np.float64)
+    out = 2.0 * p1 - p2
+    R1 = nr.so3_exp(p1[:3])[0]
+    R2 = nr.so3_exp(p2[:3])[0]
+    out[:3] = nr.so3_log(R1 @ R2.T @ R1)[0]
+    return out
 
 
 def problem_from_scene(scene, lam_prior=1e4) -> PoseProblem:

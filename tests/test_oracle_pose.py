@@ -7,6 +7,10 @@
   (bilinear sampling and central differences exact), b_i signs folded in.
 * Cholesky solve vs numpy.linalg.solve; a non-positive pivot raises.
 * Noise-free detections generated at a known pose are recovered.
+* E_temporal and E_anatomic: their Jacobian rows by finite differences; the
+  barrier's energy and Gauss-Newton step against closed forms; E_temporal
+  alone pulls the joints onto a reachable previous frame's joints.
+* The frame-start extrapolation is exact for constant-velocity motion.
 """
 import copy
 
@@ -133,3 +137,108 @@ def test_pose_stage_improves_joints(body):
     e_fin = np.linalg.norm(out["joints"] - body.meta["joints_gt"], axis=1).mean()
     assert out["e1"] < out["e0"]
     assert e_fin < 1.5 * e_init
+
+
+def _terms_problem(body, pose):
+    """A problem with E_temporal and E_anatomic switched on around `pose`:
+    previous joints a few cm away, limits that leave some DOFs outside."""
+    pb = op.problem_from_scene(body)
+    rng = np.random.default_rng(11)
+    R, t, ang = op.split_pose(pb.sk, pose)
+    _, o = op.forward_kinematics(pb.sk, R, t, ang)
+    pb.prev_joints = o + rng.normal(scale=0.02, size=o.shape)
+    pb.temporal_w = rng.uniform(1.0, 2.5, size=len(o))
+    lo = np.full(pb.sk.n_dof, -np.inf)
+    hi = np.full(pb.sk.n_dof, np.inf)
+    lo[6:] = pose[6:] - rng.uniform(-0.05, 0.3, size=pb.sk.n_dof - 6)
+    hi[6:] = pose[6:] + rng.uniform(-0.05, 0.3, size=pb.sk.n_dof - 6)
+    lo[6:], hi[6:] = np.minimum(lo[6:], hi[6:] - 0.01), np.maximum(hi[6:], lo[6:] + 0.01)
+    pb.theta_min, pb.theta_max = lo, hi
+    return pb
+
+
+def test_temporal_and_anatomic_jacobian_fd(body):
+    pose = np.asarray(body.pose_init, dtype=np.float64).copy()
+    pb = _affine_dt(_terms_problem(body, pose))
+    dec = op.problem_from_scene(body)
+    op.frame_decisions(dec, pose)
+    pb.inB, pb.bsign = dec.inB, dec.bsign
+    n_active = int(((pose[6:] > pb.theta_max[6:]) | (pose[6:] < pb.theta_min[6:])).sum())
+    assert n_active >= 3
+    # stay clear of the limits by more than the FD step
+    margin = np.minimum(np.abs(pose[6:] - pb.theta_max[6:]), np.abs(pose[6:] - pb.theta_min[6:]))
+    assert margin.min() > 1e-4
+    F, J = op.residuals_and_jacobian(pb, pose)
+    Jn = len(pb.sk.parents)
+    r_t = len(F) - (pb.sk.n_dof - 6) - n_active - 3 * Jn     # first temporal row
+    h = 1e-6
+    for d in range(J.shape[1]):
+        e = np.zeros(J.shape[1])
+        e[d] = h
+        Fp, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, e))
+        Fm, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, -e))
+        fd = (Fp - Fm) / (2 * h)
+        rows = slice(r_t, len(F))
+        assert np.abs(fd[rows] - J[rows, d]).max() <= 1e-6 * max(1.0, np.abs(J[rows]).max()), d
+
+
+def test_anatomic_barrier_closed_form(body):
+    pose = np.asarray(body.pose_init, dtype=np.float64).copy()
+    pb = _terms_problem(body, pose)
+    pb.prev_joints = None
+    pb.lam_2d = pb.lam_3d = pb.lam_sil = 0.0
+    lam_a, lam_p = pb.lam_anatomic, pb.lam_prior
+    th, lo, hi = pose[6:], pb.theta_min[6:], pb.theta_max[6:]
+    psi = np.where(th > hi, (th - hi) ** 2, np.where(th < lo, (lo - th) ** 2, 0.0))
+    assert op.energy(pb, pose) == pytest.approx(lam_a * psi.sum(), rel=1e-12)
+    # prior + barrier only: the Euler block of the normal equations is
+    # diagonal, and its Gauss-Newton step from the prior's centre lands on the
+    # quadratic minimiser (lam_p th0 + lam_a bound) / (lam_p + lam_a)
+    F, J = op.residuals_and_jacobian(pb, pose)
+    A = J.T @ J
+    g = -(J.T @ F)
+    Ae = A[6:, 6:]
+    assert np.abs(Ae - np.diag(np.diag(Ae))).max() == 0.0
+    active = (th > hi) | (th < lo)
+    assert np.allclose(np.diag(Ae), lam_p + lam_a * active, rtol=1e-14)
+    bound = np.where(th > hi, hi, np.where(th < lo, lo, th))
+    expect = np.where(active, (lam_p * th + lam_a * bound) / (lam_p + lam_a), th)
+    assert np.abs(th + g[6:] / np.diag(Ae) - expect).max() < 1e-12
+    # inside the limits the term is zero
+    pb.theta_min[6:] = th - 1.0
+    pb.theta_max[6:] = th + 1.0
+    assert op.energy(pb, pose) == 0.0
+
+
+def test_temporal_term_recovers_previous_joints(body):
+    """Only E_temporal (with a weak prior): Gauss-Newton moves the joints onto
+    the previous frame's joints when those come from a reachable pose."""
+    pb = op.problem_from_scene(body, lam_prior=1e-6)
+    pb.lam_2d = pb.lam_3d = pb.lam_sil = 0.0
+    pb.lam_temporal = 1.0e6
+    gt = body.meta["pose_gt"]
+    R, t, ang = op.split_pose(pb.sk, gt)
+    _, o = op.forward_kinematics(pb.sk, R, t, ang)
+    pb.prev_joints = o
+    pose, hist = op.gauss_newton(pb, np.asarray(body.pose_init, dtype=np.float64), 25)
+    R, t, ang = op.split_pose(pb.sk, pose)
+    _, o2 = op.forward_kinematics(pb.sk, R, t, ang)
+    assert np.abs(o2 - o).max() < 1e-6
+
+
+def test_extrapolation_is_exact_for_constant_velocity():
+    rng = np.random.default_rng(12)
+    n = 57
+    p0 = rng.normal(scale=0.3, size=n)
+    v = rng.normal(scale=0.05, size=n)
+    w = rng.normal(scale=0.1, size=3)
+    R0 = nr.so3_exp(p0[None, :3])[0]
+    poses = []
+    for k in range(3):
+        p = p0 + k * v
+        p[:3] = nr.so3_log(nr.so3_exp(k * w[None])[0] @ R0)[0]
+        poses.append(p)
+    ext = op.extrapolate(poses[1], poses[0])
+    assert np.abs(ext[3:] - poses[2][3:]).max() < 1e-12
+    assert np.abs(nr.so3_exp(ext[None, :3])[0] - nr.so3_exp(poses[2][None, :3])[0]).max() < 1e-12
+    assert np.array_equal(op.extrapolate(poses[1]), poses[1])
