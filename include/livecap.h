@@ -96,6 +96,10 @@ typedef struct {
                              (FP32 inverse by a symmetric sweep, FP64 residuals,
                              iterative refinement to 1e-10; the FP64 L D L^T when
                              that does not converge); 1: always the FP64 L D L^T */
+    float lambda_temporal;  /* pose stage E_temporal (Sec. 3.3, Sec. 5: 1.5); active
+                               once lc_pose_advance has recorded a frame */
+    float lambda_anatomic;  /* pose stage E_anatomic (Sec. 5: 1e6); active for the
+                               limits of lc_set_pose_priors */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -282,6 +286,32 @@ lc_status lc_reset_pose(lc_ctx *ctx);
  * call synchronises; e_gn / step_norm hold the history, e_total the final
  * energy, n_boundary |B|). */
 lc_status lc_solve_pose(lc_ctx *ctx, lc_solve_stats *stats);
+
+/* Pose-stage regularisers and frame bookkeeping (Sec. 3.3).
+ *   E_temporal = lambda_temporal sum_j w_j ||o_j - o_j^{t-1}||^2 on the joint
+ *     positions, against the joints recorded by lc_pose_advance (off until a
+ *     frame is recorded); 3 residual rows per joint, like the 3D joints.
+ *   E_anatomic = lambda_anatomic sum_c Psi(theta_c), Psi(x) = (x - max)^2
+ *     above the limit, (min - x)^2 below, 0 inside, on the Euler angles; in
+ *     Gauss-Newton a residual sqrt(lambda)(theta - bound) on the angles
+ *     outside their limits at each linearisation.
+ * lc_set_pose_priors: per-joint weights w (J floats, NULL = 1 each) and the
+ *   limits theta_min / theta_max (n_dof floats each in the layout of the pose
+ *   vector, the 6 root entries ignored; both NULL = no limits).
+ *   Synchronises.
+ * lc_pose_advance: end of a frame: the current joints become the previous
+ *   frame's, and the current pose enters a two-frame history.  Enqueued.
+ * lc_pose_extrapolate: start of a frame: the pose (and the prior's centre at
+ *   the next solve) becomes the explicit Euler step from the last two
+ *   recorded poses, theta = 2 theta^{t-1} - theta^{t-2} for the Euler angles
+ *   and the root translation, R = R^{t-1} (R^{t-2})^T R^{t-1} for the root
+ *   rotation; with one recorded pose, that pose.  LC_ERR_STATE without a
+ *   recorded pose.  Enqueued.
+ * lc_pose_clear_history: forgets the recorded frames. */
+lc_status lc_set_pose_priors(lc_ctx *ctx, const float *temporal_w, const float *theta_min, const float *theta_max);
+lc_status lc_pose_advance(lc_ctx *ctx);
+lc_status lc_pose_extrapolate(lc_ctx *ctx);
+lc_status lc_pose_clear_history(lc_ctx *ctx);
 /* Inspection: at the current pose, recompute B and b_i and export the pose
  * normal equations: V_skinned N x 3 (FP32 skinned template), A n_dof x n_dof
  * (J^T J + prior), g n_dof (-J^T F - prior gradient), energy 1.  Null

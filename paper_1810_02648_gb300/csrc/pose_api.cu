@@ -72,7 +72,8 @@ void lc_ctx::pose_release() {
                     (void*)pose->h.level, (void*)pose->h.pairs, pose->h.fk, pose->h.part,
                     pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.blist,
                     pose->h.bcount, pose->h.hist, pose->h.info, pose->h.expA, pose->h.status, pose->d,
-                    pose->pose_set};
+                    pose->pose_set, (void*)pose->h.temporal_w, (void*)pose->h.th_lo, (void*)pose->h.th_hi,
+                    pose->h.prev_joints, pose->h.pose_hist};
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
@@ -138,6 +139,8 @@ static void apply_pose_params(lc_ctx* ctx) {
     P.lam_3d = ctx->params.lambda_3d;
     P.lam_sil = ctx->params.lambda_sil;
     P.lam_prior = ctx->params.lambda_prior;
+    P.lam_temporal = ctx->params.lambda_temporal;
+    P.lam_anat = ctx->params.lambda_anatomic;
     P.solver = ctx->params.pose_solver;
 }
 
@@ -214,6 +217,13 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     P.info = (int*)ctx->alloc(sizeof(int) * (LC_MAX_GN + 1));
     P.expA = (double*)ctx->alloc(sizeof(double) * nd * (nd + 1));
     P.status = (int*)ctx->alloc(sizeof(int));
+    P.temporal_w = (const float*)ctx->alloc(sizeof(float) * J);
+    P.th_lo = (const float*)ctx->alloc(sizeof(float) * kMaxDof);
+    P.th_hi = (const float*)ctx->alloc(sizeof(float) * kMaxDof);
+    P.prev_joints = (float4*)ctx->alloc(sizeof(float4) * J);
+    P.pose_hist = (float*)ctx->alloc(sizeof(float) * 2 * (kMaxDof + 9));
+    P.has_prev = 0;
+    P.n_hist = 0;
     S.d = (PoseDesc*)ctx->alloc(sizeof(PoseDesc));
     S.pose_set = (float*)ctx->alloc(sizeof(float) * (kMaxDof + 9));
     if (!ctx->err.empty()) return LC_ERR_OOM;
@@ -230,6 +240,7 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     p0[4] = rest[1];
     p0[5] = rest[2];
     const float I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const std::vector<float> ones(J, 1.f), lo(kMaxDof, -INFINITY), hi(kMaxDof, INFINITY);
     cudaStream_t st = ctx->stream;
     struct Up {
         const void* dst;
@@ -242,7 +253,8 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
                {P.skin_idx, i4.data(), sizeof(int4) * N},    {P.skin_w, w4.data(), sizeof(float4) * N},
                {P.pose, p0.data(), sizeof(float) * kMaxDof}, {P.pose_start, p0.data(), sizeof(float) * kMaxDof},
                {P.Rroot, I3, sizeof(I3)},                    {S.pose_set, p0.data(), sizeof(float) * kMaxDof},
-               {S.pose_set + kMaxDof, I3, sizeof(I3)}};
+               {S.pose_set + kMaxDof, I3, sizeof(I3)},      {P.temporal_w, ones.data(), sizeof(float) * J},
+               {P.th_lo, lo.data(), sizeof(float) * kMaxDof}, {P.th_hi, hi.data(), sizeof(float) * kMaxDof}};
     for (auto& u : ups)
         if ((s = ctx->cuda(cudaMemcpyAsync((void*)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st), "skeleton upload")))
             return s;
@@ -278,6 +290,75 @@ extern "C" lc_status lc_set_pose(lc_ctx* ctx, const float* pose) {
                        "pose upload")))
         return s;
     return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+extern "C" lc_status lc_set_pose_priors(lc_ctx* ctx, const float* temporal_w, const float* theta_min,
+                                        const float* theta_max) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_set_pose_priors: no skeleton");
+    if ((theta_min == nullptr) != (theta_max == nullptr))
+        return ctx->fail(LC_ERR_ARG, "lc_set_pose_priors: give both limits or neither");
+    cudaSetDevice(ctx->device);
+    PoseDesc& P = ctx->pose->h;
+    const int J = P.J, nd = P.n_dof;
+    lc_status s;
+    std::vector<float> w(J, 1.f), lo(kMaxDof, -INFINITY), hi(kMaxDof, INFINITY);
+    if (temporal_w && (s = ctx->fetch(w.data(), temporal_w, sizeof(float) * J))) return s;
+    for (int j = 0; j < J; ++j)
+        if (!(w[j] >= 0.f) || !std::isfinite(w[j])) return ctx->fail(LC_ERR_ARG, "lc_set_pose_priors: bad weight");
+    if (theta_min) {
+        if ((s = ctx->fetch(lo.data(), theta_min, sizeof(float) * nd)) ||
+            (s = ctx->fetch(hi.data(), theta_max, sizeof(float) * nd)))
+            return s;
+        for (int c = 0; c < nd; ++c) {
+            if (c < 6) {
+                lo[c] = -INFINITY;   // the root carries no limits
+                hi[c] = INFINITY;
+            } else if (!(lo[c] <= hi[c])) {
+                return ctx->fail(LC_ERR_ARG, "lc_set_pose_priors: theta_min > theta_max");
+            }
+        }
+    }
+    if ((s = ctx->cuda(cudaMemcpyAsync((void*)P.temporal_w, w.data(), sizeof(float) * J, cudaMemcpyHostToDevice,
+                                       ctx->stream), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)P.th_lo, lo.data(), sizeof(float) * kMaxDof, cudaMemcpyHostToDevice,
+                                       ctx->stream), "upload")) ||
+        (s = ctx->cuda(cudaMemcpyAsync((void*)P.th_hi, hi.data(), sizeof(float) * kMaxDof, cudaMemcpyHostToDevice,
+                                       ctx->stream), "upload")))
+        return s;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+extern "C" lc_status lc_pose_advance(lc_ctx* ctx) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_pose_advance: no skeleton");
+    cudaSetDevice(ctx->device);
+    PoseState& S = *ctx->pose;
+    launch_pose_advance(S.d, ctx->stream);
+    lc_status s = ctx->cuda(cudaGetLastError(), "lc_pose_advance");
+    if (s) return s;
+    if (S.h.has_prev && S.h.n_hist >= 2) return LC_OK;   // the descriptor is unchanged
+    S.h.has_prev = 1;
+    S.h.n_hist = std::min(S.h.n_hist + 1, 2);
+    return pose_sync(ctx);
+}
+
+extern "C" lc_status lc_pose_extrapolate(lc_ctx* ctx) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_pose_extrapolate: no skeleton");
+    if (ctx->pose->h.n_hist == 0) return ctx->fail(LC_ERR_STATE, "lc_pose_extrapolate: no recorded pose");
+    cudaSetDevice(ctx->device);
+    launch_pose_extrapolate(ctx->pose->d, ctx->stream);
+    return ctx->cuda(cudaGetLastError(), "lc_pose_extrapolate");
+}
+
+extern "C" lc_status lc_pose_clear_history(lc_ctx* ctx) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_pose_clear_history: no skeleton");
+    cudaSetDevice(ctx->device);
+    ctx->pose->h.has_prev = 0;
+    ctx->pose->h.n_hist = 0;
+    return pose_sync(ctx);
 }
 
 extern "C" lc_status lc_reset_pose(lc_ctx* ctx) {

@@ -21,7 +21,10 @@ struct PoseDesc {
     int J, n_dof, n_levels;
     int has_j2d, has_j3d;
     float lam_2d, lam_3d, lam_sil, lam_prior;
+    float lam_temporal, lam_anat;
     int solver;                       // 0: mixed-precision refinement, 1: FP64 L D L^T
+    int has_prev;                     // previous-frame joints recorded (E_temporal on)
+    int n_hist;                       // poses recorded for the frame-start extrapolation (0..2)
     const int* parents;               // J
     const int* level;                 // J: depth in the tree (root 0)
     const unsigned short* pairs;      // (n_dof + 1)(n_dof + 2) / 2: a << 8 | b, column pairs a <= b of [J | F]
@@ -33,6 +36,11 @@ struct PoseDesc {
     const float4* skin_w;             // N
     const float2* j2d;                // J
     const float4* j3d;                // J
+    const float* temporal_w;          // J: per-joint weights of E_temporal
+    const float* th_lo;               // n_dof: joint angle limits of E_anatomic (+-inf where none)
+    const float* th_hi;
+    float4* prev_joints;              // J: joints of the previous frame
+    float* pose_hist;                 // 2 (kMaxDof + 9): poses t-1, t-2, each followed by its root rotation
     float* pose;                      // n_dof ([0:3] unused on the device)
     float* pose_start;                // n_dof: the frame's start pose (angle prior)
     float* Rroot;                     // 9
@@ -53,6 +61,11 @@ void launch_pose_blist(const CapDesc* dC, const PoseDesc* dP, cudaStream_t st);
 void launch_pose_fk(const PoseDesc* dP, cudaStream_t st);
 // re-skins the mesh into C.vw / C.uv and re-evaluates b_i of the contour set
 void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, cudaStream_t st);
+// the current joints -> prev_joints, the pose history shifted by one (after
+// a kinematics pass of the current pose)
+void launch_pose_advance(const PoseDesc* dP, cudaStream_t st);
+// the pose <- the explicit Euler step from the pose history (n_hist >= 1)
+void launch_pose_extrapolate(const PoseDesc* dP, cudaStream_t st);
 // displacement warping of the surface stage (dP null: no skeleton, Q_i = I);
 // mode 0 records sD from sV, mode 1 sets sV from sD
 void launch_surface_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int mode, cudaStream_t st);

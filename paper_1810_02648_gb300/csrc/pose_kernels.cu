@@ -288,13 +288,14 @@ __global__ void __launch_bounds__(64) pose_fk_kernel(const PoseDesc* __restrict_
 
 // ---------------------------------------------------------------------------
 // residual rows and their FP32 pair sums.  Items: t < J the 2 rows of 2D
-// joint t, t < 2J the 3 rows of 3D joint t - J, then one row per contour
+// joint t, t < 2J the 3 rows of 3D joint t - J, t < 3J the 3 temporal rows of
+// joint t - 2J (zero without a previous frame), then one row per contour
 // vertex; CTA c takes items [c kSysItems, (c + 1) kSysItems), builds their
 // rows [J | F] in shared memory (stride na | 1, odd: conflict-free) and
 // writes sum_rows a_r b_r for every column pair a <= b of [J | F].
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pose_row_of(int t, int J) {
-    return t < J ? 2 * t : (t < 2 * J ? 2 * J + 3 * (t - J) : 5 * J + (t - 2 * J));
+    return t < J ? 2 * t : (t < 3 * J ? 2 * J + 3 * (t - J) : 8 * J + (t - 3 * J));
 }
 
 __global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc* __restrict__ caps,
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc*
     const PoseDesc& P = *pd;
     const int J = P.J, nd = P.n_dof, na = nd + 1, stride = na | 1;
     const int nB = *P.bcount;
-    const int nitems = 2 * J + nB;
+    const int nitems = 3 * J + nB;
     const int t0 = blockIdx.x * kSysItems;
     if (t0 >= nitems) return;                       // uniform over the CTA
     const int t1 = min(nitems, t0 + kSysItems);
@@ -343,9 +344,23 @@ __global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc*
                 if (s3 > 0.f) add_point_row(P, fk, fk.o[j], j, coef, 1.f, row);
                 row[nd] = s3 * (fk.o[j][k] - tgt[k]);
             }
+        } else if (t < 3 * J) {
+            // temporal stabilisation rows: sqrt(l_temporal w_j) (o_j - o_j^{t-1})
+            const int j = t - 2 * J;
+            if (P.has_prev && P.lam_temporal > 0.f) {
+                const float sT = sqrtf(P.lam_temporal * P.temporal_w[j]);
+                const float4 q = P.prev_joints[j];
+                const float prev[3] = {q.x, q.y, q.z};
+                for (int k = 0; k < 3; ++k) {
+                    float* row = row0 + k * stride;
+                    const float coef[3] = {k == 0 ? sT : 0.f, k == 1 ? sT : 0.f, k == 2 ? sT : 0.f};
+                    add_point_row(P, fk, fk.o[j], j, coef, 1.f, row);
+                    row[nd] = sT * (fk.o[j][k] - prev[k]);
+                }
+            }
         } else {
             // silhouette row of a contour vertex
-            const int i = P.blist[t - 2 * J];
+            const int i = P.blist[t - 3 * J];
             const float4 v = P.tpl[i];
             const int4 bi = P.skin_idx[i];
             const float4 bw = P.skin_w[i];
@@ -487,7 +502,7 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
     const PoseDesc& P = *pd;
     const int nd = P.n_dof, na = nd + 1;
     const int npairs = na * (na + 1) / 2;
-    const int nact = (2 * P.J + *P.bcount + kSysItems - 1) / kSysItems;
+    const int nact = (3 * P.J + *P.bcount + kSysItems - 1) / kSysItems;
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_bad = 0;
@@ -530,14 +545,25 @@ __global__ void __launch_bounds__(kSolveThreads) pose_solve_kernel(const PoseDes
         }
     }
     __syncthreads();
-    // angle prior lprior (theta - theta_start) on the Euler DOF, one DOF per thread
+    // angle prior lprior (theta - theta_start) on the Euler DOF, and the
+    // joint-limit barrier l_anatomic Psi(theta) on those outside their limits
+    // (a residual sqrt(l_anatomic)(theta - bound)), one DOF per thread
     if (tid < nd) {
         double e = 0.0;
         if (tid >= 6) {
-            const double dv = (double)P.pose[tid] - (double)P.pose_start[tid];
-            Ap[tri_at(tid, tid)] += (double)P.lam_prior;
-            g[tid] -= (double)P.lam_prior * dv;
+            const double th = (double)P.pose[tid];
+            const double dv = th - (double)P.pose_start[tid];
+            double a = (double)P.lam_prior, gg = -(double)P.lam_prior * dv;
             e = (double)P.lam_prior * dv * dv;
+            const double hi = (double)P.th_hi[tid], lo = (double)P.th_lo[tid];
+            const double over = th > hi ? th - hi : (th < lo ? th - lo : 0.0);
+            if (over != 0.0 && P.lam_anat > 0.f) {
+                a += (double)P.lam_anat;
+                gg -= (double)P.lam_anat * over;
+                e += (double)P.lam_anat * over * over;
+            }
+            Ap[tri_at(tid, tid)] += a;
+            g[tid] += gg;
         }
         prior_t[tid] = e;
     }
@@ -841,6 +867,55 @@ void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, 
                       cudaStream_t st) {
     pose_skin_kernel<<<(hC.N + 255) / 256, 256, 0, st>>>(dC, dP, out_base, mode);
 }
+// ---------------------------------------------------------------------------
+// Frame bookkeeping of the pose stage (Sec. 3.3): E_temporal's previous-frame
+// joints and the two-frame pose history of the start extrapolation.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(64) pose_advance_kernel(const PoseDesc* __restrict__ pd) {
+    const PoseDesc& P = *pd;
+    constexpr int kRec = kMaxDof + 9;
+    const int t = threadIdx.x;
+    if (t < P.J) P.prev_joints[t] = make_float4(P.fk->o[t][0], P.fk->o[t][1], P.fk->o[t][2], 0.f);
+    for (int q = t; q < kRec; q += blockDim.x) {
+        const float cur = q < kMaxDof ? (q < P.n_dof ? P.pose[q] : 0.f) : P.Rroot[q - kMaxDof];
+        P.pose_hist[kRec + q] = P.pose_hist[q];
+        P.pose_hist[q] = cur;
+    }
+}
+
+// pose <- 2 theta^{t-1} - theta^{t-2} (Euler angles, root translation),
+// R <- R^{t-1} (R^{t-2})^T R^{t-1}; with one recorded pose, that pose
+__global__ void __launch_bounds__(64) pose_extrapolate_kernel(const PoseDesc* __restrict__ pd) {
+    const PoseDesc& P = *pd;
+    constexpr int kRec = kMaxDof + 9;
+    const float* h0 = P.pose_hist;
+    const float* h1 = P.pose_hist + kRec;
+    const bool two = P.n_hist >= 2;
+    const int t = threadIdx.x;
+    if (t >= 3 && t < P.n_dof) P.pose[t] = two ? 2.f * h0[t] - h1[t] : h0[t];
+    if (t == 0) {
+        const float* R0 = h0 + kMaxDof;
+        float R[9];
+        if (two) {
+            const float* R1 = h1 + kMaxDof;
+            float R1t[9], M[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) R1t[3 * a + b] = R1[3 * b + a];
+            mat3mul(R0, R1t, M);
+            mat3mul(M, R0, R);
+        } else {
+            for (int q = 0; q < 9; ++q) R[q] = R0[q];
+        }
+        for (int q = 0; q < 9; ++q) P.Rroot[q] = R[q];
+    }
+}
+
+void launch_pose_advance(const PoseDesc* dP, cudaStream_t st) {
+    pose_fk_kernel<<<1, 64, 0, st>>>(dP);
+    pose_advance_kernel<<<1, 64, 0, st>>>(dP);
+}
+void launch_pose_extrapolate(const PoseDesc* dP, cudaStream_t st) { pose_extrapolate_kernel<<<1, 64, 0, st>>>(dP); }
+
 void launch_pose_fk(const PoseDesc* dP, cudaStream_t st) { pose_fk_kernel<<<1, 64, 0, st>>>(dP); }
 void launch_surface_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int mode, cudaStream_t st) {
     if (dP) pose_fk_kernel<<<1, 64, 0, st>>>(dP);   // kinematics of the current pose
@@ -860,7 +935,7 @@ cudaError_t pose_kernels_init(int n_dof) {
     return cudaFuncSetAttribute(pose_system_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pose_system_smem(kMaxDof));
 }
-int pose_system_ctas(int J, int N) { return (2 * J + N + kSysItems - 1) / kSysItems; }
+int pose_system_ctas(int J, int N) { return (3 * J + N + kSysItems - 1) / kSysItems; }
 void launch_pose_system(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int J, int n_dof,
                         cudaStream_t st) {
     pose_system_kernel<<<pose_system_ctas(J, hC.N), kSysThreads, pose_system_smem(n_dof), st>>>(dC, dP);

@@ -27,7 +27,8 @@ class lc_params(ctypes.Structure):
                 ("n_gn_pose", ctypes.c_int), ("lambda_prior", ctypes.c_float), ("pcg_kernel", ctypes.c_int),
                 ("target_energy", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_edge", ctypes.c_float),
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
-                ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int)]
+                ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
+                ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -100,6 +101,10 @@ _SIGS = {
     "lc_set_profiling": [_P, ctypes.c_int],
     "lc_read_profile": [_P, _P, _P],
     "lc_set_rest_geometry": [_P, _P],
+    "lc_set_pose_priors": [_P, _P, _P, _P],
+    "lc_pose_advance": [_P],
+    "lc_pose_extrapolate": [_P],
+    "lc_pose_clear_history": [_P],
     "lc_set_surface": [_P, _P],
     "lc_surface_start": [_P],
     "lc_surface_history": [_P, _P, _P],
@@ -440,6 +445,21 @@ class Context:
     def reset_pose(self):
         """Restart from the pose last given to set_pose (device-side, no sync)."""
         self._check(self._lib.lc_reset_pose(self.h))
+
+    def set_pose_priors(self, temporal_w=None, theta_min=None, theta_max=None):
+        w = _arr(temporal_w, np.float32)
+        lo = _arr(theta_min, np.float32)
+        hi = _arr(theta_max, np.float32)
+        self._check(self._lib.lc_set_pose_priors(self.h, _ptr(w), _ptr(lo), _ptr(hi)))
+
+    def pose_advance(self):
+        self._check(self._lib.lc_pose_advance(self.h))
+
+    def pose_extrapolate(self):
+        self._check(self._lib.lc_pose_extrapolate(self.h))
+
+    def pose_clear_history(self):
+        self._check(self._lib.lc_pose_clear_history(self.h))
 
     def eval_pose(self) -> dict:
         nd = self.n_dof

@@ -60,3 +60,5 @@ def test_params_default(lib):
     assert (p.n_gn_surface, p.n_pcg_surface) == (3, 4)
     assert (p.w_smooth, p.w_edge, p.w_velocity, p.w_acceleration) == (1e3, 3e3, 25.0, 10.0)
     assert p.target_energy == 0.0 and p.pose_solver == 0
+    # pose-stage regularisers (Sec. 5): lambda_temporal 1.5, lambda_anatomic 1e6
+    assert (p.lambda_temporal, p.lambda_anatomic) == (1.5, 1e6)

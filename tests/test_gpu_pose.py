@@ -272,3 +272,115 @@ def test_pose_solve_ill_conditioned(body):
         assert np.isfinite(pose1).all()
         assert res <= 1e-4
         ctx.close()
+
+
+def _priors(body, pose, seed=21):
+    """Per-joint temporal weights and limits around `pose` that leave some
+    Euler angles outside (E_anatomic active)."""
+    rng = np.random.default_rng(seed)
+    J = len(body.skeleton["parents"])
+    w = rng.uniform(1.0, 2.5, size=J).astype(np.float32)
+    n = len(pose)
+    lo = np.full(n, -np.inf, np.float32)
+    hi = np.full(n, np.inf, np.float32)
+    lo[6:] = pose[6:] - rng.uniform(-0.04, 0.3, size=n - 6)
+    hi[6:] = pose[6:] + rng.uniform(-0.04, 0.3, size=n - 6)
+    lo[6:], hi[6:] = np.minimum(lo[6:], hi[6:] - 0.01), np.maximum(hi[6:], lo[6:] + 0.01)
+    return w, lo, hi
+
+
+def _oracle_joints(pb, pose):
+    _, o = op.forward_kinematics(pb.sk, *op.split_pose(pb.sk, np.asarray(pose, dtype=np.float64)))
+    return o
+
+
+def test_pose_temporal_anatomic_system_matches_oracle(body):
+    """E_temporal (joints of a recorded previous frame) and E_anatomic (some
+    angles beyond their limits) in the exported normal equations."""
+    pose_b = np.asarray(body.pose_init, dtype=np.float32)
+    pose_a = pose_b.copy()
+    pose_a[6:] += np.random.default_rng(22).normal(scale=0.05, size=len(pose_a) - 6).astype(np.float32)
+    w, lo, hi = _priors(body, pose_b)
+    ctx = _ctx(body)
+    ctx.set_pose_priors(w, lo, hi)
+    ctx.set_pose(pose_a)
+    ctx.pose_advance()
+    ctx.set_pose(pose_b)
+    ev = ctx.eval_pose()
+    flags = ctx.read_visibility()["flags"]
+    pb = _oracle_pose_problem(body, flags)
+    pb.pose_init = pose_b.astype(np.float64)
+    pb.tris = None
+    pb.prev_joints = _oracle_joints(pb, pose_a)
+    pb.temporal_w = w.astype(np.float64)
+    pb.theta_min, pb.theta_max = lo.astype(np.float64), hi.astype(np.float64)
+    active = int(((pose_b[6:] > hi[6:]) | (pose_b[6:] < lo[6:])).sum())
+    F, J = op.residuals_and_jacobian(pb, pose_b.astype(np.float64))
+    A_ref, g_ref = J.T @ J, -(J.T @ F)
+    dA = np.abs(ev["A"] - A_ref).max() / np.abs(A_ref).max()
+    dg = np.abs(ev["g"] - g_ref).max() / np.abs(g_ref).max()
+    dE = abs(ev["energy"][0] - F @ F) / (F @ F)
+    report("pose_priors_system", dA=dA, dg=dg, dE=dE, active=active)
+    assert active >= 3
+    assert dA <= 1e-4 and dg <= 1e-4 and dE <= 1e-4
+    ctx.close()
+
+
+def test_pose_temporal_anatomic_solve_matches_oracle(body):
+    pose_b = np.asarray(body.pose_init, dtype=np.float32)
+    pose_a = pose_b.copy()
+    pose_a[6:] += np.random.default_rng(23).normal(scale=0.05, size=len(pose_a) - 6).astype(np.float32)
+    w, lo, hi = _priors(body, pose_b, seed=24)
+    ctx = _ctx(body)
+    ctx.set_pose_priors(w, lo, hi)
+    ctx.set_pose(pose_a)
+    ctx.pose_advance()
+    ctx.set_pose(pose_b)
+    st = ctx.solve_pose()
+    flags = ctx.read_visibility()["flags"]
+    pose_gpu = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    pb = _oracle_pose_problem(body, flags)
+    pb.prev_joints = _oracle_joints(pb, pose_a)
+    pb.temporal_w = w.astype(np.float64)
+    pb.theta_min, pb.theta_max = lo.astype(np.float64), hi.astype(np.float64)
+    pose_ref, hist = op.gauss_newton(pb, pose_b.astype(np.float64), body.n_gn_pose)
+    dj = np.abs(_oracle_joints(pb, pose_gpu) - _oracle_joints(pb, pose_ref)).max()
+    e_ref = op.energy(pb, pose_ref)
+    de = abs(st["e_total"] - e_ref) / e_ref
+    dh = np.abs(np.array(st["e_gn"]) - [h["energy"] for h in hist]).max() / hist[0]["energy"]
+    report("pose_priors_solve", dj=dj, de=de, dh=dh, rounds=max(st["pcg_iters"]))
+    assert dj <= 2e-3 and de <= 1e-2 and dh <= 1e-3
+    ctx.close()
+
+
+def test_pose_extrapolation_matches_oracle(body):
+    p2 = np.asarray(body.pose_init, dtype=np.float32)
+    rng = np.random.default_rng(25)
+    p1 = p2.copy()
+    p1[:6] += rng.normal(scale=0.03, size=6).astype(np.float32)
+    p1[6:] += rng.normal(scale=0.05, size=len(p1) - 6).astype(np.float32)
+    ctx = _ctx(body)
+    from paper_1810_02648_gb300 import LivecapError
+    with pytest.raises(LivecapError):
+        ctx.pose_extrapolate()                       # nothing recorded yet
+    ctx.set_pose(p2)
+    ctx.pose_advance()
+    ctx.pose_extrapolate()                           # one recorded pose: that pose
+    one = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    ctx.set_pose(p1)
+    ctx.pose_advance()
+    ctx.pose_extrapolate()
+    two = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    ref1 = op.extrapolate(p2.astype(np.float64))
+    ref2 = op.extrapolate(p1.astype(np.float64), p2.astype(np.float64))
+    R_gpu = onr.so3_exp(two[None, :3].astype(np.float64))[0]
+    R_ref = onr.so3_exp(ref2[None, :3])[0]
+    report("pose_extrapolate", d1=np.abs(one - ref1).max(), d2=np.abs(two[3:] - ref2[3:]).max(),
+           dR=np.abs(R_gpu - R_ref).max())
+    assert np.abs(one - ref1).max() <= 2e-6
+    assert np.abs(two[3:] - ref2[3:]).max() <= 2e-6
+    assert np.abs(R_gpu - R_ref).max() <= 2e-6
+    ctx.pose_clear_history()
+    with pytest.raises(LivecapError):
+        ctx.pose_extrapolate()
+    ctx.close()
