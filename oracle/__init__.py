@@ -24,6 +24,8 @@ pose        the skeletal stage-1 fit (Sec. 3.3): forward kinematics, linear
 surface     the paper's own per-vertex formulation of the non-rigid stage
             (unknowns V; E_smooth, E_edge, E_velocity, E_acceleration beside
             the data terms), its sparse Jacobian and Gauss-Newton, in FP64.
+dt          the silhouette distance transform (exact squared distances to
+            the contour pixels, FP32 square root).
 mlp         the learned per-node warm start network in FP64 (forward,
             backward, Adam), the reference for the BF16 kernels.
 """
