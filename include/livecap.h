@@ -190,9 +190,20 @@ lc_status lc_set_rest_geometry(lc_ctx *ctx, const float *V_S);
  * foreground flags (non-zero = foreground).  joints2d (J x 2 pixels) and
  * joints3d (J x 3 metres) are the pose stage's detections (Sec. 3.3); both
  * may be null when no skeleton is used.  The images are repacked on the
- * device into one float4 (r, g, b, dt) per pixel. */
+ * device into one float4 (r, g, b, dt) per pixel.
+ * dt = NULL: the distance transform is computed on the device from the mask,
+ * exactly: the distance between pixel centres to the nearest contour pixel (a
+ * foreground pixel with a 4-neighbour in the background or on the image
+ * border), from integer squared distances (separable: the distance along
+ * each column, then the minimum over the row's columns), rounded once to
+ * FP32; 0 everywhere when the silhouette has no contour. */
 lc_status lc_upload_frame(lc_ctx *ctx, const float *rgb, const float *dt, const uint8_t *mask,
                           const float *joints2d, const float *joints3d);
+
+/* The frame as the solver samples it (inspection; synchronises): dt (H x W
+ * floats, the uploaded or device-computed distance transform) and mask
+ * (H x W, 0 / 1); either may be NULL. */
+lc_status lc_read_frame(lc_ctx *ctx, float *dt, uint8_t *mask);
 
 /* ---- solve ---------------------------------------------------------------- */
 

@@ -232,6 +232,8 @@ extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int
         ctx->release(ctx->stage_rgb);
         ctx->release(ctx->stage_dt);
         ctx->release(ctx->stage_mask);
+        ctx->release(ctx->edt_g);
+        ctx->edt_g = nullptr;
         const size_t P = (size_t)W * H;
         ctx->hC.img = (const float4*)ctx->alloc(sizeof(float4) * P);
         ctx->hC.mask = (const uint8_t*)ctx->alloc(P);
@@ -600,7 +602,7 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
                                      const float* joints2d, const float* joints3d) {
     if (!ctx) return LC_ERR_ARG;
     if (!ctx->has_camera) return ctx->fail(LC_ERR_STATE, "lc_upload_frame: no camera");
-    if (!rgb || !dt || !mask) return ctx->fail(LC_ERR_ARG, "lc_upload_frame: null image");
+    if (!rgb || !mask) return ctx->fail(LC_ERR_ARG, "lc_upload_frame: null image");
     cudaSetDevice(ctx->device);
     CapDesc& C = ctx->hC;
     const size_t P = (size_t)C.W * C.H;
@@ -614,7 +616,7 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
             return s;
         drgb = ctx->stage_rgb;
     }
-    if (!lc_ctx::is_device_ptr(dt)) {
+    if (dt && !lc_ctx::is_device_ptr(dt)) {
         if ((s = ctx->cuda(cudaMemcpyAsync(ctx->stage_dt, dt, sizeof(float) * P, cudaMemcpyDefault, st), "frame upload")))
             return s;
         ddt = ctx->stage_dt;
@@ -625,10 +627,41 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
     }
     launch_pack_frame(drgb, ddt, dmask, (float4*)C.img, (uint8_t*)C.mask, C.W, C.H, st);
     if ((s = ctx->cuda(cudaGetLastError(), "pack frame"))) return s;
+    if (!dt) {
+        // the distance transform of the silhouette on the device (scratch on first use)
+        if (!ctx->edt_g) {
+            ctx->edt_g = (int*)ctx->alloc(sizeof(int) * P);
+            if (!ctx->edt_g) return LC_ERR_OOM;
+        }
+        launch_edt(C.mask, ctx->edt_g, (float4*)C.img, C.W, C.H, st);
+        if ((s = ctx->cuda(cudaGetLastError(), "distance transform"))) return s;
+    }
     if ((s = ctx->pose_frame(joints2d, joints3d))) return s;
     ctx->has_frame = true;
     ctx->has_vis = false;
     ctx->has_lin = false;
+    return LC_OK;
+}
+
+extern "C" lc_status lc_read_frame(lc_ctx* ctx, float* dt, uint8_t* mask) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_frame) return ctx->fail(LC_ERR_STATE, "lc_read_frame: no frame");
+    cudaSetDevice(ctx->device);
+    const CapDesc& C = ctx->hC;
+    const size_t P = (size_t)C.W * C.H;
+    lc_status s;
+    if (dt) {
+        std::vector<float4> img(P);
+        if ((s = ctx->copy_to_host(img.data(), C.img, sizeof(float4) * P))) return s;
+        std::vector<float> d(P);
+        for (size_t p = 0; p < P; ++p) d[p] = img[p].w;
+        if ((s = ctx->deliver(dt, d.data(), sizeof(float) * P))) return s;
+    }
+    if (mask) {
+        std::vector<uint8_t> m(P);
+        if ((s = ctx->copy_to_host(m.data(), C.mask, P))) return s;
+        if ((s = ctx->deliver(mask, m.data(), P))) return s;
+    }
     return LC_OK;
 }
 

@@ -26,7 +26,7 @@ __global__ void pack_frame_kernel(const float* __restrict__ rgb, const float* __
                                   uint8_t* __restrict__ mask, int P) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
-    img[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], dt[p]);
+    img[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], dt ? dt[p] : 0.f);   // dt null: computed next
     mask[p] = mask_in[p] ? 1 : 0;
 }
 
@@ -34,6 +34,103 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
                        int W, int H, cudaStream_t st) {
     const int P = W * H;
     pack_frame_kernel<<<(P + 255) / 256, 256, 0, st>>>(rgb, dt, mask_in, img, mask, P);
+}
+
+// ---------------------------------------------------------------------------
+// Silhouette distance transform (Sec. 3.2), exact: the squared Euclidean
+// distance to the nearest contour pixel (a foreground pixel with a
+// 4-neighbour in the background or on the image border) in integers, by the
+// separable decomposition d^2(x, y) = min_i (x - i)^2 + g(i, y)^2 with
+// g(i, y) the distance along column i to its nearest contour pixel:
+//   phase 1, a CTA per 32 columns, 32 row chunks each: every thread finds the
+//     last / first contour row of its chunk, the chunks are combined through
+//     shared memory (a max / min scan over 32 values), then every thread
+//     writes g for its chunk;
+//   phase 2, a CTA per row with g of the row in shared memory: every pixel
+//     searches columns x -+ k outward while k^2 is below its best d^2 (the
+//     minimum cannot lie further out).
+// I_DT = sqrt(d^2) rounded once to FP32, written into the frame's fourth
+// channel; 0 everywhere when the silhouette has no contour.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_contour(const uint8_t* m, int W, int H, int x, int y) {
+    if (!m[(size_t)y * W + x]) return false;
+    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) return true;
+    return !m[(size_t)y * W + x - 1] || !m[(size_t)y * W + x + 1] || !m[(size_t)(y - 1) * W + x] ||
+           !m[(size_t)(y + 1) * W + x];
+}
+
+constexpr int kEdtChunks = 32;
+
+__global__ void __launch_bounds__(32 * kEdtChunks) edt_columns_kernel(const uint8_t* __restrict__ mask,
+                                                                       int* __restrict__ g, int W, int H) {
+    __shared__ int s_last[kEdtChunks][33], s_first[kEdtChunks][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + tx;
+    const int L = (H + kEdtChunks - 1) / kEdtChunks;
+    const int y0 = ty * L, y1 = min(H, y0 + L);
+    const int NONE_LO = -(W + H) - 1, NONE_HI = 2 * (W + H) + 1;
+    int last = NONE_LO, first = NONE_HI;
+    if (x < W)
+        for (int y = y0; y < y1; ++y)
+            if (is_contour(mask, W, H, x, y)) {
+                if (first == NONE_HI) first = y;
+                last = y;
+            }
+    s_last[ty][tx] = last;
+    s_first[ty][tx] = first;
+    __syncthreads();
+    // the nearest contour rows above this chunk and below it
+    int above = NONE_LO, below = NONE_HI;
+    for (int c = 0; c < ty; ++c) above = max(above, s_last[c][tx]);
+    for (int c = kEdtChunks - 1; c > ty; --c) below = min(below, s_first[c][tx]);
+    if (x >= W) return;
+    const int inf = W + H;
+    // down the chunk with the last contour row so far, then up it
+    int lastc = above;
+    for (int y = y0; y < y1; ++y) {
+        if (is_contour(mask, W, H, x, y)) lastc = y;
+        g[(size_t)y * W + x] = min(inf, y - lastc);
+    }
+    int nextc = below;
+    for (int y = y1 - 1; y >= y0; --y) {
+        const int v = g[(size_t)y * W + x];
+        if (v == 0) nextc = y;
+        const int d = min(inf, nextc - y);
+        if (d < v) g[(size_t)y * W + x] = d;
+    }
+}
+
+__global__ void __launch_bounds__(256) edt_rows_kernel(const int* __restrict__ g, float4* __restrict__ img, int W,
+                                                       int H) {
+    extern __shared__ int s_g[];   // g of this row
+    const int y = blockIdx.x;
+    const int* gy = g + (size_t)y * W;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) s_g[x] = gy[x];
+    __syncthreads();
+    const int inf = W + H;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const int gx = s_g[x];
+        int best = gx * gx;   // inf^2 when the column has no contour
+        for (int k = 1; k * k < best && (x - k >= 0 || x + k < W); ++k) {
+            const int k2 = k * k;
+            if (x - k >= 0) {
+                const int a = s_g[x - k];
+                best = min(best, k2 + a * a);
+            }
+            if (x + k < W) {
+                const int b = s_g[x + k];
+                best = min(best, k2 + b * b);
+            }
+        }
+        img[(size_t)y * W + x].w = best >= inf * inf ? 0.f : sqrtf((float)best);
+    }
+}
+
+void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st) {
+    const size_t smem = sizeof(int) * W;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(edt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    edt_columns_kernel<<<(W + 31) / 32, 32 * kEdtChunks, 0, st>>>(mask, g, W, H);
+    edt_rows_kernel<<<H, 256, smem, st>>>(g, img, W, H);
 }
 
 // ---------------------------------------------------------------------------

@@ -34,6 +34,7 @@ struct lc_ctx {
     float* stage_rgb = nullptr;
     float* stage_dt = nullptr;
     uint8_t* stage_mask = nullptr;
+    int* edt_g = nullptr;         // distance-transform scratch (first use of a null dt)
     // scratch node vectors
     float4* tmp_vec = nullptr;
     float4* tmp_vec2 = nullptr;

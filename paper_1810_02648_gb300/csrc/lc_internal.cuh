@@ -361,6 +361,9 @@ inline Tiles single_tiles(const CapDesc& C) {
 // ---- kernel launchers (frame_kernels.cu, solver_kernels.cu, graph_kernels.cu)
 void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in, float4* img,
                        uint8_t* mask, int W, int H, cudaStream_t st);
+// exact silhouette distance transform of the packed mask into img's 4th
+// channel (g: W x H int scratch; W <= 16384, g of a row in shared memory)
+void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st);
 void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st, bool gated = false);
 // gated: skipped for captures whose GN loop has stopped (steps after the first)
 void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st, bool gated = false);

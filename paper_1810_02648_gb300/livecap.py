@@ -101,6 +101,7 @@ _SIGS = {
     "lc_set_profiling": [_P, ctypes.c_int],
     "lc_read_profile": [_P, _P, _P],
     "lc_set_rest_geometry": [_P, _P],
+    "lc_read_frame": [_P, _P, _P],
     "lc_set_pose_priors": [_P, _P, _P, _P],
     "lc_pose_advance": [_P],
     "lc_pose_extrapolate": [_P],
@@ -276,6 +277,13 @@ class Context:
         j2 = _arr(joints2d, np.float32)
         j3 = _arr(joints3d, np.float32)
         self._check(self._lib.lc_upload_frame(self.h, _ptr(rgb), _ptr(dt), _ptr(mask), _ptr(j2), _ptr(j3)))
+
+    def read_frame(self):
+        """(dt H x W float32, mask H x W uint8) as the solver samples them."""
+        dt = np.zeros((self.H, self.W), np.float32)
+        mask = np.zeros((self.H, self.W), np.uint8)
+        self._check(self._lib.lc_read_frame(self.h, _ptr(dt), _ptr(mask)))
+        return dt, mask
 
     # ---- solve
     def solve_nonrigid(self, stats: bool = True):
