@@ -100,6 +100,11 @@ typedef struct {
                                once lc_pose_advance has recorded a frame */
     float lambda_anatomic;  /* pose stage E_anatomic (Sec. 5: 1e6); active for the
                                limits of lc_set_pose_priors */
+    float sigma_c;          /* robust colour kernel of E_photo (Sec. 3.4): a visible
+                               vertex whose colour difference ||I(pi(v)) - C|| (FP32,
+                               Euclidean over RGB) exceeds sigma_c has its photometric
+                               residual and rows zeroed at that linearisation
+                               (LC_FLAG_PRUNED); 0 (default) = off */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -127,6 +132,7 @@ typedef struct {
 #define LC_FLAG_ONSIL 2u     /* vertex on a silhouette edge */
 #define LC_FLAG_INB 4u       /* vertex in the contour set B */
 #define LC_FLAG_BNEG 8u      /* b_i = -1 */
+#define LC_FLAG_PRUNED 16u   /* photometric residual pruned by sigma_c at the last linearisation */
 
 /* ---- context ------------------------------------------------------------- */
 

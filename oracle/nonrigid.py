@@ -109,6 +109,8 @@ class Problem:
     inB: Optional[np.ndarray] = None     # (N,) bool
     bsign: Optional[np.ndarray] = None   # (N,) +-1
     tris: Optional[np.ndarray] = None    # (T,3): when set, b_i follows the current surface
+    sigma_c: float = 0.0                 # robust colour kernel threshold (0: off)
+    pruned: Optional[np.ndarray] = None  # (N,) given pruning decisions (None: decide here)
 
     @property
     def n(self) -> int:
@@ -214,6 +216,25 @@ def dproj(P: Problem, v: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Residuals and Jacobian
 # ----------------------------------------------------------------------------
+def prune(P, photo_on: np.ndarray, u: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """The robust colour kernel sigma_c (Sec. 3.4): photometric
+    correspondences whose colour difference ||I(pi(v)) - C|| exceeds sigma_c
+    are dropped (their residual and Jacobian rows are zero).  P.pruned, when
+    given, holds the decisions instead (taken in FP32 by the kernel; the
+    FP64 distance here differs from it only within rounding of sigma_c)."""
+    if not getattr(P, "sigma_c", 0.0) > 0.0:
+        return photo_on
+    if P.pruned is not None:
+        return photo_on & ~np.asarray(P.pruned, dtype=bool)
+    out = photo_on.copy()
+    idx = np.nonzero(photo_on)[0]
+    if len(idx):
+        d = np.linalg.norm(bilinear(P.rgb, u[idx], w[idx]) - P.albedo[idx], axis=1)
+        out[idx] = d <= P.sigma_c
+    return out
+
+
+
 def vertex_residuals(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     """Per-vertex data residuals at the given parameters.
 
@@ -222,7 +243,7 @@ def vertex_residuals(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     """
     v = warp(P, R, t)
     u, w, valid, inimg = project(P, v)
-    photo_on = inimg & P.vis
+    photo_on = prune(P, inimg & P.vis, u, w)
     sil_on = inimg & P.inB
     photo = np.zeros((len(v), 3))
     sil = np.zeros(len(v))

@@ -93,6 +93,8 @@ class SurfaceProblem:
     vis: Optional[np.ndarray] = None
     inB: Optional[np.ndarray] = None
     bsign: Optional[np.ndarray] = None
+    sigma_c: float = 0.0                 # robust colour kernel threshold (0: off)
+    pruned: Optional[np.ndarray] = None  # (N,) given pruning decisions (None: decide here)
 
     def __post_init__(self):
         f64 = lambda a: np.asarray(a, dtype=np.float64)  # noqa: E731
@@ -132,7 +134,7 @@ def residuals(P: SurfaceProblem, V: np.ndarray) -> dict:
     """All residual blocks at vertex positions V (N,3)."""
     V = np.asarray(V, dtype=np.float64)
     u, w, valid, inimg = _nr.project(P, V)
-    photo_on = inimg & P.vis
+    photo_on = _nr.prune(P, inimg & P.vis, u, w)
     sil_on = inimg & P.inB
     photo = np.zeros((P.N, 3))
     sil = np.zeros(P.N)

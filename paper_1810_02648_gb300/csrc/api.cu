@@ -124,6 +124,7 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->pose_solver = 0;
     p->lambda_temporal = 1.5f;
     p->lambda_anatomic = 1.0e6f;
+    p->sigma_c = 0.0f;
     return LC_OK;
 }
 
@@ -197,6 +198,7 @@ void lc_ctx::apply_params() {
     hC.w_arap = params.w_arap;
     hC.eps_vis = params.eps_vis;
     hC.target_energy = params.target_energy;
+    hC.sigma_c = params.sigma_c;
     surface_weights();
 }
 
@@ -207,7 +209,8 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->lambda_2d >= 0.f) || !(p->lambda_3d >= 0.f) || !(p->lambda_sil >= 0.f) || !(p->lambda_prior >= 0.f) ||
         !(p->target_energy >= 0.f) || p->n_gn_surface < 1 || p->n_gn_surface > LC_MAX_GN || p->n_pcg_surface < 1 ||
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
-        p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f))
+        p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
+        !(p->sigma_c >= 0.f))
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 2) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0, 1 or 2");

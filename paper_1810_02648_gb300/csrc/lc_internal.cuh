@@ -28,6 +28,7 @@ constexpr uint32_t LC_VIS_BIT = LC_FLAG_VISIBLE;
 constexpr uint32_t LC_ONSIL_BIT = LC_FLAG_ONSIL;
 constexpr uint32_t LC_INB_BIT = LC_FLAG_INB;
 constexpr uint32_t LC_BNEG_BIT = LC_FLAG_BNEG;
+constexpr uint32_t LC_PRUNED_BIT = LC_FLAG_PRUNED;
 
 // Per-capture reduction scalars (FP64; PCG dots and energies).
 struct Scalars {
@@ -59,6 +60,7 @@ struct CapDesc {
     int vert_tiles, node_tiles, tri_tiles, medge_tiles;
     float f, cx, cy;
     float w_photo, w_sil, w_arap, eps_vis;
+    float sigma_c;         // robust colour kernel threshold (0: off)
     float target_energy;   // > 0: stop the GN loop once the energy is <= this
     // template (rest geometry of this stage) and mesh topology
     const float4* base;      // N (x, y, z, 0)

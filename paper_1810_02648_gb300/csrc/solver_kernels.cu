@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         const float4 v = C.vw[i];
         const float2 uv = C.uv[i];
         const bool ok = v.w > 0.f && in_image(uv, C.W, C.H);
-        const bool ph = ok && (fl & LC_VIS_BIT);
+        bool ph = ok && (fl & LC_VIS_BIT);
         const bool si = ok && (fl & LC_INB_BIT);
         if (update_b && si) {
             // b_i follows the current surface; the contour set stays the frame's
@@ -118,6 +118,14 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
                 h11 += a1 * a1; h12 += a1 * a2; h22 += a2 * a2;
                 e0 += a0 * r; e1 += a1 * r; e2 += a2 * r;
             };
+            if (ph && C.sigma_c > 0.f) {
+                // robust colour kernel: prune a correspondence whose colour
+                // differs by more than sigma_c (FP32, fixed order)
+                const float4 alb = C.albedo[i];
+                const float dx = xsub(I.x, alb.x), dy = xsub(I.y, alb.y), dz = xsub(I.z, alb.z);
+                const float d2 = xadd(xadd(xmul(dx, dx), xmul(dy, dy)), xmul(dz, dz));
+                if (d2 > xmul(C.sigma_c, C.sigma_c)) ph = false;
+            }
             if (ph) {
                 const float sw = sqrtf(C.w_photo);
                 const float4 alb = C.albedo[i];
@@ -136,6 +144,11 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
                 add_row(Gx.w, Gy.w, bs, res.w);
                 enf[1] = res.w * res.w;
             }
+        }
+        if (C.sigma_c > 0.f) {
+            const bool pruned = ok && (fl & LC_VIS_BIT) && !ph;
+            const uint32_t nf = pruned ? (fl | LC_PRUNED_BIT) : (fl & ~LC_PRUNED_BIT);
+            if (nf != fl) C.flags[i] = nf;
         }
         C.res[i] = res;
         C.HA[i] = make_float4(h00, h01, h02, h11);

@@ -17,7 +17,7 @@ from . import build as _build
 
 LC_OK, LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_NUMERIC, LC_ERR_TIMEOUT, LC_ERR_OOM = 0, -1, -2, -3, -4, -5, -6
 LC_MAX_GN = 64
-FLAG_VISIBLE, FLAG_ONSIL, FLAG_INB, FLAG_BNEG = 1, 2, 4, 8
+FLAG_VISIBLE, FLAG_ONSIL, FLAG_INB, FLAG_BNEG, FLAG_PRUNED = 1, 2, 4, 8, 16
 
 
 class lc_params(ctypes.Structure):
@@ -28,7 +28,7 @@ class lc_params(ctypes.Structure):
                 ("target_energy", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_edge", ctypes.c_float),
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
                 ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
-                ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float)]
+                ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float)]
 
 
 class lc_solve_stats(ctypes.Structure):
