@@ -15,8 +15,11 @@ What it computes (paper references are to sections and equations):
   s-th node bound to vertex i (the normalised-weight form of
   sum_s w_is (R_k (v_i - g_k) + g_k + t_k)), and the pinhole projection
   pi(X,Y,Z) = (f X/Z + cx, f Y/Z + cy) (Sec. 3.3, full perspective camera).
-* The robust colour kernel sigma_c is off (its threshold is not given) and
-  the image is sampled at one pyramid level without blur.
+* The robust colour kernel sigma_c (Sec. 3.4) is off by default (its
+  threshold is not given); when on, it zeroes the photometric rows of a
+  correspondence whose colour differs by more than sigma_c.  The
+  photometric term samples the raw image by default, or the Gaussian
+  pyramid of module ``pyramid`` with one Gauss-Newton iteration per level.
 * Sampling: bilinear, clamp to edge, lerp(a,b,t) = a + t (b - a); image
   gradients are central differences (one-sided at the border) sampled
   bilinearly.  Vertices with Z <= 1e-3 or a projection outside
@@ -46,6 +49,8 @@ from typing import Optional
 
 import numpy as np
 import scipy.sparse as sp
+
+from . import pyramid as _pyr
 
 
 # ----------------------------------------------------------------------------
@@ -111,6 +116,9 @@ class Problem:
     tris: Optional[np.ndarray] = None    # (T,3): when set, b_i follows the current surface
     sigma_c: float = 0.0                 # robust colour kernel threshold (0: off)
     pruned: Optional[np.ndarray] = None  # (N,) given pruning decisions (None: decide here)
+    pyr_levels: int = 0                  # photometric pyramid levels (0: raw image)
+    pyr_ksize: tuple = _pyr.DEFAULT_KSIZE
+    level: Optional[int] = None          # pyramid level sampled now (None: raw image)
 
     @property
     def n(self) -> int:
@@ -180,6 +188,40 @@ def central_differences(img: np.ndarray):
     return gx, gy
 
 
+def photo_level(P, j: int):
+    """Level j of the photometric pyramid and its central differences,
+    cached for the problem's current image."""
+    key = (tuple(int(k) for k in P.pyr_ksize), j)
+    cache = P.__dict__.get("_pyr_cache")
+    if cache is None or cache[0] is not P.rgb:
+        cache = (P.rgb, {})
+        P._pyr_cache = cache
+    if key not in cache[1]:
+        img = _pyr.level_image(P.rgb, j, P.pyr_ksize)
+        cache[1][key] = (img, central_differences(img))
+    return cache[1][key]
+
+
+def photo_sample(P, u: np.ndarray, v: np.ndarray, grad: bool = False):
+    """Colour I(u, v) (m,3) sampled for the photometric term at full-resolution
+    coordinates, from the raw image or the current pyramid level; with grad,
+    also d I / d(u, v) (m,3,2) in full-resolution pixels."""
+    j = getattr(P, "level", None)
+    if j is None:
+        I = bilinear(P.rgb, u, v)
+        if not grad:
+            return I
+        gx, gy = P.grads()[0]
+        return I, np.stack([bilinear(gx, u, v), bilinear(gy, u, v)], axis=2)
+    img, (gx, gy) = photo_level(P, j)
+    uj, vj = _pyr.to_level(u, j), _pyr.to_level(v, j)
+    I = bilinear(img, uj, vj)
+    if not grad:
+        return I
+    d = float(_pyr.FACTORS[j])
+    return I, np.stack([bilinear(gx, uj, vj), bilinear(gy, uj, vj)], axis=2) / d
+
+
 def bilinear(img: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Bilinear sample with clamp to edge; lerp(a,b,t) = a + t(b-a)."""
     H, W = img.shape[:2]
@@ -229,7 +271,7 @@ def prune(P, photo_on: np.ndarray, u: np.ndarray, w: np.ndarray) -> np.ndarray:
     out = photo_on.copy()
     idx = np.nonzero(photo_on)[0]
     if len(idx):
-        d = np.linalg.norm(bilinear(P.rgb, u[idx], w[idx]) - P.albedo[idx], axis=1)
+        d = np.linalg.norm(photo_sample(P, u[idx], w[idx]) - P.albedo[idx], axis=1)
         out[idx] = d <= P.sigma_c
     return out
 
@@ -248,7 +290,7 @@ def vertex_residuals(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     photo = np.zeros((len(v), 3))
     sil = np.zeros(len(v))
     if photo_on.any():
-        photo[photo_on] = np.sqrt(P.w_photo) * (bilinear(P.rgb, u[photo_on], w[photo_on])
+        photo[photo_on] = np.sqrt(P.w_photo) * (photo_sample(P, u[photo_on], w[photo_on])
                                                 - P.albedo[photo_on])
     if sil_on.any():
         sil[sil_on] = np.sqrt(P.w_sil) * bilinear(P.dt, u[sil_on], w[sil_on])
@@ -294,7 +336,7 @@ def linearise(P: Problem, R: np.ndarray, t: np.ndarray):
     update_directions(P, R, t)
     vr = vertex_residuals(P, R, t)
     v, u, w = vr["v"], vr["u"], vr["w"]
-    (gxI, gyI), (gxD, gyD) = P.grads()
+    gxD, gyD = P.grads()[1]
     Dp = dproj(P, v)
     rows, cols, vals, Fs = [], [], [], []
     row0 = 0
@@ -315,7 +357,7 @@ def linearise(P: Problem, R: np.ndarray, t: np.ndarray):
 
     ip = np.nonzero(vr["photo_on"])[0]
     if len(ip):
-        G = np.stack([bilinear(gxI, u[ip], w[ip]), bilinear(gyI, u[ip], w[ip])], axis=2)  # (m,3,2)
+        G = photo_sample(P, u[ip], w[ip], grad=True)[1]                     # (m,3,2)
         A = np.sqrt(P.w_photo) * (G @ Dp[ip])
         node_blocks(ip, A)
         Fs.append(vr["photo"][ip].ravel())
@@ -406,13 +448,20 @@ def apply_update(R: np.ndarray, t: np.ndarray, delta: np.ndarray):
 def gauss_newton(P: Problem, R: np.ndarray, t: np.ndarray, n_gn: int, n_pcg: int):
     """Fixed-count Gauss-Newton (no damping, no line search)."""
     hist = []
-    for _ in range(n_gn):
+    for gn in range(n_gn):
+        P.level = _pyr.level_of(gn, P.pyr_levels)
         A, b, F, _ = normal_equations(P, R, t)
         delta, info = pcg(A, b, n_pcg)
         hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta)),
                          pcg_iters=info["iters"], breakdown=info["breakdown"]))
         R, t = apply_update(R, t, delta)
+    P.level = final_level(P)
     return R, t, hist
+
+
+def final_level(P):
+    """Level of the energy after the last update: the finest one."""
+    return _pyr.level_of(1 << 20, P.pyr_levels)
 
 
 # ----------------------------------------------------------------------------
@@ -449,14 +498,20 @@ def problem_from_scene(scene, graph: dict, base32: Optional[np.ndarray] = None) 
         rgb=scene.rgb, dt=scene.dt, mask=scene.mask, tris=np.asarray(scene.F, dtype=np.int32), w_photo=wp, w_sil=ws, w_arap=wa)
 
 
-def solve_scene(scene, graph: Optional[dict] = None, base32=None, n_gn=None, n_pcg=None):
-    """Whole non-rigid solve from identity parameters.  Returns a dict."""
+def solve_scene(scene, graph: Optional[dict] = None, base32=None, n_gn=None, n_pcg=None,
+                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE):
+    """Whole non-rigid solve from identity parameters (``sigma_c``: the robust
+    colour kernel's threshold, 0 = off; ``pyr_levels``: photometric pyramid
+    levels, 0 = raw image).  Returns a dict."""
     from . import graph as _graph
     if graph is None:
         graph = _graph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
     P = problem_from_scene(scene, graph, base32)
+    P.sigma_c = float(sigma_c)
+    P.pyr_levels, P.pyr_ksize = int(pyr_levels), tuple(pyr_ksize)
     R, t = identity_params(P.n)
     frame_decisions(P, scene.F, R, t)
+    P.level = _pyr.level_of(0, P.pyr_levels)
     e0 = energy(P, R, t)
     R, t, hist = gauss_newton(P, R, t, scene.n_gn if n_gn is None else n_gn,
                               scene.n_pcg if n_pcg is None else n_pcg)

@@ -30,7 +30,9 @@ Readings of points the paper leaves open:
 * The data terms are those of the embedded-graph stage (module
   ``nonrigid``): bilinear sampling with clamp to edge, central-difference
   image gradients, visibility V and contour set B fixed per frame from the
-  exact-arithmetic module, b_i re-evaluated at each linearisation.
+  exact-arithmetic module, b_i re-evaluated at each linearisation; the
+  robust colour kernel sigma_c and the photometric pyramid (module
+  ``pyramid``, one Gauss-Newton iteration per level) as there.
 * Unknowns update additively, V <- V + delta (no damping, no line search).
 """
 from __future__ import annotations
@@ -42,6 +44,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import nonrigid as _nr
+from . import pyramid as _pyr
 
 
 # ----------------------------------------------------------------------------
@@ -95,6 +98,9 @@ class SurfaceProblem:
     bsign: Optional[np.ndarray] = None
     sigma_c: float = 0.0                 # robust colour kernel threshold (0: off)
     pruned: Optional[np.ndarray] = None  # (N,) given pruning decisions (None: decide here)
+    pyr_levels: int = 0                  # photometric pyramid levels (0: raw image)
+    pyr_ksize: tuple = _pyr.DEFAULT_KSIZE
+    level: Optional[int] = None          # pyramid level sampled now (None: raw image)
 
     def __post_init__(self):
         f64 = lambda a: np.asarray(a, dtype=np.float64)  # noqa: E731
@@ -139,7 +145,7 @@ def residuals(P: SurfaceProblem, V: np.ndarray) -> dict:
     photo = np.zeros((P.N, 3))
     sil = np.zeros(P.N)
     if photo_on.any():
-        photo[photo_on] = np.sqrt(P.w_photo) * (_nr.bilinear(P.rgb, u[photo_on], w[photo_on])
+        photo[photo_on] = np.sqrt(P.w_photo) * (_nr.photo_sample(P, u[photo_on], w[photo_on])
                                                 - P.albedo[photo_on])
     if sil_on.any():
         sil[sil_on] = np.sqrt(P.w_sil) * _nr.bilinear(P.dt, u[sil_on], w[sil_on])
@@ -198,7 +204,7 @@ def linearise(P: SurfaceProblem, V: np.ndarray, directions: bool = True):
         update_directions(P, V)
     r = residuals(P, V)
     u, w = r["u"], r["w"]
-    (gxI, gyI), (gxD, gyD) = P.grads()
+    gxD, gyD = P.grads()[1]
     Dp = _nr.dproj(P, V)
     rows, cols, vals, Fs = [], [], [], []
     row0 = 0
@@ -210,7 +216,7 @@ def linearise(P: SurfaceProblem, V: np.ndarray, directions: bool = True):
 
     ip = np.nonzero(r["photo_on"])[0]
     if len(ip):
-        G = np.stack([_nr.bilinear(gxI, u[ip], w[ip]), _nr.bilinear(gyI, u[ip], w[ip])], axis=2)
+        G = _nr.photo_sample(P, u[ip], w[ip], grad=True)[1]               # (m,3,2)
         A = np.sqrt(P.w_photo) * (G @ Dp[ip])                          # (m,3,3)
         block(row0 + 3 * np.arange(len(ip))[:, None, None] + np.arange(3)[None, :, None],
               3 * ip[:, None, None] + np.arange(3)[None, None, :], A)
@@ -269,12 +275,14 @@ def gauss_newton(P: SurfaceProblem, V: np.ndarray, n_gn: int, n_pcg: int):
     """Fixed-count Gauss-Newton over the vertex positions (no damping)."""
     V = np.asarray(V, dtype=np.float64).copy()
     hist = []
-    for _ in range(n_gn):
+    for gn in range(n_gn):
+        P.level = _pyr.level_of(gn, P.pyr_levels)
         A, b, F, _ = normal_equations(P, V)
         delta, info = _nr.pcg(A, b, n_pcg)
         hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta)),
                          pcg_iters=info["iters"], breakdown=info["breakdown"]))
         V = V + delta.reshape(-1, 3)
+    P.level = _nr.final_level(P)
     return V, hist
 
 
@@ -331,12 +339,18 @@ def problem_from_scene(scene, base32: Optional[np.ndarray] = None, weights=None,
         prev1=prev1, prev2=prev2)
 
 
-def solve_scene(scene, base32=None, V0=None, n_gn=None, n_pcg=None, prev1=None, prev2=None):
+def solve_scene(scene, base32=None, V0=None, n_gn=None, n_pcg=None, prev1=None, prev2=None,
+                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE):
     """Whole surface solve of one frame: decisions at the FP32 start V0
-    (default V^S), then n_gn x n_pcg Gauss-Newton.  Returns a dict."""
+    (default V^S), then n_gn x n_pcg Gauss-Newton (``sigma_c``, the robust
+    colour kernel's threshold, 0 = off; ``pyr_levels``, the photometric
+    pyramid's levels, 0 = raw image).  Returns a dict."""
     P = problem_from_scene(scene, base32, prev1=prev1, prev2=prev2)
+    P.sigma_c = float(sigma_c)
+    P.pyr_levels, P.pyr_ksize = int(pyr_levels), tuple(pyr_ksize)
     V = P.base.copy() if V0 is None else np.asarray(V0, dtype=np.float32).astype(np.float64)
     frame_decisions(P, V.astype(np.float32))
+    P.level = _pyr.level_of(0, P.pyr_levels)
     e0 = energy(P, V)
     V, hist = gauss_newton(P, V, scene.n_gn_surface if n_gn is None else n_gn,
                            scene.n_pcg_surface if n_pcg is None else n_pcg)

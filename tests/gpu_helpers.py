@@ -69,13 +69,16 @@ def vec6(x):
     return np.asarray(x, dtype=np.float64).reshape(-1)
 
 
-def oracle_vertex_blocks(P, v32, uv32):
+def oracle_vertex_blocks(P, v32, uv32, pruned=None):
     """Residuals and A_i^T A_i, A_i^T r_i at given FP32 warped positions and
-    projections (the inputs of the GPU's residual kernel), in FP64."""
+    projections (the inputs of the GPU's residual kernel), in FP64; ``pruned``
+    marks photometric correspondences dropped by the robust colour kernel."""
     v = v32.astype(np.float64)
     u, w = uv32[:, 0].astype(np.float64), uv32[:, 1].astype(np.float64)
     ok = (v[:, 2] > 1e-3) & (u >= 0) & (u <= P.W - 1) & (w >= 0) & (w <= P.H - 1)
     ph = ok & P.vis
+    if pruned is not None:
+        ph = ph & ~pruned
     si = ok & P.inB
     (gxI, gyI), (gxD, gyD) = P.grads()
     Dp = onr.dproj(P, v)
@@ -144,7 +147,7 @@ def pcg32(A, b, n, r32):
     return x, info
 
 
-def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None):
+def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None, sigma_c=0.0):
     """Spread of the oracle's end-to-end result under FP32 rounding, with a
     random tie-break perturbation of one unit roundoff (seeded), of what an
     FP32 execution rounds: the node parameters after every update, the warped
@@ -155,7 +158,7 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
     rounding of a pixel boundary takes the other cell of the piecewise
     bilinear image and DT gradients.
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
-    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
+    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c)
     orig = (onr.pcg, onr.linearise, onr.apply_update, onr.warp)
     dE, dV = 0.0, 0.0
     for seed in range(n_runs):
@@ -181,7 +184,7 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
 
         onr.warp = warp32
         try:
-            o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg)
+            o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c)
         finally:
             onr.pcg, onr.linearise, onr.apply_update, onr.warp = orig
         dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
