@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
                 enf[1] = res.w * res.w;
             }
         }
-        if (C.sigma_c > 0.f) {
-            const bool pruned = ok && (fl & LC_VIS_BIT) && !ph;
+        {
+            // the bit always reflects this linearisation (cleared when the kernel is off)
+            const bool pruned = C.sigma_c > 0.f && ok && (fl & LC_VIS_BIT) && !ph;
             const uint32_t nf = pruned ? (fl | LC_PRUNED_BIT) : (fl & ~LC_PRUNED_BIT);
             if (nf != fl) C.flags[i] = nf;
         }
