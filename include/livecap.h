@@ -105,6 +105,17 @@ typedef struct {
                                Euclidean over RGB) exceeds sigma_c has its photometric
                                residual and rows zeroed at that linearisation
                                (LC_FLAG_PRUNED); 0 (default) = off */
+    int pyr_levels;         /* photometric pyramid (Sec. 3.4): 0 (default) samples the raw
+                               image.  1..3: level j = 0, 1, 2 (coarse to fine) is the
+                               frame's RGB box-averaged over d x d blocks, d = 4, 2, 1
+                               (ceil(W/d) x ceil(H/d) pixels, pixel centre at full-resolution
+                               d x + (d-1)/2), then blurred by a separable Gaussian of
+                               pyr_ksize[j] taps (sigma = 0.3((k-1)/2 - 1) + 0.8, rows first,
+                               clamp to edge); Gauss-Newton step g samples level
+                               min(3 - pyr_levels + g, 2), the energy after the last update
+                               the finest.  Only E_photo samples it; the silhouette term
+                               keeps the full-resolution distance transform. */
+    int pyr_ksize[3];       /* Gaussian taps per level, odd, 1..31; default 15, 9, 3 */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -210,6 +221,12 @@ lc_status lc_upload_frame(lc_ctx *ctx, const float *rgb, const float *dt, const 
  * floats, the uploaded or device-computed distance transform) and mask
  * (H x W, 0 / 1); either may be NULL. */
 lc_status lc_read_frame(lc_ctx *ctx, float *dt, uint8_t *mask);
+/* Level j (0 coarsest .. 2 finest) of the photometric pyramid of the current
+ * frame (inspection; synchronises): rgb receives ceil(H/d) x ceil(W/d) x 3
+ * floats (d = 4, 2, 1), W_out / H_out (nullable) its size.  LC_ERR_STATE
+ * when pyr_levels is 0, no frame is loaded or level j is not among the
+ * pyr_levels finest; LC_ERR_ARG for j outside 0..2. */
+lc_status lc_read_pyramid_level(lc_ctx *ctx, int j, float *rgb, int *W_out, int *H_out);
 
 /* ---- solve ---------------------------------------------------------------- */
 

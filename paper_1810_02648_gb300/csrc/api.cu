@@ -125,6 +125,10 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->lambda_temporal = 1.5f;
     p->lambda_anatomic = 1.0e6f;
     p->sigma_c = 0.0f;
+    p->pyr_levels = 0;
+    p->pyr_ksize[0] = 15;
+    p->pyr_ksize[1] = 9;
+    p->pyr_ksize[2] = 3;
     return LC_OK;
 }
 
@@ -210,16 +214,25 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->target_energy >= 0.f) || p->n_gn_surface < 1 || p->n_gn_surface > LC_MAX_GN || p->n_pcg_surface < 1 ||
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
         p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
-        !(p->sigma_c >= 0.f))
+        !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3)
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
+    for (int j = 0; j < 3; ++j)
+        if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)
+            return ctx->fail(LC_ERR_ARG, "lc_set_params: pyr_ksize must be odd, 1..%d", kPyrMaxTaps);
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 2) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0, 1 or 2");
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
         p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
     if (p->n_gn_pose != ctx->params.n_gn_pose) ctx->pose_drop_graph();
+    const bool pyr_changed = p->pyr_levels != ctx->params.pyr_levels ||
+                             memcmp(p->pyr_ksize, ctx->params.pyr_ksize, sizeof(p->pyr_ksize)) != 0;
     ctx->params = *p;
     ctx->apply_params();
+    if (pyr_changed && ctx->has_frame) {
+        lc_status s = ctx->build_pyramid();
+        if (s) return s;
+    }
     return ctx->sync_desc();
 }
 
@@ -237,6 +250,7 @@ extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int
         ctx->release(ctx->stage_mask);
         ctx->release(ctx->edt_g);
         ctx->edt_g = nullptr;
+        ctx->pyr_release();
         const size_t P = (size_t)W * H;
         ctx->hC.img = (const float4*)ctx->alloc(sizeof(float4) * P);
         ctx->hC.mask = (const uint8_t*)ctx->alloc(P);
@@ -639,11 +653,95 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
         launch_edt(C.mask, ctx->edt_g, (float4*)C.img, C.W, C.H, st);
         if ((s = ctx->cuda(cudaGetLastError(), "distance transform"))) return s;
     }
+    if (ctx->params.pyr_levels > 0) {
+        const lc::CapDesc before = C;
+        if ((s = ctx->build_pyramid())) return s;
+        if (memcmp(&before, &C, sizeof(lc::CapDesc)) != 0 && (s = ctx->sync_desc())) return s;
+    }
     if ((s = ctx->pose_frame(joints2d, joints3d))) return s;
     ctx->has_frame = true;
     ctx->has_vis = false;
     ctx->has_lin = false;
     return LC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// photometric pyramid (Sec. 3.4)
+// ---------------------------------------------------------------------------
+void lc_ctx::pyr_release() {
+    for (int j = 0; j < 3; ++j) {
+        release(pyr_buf[j]);
+        pyr_buf[j] = nullptr;
+        hC.lvl[j] = nullptr;
+        hC.lvl_W[j] = hC.lvl_H[j] = 0;
+    }
+    release(pyr_tmp);
+    pyr_tmp = nullptr;
+    hC.pyr_levels = 0;
+}
+
+// Gaussian taps of an odd size k: sigma = 0.3((k-1)/2 - 1) + 0.8, normalised
+// in FP64 and rounded once to FP32
+static PyrTaps pyramid_taps(int k) {
+    PyrTaps T{};
+    T.r = (k - 1) / 2;
+    if (T.r == 0) {
+        T.w[0] = 1.f;
+        return T;
+    }
+    const double sigma = 0.3 * (T.r - 1) + 0.8;
+    double w[kPyrMaxTaps], sum = 0.0;
+    for (int i = -T.r; i <= T.r; ++i) {
+        w[i + T.r] = exp(-(double)(i * i) / (2.0 * sigma * sigma));
+        sum += w[i + T.r];
+    }
+    for (int i = 0; i < 2 * T.r + 1; ++i) T.w[i] = (float)(w[i] / sum);
+    return T;
+}
+
+lc_status lc_ctx::build_pyramid() {
+    const int L = params.pyr_levels;
+    const int W = hC.W, H = hC.H;
+    if (L > 0 && !pyr_tmp && !(pyr_tmp = (float4*)alloc(sizeof(float4) * (size_t)W * H))) return LC_ERR_OOM;
+    for (int j = 0; j < 3; ++j) {
+        if (j < 3 - L) {
+            hC.lvl[j] = nullptr;
+            hC.lvl_W[j] = hC.lvl_H[j] = 0;
+            continue;
+        }
+        const int d = pyr_factor(j), Wd = (W + d - 1) / d, Hd = (H + d - 1) / d;
+        if (!pyr_buf[j] && !(pyr_buf[j] = (float4*)alloc(sizeof(float4) * (size_t)Wd * Hd))) return LC_ERR_OOM;
+        launch_pyramid_level(hC.img, W, H, d, pyramid_taps(params.pyr_ksize[j]), pyr_tmp, pyr_buf[j], Wd, Hd, stream);
+        hC.lvl[j] = pyr_buf[j];
+        hC.lvl_W[j] = Wd;
+        hC.lvl_H[j] = Hd;
+    }
+    hC.pyr_levels = L;
+    return cuda(cudaGetLastError(), "pyramid");
+}
+
+extern "C" lc_status lc_read_pyramid_level(lc_ctx* ctx, int j, float* rgb, int* W_out, int* H_out) {
+    if (!ctx) return LC_ERR_ARG;
+    if (j < 0 || j > 2) return ctx->fail(LC_ERR_ARG, "lc_read_pyramid_level: level must be 0, 1 or 2");
+    const CapDesc& C = ctx->hC;
+    if (!ctx->has_frame || C.pyr_levels == 0 || j < 3 - C.pyr_levels)
+        return ctx->fail(LC_ERR_STATE, "lc_read_pyramid_level: level %d not built", j);
+    cudaSetDevice(ctx->device);
+    const int Wd = C.lvl_W[j], Hd = C.lvl_H[j];
+    if (W_out) *W_out = Wd;
+    if (H_out) *H_out = Hd;
+    if (!rgb) return LC_OK;
+    const size_t P = (size_t)Wd * Hd;
+    std::vector<float4> img(P);
+    lc_status s;
+    if ((s = ctx->copy_to_host(img.data(), C.lvl[j], sizeof(float4) * P))) return s;
+    std::vector<float> out(3 * P);
+    for (size_t p = 0; p < P; ++p) {
+        out[3 * p] = img[p].x;
+        out[3 * p + 1] = img[p].y;
+        out[3 * p + 2] = img[p].z;
+    }
+    return ctx->deliver(rgb, out.data(), sizeof(float) * 3 * P);
 }
 
 extern "C" lc_status lc_read_frame(lc_ctx* ctx, float* dt, uint8_t* mask) {
@@ -742,7 +840,7 @@ void lc_ctx::enqueue_nonrigid() {
             launch_warp(dC, C, st, true);
         }
         mark(LC_PH_LIN);
-        launch_linearize(dC, C, true, st);
+        launch_linearize(dC, C, true, gn, st);
         mark(LC_PH_RHS);
         launch_rhs(dC, C, gn, false, st);
         enqueue_pcg();
@@ -752,7 +850,7 @@ void lc_ctx::enqueue_nonrigid() {
     mark(LC_PH_WARP);
     launch_warp(dC, C, st);
     mark(LC_PH_LIN);
-    launch_linearize(dC, C, false, st);
+    launch_linearize(dC, C, false, LC_MAX_GN, st);
     mark(LC_PH_RHS);
     launch_rhs(dC, C, params.n_gn, true, st);
     launch_vis_unfreeze(dC, st);
@@ -981,7 +1079,7 @@ extern "C" lc_status lc_read_visibility(lc_ctx* ctx, uint64_t* zbuf, uint8_t* fl
 lc_status lc_ctx::linearize_now(bool with_rhs) {
     cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, gn_stop), 0, sizeof(int), stream);
     launch_warp(dC, hC, stream);
-    launch_linearize(dC, hC, true, stream);
+    launch_linearize(dC, hC, true, 0, stream);
     launch_rhs(dC, hC, LC_MAX_GN, !with_rhs, stream);
     has_lin = true;
     return cuda(cudaGetLastError(), "linearize");

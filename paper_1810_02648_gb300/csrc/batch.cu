@@ -255,7 +255,7 @@ void lc_batch::enqueue(bool from_identity) {
     launch_visibility_kernels(dC, all, st);
     for (int gn = 0; gn < n_gn; ++gn) {
         if (gn > 0) launch_warp(dC, all, st, true);
-        launch_linearize(dC, all, true, st);
+        launch_linearize(dC, all, true, gn, st);
         launch_rhs(dC, all, gn, false, st);
         for (const BatchGroup& g : groups)
             launch_pcg_cluster(dC + g.first, g.plan, g.K, n_pcg, st, g.count);
@@ -276,7 +276,7 @@ void lc_batch::enqueue(bool from_identity) {
         launch_update(dC, all, gn, st);
     }
     launch_warp(dC, all, st);
-    launch_linearize(dC, all, false, st);
+    launch_linearize(dC, all, false, LC_MAX_GN, st);
     launch_rhs(dC, all, n_gn, true, st);
 }
 

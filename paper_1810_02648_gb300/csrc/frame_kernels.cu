@@ -134,6 +134,60 @@ void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStre
 }
 
 // ---------------------------------------------------------------------------
+// Photometric pyramid (Sec. 3.4: a 3-level pyramid of the input image, each
+// level Gaussian blurred).  Level pixel (x, y) with factor d is the FP32 mean
+// of the frame's pixels in [d x, d x + d) x [d y, d y + d) inside the image
+// (rows then columns, in order); the blur is separable, rows first, taps
+// applied from -r to r with clamp to edge.  Channels r, g, b; the fourth is 0.
+// ---------------------------------------------------------------------------
+__global__ void pyr_down_kernel(const float4* __restrict__ img, int W, int H, int d, float4* __restrict__ out,
+                                int Wd, int Hd) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= Wd || y >= Hd) return;
+    const int x0 = x * d, y0 = y * d, x1 = min(W, x0 + d), y1 = min(H, y0 + d);
+    float r = 0.f, g = 0.f, b = 0.f;
+    for (int yy = y0; yy < y1; ++yy)
+        for (int xx = x0; xx < x1; ++xx) {
+            const float4 p = __ldg(&img[(size_t)yy * W + xx]);
+            r += p.x;
+            g += p.y;
+            b += p.z;
+        }
+    const float c = (float)((x1 - x0) * (y1 - y0));
+    out[(size_t)y * Wd + x] = make_float4(r / c, g / c, b / c, 0.f);
+}
+
+template <bool kRows>
+__global__ void pyr_blur_kernel(const float4* __restrict__ in, int W, int H, const PyrTaps T,
+                                float4* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    float r = 0.f, g = 0.f, b = 0.f;
+    for (int i = -T.r; i <= T.r; ++i) {
+        const int xs = kRows ? min(max(x + i, 0), W - 1) : x;
+        const int ys = kRows ? y : min(max(y + i, 0), H - 1);
+        const float4 p = __ldg(&in[(size_t)ys * W + xs]);
+        const float w = T.w[i + T.r];
+        r += w * p.x;
+        g += w * p.y;
+        b += w * p.z;
+    }
+    out[(size_t)y * W + x] = make_float4(r, g, b, 0.f);
+}
+
+void launch_pyramid_level(const float4* img, int W, int H, int d, const PyrTaps& taps, float4* tmp, float4* out,
+                          int Wd, int Hd, cudaStream_t st) {
+    const dim3 blk(32, 8), grd((Wd + 31) / 32, (Hd + 7) / 8);
+    const float4* src = img;
+    if (d > 1) {
+        pyr_down_kernel<<<grd, blk, 0, st>>>(img, W, H, d, out, Wd, Hd);
+        src = out;
+    }
+    pyr_blur_kernel<true><<<grd, blk, 0, st>>>(src, Wd, Hd, taps, tmp);
+    pyr_blur_kernel<false><<<grd, blk, 0, st>>>(tmp, Wd, Hd, taps, out);
+}
+
+// ---------------------------------------------------------------------------
 // Warp + project: v'_i = v_i + sum_s w_is ((R_k - I)(v_i - g_k) + t_k).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) warp_kernel(const CapDesc* __restrict__ caps,

@@ -84,6 +84,11 @@ struct CapDesc {
     float4* node_t;          // n (t, 0)
     // frame
     const float4* img;       // H*W (r, g, b, dt)
+    // photometric pyramid (Sec. 3.4): level j = 0..2 box-averaged by
+    // pyr_factor(j) and Gaussian blurred, (r, g, b, 0); pyr_levels = 0: off
+    const float4* lvl[3];
+    int lvl_W[3], lvl_H[3];
+    int pyr_levels;
     const uint8_t* mask;     // H*W
     // per-frame decisions
     unsigned long long* zbuf;  // H*W
@@ -366,6 +371,17 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
 // exact silhouette distance transform of the packed mask into img's 4th
 // channel (g: W x H int scratch; W <= 16384, g of a row in shared memory)
 void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st);
+// level j of the photometric pyramid from the packed frame (rgb of img):
+// box mean over d x d blocks (into out when d > 1), then the separable
+// Gaussian `taps` (2r+1 of them), rows into tmp, columns into out (Wd x Hd)
+constexpr int kPyrMaxTaps = 31;
+__host__ __device__ constexpr int pyr_factor(int j) { return 4 >> j; }   // 4, 2, 1
+struct PyrTaps {
+    float w[kPyrMaxTaps];
+    int r;
+};
+void launch_pyramid_level(const float4* img, int W, int H, int d, const PyrTaps& taps, float4* tmp, float4* out,
+                          int Wd, int Hd, cudaStream_t st);
 void launch_warp(const CapDesc* dC, const CapDesc& hC, cudaStream_t st, bool gated = false);
 // gated: skipped for captures whose GN loop has stopped (steps after the first)
 void launch_warp(const CapDesc* dC, const Tiles& T, cudaStream_t st, bool gated = false);
@@ -373,8 +389,10 @@ void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_visibility_kernels(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 // the next visibility pass runs again (clears vis_frozen)
 void launch_vis_unfreeze(const CapDesc* dC, cudaStream_t st);
-void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st);
-void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st);
+// gn: the Gauss-Newton step being linearised (selects the pyramid level;
+// LC_MAX_GN for the energy after the last update)
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, int gn, cudaStream_t st);
+void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, int gn, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only, cudaStream_t st);
 void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, cudaStream_t st);
 // rotated offsets of bindings, entries and edges for the per-iteration J^T J p

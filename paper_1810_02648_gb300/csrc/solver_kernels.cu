@@ -55,27 +55,47 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
 __device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
 
-__device__ __forceinline__ float4 pix(const CapDesc& C, int x, int y) { return __ldg(&C.img[(size_t)y * C.W + x]); }
+__device__ __forceinline__ float4 pix(const float4* img, int W, int x, int y) {
+    return __ldg(&img[(size_t)y * W + x]);
+}
 
 // central difference (one-sided at the border) of all four channels
-__device__ __forceinline__ float4 grad_x(const CapDesc& C, int x, int y) {
-    if (C.W < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (x == 0) return sub4(pix(C, 1, y), pix(C, 0, y));
-    if (x == C.W - 1) return sub4(pix(C, C.W - 1, y), pix(C, C.W - 2, y));
-    return scale4(sub4(pix(C, x + 1, y), pix(C, x - 1, y)), 0.5f);
+__device__ __forceinline__ float4 grad_x(const float4* img, int W, int x, int y) {
+    if (W < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x == 0) return sub4(pix(img, W, 1, y), pix(img, W, 0, y));
+    if (x == W - 1) return sub4(pix(img, W, W - 1, y), pix(img, W, W - 2, y));
+    return scale4(sub4(pix(img, W, x + 1, y), pix(img, W, x - 1, y)), 0.5f);
 }
-__device__ __forceinline__ float4 grad_y(const CapDesc& C, int x, int y) {
-    if (C.H < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (y == 0) return sub4(pix(C, x, 1), pix(C, x, 0));
-    if (y == C.H - 1) return sub4(pix(C, x, C.H - 1), pix(C, x, C.H - 2));
-    return scale4(sub4(pix(C, x, y + 1), pix(C, x, y - 1)), 0.5f);
+__device__ __forceinline__ float4 grad_y(const float4* img, int W, int H, int x, int y) {
+    if (H < 2) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (y == 0) return sub4(pix(img, W, x, 1), pix(img, W, x, 0));
+    if (y == H - 1) return sub4(pix(img, W, x, H - 1), pix(img, W, x, H - 2));
+    return scale4(sub4(pix(img, W, x, y + 1), pix(img, W, x, y - 1)), 0.5f);
+}
+
+// bilinear sample of an image and of its central differences at (u, v),
+// clamp to edge
+__device__ __forceinline__ void sample_image(const float4* img, int W, int H, float u, float v, float4& I,
+                                             float4& Gx, float4& Gy) {
+    u = fminf(fmaxf(u, 0.f), (float)(W - 1));
+    v = fminf(fmaxf(v, 0.f), (float)(H - 1));
+    const int x0 = (int)floorf(u), y0 = (int)floorf(v);
+    const float fx = u - (float)x0, fy = v - (float)y0;
+    const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+    I = lerp4(lerp4(pix(img, W, x0, y0), pix(img, W, x1, y0), fx), lerp4(pix(img, W, x0, y1), pix(img, W, x1, y1), fx),
+              fy);
+    Gx = lerp4(lerp4(grad_x(img, W, x0, y0), grad_x(img, W, x1, y0), fx),
+               lerp4(grad_x(img, W, x0, y1), grad_x(img, W, x1, y1), fx), fy);
+    Gy = lerp4(lerp4(grad_y(img, W, H, x0, y0), grad_y(img, W, H, x1, y0), fx),
+               lerp4(grad_y(img, W, H, x0, y1), grad_y(img, W, H, x1, y1), fx), fy);
 }
 
 // ---------------------------------------------------------------------------
 // Linearisation: residuals, H_i, e_i and the data energy.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __restrict__ caps,
-                                                               const WorkItem* __restrict__ items, int update_b) {
+                                                               const WorkItem* __restrict__ items, int update_b,
+                                                               int gn) {
     __shared__ float sh[kVertTile / 32][2];
     int cap, tile;
     decode(items, cap, tile);
@@ -100,15 +120,20 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         if (ph || si) {
-            const int x0 = (int)floorf(uv.x), y0 = (int)floorf(uv.y);
-            const float fx = uv.x - (float)x0, fy = uv.y - (float)y0;
-            const int x1 = min(x0 + 1, C.W - 1), y1 = min(y0 + 1, C.H - 1);
-            const float4 I = lerp4(lerp4(pix(C, x0, y0), pix(C, x1, y0), fx),
-                                   lerp4(pix(C, x0, y1), pix(C, x1, y1), fx), fy);
-            const float4 Gx = lerp4(lerp4(grad_x(C, x0, y0), grad_x(C, x1, y0), fx),
-                                    lerp4(grad_x(C, x0, y1), grad_x(C, x1, y1), fx), fy);
-            const float4 Gy = lerp4(lerp4(grad_y(C, x0, y0), grad_y(C, x1, y0), fx),
-                                    lerp4(grad_y(C, x0, y1), grad_y(C, x1, y1), fx), fy);
+            float4 I, Gx, Gy;
+            sample_image(C.img, C.W, C.H, uv.x, uv.y, I, Gx, Gy);
+            if (ph && C.pyr_levels > 0) {
+                // E_photo samples pyramid level j at u_j = (u - (d-1)/2) / d,
+                // its gradient scaled by 1/d to full-resolution pixels
+                const int j = min(3 - C.pyr_levels + gn, 2);
+                const int d = pyr_factor(j);
+                const float inv = 1.0f / (float)d, o = 0.5f * (float)(d - 1);
+                float4 Il, Gxl, Gyl;
+                sample_image(C.lvl[j], C.lvl_W[j], C.lvl_H[j], (uv.x - o) * inv, (uv.y - o) * inv, Il, Gxl, Gyl);
+                I = make_float4(Il.x, Il.y, Il.z, I.w);
+                Gx = make_float4(Gxl.x * inv, Gxl.y * inv, Gxl.z * inv, Gx.w);
+                Gy = make_float4(Gyl.x * inv, Gyl.y * inv, Gyl.z * inv, Gy.w);
+            }
             const float iz = 1.0f / v.z;
             const float fz = C.f * iz;
             const float px = -fz * v.x * iz, py = -fz * v.y * iz;   // d pi / dZ terms
@@ -164,11 +189,11 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     });
 }
 
-void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, cudaStream_t st) {
-    linearize_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, update_b ? 1 : 0);
+void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, int gn, cudaStream_t st) {
+    linearize_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, update_b ? 1 : 0, gn);
 }
-void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, cudaStream_t st) {
-    launch_linearize(dC, single_tiles(hC), update_b, st);
+void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, int gn, cudaStream_t st) {
+    launch_linearize(dC, single_tiles(hC), update_b, gn, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -630,7 +630,7 @@ void lc_ctx::enqueue_surface() {
     const int n_gn = params.n_gn_surface, n_pcg = params.n_pcg_surface;
     for (int gn = 0; gn < n_gn; ++gn) {
         mark(LC_PH_LIN);
-        launch_linearize(dC, C, true, st);
+        launch_linearize(dC, C, true, gn, st);
         mark(LC_PH_RHS);
         launch_surface_rhs(dC, C, gn, false, nullptr, st);
         if (surf_cl > 0 && params.pcg_kernel == 0) {
@@ -650,7 +650,7 @@ void lc_ctx::enqueue_surface() {
         launch_surface_update(dC, C, gn, st);
     }
     mark(LC_PH_LIN);
-    launch_linearize(dC, C, false, st);
+    launch_linearize(dC, C, false, LC_MAX_GN, st);
     mark(LC_PH_RHS);
     launch_surface_rhs(dC, C, n_gn, true, nullptr, st);
     launch_vis_unfreeze(dC, st);
@@ -836,7 +836,7 @@ extern "C" lc_status lc_surface_linearize(lc_ctx* ctx, float* rhs, float* diag, 
     cudaStream_t st = ctx->stream;
     cudaMemsetAsync((char*)C.sc + offsetof(Scalars, gn_stop), 0, 2 * sizeof(int), st);
     launch_surface_project(ctx->dC, C, st);
-    launch_linearize(ctx->dC, C, true, st);
+    launch_linearize(ctx->dC, C, true, 0, st);
     launch_surface_rhs(ctx->dC, C, 0, false, ctx->surf_diag, st);
     if ((s = ctx->cuda(cudaStreamSynchronize(st), "lc_surface_linearize"))) return s;
     ctx->surf_has_lin = true;

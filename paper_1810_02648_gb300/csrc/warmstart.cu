@@ -765,7 +765,7 @@ static void enqueue_warm(lc_ctx* ctx, lc_mlp* m) {
     launch_visibility(ctx->dC, ctx->hC, st);
     cudaMemsetAsync((char*)ctx->hC.sc + offsetof(Scalars, gn_stop), 0, sizeof(int), st);
     launch_warp(ctx->dC, ctx->hC, st);
-    launch_linearize(ctx->dC, ctx->hC, true, st);
+    launch_linearize(ctx->dC, ctx->hC, true, 0, st);
     launch_rhs(ctx->dC, ctx->hC, LC_MAX_GN, false, st);
     node_features_kernel<<<(n + 7) / 8, 256, 0, st>>>(ctx->dC, w.motion, w.F);
     energy_copy_kernel<<<1, 1, 0, st>>>(ctx->dC, w.e);
@@ -775,7 +775,7 @@ static void enqueue_warm(lc_ctx* ctx, lc_mlp* m) {
     apply_prediction_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctx->dC, m->Y, w.R0, w.t0);
     // energy at the prediction (same frame decisions), then accept or restore
     launch_warp(ctx->dC, ctx->hC, st);
-    launch_linearize(ctx->dC, ctx->hC, false, st);
+    launch_linearize(ctx->dC, ctx->hC, false, 0, st);
     launch_rhs(ctx->dC, ctx->hC, LC_MAX_GN, true, st);
     energy_copy_kernel<<<1, 1, 0, st>>>(ctx->dC, w.e + 1);
     accept_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctx->dC, w.e, w.R0, w.t0, w.accepted);

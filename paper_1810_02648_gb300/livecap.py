@@ -28,7 +28,8 @@ class lc_params(ctypes.Structure):
                 ("target_energy", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_edge", ctypes.c_float),
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
                 ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
-                ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float)]
+                ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float),
+                ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -102,6 +103,7 @@ _SIGS = {
     "lc_read_profile": [_P, _P, _P],
     "lc_set_rest_geometry": [_P, _P],
     "lc_read_frame": [_P, _P, _P],
+    "lc_read_pyramid_level": [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "lc_set_pose_priors": [_P, _P, _P, _P],
     "lc_pose_advance": [_P],
     "lc_pose_extrapolate": [_P],
@@ -226,8 +228,10 @@ class Context:
         return p
 
     def set_params(self, **kw):
-        p = self.params() if not hasattr(self, "_params") else self._params
+        p = self.params() if not hasattr(self, "_params") else lc_params.from_buffer_copy(self._params)
         for k, v in kw.items():
+            if k == "pyr_ksize":
+                v = (ctypes.c_int * 3)(*[int(x) for x in v])
             setattr(p, k, v)
         self._check(self._lib.lc_set_params(self.h, ctypes.byref(p)))
         self._params = p
@@ -284,6 +288,14 @@ class Context:
         mask = np.zeros((self.H, self.W), np.uint8)
         self._check(self._lib.lc_read_frame(self.h, _ptr(dt), _ptr(mask)))
         return dt, mask
+
+    def read_pyramid_level(self, j: int):
+        """Level j (0 coarsest) of the photometric pyramid, (Hj, Wj, 3) float32."""
+        Wd, Hd = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._lib.lc_read_pyramid_level(self.h, int(j), None, ctypes.byref(Wd), ctypes.byref(Hd)))
+        out = np.zeros((Hd.value, Wd.value, 3), np.float32)
+        self._check(self._lib.lc_read_pyramid_level(self.h, int(j), _ptr(out), None, None))
+        return out
 
     # ---- solve
     def solve_nonrigid(self, stats: bool = True):

@@ -80,7 +80,7 @@ def oracle_vertex_blocks(P, v32, uv32, pruned=None):
     if pruned is not None:
         ph = ph & ~pruned
     si = ok & P.inB
-    (gxI, gyI), (gxD, gyD) = P.grads()
+    gxD, gyD = P.grads()[1]
     Dp = onr.dproj(P, v)
     N = len(v)
     r_photo = np.zeros((N, 3))
@@ -89,8 +89,8 @@ def oracle_vertex_blocks(P, v32, uv32, pruned=None):
     e = np.zeros((N, 3))
     ip = np.nonzero(ph)[0]
     if len(ip):
-        r_photo[ip] = np.sqrt(P.w_photo) * (onr.bilinear(P.rgb, u[ip], w[ip]) - P.albedo[ip])
-        G = np.stack([onr.bilinear(gxI, u[ip], w[ip]), onr.bilinear(gyI, u[ip], w[ip])], 2)
+        I, G = onr.photo_sample(P, u[ip], w[ip], grad=True)      # raw image or pyramid level P.level
+        r_photo[ip] = np.sqrt(P.w_photo) * (I - P.albedo[ip])
         A = np.sqrt(P.w_photo) * (G @ Dp[ip])
         H[ip] += np.einsum("nri,nrj->nij", A, A)
         e[ip] += np.einsum("nri,nr->ni", A, r_photo[ip])
@@ -147,7 +147,7 @@ def pcg32(A, b, n, r32):
     return x, info
 
 
-def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None, sigma_c=0.0):
+def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None, sigma_c=0.0, pyr_levels=0):
     """Spread of the oracle's end-to-end result under FP32 rounding, with a
     random tie-break perturbation of one unit roundoff (seeded), of what an
     FP32 execution rounds: the node parameters after every update, the warped
@@ -158,7 +158,8 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
     rounding of a pixel boundary takes the other cell of the piecewise
     bilinear image and DT gradients.
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
-    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c)
+    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c,
+                          pyr_levels=pyr_levels)
     orig = (onr.pcg, onr.linearise, onr.apply_update, onr.warp)
     dE, dV = 0.0, 0.0
     for seed in range(n_runs):
@@ -184,7 +185,8 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
 
         onr.warp = warp32
         try:
-            o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c)
+            o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c,
+                                pyr_levels=pyr_levels)
         finally:
             onr.pcg, onr.linearise, onr.apply_update, onr.warp = orig
         dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
@@ -226,14 +228,16 @@ def ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
 
 
 def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n_gn=None, n_pcg=None,
-                          n_runs=3):
+                          n_runs=3, sigma_c=0.0, pyr_levels=0):
     """``fp32_rounding_band`` for the per-vertex surface stage: the spread of
     the oracle's result when its Jacobian entries, residuals, CG vectors and
     products and the vertex positions after every update are rounded to FP32
     with a random tie-break of one unit roundoff.
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
+    from oracle import pyramid as opyr
     from oracle import surface as osf
-    kw = dict(base32=base32, V0=V0, n_gn=n_gn, n_pcg=n_pcg, prev1=prev1, prev2=prev2)
+    kw = dict(base32=base32, V0=V0, n_gn=n_gn, n_pcg=n_pcg, prev1=prev1, prev2=prev2, sigma_c=sigma_c,
+              pyr_levels=pyr_levels)
     ref = osf.solve_scene(scene, **kw)
     orig_pcg, orig_lin, orig_gn = onr.pcg, osf.linearise, osf.gauss_newton
     dE, dV = 0.0, 0.0
@@ -249,12 +253,14 @@ def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n
         def gn32(P, V, n_gn, n_pcg):
             V = np.asarray(V, dtype=np.float64).copy()
             hist = []
-            for _ in range(n_gn):
+            for gn in range(n_gn):
+                P.level = opyr.level_of(gn, P.pyr_levels)
                 A, b, F, _ = osf.normal_equations(P, V)
                 delta, info = onr.pcg(A, b, n_pcg)
                 hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta)),
                                  pcg_iters=info["iters"], breakdown=info["breakdown"]))
                 V = r32(V + delta.reshape(-1, 3))
+            P.level = onr.final_level(P)
             return V, hist
 
         onr.pcg = lambda A, b, n: pcg32(A, b, n, r32)

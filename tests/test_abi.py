@@ -62,3 +62,7 @@ def test_params_default(lib):
     assert p.target_energy == 0.0 and p.pose_solver == 0
     # pose-stage regularisers (Sec. 5): lambda_temporal 1.5, lambda_anatomic 1e6
     assert (p.lambda_temporal, p.lambda_anatomic) == (1.5, 1e6)
+    # robust colour kernel off; photometric pyramid off, the paper's kernel
+    # sizes (Sec. 3.4: 15, 9, 3) ready for it
+    assert p.sigma_c == 0.0 and p.pyr_levels == 0
+    assert list(p.pyr_ksize) == [15, 9, 3]
