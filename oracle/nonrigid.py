@@ -20,6 +20,8 @@ What it computes (paper references are to sections and equations):
   correspondence whose colour differs by more than sigma_c.  The
   photometric term samples the raw image by default, or the Gaussian
   pyramid of module ``pyramid`` with one Gauss-Newton iteration per level.
+  With a body-part mask (module ``parts``) a contour vertex whose projection
+  lands on another part's region has no silhouette residual there.
 * Sampling: bilinear, clamp to edge, lerp(a,b,t) = a + t (b - a); image
   gradients are central differences (one-sided at the border) sampled
   bilinearly.  Vertices with Z <= 1e-3 or a projection outside
@@ -50,6 +52,7 @@ from typing import Optional
 import numpy as np
 import scipy.sparse as sp
 
+from . import parts as _parts
 from . import pyramid as _pyr
 
 
@@ -119,6 +122,8 @@ class Problem:
     pyr_levels: int = 0                  # photometric pyramid levels (0: raw image)
     pyr_ksize: tuple = _pyr.DEFAULT_KSIZE
     level: Optional[int] = None          # pyramid level sampled now (None: raw image)
+    part_mask: Optional[np.ndarray] = None   # (H,W) uint8 body-part mask of V^S (None: off)
+    vpart: Optional[np.ndarray] = None       # (N,) uint8 part of every vertex
 
     @property
     def n(self) -> int:
@@ -286,7 +291,7 @@ def vertex_residuals(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     v = warp(P, R, t)
     u, w, valid, inimg = project(P, v)
     photo_on = prune(P, inimg & P.vis, u, w)
-    sil_on = inimg & P.inB
+    sil_on = inimg & P.inB & ~_parts.masked(P, u, w)
     photo = np.zeros((len(v), 3))
     sil = np.zeros(len(v))
     if photo_on.any():
@@ -499,16 +504,19 @@ def problem_from_scene(scene, graph: dict, base32: Optional[np.ndarray] = None) 
 
 
 def solve_scene(scene, graph: Optional[dict] = None, base32=None, n_gn=None, n_pcg=None,
-                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE):
+                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE,
+                part_mask=None, vpart=None):
     """Whole non-rigid solve from identity parameters (``sigma_c``: the robust
     colour kernel's threshold, 0 = off; ``pyr_levels``: photometric pyramid
-    levels, 0 = raw image).  Returns a dict."""
+    levels, 0 = raw image; ``part_mask`` / ``vpart``: the body-part mask of
+    the silhouette term, None = off).  Returns a dict."""
     from . import graph as _graph
     if graph is None:
         graph = _graph.build_graph(scene.V, scene.material, scene.n_nodes, scene.K)
     P = problem_from_scene(scene, graph, base32)
     P.sigma_c = float(sigma_c)
     P.pyr_levels, P.pyr_ksize = int(pyr_levels), tuple(pyr_ksize)
+    P.part_mask, P.vpart = part_mask, vpart
     R, t = identity_params(P.n)
     frame_decisions(P, scene.F, R, t)
     P.level = _pyr.level_of(0, P.pyr_levels)

@@ -31,8 +31,9 @@ Readings of points the paper leaves open:
   ``nonrigid``): bilinear sampling with clamp to edge, central-difference
   image gradients, visibility V and contour set B fixed per frame from the
   exact-arithmetic module, b_i re-evaluated at each linearisation; the
-  robust colour kernel sigma_c and the photometric pyramid (module
-  ``pyramid``, one Gauss-Newton iteration per level) as there.
+  robust colour kernel sigma_c, the photometric pyramid (module
+  ``pyramid``, one Gauss-Newton iteration per level) and the body-part mask
+  of the silhouette term (module ``parts``) as there.
 * Unknowns update additively, V <- V + delta (no damping, no line search).
 """
 from __future__ import annotations
@@ -44,6 +45,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import nonrigid as _nr
+from . import parts as _parts
 from . import pyramid as _pyr
 
 
@@ -101,6 +103,8 @@ class SurfaceProblem:
     pyr_levels: int = 0                  # photometric pyramid levels (0: raw image)
     pyr_ksize: tuple = _pyr.DEFAULT_KSIZE
     level: Optional[int] = None          # pyramid level sampled now (None: raw image)
+    part_mask: Optional[np.ndarray] = None   # (H,W) uint8 body-part mask of V^S (None: off)
+    vpart: Optional[np.ndarray] = None       # (N,) uint8 part of every vertex
 
     def __post_init__(self):
         f64 = lambda a: np.asarray(a, dtype=np.float64)  # noqa: E731
@@ -141,7 +145,7 @@ def residuals(P: SurfaceProblem, V: np.ndarray) -> dict:
     V = np.asarray(V, dtype=np.float64)
     u, w, valid, inimg = _nr.project(P, V)
     photo_on = _nr.prune(P, inimg & P.vis, u, w)
-    sil_on = inimg & P.inB
+    sil_on = inimg & P.inB & ~_parts.masked(P, u, w)
     photo = np.zeros((P.N, 3))
     sil = np.zeros(P.N)
     if photo_on.any():
@@ -340,14 +344,17 @@ def problem_from_scene(scene, base32: Optional[np.ndarray] = None, weights=None,
 
 
 def solve_scene(scene, base32=None, V0=None, n_gn=None, n_pcg=None, prev1=None, prev2=None,
-                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE):
+                sigma_c: float = 0.0, pyr_levels: int = 0, pyr_ksize=_pyr.DEFAULT_KSIZE,
+                part_mask=None, vpart=None):
     """Whole surface solve of one frame: decisions at the FP32 start V0
     (default V^S), then n_gn x n_pcg Gauss-Newton (``sigma_c``, the robust
     colour kernel's threshold, 0 = off; ``pyr_levels``, the photometric
-    pyramid's levels, 0 = raw image).  Returns a dict."""
+    pyramid's levels, 0 = raw image; ``part_mask`` / ``vpart``, the body-part
+    mask of the silhouette term, None = off).  Returns a dict."""
     P = problem_from_scene(scene, base32, prev1=prev1, prev2=prev2)
     P.sigma_c = float(sigma_c)
     P.pyr_levels, P.pyr_ksize = int(pyr_levels), tuple(pyr_ksize)
+    P.part_mask, P.vpart = part_mask, vpart
     V = P.base.copy() if V0 is None else np.asarray(V0, dtype=np.float32).astype(np.float64)
     frame_decisions(P, V.astype(np.float32))
     P.level = _pyr.level_of(0, P.pyr_levels)

@@ -168,6 +168,15 @@ SKELETON_PARENTS = np.array(
      0, 15, 16, 17,
      0, 19, 20, 21], dtype=np.int32)
 SKELETON_SITES = np.array([4, 9, 14, 18, 22])
+# body part of every joint's bone: torso 0, head 1, left arm 2, right arm 3,
+# left leg 4, right leg 5 (the labels of the silhouette term's part mask)
+SKELETON_BONE_PART = np.array(
+    [0, 0, 0, 1, 1,
+     2, 2, 2, 2, 2,
+     3, 3, 3, 3, 3,
+     4, 4, 4, 4,
+     5, 5, 5, 5], dtype=np.int32)
+TORSO_PART = 0
 N_POSE_DOF = 57
 
 # Rest joint positions relative to the pelvis.  Camera convention: +Y points
@@ -680,7 +689,7 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
         skel = dict(parents=tpl["parents"], joints_rest=tpl["joints_rest"].astype(np.float32),
                     skin_idx=tpl["skin_idx"].astype(np.int32),
                     skin_w=tpl["skin_w"].astype(np.float32),
-                    segment=tpl["segment"])
+                    segment=tpl["segment"], bone_part=SKELETON_BONE_PART.copy(), torso_part=TORSO_PART)
         return Scene(name, cam, V32, F.astype(np.int32), albedo.astype(np.float32),
                      material.astype(np.float32), rgb, dt, mask, n_nodes,
                      over.get("K", 4 if not stress else 8),
