@@ -144,6 +144,8 @@ typedef struct {
 #define LC_FLAG_INB 4u       /* vertex in the contour set B */
 #define LC_FLAG_BNEG 8u      /* b_i = -1 */
 #define LC_FLAG_PRUNED 16u   /* photometric residual pruned by sigma_c at the last linearisation */
+#define LC_FLAG_MASKED 32u   /* silhouette term off at the last linearisation: the vertex projects
+                                onto another body part's region of the part mask */
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -299,6 +301,28 @@ lc_status lc_solve_linear(lc_ctx *ctx, float *delta, int *iters);
  * excluding the root).  J <= 64. */
 lc_status lc_upload_skeleton(lc_ctx *ctx, int J, const int32_t *parents, const float *joints_rest,
                              const uint8_t *dof, const int32_t *skin_idx, const float *skin_w);
+/* Body-part mask of the silhouette term (Sec. 3.4, dense silhouette
+ * alignment).  bone_part (J entries, host or device) gives the body part
+ * (0..254) of each joint's bone; a vertex belongs to the part of its
+ * heaviest skinning bone (the first of equal weights).  Then, once per frame
+ * (at the frame decisions of lc_solve_nonrigid, lc_solve_surface,
+ * lc_compute_visibility and lc_surface_visibility), the stage's rest geometry
+ * V^S is rasterised (the exact rasteriser of the visibility pass) into a
+ * label image, a covered pixel taking the label shared by two or three
+ * vertices of its front triangle (else the first vertex's), and every part
+ * grows into uncovered pixels within dilate_px pixels (Euclidean, pixel
+ * centres): such a pixel takes torso_part if a torso pixel is within reach
+ * (torso_part -1: no precedence), else the nearest part (the lower label on
+ * equal distances).  At every linearisation a contour vertex whose pixel
+ * (floor(u + 1/2), floor(v + 1/2)) carries another part's label has its
+ * silhouette residual switched off (b_i = 0, LC_FLAG_MASKED).  bone_part
+ * NULL switches the mask off.  Needs a skeleton (LC_ERR_STATE); labels above
+ * 254, torso_part outside -1..254 or dilate_px outside 0..32: LC_ERR_ARG.
+ * Contexts with a mask cannot join an lc_batch solve.  Synchronises. */
+lc_status lc_set_body_parts(lc_ctx *ctx, const int32_t *bone_part, int torso_part, int dilate_px);
+/* Inspection of the mask of the last frame decisions (synchronises): mask
+ * H x W labels (255 = no part) and vertex_part N; either may be NULL. */
+lc_status lc_read_part_mask(lc_ctx *ctx, uint8_t *mask, uint8_t *vertex_part);
 /* Set the pose vector (N_DOF values) the next pose solve starts from.
  * Synchronises. */
 lc_status lc_set_pose(lc_ctx *ctx, const float *pose);

@@ -291,7 +291,7 @@ def vertex_residuals(P: Problem, R: np.ndarray, t: np.ndarray) -> dict:
     v = warp(P, R, t)
     u, w, valid, inimg = project(P, v)
     photo_on = prune(P, inimg & P.vis, u, w)
-    sil_on = inimg & P.inB & ~_parts.masked(P, u, w)
+    sil_on = inimg & P.inB & ~_parts.masked(P, v)
     photo = np.zeros((len(v), 3))
     sil = np.zeros(len(v))
     if photo_on.any():

@@ -20,9 +20,10 @@ Readings (the paper names the ingredients only):
   among them, else the label of the nearest one (the lower label on equal
   distances); labelled pixels keep their label.
 * At each linearisation a contour vertex with projection (u, v) reads the
-  label at pixel (floor(u + 1/2), floor(v + 1/2)), computed in FP32 (the
-  kernel's precision, which decides an integer); a label other than NONE and
-  other than the vertex's part switches its silhouette residual off.
+  label at pixel (floor(u + 1/2), floor(v + 1/2)), decided in FP32 (the
+  kernel's precision: positions rounded to FP32, the projection's operations
+  each rounded once); a label other than NONE and other than the vertex's
+  part switches its silhouette residual off.
 """
 from __future__ import annotations
 
@@ -118,16 +119,25 @@ def part_mask(V32: np.ndarray, F: np.ndarray, f, cx, cy, W, H, vpart, radius=10,
     return dilate(label_image(out["zbuf"], F, vpart), radius, torso)
 
 
-def masked(P, u: np.ndarray, v: np.ndarray) -> np.ndarray:
-    """Vertices whose silhouette term is switched off at projections (u, v):
-    the label at the FP32-rounded pixel differs from the vertex's part."""
+def masked(P, V: np.ndarray) -> np.ndarray:
+    """Vertices at positions V (N,3) whose silhouette term is switched off:
+    the label at the pixel of their projection differs from their part.  The
+    pixel is decided in FP32 like the kernel: the positions rounded to FP32,
+    u = (f X) / Z + cx with every operation rounded once, then
+    floor(u + 1/2)."""
+    N = len(V)
     if getattr(P, "part_mask", None) is None:
-        return np.zeros(len(u), dtype=bool)
+        return np.zeros(N, dtype=bool)
     H, W = P.part_mask.shape
-    half = np.float32(0.5)
-    px = np.floor(np.asarray(u, dtype=np.float32) + half).astype(np.int64)
-    py = np.floor(np.asarray(v, dtype=np.float32) + half).astype(np.int64)
-    ok = (px >= 0) & (px < W) & (py >= 0) & (py < H)
-    lab = np.full(len(u), NONE, dtype=np.int64)
-    lab[ok] = P.part_mask[py[ok], px[ok]]
+    V32 = np.asarray(V, dtype=np.float32)
+    f, cx, cy, half = np.float32(P.f), np.float32(P.cx), np.float32(P.cy), np.float32(0.5)
+    ok = V32[:, 2] > np.float32(1e-3)
+    Z = np.where(ok, V32[:, 2], np.float32(1.0))
+    u = (f * V32[:, 0]) / Z + cx
+    v = (f * V32[:, 1]) / Z + cy
+    px = np.floor(u + half)
+    py = np.floor(v + half)
+    ok &= (px >= 0) & (px < W) & (py >= 0) & (py < H)
+    lab = np.full(N, NONE, dtype=np.int64)
+    lab[ok] = P.part_mask[py[ok].astype(np.int64), px[ok].astype(np.int64)]
     return (lab != NONE) & (lab != np.asarray(P.vpart, dtype=np.int64))

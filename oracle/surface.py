@@ -145,7 +145,7 @@ def residuals(P: SurfaceProblem, V: np.ndarray) -> dict:
     V = np.asarray(V, dtype=np.float64)
     u, w, valid, inimg = _nr.project(P, V)
     photo_on = _nr.prune(P, inimg & P.vis, u, w)
-    sil_on = inimg & P.inB & ~_parts.masked(P, u, w)
+    sil_on = inimg & P.inB & ~_parts.masked(P, V)
     photo = np.zeros((P.N, 3))
     sil = np.zeros(P.N)
     if photo_on.any():

@@ -263,6 +263,12 @@ extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int
         ctx->has_frame = false;
         ctx->has_vis = false;
         ctx->drop_graph();
+        ctx->hC.W = W;
+        ctx->hC.H = H;
+        if (ctx->hC.part_on) {
+            lc_status s = ctx->part_images();
+            if (s) return s;
+        }
     }
     ctx->hC.f = f;
     ctx->hC.cx = cx;
@@ -830,6 +836,8 @@ void lc_ctx::enqueue_nonrigid() {
     cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
     cudaMemsetAsync((char*)C.sc + offsetof(Scalars, gn_stop), 0, 2 * sizeof(int), st);
+    mark(LC_PH_VIS);
+    launch_part_mask(dC, C, st);
     mark(LC_PH_WARP);
     launch_warp(dC, C, st);
     mark(LC_PH_VIS);
@@ -1048,8 +1056,9 @@ extern "C" lc_status lc_compute_visibility(lc_ctx* ctx) {
     lc_status s;
     if ((s = ctx->check_solve_state("lc_compute_visibility"))) return s;
     cudaSetDevice(ctx->device);
-    launch_warp(ctx->dC, ctx->hC, ctx->stream);
     launch_vis_unfreeze(ctx->dC, ctx->stream);
+    launch_part_mask(ctx->dC, ctx->hC, ctx->stream);
+    launch_warp(ctx->dC, ctx->hC, ctx->stream);
     launch_visibility(ctx->dC, ctx->hC, ctx->stream);
     ctx->has_vis = true;
     ctx->has_lin = false;

@@ -287,6 +287,8 @@ static lc_status batch_check(lc_batch* b) {
         if (c->device != b->device) return b->fail(LC_ERR_ARG, "lc_batch: contexts on different devices");
         if (c->params.n_gn != b->n_gn || c->params.n_pcg != b->n_pcg)
             return b->fail(LC_ERR_ARG, "lc_batch: contexts differ in n_gn / n_pcg");
+        if (c->hC.part_on)
+            return b->fail(LC_ERR_STATE, "lc_batch: body-part masks are built by per-context solves only");
     }
     return LC_OK;
 }

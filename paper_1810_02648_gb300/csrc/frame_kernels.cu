@@ -466,4 +466,118 @@ void launch_visibility(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
 
 void launch_vis_unfreeze(const CapDesc* dC, cudaStream_t st) { vis_unfreeze_kernel<<<1, 1, 0, st>>>(dC); }
 
+// ---------------------------------------------------------------------------
+// Body-part mask of the silhouette term (Sec. 3.4): the rest geometry V^S is
+// projected and rasterised into the z-buffer (the same exact rasteriser),
+// each covered pixel takes the label of its front triangle (the label two
+// or three of its vertices share, else the first vertex's), then every part
+// grows into uncovered pixels within part_dilate pixels: the torso label if
+// a torso pixel is within reach, else the nearest label, the lower one on
+// equal squared distances.  The visibility pass of the current surface
+// rasterises into the z-buffer again afterwards.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVertTile) project_base_kernel(const CapDesc* __restrict__ caps) {
+    const CapDesc& C = caps[0];
+    const int i = blockIdx.x * kVertTile + threadIdx.x;
+    if (i >= C.N || C.sc->vis_frozen) return;
+    const float4 v = C.base[i];
+    const bool ok = valid_depth(v.z);
+    C.vw[i] = make_float4(v.x, v.y, v.z, ok ? 1.f : 0.f);
+    C.uv[i] = ok ? project_exact(C.f, C.cx, C.cy, v.x, v.y, v.z) : make_float2(0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) part_label_kernel(const CapDesc* __restrict__ caps) {
+    const CapDesc& C = caps[0];
+    if (C.sc->vis_frozen) return;
+    const size_t P = (size_t)C.W * C.H;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = C.zbuf[p];
+        uint8_t lab = 255;
+        if (key != ~0ULL) {
+            const int4 t = C.tris[(int)(unsigned)(key & 0xffffffffULL)];
+            const uint8_t a = C.vpart[t.x], b = C.vpart[t.y], c = C.vpart[t.z];
+            lab = (a == b || a == c) ? a : (b == c ? b : a);
+        }
+        C.part_raw[p] = lab;
+    }
+}
+
+constexpr int kPartTile = 32;
+constexpr int kPartMaxDilate = 32;
+
+// one CTA per 32 x 32 pixels, the labels of the tile and its halo of
+// part_dilate pixels in shared memory
+__global__ void __launch_bounds__(kPartTile * kPartTile) part_dilate_kernel(const CapDesc* __restrict__ caps) {
+    extern __shared__ uint8_t s_lab[];
+    const CapDesc& C = caps[0];
+    if (C.sc->vis_frozen) return;
+    const int R = C.part_dilate, S = kPartTile + 2 * R;
+    const int bx = blockIdx.x * kPartTile - R, by = blockIdx.y * kPartTile - R;
+    int any = 0;
+    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
+        const int x = bx + q % S, y = by + q / S;
+        uint8_t l = 255;
+        if (x >= 0 && x < C.W && y >= 0 && y < C.H) l = C.part_raw[(size_t)y * C.W + x];
+        s_lab[q] = l;
+        any |= l != 255;
+    }
+    any = __syncthreads_or(any);
+    const int tx = threadIdx.x % kPartTile, ty = threadIdx.x / kPartTile;
+    const int x = blockIdx.x * kPartTile + tx, y = blockIdx.y * kPartTile + ty;
+    if (x >= C.W || y >= C.H) return;
+    int lab = s_lab[(ty + R) * S + tx + R];
+    if (lab == 255 && any) {
+        int best_d = 1 << 30, best_l = 255;
+        bool torso = false;
+        for (int dy = -R; dy <= R; ++dy) {
+            const uint8_t* row = s_lab + (ty + R + dy) * S + tx + R;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int d2 = dy * dy + dx * dx;
+                const int l = row[dx];
+                if (d2 > R * R || l == 255) continue;
+                torso |= l == C.torso_part;
+                if (d2 < best_d || (d2 == best_d && l < best_l)) {
+                    best_d = d2;
+                    best_l = l;
+                }
+            }
+        }
+        lab = torso ? C.torso_part : best_l;
+    }
+    C.part_mask[(size_t)y * C.W + x] = (uint8_t)lab;
+}
+
+void launch_part_mask(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
+    if (!hC.part_on) return;
+    const Tiles T = single_tiles(hC);
+    project_base_kernel<<<(hC.N + kVertTile - 1) / kVertTile, kVertTile, 0, st>>>(dC);
+    const size_t P = (size_t)hC.W * hC.H;
+    const int blocks = (int)std::min<size_t>((P + 255) / 256, 2048);
+    vis_clear_kernel<<<blocks, 256, 0, st>>>(dC);
+    if (T.tri) raster_kernel<<<T.tri, kRasterThreads, 0, st>>>(dC, T.tri_items);
+    part_label_kernel<<<blocks, 256, 0, st>>>(dC);
+    const int S = kPartTile + 2 * hC.part_dilate;
+    const dim3 grd((hC.W + kPartTile - 1) / kPartTile, (hC.H + kPartTile - 1) / kPartTile);
+    part_dilate_kernel<<<grd, kPartTile * kPartTile, S * S, st>>>(dC);
+}
+
+__global__ void vertex_parts_kernel(const int4* __restrict__ skin_idx, const float4* __restrict__ skin_w,
+                                    const int* __restrict__ bone_part, int N, uint8_t* __restrict__ vpart) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int4 b = skin_idx[i];
+    const float4 w = skin_w[i];
+    int best = b.x;
+    float bw = w.x;
+    if (w.y > bw) { best = b.y; bw = w.y; }
+    if (w.z > bw) { best = b.z; bw = w.z; }
+    if (w.w > bw) { best = b.w; bw = w.w; }
+    vpart[i] = (uint8_t)bone_part[best];
+}
+
+void launch_vertex_parts(const int4* skin_idx, const float4* skin_w, const int* bone_part, int N, uint8_t* vpart,
+                         cudaStream_t st) {
+    vertex_parts_kernel<<<(N + 255) / 256, 256, 0, st>>>(skin_idx, skin_w, bone_part, N, vpart);
+}
+
 }  // namespace lc

@@ -39,6 +39,12 @@ struct lc_ctx {
     float4* pyr_tmp = nullptr;    // row-blur scratch of the pyramid (W x H)
     lc_status build_pyramid();    // the levels of params.pyr_levels from the current frame
     void pyr_release();
+    // body-part mask of the silhouette term (lc_set_body_parts)
+    uint8_t* vpart_buf = nullptr;      // N
+    uint8_t* part_raw_buf = nullptr;   // W x H
+    uint8_t* part_mask_buf = nullptr;  // W x H
+    int* bone_part_buf = nullptr;      // J
+    lc_status part_images();           // (re)allocate the W x H label images of an active mask
     // scratch node vectors
     float4* tmp_vec = nullptr;
     float4* tmp_vec2 = nullptr;

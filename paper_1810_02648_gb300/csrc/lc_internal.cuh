@@ -29,6 +29,7 @@ constexpr uint32_t LC_ONSIL_BIT = LC_FLAG_ONSIL;
 constexpr uint32_t LC_INB_BIT = LC_FLAG_INB;
 constexpr uint32_t LC_BNEG_BIT = LC_FLAG_BNEG;
 constexpr uint32_t LC_PRUNED_BIT = LC_FLAG_PRUNED;
+constexpr uint32_t LC_MASKED_BIT = LC_FLAG_MASKED;
 
 // Per-capture reduction scalars (FP64; PCG dots and energies).
 struct Scalars {
@@ -89,6 +90,11 @@ struct CapDesc {
     const float4* lvl[3];
     int lvl_W[3], lvl_H[3];
     int pyr_levels;
+    // body-part mask of the silhouette term (Sec. 3.4); part_on = 0: off
+    const uint8_t* vpart;    // N part of each vertex
+    uint8_t* part_raw;       // H*W label of the front triangle of V^S (255: none)
+    uint8_t* part_mask;      // H*W dilated labels
+    int part_on, torso_part, part_dilate;
     const uint8_t* mask;     // H*W
     // per-frame decisions
     unsigned long long* zbuf;  // H*W
@@ -371,6 +377,12 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
 // exact silhouette distance transform of the packed mask into img's 4th
 // channel (g: W x H int scratch; W <= 16384, g of a row in shared memory)
 void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st);
+// the body-part mask of the frame (projection and raster of V^S, labels,
+// dilation); nothing when the capture's mask is off or its decisions frozen
+void launch_part_mask(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
+// vertex part = bone_part of the heaviest of the 4 skinning slots
+void launch_vertex_parts(const int4* skin_idx, const float4* skin_w, const int* bone_part, int N, uint8_t* vpart,
+                         cudaStream_t st);
 // level j of the photometric pyramid from the packed frame (rgb of img):
 // box mean over d x d blocks (into out when d > 1), then the separable
 // Gaussian `taps` (2r+1 of them), rows into tmp, columns into out (Wd x Hd)

@@ -77,6 +77,11 @@ void lc_ctx::pose_release() {
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
+    // the body-part mask follows the skinning weights of the skeleton
+    if (hC.part_on) {
+        hC.part_on = 0;
+        drop_graph();
+    }
 }
 
 static lc_status pose_sync(lc_ctx* ctx) {
@@ -513,6 +518,83 @@ extern "C" lc_status lc_eval_pose(lc_ctx* ctx, float* V_skinned, double* A, doub
         std::vector<double> hist(2 * (LC_MAX_GN + 1));
         if ((s = ctx->copy_to_host(hist.data(), S.h.hist, sizeof(double) * hist.size()))) return s;
         if ((s = ctx->deliver(energy, &hist[2 * LC_MAX_GN], sizeof(double)))) return s;
+    }
+    return LC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// body-part mask of the silhouette term (Sec. 3.4)
+// ---------------------------------------------------------------------------
+lc_status lc_ctx::part_images() {
+    release(part_raw_buf);
+    release(part_mask_buf);
+    const size_t P = (size_t)hC.W * hC.H;
+    part_raw_buf = (uint8_t*)alloc(P);
+    part_mask_buf = (uint8_t*)alloc(P);
+    if (!part_raw_buf || !part_mask_buf) return LC_ERR_OOM;
+    // nothing labelled until the first frame decisions
+    if (lc_status s = cuda(cudaMemsetAsync(part_mask_buf, 0xff, P, stream), "part mask")) return s;
+    if (lc_status s = cuda(cudaMemsetAsync(part_raw_buf, 0xff, P, stream), "part mask")) return s;
+    hC.part_raw = part_raw_buf;
+    hC.part_mask = part_mask_buf;
+    return LC_OK;
+}
+
+extern "C" lc_status lc_set_body_parts(lc_ctx* ctx, const int32_t* bone_part, int torso_part, int dilate_px) {
+    if (!ctx) return LC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!bone_part) {
+        if (ctx->hC.part_on) {
+            ctx->hC.part_on = 0;
+            ctx->drop_graph();
+        }
+        return ctx->sync_desc();
+    }
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_set_body_parts: no skeleton");
+    if (!ctx->has_camera) return ctx->fail(LC_ERR_STATE, "lc_set_body_parts: no camera");
+    if (torso_part < -1 || torso_part > 254 || dilate_px < 0 || dilate_px > 32)
+        return ctx->fail(LC_ERR_ARG, "lc_set_body_parts: torso_part -1..254, dilate_px 0..32");
+    const int J = ctx->pose->h.J, N = ctx->hC.N;
+    std::vector<int32_t> bp(J);
+    lc_status s;
+    if ((s = ctx->fetch(bp.data(), bone_part, sizeof(int32_t) * J))) return s;
+    for (int j = 0; j < J; ++j)
+        if (bp[j] < 0 || bp[j] > 254) return ctx->fail(LC_ERR_ARG, "lc_set_body_parts: part labels are 0..254");
+    ctx->release(ctx->bone_part_buf);
+    ctx->release(ctx->vpart_buf);
+    ctx->bone_part_buf = (int*)ctx->alloc(sizeof(int) * J);
+    ctx->vpart_buf = (uint8_t*)ctx->alloc((size_t)N);
+    if (!ctx->bone_part_buf || !ctx->vpart_buf) return LC_ERR_OOM;
+    if ((s = ctx->part_images())) return s;
+    if ((s = ctx->cuda(cudaMemcpyAsync(ctx->bone_part_buf, bp.data(), sizeof(int32_t) * J, cudaMemcpyHostToDevice,
+                                       ctx->stream), "body parts")))
+        return s;
+    launch_vertex_parts(ctx->pose->h.skin_idx, ctx->pose->h.skin_w, ctx->bone_part_buf, N, ctx->vpart_buf, ctx->stream);
+    if ((s = ctx->cuda(cudaGetLastError(), "body parts"))) return s;
+    CapDesc& C = ctx->hC;
+    if (!C.part_on) ctx->drop_graph();
+    C.vpart = ctx->vpart_buf;
+    C.part_on = 1;
+    C.torso_part = torso_part;
+    C.part_dilate = dilate_px;
+    return ctx->sync_desc();
+}
+
+extern "C" lc_status lc_read_part_mask(lc_ctx* ctx, uint8_t* mask, uint8_t* vertex_part) {
+    if (!ctx) return LC_ERR_ARG;
+    const CapDesc& C = ctx->hC;
+    if (!C.part_on) return ctx->fail(LC_ERR_STATE, "lc_read_part_mask: no body-part mask");
+    cudaSetDevice(ctx->device);
+    lc_status s;
+    if (mask) {
+        std::vector<uint8_t> m((size_t)C.W * C.H);
+        if ((s = ctx->copy_to_host(m.data(), C.part_mask, m.size()))) return s;
+        if ((s = ctx->deliver(mask, m.data(), m.size()))) return s;
+    }
+    if (vertex_part) {
+        std::vector<uint8_t> v((size_t)C.N);
+        if ((s = ctx->copy_to_host(v.data(), C.vpart, v.size()))) return s;
+        if ((s = ctx->deliver(vertex_part, v.data(), v.size()))) return s;
     }
     return LC_OK;
 }

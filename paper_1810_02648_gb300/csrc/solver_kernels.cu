@@ -109,12 +109,20 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
         const float2 uv = C.uv[i];
         const bool ok = v.w > 0.f && in_image(uv, C.W, C.H);
         bool ph = ok && (fl & LC_VIS_BIT);
-        const bool si = ok && (fl & LC_INB_BIT);
+        bool si = ok && (fl & LC_INB_BIT);
         if (update_b && si) {
             // b_i follows the current surface; the contour set stays the frame's
             const uint32_t nf = direction_neg(C, i) ? (fl | LC_BNEG_BIT) : (fl & ~LC_BNEG_BIT);
             if (nf != fl) C.flags[i] = nf;
             fl = nf;
+        }
+        bool masked = false;
+        if (si && C.part_on) {
+            // body-part mask: the silhouette term is off on another part's region
+            const int px = min((int)floorf(uv.x + 0.5f), C.W - 1), py = min((int)floorf(uv.y + 0.5f), C.H - 1);
+            const int lab = C.part_mask[(size_t)py * C.W + px];
+            masked = lab != 255 && lab != (int)C.vpart[i];
+            si = !masked;
         }
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
@@ -171,9 +179,10 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
             }
         }
         {
-            // the bit always reflects this linearisation (cleared when the kernel is off)
+            // the bits always reflect this linearisation (cleared when sigma_c / the mask is off)
             const bool pruned = C.sigma_c > 0.f && ok && (fl & LC_VIS_BIT) && !ph;
-            const uint32_t nf = pruned ? (fl | LC_PRUNED_BIT) : (fl & ~LC_PRUNED_BIT);
+            uint32_t nf = pruned ? (fl | LC_PRUNED_BIT) : (fl & ~LC_PRUNED_BIT);
+            nf = masked ? (nf | LC_MASKED_BIT) : (nf & ~LC_MASKED_BIT);
             if (nf != fl) C.flags[i] = nf;
         }
         C.res[i] = res;

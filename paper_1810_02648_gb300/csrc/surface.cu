@@ -623,6 +623,8 @@ void lc_ctx::enqueue_surface() {
     cudaMemsetAsync(C.hist, 0, sizeof(double) * 2 * (LC_MAX_GN + 1), st);
     cudaMemsetAsync(C.hist_iters, 0, sizeof(int) * (LC_MAX_GN + 2), st);
     cudaMemsetAsync((char*)C.sc + offsetof(Scalars, gn_stop), 0, 2 * sizeof(int), st);
+    mark(LC_PH_VIS);
+    launch_part_mask(dC, C, st);
     mark(LC_PH_WARP);
     launch_surface_project(dC, C, st);
     mark(LC_PH_VIS);
@@ -817,6 +819,7 @@ extern "C" lc_status lc_surface_visibility(lc_ctx* ctx) {
     lc_status s;
     if ((s = ctx->check_surface_state("lc_surface_visibility"))) return s;
     cudaSetDevice(ctx->device);
+    launch_part_mask(ctx->dC, ctx->hC, ctx->stream);
     launch_surface_project(ctx->dC, ctx->hC, ctx->stream);
     launch_visibility(ctx->dC, ctx->hC, ctx->stream);
     if ((s = ctx->cuda(cudaStreamSynchronize(ctx->stream), "lc_surface_visibility"))) return s;

@@ -17,7 +17,7 @@ from . import build as _build
 
 LC_OK, LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_NUMERIC, LC_ERR_TIMEOUT, LC_ERR_OOM = 0, -1, -2, -3, -4, -5, -6
 LC_MAX_GN = 64
-FLAG_VISIBLE, FLAG_ONSIL, FLAG_INB, FLAG_BNEG, FLAG_PRUNED = 1, 2, 4, 8, 16
+FLAG_VISIBLE, FLAG_ONSIL, FLAG_INB, FLAG_BNEG, FLAG_PRUNED, FLAG_MASKED = 1, 2, 4, 8, 16, 32
 
 
 class lc_params(ctypes.Structure):
@@ -103,6 +103,8 @@ _SIGS = {
     "lc_read_profile": [_P, _P, _P],
     "lc_set_rest_geometry": [_P, _P],
     "lc_read_frame": [_P, _P, _P],
+    "lc_set_body_parts": [_P, _P, ctypes.c_int, ctypes.c_int],
+    "lc_read_part_mask": [_P, _P, _P],
     "lc_read_pyramid_level": [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "lc_set_pose_priors": [_P, _P, _P, _P],
     "lc_pose_advance": [_P],
@@ -288,6 +290,18 @@ class Context:
         mask = np.zeros((self.H, self.W), np.uint8)
         self._check(self._lib.lc_read_frame(self.h, _ptr(dt), _ptr(mask)))
         return dt, mask
+
+    def set_body_parts(self, bone_part, torso_part: int = 0, dilate_px: int = 10):
+        """Body-part mask of the silhouette term (None: off)."""
+        bp = _arr(bone_part, np.int32)
+        self._check(self._lib.lc_set_body_parts(self.h, _ptr(bp), int(torso_part), int(dilate_px)))
+
+    def read_part_mask(self):
+        """(H x W uint8 labels, 255 = none; N uint8 vertex parts)."""
+        m = np.zeros((self.H, self.W), np.uint8)
+        v = np.zeros(self.N, np.uint8)
+        self._check(self._lib.lc_read_part_mask(self.h, _ptr(m), _ptr(v)))
+        return m, v
 
     def read_pyramid_level(self, j: int):
         """Level j (0 coarsest) of the photometric pyramid, (Hj, Wj, 3) float32."""

@@ -5,6 +5,7 @@ import os
 import numpy as np
 
 from oracle import nonrigid as onr
+from oracle import parts as oparts
 from oracle import visibility as ovis
 
 REPORT = {}
@@ -79,7 +80,7 @@ def oracle_vertex_blocks(P, v32, uv32, pruned=None):
     ph = ok & P.vis
     if pruned is not None:
         ph = ph & ~pruned
-    si = ok & P.inB
+    si = ok & P.inB & ~oparts.masked(P, v32)
     gxD, gyD = P.grads()[1]
     Dp = onr.dproj(P, v)
     N = len(v)
@@ -228,7 +229,7 @@ def ragged_scene(rings, segs, n_nodes, K, side=96, shift=0.0, seed=5):
 
 
 def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n_gn=None, n_pcg=None,
-                          n_runs=3, sigma_c=0.0, pyr_levels=0):
+                          n_runs=3, sigma_c=0.0, pyr_levels=0, part_mask=None, vpart=None):
     """``fp32_rounding_band`` for the per-vertex surface stage: the spread of
     the oracle's result when its Jacobian entries, residuals, CG vectors and
     products and the vertex positions after every update are rounded to FP32
@@ -237,7 +238,7 @@ def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n
     from oracle import pyramid as opyr
     from oracle import surface as osf
     kw = dict(base32=base32, V0=V0, n_gn=n_gn, n_pcg=n_pcg, prev1=prev1, prev2=prev2, sigma_c=sigma_c,
-              pyr_levels=pyr_levels)
+              pyr_levels=pyr_levels, part_mask=part_mask, vpart=vpart)
     ref = osf.solve_scene(scene, **kw)
     orig_pcg, orig_lin, orig_gn = onr.pcg, osf.linearise, osf.gauss_newton
     dE, dV = 0.0, 0.0

@@ -95,10 +95,12 @@ def test_torso_precedence_in_a_gap():
 
 def test_lookup_rounding():
     class _P:
+        f, cx, cy = 1.0, 0.0, 0.0
         part_mask = np.array([[0, 1, 2, 3, 4, 5]], np.uint8)
         vpart = np.array([2, 2, 2, 2], np.uint8)
-    u = np.array([2.5, np.nextafter(np.float32(2.5), np.float32(0)), 1.49, 5.0])
-    m = op.masked(_P, u, np.zeros(4))
+    X = np.array([2.5, np.nextafter(np.float32(2.5), np.float32(0)), 1.49, 5.0])
+    V = np.stack([X, np.zeros(4), np.ones(4)], 1)
+    m = op.masked(_P, V)
     # 2.5 -> pixel 3 (label 3: masked); just below 2.5 -> pixel 2 (own part)
     assert m.tolist() == [True, False, True, True]
 
@@ -114,7 +116,7 @@ def test_energy_drops_exactly_the_masked_rows(tiny_problem):
     Q.part_mask[:, : P.W // 2] = 1          # left half belongs to another part
     Q.vpart = np.zeros(len(P.base), np.uint8)
     vr = nr.vertex_residuals(Q, R, t)
-    m = op.masked(Q, vr0["u"], vr0["w"])
+    m = op.masked(Q, vr0["v"])
     assert (m & vr0["sil_on"]).sum() > 0 and (~m & vr0["sil_on"]).sum() > 0
     assert np.array_equal(vr["sil_on"], vr0["sil_on"] & ~m)
     e0, e1 = nr.energy(P, R, t), nr.energy(Q, R, t)
