@@ -54,7 +54,28 @@ def parse():
     ap.add_argument("--pcg-mode", type=int, default=-1, help="batch PCG strategy (-1: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # options of the per-frame path (Sec. 3.2-3.4), off in the default line
+    ap.add_argument("--pyramid", type=int, default=0, help="photometric pyramid levels (0: raw image)")
+    ap.add_argument("--sigma-c", type=float, default=0.0, help="robust colour kernel threshold (0: off)")
+    ap.add_argument("--body-parts", action="store_true", help="body-part mask of the silhouette term")
+    ap.add_argument("--frame-prep", action="store_true",
+                    help="every step first prepares the frame from device-resident RGB, mask and joints "
+                         "(packing, distance transform of the silhouette on the device, pyramid levels)")
     return ap.parse_args()
+
+
+def path_options(a):
+    """The non-default options of the per-frame path, as config keys."""
+    opt = {}
+    if a.pyramid:
+        opt["pyramid_levels"] = a.pyramid
+    if a.sigma_c:
+        opt["sigma_c"] = a.sigma_c
+    if a.body_parts:
+        opt["body_parts"] = "6 parts, 10 px dilation, torso precedence"
+    if a.frame_prep:
+        opt["frame_prep"] = "in the step: frame packing + device distance transform (+ pyramid levels)"
+    return opt
 
 
 def is_surface(workload):
@@ -302,7 +323,8 @@ def run_ours(a):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     cpu_base = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    opts = path_options(a)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and not opts:
         # spawn the oracle pool before the first GPU call
         cpu_base = cpu_baseline(a.workload, a.cpu_seconds)
 
@@ -314,13 +336,32 @@ def run_ours(a):
     ctx = Context(local, stream=stream)
     setup_scene(ctx, scene)
     has_pose = scene.skeleton is not None
+    if a.pyramid:
+        ctx.set_params(pyr_levels=a.pyramid)
+    if a.sigma_c:
+        ctx.set_params(sigma_c=a.sigma_c)
+    if a.body_parts:
+        if not has_pose:
+            raise SystemExit("--body-parts needs a capture with a skeleton")
+        ctx.set_body_parts(scene.skeleton["bone_part"], scene.skeleton["torso_part"], 10)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    frame_dev = None
+    if a.frame_prep:
+        frame_dev = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in
+                     (scene.rgb.astype(np.float32), scene.mask.astype(np.uint8))]
+        if has_pose:
+            frame_dev += [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+                          for x in (scene.joints2d, scene.joints3d)]
+        else:
+            frame_dev += [None, None]
 
     def step():
         # every frame starts from the same pose (device-side reset, no host
         # round trip); the graph stage from the identity deformation, the
         # surface stage from the skinned mesh plus the warped displacement of
         # the previous frame, which it then records with its history
+        if frame_dev is not None:
+            ctx.upload_frame(frame_dev[0], None, frame_dev[1], frame_dev[2], frame_dev[3])
         if has_pose:
             ctx.reset_pose()
             ctx.solve_pose(stats=False)
@@ -425,8 +466,8 @@ def run_ours(a):
     n_e2e = max(10, a.steps // 2)
 
     def e2e_step():
-        ctx._check(lib.lc_upload_frame(ctx.h, _ptr(rgb), _ptr(dtm), _ptr(msk), _ptr(j2) if has_pose else None,
-                                       _ptr(j3) if has_pose else None))
+        ctx._check(lib.lc_upload_frame(ctx.h, _ptr(rgb), None if a.frame_prep else _ptr(dtm), _ptr(msk),
+                                       _ptr(j2) if has_pose else None, _ptr(j3) if has_pose else None))
         if has_pose:
             ctx._check(lib.lc_reset_pose(ctx.h))
             ctx._check(lib.lc_solve_pose(ctx.h, None))
@@ -451,7 +492,8 @@ def run_ours(a):
         e2e_step()
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    h2d = rgb.numel() * 4 + dtm.numel() * 4 + msk.numel() + ((j2.numel() + j3.numel()) * 4 if has_pose else 0)
+    h2d = (rgb.numel() * 4 + (0 if a.frame_prep else dtm.numel() * 4) + msk.numel()
+           + ((j2.numel() + j3.numel()) * 4 if has_pose else 0))
     d2h = ((0 if surface else outR.numel() + outT.numel()) + outV.numel() + (outP.numel() if has_pose else 0)) * 4
 
     if rank != 0:
@@ -462,11 +504,15 @@ def run_ours(a):
     phases = {k: {"ms_per_frame": v[0] / n_prof, "segments_per_frame": v[1] / n_prof}
               for k, v in prof.items() if v[1]}
     extra_kernels = (5 if has_pose else 3) if surface else 1
+    if a.frame_prep:
+        # packing, the two distance-transform passes, per pyramid level a box
+        # mean (factor > 1) and two blur passes
+        extra_kernels += 3 + sum((1 if j < 2 else 0) + 2 for j in range(3 - a.pyramid, 3))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(scene, surface),
+        "config": {**workload_config(scene, surface), **opts},
         "clocks": clk.summary(),
         "e2e": {"value": world * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

@@ -148,12 +148,23 @@ def pcg32(A, b, n, r32):
     return x, info
 
 
+def _project32(project, r32):
+    """The projection with its pixel coordinates rounded like an FP32
+    execution's (the sampling position of every data term)."""
+    def proj(P, v):
+        u, w, valid, _ = project(P, v)
+        u, w = r32(u), r32(w)
+        inimg = valid & (u >= 0) & (u <= P.W - 1) & (w >= 0) & (w <= P.H - 1)
+        return u, w, valid, inimg
+    return proj
+
+
 def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=None, sigma_c=0.0, pyr_levels=0):
     """Spread of the oracle's end-to-end result under FP32 rounding, with a
     random tie-break perturbation of one unit roundoff (seeded), of what an
     FP32 execution rounds: the node parameters after every update, the warped
-    vertices, the residuals and Jacobian entries, and the CG vectors and
-    matrix-vector products.  This measures how far any FP32 execution of the
+    vertices, their pixel coordinates, the residuals and Jacobian entries, and
+    the CG vectors and matrix-vector products.  This measures how far any FP32 execution of the
     same algorithm may land from the FP64 result: CG amplifies rounding along
     the system's ill-conditioned (depth) directions, and a projection within
     rounding of a pixel boundary takes the other cell of the piecewise
@@ -161,7 +172,7 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
     ref = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c,
                           pyr_levels=pyr_levels)
-    orig = (onr.pcg, onr.linearise, onr.apply_update, onr.warp)
+    orig = (onr.pcg, onr.linearise, onr.apply_update, onr.warp, onr.project)
     dE, dV = 0.0, 0.0
     for seed in range(n_runs):
         r32 = _r32(np.random.default_rng(1000 + seed))
@@ -185,11 +196,12 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
             return np.where(v != P.base, r32(v), v)
 
         onr.warp = warp32
+        onr.project = _project32(orig[4], r32)
         try:
             o = onr.solve_scene(scene, graph=graph, base32=base32, n_gn=n_gn, n_pcg=n_pcg, sigma_c=sigma_c,
                                 pyr_levels=pyr_levels)
         finally:
-            onr.pcg, onr.linearise, onr.apply_update, onr.warp = orig
+            onr.pcg, onr.linearise, onr.apply_update, onr.warp, onr.project = orig
         dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
         dV = max(dV, float(np.abs(o["v"] - ref["v"]).max()))
     return ref, dE, dV
@@ -232,15 +244,16 @@ def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n
                           n_runs=3, sigma_c=0.0, pyr_levels=0, part_mask=None, vpart=None):
     """``fp32_rounding_band`` for the per-vertex surface stage: the spread of
     the oracle's result when its Jacobian entries, residuals, CG vectors and
-    products and the vertex positions after every update are rounded to FP32
-    with a random tie-break of one unit roundoff.
+    products, the vertex positions after every update and their pixel
+    coordinates are rounded to FP32 with a random tie-break of one unit
+    roundoff.
     Returns (oracle result dict, max |E_k - E_ref|, max |V_k - V_ref|)."""
     from oracle import pyramid as opyr
     from oracle import surface as osf
     kw = dict(base32=base32, V0=V0, n_gn=n_gn, n_pcg=n_pcg, prev1=prev1, prev2=prev2, sigma_c=sigma_c,
               pyr_levels=pyr_levels, part_mask=part_mask, vpart=vpart)
     ref = osf.solve_scene(scene, **kw)
-    orig_pcg, orig_lin, orig_gn = onr.pcg, osf.linearise, osf.gauss_newton
+    orig_pcg, orig_lin, orig_gn, orig_proj = onr.pcg, osf.linearise, osf.gauss_newton, onr.project
     dE, dV = 0.0, 0.0
     for seed in range(n_runs):
         r32 = _r32(np.random.default_rng(3000 + seed))
@@ -267,10 +280,11 @@ def surface_rounding_band(scene, base32=None, V0=None, prev1=None, prev2=None, n
         onr.pcg = lambda A, b, n: pcg32(A, b, n, r32)
         osf.linearise = lin32
         osf.gauss_newton = gn32
+        onr.project = _project32(orig_proj, r32)
         try:
             o = osf.solve_scene(scene, **kw)
         finally:
-            onr.pcg, osf.linearise, osf.gauss_newton = orig_pcg, orig_lin, orig_gn
+            onr.pcg, osf.linearise, osf.gauss_newton, onr.project = orig_pcg, orig_lin, orig_gn, orig_proj
         dE = max(dE, abs(o["e1"]["total"] - ref["e1"]["total"]))
         dV = max(dV, float(np.abs(o["V"] - ref["V"]).max()))
     return ref, dE, dV

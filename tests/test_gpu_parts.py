@@ -158,7 +158,9 @@ def test_surface_end_to_end_masked(body, body_parts):
     ctx.set_surface(V0)
     stats = ctx.solve_surface()
     Vg, flags = ctx.read_surface(flags=True)
-    ref, band_E, band_V = surface_rounding_band(body, base32=VS, V0=V0, part_mask=mask_posed, vpart=vp)
+    # the body's surface solve spreads by ~1e-4 of its energy under FP32
+    # rounding; 8 rounded runs estimate that band
+    ref, band_E, band_V = surface_rounding_band(body, base32=VS, V0=V0, part_mask=mask_posed, vpart=vp, n_runs=8)
     e_gpu, e_ref = stats["e_total"], ref["e1"]["total"]
     diag = np.linalg.norm(body.V.max(0) - body.V.min(0))
     dv = float(np.abs(Vg.astype(np.float64) - ref["V"]).max())
