@@ -653,10 +653,11 @@ extern "C" lc_status lc_upload_frame(lc_ctx* ctx, const float* rgb, const float*
     if (!dt) {
         // the distance transform of the silhouette on the device (scratch on first use)
         if (!ctx->edt_g) {
-            ctx->edt_g = (int*)ctx->alloc(sizeof(int) * P);
+            // column distances (int per pixel), then the contour flags (a byte per pixel)
+            ctx->edt_g = (int*)ctx->alloc((sizeof(int) + 1) * P);
             if (!ctx->edt_g) return LC_ERR_OOM;
         }
-        launch_edt(C.mask, ctx->edt_g, (float4*)C.img, C.W, C.H, st);
+        launch_edt(C.mask, (uint8_t*)(ctx->edt_g + P), ctx->edt_g, (float4*)C.img, C.W, C.H, st);
         if ((s = ctx->cuda(cudaGetLastError(), "distance transform"))) return s;
     }
     if (ctx->params.pyr_levels > 0) {

@@ -42,37 +42,44 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
 // 4-neighbour in the background or on the image border) in integers, by the
 // separable decomposition d^2(x, y) = min_i (x - i)^2 + g(i, y)^2 with
 // g(i, y) the distance along column i to its nearest contour pixel:
-//   phase 1, a CTA per 32 columns, 32 row chunks each: every thread finds the
+//   phase 0, one thread per pixel: the contour flags;
+//   phase 1, a CTA per 8 columns, 128 row chunks each: every thread finds the
 //     last / first contour row of its chunk, the chunks are combined through
-//     shared memory (a max / min scan over 32 values), then every thread
-//     writes g for its chunk;
-//   phase 2, a CTA per row with g of the row in shared memory: every pixel
-//     searches columns x -+ k outward while k^2 is below its best d^2 (the
-//     minimum cannot lie further out).
+//     shared memory, then every thread writes g for its chunk;
+//   phase 2, a CTA per row with g^2 of the row and its minimum over every 32
+//     columns in shared memory: every pixel scans its own 32-column block,
+//     then the blocks outward, skipping a block when its nearest column's
+//     distance^2 plus the block's minimum g^2 cannot beat the best so far,
+//     and stopping where the distance^2 alone cannot.
 // I_DT = sqrt(d^2) rounded once to FP32, written into the frame's fourth
 // channel; 0 everywhere when the silhouette has no contour.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool is_contour(const uint8_t* m, int W, int H, int x, int y) {
-    if (!m[(size_t)y * W + x]) return false;
-    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) return true;
-    return !m[(size_t)y * W + x - 1] || !m[(size_t)y * W + x + 1] || !m[(size_t)(y - 1) * W + x] ||
-           !m[(size_t)(y + 1) * W + x];
+__global__ void __launch_bounds__(256) edt_contour_kernel(const uint8_t* __restrict__ m, int W, int H,
+                                                          uint8_t* __restrict__ c) {
+    const size_t P = (size_t)W * H;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+        bool on = m[p] != 0;
+        if (on && x > 0 && y > 0 && x < W - 1 && y < H - 1)
+            on = !m[p - 1] || !m[p + 1] || !m[p - W] || !m[p + W];
+        c[p] = on ? 1 : 0;
+    }
 }
 
-constexpr int kEdtChunks = 32;
+constexpr int kEdtCols = 8, kEdtChunks = 128;
 
-__global__ void __launch_bounds__(32 * kEdtChunks) edt_columns_kernel(const uint8_t* __restrict__ mask,
-                                                                       int* __restrict__ g, int W, int H) {
-    __shared__ int s_last[kEdtChunks][33], s_first[kEdtChunks][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + tx;
+__global__ void __launch_bounds__(kEdtCols * kEdtChunks) edt_columns_kernel(const uint8_t* __restrict__ c,
+                                                                             int* __restrict__ g, int W, int H) {
+    __shared__ int s_last[kEdtChunks][kEdtCols], s_first[kEdtChunks][kEdtCols];
+    const int tx = threadIdx.x % kEdtCols, ty = threadIdx.x / kEdtCols;
+    const int x = blockIdx.x * kEdtCols + tx;
     const int L = (H + kEdtChunks - 1) / kEdtChunks;
-    const int y0 = ty * L, y1 = min(H, y0 + L);
+    const int y0 = min(H, ty * L), y1 = min(H, y0 + L);
     const int NONE_LO = -(W + H) - 1, NONE_HI = 2 * (W + H) + 1;
     int last = NONE_LO, first = NONE_HI;
     if (x < W)
         for (int y = y0; y < y1; ++y)
-            if (is_contour(mask, W, H, x, y)) {
+            if (c[(size_t)y * W + x]) {
                 if (first == NONE_HI) first = y;
                 last = y;
             }
@@ -81,14 +88,14 @@ __global__ void __launch_bounds__(32 * kEdtChunks) edt_columns_kernel(const uint
     __syncthreads();
     // the nearest contour rows above this chunk and below it
     int above = NONE_LO, below = NONE_HI;
-    for (int c = 0; c < ty; ++c) above = max(above, s_last[c][tx]);
-    for (int c = kEdtChunks - 1; c > ty; --c) below = min(below, s_first[c][tx]);
+    for (int k = 0; k < ty; ++k) above = max(above, s_last[k][tx]);
+    for (int k = kEdtChunks - 1; k > ty; --k) below = min(below, s_first[k][tx]);
     if (x >= W) return;
     const int inf = W + H;
     // down the chunk with the last contour row so far, then up it
     int lastc = above;
     for (int y = y0; y < y1; ++y) {
-        if (is_contour(mask, W, H, x, y)) lastc = y;
+        if (c[(size_t)y * W + x]) lastc = y;
         g[(size_t)y * W + x] = min(inf, y - lastc);
     }
     int nextc = below;
@@ -100,36 +107,69 @@ __global__ void __launch_bounds__(32 * kEdtChunks) edt_columns_kernel(const uint
     }
 }
 
+constexpr int kEdtBlock = 32;
+
+__device__ __forceinline__ int edt_scan_block(const int* s_g2, int W, int x, int b, int best) {
+    const int i0 = b * kEdtBlock, i1 = min(W, i0 + kEdtBlock);
+    for (int i = i0; i < i1; ++i) {
+        const int d = x - i;
+        best = min(best, d * d + s_g2[i]);
+    }
+    return best;
+}
+
 __global__ void __launch_bounds__(256) edt_rows_kernel(const int* __restrict__ g, float4* __restrict__ img, int W,
                                                        int H) {
-    extern __shared__ int s_g[];   // g of this row
+    extern __shared__ int s_g2[];   // g^2 of this row, then the block minima
+    const int nb = (W + kEdtBlock - 1) / kEdtBlock;
+    int* s_bmin = s_g2 + W;
     const int y = blockIdx.x;
     const int* gy = g + (size_t)y * W;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) s_g[x] = gy[x];
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const int v = gy[x];
+        s_g2[x] = v * v;   // (W + H)^2 when the column has no contour
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        int m = s_g2[b * kEdtBlock];
+        for (int i = b * kEdtBlock + 1; i < min(W, (b + 1) * kEdtBlock); ++i) m = min(m, s_g2[i]);
+        s_bmin[b] = m;
+    }
     __syncthreads();
     const int inf = W + H;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const int gx = s_g[x];
-        int best = gx * gx;   // inf^2 when the column has no contour
-        for (int k = 1; k * k < best && (x - k >= 0 || x + k < W); ++k) {
-            const int k2 = k * k;
-            if (x - k >= 0) {
-                const int a = s_g[x - k];
-                best = min(best, k2 + a * a);
+        const int bx = x / kEdtBlock;
+        int best = edt_scan_block(s_g2, W, x, bx, s_g2[x]);
+        for (int j = 1;; ++j) {
+            bool more = false;
+            const int bl = bx - j, br = bx + j;
+            if (bl >= 0) {
+                const int dl = x - (bl * kEdtBlock + kEdtBlock - 1);
+                if (dl * dl < best) {
+                    more = true;
+                    if (dl * dl + s_bmin[bl] < best) best = edt_scan_block(s_g2, W, x, bl, best);
+                }
             }
-            if (x + k < W) {
-                const int b = s_g[x + k];
-                best = min(best, k2 + b * b);
+            if (br < nb) {
+                const int dr = br * kEdtBlock - x;
+                if (dr * dr < best) {
+                    more = true;
+                    if (dr * dr + s_bmin[br] < best) best = edt_scan_block(s_g2, W, x, br, best);
+                }
             }
+            if (!more) break;
         }
         img[(size_t)y * W + x].w = best >= inf * inf ? 0.f : sqrtf((float)best);
     }
 }
 
-void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st) {
-    const size_t smem = sizeof(int) * W;
+void launch_edt(const uint8_t* mask, uint8_t* contour, int* g, float4* img, int W, int H, cudaStream_t st) {
+    const size_t P = (size_t)W * H;
+    const int nb = (W + kEdtBlock - 1) / kEdtBlock;
+    const size_t smem = sizeof(int) * (W + nb);
     if (smem > 48 * 1024) cudaFuncSetAttribute(edt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    edt_columns_kernel<<<(W + 31) / 32, 32 * kEdtChunks, 0, st>>>(mask, g, W, H);
+    edt_contour_kernel<<<(int)std::min<size_t>((P + 255) / 256, 4096), 256, 0, st>>>(mask, W, H, contour);
+    edt_columns_kernel<<<(W + kEdtCols - 1) / kEdtCols, kEdtCols * kEdtChunks, 0, st>>>(contour, g, W, H);
     edt_rows_kernel<<<H, 256, smem, st>>>(g, img, W, H);
 }
 
@@ -503,15 +543,26 @@ __global__ void __launch_bounds__(256) part_label_kernel(const CapDesc* __restri
 }
 
 constexpr int kPartTile = 32;
-constexpr int kPartMaxDilate = 32;
+constexpr unsigned short kPartFar = 0xffff;
 
-// one CTA per 32 x 32 pixels, the labels of the tile and its halo of
-// part_dilate pixels in shared memory
+// One CTA per 32 x 32 pixels with the labels of the tile and its halo of
+// R = part_dilate pixels in shared memory.  The nearest-label search is
+// separable: (d^2, label) minimised lexicographically over the labelled
+// pixels within R equals, over the columns c within R, (x - c)^2 plus the
+// column's own lexicographic minimum of ((y - r)^2, label) over its rows r
+// within R (adding a constant keeps the order); likewise for the nearest
+// torso pixel.  Pass 1: per (tile row, halo column) the nearest labelled and
+// the nearest torso row; pass 2: per pixel the minimum over its 2R + 1
+// columns.  Labelled pixels keep their label.
 __global__ void __launch_bounds__(kPartTile * kPartTile) part_dilate_kernel(const CapDesc* __restrict__ caps) {
-    extern __shared__ uint8_t s_lab[];
+    extern __shared__ unsigned char s_raw[];
     const CapDesc& C = caps[0];
     if (C.sc->vis_frozen) return;
     const int R = C.part_dilate, S = kPartTile + 2 * R;
+    uint8_t* s_lab = s_raw;                                                 // S x S
+    unsigned short* s_d = (unsigned short*)(s_raw + ((S * S + 15) & ~15));  // kPartTile x S
+    unsigned short* s_t = s_d + kPartTile * S;
+    uint8_t* s_l = (uint8_t*)(s_t + kPartTile * S);
     const int bx = blockIdx.x * kPartTile - R, by = blockIdx.y * kPartTile - R;
     int any = 0;
     for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
@@ -524,27 +575,54 @@ __global__ void __launch_bounds__(kPartTile * kPartTile) part_dilate_kernel(cons
     any = __syncthreads_or(any);
     const int tx = threadIdx.x % kPartTile, ty = threadIdx.x / kPartTile;
     const int x = blockIdx.x * kPartTile + tx, y = blockIdx.y * kPartTile + ty;
+    if (!any) {
+        if (x < C.W && y < C.H) C.part_mask[(size_t)y * C.W + x] = 255;
+        return;
+    }
+    // pass 1: column minima for the tile's rows
+    for (int q = threadIdx.x; q < kPartTile * S; q += blockDim.x) {
+        const int r = q / S, c = q % S;   // tile row, halo column
+        unsigned short dn = kPartFar, dt = kPartFar;
+        int ln = 255;
+        for (int dy = 0; dy <= R && dt == kPartFar; ++dy) {
+            const int a = s_lab[(r + R - dy) * S + c], b = s_lab[(r + R + dy) * S + c];
+            if (dn == kPartFar && (a != 255 || b != 255)) {
+                dn = (unsigned short)(dy * dy);
+                ln = min(a, b);   // 255 when absent: the lower present label
+            }
+            if (a == C.torso_part || b == C.torso_part) dt = (unsigned short)(dy * dy);
+        }
+        s_d[q] = dn;
+        s_t[q] = dt;
+        s_l[q] = (uint8_t)ln;
+    }
+    __syncthreads();
     if (x >= C.W || y >= C.H) return;
     int lab = s_lab[(ty + R) * S + tx + R];
-    if (lab == 255 && any) {
+    if (lab == 255) {
         int best_d = 1 << 30, best_l = 255;
         bool torso = false;
-        for (int dy = -R; dy <= R; ++dy) {
-            const uint8_t* row = s_lab + (ty + R + dy) * S + tx + R;
-            for (int dx = -R; dx <= R; ++dx) {
-                const int d2 = dy * dy + dx * dx;
-                const int l = row[dx];
-                if (d2 > R * R || l == 255) continue;
-                torso |= l == C.torso_part;
-                if (d2 < best_d || (d2 == best_d && l < best_l)) {
-                    best_d = d2;
-                    best_l = l;
-                }
+        const int R2 = R * R;
+        for (int dx = -R; dx <= R; ++dx) {
+            const int q = ty * S + tx + R + dx;
+            const int dx2 = dx * dx;
+            if (s_t[q] != kPartFar && dx2 + s_t[q] <= R2) torso = true;
+            if (s_d[q] == kPartFar) continue;
+            const int d2 = dx2 + s_d[q];
+            const int l = s_l[q];
+            if (d2 <= R2 && (d2 < best_d || (d2 == best_d && l < best_l))) {
+                best_d = d2;
+                best_l = l;
             }
         }
         lab = torso ? C.torso_part : best_l;
     }
     C.part_mask[(size_t)y * C.W + x] = (uint8_t)lab;
+}
+
+static size_t part_dilate_smem(int R) {
+    const int S = kPartTile + 2 * R;
+    return (size_t)((S * S + 15) & ~15) + (size_t)kPartTile * S * (2 * sizeof(unsigned short) + 1);
 }
 
 void launch_part_mask(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
@@ -556,9 +634,8 @@ void launch_part_mask(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
     vis_clear_kernel<<<blocks, 256, 0, st>>>(dC);
     if (T.tri) raster_kernel<<<T.tri, kRasterThreads, 0, st>>>(dC, T.tri_items);
     part_label_kernel<<<blocks, 256, 0, st>>>(dC);
-    const int S = kPartTile + 2 * hC.part_dilate;
     const dim3 grd((hC.W + kPartTile - 1) / kPartTile, (hC.H + kPartTile - 1) / kPartTile);
-    part_dilate_kernel<<<grd, kPartTile * kPartTile, S * S, st>>>(dC);
+    part_dilate_kernel<<<grd, kPartTile * kPartTile, part_dilate_smem(hC.part_dilate), st>>>(dC);
 }
 
 __global__ void vertex_parts_kernel(const int4* __restrict__ skin_idx, const float4* __restrict__ skin_w,

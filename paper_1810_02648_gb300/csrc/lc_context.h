@@ -34,7 +34,7 @@ struct lc_ctx {
     float* stage_rgb = nullptr;
     float* stage_dt = nullptr;
     uint8_t* stage_mask = nullptr;
-    int* edt_g = nullptr;         // distance-transform scratch (first use of a null dt)
+    int* edt_g = nullptr;         // distance-transform scratch (first use of a null dt): W x H ints + W x H bytes
     float4* pyr_buf[3] = {nullptr, nullptr, nullptr};   // photometric pyramid levels
     float4* pyr_tmp = nullptr;    // row-blur scratch of the pyramid (W x H)
     lc_status build_pyramid();    // the levels of params.pyr_levels from the current frame

@@ -376,7 +376,9 @@ void launch_pack_frame(const float* rgb, const float* dt, const uint8_t* mask_in
                        uint8_t* mask, int W, int H, cudaStream_t st);
 // exact silhouette distance transform of the packed mask into img's 4th
 // channel (g: W x H int scratch; W <= 16384, g of a row in shared memory)
-void launch_edt(const uint8_t* mask, int* g, float4* img, int W, int H, cudaStream_t st);
+// distance transform of the silhouette into img's fourth channel; contour
+// (W x H bytes) and g (W x H ints) are scratch
+void launch_edt(const uint8_t* mask, uint8_t* contour, int* g, float4* img, int W, int H, cudaStream_t st);
 // the body-part mask of the frame (projection and raster of V^S, labels,
 // dilation); nothing when the capture's mask is off or its decisions frozen
 void launch_part_mask(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
