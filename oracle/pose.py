@@ -42,6 +42,12 @@ Readings:
   last two frames, theta = 2 theta^{t-1} - theta^{t-2} for the Euler angles
   and the root translation; the root rotation takes the same
   constant-velocity step on SO(3), R = R^{t-1} (R^{t-2})^T R^{t-1}.
+* Skinned displacement (Sec. 3.4, displacement warping): the previous
+  frame's rest-pose displacement, carried by the dual-quaternion blend
+  rotation of the frame's start pose, d^S = Q(theta_start) dhat, is added to
+  the skinned model for the silhouette term and the frame decisions.  Reading:
+  it is held fixed during the pose solve (the paper does not say how it
+  enters the Jacobian), so the Jacobian is the skinning's.
 * The normal equations are solved by a Cholesky factorisation (FP64).
 """
 from __future__ import annotations
@@ -209,6 +215,7 @@ class PoseProblem:
     theta_max: Optional[np.ndarray] = None
     inB: Optional[np.ndarray] = None
     bsign: Optional[np.ndarray] = None
+    disp: Optional[np.ndarray] = None          # (N,3) skinned displacement d^S added to the skinned model
 
     def __post_init__(self):
         self.V = np.asarray(self.V, dtype=np.float64)
@@ -262,6 +269,8 @@ def residuals_and_jacobian(pb: PoseProblem, pose: np.ndarray):
     rows.append(s3 * Jo.reshape(-1, sk.n_dof))
     if pb.inB is not None and pb.inB.any():
         P, VS = skin(sk, pb.V, G, o)
+        if pb.disp is not None:
+            VS = VS + pb.disp      # held fixed over the solve: the Jacobian is the skinning's
         # b_i follows the current skinned surface (the contour set B does not);
         # with no triangles given the caller's b_i stay fixed
         if pb.tris is not None:
@@ -354,6 +363,8 @@ def frame_decisions(pb: PoseProblem, pose):
     R, t, ang = split_pose(pb.sk, pose)
     G, o = forward_kinematics(pb.sk, R, t, ang)
     _, VS = skin(pb.sk, pb.V, G, o)
+    if pb.disp is not None:
+        VS = VS + pb.disp
     out = _vis.visibility(VS.astype(np.float32), pb.tris, pb.f, pb.cx, pb.cy, pb.W, pb.H,
                           pb.dt.astype(np.float32), pb.mask, 1e-2)
     fl = out["flags"]
@@ -373,6 +384,17 @@ def gauss_newton(pb: PoseProblem, pose0, n_gn: int):
         hist.append(dict(energy=float(F @ F), step_norm=float(np.linalg.norm(delta))))
         pose = apply_update(pb.sk, pose, delta)
     return pose, hist
+
+
+def skinned_displacement(sk: Skeleton, pose: np.ndarray, dhat: np.ndarray) -> np.ndarray:
+    """d^S = Q(pose) dhat: the rest-pose displacement of the previous frame
+    carried by the rotation of the dual-quaternion blend of the bone
+    rotations at `pose` (Sec. 3.4, displacement warping)."""
+    from .surface import blend_rotations
+    R, t, ang = split_pose(sk, pose)
+    G, o = forward_kinematics(sk, R, t, ang)
+    Q = blend_rotations(G, sk.skin_idx, sk.skin_w)
+    return np.einsum("nij,nj->ni", Q, np.asarray(dhat, dtype=np.float64))
 
 
 def extrapolate(pose1: np.ndarray, pose2: Optional[np.ndarray] = None) -> np.ndarray:

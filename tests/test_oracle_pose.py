@@ -242,3 +242,64 @@ def test_extrapolation_is_exact_for_constant_velocity():
     assert np.abs(ext[3:] - poses[2][3:]).max() < 1e-12
     assert np.abs(nr.so3_exp(ext[None, :3])[0] - nr.so3_exp(poses[2][None, :3])[0]).max() < 1e-12
     assert np.array_equal(op.extrapolate(poses[1]), poses[1])
+
+
+def test_skinned_displacement_special_cases(body):
+    """d^S = dhat at the rest pose; a pure root rotation R rotates every
+    displacement by R (every bone carries R, so does their blend)."""
+    pb = op.problem_from_scene(body)
+    sk = pb.sk
+    rng = np.random.default_rng(11)
+    dhat = rng.normal(scale=0.01, size=(len(pb.V), 3))
+    rest = np.zeros(sk.n_dof)
+    rest[3:6] = body.skeleton["joints_rest"][0]
+    assert np.abs(op.skinned_displacement(sk, rest, dhat) - dhat).max() <= 1e-15
+    rot = rest.copy()
+    rot[:3] = [0.3, -0.2, 0.5]
+    R = nr.so3_exp(rot[:3][None])[0]
+    assert np.abs(op.skinned_displacement(sk, rot, dhat) - dhat @ R.T).max() <= 1e-14
+
+
+def test_jacobian_fd_with_displacement(body):
+    """The displacement is held fixed: the silhouette rows of the displaced
+    model still match finite differences, and a zero displacement changes
+    nothing."""
+    pose0 = np.asarray(body.pose_init, dtype=np.float64)
+    base = op.problem_from_scene(body)
+    op.frame_decisions(base, pose0)
+    F0, J0 = op.residuals_and_jacobian(base, pose0)
+    z = op.problem_from_scene(body)
+    z.disp = np.zeros((len(z.V), 3))
+    op.frame_decisions(z, pose0)
+    Fz, Jz = op.residuals_and_jacobian(z, pose0)
+    assert np.array_equal(F0, Fz) and np.array_equal(J0, Jz)
+    rng = np.random.default_rng(12)
+    dhat = 0.004 * np.sin(base.V @ rng.normal(size=(3, 3)) * 5.0)
+    dec = op.problem_from_scene(body)
+    dec.disp = op.skinned_displacement(dec.sk, pose0, dhat)
+    op.frame_decisions(dec, pose0)
+    assert (dec.inB != base.inB).any()          # the displaced model has its own contour set
+    pb = _affine_dt(dec)
+    pb.inB, pb.bsign, pb.disp = dec.inB, dec.bsign, dec.disp
+    pose = pose0.copy()
+    pose[6:] += rng.normal(scale=0.05, size=len(pose) - 6)
+    F, J = op.residuals_and_jacobian(pb, pose)
+    h = 1e-6
+    Jfd = np.zeros_like(J)
+    for d in range(J.shape[1]):
+        e = np.zeros(J.shape[1])
+        e[d] = h
+        Fp, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, e))
+        Fm, _ = op.residuals_and_jacobian(pb, op.apply_update(pb.sk, pose, -e))
+        assert len(Fp) == len(F) == len(Fm)
+        Jfd[:, d] = (Fp - Fm) / (2 * h)
+    R, t, ang = op.split_pose(pb.sk, pose)
+    G, o = op.forward_kinematics(pb.sk, R, t, ang)
+    _, VS = op.skin(pb.sk, pb.V, G, o)
+    _, _, _, okj, _ = op._proj(pb, o)
+    _, _, _, _, inimg = op._proj(pb, VS + pb.disp)
+    sel = np.nonzero(pb.inB & inimg)[0]
+    r0 = 2 * int(okj.sum()) + 3 * len(o)
+    Jfd[r0:r0 + len(sel)] *= pb.bsign[sel][:, None]
+    err = np.abs(J - Jfd).max() / np.abs(Jfd).max()
+    assert err < 1e-6, err
