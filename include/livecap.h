@@ -116,6 +116,13 @@ typedef struct {
                                the finest.  Only E_photo samples it; the silhouette term
                                keeps the full-resolution distance transform. */
     int pyr_ksize[3];       /* Gaussian taps per level, odd, 1..31; default 15, 9, 3 */
+    int pose_displacement;  /* 1: once lc_surface_advance has recorded a displacement, the pose
+                               stage adds the skinned displacement d^S = Q(theta_start) dhat
+                               (the recorded rest-pose displacement carried by the
+                               dual-quaternion blend rotation of the frame's start pose) to
+                               its skinned model for the silhouette term and the contour set
+                               (Sec. 3.4, displacement warping); held fixed during the pose
+                               solve.  0 (default): the plain skinned model */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -371,7 +378,8 @@ lc_status lc_pose_advance(lc_ctx *ctx);
 lc_status lc_pose_extrapolate(lc_ctx *ctx);
 lc_status lc_pose_clear_history(lc_ctx *ctx);
 /* Inspection: at the current pose, recompute B and b_i and export the pose
- * normal equations: V_skinned N x 3 (FP32 skinned template), A n_dof x n_dof
+ * normal equations: V_skinned N x 3 (FP32 skinned template, plus the skinned
+ * displacement when pose_displacement applies), A n_dof x n_dof
  * (J^T J + prior), g n_dof (-J^T F - prior gradient), energy 1.  Null
  * pointers are skipped.  Synchronises. */
 lc_status lc_eval_pose(lc_ctx *ctx, float *V_skinned, double *A, double *g, double *energy);

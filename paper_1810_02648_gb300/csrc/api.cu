@@ -214,7 +214,8 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->target_energy >= 0.f) || p->n_gn_surface < 1 || p->n_gn_surface > LC_MAX_GN || p->n_pcg_surface < 1 ||
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
         p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
-        !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3)
+        !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3 || p->pose_displacement < 0 ||
+        p->pose_displacement > 1)
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     for (int j = 0; j < 3; ++j)
         if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)

@@ -18,6 +18,9 @@ struct PoseState {
     int graph_n_gn = 0;
     bool has_pose = false;
     float* pose_set = nullptr;      // kMaxDof + 9: the pose last given to lc_set_pose, then its root rotation
+    PoseDesc last{};                // the descriptor as last copied to the device
+    bool synced = false;
+    int graph_disp = 0;             // use_disp when the graph was captured
 };
 
 static void rodrigues(const double* w, double* R) {
@@ -73,7 +76,7 @@ void lc_ctx::pose_release() {
                     pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.blist,
                     pose->h.bcount, pose->h.hist, pose->h.info, pose->h.expA, pose->h.status, pose->d,
                     pose->pose_set, (void*)pose->h.temporal_w, (void*)pose->h.th_lo, (void*)pose->h.th_hi,
-                    pose->h.prev_joints, pose->h.pose_hist};
+                    pose->h.prev_joints, pose->h.pose_hist, pose->h.disp};
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
@@ -89,6 +92,8 @@ static lc_status pose_sync(lc_ctx* ctx) {
                                             ctx->stream),
                             "pose descriptor");
     if (s) return s;
+    ctx->pose->last = ctx->pose->h;
+    ctx->pose->synced = true;
     return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
 }
 
@@ -147,6 +152,8 @@ static void apply_pose_params(lc_ctx* ctx) {
     P.lam_temporal = ctx->params.lambda_temporal;
     P.lam_anat = ctx->params.lambda_anatomic;
     P.solver = ctx->params.pose_solver;
+    // the skinned displacement of Sec. 3.4 once the surface stage recorded one
+    P.use_disp = ctx->params.pose_displacement && ctx->surf_has_disp && ctx->hC.sD ? 1 : 0;
 }
 
 extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* parents, const float* joints_rest,
@@ -225,6 +232,8 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     P.temporal_w = (const float*)ctx->alloc(sizeof(float) * J);
     P.th_lo = (const float*)ctx->alloc(sizeof(float) * kMaxDof);
     P.th_hi = (const float*)ctx->alloc(sizeof(float) * kMaxDof);
+    P.disp = (float4*)ctx->alloc(sizeof(float4) * N);
+    P.use_disp = 0;
     P.prev_joints = (float4*)ctx->alloc(sizeof(float4) * J);
     P.pose_hist = (float*)ctx->alloc(sizeof(float) * 2 * (kMaxDof + 9));
     P.has_prev = 0;
@@ -393,6 +402,7 @@ void lc_ctx::enqueue_pose() {
     cudaMemcpyAsync(P.pose_start, P.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
     mark(LC_PH_POSE_VIS);
     launch_pose_fk(S.d, st);
+    if (P.use_disp) launch_surface_warp(dC, hC, S.d, 2, st);   // d^S at the start pose
     launch_pose_skin(dC, hC, S.d, nullptr, 0, st);
     launch_vis_unfreeze(dC, st);
     launch_visibility(dC, hC, st);
@@ -427,11 +437,16 @@ extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
     PoseState& S = *ctx->pose;
     lc_status s;
     apply_pose_params(ctx);
-    if ((s = pose_sync(ctx))) return s;
-    if (S.gexec && S.graph_n_gn != ctx->params.n_gn_pose) ctx->pose_drop_graph();
+    // the descriptor goes to the device only when it changed (a copy and a
+    // synchronisation per frame otherwise)
+    if (!S.synced || memcmp(&S.h, &S.last, sizeof(PoseDesc)) != 0) {
+        if ((s = pose_sync(ctx))) return s;
+    }
+    if (S.gexec && (S.graph_n_gn != ctx->params.n_gn_pose || S.graph_disp != S.h.use_disp)) ctx->pose_drop_graph();
     if (!S.gexec) {
         if ((s = ctx->capture(&S.gexec, &S.graph_kernels, &lc_ctx::enqueue_pose))) return s;
         S.graph_n_gn = ctx->params.n_gn_pose;
+        S.graph_disp = S.h.use_disp;   // the displacement kernel is in the graph or not
     }
     if ((s = ctx->cuda(cudaGraphLaunch(S.gexec, ctx->stream), "graph launch"))) return s;
     if ((s = ctx->accumulate_profile(ctx->prof_pose))) return s;
@@ -481,6 +496,7 @@ extern "C" lc_status lc_eval_pose(lc_ctx* ctx, float* V_skinned, double* A, doub
     // contour set at the current pose, then the system at the current pose
     cudaMemcpyAsync(S.h.pose_start, S.h.pose, sizeof(float) * kMaxDof, cudaMemcpyDeviceToDevice, st);
     launch_pose_fk(S.d, st);
+    if (S.h.use_disp) launch_surface_warp(ctx->dC, ctx->hC, S.d, 2, st);
     launch_pose_skin(ctx->dC, ctx->hC, S.d, nullptr, 0, st);
     launch_vis_unfreeze(ctx->dC, st);
     launch_visibility(ctx->dC, ctx->hC, st);

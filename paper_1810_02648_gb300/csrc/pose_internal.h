@@ -52,6 +52,8 @@ struct PoseDesc {
     int* info;                        // LC_MAX_GN + 1: refinement rounds of each step's solve (-1: FP64 factorisation)
     double* expA;                     // n_dof x (n_dof + 1) exported system (inspection)
     int* status;                      // 1: non-positive Cholesky pivot
+    float4* disp;                     // N: skinned displacement d^S added to the skinned model (Sec. 3.4)
+    int use_disp;                     // disp is set at every solve's start and used
 };
 
 void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* out_base, int mode,
@@ -67,7 +69,8 @@ void launch_pose_advance(const PoseDesc* dP, cudaStream_t st);
 // the pose <- the explicit Euler step from the pose history (n_hist >= 1)
 void launch_pose_extrapolate(const PoseDesc* dP, cudaStream_t st);
 // displacement warping of the surface stage (dP null: no skeleton, Q_i = I);
-// mode 0 records sD from sV, mode 1 sets sV from sD
+// mode 0 records sD from sV, mode 1 sets sV from sD, mode 2 writes Q_i sD_i
+// into the pose stage's dP->disp
 void launch_surface_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, int mode, cudaStream_t st);
 // residual rows -> partial pair sums (P.part)
 cudaError_t pose_kernels_init(int n_dof);

@@ -224,6 +224,13 @@ __global__ void __launch_bounds__(256) pose_skin_kernel(const CapDesc* __restric
         Z += ws[s] * (G[6] * d0 + G[7] * d1 + G[8] * d2 + fk.o[b][2]);
     }
     if (mode == 0) {
+        if (P.use_disp) {
+            // the skinned displacement rides on the skinned model (Sec. 3.4)
+            const float4 d = P.disp[i];
+            X += d.x;
+            Y += d.y;
+            Z += d.z;
+        }
         const bool ok = valid_depth(Z);
         C.vw[i] = make_float4(X, Y, Z, ok ? 1.f : 0.f);
         C.uv[i] = ok ? project_exact(C.f, C.cx, C.cy, X, Y, Z) : make_float2(0.f, 0.f);
@@ -380,6 +387,13 @@ __global__ void __launch_bounds__(kSysThreads) pose_system_kernel(const CapDesc*
                 X += ws[s] * Pt[s][0];
                 Y += ws[s] * Pt[s][1];
                 Z += ws[s] * Pt[s][2];
+            }
+            if (P.use_disp) {
+                // held fixed over the solve: the Jacobian stays the skinning's
+                const float4 dd = P.disp[i];
+                X += dd.x;
+                Y += dd.y;
+                Z += dd.z;
             }
             const float2 uv = project_exact(C.f, C.cx, C.cy, X, Y, Z);
             if (valid_depth(Z) && in_image(uv, C.W, C.H)) {
@@ -849,6 +863,12 @@ __global__ void __launch_bounds__(256) surface_warp_kernel(const CapDesc* __rest
             R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
             R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
         }
+    }
+    if (mode == 2) {
+        const float4 d = C.sD[i];
+        pd->disp[i] = make_float4(R[0] * d.x + R[1] * d.y + R[2] * d.z, R[3] * d.x + R[4] * d.y + R[5] * d.z,
+                                  R[6] * d.x + R[7] * d.y + R[8] * d.z, 0.f);
+        return;
     }
     const float4 S = C.base[i];
     if (mode == 0) {

@@ -29,7 +29,7 @@ class lc_params(ctypes.Structure):
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
                 ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
                 ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float),
-                ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3)]
+                ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3), ("pose_displacement", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):

@@ -384,3 +384,64 @@ def test_pose_extrapolation_matches_oracle(body):
     with pytest.raises(LivecapError):
         ctx.pose_extrapolate()
     ctx.close()
+
+
+def test_pose_displacement_matches_oracle(body):
+    """Sec. 3.4: the recorded displacement, carried by the start pose's blend
+    rotation, rides on the skinned model of the pose stage: normal equations
+    and the 5-step solve against the oracle with the same fixed d^S."""
+    from oracle import surface as osf
+    ctx = _ctx(body, pose_displacement=1, n_gn_pose=2)
+    ctx.solve_pose(stats=False)
+    pose_a = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    VS_a = ctx.eval_pose()["V"]                      # no displacement recorded yet
+    c = VS_a.mean(0)
+    d = (0.006 * np.sin((VS_a - c) @ np.random.default_rng(26).normal(size=(3, 3)) * 5.0)).astype(np.float32)
+    Va = (VS_a + d).astype(np.float32)
+    ctx.set_surface(Va)
+    ctx.surface_advance()
+    sk = op.skeleton_from_scene(body)
+    Ra, ta, anga = op.split_pose(sk, pose_a.astype(np.float64))
+    Ga, _ = op.forward_kinematics(sk, Ra, ta, anga)
+    dh = osf.record_displacement(Va, VS_a, osf.blend_rotations(Ga, sk.skin_idx, sk.skin_w))
+    pose_b = np.asarray(body.pose_init, dtype=np.float32)
+    disp = op.skinned_displacement(sk, pose_b.astype(np.float64), dh)
+    # normal equations at the start pose
+    ctx.set_params(n_gn_pose=body.n_gn_pose)
+    ctx.set_pose(pose_b)
+    ev = ctx.eval_pose()
+    flags = ctx.read_visibility()["flags"]
+    pb = _oracle_pose_problem(body, flags)
+    pb.tris = None
+    pb.disp = disp
+    Rb, tb, angb = op.split_pose(sk, pose_b.astype(np.float64))
+    Gb, ob = op.forward_kinematics(sk, Rb, tb, angb)
+    _, VSb = op.skin(sk, pb.V, Gb, ob)
+    dV = np.abs(ev["V"] - (VSb + disp)).max() / np.abs(VSb).max()
+    F, J = op.residuals_and_jacobian(pb, pose_b.astype(np.float64))
+    A_ref, g_ref = J.T @ J, -(J.T @ F)
+    dA = np.abs(ev["A"] - A_ref).max() / np.abs(A_ref).max()
+    dg = np.abs(ev["g"] - g_ref).max() / np.abs(g_ref).max()
+    # the solve
+    ctx.set_pose(pose_b)
+    st = ctx.solve_pose()
+    flags = ctx.read_visibility()["flags"]
+    pose_gpu = ctx.read_back(R=False, t=False, V=False, flags=False, pose=True)["pose"]
+    pb = _oracle_pose_problem(body, flags)
+    pb.disp = disp
+    pose_ref, hist = op.gauss_newton(pb, pose_b.astype(np.float64), body.n_gn_pose)
+    dj = np.abs(_oracle_joints(pb, pose_gpu) - _oracle_joints(pb, pose_ref)).max()
+    e_ref = op.energy(pb, pose_ref)
+    de = abs(st["e_total"] - e_ref) / e_ref
+    dh_rel = np.abs(np.array(st["e_gn"]) - [h["energy"] for h in hist]).max() / hist[0]["energy"]
+    # without the displacement the same frame ends elsewhere
+    ctx.set_params(pose_displacement=0)
+    ctx.set_pose(pose_b)
+    st0 = ctx.solve_pose()
+    report("pose_displacement", dV=dV, dA=dA, dg=dg, dj=dj, de=de, dh=dh_rel, e=st["e_total"], e_plain=st0["e_total"],
+           max_disp=float(np.abs(disp).max()))
+    assert dV <= 4e-6
+    assert dA <= 1e-4 and dg <= 1e-4
+    assert dj <= 2e-3 and de <= 1e-2 and dh_rel <= 1e-3
+    assert abs(st0["e_total"] - st["e_total"]) > 1e-3 * st["e_total"]
+    ctx.close()
