@@ -15,6 +15,7 @@
 // One iteration is then computed from shared memory alone:
 //   (J^T J p)_k = sum_entries w_is [a_is x q_i ; q_i] + ARAP terms, with
 //   q_i = H_i sum_s w_is (p_omega,s x a_is + p_t,s) recomputed per entry,
+// one warp per owned node (entries and edges lane-strided, one shuffle tree),
 // followed by FP64 partial dot products exchanged through distributed shared
 // memory (each CTA writes its partial into every CTA's slot array, all sum in
 // rank order: deterministic and identical in every CTA).  The preconditioned
@@ -37,8 +38,7 @@ constexpr int kPcgWarps = kPcgThreads / 32;
 
 // shared-memory carve-up (byte offsets, all 16-byte aligned)
 struct Smem {
-    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vminv, zloc, chunks,
-        chunkAcc, nodeChunk, total;
+    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vminv, zloc, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -63,10 +63,6 @@ __host__ __device__ inline Smem smem_layout(int n, int K, int cap_e, int cap_d, 
     s.vAp = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vminv = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.zloc = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
-    const size_t max_chunks = (size_t)cap_e / 32 + (size_t)cap_d / 32 + 2 * (size_t)cap_n + 1;
-    s.chunks = o; o = al16(o + 12 * max_chunks);
-    s.chunkAcc = o; o = al16(o + sizeof(float) * 6 * max_chunks);
-    s.nodeChunk = o; o = al16(o + sizeof(int) * ((size_t)cap_n + 1));
     s.total = o;
     return s;
 }
@@ -99,15 +95,6 @@ __device__ __forceinline__ float3 rot(const float4* R, int k, float3 v) {
     return make_float3(a.x * v.x + a.y * v.y + a.z * v.z, b.x * v.x + b.y * v.y + b.z * v.z,
                        c.x * v.x + c.y * v.y + c.z * v.z);
 }
-
-// One work chunk of phase 1: up to 32 CSR entries, or up to 32 ARAP edges,
-// of one owned node.
-struct Chunk {
-    unsigned short node;   // owned-node index
-    unsigned short edge;   // 1 = ARAP edges, 0 = CSR entries
-    int start;             // first entry / edge (CTA-local)
-    int count;             // <= 32
-};
 
 // Block-wide FP32 sum; the result is valid in warp 0.  Fixed shuffle tree.
 __device__ __forceinline__ float block_sum_f32(float v, float* s_warpf, int warp, int lane) {
@@ -182,7 +169,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     __shared__ float s_warpf[kPcgWarps];
     __shared__ double s_scalar[4];   // rz, alpha, beta
     __shared__ int s_flag[2];        // stop, breakdown
-    __shared__ int s_nchunks;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int cl = (int)cluster.num_blocks();
@@ -212,9 +198,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     float4* vAp = (float4*)(smem + L.vAp);
     float4* vminv = (float4*)(smem + L.vminv);
     float4* zloc = (float4*)(smem + L.zloc);
-    Chunk* chunks = (Chunk*)(smem + L.chunks);
-    float* chunkAcc = (float*)(smem + L.chunkAcc);
-    int* nodeChunk = (int*)(smem + L.nodeChunk);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // ---------------- staging ----------------
@@ -278,19 +261,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
         }
     }
     __syncthreads();
-    // chunk table: per node its entry chunks, then its edge chunks
-    if (tid == 0) {
-        int c = 0;
-        for (int kk = 0; kk < nown; ++kk) {
-            nodeChunk[kk] = c;
-            for (int b = 0; b < nodeCnt[kk]; b += 32)
-                chunks[c++] = {(unsigned short)kk, 0, nodeStart[kk] + b, min(32, nodeCnt[kk] - b)};
-            for (int b = dOff[kk]; b < dOff[kk + 1]; b += 32)
-                chunks[c++] = {(unsigned short)kk, 1, b, min(32, dOff[kk + 1] - b)};
-        }
-        nodeChunk[nown] = c;
-        s_nchunks = c;
-    }
     // vectors: x = 0, r = b, M^-1 (own nodes); initial r^T z
     float my_rz = 0.f;
     for (int j = tid; j < 2 * nown; j += kPcgThreads) {
@@ -321,56 +291,45 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
         }
     }
     __syncthreads();
-    const int nchunks = s_nchunks;
 
     // ---------------- iterations ----------------
     int iters = 0;
     for (int it = 0; it < n_pcg && !s_flag[0]; ++it) {
-        // phase 1a: per chunk 6-float partial of (J^T J p) for its node
-        for (int c = warp; c < nchunks; c += kPcgWarps) {
-            const Chunk ch = chunks[c];
+        // phase 1: one warp per owned node: its CSR entries and ARAP edges
+        // lane-strided, a fixed 6-float shuffle tree, then lane 0 stores the
+        // node's (J^T J p) and its p^T A p term (FP32 per CTA)
+        float my_pap = 0.f;
+        for (int kk = warp; kk < nown; kk += kPcgWarps) {
             float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (lane < ch.count) {
-                if (!ch.edge) {
-                    entry_term<KT>(ch.start + lane, K, cap_e, eA, eK, eH, eSelf, p_all, acc);
-                } else {
-                    const int k = lo + ch.node;
-                    const int d = ch.start + lane;
-                    const float3 pw = f3_(p_all[2 * k]), pt = f3_(p_all[2 * k + 1]);
-                    const int l = dL[d];
-                    const float4 bk = dB[2 * d], bl = dB[2 * d + 1];
-                    const float cc = bk.w;
-                    const float3 plw = f3_(p_all[2 * l]), plt = f3_(p_all[2 * l + 1]);
-                    const float3 D0 = cr(pw, f3_(bk));
-                    const float3 D = make_float3(D0.x + pt.x - plt.x, D0.y + pt.y - plt.y, D0.z + pt.z - plt.z);
-                    const float3 bD = cr(f3_(bk), D);
-                    const float3 E0 = cr(plw, f3_(bl));
-                    acc[0] = cc * bD.x; acc[1] = cc * bD.y; acc[2] = cc * bD.z;
-                    acc[3] = cc * D.x - cc * (E0.x + plt.x - pt.x);
-                    acc[4] = cc * D.y - cc * (E0.y + plt.y - pt.y);
-                    acc[5] = cc * D.z - cc * (E0.z + plt.z - pt.z);
-                }
+            const int e0 = nodeStart[kk], ne = nodeCnt[kk];
+            for (int j = lane; j < ne; j += 32) entry_term<KT>(e0 + j, K, cap_e, eA, eK, eH, eSelf, p_all, acc);
+            const int k = lo + kk;
+            const float3 pw = f3_(p_all[2 * k]), pt = f3_(p_all[2 * k + 1]);
+            for (int d = dOff[kk] + lane; d < dOff[kk + 1]; d += 32) {
+                const int l = dL[d];
+                const float4 bk = dB[2 * d], bl = dB[2 * d + 1];
+                const float cc = bk.w;
+                const float3 plw = f3_(p_all[2 * l]), plt = f3_(p_all[2 * l + 1]);
+                const float3 D0 = cr(pw, f3_(bk));
+                const float3 D = make_float3(D0.x + pt.x - plt.x, D0.y + pt.y - plt.y, D0.z + pt.z - plt.z);
+                const float3 bD = cr(f3_(bk), D);
+                const float3 E0 = cr(plw, f3_(bl));
+                acc[0] += cc * bD.x;
+                acc[1] += cc * bD.y;
+                acc[2] += cc * bD.z;
+                acc[3] += cc * D.x - cc * (E0.x + plt.x - pt.x);
+                acc[4] += cc * D.y - cc * (E0.y + plt.y - pt.y);
+                acc[5] += cc * D.z - cc * (E0.z + plt.z - pt.z);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) chunkAcc[6 * c + q] = acc[q];
-        }
-        __syncthreads();
-        // phase 1b: node totals (chunk order) and p^T A p (FP32 per CTA)
-        float my_pap = 0.f;
-        for (int kk = tid; kk < nown; kk += kPcgThreads) {
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int c = nodeChunk[kk]; c < nodeChunk[kk + 1]; ++c)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) a[q] += chunkAcc[6 * c + q];
-            vAp[2 * kk] = make_float4(a[0], a[1], a[2], 0.f);
-            vAp[2 * kk + 1] = make_float4(a[3], a[4], a[5], 0.f);
-            const float4 pw = p_all[2 * (lo + kk)], pt = p_all[2 * (lo + kk) + 1];
-            my_pap += pw.x * a[0] + pw.y * a[1] + pw.z * a[2] + pt.x * a[3] + pt.y * a[4] + pt.z * a[5];
+            if (lane == 0) {
+                vAp[2 * kk] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                vAp[2 * kk + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+                my_pap += pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
+            }
         }
         {
             const float t = block_sum_f32(my_pap, s_warpf, warp, lane);
