@@ -38,7 +38,7 @@ constexpr int kPcgWarps = kPcgThreads / 32;
 
 // shared-memory carve-up (byte offsets, all 16-byte aligned)
 struct Smem {
-    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vminv, zloc, total;
+    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vAz, vminv, zloc, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -61,6 +61,7 @@ __host__ __device__ inline Smem smem_layout(int n, int K, int cap_e, int cap_d, 
     s.vx = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vr = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vAp = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
+    s.vAz = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vminv = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.zloc = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.total = o;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     __shared__ float s_warpf[kPcgWarps];
     __shared__ double s_scalar[4];   // rz, alpha, beta
     __shared__ int s_flag[2];        // stop, breakdown
+    __shared__ int s_stopz;          // the last r^T z was zero (set by warp 0 before a barrier)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int cl = (int)cluster.num_blocks();
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     float4* vx = (float4*)(smem + L.vx);
     float4* vr = (float4*)(smem + L.vr);
     float4* vAp = (float4*)(smem + L.vAp);
+    float4* vAz = (float4*)(smem + L.vAz);
     float4* vminv = (float4*)(smem + L.vminv);
     float4* zloc = (float4*)(smem + L.zloc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -287,11 +290,16 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
         vminv[j] = mi;
         my_rz += b.x * (mi.x * b.x) + b.y * (mi.y * b.y) + b.z * (mi.z * b.z);
     }
-    // initial p = z for all nodes (every CTA computes the full vector)
+    // the first direction is z_0 = M^-1 b: every CTA holds z for all nodes;
+    // the owned p and A p start at zero (p_0 = z_0 + 0 p, A p_0 = A z_0 + 0)
     for (int j = tid; j < 2 * n; j += kPcgThreads) {
         const float4 b = C.b[j];
         const float4 mi = C.minv[j];
-        p_all[j] = make_float4(mi.x * b.x, mi.y * b.y, mi.z * b.z, 0.f);
+        z_all[j] = make_float4(mi.x * b.x, mi.y * b.y, mi.z * b.z, 0.f);
+    }
+    for (int j = tid; j < 2 * nown; j += kPcgThreads) {
+        p_all[2 * lo + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        vAp[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     {
         const float t = block_sum_f32(my_rz, s_warpf, warp, lane);
@@ -302,30 +310,49 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
         const double rz = cluster_total(s_rz_part, cl);
         if (lane == 0) {
             s_scalar[0] = rz;
+            s_scalar[2] = 0.0;   // beta of the first direction
             s_flag[0] = rz == 0.0 ? 1 : 0;
             s_flag[1] = 0;
+            s_stopz = 0;
         }
     }
     __syncthreads();
 
     // ---------------- iterations ----------------
+    // The product is taken on z: A p = A z + beta A p_prev (A is linear), so
+    // the heavy A z of iteration it runs while warp 0 forms beta from the
+    // previous r^T z, and only the owned entries of p and A p are updated.
+    // Flags written inside an iteration are read only after a barrier, so
+    // every thread leaves the loop at the same point.
     int iters = 0;
-    for (int it = 0; it < n_pcg && !s_flag[0]; ++it) {
-        // phase 1: one warp per owned node: its CSR entries and ARAP edges
-        // lane-strided, a fixed 6-float shuffle tree, then lane 0 stores the
-        // node's (J^T J p) and its p^T A p term (FP32 per CTA)
-        float my_pap = 0.f;
+    bool completed = true;
+    const int n_it = s_flag[0] ? 0 : n_pcg;
+    for (int it = 0; it < n_it; ++it) {
+        // warp 0 first: beta = r^T z / (r^T z)_prev from the cluster partials
+        if (it > 0 && warp == 0) {
+            const double rz_new = cluster_total(s_rz_part, cl);
+            if (lane == 0) {
+                if (rz_new == 0.0) {
+                    s_stopz = 1;
+                } else {
+                    s_scalar[2] = (double)__fdiv_rn((float)rz_new, (float)s_scalar[0]);
+                    s_scalar[0] = rz_new;
+                }
+            }
+        }
+        // phase 1: (A z)_k for the owned nodes, one warp per node: its CSR
+        // entries and ARAP edges lane-strided, a fixed 6-float shuffle tree
         for (int kk = warp; kk < nown; kk += kPcgWarps) {
             float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int e0 = nodeStart[kk], ne = nodeCnt[kk];
-            for (int j = lane; j < ne; j += 32) entry_term<KT>(e0 + j, K, cap_e, eA, eK, eH, eSelf, p_all, acc);
+            for (int j = lane; j < ne; j += 32) entry_term<KT>(e0 + j, K, cap_e, eA, eK, eH, eSelf, z_all, acc);
             const int k = lo + kk;
-            const float3 pw = f3_(p_all[2 * k]), pt = f3_(p_all[2 * k + 1]);
+            const float3 pw = f3_(z_all[2 * k]), pt = f3_(z_all[2 * k + 1]);
             for (int d = dOff[kk] + lane; d < dOff[kk + 1]; d += 32) {
                 const int l = dL[d];
                 const float4 bk = dB[2 * d], bl = dB[2 * d + 1];
                 const float cc = bk.w;
-                const float3 plw = f3_(p_all[2 * l]), plt = f3_(p_all[2 * l + 1]);
+                const float3 plw = f3_(z_all[2 * l]), plt = f3_(z_all[2 * l + 1]);
                 const float3 D0 = cr(pw, f3_(bk));
                 const float3 D = make_float3(D0.x + pt.x - plt.x, D0.y + pt.y - plt.y, D0.z + pt.z - plt.z);
                 const float3 bD = cr(f3_(bk), D);
@@ -342,13 +369,29 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
             if (lane == 0) {
-                vAp[2 * kk] = make_float4(acc[0], acc[1], acc[2], 0.f);
-                vAp[2 * kk + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
-                my_pap += pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
+                vAz[2 * kk] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                vAz[2 * kk + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
             }
         }
+        __syncthreads();
+        if (s_stopz) {
+            completed = false;
+            break;
+        }
+        // owned p = z + beta p, A p = A z + beta A p; p^T A p (FP32 per CTA)
+        const float beta = (float)s_scalar[2];
+        float my_pap = 0.f;
+        for (int j = tid; j < 2 * nown; j += kPcgThreads) {
+            const float4 z = z_all[2 * lo + j], pp = p_all[2 * lo + j];
+            const float4 az = vAz[j], ap0 = vAp[j];
+            const float4 p = make_float4(z.x + beta * pp.x, z.y + beta * pp.y, z.z + beta * pp.z, 0.f);
+            const float4 ap = make_float4(az.x + beta * ap0.x, az.y + beta * ap0.y, az.z + beta * ap0.z, 0.f);
+            p_all[2 * lo + j] = p;
+            vAp[j] = ap;
+            my_pap += p.x * ap.x + p.y * ap.y + p.z * ap.z;
+        }
         {
-            const float t = block_sum_lane0_f32(my_pap, s_warpf, warp, lane);
+            const float t = block_sum_f32(my_pap, s_warpf, warp, lane);
             publish(cluster, (double)t, s_pAp_part, rank, cl);
         }
         cluster.sync();
@@ -365,7 +408,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
             }
         }
         __syncthreads();
-        if (s_flag[0]) break;
+        if (s_flag[0]) {
+            completed = false;
+            break;
+        }
         // phase 2: x, r, z for owned nodes; r^T z partial
         const float alpha = (float)s_scalar[1];
         float my_rz2 = 0.f;
@@ -394,28 +440,17 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
         }
         cluster.sync();
         ++iters;
-        if (warp == 0) {
-            const double rz_new = cluster_total(s_rz_part, cl);
-            if (lane == 0) {
-                if (rz_new == 0.0) {
-                    s_flag[0] = 1;
-                } else {
-                    s_scalar[2] = (double)__fdiv_rn((float)rz_new, (float)s_scalar[0]);
-                    s_scalar[0] = rz_new;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_flag[0]) break;
-        // phase 3 (local): p = z + beta p for every node from the replicated z
-        const float beta = (float)s_scalar[2];
-        for (int j = tid; j < 2 * n; j += kPcgThreads) {
-            const float4 p = p_all[j];
-            const float4 z = z_all[j];
-            p_all[j] = make_float4(z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, 0.f);
-        }
-        __syncthreads();
     }
+    // the r^T z of the last iteration (its beta is never needed)
+    if (completed && iters > 0 && warp == 0) {
+        const double rz_new = cluster_total(s_rz_part, cl);
+        if (lane == 0) {
+            if (rz_new == 0.0) s_flag[0] = 1;
+            else s_scalar[0] = rz_new;
+        }
+    }
+    if (tid == 0 && s_stopz) s_flag[0] = 1;
+    __syncthreads();
     // ---------------- results ----------------
     for (int j = tid; j < 2 * nown; j += kPcgThreads) C.x[2 * lo + j] = vx[j];
     if (rank == 0 && tid == 0) {
