@@ -340,9 +340,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
                 }
             }
         }
-        // phase 1: (A z)_k for the owned nodes, one warp per node: its CSR
-        // entries and ARAP edges lane-strided, a fixed 6-float shuffle tree
-        for (int kk = warp; kk < nown; kk += kPcgWarps) {
+        // phase 1: (A z)_k for the owned nodes, one warp per node (warps 1..31:
+        // warp 0 is busy with beta): its CSR entries and ARAP edges
+        // lane-strided, a fixed 6-float shuffle tree
+        for (int kk = warp - 1; kk < nown; kk += kPcgWarps - 1) {
+            if (kk < 0) break;
             float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int e0 = nodeStart[kk], ne = nodeCnt[kk];
             for (int j = lane; j < ne; j += 32) entry_term<KT>(e0 + j, K, cap_e, eA, eK, eH, eSelf, z_all, acc);
