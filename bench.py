@@ -64,6 +64,20 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(total_ms, dist, device=None):
+    """The slowest rank's timed total; every rank receives it."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, total_ms):
+    """Whole-job frames/s: each of the `world` replicas solves `steps` frames
+    of its own capture; the job lasts as long as the slowest one."""
+    return world * steps / (total_ms / 1e3)
+
+
 def path_options(a):
     """The non-default options of the per-frame path, as config keys."""
     opt = {}
@@ -406,10 +420,8 @@ def run_ours(a):
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * a.steps / (total_ms / 1e3)
+        total_ms = max_over_ranks(total_ms, dist, dev)
+    value = job_throughput(world, a.steps, total_ms)
 
     # per-phase device time (event chain in the captured solve), same workload
     ctx.set_profiling(True)
