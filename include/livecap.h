@@ -277,8 +277,10 @@ lc_status lc_read_visibility(lc_ctx *ctx, uint64_t *zbuf, uint8_t *flags, float 
  * r_photo N x 3 (sqrt(w_p)(I - C), zero where inactive) and r_sil N
  * (sqrt(w_s) DT), per-vertex normal blocks H N x 6 (h00 h01 h02 h11 h12 h22
  * of A_i^T A_i, A_i = d r_i / d v'_i with the b_i sign) and e N x 3
- * (A_i^T r_i), energy 3 (photo, sil, arap).  Null pointers are skipped.
- * Synchronises. */
+ * (A_i^T r_i), energy 3 (photo, sil, arap).  The photometric term samples
+ * the pyramid level of Gauss-Newton step 0 (level 3 - pyr_levels) when the
+ * pyramid is on; sigma_c and the body-part mask apply as in a solve.  Null
+ * pointers are skipped.  Synchronises. */
 lc_status lc_eval_linearization(lc_ctx *ctx, float *v_warp, float *uv, float *r_photo,
                                 float *r_sil, float *H, float *e, double *energy);
 
@@ -553,7 +555,8 @@ lc_status lc_read_surface(lc_ctx *ctx, float *V, uint8_t *flags);
 /* Inspection (each synchronises).  lc_surface_visibility: the frame
  * decisions at the current V (lc_read_visibility returns them).
  * lc_surface_linearize: at the current V with those decisions (b_i
- * re-evaluated), rhs = -J^T F (N x 3), diag = diag(J^T J) (N x 3) and
+ * re-evaluated; the pyramid level of Gauss-Newton step 0, sigma_c and the
+ * body-part mask as in a solve), rhs = -J^T F (N x 3), diag = diag(J^T J) (N x 3) and
  * energies[6] = photo, silhouette, smooth, edge, velocity, acceleration;
  * any output may be NULL.  lc_surface_apply_jtj: out = J^T J p (N x 3) at
  * that linearisation.  lc_surface_solve_linear: n_pcg_surface Jacobi-PCG
