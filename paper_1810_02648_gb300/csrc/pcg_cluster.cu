@@ -11,18 +11,18 @@
 //     a_is = R_k (v_i - g_k), plus which slot is k;
 //   * per owned ARAP edge (k, l): l, c = w_a s_kl, b_kl = R_k (g_l - g_k),
 //     b_lk = R_l (g_k - g_l);
-//   * the full search direction p of all nodes (every CTA holds a copy).
+//   * the preconditioned residual z of all nodes (every CTA holds a copy).
 // One iteration is then computed from shared memory alone:
-//   (J^T J p)_k = sum_entries w_is [a_is x q_i ; q_i] + ARAP terms, with
-//   q_i = H_i sum_s w_is (p_omega,s x a_is + p_t,s) recomputed per entry,
+//   (J^T J z)_k = sum_entries w_is [a_is x q_i ; q_i] + ARAP terms, with
+//   q_i = H_i sum_s w_is (z_omega,s x a_is + z_t,s) recomputed per entry,
 // one warp per owned node (entries and edges lane-strided, one shuffle tree),
-// followed by FP64 partial dot products exchanged through distributed shared
-// memory (each CTA writes its partial into every CTA's slot array, all sum in
-// rank order: deterministic and identical in every CTA).  The preconditioned
-// residual z of the owned nodes is broadcast the same way, so after the r^T z
-// barrier every CTA forms the new p = z + beta p for all nodes locally.  Two
-// hardware cluster barriers per iteration; no spin loops, no global-memory
-// round trips.
+// then for the owned nodes p = z + beta p and A p = A z + beta A p (A is
+// linear; warp 0 forms beta while the others compute A z), followed by FP64
+// partial dot products exchanged through distributed shared memory (each CTA
+// writes its partial into every CTA's slot array, all sum in rank order:
+// deterministic and identical in every CTA).  The new z of the owned nodes is
+// stored into every CTA's copy as each thread forms it.  Two hardware cluster
+// barriers per iteration; no spin loops, no global-memory round trips.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -38,7 +38,7 @@ constexpr int kPcgWarps = kPcgThreads / 32;
 
 // shared-memory carve-up (byte offsets, all 16-byte aligned)
 struct Smem {
-    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vAz, vminv, zloc, total;
+    size_t p_all, z_all, eH, eA, eK, eSelf, nodeStart, nodeCnt, dL, dB, dC, dCnt, vx, vr, vAp, vAz, vminv, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -63,7 +63,6 @@ __host__ __device__ inline Smem smem_layout(int n, int K, int cap_e, int cap_d, 
     s.vAp = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vAz = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.vminv = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
-    s.zloc = o; o = al16(o + sizeof(float4) * 2 * (size_t)cap_n);
     s.total = o;
     return s;
 }
@@ -187,6 +186,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     __shared__ double s_scalar[4];   // rz, alpha, beta
     __shared__ int s_flag[2];        // stop, breakdown
     __shared__ int s_stopz;          // the last r^T z was zero (set by warp 0 before a barrier)
+    __shared__ float4* s_zdst[16];   // z of every cluster CTA (distributed shared memory)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int cl = (int)cluster.num_blocks();
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     float4* vAp = (float4*)(smem + L.vAp);
     float4* vAz = (float4*)(smem + L.vAz);
     float4* vminv = (float4*)(smem + L.vminv);
-    float4* zloc = (float4*)(smem + L.zloc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < cl) s_zdst[tid] = cluster.map_shared_rank(z_all, tid);
 
     // ---------------- staging ----------------
     const int e_base = C.ent_off[lo];
@@ -427,18 +427,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
             const float4 z = make_float4(mi.x * r.x, mi.y * r.y, mi.z * r.z, 0.f);
             vx[j] = x;
             vr[j] = r;
-            zloc[j] = z;
+            // the owned z into every CTA's copy (this one's included)
+            for (int d = 0; d < cl; ++d) s_zdst[d][2 * lo + j] = z;
             my_rz2 += r.x * z.x + r.y * z.y + r.z * z.z;
         }
         {
-            const float t = block_sum_f32(my_rz2, s_warpf, warp, lane);   // syncs zloc too
+            const float t = block_sum_f32(my_rz2, s_warpf, warp, lane);
             publish(cluster, (double)t, s_rz_part, rank, cl);
-        }
-        // broadcast the owned z into every CTA's copy, one store per thread
-        for (int j = tid; j < 2 * nown * cl; j += kPcgThreads) {
-            const int jn = j % (2 * nown), d = j / (2 * nown);
-            float4* dst = cluster.map_shared_rank(z_all, d);
-            dst[2 * lo + jn] = zloc[jn];
         }
         cluster.sync();
         ++iters;
