@@ -78,6 +78,13 @@ def job_throughput(world, steps, total_ms):
     return world * steps / (total_ms / 1e3)
 
 
+def frame_prep_kernels(pyramid_levels):
+    """Kernels of one on-device frame preparation: packing, the three passes
+    of the distance transform (contour flags, columns, rows), then per
+    pyramid level a box mean (factor > 1) and two blur passes."""
+    return 4 + sum((1 if j < 2 else 0) + 2 for j in range(3 - pyramid_levels, 3))
+
+
 def path_options(a):
     """The non-default options of the per-frame path, as config keys."""
     opt = {}
@@ -517,9 +524,7 @@ def run_ours(a):
               for k, v in prof.items() if v[1]}
     extra_kernels = (5 if has_pose else 3) if surface else 1
     if a.frame_prep:
-        # packing, the two distance-transform passes, per pyramid level a box
-        # mean (factor > 1) and two blur passes
-        extra_kernels += 3 + sum((1 if j < 2 else 0) + 2 for j in range(3 - a.pyramid, 3))
+        extra_kernels += frame_prep_kernels(a.pyramid)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,

@@ -66,3 +66,22 @@ def test_params_default(lib):
     # sizes (Sec. 3.4: 15, 9, 3) ready for it
     assert p.sigma_c == 0.0 and p.pyr_levels == 0
     assert list(p.pyr_ksize) == [15, 9, 3]
+    # the pose stage's skinned displacement (Sec. 3.4) is opt-in
+    assert p.pose_displacement == 0
+
+
+def test_bench_options_and_launch_count():
+    """Host logic of bench.py: the options of the per-frame path become
+    config keys, and the frame preparation's kernel count per step."""
+    import argparse
+    import bench
+    a = argparse.Namespace(pyramid=0, sigma_c=0.0, body_parts=False, frame_prep=False)
+    assert bench.path_options(a) == {}
+    a = argparse.Namespace(pyramid=3, sigma_c=0.5, body_parts=True, frame_prep=True)
+    opt = bench.path_options(a)
+    assert opt["pyramid_levels"] == 3 and opt["sigma_c"] == 0.5 and "body_parts" in opt and "frame_prep" in opt
+    # packing + contour flags + column pass + row pass, then per level a box
+    # mean where the factor exceeds 1 and two blur passes
+    assert bench.frame_prep_kernels(0) == 4
+    assert bench.frame_prep_kernels(1) == 6          # the finest level: two blur passes
+    assert bench.frame_prep_kernels(3) == 4 + 3 + 3 + 2
