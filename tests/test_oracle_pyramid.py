@@ -13,7 +13,8 @@ use in oracle.nonrigid / oracle.surface):
 * the per-iteration level schedule;
 * the Jacobian at every level against central finite differences on an
   affine image, and a planted mistake (the 1/d gradient scale dropped) that
-  the same check catches.
+  the same check catches;
+* the finest level without blur reproduces the raw-image path exactly.
 """
 import copy
 
@@ -166,3 +167,19 @@ def test_raw_image_path_unchanged(tiny_scene, tiny_graph):
     b = nr.solve_scene(tiny_scene, graph=tiny_graph, n_gn=2, n_pcg=3, pyr_levels=3)
     assert b["problem"].level == 2
     assert a["hist"][0]["energy"] != b["hist"][0]["energy"]
+
+
+def test_finest_level_without_blur_is_the_raw_image(tiny_problem):
+    """Factor 1 and one tap: level 2 is the frame itself, so sampling it
+    reproduces the raw-image path exactly (values and gradients)."""
+    Q = copy.copy(tiny_problem)
+    Q.pyr_ksize = (15, 9, 1)
+    rng = np.random.default_rng(3)
+    u = rng.uniform(0, Q.W - 1, 300)
+    w = rng.uniform(0, Q.H - 1, 300)
+    Q.level = None
+    I0, G0 = nr.photo_sample(Q, u, w, grad=True)
+    Q.level = 2
+    I2, G2 = nr.photo_sample(Q, u, w, grad=True)
+    assert np.array_equal(I0, I2) and np.array_equal(G0, G2)
+    assert np.array_equal(pyr.level_image(Q.rgb, 2, Q.pyr_ksize), Q.rgb)
