@@ -73,10 +73,11 @@ typedef struct {
                            iterations of a Gauss-Newton step when the capture's
                            per-CTA data fits in shared memory, else one launch
                            per PCG phase; 1: one launch per PCG phase (J^T J p,
-                           vector updates); 2: one grid-persistent cooperative
-                           kernel over the GPU (four grid barriers per
-                           iteration: slower than 1 on GB300, kept for
-                           comparison) */
+                           vector updates).  Either way the PCG vectors, the
+                           J^T J p products and the dot products are carried as
+                           compensated FP32 pairs (about 48 significant bits):
+                           its iterate matches an FP64 CG on the FP32 operator
+                           to ~1e-8 relative */
     float target_energy; /* 0 (default): run all n_gn steps.  > 0: the non-rigid
                            solve stops at the first step whose linearisation
                            energy is <= target_energy (the remaining steps are

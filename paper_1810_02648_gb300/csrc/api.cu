@@ -160,11 +160,7 @@ extern "C" lc_status lc_create(lc_ctx** out, int device, void* cuda_stream) {
     c->hC.counters = (unsigned*)c->alloc(sizeof(unsigned) * CNT_N);
     c->hC.hist = (double*)c->alloc(sizeof(double) * 2 * (LC_MAX_GN + 1));
     c->hC.hist_iters = (int*)c->alloc(sizeof(int) * (LC_MAX_GN + 2));
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
-    c->grid_pcg_ok = coop != 0;
-    c->grid_part = (float*)c->alloc(sizeof(float) * 2 * std::max(pcg_grid_max_ctas(), 1));
-    if (!c->dC || !c->hC.sc || !c->hC.counters || !c->hC.hist || !c->hC.hist_iters || !c->grid_part) {
+    if (!c->dC || !c->hC.sc || !c->hC.counters || !c->hC.hist || !c->hC.hist_iters) {
         lc_destroy(c);
         return LC_ERR_OOM;
     }
@@ -221,7 +217,7 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)
             return ctx->fail(LC_ERR_ARG, "lc_set_params: pyr_ksize must be odd, 1..%d", kPyrMaxTaps);
     cudaSetDevice(ctx->device);
-    if (p->pcg_kernel < 0 || p->pcg_kernel > 2) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0, 1 or 2");
+    if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
         p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
@@ -361,6 +357,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
     C.HB = (float4*)ctx->alloc(sizeof(float4) * N);
     C.ev = (float4*)ctx->alloc(sizeof(float4) * N);
     C.q = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.q_lo = (float4*)ctx->alloc(sizeof(float4) * N);
     if (!ctx->err.empty()) return LC_ERR_OOM;
     C.base = ctx->base_buf;
     cudaStream_t st = ctx->stream;
@@ -400,13 +397,17 @@ void lc_ctx::free_graph() {
     void* bufs[] = {(void*)hC.node_vid, (void*)hC.bind_idx, (void*)hC.bind_w, (void*)hC.node_g, (void*)hC.ent_off,
                     (void*)hC.ent, (void*)hC.edge_off, (void*)hC.edge_dst, (void*)hC.edge_s, hC.node_R, hC.node_t,
                     hC.vA, hC.eA, hC.dB,
-                    hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2};
+                    hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2,
+                    hC.x_lo, hC.r_lo, hC.z_lo, hC.p_lo, hC.Ap_lo};
+    release_pcg_tables();
     for (void* p : bufs) release(p);
     hC.node_vid = nullptr; hC.bind_idx = nullptr; hC.bind_w = nullptr; hC.node_g = nullptr;
     hC.ent_off = nullptr; hC.ent = nullptr; hC.edge_off = nullptr; hC.edge_dst = nullptr; hC.edge_s = nullptr;
     hC.node_R = nullptr; hC.node_t = nullptr;
     hC.vA = hC.eA = hC.dB = nullptr;
     hC.b = hC.minv = hC.diag = hC.x = hC.r = hC.z = hC.p = hC.Ap = nullptr;
+    hC.x_lo = hC.r_lo = hC.z_lo = hC.p_lo = hC.Ap_lo = nullptr;
+    pcg_part = lc::PcgPartition();
     tmp_vec = tmp_vec2 = nullptr;
     pcg_plan_ok = false;
     hC.n = 0;
@@ -423,13 +424,13 @@ void lc_ctx::free_template() {
     pose_release();
     surface_release();
     void* bufs[] = {tpl, base_buf, (void*)hC.albedo, (void*)hC.tris, (void*)hC.vt_off, (void*)hC.vt_tri,
-                    (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q};
+                    (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q, hC.q_lo};
     for (void* p : bufs) release(p);
     tpl = base_buf = nullptr;
     material = nullptr;
     hC.base = nullptr; hC.albedo = nullptr; hC.tris = nullptr; hC.vt_off = nullptr; hC.vt_tri = nullptr;
     hC.medges = nullptr; hC.flags = nullptr; hC.vw = nullptr; hC.uv = nullptr; hC.res = nullptr;
-    hC.HA = hC.HB = hC.ev = hC.q = nullptr;
+    hC.HA = hC.HB = hC.ev = hC.q = hC.q_lo = nullptr;
     hC.N = hC.F = hC.n_medges = 0;
     has_template = false;
 }
@@ -437,6 +438,64 @@ void lc_ctx::free_template() {
 // ---------------------------------------------------------------------------
 // graph
 // ---------------------------------------------------------------------------
+void lc_ctx::release_pcg_tables() {
+    void* bufs[] = {(void*)hC.pcg_perm, (void*)hC.pcg_leaf_off, (void*)hC.pcg_leaf,
+                    (void*)hC.pcg_loc_off[0], (void*)hC.pcg_loc_vid[0], (void*)hC.pcg_eus_off[0], (void*)hC.pcg_ent_us[0],
+                    (void*)hC.pcg_loc_off[1], (void*)hC.pcg_loc_vid[1], (void*)hC.pcg_eus_off[1], (void*)hC.pcg_ent_us[1]};
+    for (void* p : bufs) release(p);
+    hC.pcg_perm = nullptr;
+    hC.pcg_leaf_off = nullptr;
+    hC.pcg_leaf = nullptr;
+    for (int ti = 0; ti < 2; ++ti) {
+        hC.pcg_loc_off[ti] = nullptr;
+        hC.pcg_loc_vid[ti] = nullptr;
+        hC.pcg_eus_off[ti] = nullptr;
+        hC.pcg_ent_us[ti] = nullptr;
+    }
+}
+
+// Spatial partition of the graph's nodes (host, from the node positions,
+// bindings and CSR), its per-CTA tables uploaded to the device, and the
+// cluster PCG plan.
+lc_status lc_ctx::plan_pcg() {
+    CapDesc& C = hC;
+    const int n = C.n, N = C.N, K = C.K;
+    std::vector<int> eo(n + 1), go(n + 1), bi((size_t)N * K);
+    std::vector<float4> g(n);
+    lc_status s;
+    if ((s = copy_to_host(eo.data(), C.ent_off, sizeof(int) * (n + 1))) ||
+        (s = copy_to_host(go.data(), C.edge_off, sizeof(int) * (n + 1))) ||
+        (s = copy_to_host(bi.data(), C.bind_idx, sizeof(int) * (size_t)N * K)) ||
+        (s = copy_to_host(g.data(), C.node_g, sizeof(float4) * n)))
+        return s;
+    std::vector<int2> en((size_t)std::max(eo[n], 1));
+    if ((s = copy_to_host(en.data(), C.ent, sizeof(int2) * (size_t)eo[n]))) return s;
+    spatial_partition(n, N, K, g.data(), eo.data(), en.data(), go.data(), bi.data(), pcg_part);
+    release_pcg_tables();
+    // upload one host array into a fresh device buffer
+    auto put = [&](const void* src, size_t bytes) -> void* {
+        void* d = alloc(std::max<size_t>(bytes, 16));
+        if (d && bytes) cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, stream);
+        return d;
+    };
+    C.pcg_perm = (const int*)put(pcg_part.perm.data(), sizeof(int) * n);
+    C.pcg_leaf_off = (const int*)put(pcg_part.leaf_off.data(), sizeof(int) * (kPcgLeaves + 1));
+    C.pcg_leaf = (const uint8_t*)put(pcg_part.leaf.data(), n);
+    bool ok = C.pcg_perm && C.pcg_leaf_off && C.pcg_leaf;
+    for (int ti = 0; ti < 2; ++ti) {
+        C.pcg_loc_off[ti] = (const int*)put(pcg_part.loc_off[ti].data(), sizeof(int) * pcg_part.loc_off[ti].size());
+        C.pcg_loc_vid[ti] = (const int*)put(pcg_part.loc_vid[ti].data(), sizeof(int) * pcg_part.loc_vid[ti].size());
+        C.pcg_eus_off[ti] = (const int*)put(pcg_part.eus_off[ti].data(), sizeof(int) * pcg_part.eus_off[ti].size());
+        C.pcg_ent_us[ti] = (const unsigned*)put(pcg_part.ent_us[ti].data(), sizeof(unsigned) * pcg_part.ent_us[ti].size());
+        ok = ok && C.pcg_loc_off[ti] && C.pcg_loc_vid[ti] && C.pcg_eus_off[ti] && C.pcg_ent_us[ti];
+    }
+    if (!ok) return fail(LC_ERR_OOM, "plan_pcg: device allocation failed");
+    if ((s = cuda(cudaStreamSynchronize(stream), "upload"))) return s;
+    pcg_plan_ok = plan_pcg_cluster(pcg_part, n, K, &pcg_plan);
+    cudaGetLastError();
+    return LC_OK;
+}
+
 extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     if (!ctx) return LC_ERR_ARG;
     if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_build_graph: no template");
@@ -459,7 +518,8 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     C.edge_off = (const int*)ctx->alloc(sizeof(int) * (n + 1));
     C.node_R = (float4*)ctx->alloc(sizeof(float4) * 3 * n);
     C.node_t = (float4*)ctx->alloc(sizeof(float4) * n);
-    float4** vecs[] = {&C.b, &C.minv, &C.diag, &C.x, &C.r, &C.z, &C.p, &C.Ap, &ctx->tmp_vec, &ctx->tmp_vec2};
+    float4** vecs[] = {&C.b, &C.minv, &C.diag, &C.x, &C.r, &C.z, &C.p, &C.Ap, &ctx->tmp_vec, &ctx->tmp_vec2,
+                       &C.x_lo, &C.r_lo, &C.z_lo, &C.p_lo, &C.Ap_lo};
     for (float4** v : vecs) *v = (float4*)ctx->alloc(sizeof(float4) * 2 * n);
     GraphScratch gs;
     std::vector<void*> scratch;
@@ -527,14 +587,7 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     s = ctx->cuda(cudaStreamSynchronize(st), "graph build");
     cleanup();
     if (s != LC_OK) return s;
-    {
-        std::vector<int> eo(n + 1), go(n + 1);
-        if ((s = ctx->copy_to_host(eo.data(), C.ent_off, sizeof(int) * (n + 1))) ||
-            (s = ctx->copy_to_host(go.data(), C.edge_off, sizeof(int) * (n + 1))))
-            return s;
-        ctx->pcg_plan_ok = plan_pcg_cluster(n, K, eo.data(), go.data(), &ctx->pcg_plan);
-        cudaGetLastError();
-    }
+    if ((s = ctx->plan_pcg())) return s;
     ctx->ensure_partials();
     ctx->has_graph = true;
     ctx->drop_graph();
@@ -814,18 +867,12 @@ void lc_ctx::enqueue_pcg() {
         launch_pcg_cluster(dC, pcg_plan, hC.K, params.n_pcg, stream);
         return;
     }
-    if (use_grid_pcg()) {
-        mark(LC_PH_PCG);
-        launch_jtj_stage(dC, hC, stream);
-        launch_pcg_grid(dC, hC.K, params.n_pcg, grid_part, stream);
-        return;
-    }
     mark(LC_PH_PCG_INIT);
     launch_jtj_stage(dC, hC, stream);
     launch_pcg_init(dC, hC, stream);
     for (int it = 0; it < params.n_pcg; ++it) {
         mark(LC_PH_JTJ);
-        launch_jtj(dC, hC, hC.p, hC.Ap, true, stream);
+        launch_jtj(dC, hC, nullptr, nullptr, nullptr, nullptr, true, stream);
         mark(LC_PH_PCG_VEC);
         launch_pcg_vectors(dC, hC, stream);
     }
@@ -904,6 +951,10 @@ lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn, bool surface) {
     if ((s = copy_to_host(&sc, hC.sc, sizeof(Scalars))) || (s = copy_to_host(hist.data(), hC.hist, sizeof(double) * hist.size())) ||
         (s = copy_to_host(it.data(), hC.hist_iters, sizeof(int) * it.size())))
         return s;
+    if (sc.status & kDevErrCapacity) {
+        cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, status), 0, sizeof(int), stream);
+        return fail(LC_ERR_NUMERIC, "internal: the cluster PCG's staging exceeded its planned capacity");
+    }
     memset(stats, 0, sizeof(*stats));
     stats->e_photo = sc.e_lin[0];
     stats->e_sil = sc.e_lin[1];
@@ -1188,7 +1239,7 @@ extern "C" lc_status lc_apply_jtj(lc_ctx* ctx, const float* p, float* out) {
         return s;
     launch_pack_vec(ctx->tmp_out(), ctx->tmp_vec, n, ctx->stream);
     launch_jtj_stage(ctx->dC, ctx->hC, ctx->stream);
-    launch_jtj(ctx->dC, ctx->hC, ctx->tmp_vec, ctx->tmp_vec2, false, ctx->stream);
+    launch_jtj(ctx->dC, ctx->hC, ctx->tmp_vec, nullptr, ctx->tmp_vec2, nullptr, false, ctx->stream);
     if ((s = ctx->cuda(cudaGetLastError(), "jtj"))) return s;
     return ctx->vec_out(out, ctx->tmp_vec2);
 }

@@ -87,7 +87,6 @@ struct lc_batch {
     std::vector<BatchGroup> groups;   // captures on the cluster PCG
     int mode = LC_BATCH_PCG_AUTO;
     int first_multi = 0;              // first slot on the per-iteration / grid PCG
-    bool grid_multi = false;          // the non-cluster members all use the grid-persistent PCG
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
     bool gexec_identity = false;
@@ -123,7 +122,6 @@ lc_status lc_batch::build() {
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::vector<int> cl_of(count, 0);
-    std::vector<std::vector<int>> eo(count), go(count);
     for (int i = 0; i < count; ++i) {
         lc_ctx* c = ctxs[i];
         int cl = 0;
@@ -131,25 +129,13 @@ lc_status lc_batch::build() {
         if (mode == LC_BATCH_PCG_CLUSTER8 || mode == LC_BATCH_PCG_CLUSTER16) {
             const int want = mode == LC_BATCH_PCG_CLUSTER8 ? 8 : 16;
             const int n = c->hC.n;
-            eo[i].resize(n + 1);
-            go[i].resize(n + 1);
-            cudaMemcpy(eo[i].data(), c->hC.ent_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
-            cudaMemcpy(go[i].data(), c->hC.edge_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
-            const int* e0 = eo[i].data();
-            const int* g0 = go[i].data();
+            const PcgPartition* pp = &c->pcg_part;
             PcgPlan pl;
-            if (plan_pcg_cluster_group(want, &n, c->hC.K, &e0, &g0, 1, &pl)) cl = want;
+            if (plan_pcg_cluster_group(want, &pp, &n, c->hC.K, 1, &pl)) cl = want;
         }
         cl_of[i] = cl;
-        if (cl && eo[i].empty()) {
-            const int n = c->hC.n;
-            eo[i].resize(n + 1);
-            go[i].resize(n + 1);
-            cudaMemcpy(eo[i].data(), c->hC.ent_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
-            cudaMemcpy(go[i].data(), c->hC.edge_off, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost);
-        }
     }
-    if (cudaGetLastError() != cudaSuccess) return fail(LC_ERR_CUDA, "lc_batch: reading the graphs");
+    cudaGetLastError();
     // slot order: cluster captures by (cl, K, n), then the rest
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const bool ca = cl_of[a] != 0, cb = cl_of[b] != 0;
@@ -166,17 +152,17 @@ lc_status lc_batch::build() {
         g.K = ctxs[order[s]]->hC.K;
         const int cl = cl_of[order[s]];
         std::vector<int> ns;
-        std::vector<const int*> es, gs;
+        std::vector<const PcgPartition*> ps;
         int e = s;
         PcgPlan best{};
         while (e < count && cl_of[order[e]] == cl && ctxs[order[e]]->hC.K == g.K) {
             const int i = order[e];
             ns.push_back(ctxs[i]->hC.n);
-            es.push_back(eo[i].data());
-            gs.push_back(go[i].data());
+            ps.push_back(&ctxs[i]->pcg_part);
             PcgPlan pl;
-            if (!plan_pcg_cluster_group(cl, ns.data(), g.K, es.data(), gs.data(), (int)ns.size(), &pl)) {
+            if (!plan_pcg_cluster_group(cl, ps.data(), ns.data(), g.K, (int)ns.size(), &pl)) {
                 ns.pop_back();
+                ps.pop_back();
                 break;
             }
             best = pl;
@@ -189,8 +175,6 @@ lc_status lc_batch::build() {
         s = e;
     }
     first_multi = s;
-    grid_multi = mode != LC_BATCH_PCG_PER_ITERATION && first_multi < count;
-    for (int j = first_multi; j < count; ++j) grid_multi = grid_multi && ctxs[order[j]]->use_grid_pcg();
     slot_of.assign(count, 0);
     ctx_of.assign(count, 0);
     snap.resize(count);
@@ -261,16 +245,10 @@ void lc_batch::enqueue(bool from_identity) {
             launch_pcg_cluster(dC + g.first, g.plan, g.K, n_pcg, st, g.count);
         if (multi.vec) {
             launch_jtj_stage(dC, multi, st);
-            if (!grid_multi) {
-                launch_pcg_init(dC, multi, st);
-                for (int it = 0; it < n_pcg; ++it) {
-                    launch_jtj(dC, multi, nullptr, nullptr, true, st);
-                    launch_pcg_vectors(dC, multi, st);
-                }
-            } else {
-                // members that asked for the grid-persistent PCG (pcg_kernel 2), one at a time
-                for (int j = first_multi; j < (int)snap.size(); ++j)
-                    launch_pcg_grid(dC + j, snap[j].K, n_pcg, ctxs[ctx_of[j]]->grid_part, st);
+            launch_pcg_init(dC, multi, st);
+            for (int it = 0; it < n_pcg; ++it) {
+                launch_jtj(dC, multi, nullptr, nullptr, nullptr, nullptr, true, st);
+                launch_pcg_vectors(dC, multi, st);
             }
         }
         launch_update(dC, all, gn, st);
@@ -476,7 +454,7 @@ extern "C" lc_status lc_batch_apply_jtj(lc_batch* b, int stage) {
     if (!b->solved) return b->fail(LC_ERR_STATE, "lc_batch_apply_jtj: no batch solve yet");
     cudaSetDevice(b->device);
     if (stage) launch_jtj_stage(b->dC, b->all, b->stream);
-    launch_jtj(b->dC, b->all, nullptr, nullptr, false, b->stream);
+    launch_jtj(b->dC, b->all, nullptr, nullptr, nullptr, nullptr, false, b->stream);
     if (cudaGetLastError() != cudaSuccess) return b->fail(LC_ERR_CUDA, "lc_batch_apply_jtj: launch");
     return LC_OK;
 }

@@ -52,11 +52,11 @@ struct lc_ctx {
     int tmp6_cap = 0;
     int part_cap = 0;
     lc::PcgPlan pcg_plan{};
+    lc::PcgPartition pcg_part;    // spatial node partition (host copy)
     bool pcg_plan_ok = false;     // the cluster-persistent PCG fits this capture
     bool use_cluster_pcg() const { return pcg_plan_ok && params.pcg_kernel == 0; }
-    float* grid_part = nullptr;   // partial sums of the grid-persistent PCG
-    bool grid_pcg_ok = false;     // the device supports cooperative launches
-    bool use_grid_pcg() const { return grid_pcg_ok && params.pcg_kernel == 2; }
+    lc_status plan_pcg();         // partition + plan for the current graph
+    void release_pcg_tables();
     void enqueue_pcg();
     PoseState* pose = nullptr;
     WarmState* warm = nullptr;    // learned warm start (warmstart.cu)

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "livecap.h"
@@ -47,9 +48,14 @@ struct Scalars {
     int gn_stop;       // the solve reached its target energy: later GN steps are skipped
     int gn_done;       // GN updates made in the current solve (gn_stop, gn_done are reset together)
     int vis_frozen;    // keep the frame decisions (V, B) of the start for the next solve
-    float alpha, beta_f;   // PCG step lengths in FP32 (FP64 sums divided in FP32)
+    float alpha_h, alpha_l;   // graph-stage PCG step length alpha as a compensated FP32 pair
+    float beta_h, beta_l;     // graph-stage PCG direction update beta as a pair
+    float alpha, beta_f;      // surface-stage PCG step lengths (FP64 sums divided in FP32)
     double e_reg[4];       // surface stage: smooth, edge, velocity, acceleration
 };
+
+// Bits of Scalars::status.
+constexpr int kDevErrCapacity = 1;   // the cluster PCG's staging exceeded its planned capacity
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
 // the per-tile partials in a fixed order (deterministic, no float atomics).
@@ -115,9 +121,31 @@ struct CapDesc {
     float4* z;
     float4* p;
     float4* Ap;
-    float4* q;               // per-vertex H_i dv_i scratch (N)
+    // low parts of the compensated FP32 pairs of the per-iteration PCG
+    // (fpair.cuh): the vector is hi + lo
+    float4* x_lo;
+    float4* r_lo;
+    float4* z_lo;
+    float4* p_lo;
+    float4* Ap_lo;
+    float4* q;               // per-vertex H_i dv_i scratch (N), high part
+    float4* q_lo;            // its low part
+    // spatial node partition of the cluster PCG (kPcgLeaves leaves; a
+    // cluster of cl CTAs gives CTA r the leaves r*L/cl .. (r+1)*L/cl - 1)
+    const int* pcg_perm;      // n nodes in leaf order
+    const int* pcg_leaf_off;  // kPcgLeaves + 1 offsets into pcg_perm
+    const uint8_t* pcg_leaf;  // n leaf of every node
+    // per cluster size (index 0: 8 CTAs, 1: 16 CTAs), fixed per graph:
+    // CTA r's local vertices (bound to an owned node, ascending id) are
+    // pcg_loc_vid[pcg_loc_off[r] ..), and the CSR entries of its owned nodes
+    // (owned nodes in pcg_perm order, each node's entries in CSR order) are
+    // pcg_ent_us[pcg_eus_off[r] ..) as (local vertex | slot << 16)
+    const int* pcg_loc_off[2];
+    const int* pcg_loc_vid[2];
+    const int* pcg_eus_off[2];
+    const unsigned* pcg_ent_us[2];
     // operands of the per-iteration J^T J p, staged once per linearisation
-    float4* vA;              // N*K: (R_k (v_i - g_k), w_is) per binding, 0 weight for inactive vertices
+    float4* vA;              // N*K: (w_is R_k (v_i - g_k), w_is) per binding, zero for inactive vertices
     float4* eA;              // N*K: the same per node -> vertex CSR entry
     float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)
     // per-vertex surface stage (unknowns V)
@@ -413,11 +441,13 @@ void launch_rhs(const CapDesc* dC, const Tiles& T, int slot, bool energy_only, c
 // (once per linearisation; node parameters and activity must be current)
 void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st);
-// p / out null: each capture's own p and Ap
-void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st);
+// J^T J p in compensated pairs: p (+ p_lo, nullable) -> out (+ out_lo,
+// nullable: the low part is dropped); p / out null: each capture's own p and Ap
+void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const float4* p_lo, float4* out,
+                float4* out_lo, bool dot, cudaStream_t st);
 // K: the captures' common K selects an unrolled vertex phase (0: any K)
-void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st,
-                int K = 0);
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
+                float4* out_lo, bool dot, cudaStream_t st, int K = 0);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
@@ -446,24 +476,42 @@ SurfCluster plan_surface_cluster(int vert_tiles);
 cudaError_t launch_surface_pcg_cluster(const CapDesc* dC, SurfCluster shape, int n_pcg, cudaStream_t st);
 
 // cluster-persistent PCG (pcg_cluster.cu)
+constexpr int kPcgLeaves = 16;
+// Spatial partition of a capture's nodes into kPcgLeaves leaves (recursive
+// coordinate bisection of the node positions, balanced by CSR entries and
+// edges), and the per-CTA capacities it implies for clusters of 1, 2, 4, 8
+// and 16 CTAs (index log2 cl).
+struct PcgPartition {
+    std::vector<int> perm;
+    std::vector<int> leaf_off;
+    std::vector<uint8_t> leaf;
+    // clusters of 8 and 16 CTAs (index 0, 1): local vertex lists and entry
+    // tables (CapDesc::pcg_loc_* / pcg_ent_us)
+    std::vector<int> loc_off[2], loc_vid[2], eus_off[2];
+    std::vector<unsigned> ent_us[2];
+    int cap_n[5] = {0, 0, 0, 0, 0};   // owned nodes
+    int cap_e[5] = {0, 0, 0, 0, 0};   // CSR entries of the owned nodes
+    int cap_d[5] = {0, 0, 0, 0, 0};   // directed edges of the owned nodes
+    int cap_v[5] = {0, 0, 0, 0, 0};   // distinct vertices bound to an owned node
+};
+constexpr int kPcgMinCluster = 8;   // the cluster PCG runs 8 or 16 CTAs per capture
+void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off, const int2* ent,
+                       const int* edge_off, const int* bind_idx, PcgPartition& out);
 struct PcgPlan {
     int cl;          // CTAs per cluster
+    int cap_v;       // local-vertex capacity per CTA
     int cap_e;       // CSR-entry capacity per CTA
     int cap_d;       // node-edge capacity per CTA
     int cap_n;       // owned-node capacity per CTA
     size_t smem;     // dynamic shared memory bytes
 };
-bool plan_pcg_cluster(int n, int K, const int* ent_off_host, const int* edge_off_host, PcgPlan* out);
-// grid-persistent PCG of capture 0 of dC (cooperative launch over the GPU);
-// part holds 2 * pcg_grid_max_ctas() floats
-int pcg_grid_max_ctas();
-cudaError_t launch_pcg_grid(const CapDesc* dC, int K, int n_pcg, float* part, cudaStream_t st);
+bool plan_pcg_cluster(const PcgPartition& part, int n, int K, PcgPlan* out);
 // one cluster per capture: captures 0 .. ncap-1 of dC, all fitting the plan
 cudaError_t launch_pcg_cluster(const CapDesc* dC, const PcgPlan& pl, int K, int n_pcg, cudaStream_t st, int ncap = 1);
-// a plan that fits every capture of a group (same K): per-CTA capacities are
-// the maxima over the captures, shared memory sized for the largest n
-bool plan_pcg_cluster_group(int cl, const int* n, int K, const int* const* ent_off_host,
-                            const int* const* edge_off_host, int count, PcgPlan* out);
+// a plan of cl CTAs that fits every capture of a group (same K): per-CTA
+// capacities are the maxima over the captures, shared memory sized for the
+// largest n
+bool plan_pcg_cluster_group(int cl, const PcgPartition* const* parts, const int* n, int K, int count, PcgPlan* out);
 
 // graph construction
 struct GraphScratch {

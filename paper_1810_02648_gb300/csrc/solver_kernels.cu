@@ -19,6 +19,7 @@
 
 #include <cooperative_groups.h>
 
+#include "jtj_pair.cuh"
 #include "lc_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -307,13 +308,17 @@ void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only
 }
 
 // ---------------------------------------------------------------------------
-// J^T J p: vertex phase (q_i = H_i dv_i), node phase (gather + ARAP).
+// J^T J p: vertex phase (q_i = H_i dv_i), node phase (gather + ARAP), in
+// compensated FP32 pairs (jtj_pair.cuh) on FP32 operator data.
 //
-// The rotated offsets a_is = R_k (v_i - g_k) of every binding, of every node
-// -> vertex entry, and of every node edge do not change during the PCG, so
-// they are staged once per linearisation (the kernels below); the PCG's
-// J^T J p then reads them coalesced instead of gathering node rotations and
-// positions, and skips inactive vertices without touching them.
+// The staged coefficients (c_is = w_is R_k (v_i - g_k), w_is) of every
+// binding, of every node -> vertex entry, and the rotated offsets of every
+// node edge do not change during the PCG, so they are staged once per
+// linearisation (the kernels below); the PCG's J^T J p then reads them
+// coalesced instead of gathering node rotations and positions, and skips
+// inactive vertices without touching them.  Bindings and entries are staged
+// by the same function, so the forward and transposed products use the same
+// bits.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) jtj_stage_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                       const WorkItem* __restrict__ items) {
@@ -324,13 +329,12 @@ __global__ void __launch_bounds__(kVertTile) jtj_stage_vertex_kernel(const CapDe
     const int i = tile * kVertTile + threadIdx.x;
     if (i >= C.N) return;
     const bool active = C.ev[i].w != 0.f;
-    const float3 v = f3(C.base[i]);
+    const float4 v = C.base[i];
     const int K = C.K;
     for (int s = 0; s < K; ++s) {
         const size_t e = (size_t)i * K + s;
         const int k = C.bind_idx[e];
-        const float3 a = mul(load_R(C.node_R, k), v - f3(C.node_g[k]));
-        C.vA[e] = make_float4(a.x, a.y, a.z, active ? C.bind_w[e] : 0.f);
+        C.vA[e] = active ? staged_coef(C.node_R, k, v, C.node_g[k], C.bind_w[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -343,19 +347,18 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const C
     const int lane = threadIdx.x & 31;
     const int k = tile * kNodeTile + (threadIdx.x >> 5);
     if (k >= C.n) return;
-    const Rot R = load_R(C.node_R, k);
-    const float3 g = f3(C.node_g[k]);
+    const float4 g = C.node_g[k];
     for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
         const int2 en = C.ent[j];
         const bool active = C.ev[en.x].w != 0.f;
-        const float3 a = mul(R, f3(C.base[en.x]) - g);
-        C.eA[j] = make_float4(a.x, a.y, a.z, active ? __int_as_float(en.y) : 0.f);
+        C.eA[j] = active ? staged_coef(C.node_R, k, C.base[en.x], g, __int_as_float(en.y))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
         const int l = C.edge_dst[j];
-        const float3 gl = f3(C.node_g[l]);
-        const float3 b = mul(R, gl - g);
-        const float3 bl = mul(load_R(C.node_R, l), g - gl);
+        const float4 gl = C.node_g[l];
+        const float3 b = staged_edge_offset(C.node_R, k, g, gl);
+        const float3 bl = staged_edge_offset(C.node_R, l, gl, g);
         C.dB[2 * j] = make_float4(b.x, b.y, b.z, C.w_arap * C.edge_s[j]);
         C.dB[2 * j + 1] = make_float4(bl.x, bl.y, bl.z, 0.f);
     }
@@ -368,66 +371,68 @@ void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
 void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_jtj_stage(dC, single_tiles(hC), st); }
 
 template <int KT>
-__device__ __forceinline__ float3 vertex_dv(const float4* __restrict__ A, const int* __restrict__ idx,
-                                            const float4* __restrict__ p, int K) {
-    // all K (offset, node) pairs loaded before the p gathers, so the loads of
-    // the slots are in flight together
+__global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
+                                                                const WorkItem* __restrict__ items,
+                                                                const float4* __restrict__ p_in,
+                                                                const float4* __restrict__ p_lo_in, int check_stop) {
+    int cap, tile;
+    decode(items, cap, tile);
+    const CapDesc& C = caps[cap];
+    if (check_stop && (C.sc->stop || C.sc->gn_stop)) return;
+    // null: the capture's PCG direction (both parts)
+    const float4* __restrict__ p = p_in ? p_in : C.p;
+    const float4* __restrict__ p_lo = p_in ? p_lo_in : C.p_lo;
+    const int i = tile * kVertTile + threadIdx.x;
+    if (i >= C.N) return;
+    const int K = C.K;
+    const float4* __restrict__ A = C.vA + (size_t)i * K;
+    if (A[0].w == 0.f) return;   // inactive vertex: no entry of the node phase reads its q
     constexpr int KM = KT > 0 ? KT : kMaxK;
     const int kk = KT > 0 ? KT : K;
+    // all K (coefficient, node) pairs loaded before the p gathers, so the
+    // loads of the slots are in flight together
     float4 a[KM];
     int k[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s)
         if (s < kk) {
             a[s] = A[s];
-            k[s] = idx[s];
+            k[s] = C.bind_idx[(size_t)i * K + s];
         }
-    float3 dv = make_float3(0.f, 0.f, 0.f);
+    fp2acc dv[3];
 #pragma unroll
     for (int s = 0; s < KM; ++s)
-        if (s < kk) {
-            const float3 pw = f3(p[2 * k[s]]), pt = f3(p[2 * k[s] + 1]);
-            dv = dv + a[s].w * (cross3(pw, f3(a[s])) + pt);
-        }
-    return dv;
-}
-
-template <int KT>
-__global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
-                                                                const WorkItem* __restrict__ items,
-                                                                const float4* __restrict__ p_in, int check_stop) {
-    int cap, tile;
-    decode(items, cap, tile);
-    const CapDesc& C = caps[cap];
-    if (check_stop && (C.sc->stop || C.sc->gn_stop)) return;
-    const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's PCG direction
-    const int i = tile * kVertTile + threadIdx.x;
-    if (i >= C.N) return;
-    const int K = C.K;
-    const float4* __restrict__ A = C.vA + (size_t)i * K;
-    if (A[0].w == 0.f) return;   // inactive vertex: no entry of the node phase reads its q
-    const float3 dv = vertex_dv<KT>(A, C.bind_idx + (size_t)i * K, p, K);
-    const float3 q = mulH(C.HA[i], C.HB[i], dv);
-    C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
+        if (s < kk) jtj_slot(a[s], node_pair44(p, p_lo, k[s]), dv);
+    const float4 HA = C.HA[i], HB = C.HB[i];
+    const float h[6] = {HA.x, HA.y, HA.z, HA.w, HB.x, HB.y};
+    const fp2 d[3] = {dv[0].get(), dv[1].get(), dv[2].get()};
+    fp2 q[3];
+    jtj_block(h, d, q);
+    C.q[i] = make_float4(q[0].h, q[1].h, q[2].h, 1.f);
+    C.q_lo[i] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
 }
 
 __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
                                                                     const WorkItem* __restrict__ items,
                                                                     const float4* __restrict__ p_in,
-                                                                    float4* __restrict__ out_in, int dot) {
-    __shared__ float sh[kNodeWarps][1];
+                                                                    const float4* __restrict__ p_lo_in,
+                                                                    float4* __restrict__ out_in,
+                                                                    float4* __restrict__ out_lo_in, int dot) {
+    __shared__ float2 sh[kNodeWarps];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (dot && (C.sc->stop || C.sc->gn_stop)) return;
-    const float4* __restrict__ p = p_in ? p_in : C.p;   // null: the capture's p and Ap
+    // null: the capture's p and Ap (both parts); out_lo null: the low part is dropped
+    const float4* __restrict__ p = p_in ? p_in : C.p;
+    const float4* __restrict__ p_lo = p_in ? p_lo_in : C.p_lo;
     float4* __restrict__ out = out_in ? out_in : C.Ap;
+    float4* __restrict__ out_lo = out_in ? out_lo_in : C.Ap_lo;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = tile * kNodeTile + w;
-    float papf[1] = {0.f};
+    fp2acc pap;
     if (k < C.n) {
-        const float3 pw = f3(p[2 * k]), pt = f3(p[2 * k + 1]);
-        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        fp2acc acc[6];
         // four rounds of the node's entries at a time: their loads are issued
         // together before any result is used
         constexpr int U = 4;
@@ -441,102 +446,120 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
                 a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
                 vi[u] = j < e1 ? C.ent[j].x : 0;
             }
-            float4 q4[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) q4[u] = a[u].w != 0.f ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 qh[U], ql[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float3 q = f3(q4[u]);
-                const float3 c = cross3(f3(a[u]), q);
-                const float wv = a[u].w;
-                acc[0] += wv * c.x; acc[1] += wv * c.y; acc[2] += wv * c.z;
-                acc[3] += wv * q.x; acc[4] += wv * q.y; acc[5] += wv * q.z;
+                const bool on = a[u].w != 0.f;
+                qh[u] = on ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ql[u] = on ? C.q_lo[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (a[u].w == 0.f) continue;
+                const fp2 q[3] = {{qh[u].x, ql[u].x}, {qh[u].y, ql[u].y}, {qh[u].z, ql[u].z}};
+                jtj_entry(a[u], q, acc);
             }
         }
-        for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
-            const int l = C.edge_dst[j];
-            const float4 bk = C.dB[2 * j], bl = C.dB[2 * j + 1];
-            const float c = bk.w;
-            const float3 plw = f3(p[2 * l]), plt = f3(p[2 * l + 1]);
-            const float3 D = cross3(pw, f3(bk)) + pt - plt;
-            const float3 bD = cross3(f3(bk), D);
-            acc[0] += c * bD.x; acc[1] += c * bD.y; acc[2] += c * bD.z;
-            acc[3] += c * D.x; acc[4] += c * D.y; acc[5] += c * D.z;
-            const float3 Dl = cross3(plw, f3(bl)) + plt - pt;
-            acc[3] -= c * Dl.x; acc[4] -= c * Dl.y; acc[5] -= c * Dl.z;
-        }
-        warp_sumf<6>(acc);
+        const NodeP pk = node_pair44(p, p_lo, k);
+        for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32)
+            jtj_edge(C.dB[2 * j], C.dB[2 * j + 1], pk, node_pair44(p, p_lo, C.edge_dst[j]), acc);
+        fp2 t[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[c] = fp2_warp_sum(acc[c].get());
         if (lane == 0) {
-            out[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
-            out[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+            out[2 * k] = make_float4(t[0].h, t[1].h, t[2].h, 0.f);
+            out[2 * k + 1] = make_float4(t[3].h, t[4].h, t[5].h, 0.f);
+            if (out_lo) {
+                out_lo[2 * k] = make_float4(t[0].l, t[1].l, t[2].l, 0.f);
+                out_lo[2 * k + 1] = make_float4(t[3].l, t[4].l, t[5].l, 0.f);
+            }
+            if (dot) {
+                pap.mac(pk.w[0], t[0]); pap.mac(pk.w[1], t[1]); pap.mac(pk.w[2], t[2]);
+                pap.mac(pk.t[0], t[3]); pap.mac(pk.t[1], t[4]); pap.mac(pk.t[2], t[5]);
+            }
         }
-        if (dot && lane == 0)
-            papf[0] = pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
     }
     if (!dot) return;
-    double pap[1];
-    block_sum_f<1, kNodeWarps>(papf, pap, sh);
-    reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, pap, [&](const double (&tot)[1]) {
+    const fp2 tot = block_sum_fp2<kNodeWarps>(pap.get(), sh);
+    const double part[1] = {fp2_to_double(tot)};
+    reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, part, [&](const double (&sum)[1]) {
         Scalars* sc = C.sc;
-        sc->pAp = tot[0];
-        if (!(tot[0] > 0.0)) {
+        sc->pAp = sum[0];
+        if (!(sum[0] > 0.0)) {
             sc->stop = 1;
             sc->breakdown = 1;
         } else {
-            sc->alpha = __fdiv_rn((float)sc->rz, (float)tot[0]);
+            const fp2 alpha = fp2_div(fp2_from_double(sc->rz), fp2_from_double(sum[0]));
+            sc->alpha_h = alpha.h;
+            sc->alpha_l = alpha.l;
         }
     });
 }
 
-void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, float4* out, bool dot, cudaStream_t st, int K) {
+void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
+                float4* out_lo, bool dot, cudaStream_t st, int K) {
     if (K == 4)
-        jtj_vertex_kernel<4><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+        jtj_vertex_kernel<4><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
     else if (K == 8)
-        jtj_vertex_kernel<8><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
+        jtj_vertex_kernel<8><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
     else
-        jtj_vertex_kernel<0><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, dot ? 1 : 0);
-    jtj_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, p, out, dot ? 1 : 0);
+        jtj_vertex_kernel<0><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
+    jtj_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, p, p_lo, out, out_lo, dot ? 1 : 0);
 }
-void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, float4* out, bool dot, cudaStream_t st) {
-    launch_jtj(dC, single_tiles(hC), p, out, dot, st, hC.K);
+void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const float4* p_lo, float4* out,
+                float4* out_lo, bool dot, cudaStream_t st) {
+    launch_jtj(dC, single_tiles(hC), p, p_lo, out, out_lo, dot, st, hC.K);
 }
 
 // ---------------------------------------------------------------------------
-// PCG vector kernels (node-parallel, 2 float4 per node, FP64 dots).
+// PCG vector kernels (node-parallel, 2 float4 per node for each part of a
+// pair; dot products as pairs per tile, FP64 across tiles).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
-__device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
-__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
-    return make_float4(y.x + a * x.x, y.y + a * x.y, y.z + a * x.z, y.w + a * x.w);
+
+// the three components of element j of a pair vector
+__device__ __forceinline__ void load_pair3(const float4* hi, const float4* lo, int j, fp2 (&v)[3]) {
+    const float4 h = hi[j], l = lo[j];
+    v[0] = {h.x, l.x};
+    v[1] = {h.y, l.y};
+    v[2] = {h.z, l.z};
+}
+__device__ __forceinline__ void store_pair3(float4* hi, float4* lo, int j, const fp2 (&v)[3]) {
+    hi[j] = make_float4(v[0].h, v[1].h, v[2].h, 0.f);
+    lo[j] = make_float4(v[0].l, v[1].l, v[2].l, 0.f);
 }
 
 __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items) {
-    __shared__ float sh[kVecThreads / 32][1];
+    __shared__ float2 sh[kVecThreads / 32];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
-    float rzf[1] = {0.f};
+    fp2acc rz;
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
-            const float4 b = C.b[2 * k + h];
-            const float4 z = mul4(C.minv[2 * k + h], b);
-            C.x[2 * k + h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            C.r[2 * k + h] = b;
-            C.z[2 * k + h] = z;
-            C.p[2 * k + h] = z;
-            rzf[0] += dot4(b, z);
+            const int j = 2 * k + h;
+            const float4 b = C.b[j], mi = C.minv[j];
+            const fp2 z[3] = {two_prod(mi.x, b.x), two_prod(mi.y, b.y), two_prod(mi.z, b.z)};
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            C.x[j] = zero;
+            C.x_lo[j] = zero;
+            C.r[j] = make_float4(b.x, b.y, b.z, 0.f);
+            C.r_lo[j] = zero;
+            store_pair3(C.z, C.z_lo, j, z);
+            store_pair3(C.p, C.p_lo, j, z);
+            rz.mac(b.x, z[0]); rz.mac(b.y, z[1]); rz.mac(b.z, z[2]);
         }
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    double rz[1];
-    block_sum_f<1, kVecThreads / 32>(rzf, rz, sh);
-    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
+    const fp2 tot = block_sum_fp2<kVecThreads / 32>(rz.get(), sh);
+    const double part[1] = {fp2_to_double(tot)};
+    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, part, [&](const double (&sum)[1]) {
         Scalars* sc = C.sc;
-        sc->rz = tot[0];
-        sc->stop = tot[0] == 0.0 ? 1 : 0;
+        sc->rz = sum[0];
+        sc->stop = sum[0] == 0.0 ? 1 : 0;
         sc->breakdown = 0;
         sc->iters = 0;
     });
@@ -544,40 +567,52 @@ __global__ void __launch_bounds__(kVecThreads) pcg_init_kernel(const CapDesc* __
 
 __global__ void __launch_bounds__(kVecThreads) pcg_step_kernel(const CapDesc* __restrict__ caps,
                                                                 const WorkItem* __restrict__ items) {
-    __shared__ float sh[kVecThreads / 32][1];
+    __shared__ float2 sh[kVecThreads / 32];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
     if (sc->stop || sc->gn_stop) return;
-    const float alpha = sc->alpha;
+    const fp2 alpha = {sc->alpha_h, sc->alpha_l};
     const int k = tile * kVecThreads + threadIdx.x;
-    float rzf[1] = {0.f};
+    fp2acc rz;
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * k + h;
-            const float4 p = C.p[j];
-            C.x[j] = axpy4(alpha, p, C.x[j]);
-            const float4 r = axpy4(-alpha, C.Ap[j], C.r[j]);
-            const float4 z = mul4(C.minv[j], r);
-            C.r[j] = r;
-            C.z[j] = z;
-            rzf[0] += dot4(r, z);
+            fp2 p[3], x[3], r[3], ap[3], z[3];
+            load_pair3(C.p, C.p_lo, j, p);
+            load_pair3(C.x, C.x_lo, j, x);
+            load_pair3(C.r, C.r_lo, j, r);
+            load_pair3(C.Ap, C.Ap_lo, j, ap);
+            const float4 mi = C.minv[j];
+            const float m[3] = {mi.x, mi.y, mi.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                x[c] = fp2_add(x[c], fp2_mul(alpha, p[c]));
+                r[c] = fp2_sub(r[c], fp2_mul(alpha, ap[c]));
+                z[c] = fp2_scale(m[c], r[c]);
+                rz.mac(r[c], z[c]);
+            }
+            store_pair3(C.x, C.x_lo, j, x);
+            store_pair3(C.r, C.r_lo, j, r);
+            store_pair3(C.z, C.z_lo, j, z);
         }
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    double rz[1];
-    block_sum_f<1, kVecThreads / 32>(rzf, rz, sh);
-    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, rz, [&](const double (&tot)[1]) {
+    const fp2 tot = block_sum_fp2<kVecThreads / 32>(rz.get(), sh);
+    const double part[1] = {fp2_to_double(tot)};
+    reduce_partials<1>(C, CNT_DOT2, tile, ntiles, part, [&](const double (&sum)[1]) {
         sc->iters += 1;
-        sc->rz_new = tot[0];
-        if (tot[0] == 0.0) {
+        sc->rz_new = sum[0];
+        if (sum[0] == 0.0) {
             sc->stop = 1;
         } else {
             // every other tile has read its inputs already (it finished before this one)
-            sc->beta = tot[0] / sc->rz;
-            sc->beta_f = __fdiv_rn((float)tot[0], (float)sc->rz);
-            sc->rz = tot[0];
+            const fp2 beta = fp2_div(fp2_from_double(sum[0]), fp2_from_double(sc->rz));
+            sc->beta_h = beta.h;
+            sc->beta_l = beta.l;
+            sc->beta = sum[0] / sc->rz;
+            sc->rz = sum[0];
         }
     });
 }
@@ -589,12 +624,17 @@ __global__ void __launch_bounds__(kVecThreads) pcg_dir_kernel(const CapDesc* __r
     const CapDesc& C = caps[cap];
     Scalars* sc = C.sc;
     if (sc->stop || sc->gn_stop) return;
-    const float beta = sc->beta_f;
+    const fp2 beta = {sc->beta_h, sc->beta_l};
     const int k = tile * kVecThreads + threadIdx.x;
     if (k < C.n) {
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * k + h;
-            C.p[j] = axpy4(beta, C.p[j], C.z[j]);
+            fp2 p[3], z[3];
+            load_pair3(C.p, C.p_lo, j, p);
+            load_pair3(C.z, C.z_lo, j, z);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p[c] = fp2_add(z[c], fp2_mul(beta, p[c]));
+            store_pair3(C.p, C.p_lo, j, p);
         }
     }
 }
@@ -613,254 +653,21 @@ void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid-persistent PCG: all n_pcg iterations of one Gauss-Newton step in one
-// cooperative launch over the whole GPU, for captures whose data does not fit
-// a cluster's shared memory.  Per iteration: the vertex phase (q_i), a grid
-// barrier, the node phase (A p and the CTA's p.Ap partial), a barrier, every
-// CTA sums the partials in the same fixed order (FP64 across CTAs) for
-// alpha, the vector phase (x, r, z and the r.z partial), a barrier, beta the
-// same way, p = z + beta p, a barrier.  Operands are the staged rotated
-// offsets (jtj_stage_*); vectors live in global memory (L2).
-// ---------------------------------------------------------------------------
-constexpr int kGridThreads = 256;
-
-__device__ __forceinline__ double grid_total(const float* __restrict__ part, int G) {
-    // warp 0: lanes add CTAs lane, lane + 32, ... then a fixed shuffle tree
-    const int lane = threadIdx.x & 31;
-    double v = 0.0;
-    for (int c = lane; c < G; c += 32) v += (double)__ldcg(&part[c]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float block_total_f32(float v, float* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    float t = 0.f;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < kGridThreads / 32; ++i) t += sh[i];
-    return t;   // thread 0
-}
-
-template <int KT>
-__global__ void __launch_bounds__(kGridThreads) pcg_grid_kernel(const CapDesc* __restrict__ caps, int n_pcg,
-                                                                 float* __restrict__ part) {
-    __shared__ float sh[kGridThreads / 32];
-    __shared__ float s_scal[2];   // alpha / beta of this iteration (thread 0 -> block)
-    __shared__ int s_stop;
-    cg::grid_group grid = cg::this_grid();
-    const CapDesc& C = caps[0];
-    if (C.sc->gn_stop) return;   // uniform: read before any barrier
-    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-    const int gtid = b * kGridThreads + tid, gthreads = G * kGridThreads;
-    const int lane = tid & 31, gwarp = gtid >> 5, gwarps = gthreads >> 5;
-    const int n = C.n, N = C.N, K = C.K;
-    float* partA = part;        // G: p.Ap partials
-    float* partB = part + G;    // G: r.z partials
-    // x = 0, r = b, z = M^-1 r, p = z; r.z
-    float rz_p = 0.f;
-    for (int j = gtid; j < 2 * n; j += gthreads) {
-        const float4 bb = C.b[j], mi = C.minv[j];
-        const float4 z = make_float4(mi.x * bb.x, mi.y * bb.y, mi.z * bb.z, 0.f);
-        C.x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        C.r[j] = bb;
-        C.z[j] = z;
-        C.p[j] = z;
-        rz_p += bb.x * z.x + bb.y * z.y + bb.z * z.z;
-    }
-    {
-        const float t = block_total_f32(rz_p, sh);
-        if (tid == 0) partB[b] = t;
-    }
-    grid.sync();
-    double rz = 0.0;
-    if (tid < 32) rz = grid_total(partB, G);
-    if (tid == 0) s_stop = rz == 0.0 ? 1 : 0;
-    __syncthreads();
-    rz = __shfl_sync(0xffffffffu, rz, 0);
-    int iters = 0, breakdown = 0;
-    int stop = s_stop;
-    for (int it = 0; it < n_pcg && !stop; ++it) {
-        // vertex phase: q_i = H_i dv_i for the active vertices
-        for (int i = gtid; i < N; i += gthreads) {
-            const float4* __restrict__ A = C.vA + (size_t)i * K;
-            if (A[0].w == 0.f) continue;
-            const float3 dv = vertex_dv<KT>(A, C.bind_idx + (size_t)i * K, C.p, K);
-            const float3 q = mulH(C.HA[i], C.HB[i], dv);
-            C.q[i] = make_float4(q.x, q.y, q.z, 1.f);
-        }
-        grid.sync();
-        // node phase: (J^T J p)_k, warp per node; p.Ap partial of the CTA
-        float pap = 0.f;
-        for (int k = gwarp; k < n; k += gwarps) {
-            const float3 pw = f3(C.p[2 * k]), pt = f3(C.p[2 * k + 1]);
-            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            constexpr int U = 4;
-            const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
-            for (int jb = e0 + lane; jb < e1; jb += 32 * U) {
-                float4 a[U];
-                int vi[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int j = jb + 32 * u;
-                    a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    vi[u] = j < e1 ? C.ent[j].x : 0;
-                }
-                float4 q4[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) q4[u] = a[u].w != 0.f ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float3 q = f3(q4[u]);
-                    const float3 c = cross3(f3(a[u]), q);
-                    const float wv = a[u].w;
-                    acc[0] += wv * c.x; acc[1] += wv * c.y; acc[2] += wv * c.z;
-                    acc[3] += wv * q.x; acc[4] += wv * q.y; acc[5] += wv * q.z;
-                }
-            }
-            for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
-                const int l = C.edge_dst[j];
-                const float4 bk = C.dB[2 * j], bl = C.dB[2 * j + 1];
-                const float c = bk.w;
-                const float3 plw = f3(C.p[2 * l]), plt = f3(C.p[2 * l + 1]);
-                const float3 D = cross3(pw, f3(bk)) + pt - plt;
-                const float3 bD = cross3(f3(bk), D);
-                acc[0] += c * bD.x; acc[1] += c * bD.y; acc[2] += c * bD.z;
-                acc[3] += c * D.x; acc[4] += c * D.y; acc[5] += c * D.z;
-                const float3 Dl = cross3(plw, f3(bl)) + plt - pt;
-                acc[3] -= c * Dl.x; acc[4] -= c * Dl.y; acc[5] -= c * Dl.z;
-            }
-            warp_sumf<6>(acc);
-            if (lane == 0) {
-                C.Ap[2 * k] = make_float4(acc[0], acc[1], acc[2], 0.f);
-                C.Ap[2 * k + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
-                pap += pw.x * acc[0] + pw.y * acc[1] + pw.z * acc[2] + pt.x * acc[3] + pt.y * acc[4] + pt.z * acc[5];
-            }
-        }
-        {
-            const float t = block_total_f32(pap, sh);
-            if (tid == 0) partA[b] = t;
-        }
-        grid.sync();
-        if (tid < 32) {
-            const double pAp = grid_total(partA, G);
-            if (tid == 0) {
-                if (!(pAp > 0.0)) {
-                    s_stop = 1;
-                } else {
-                    // the step length is applied in FP32: the FP64 sums are divided in FP32
-                    s_scal[0] = __fdiv_rn((float)rz, (float)pAp);
-                    s_stop = 0;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_stop) {
-            stop = 1;
-            breakdown = 1;
-            break;
-        }
-        const float alpha = s_scal[0];
-        // vector phase: x, r, z; r.z partial
-        float rzp = 0.f;
-        for (int j = gtid; j < 2 * n; j += gthreads) {
-            const float4 pp = C.p[j], ap = C.Ap[j], mi = C.minv[j];
-            float4 x = C.x[j], r = C.r[j];
-            x.x += alpha * pp.x; x.y += alpha * pp.y; x.z += alpha * pp.z;
-            r.x -= alpha * ap.x; r.y -= alpha * ap.y; r.z -= alpha * ap.z;
-            const float4 z = make_float4(mi.x * r.x, mi.y * r.y, mi.z * r.z, 0.f);
-            C.x[j] = x;
-            C.r[j] = r;
-            C.z[j] = z;
-            rzp += r.x * z.x + r.y * z.y + r.z * z.z;
-        }
-        {
-            const float t = block_total_f32(rzp, sh);
-            if (tid == 0) partB[b] = t;
-        }
-        grid.sync();
-        ++iters;
-        double rz_new = 0.0;
-        if (tid < 32) {
-            rz_new = grid_total(partB, G);
-            if (tid == 0) {
-                if (rz_new == 0.0) {
-                    s_stop = 1;
-                } else {
-                    s_scal[1] = __fdiv_rn((float)rz_new, (float)rz);
-                    s_stop = 0;
-                }
-            }
-        }
-        __syncthreads();
-        rz = rz_new;   // meaningful in warp 0; only thread 0 reports it
-        if (s_stop) {
-            stop = 1;
-            break;
-        }
-        const float beta = s_scal[1];
-        for (int j = gtid; j < 2 * n; j += gthreads) {
-            const float4 pp = C.p[j], z = C.z[j];
-            C.p[j] = make_float4(z.x + beta * pp.x, z.y + beta * pp.y, z.z + beta * pp.z, 0.f);
-        }
-        grid.sync();
-    }
-    if (b == 0 && tid == 0) {
-        Scalars* sc = C.sc;
-        sc->iters = iters;
-        sc->breakdown = breakdown;
-        sc->stop = stop;
-        sc->rz = rz;
-    }
-}
-
-static int pcg_grid_ctas(const void* kern) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGridThreads, 0);
-    return std::max(1, std::min(2, per_sm) * sms);
-}
-
-int pcg_grid_max_ctas() { return pcg_grid_ctas((const void*)pcg_grid_kernel<0>); }
-
-cudaError_t launch_pcg_grid(const CapDesc* dC, int K, int n_pcg, float* part, cudaStream_t st) {
-    const void* kern = K == 4 ? (const void*)pcg_grid_kernel<4>
-                               : (K == 8 ? (const void*)pcg_grid_kernel<8> : (const void*)pcg_grid_kernel<0>);
-    const int G = pcg_grid_ctas(kern);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(kGridThreads);
-    cfg.stream = st;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeCooperative;
-    attr.val.cooperative = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    if (K == 4) return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<4>, dC, n_pcg, part);
-    if (K == 8) return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<8>, dC, n_pcg, part);
-    return cudaLaunchKernelEx(&cfg, pcg_grid_kernel<0>, dC, n_pcg, part);
-}
-
-// ---------------------------------------------------------------------------
 // Parameter update: R_k <- Exp(d_omega_k) R_k, t_k += d_t_k.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __restrict__ caps,
                                                               const WorkItem* __restrict__ items, int slot) {
-    __shared__ float sh[kVecThreads / 32][1];
+    __shared__ float2 sh[kVecThreads / 32];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (C.sc->gn_stop) return;
     const int k = tile * kVecThreads + threadIdx.x;
-    float s2f[1] = {0.f};
+    fp2acc s2a;   // ||delta||^2 as a pair (exact products)
     if (k < C.n) {
         const float4 xw = C.x[2 * k], xt = C.x[2 * k + 1];
-        s2f[0] = dot4(xw, xw) + dot4(xt, xt);
+        s2a.mac(xw.x, xw.x); s2a.mac(xw.y, xw.y); s2a.mac(xw.z, xw.z);
+        s2a.mac(xt.x, xt.x); s2a.mac(xt.y, xt.y); s2a.mac(xt.z, xt.z);
         const float th2 = xw.x * xw.x + xw.y * xw.y + xw.z * xw.z;
         const float th = sqrtf(th2);
         float A, B;
@@ -890,8 +697,8 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(const CapDesc* __re
         C.node_t[k] = make_float4(t.x + xt.x, t.y + xt.y, t.z + xt.z, 0.f);
     }
     const int ntiles = (C.n + kVecThreads - 1) / kVecThreads;
-    double s2[1];
-    block_sum_f<1, kVecThreads / 32>(s2f, s2, sh);
+    const fp2 s2t = block_sum_fp2<kVecThreads / 32>(s2a.get(), sh);
+    const double s2[1] = {fp2_to_double(s2t)};
     reduce_partials<1>(C, CNT_STEP, tile, ntiles, s2, [&](const double (&tot)[1]) {
         Scalars* sc = C.sc;
         sc->step2 = tot[0];

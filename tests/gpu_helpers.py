@@ -207,6 +207,45 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
     return ref, dE, dV
 
 
+def oracle_cg_spread(A, b, n, rel=1e-14, n_runs=3):
+    """How reproducible the oracle's own n-step PCG is: the FP64 CG rerun with
+    every matrix-vector product perturbed by a relative error of ``rel``
+    (seeded normal), the magnitude of a compensated-FP32 pair product.  On
+    nearly singular systems the n-step iterate is forward unstable: one part
+    in 1e14 per product moves it by up to ~4e-3 at some Gauss-Newton steps of
+    the body solve.  Returns (FP64 iterate, its info, max relative iterate
+    change, max relative change of q(d) = d^T A d / 2 - b^T d)."""
+    from oracle.nonrigid import pcg
+    dref, info = pcg(A, b, n)
+    d = np.asarray(A.diagonal(), dtype=np.float64)
+    minv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    q = lambda v: 0.5 * v @ (A @ v) - b @ v  # noqa: E731
+    q0 = q(dref)
+    s_it = s_q = 0.0
+    for seed in range(n_runs):
+        rng = np.random.default_rng(3000 + seed)
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = minv * r
+        p = z.copy()
+        rz = float(r @ z)
+        for _ in range(info["iters"]):
+            Ap = A @ p
+            Ap = Ap * (1.0 + rel * rng.standard_normal(Ap.shape))
+            al = rz / float(p @ Ap)
+            x = x + al * p
+            r = r - al * Ap
+            z = minv * r
+            rzn = float(r @ z)
+            if rzn == 0.0:
+                break
+            p = z + (rzn / rz) * p
+            rz = rzn
+        s_it = max(s_it, np.linalg.norm(x - dref) / max(np.linalg.norm(dref), 1e-300))
+        s_q = max(s_q, abs(q(x) - q0) / max(abs(q0), 1e-300))
+    return dref, info, s_it, s_q
+
+
 def q_band(A, b, n, n_runs=3):
     """Spread of the quadratic model q(d) = d^T A d / 2 - b^T d at the n-step
     PCG iterate over FP32 executions (``pcg32``), relative to the FP64

@@ -12,12 +12,19 @@ be bit-exact.  Floating-point tolerances (FP32 kernels vs FP64 oracle):
 * J^T F, diag(J^T J), J^T J p per node vector: 1e-4 of the vector's largest
   entry (FP32 accumulation over the node's ~50-200 vertex terms plus the
   FP32-vs-FP64 warp, ~1e-7 relative per term);
-* end to end: final energy relative difference <= 1e-4, vertex positions
-  within 1e-4 x the template's bounding-box diagonal, with few PCG
-  iterations.  With many PCG iterations CG amplifies FP32 rounding along the
-  depth-ambiguous directions of the system (an FP64 solve whose CG is fed
-  FP32-level rounding moves by up to ~4e-3 in energy on the capsule); there
-  the bound is twice that measured spread.
+* PCG (vectors, products and dot products in compensated FP32 pairs on the
+  FP32 operator): the iteration count exact, the quadratic model
+  q(d) = d^T A d / 2 - b^T d within 1e-6, the iterate within 1e-5 after 1
+  iteration and within 1e-4 after 3 and after the configuration's count;
+  after many iterations, or three times the oracle's own change when its
+  FP64 products are perturbed by one part in 1e14 where that is larger
+  (``oracle_cg_spread``: the 40-iteration CG of the body is forward unstable
+  in FP64 at some linearisations).  CG on the FP64 operator and on the same
+  operator rounded to FP32 (exact vector arithmetic) differ by ~3e-6 after
+  20 iterations on the capsule; FP32 CG recurrences instead land ~2e-2 away.
+* end to end, at the configuration's full iteration counts (capsule 5 GN x
+  20 PCG): final energy relative difference <= 1e-4, vertex positions within
+  1e-4 x the template's bounding-box diagonal.
 """
 import numpy as np
 import pytest
@@ -178,35 +185,33 @@ def _lin_case(scene, seed, tag, pcg_kernel=0, pcg_counts=None):
     report(f"normal_eq_{tag}", rhs=d_rhs, diag=d_diag, jtjp=d_Ap)
     assert d_rhs <= 1e-4 and d_diag <= 1e-4 and d_Ap <= 1e-4
 
-    # PCG: the GPU's n_pcg-step solution vs the oracle's on J^T J from the oracle.
-    # CG amplifies FP32 rounding along the system's ill-conditioned directions
-    # (Jacobi-scaled condition number ~1e4 here): an FP32-vector run of the
-    # same algorithm lands ~2e-2 (relative) from the FP64 iterate after 20
-    # steps, while the quadratic model q(d) = d^T A d / 2 - b^T d that CG
-    # minimises agrees to ~4e-5.  So: exact iteration counts, q within 1e-4,
-    # the iterate within 5e-2, and the iterate after 1 and 3 steps (before the
-    # amplification sets in) within 1e-5 and 1e-4.
+    # PCG: the GPU's n_pcg-step solution vs the oracle's on J^T J from the
+    # oracle: exact iteration counts, q within 1e-6, the iterate within 1e-5
+    # after 1 and 3 iterations and 1e-4 after the configuration's count (the
+    # module docstring gives the measured reasons).
     A = (JT @ J).tocsr()
     q = lambda d: 0.5 * d @ (A @ d) - rhs_ref @ d  # noqa: E731
-    counts = pcg_counts or ((1, 1e-5), (3, 1e-4), (scene.n_pcg, 5e-2))
+    from gpu_helpers import oracle_cg_spread
+    counts = pcg_counts or ((1, 1e-5), (3, 1e-4), (scene.n_pcg, 1e-4))
     for n_pcg, tol in counts:
         ctx.set_params(n_pcg=n_pcg)
         delta, iters = ctx.solve_linear()
-        dref, info = onr.pcg(A, rhs_ref, n_pcg)
+        dref, info, s_it, s_q = oracle_cg_spread(A, rhs_ref, n_pcg)
         d_pcg = np.linalg.norm(vec6(delta) - dref) / np.linalg.norm(dref)
         d_q = abs(q(vec6(delta)) - q(dref)) / abs(q(dref))
-        report(f"pcg_{tag}_{n_pcg}", rel=d_pcg, q_rel=d_q, iters=iters, iters_ref=info["iters"])
+        report(f"pcg_{tag}_{n_pcg}", rel=d_pcg, q_rel=d_q, iters=iters, iters_ref=info["iters"],
+               spread_iterate=s_it, spread_q=s_q)
         assert iters == info["iters"]
-        assert d_pcg <= tol and d_q <= 1e-4
+        assert d_pcg <= max(tol, 3 * s_it) and d_q <= max(1e-6, 3 * s_q)
     ctx.close()
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
 def test_linearization_tiny(tiny, pcg_kernel):
     _lin_case(tiny, 11, f"tiny_k{pcg_kernel}", pcg_kernel)
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
 def test_linearization_body(body, pcg_kernel):
     _lin_case(body, 12, f"body_k{pcg_kernel}", pcg_kernel)
 
@@ -218,15 +223,10 @@ def test_linearization_ragged():
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------
-def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
-    """Full solve on the GPU vs the oracle from the same graph.
-
-    strict: final energy within 1e-4 (relative) and vertices within 1e-4 of
-    the bounding-box diagonal.  Otherwise (many PCG iterations on a
-    depth-ambiguous system) the bound is twice the spread of the oracle's own
-    result under FP32 rounding of its CG (``fp32_rounding_band``), or the
-    strict bound if larger."""
-    from gpu_helpers import fp32_rounding_band
+def _e2e(scene, tag, base32=None, n_pcg=None, pcg_kernel=0):
+    """Full solve on the GPU vs the oracle from the same graph: final energy
+    within 1e-4 (relative), vertices within 1e-4 of the bounding-box diagonal,
+    every Gauss-Newton step's energy within 1e-4 of the oracle's."""
     ctx = _ctx(scene, pcg_kernel=pcg_kernel)
     if n_pcg is not None:
         ctx.set_params(n_pcg=n_pcg)
@@ -234,7 +234,7 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
     out = ctx.read_back()
     g = ctx.read_graph()
     graph = graph_from_gpu(g)
-    ref, band_E, band_V = fp32_rounding_band(scene, graph, base32=base32, n_pcg=n_pcg)
+    ref = onr.solve_scene(scene, graph=graph, base32=base32, n_pcg=n_pcg)
     e_gpu, e_ref = stats["e_total"], ref["e1"]["total"]
     rel = abs(e_gpu - e_ref) / abs(e_ref)
     diag = np.linalg.norm(scene.V.max(0) - scene.V.min(0))
@@ -249,18 +249,14 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
     assert stats["pcg_iters"] == [h["pcg_iters"] for h in ref["hist"]]
     report(f"e2e_{tag}", e_gpu=e_gpu, e_ref=e_ref, rel=rel, dv=dv, dv_over_diag=dv / diag,
            cluster=stats["pcg_cluster_size"],
-           band_E_rel=band_E / abs(e_ref), band_V=band_V,
-           hist_rel=np.abs(e_hist - e_hist_ref).max() / e_hist_ref.max(),
+           hist_rel=(np.abs(e_hist - e_hist_ref) / e_hist_ref).max(),
            n_vis=stats["n_visible"], n_B=stats["n_boundary"])
     nb = check_frame_flags(out["flags"], P)
     report(f"e2e_{tag}_flags", bneg_mismatch=nb)
     assert stats["n_visible"] == int(P.vis.sum()) and stats["n_boundary"] == int(P.inB.sum())
-    if strict:
-        assert rel <= 1e-4
-        assert dv <= 1e-4 * diag
-    else:
-        assert abs(e_gpu - e_ref) <= max(1e-4 * abs(e_ref), 2.0 * band_E)
-        assert dv <= max(1e-4 * diag, 2.0 * band_V)
+    assert rel <= 1e-4
+    assert dv <= 1e-4 * diag
+    assert (np.abs(e_hist - e_hist_ref) <= 1e-4 * e_hist_ref).all()
     # replaying the captured solve from the same state is bit-identical
     ctx.set_node_params(None, None)
     stats2 = ctx.solve_nonrigid()
@@ -270,14 +266,15 @@ def _e2e(scene, tag, base32=None, n_pcg=None, strict=True, pcg_kernel=0):
     return stats
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
 def test_end_to_end_tiny_strict(tiny, pcg_kernel):
     _e2e(tiny, f"tiny_pcg3_k{pcg_kernel}", n_pcg=3, pcg_kernel=pcg_kernel)
 
 
-@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
+@pytest.mark.parametrize("pcg_kernel", [0, 1])
 def test_end_to_end_tiny(tiny, pcg_kernel):
-    _e2e(tiny, f"tiny_k{pcg_kernel}", strict=False, pcg_kernel=pcg_kernel)
+    """The capsule configuration at its full counts, 5 GN x 20 PCG."""
+    _e2e(tiny, f"tiny_k{pcg_kernel}", pcg_kernel=pcg_kernel)
 
 
 def test_end_to_end_ragged_strict():
@@ -285,7 +282,7 @@ def test_end_to_end_ragged_strict():
 
 
 def test_end_to_end_ragged():
-    _e2e(_ragged_scene(15, 13, 41, 4, side=90, shift=0.2), "ragged", strict=False)
+    _e2e(_ragged_scene(15, 13, 41, 4, side=90, shift=0.2), "ragged")
 
 
 def test_empty_frame(tiny):
@@ -294,5 +291,5 @@ def test_empty_frame(tiny):
     s.rgb = np.zeros_like(s.rgb)
     s.dt = np.zeros_like(s.dt)
     s.mask = np.zeros_like(s.mask)
-    stats = _e2e(s, "empty", strict=False)
+    stats = _e2e(s, "empty")
     assert stats["n_boundary_neg"] == 0

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_helpers import check_frame_flags, graph_from_gpu, q_band, report, set_flags, vec6
+from gpu_helpers import check_frame_flags, graph_from_gpu, oracle_cg_spread, report, set_flags, vec6
 from oracle import nonrigid as onr
 from oracle import pose as op
 from oracle import visibility as ovis
@@ -114,7 +114,6 @@ def test_body_pipeline_matches_oracle(body):
     steps, with identical b_i), and an FP32 right-hand side carries a
     summation error of ~4e-5 of its largest entry.  The trajectory test below
     checks every step of the full solve on its own instead."""
-    from gpu_helpers import fp32_rounding_band
     ctx = _ctx(body, n_gn=2, n_pcg=3)
     ctx.solve_pose(stats=False)
     ctx.set_node_params(None, None)
@@ -123,18 +122,18 @@ def test_body_pipeline_matches_oracle(body):
     st = ctx.solve_nonrigid()
     out = ctx.read_back()
     graph = graph_from_gpu(ctx.read_graph())
-    ref, band_E, band_V = fp32_rounding_band(body, graph, base32=base, n_gn=2, n_pcg=3, n_runs=2)
+    ref = onr.solve_scene(body, graph=graph, base32=base, n_gn=2, n_pcg=3)
     rel = abs(st["e_total"] - ref["e1"]["total"]) / ref["e1"]["total"]
     diag = np.linalg.norm(body.V.max(0) - body.V.min(0))
     dv = np.abs(out["V"] - ref["v"]).max()
     nb = check_frame_flags(out["flags"], ref["problem"])
     hist = np.array(st["e_gn"])
     hist_ref = np.array([h["energy"] for h in ref["hist"]])
-    report("body_pipeline_gn2_pcg3", rel=rel, dv_over_diag=dv / diag, band_E_rel=band_E / ref["e1"]["total"],
+    report("body_pipeline_gn2_pcg3", rel=rel, dv_over_diag=dv / diag,
            e_gpu=st["e_total"], e_ref=ref["e1"]["total"], bneg_mismatch=nb,
            hist_rel=np.abs(hist - hist_ref).max() / hist_ref.max())
-    assert abs(st["e_total"] - ref["e1"]["total"]) <= max(1e-4 * ref["e1"]["total"], 2 * band_E)
-    assert dv <= max(1e-4 * diag, 2 * band_V)
+    assert rel <= 1e-4
+    assert dv <= 1e-4 * diag
     assert np.abs(hist - hist_ref).max() <= 1e-4 * hist_ref.max()
     ctx.close()
 
@@ -142,17 +141,22 @@ def test_body_pipeline_matches_oracle(body):
 def test_body_gn_steps_along_oracle_trajectory(body):
     """The body at its full settings (10 GN steps x 40 PCG iterations).
 
-    The undamped Gauss-Newton iteration with b_i re-decided at every step is
-    chaotic on this scene: the oracle's own final energy moves by more than
-    100% when its CG vectors are rounded to FP32.  So every step is checked
-    on its own: the GPU linearises at the oracle's k-th iterate (its node
-    parameters rounded to FP32) through the same kernels and launch shapes as
-    the captured solve, and against the oracle at those parameters
+    The final energy of this solve is not a well-conditioned function of its
+    inputs: the FP64 oracle itself, given the frame's image perturbed by one
+    part in 1e15, ends 10-15% away after 10 steps (40-iteration CG on a
+    system of Jacobi-scaled condition number ~2e6 is forward unstable).  So
+    every step is checked on its own: the GPU linearises at the oracle's k-th
+    iterate (its node parameters rounded to FP32) through the same kernels
+    and launch shapes as the captured solve, and against the oracle at those
+    parameters
       * b_i of the contour set bit-exact on the GPU's own vertices,
       * the energy within 1e-5, J^T F and diag(J^T J) within 1e-4,
-      * the PCG step: same iteration count, the quadratic model
-        q(d) = d^T A d / 2 - b^T d within 1e-4 or three times its spread over
-        FP32 executions of the oracle's PCG (``q_band``), whichever is larger.
+      * the PCG step: same iteration count; the iterate within 1e-4 and the
+        quadratic model q(d) = d^T A d / 2 - b^T d within 1e-6, or within
+        three times the oracle's own change when each of its FP64 products
+        is perturbed by one part in 1e14 (``oracle_cg_spread``), where that
+        is larger: at some steps the 40-iteration CG is forward unstable in
+        FP64 itself (one ulp per product moves its iterate by ~2e-4).
     The oracle's step then gives the next iterate."""
     ctx = _ctx(body)
     ctx.solve_pose(stats=False)
@@ -169,7 +173,7 @@ def test_body_gn_steps_along_oracle_trajectory(body):
     tris = P.tris
     n = P.n
     cam = body.cam
-    worst = dict(energy=0.0, rhs=0.0, diag=0.0, q=0.0, q_band=0.0)
+    worst = dict(energy=0.0, rhs=0.0, diag=0.0, q=0.0, iterate=0.0, spread_q=0.0, spread_iterate=0.0)
     for k in range(body.n_gn):
         R32, t32 = R.astype(np.float32), t.astype(np.float32)
         ctx.set_node_params(R32.reshape(n, 9), t32)
@@ -196,14 +200,16 @@ def test_body_gn_steps_along_oracle_trajectory(body):
         d_rhs = np.abs(vec6(rhs) - b).max() / np.abs(b).max()
         d_diag = np.abs(vec6(diag) - diag_ref).max() / np.abs(diag_ref).max()
         delta, iters = ctx.solve_linear()
-        dref, info, q_spread = q_band(A, b, body.n_pcg)
+        dref, info, s_it, s_q = oracle_cg_spread(A, b, body.n_pcg)
         q = lambda d: 0.5 * d @ (A @ d) - b @ d  # noqa: E731
         d_q = abs(q(vec6(delta)) - q(dref)) / abs(q(dref))
-        for key, val in (("energy", d_en), ("rhs", d_rhs), ("diag", d_diag), ("q", d_q), ("q_band", q_spread)):
+        d_it = np.linalg.norm(vec6(delta) - dref) / np.linalg.norm(dref)
+        for key, val in (("energy", d_en), ("rhs", d_rhs), ("diag", d_diag), ("q", d_q), ("iterate", d_it),
+                         ("spread_q", s_q), ("spread_iterate", s_it)):
             worst[key] = max(worst[key], val)
         assert iters == info["iters"], f"PCG iterations at step {k}"
         assert d_en <= 1e-5 and d_rhs <= 1e-4 and d_diag <= 1e-4, (k, d_en, d_rhs, d_diag)
-        assert d_q <= max(1e-4, 3 * q_spread), (k, d_q, q_spread)
+        assert d_q <= max(1e-6, 3 * s_q) and d_it <= max(1e-4, 3 * s_it), (k, d_q, s_q, d_it, s_it)
         R, t = onr.apply_update(Rd, td, dref)
     report("body_gn_steps_full", **worst)
     ctx.close()
