@@ -124,6 +124,11 @@ typedef struct {
                                its skinned model for the silhouette term and the contour set
                                (Sec. 3.4, displacement warping); held fixed during the pose
                                solve.  0 (default): the plain skinned model */
+    int gn_block;           /* with a target energy: the non-rigid solve's Gauss-Newton steps are
+                               captured in blocks of gn_block steps; every block after the first
+                               is a conditional graph node that runs only while the target is
+                               not reached (the steps after the target inside a block return at
+                               once).  0 (default): all n_gn steps unrolled */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -141,9 +146,12 @@ typedef struct {
     int n_boundary;                          /* |B| contour vertices */
     int n_boundary_neg;                      /* contour vertices with b_i = -1 */
     int pcg_breakdowns;                      /* steps whose PCG stopped on p^T A p <= 0 */
-    int n_kernels;                           /* kernel launches in one solve (captured graph) */
+    int n_kernels;                           /* kernel nodes of the captured solve outside conditional bodies
+                                                (all of them when no step is conditional) */
     int pcg_cluster_size;                    /* CTAs per cluster of the persistent PCG, 0 = per-phase kernels */
     double e_smooth, e_edge, e_velocity, e_acceleration;  /* surface stage terms (0 after a graph solve) */
+    int n_kernels_step;                      /* kernel nodes of one conditional block of gn_block
+                                                Gauss-Newton steps (0: the solve is unrolled) */
 } lc_solve_stats;
 
 /* Vertex flag bits returned by lc_read_visibility / lc_read_back. */

@@ -4,4 +4,4 @@ The compute lives in the CUDA library ``_lib/liblivecap.so`` (C ABI declared
 in ``include/livecap.h``); ``livecap`` is its ctypes binding.  There is no
 CPU fallback: without the built library and a CUDA device every call fails.
 """
-from .livecap import MLP, Batch, Context, LivecapError, load, setup_scene  # noqa: F401
+from .livecap import MLP, Batch, Context, LivecapError, load  # noqa: F401

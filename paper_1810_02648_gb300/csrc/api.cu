@@ -185,6 +185,7 @@ extern "C" lc_status lc_destroy(lc_ctx* ctx) {
     ctx->prof_ev.clear();
     for (void* p : ctx->owned) cudaFree(p);
     ctx->owned.clear();
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LC_OK;
@@ -211,13 +212,16 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
         p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
         !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3 || p->pose_displacement < 0 ||
-        p->pose_displacement > 1)
+        p->pose_displacement > 1 || p->gn_block < 0)
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     for (int j = 0; j < 3; ++j)
         if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)
             return ctx->fail(LC_ERR_ARG, "lc_set_params: pyr_ksize must be odd, 1..%d", kPyrMaxTaps);
     cudaSetDevice(ctx->device);
     if (p->pcg_kernel < 0 || p->pcg_kernel > 1) return ctx->fail(LC_ERR_ARG, "lc_set_params: pcg_kernel must be 0 or 1");
+    // a target energy switches the captured solve to conditional blocks of steps
+    if ((p->target_energy > 0.f) != (ctx->params.target_energy > 0.f) || p->gn_block != ctx->params.gn_block)
+        ctx->drop_graph();
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
         p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
@@ -878,6 +882,46 @@ void lc_ctx::enqueue_pcg() {
     }
 }
 
+// A conditional IF node at the end of the capture in progress on `stream`;
+// the capture continues into its body on the side stream until end_if().
+void lc_ctx::begin_if(cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaStreamGetCaptureInfo(stream, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+        cudaGraphAddNode(&node, g, deps, nullptr, nd, &p) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(side_stream, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cond_failed = true;
+        return;
+    }
+    cond_bodies.push_back(p.conditional.phGraph_out[0]);
+    saved_stream = stream;
+    stream = side_stream;
+}
+
+void lc_ctx::end_if() {
+    if (stream != side_stream) return;
+    cudaGraph_t b = nullptr;
+    if (cudaStreamEndCapture(side_stream, &b) != cudaSuccess) cond_failed = true;
+    stream = saved_stream;
+}
+
+// The non-rigid solve.  With a target energy and gn_block > 0 (and no
+// profiling: event records are not allowed in conditional bodies), the
+// Gauss-Newton steps are captured in blocks of gn_block steps and every
+// block after the first is the body of a conditional IF node whose condition
+// the previous block's last kernel sets: the blocks after the target launch
+// nothing.  Otherwise all n_gn steps are unrolled (steps after a target
+// return at once).
 void lc_ctx::enqueue_nonrigid() {
     const CapDesc& C = hC;
     cudaStream_t st = stream;
@@ -891,18 +935,37 @@ void lc_ctx::enqueue_nonrigid() {
     launch_warp(dC, C, st);
     mark(LC_PH_VIS);
     launch_visibility(dC, C, st);
+    const int B = params.gn_block;
+    const int n_blocks = B > 0 ? (params.n_gn + B - 1) / B : 1;
+    std::vector<cudaGraphConditionalHandle> hs(n_blocks, 0);
+    bool cond = !profiling && params.target_energy > 0.f && n_blocks > 1 && side_stream;
+    if (cond) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamGetCaptureInfo(stream, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive)
+            cond = false;
+        for (int b = 1; cond && b < n_blocks; ++b)
+            if (cudaGraphConditionalHandleCreate(&hs[b], g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+                cond_failed = true;
+        cudaGetLastError();
+    }
     for (int gn = 0; gn < params.n_gn; ++gn) {
+        const int blk = cond ? gn / B : 0;
+        const bool first_of_block = cond && gn % B == 0, last_of_block = cond && (gn % B == B - 1 || gn == params.n_gn - 1);
+        if (first_of_block && blk > 0) begin_if(hs[blk]);
         if (gn > 0) {
             mark(LC_PH_WARP);
-            launch_warp(dC, C, st, true);
+            launch_warp(dC, C, stream, true);
         }
         mark(LC_PH_LIN);
-        launch_linearize(dC, C, true, gn, st);
+        launch_linearize(dC, C, true, gn, stream);
         mark(LC_PH_RHS);
-        launch_rhs(dC, C, gn, false, st);
+        launch_rhs(dC, C, gn, false, stream);
         enqueue_pcg();
         mark(LC_PH_UPDATE);
-        launch_update(dC, C, gn, st);
+        launch_update(dC, C, gn, stream);
+        if (last_of_block && blk + 1 < n_blocks) launch_gn_gate(dC, hs[blk + 1], stream);
+        if (last_of_block && blk > 0) end_if();
     }
     mark(LC_PH_WARP);
     launch_warp(dC, C, st);
@@ -915,13 +978,7 @@ void lc_ctx::enqueue_nonrigid() {
     prof_nonrigid.end = prof_used;
 }
 
-lc_status lc_ctx::capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)()) {
-    cudaGraph_t g = nullptr;
-    lc_status s;
-    if ((s = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
-    (this->*enqueue)();
-    cudaError_t e = cudaStreamEndCapture(stream, &g);
-    if ((s = cuda(e, "end capture"))) return s;
+static int kernel_nodes(cudaGraph_t g) {
     size_t nn = 0;
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -931,7 +988,31 @@ lc_status lc_ctx::capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*
         cudaGraphNodeType ty;
         if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
     }
-    *n_kernels = k;
+    return k;
+}
+
+lc_status lc_ctx::capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)(), int* n_kernels_step) {
+    cudaGraph_t g = nullptr;
+    lc_status s;
+    if (!side_stream && cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        side_stream = nullptr;   // no conditional steps
+    }
+    cond_bodies.clear();
+    cond_failed = false;
+    if ((s = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture"))) return s;
+    (this->*enqueue)();
+    if (stream == side_stream) end_if();   // an unbalanced body (cannot happen) is closed
+    cudaError_t e = cudaStreamEndCapture(stream, &g);
+    if ((s = cuda(e, "end capture"))) return s;
+    if (cond_failed) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(LC_ERR_CUDA, "capture: conditional graph nodes could not be built");
+    }
+    *n_kernels = kernel_nodes(g);
+    if (n_kernels_step) *n_kernels_step = cond_bodies.empty() ? 0 : kernel_nodes(cond_bodies[0]);
+    cond_bodies.clear();
     e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     return cuda(e, "graph instantiate");
@@ -986,7 +1067,9 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     lc_status s;
     if ((s = ctx->check_solve_state("lc_solve_nonrigid"))) return s;
     cudaSetDevice(ctx->device);
-    if (!ctx->gexec && (s = ctx->capture(&ctx->gexec, &ctx->graph_kernels, &lc_ctx::enqueue_nonrigid))) return s;
+    if (!ctx->gexec && (s = ctx->capture(&ctx->gexec, &ctx->graph_kernels, &lc_ctx::enqueue_nonrigid,
+                                         &ctx->graph_kernels_step)))
+        return s;
     if ((s = ctx->cuda(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch"))) return s;
     if ((s = ctx->accumulate_profile(ctx->prof_nonrigid))) return s;
     ctx->has_vis = true;
@@ -996,6 +1079,7 @@ extern "C" lc_status lc_solve_nonrigid(lc_ctx* ctx, lc_solve_stats* stats) {
     if (stats) {
         if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
         stats->n_kernels = ctx->graph_kernels;
+        stats->n_kernels_step = ctx->graph_kernels_step;
         stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
     }
     return LC_OK;
@@ -1015,6 +1099,7 @@ extern "C" lc_status lc_read_stats(lc_ctx* ctx, lc_solve_stats* stats) {
     }
     if ((s = ctx->read_stats(stats, ctx->params.n_gn))) return s;
     stats->n_kernels = ctx->graph_kernels;
+    stats->n_kernels_step = ctx->graph_kernels_step;
     stats->pcg_cluster_size = ctx->use_cluster_pcg() ? ctx->pcg_plan.cl : 0;
     return LC_OK;
 }

@@ -23,7 +23,15 @@ struct lc_ctx {
     lc::CapDesc* dC = nullptr;    // device copy
     std::vector<void*> owned;     // every device allocation of this context
     cudaGraphExec_t gexec = nullptr;
-    int graph_kernels = 0;        // kernel nodes in the captured non-rigid solve
+    int graph_kernels = 0;        // kernel nodes in the captured non-rigid solve (outside conditional bodies)
+    int graph_kernels_step = 0;   // kernel nodes of one conditional Gauss-Newton step (0: unrolled)
+    // conditional Gauss-Newton steps (captured solves with a target energy)
+    cudaStream_t side_stream = nullptr;    // captures the bodies of conditional nodes
+    cudaStream_t saved_stream = nullptr;
+    std::vector<cudaGraph_t> cond_bodies;  // bodies of the capture in progress
+    bool cond_failed = false;
+    void begin_if(cudaGraphConditionalHandle h);
+    void end_if();
     bool has_camera = false, has_template = false, has_graph = false, has_frame = false;
     bool has_vis = false, has_lin = false;
     // template
@@ -92,7 +100,7 @@ struct lc_ctx {
     void enqueue_nonrigid();
     lc_status check_solve_state(const char* who);
     lc_status read_stats(lc_solve_stats* stats, int n_gn, bool surface = false);
-    lc_status capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)());
+    lc_status capture(cudaGraphExec_t* exec, int* n_kernels, void (lc_ctx::*enqueue)(), int* n_kernels_step = nullptr);
     lc_status linearize_now(bool with_rhs);
     lc_status vec_out(float* dst, const float4* src);
     float* tmp_out();

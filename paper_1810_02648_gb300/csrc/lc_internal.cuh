@@ -453,6 +453,9 @@ void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream_t st);
+// one thread sets the condition of the next step's conditional graph node to
+// "the solve goes on" (capture 0 of dC has not reached its target)
+void launch_gn_gate(const CapDesc* dC, cudaGraphConditionalHandle next, cudaStream_t st);
 void launch_update(const CapDesc* dC, const Tiles& T, int gn_slot, cudaStream_t st);
 void launch_pack_vec(const float* in6, float4* out, int n, cudaStream_t st);
 void launch_unpack_vec(const float4* in, float* out6, int n, cudaStream_t st);

@@ -717,6 +717,18 @@ void launch_update(const CapDesc* dC, const CapDesc& hC, int gn_slot, cudaStream
 }
 
 // ---------------------------------------------------------------------------
+// Condition of the next Gauss-Newton step's conditional graph node: the
+// solve goes on unless it reached its target energy.
+// ---------------------------------------------------------------------------
+__global__ void gn_gate_kernel(const CapDesc* __restrict__ caps, cudaGraphConditionalHandle next) {
+    cudaGraphSetConditional(next, caps[0].sc->gn_stop ? 0u : 1u);
+}
+
+void launch_gn_gate(const CapDesc* dC, cudaGraphConditionalHandle next, cudaStream_t st) {
+    gn_gate_kernel<<<1, 1, 0, st>>>(dC, next);
+}
+
+// ---------------------------------------------------------------------------
 // 6n <-> two float4 per node
 // ---------------------------------------------------------------------------
 __global__ void pack_vec_kernel(const float* __restrict__ in, float4* __restrict__ out, int n) {

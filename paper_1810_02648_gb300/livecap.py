@@ -29,7 +29,8 @@ class lc_params(ctypes.Structure):
                 ("w_velocity", ctypes.c_float), ("w_acceleration", ctypes.c_float),
                 ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
                 ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float),
-                ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3), ("pose_displacement", ctypes.c_int)]
+                ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3), ("pose_displacement", ctypes.c_int),
+                ("gn_block", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -40,7 +41,7 @@ class lc_solve_stats(ctypes.Structure):
                 ("n_boundary_neg", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int),
                 ("n_kernels", ctypes.c_int), ("pcg_cluster_size", ctypes.c_int),
                 ("e_smooth", ctypes.c_double), ("e_edge", ctypes.c_double), ("e_velocity", ctypes.c_double),
-                ("e_acceleration", ctypes.c_double)]
+                ("e_acceleration", ctypes.c_double), ("n_kernels_step", ctypes.c_int)]
 
     def to_dict(self) -> dict:
         g = self.n_gn_done
@@ -51,7 +52,8 @@ class lc_solve_stats(ctypes.Structure):
                     pcg_breakdowns=self.pcg_breakdowns, n_kernels=self.n_kernels,
                     pcg_cluster_size=self.pcg_cluster_size, n_gn_done=g,
                     e_gn_all=list(self.e_gn), e_smooth=self.e_smooth, e_edge=self.e_edge,
-                    e_velocity=self.e_velocity, e_acceleration=self.e_acceleration)
+                    e_velocity=self.e_velocity, e_acceleration=self.e_acceleration,
+                    n_kernels_step=self.n_kernels_step)
 
 
 _P = ctypes.c_void_p
@@ -628,25 +630,3 @@ class Batch:
         ms = np.zeros(4, np.float32)
         self._check(self._lib.lc_batch_autotune(self.h, int(reps), ctypes.byref(mode), _ptr(ms)))
         return mode.value, ms
-
-
-def setup_scene(ctx: Context, scene, with_frame: bool = True):
-    """Upload a ``synth.Scene`` (template, camera, graph, weights, frame, and
-    for body scenes the skeleton and start pose)."""
-    wp, ws, wa = scene.weights
-    _, _, wsm, wed, wv, wac = scene.surface_weights
-    ctx.set_params(w_photo=wp, w_sil=ws, w_arap=wa, n_gn=scene.n_gn, n_pcg=scene.n_pcg,
-                   n_gn_pose=scene.n_gn_pose, w_smooth=wsm, w_edge=wed, w_velocity=wv, w_acceleration=wac,
-                   n_gn_surface=scene.n_gn_surface, n_pcg_surface=scene.n_pcg_surface)
-    ctx.set_camera(scene.cam.f, scene.cam.cx, scene.cam.cy, scene.cam.W, scene.cam.H)
-    ctx.upload_template(scene.V, scene.F, scene.albedo, scene.material)
-    ctx.build_graph(scene.n_nodes, scene.K)
-    if scene.skeleton is not None:
-        sk = scene.skeleton
-        from synth.scenes import SKELETON_SITES
-        dof = np.ones(len(sk["parents"]), np.uint8)
-        dof[SKELETON_SITES] = 0
-        ctx.upload_skeleton(sk["parents"], sk["joints_rest"], dof, sk["skin_idx"], sk["skin_w"])
-        ctx.set_pose(scene.pose_init)
-    if with_frame:
-        ctx.upload_frame(scene.rgb, scene.dt, scene.mask.astype(np.uint8), scene.joints2d, scene.joints3d)

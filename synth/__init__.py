@@ -32,3 +32,4 @@ from .scenes import (  # noqa: F401
     SKELETON_NAMES,
     N_POSE_DOF,
 )
+from .upload import setup_scene  # noqa: F401

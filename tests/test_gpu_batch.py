@@ -33,7 +33,8 @@ def scenes():
 
 
 def _contexts(scenes, pcg_kernel):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctxs = []
     for sc in scenes:
         c = Context(0)

@@ -61,7 +61,8 @@ def test_device_distance_transform_bit_exact(case):
 
 
 def test_solve_on_device_transform_equals_uploaded():
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     scene = synth.make_scene("body")
     out = []
     for device_dt in (False, True):

@@ -34,7 +34,8 @@ def _gap_sigma(d, quantile):
 
 
 def test_surface_all_options_end_to_end():
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     body = synth.make_scene("body")
     scene = copy.copy(body)
     scene.dt = odt.distance_transform(body.mask)        # what the device computes

@@ -42,7 +42,8 @@ def body_parts(body):
 
 
 def _ctx(scene):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctx = Context(0)
     setup_scene(ctx, scene)
     sk = scene.skeleton
@@ -188,7 +189,8 @@ def test_surface_end_to_end_masked(body, body_parts):
 
 
 def test_body_parts_arguments(body):
-    from paper_1810_02648_gb300 import Context, LivecapError, setup_scene
+    from paper_1810_02648_gb300 import Context, LivecapError
+    from synth import setup_scene
     tiny = synth.make_scene("tiny")
     ctx = Context(0)
     setup_scene(ctx, tiny)

@@ -30,7 +30,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _ctx(scene, **params):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctx = Context(0)
     setup_scene(ctx, scene)
     if params:
@@ -185,7 +186,8 @@ def test_graph_end_to_end_tiny(tiny):
 def test_surface_end_to_end_body(body):
     """The paper's schedule: 3 Gauss-Newton steps x 4 PCG, one per level."""
     from gpu_helpers import surface_rounding_band
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     VS = np.asarray(body.meta["V_posed"], dtype=np.float32)
     V = VS.astype(np.float64)
     rng = np.random.default_rng(3)

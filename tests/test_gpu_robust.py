@@ -32,7 +32,8 @@ FLAG_PRUNED = 16
 
 
 def _ctx(scene, **params):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctx = Context(0)
     setup_scene(ctx, scene)
     if params:
@@ -216,7 +217,8 @@ def test_robust_surface_linearization(body):
     """The surface stage's data rows come from the same kernel: with the
     kernel's pruning decisions given to the oracle, energies and normal
     equations agree as without pruning."""
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     scene = body
     rng = np.random.default_rng(3)
     c = scene.V.mean(0)

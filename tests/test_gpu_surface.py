@@ -31,7 +31,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _ctx(scene, **params):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctx = Context(0)
     setup_scene(ctx, scene)
     if params:

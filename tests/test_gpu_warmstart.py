@@ -136,7 +136,8 @@ def test_adam_step_matches_oracle():
 
 
 def _ctx(scene, **params):
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     ctx = Context(0)
     setup_scene(ctx, scene)
     if params:
@@ -213,17 +214,30 @@ def test_solve_stops_at_target_energy():
     hist = np.array(full["e_gn_all"][:tiny.n_gn])
     target = float(hist[2]) * (1 + 1e-6)          # reached at the third linearisation at the latest
     stop = int(np.nonzero(hist <= target)[0][0])
-    ctx.set_params(n_pcg=3, target_energy=target)
+    ctx.set_params(n_pcg=3, target_energy=target, gn_block=1)
     ctx.set_node_params(None, None)
     st = ctx.solve_nonrigid()
     report("target_energy", n_gn_done=st["n_gn_done"], e_total=st["e_total"], target=target, stop=stop)
     assert st["n_gn_done"] == stop
     assert abs(st["e_total"] - hist[stop]) <= 1e-9 * hist[stop]
     assert st["e_gn_all"][:stop + 1] == full["e_gn_all"][:stop + 1]
-    # switching the target off restores the full solve
+    # with gn_block 1 the steps after the first are conditional graph nodes:
+    # the stopped solve launched only the steps it took
+    assert full["n_kernels_step"] == 0 and st["n_kernels_step"] > 0
+    # a target below every energy: the chain of conditional steps runs them
+    # all, bit-identical to the unrolled solve
+    ctx.set_params(n_pcg=3, target_energy=float(hist.min()) * 0.5, gn_block=2)
+    ctx.set_node_params(None, None)
+    never = ctx.solve_nonrigid()
+    out_never = ctx.read_back(flags=False)
+    assert never["n_gn_done"] == tiny.n_gn and never["e_gn_all"] == full["e_gn_all"]
+    assert never["e_total"] == full["e_total"]
+    # switching the target off restores the unrolled solve
     ctx.set_params(n_pcg=3, target_energy=0.0)
     ctx.set_node_params(None, None)
     assert ctx.solve_nonrigid()["e_total"] == full["e_total"]
+    out_full = ctx.read_back(flags=False)
+    assert np.array_equal(out_full["R"], out_never["R"]) and np.array_equal(out_full["V"], out_never["V"])
     ctx.close()
 
 
@@ -256,7 +270,8 @@ def test_learned_warm_start_gain():
     Gauss-Newton steps on average; the frames/s gain (device time of warm
     start + solve vs the plain solve) is reported."""
     import torch
-    from paper_1810_02648_gb300 import Context, setup_scene
+    from paper_1810_02648_gb300 import Context
+    from synth import setup_scene
     from paper_1810_02648_gb300 import warmstart as ws
     tiny = synth.make_scene("tiny")
     seqs = _tiny_sequences(list(range(1, 41)) + [999], 41)

@@ -31,7 +31,8 @@ def _context_visibility(ctx, n, seed):
 def test_visibility_noalloc_matches_context_path():
     import torch
 
-    from paper_1810_02648_gb300 import Context, load, setup_scene
+    from paper_1810_02648_gb300 import Context, load
+    from synth import setup_scene
     from paper_1810_02648_gb300.livecap import LC_OK, LC_ERR_ARG
 
     lib = load()
