@@ -625,8 +625,9 @@ lc_status lc_read_profile(lc_ctx *ctx, double *ms, int *count);
  * No device memory is allocated, on any path: the z-buffer scratch is a
  * static device array of LC_NOALLOC_MAX_PIXELS 64-bit entries (8 MiB) that
  * every GPU which loads this library holds until the process exits.  W * H
- * above LC_NOALLOC_MAX_PIXELS returns LC_ERR_ARG; host (non-device)
- * pointers return LC_ERR_ARG.  The first call on a device looks up the
+ * above LC_NOALLOC_MAX_PIXELS returns LC_ERR_ARG; host pointers, memory of
+ * another device and a negative or NaN eps_vis return LC_ERR_ARG.  The
+ * first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, which may load the module):
  * make that first call outside any stream capture.  All calls share the
  * scratch, each clearing what it uses first; calls that overlap on the GPU

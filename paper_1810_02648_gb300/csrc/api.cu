@@ -445,7 +445,8 @@ void lc_ctx::free_template() {
 void lc_ctx::release_pcg_tables() {
     void* bufs[] = {(void*)hC.pcg_perm, (void*)hC.pcg_leaf_off, (void*)hC.pcg_leaf,
                     (void*)hC.pcg_loc_off[0], (void*)hC.pcg_loc_vid[0], (void*)hC.pcg_eus_off[0], (void*)hC.pcg_ent_us[0],
-                    (void*)hC.pcg_loc_off[1], (void*)hC.pcg_loc_vid[1], (void*)hC.pcg_eus_off[1], (void*)hC.pcg_ent_us[1]};
+                    (void*)hC.pcg_loc_off[1], (void*)hC.pcg_loc_vid[1], (void*)hC.pcg_eus_off[1], (void*)hC.pcg_ent_us[1],
+                    (void*)hC.pcg_zdst[0], (void*)hC.pcg_zdst[1]};
     for (void* p : bufs) release(p);
     hC.pcg_perm = nullptr;
     hC.pcg_leaf_off = nullptr;
@@ -455,6 +456,7 @@ void lc_ctx::release_pcg_tables() {
         hC.pcg_loc_vid[ti] = nullptr;
         hC.pcg_eus_off[ti] = nullptr;
         hC.pcg_ent_us[ti] = nullptr;
+        hC.pcg_zdst[ti] = nullptr;
     }
 }
 
@@ -473,8 +475,11 @@ lc_status lc_ctx::plan_pcg() {
         (s = copy_to_host(g.data(), C.node_g, sizeof(float4) * n)))
         return s;
     std::vector<int2> en((size_t)std::max(eo[n], 1));
-    if ((s = copy_to_host(en.data(), C.ent, sizeof(int2) * (size_t)eo[n]))) return s;
-    spatial_partition(n, N, K, g.data(), eo.data(), en.data(), go.data(), bi.data(), pcg_part);
+    std::vector<int> ed((size_t)std::max(go[n], 1));
+    if ((s = copy_to_host(en.data(), C.ent, sizeof(int2) * (size_t)eo[n])) ||
+        (s = copy_to_host(ed.data(), C.edge_dst, sizeof(int) * (size_t)go[n])))
+        return s;
+    spatial_partition(n, N, K, g.data(), eo.data(), en.data(), go.data(), ed.data(), bi.data(), pcg_part);
     release_pcg_tables();
     // upload one host array into a fresh device buffer
     auto put = [&](const void* src, size_t bytes) -> void* {
@@ -491,7 +496,8 @@ lc_status lc_ctx::plan_pcg() {
         C.pcg_loc_vid[ti] = (const int*)put(pcg_part.loc_vid[ti].data(), sizeof(int) * pcg_part.loc_vid[ti].size());
         C.pcg_eus_off[ti] = (const int*)put(pcg_part.eus_off[ti].data(), sizeof(int) * pcg_part.eus_off[ti].size());
         C.pcg_ent_us[ti] = (const unsigned*)put(pcg_part.ent_us[ti].data(), sizeof(unsigned) * pcg_part.ent_us[ti].size());
-        ok = ok && C.pcg_loc_off[ti] && C.pcg_loc_vid[ti] && C.pcg_eus_off[ti] && C.pcg_ent_us[ti];
+        C.pcg_zdst[ti] = (const unsigned short*)put(pcg_part.zdst[ti].data(), sizeof(unsigned short) * pcg_part.zdst[ti].size());
+        ok = ok && C.pcg_loc_off[ti] && C.pcg_loc_vid[ti] && C.pcg_eus_off[ti] && C.pcg_ent_us[ti] && C.pcg_zdst[ti];
     }
     if (!ok) return fail(LC_ERR_OOM, "plan_pcg: device allocation failed");
     if ((s = cuda(cudaStreamSynchronize(stream), "upload"))) return s;

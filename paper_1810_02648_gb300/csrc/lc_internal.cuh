@@ -144,6 +144,9 @@ struct CapDesc {
     const int* pcg_loc_vid[2];
     const int* pcg_eus_off[2];
     const unsigned* pcg_ent_us[2];
+    // per node: bit r set if CTA r reads the node's z (it owns the node, a
+    // local vertex of it binds to the node, or an owned edge ends there)
+    const unsigned short* pcg_zdst[2];
     // operands of the per-iteration J^T J p, staged once per linearisation
     float4* vA;              // N*K: (w_is R_k (v_i - g_k), w_is) per binding, zero for inactive vertices
     float4* eA;              // N*K: the same per node -> vertex CSR entry
@@ -492,6 +495,7 @@ struct PcgPartition {
     // tables (CapDesc::pcg_loc_* / pcg_ent_us)
     std::vector<int> loc_off[2], loc_vid[2], eus_off[2];
     std::vector<unsigned> ent_us[2];
+    std::vector<unsigned short> zdst[2];
     int cap_n[5] = {0, 0, 0, 0, 0};   // owned nodes
     int cap_e[5] = {0, 0, 0, 0, 0};   // CSR entries of the owned nodes
     int cap_d[5] = {0, 0, 0, 0, 0};   // directed edges of the owned nodes
@@ -499,7 +503,7 @@ struct PcgPartition {
 };
 constexpr int kPcgMinCluster = 8;   // the cluster PCG runs 8 or 16 CTAs per capture
 void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off, const int2* ent,
-                       const int* edge_off, const int* bind_idx, PcgPartition& out);
+                       const int* edge_off, const int* edge_dst, const int* bind_idx, PcgPartition& out);
 struct PcgPlan {
     int cl;          // CTAs per cluster
     int cap_v;       // local-vertex capacity per CTA

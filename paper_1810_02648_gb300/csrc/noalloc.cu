@@ -116,13 +116,15 @@ __global__ void na_visible(const float* __restrict__ V, int N, float f, float cx
     out[i] = vis;
 }
 
-bool is_device_memory(const void* p) {
+// Device (or managed) memory of device `dev`: memory of another GPU would be
+// dereferenced by kernels running on this one.
+bool is_device_memory(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -130,11 +132,13 @@ bool is_device_memory(const void* p) {
 extern "C" lc_status lc_visibility_noalloc(const float* V_warp, int N, const int32_t* tris, int F, float f, float cx,
                                            float cy, int W, int H, float eps_vis, uint8_t* visible,
                                            void* cuda_stream) {
-    if (!V_warp || !tris || !visible || N < 1 || F < 0 || W < 1 || H < 1 || !(f > 0.f)) return LC_ERR_ARG;
+    if (!V_warp || !tris || !visible || N < 1 || F < 0 || W < 1 || H < 1 || !(f > 0.f) || !(eps_vis >= 0.f))
+        return LC_ERR_ARG;
     if ((long long)W * (long long)H > (long long)LC_NOALLOC_MAX_PIXELS) return LC_ERR_ARG;
-    if (!is_device_memory(V_warp) || !is_device_memory(tris) || !is_device_memory(visible)) return LC_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LC_ERR_CUDA;
+    if (!is_device_memory(V_warp, dev) || !is_device_memory(tris, dev) || !is_device_memory(visible, dev))
+        return LC_ERR_ARG;
     unsigned long long* zbuf = nullptr;
     {
         // once per device, with that device current: the host-side name of a

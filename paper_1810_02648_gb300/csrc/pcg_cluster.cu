@@ -4,7 +4,7 @@
 //
 // One thread-block cluster of CL CTAs solves one capture.  The capture's
 // nodes are split into kPcgLeaves spatially compact leaves (recursive
-// coordinate bisection at graph build, balanced by CSR entries and edges);
+// coordinate bisection at graph build, balanced by node count);
 // CTA r owns the nodes of leaves r*L/CL .. (r+1)*L/CL - 1, so most vertices
 // have all K of their nodes in one CTA.  At the start the CTA stages in its
 // own shared memory:
@@ -20,18 +20,19 @@
 //   phase B: (J^T J z)_k = sum_entries [c_is x q_i ; w_is q_i] + the edges'
 //     contributions, sixteen threads per owned node (each a share of its
 //     entries and edges, all six components), combined by shuffles;
-//   then for the owned nodes p = z + beta p and A p = A z + beta A p (A is
-//   linear; warp 0 forms beta during phase A), p.Ap, alpha, x, r, z and r.z.
-// The nodes are split by count (one warp-sized round per phase in every
-// CTA).  Vectors, products and dot products are compensated FP32 pairs
-// (fpair.cuh, jtj_pair.cuh): CG at tens of iterations on these systems amplifies FP32
+//   the lanes that finish a node's product apply p = z + beta p and
+//   A p = A z + beta A p (A is linear; warp 0 forms beta during phase A) and
+//   add their terms of p.Ap; then alpha (warp 0), x, r, z and r.z.
+// Vectors, products and dot products are compensated FP32 pairs (fpair.cuh,
+// jtj_pair.cuh): CG at tens of iterations on these systems amplifies FP32
 // rounding of its recurrences to percent-level changes of the iterate.  The
 // operator data stay FP32.  Each CTA's dot-product total (a pair) is
 // converted exactly to FP64 and written into every CTA's slot array through
 // distributed shared memory; all CTAs sum the slots in rank order in FP64
 // (deterministic, identical everywhere), and alpha / beta are pair divisions
-// of those totals.  The new z of the owned nodes goes into every CTA's copy
-// as 16-byte distributed-shared-memory stores.  Two hardware cluster barriers
+// of those totals.  The new z of an owned node goes into the copies of the
+// CTAs that read it (a per-node mask built with the partition) as 16-byte
+// distributed-shared-memory stores.  Two hardware cluster barriers
 // per iteration; no spin loops, no global-memory round trips.
 #include <algorithm>
 #include <numeric>
@@ -48,7 +49,7 @@ namespace lc {
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgWarps = kPcgThreads / 32;
 constexpr int kNodeLanes = 16;  // phase B threads per owned node
-constexpr int kVecArrays = 10;   // x_h, x_l, minv, p_h, p_l, r_h, r_l, ap_h, ap_l, az_h (+ az_l)
+constexpr int kVecArrays = 9;    // x_h, x_l, minv, p_h, p_l, r_h, r_l, ap_h, ap_l
 
 // shared-memory carve-up (byte offsets, all 16-byte aligned)
 struct Smem {
@@ -75,7 +76,7 @@ __host__ __device__ inline Smem smem_layout(int n, int K, int cap_v, int cap_e, 
     s.dE = o; o = al16(o + sizeof(float) * 12 * (size_t)cap_d);
     s.dNode = o; o = al16(o + sizeof(int) * (size_t)cap_d);
     s.dOff = o; o = al16(o + sizeof(int) * (size_t)(cap_n + 1));
-    s.vec = o; o = al16(o + sizeof(float) * (kVecArrays + 1) * 6 * (size_t)cap_n);
+    s.vec = o; o = al16(o + sizeof(float) * kVecArrays * 6 * (size_t)cap_n);
     s.total = o;
     return s;
 }
@@ -110,13 +111,15 @@ __device__ __forceinline__ void publish(cg::cluster_group& cluster, double total
     }
 }
 
-// Sum of the cl (<= 16) cluster partials in FP64 (fixed shuffle tree over 16
-// lanes; every lane holds the total); warp 0 only.
+// Sum of the cl (<= 16) cluster partials in FP64: a fixed xor-shuffle tree
+// over lanes 0..15 (which then hold the total), broadcast from lane 0 so that
+// every lane of the calling warp returns the same value (a caller that
+// branches on it in every lane then branches alike).
 __device__ __forceinline__ double cluster_total(const double* slots, int cl) {
     double v = (int)(threadIdx.x & 31) < cl ? slots[threadIdx.x & 31] : 0.0;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // Block-wide exclusive prefix sum of cnt[0..m) into off[0..m] (off[m] = total),
@@ -197,8 +200,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     float* r_l = vbase + 6 * V6;
     float* ap_h = vbase + 7 * V6;
     float* ap_l = vbase + 8 * V6;
-    float* az_h = vbase + 9 * V6;
-    float* az_l = vbase + 10 * V6;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < cl) s_zdst[tid] = cluster.map_shared_rank(z_all, tid);
     if (tid == 0) {
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
     // entries: each warp compacts the active entries of its nodes in place,
     // remapping the table's local vertex to its active index
     const unsigned* __restrict__ ent_us = C.pcg_ent_us[ti] + C.pcg_eus_off[ti][rank];
+    const unsigned short* __restrict__ zdst = C.pcg_zdst[ti];   // CTAs reading each node's z
     for (int j = warp; j < nown && !s_flag[2]; j += kPcgWarps) {
         const int start = nodeStart[j], ne = nodeStart[j + 1] - start;
         int cnt = 0;
@@ -416,10 +418,18 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
             }
         }
         __syncthreads();
+        if (s_stopz) {
+            completed = false;
+            break;
+        }
         // phase B: (A z)_k, kNodeLanes threads per owned node, each a share of
         // its entries and edges accumulating all six components; the partial
         // vectors are combined by a transposed shuffle reduction after which
-        // lane h of the group holds component h.  Warps without a node skip.
+        // lane h of the group holds component h >> 1, and that lane applies
+        // p = z + beta p, A p = A z + beta A p and adds its term of p^T A p.
+        // Warps without a node skip.
+        const fp2 beta = {s_scalar[4], s_scalar[5]};
+        fp2acc my_pap;
         for (int t0 = 0; t0 < nown * kNodeLanes; t0 += kPcgThreads) {
             if (t0 + 32 * warp >= nown * kNodeLanes) continue;
             const int t = t0 + tid;
@@ -479,32 +489,22 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
                 v[0] = fp2_add(v[0], recv);
             }
             if (on && (h & 1) == 0 && (h >> 1) < 6) {
-                az_h[6 * j + (h >> 1)] = v[0].h;
-                az_l[6 * j + (h >> 1)] = v[0].l;
+                const int c = h >> 1, e = 6 * j + c, k = perm[j];
+                const fp2 z = {z_all[12 * k + c], z_all[12 * k + 6 + c]};
+                const fp2 p = fp2_add(z, fp2_mul(beta, fp2{p_h[e], p_l[e]}));
+                const fp2 ap = fp2_add(v[0], fp2_mul(beta, fp2{ap_h[e], ap_l[e]}));
+                p_h[e] = p.h; p_l[e] = p.l;
+                ap_h[e] = ap.h; ap_l[e] = ap.l;
+                my_pap.mac(p, ap);
             }
         }
-        __syncthreads();
-        if (s_stopz) {
-            completed = false;
-            break;
-        }
-        // owned p = z + beta p, A p = A z + beta A p; p^T A p
-        const fp2 beta = {s_scalar[4], s_scalar[5]};
-        fp2acc my_pap;
-        for (int e = tid; e < 6 * nown; e += kPcgThreads) {
-            const int k = perm[e / 6], c = e % 6;
-            const fp2 z = {z_all[12 * k + c], z_all[12 * k + 6 + c]};
-            const fp2 p = fp2_add(z, fp2_mul(beta, fp2{p_h[e], p_l[e]}));
-            const fp2 ap = fp2_add(fp2{az_h[e], az_l[e]}, fp2_mul(beta, fp2{ap_h[e], ap_l[e]}));
-            p_h[e] = p.h; p_l[e] = p.l;
-            ap_h[e] = ap.h; ap_l[e] = ap.l;
-            my_pap.mac(p, ap);
-        }
         {
-            const fp2 t = block_sum_fp2_warps(my_pap.get(), s_warp2, (6 * nown + 31) / 32);
+            const fp2 t = block_sum_fp2_warps(my_pap.get(), s_warp2, (nown * kNodeLanes + 31) / 32);
             publish(cluster, fp2_to_double(t), s_pAp_part, rank, cl);
         }
         cluster.sync();
+        // warp 0 forms p^T A p and alpha (GB300's FP64 pipe issues a warp
+        // instruction in ~19 clocks: one warp, not all of them, does this)
         if (warp == 0) {
             const double pAp = cluster_total(s_pAp_part, cl);
             if (lane == 0) {
@@ -522,8 +522,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
             completed = false;
             break;
         }
-        // x, r, z for owned nodes; r^T z partial
         const fp2 alpha = {s_scalar[2], s_scalar[3]};
+        // x, r, z for owned nodes; r^T z partial
         fp2acc my_rz2;
         for (int e = tid; e < 6 * nown; e += kPcgThreads) {
             const int k = perm[e / 6], c = e % 6;
@@ -541,12 +541,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const CapDe
             const fp2 t = block_sum_fp2_warps(my_rz2.get(), s_warp2, (6 * nown + 31) / 32);
             publish(cluster, fp2_to_double(t), s_rz_part, rank, cl);
         }
-        // the owned nodes' new z (12 floats each) into every other CTA's
-        // copy, three 16-byte stores per node and destination
+        // the owned nodes' new z (12 floats each) into the copies of the CTAs
+        // that read it (their local vertices or ARAP edges reference the
+        // node), three 16-byte stores per node and destination
         for (int t = tid; t < nown * cl; t += kPcgThreads) {
             const int j = t / cl, d = t % cl;
-            if (d == rank) continue;
             const int k = perm[j];
+            if (d == rank || !((zdst[k] >> d) & 1u)) continue;
             const float4* src = reinterpret_cast<const float4*>(z_all + 12 * k);
             float4* dst = reinterpret_cast<float4*>(s_zdst[d] + 12 * k);
             dst[0] = src[0];
@@ -625,7 +626,7 @@ static void rcb(std::vector<int>& idx, int a, int b, int levels, int leaf0, cons
 }
 
 void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off, const int2* ent,
-                       const int* edge_off, const int* bind_idx, PcgPartition& out) {
+                       const int* edge_off, const int* edge_dst, const int* bind_idx, PcgPartition& out) {
     out.perm.resize(n);
     std::iota(out.perm.begin(), out.perm.end(), 0);
     out.leaf_off.assign(kPcgLeaves + 1, 0);
@@ -647,6 +648,7 @@ void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off,
             out.loc_vid[ti].clear();
             out.eus_off[ti].assign(cl + 1, 0);
             out.ent_us[ti].clear();
+            out.zdst[ti].assign(n, 0);
         }
         int cn = 0, ce = 0, cd = 0, cv = 0;
         std::fill(mark.begin(), mark.end(), -1);
@@ -658,6 +660,9 @@ void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off,
                     if ((out.leaf[bind_idx[(size_t)i * K + s]] / lpc) == r && mark[i] != r) {
                         mark[i] = r;
                         loc.push_back(i);   // ascending i
+                        if (tables)
+                            for (int s2 = 0; s2 < K; ++s2)
+                                out.zdst[ti][bind_idx[(size_t)i * K + s2]] |= (unsigned short)(1u << r);
                     }
             for (int j = out.leaf_off[r * lpc]; j < out.leaf_off[(r + 1) * lpc]; ++j) {
                 const int k = out.perm[j];
@@ -665,6 +670,8 @@ void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off,
                 ne += ent_off[k + 1] - ent_off[k];
                 nd += edge_off[k + 1] - edge_off[k];
                 if (!tables) continue;
+                out.zdst[ti][k] |= (unsigned short)(1u << r);
+                for (int e = edge_off[k]; e < edge_off[k + 1]; ++e) out.zdst[ti][edge_dst[e]] |= (unsigned short)(1u << r);
                 for (int e = ent_off[k]; e < ent_off[k + 1]; ++e) {
                     const int i = ent[e].x;
                     const int u = (int)(std::lower_bound(loc.begin(), loc.end(), i) - loc.begin());

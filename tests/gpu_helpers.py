@@ -207,13 +207,14 @@ def fp32_rounding_band(scene, graph, n_runs=3, base32=None, n_gn=None, n_pcg=Non
     return ref, dE, dV
 
 
-def oracle_cg_spread(A, b, n, rel=1e-14, n_runs=3):
+def oracle_cg_spread(A, b, n, rel=1e-13, n_runs=3):
     """How reproducible the oracle's own n-step PCG is: the FP64 CG rerun with
     every matrix-vector product perturbed by a relative error of ``rel``
-    (seeded normal), the magnitude of a compensated-FP32 pair product.  On
-    nearly singular systems the n-step iterate is forward unstable: one part
-    in 1e14 per product moves it by up to ~4e-3 at some Gauss-Newton steps of
-    the body solve.  Returns (FP64 iterate, its info, max relative iterate
+    (seeded normal), the magnitude of a compensated-FP32 pair product's error
+    (2^-48 of the sum of |terms| per product, up to ~1e-13 of the result where
+    the J^T J p terms cancel).  On nearly singular systems the n-step iterate
+    is forward unstable: one part in 1e14 per product moves it by up to ~4e-3
+    at some Gauss-Newton steps of the body solve.  Returns (FP64 iterate, its info, max relative iterate
     change, max relative change of q(d) = d^T A d / 2 - b^T d)."""
     from oracle.nonrigid import pcg
     dref, info = pcg(A, b, n)

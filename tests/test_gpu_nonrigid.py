@@ -17,7 +17,7 @@ be bit-exact.  Floating-point tolerances (FP32 kernels vs FP64 oracle):
   q(d) = d^T A d / 2 - b^T d within 1e-6, the iterate within 1e-5 after 1
   iteration and within 1e-4 after 3 and after the configuration's count;
   after many iterations, or three times the oracle's own change when its
-  FP64 products are perturbed by one part in 1e14 where that is larger
+  FP64 products are perturbed by one part in 1e13 where that is larger
   (``oracle_cg_spread``: the 40-iteration CG of the body is forward unstable
   in FP64 at some linearisations).  CG on the FP64 operator and on the same
   operator rounded to FP32 (exact vector arithmetic) differ by ~3e-6 after

@@ -155,7 +155,7 @@ def test_body_gn_steps_along_oracle_trajectory(body):
       * the PCG step: same iteration count; the iterate within 1e-4 and the
         quadratic model q(d) = d^T A d / 2 - b^T d within 1e-6, or within
         three times the oracle's own change when each of its FP64 products
-        is perturbed by one part in 1e14 (``oracle_cg_spread``), where that
+        is perturbed by one part in 1e13 (``oracle_cg_spread``), where that
         is larger: at some steps the 40-iteration CG is forward unstable in
         FP64 itself (one ulp per product moves its iterate by ~2e-4).
     The oracle's step then gives the next iterate."""
@@ -451,4 +451,34 @@ def test_pose_displacement_matches_oracle(body):
     assert dA <= 1e-4 and dg <= 1e-4
     assert dj <= 2e-3 and de <= 1e-2 and dh_rel <= 1e-3
     assert abs(st0["e_total"] - st["e_total"]) > 1e-3 * st["e_total"]
+    ctx.close()
+
+
+def test_body_reaches_oracle_final_energy(body):
+    """The body frame as the benchmark solves it: pose stage, body-part mask
+    of the silhouette term, then the non-rigid stage with a target energy:
+    the FP64 oracle's final energy after the configuration's 10 GN x 40 PCG
+    (its own pose stage, mask and non-rigid stage), within 1e-4.  The GPU's
+    energy must reach it within 30 Gauss-Newton steps.  (The final energy of
+    the 10-step solve itself is not comparable to 1e-4: the FP64 oracle moves
+    by 10-15% when its input image is perturbed by one part in 1e15.)"""
+    from oracle import graph as ograph
+    from oracle import parts as oparts
+    sk, cam = body.skeleton, body.cam
+    g = ograph.build_graph(body.V, body.material, body.n_nodes, body.K)
+    VS = op.solve_scene(body)["VS"].astype(np.float32)
+    vp = oparts.vertex_parts(sk["skin_idx"], sk["skin_w"], sk["bone_part"])
+    pm = oparts.part_mask(VS, body.F, cam.f, cam.cx, cam.cy, cam.W, cam.H, vp, 10, sk["torso_part"])
+    ref = onr.solve_scene(body, graph=g, base32=VS, part_mask=pm, vpart=vp)
+    e_star = ref["e1"]["total"]
+    target = e_star * (1.0 + 1e-4)
+    ctx = _ctx(body, n_gn=30, target_energy=target, gn_block=10)
+    ctx.set_body_parts(sk["bone_part"], sk["torso_part"], 10)
+    ctx.solve_pose(stats=False)
+    ctx.set_node_params(None, None)
+    st = ctx.solve_nonrigid()
+    report("body_reach_oracle_energy", e_star=e_star, e_gpu=st["e_total"], gn_steps=st["n_gn_done"],
+           oracle_hist=[h["energy"] for h in ref["hist"]])
+    assert st["e_total"] <= target, (st["e_total"], e_star, st["e_gn"])
+    assert st["n_gn_done"] < 30
     ctx.close()

@@ -67,3 +67,8 @@ def test_visibility_noalloc_matches_context_path():
                                    128, 128, ctypes.c_float(1e-2), host.ctypes.data, None)
     assert st == LC_ERR_ARG
     ctx.close()
+    # a negative or NaN depth tolerance is refused like in the context path
+    for eps in (-1e-2, float("nan")):
+        st = lib.lc_visibility_noalloc(V.data_ptr(), scene.N, F.data_ptr(), len(scene.F), 150.0, 63.5, 63.5,
+                                       128, 128, ctypes.c_float(eps), out.data_ptr(), None)
+        assert st == LC_ERR_ARG
