@@ -59,6 +59,8 @@ def parse():
                     help="body / tiny: Gauss-Newton steps at most while a frame works toward the oracle's energy")
     ap.add_argument("--gn-block", type=int, default=10,
                     help="body / tiny: Gauss-Newton steps per conditional graph block (0: unrolled)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="start / stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--no-body-parts", action="store_true",
                     help="body: solve without the body-part mask of the silhouette term")
     # options of the per-frame path (Sec. 3.2-3.4), off in the default line
@@ -614,6 +616,22 @@ def run_ours(a):
 # ---------------------------------------------------------------------------
 TARGET_TOL = 1e-4     # a frame counts once its energy is within 1e-4 of the oracle's final energy
 
+# DRAM bytes (read + write) of one 40-iteration launch of the cluster PCG on
+# the body capture, from one ncu capture of these kernel sources
+# (profiles/pcg_cluster_body_full.md); reported only while the sources still
+# hash to the captured version, else null.
+PCG_TRAFFIC = {"sources": ("pcg_cluster.cu", "jtj_pair.cuh", "fpair.cuh"), "sha256_16": "16b429668c3b5c58",
+               "bytes": 709632 + 0}
+
+
+def pcg_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in PCG_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1810_02648_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return PCG_TRAFFIC["bytes"] if h.hexdigest()[:16] == PCG_TRAFFIC["sha256_16"] else None
+
 
 def frame_seeds(a, rank=0):
     """Seeds of the benchmark's frames: the workload's own capture first."""
@@ -740,6 +758,8 @@ def run_frames(a):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    if a.profile_region:
+        torch.cuda.profiler.start()
     with ClockSampler(local) as clk:
         for k in range(a.steps):
             with torch.cuda.stream(stream):
@@ -748,6 +768,8 @@ def run_frames(a):
             step(ctxs[k % len(ctxs)])
             ends[k].record(stream)
         torch.cuda.synchronize(dev)
+    if a.profile_region:
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -867,7 +889,8 @@ def run_frames(a):
         # the steps it takes), the identity reset kernel
         "gpu_launches": sum(per[k % len(per)]["kernels"] for k in range(a.steps)),
         "roofline": {"kernel": k_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "peak_source": peak_kind, "traffic": None,
+                     "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+                     "traffic": pcg_traffic() if name == "body" and prof.get("pcg", (0, 0))[1] else None,
                      "algorithmic_bytes_per_launch": k_bytes, "jtjp_algorithmic_bytes": jtj_bytes,
                      "avg_launch_us": avg_us,
                      "note": "the capture's working set (~0.3 MB per J^T J p) stays on chip across the PCG "
