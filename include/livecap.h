@@ -201,6 +201,24 @@ lc_status lc_upload_template(lc_ctx *ctx, const float *V, int N, const int32_t *
  * the identity. */
 lc_status lc_build_graph(lc_ctx *ctx, int n_nodes, int K);
 
+/* Upload a caller-built embedded deformation graph (Sec. 3.1) in place of
+ * lc_build_graph, in the layout lc_read_graph returns: node_vid n (the
+ * template vertex of each node, 0 <= v < N), bind_idx / bind_w N x K (each
+ * vertex's K nodes and weights, finite and >= 0; the solver uses them as
+ * given, without normalising), edge_off n+1 (CSR offsets of the directed
+ * edges by source node, edge_off[0] = 0, non-decreasing), edge_dst E and
+ * edge_s E (finite, >= 0: the ARAP weight of the pair).  The edge set must
+ * be symmetric with equal weights both ways (the solver evaluates a pair's
+ * two residuals from either node's out-edges), without self or duplicate
+ * edges; edge_dst / edge_s may be null when E = 0.  1 <= K <= 8,
+ * 1 <= n_nodes <= N.  Arrays may be host or device memory; they are copied
+ * and checked on the host, and a violation returns LC_ERR_ARG and leaves
+ * the previous graph in place.  Node parameters are reset to the identity.
+ * Synchronises. */
+lc_status lc_upload_graph(lc_ctx *ctx, int n_nodes, int K, const int32_t *node_vid, const int32_t *bind_idx,
+                          const float *bind_w, const int32_t *edge_off, const int32_t *edge_dst,
+                          const float *edge_s);
+
 /* Copy the graph out.  node_vid n, bind_idx N x K, bind_w N x K,
  * edge_off n+1 (CSR offsets of the directed edges by source node),
  * edge_dst E, edge_s E.  Any pointer may be null to skip it; *n_edges (if
@@ -455,7 +473,8 @@ lc_status lc_batch_apply_jtj(lc_batch *batch, int stage);
  * energy at the predicted parameters does not exceed the energy at the start.
  *
  * Network: x = (f - mu) / sigma (per feature), h1 = relu(x W1 + b1),
- * h2 = relu(h1 W2 + b2), y = h2 W3 + b3, sizes 64 -> 256 -> 256 -> 6;
+ * h2 = relu(h1 W2 + b2), y = (h2 W3 + b3) * s_out (per output), sizes
+ * 64 -> 256 -> 256 -> 6;
  * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
  * master parameters.  Parameter vector (LC_MLP_PARAMS floats): W1 row-major
  * 64 x 256, b1 256, W2 256 x 256, b2 256, W3 256 x 6, b3 6.  Loss over M
@@ -483,6 +502,20 @@ lc_status lc_mlp_destroy(lc_mlp *mlp);
 const char *lc_mlp_last_error(const lc_mlp *mlp);
 /* Current FP32 parameters (LC_MLP_PARAMS).  Synchronises. */
 lc_status lc_mlp_get_params(lc_mlp *mlp, float *params);
+/* The network's input normalisation mu / sigma (64 each) and output scale
+ * s_out (6; 1 after lc_mlp_create).  Each pointer is nullable (that part is
+ * left as is or not read) and may be host or device.  Synchronises. */
+lc_status lc_mlp_set_scaling(lc_mlp *mlp, const float *mu, const float *sigma, const float *s_out);
+lc_status lc_mlp_get_scaling(lc_mlp *mlp, float *mu, float *sigma, float *s_out);
+/* Fit the scaling to training rows, on the device: mu_j / sigma_j = mean and
+ * population standard deviation of feature column j of F (rows x 64; sigma
+ * 1 where below 1e-12, and feature 63, the constant, keeps mu 0 and sigma 1);
+ * s_out_c = root mean square of target column c of T (rows x 6; 1 where
+ * below 1e-12), so that the layers fit targets of unit scale.  Moments are
+ * accumulated in FP64 in a fixed order, shifted by the first row (exact for
+ * a constant column).  F and T must be device arrays (LC_ERR_ARG
+ * otherwise).  Synchronises. */
+lc_status lc_mlp_fit_scaling(lc_mlp *mlp, const float *F, const float *T, long long rows);
 /* Y (M x 6) for raw features F (M x 64).  Synchronises. */
 lc_status lc_mlp_forward(lc_mlp *mlp, const float *F, int M, float *Y);
 /* Loss and its gradient (LC_MLP_PARAMS, nullable) for features F (M x 64)
@@ -501,6 +534,12 @@ lc_status lc_node_features(lc_ctx *ctx, float *F);
  * graph was built): u_k = (Log(R_k R_prev,k^T), t_k - t_prev,k).  Call once
  * per frame after its solve.  Enqueue only. */
 lc_status lc_record_motion(lc_ctx *ctx);
+/* The motion recorded by the last lc_record_motion, n x 6 floats per node
+ * (Log(R R_prev^T), t - t_prev), into u (host or device).  Called after a
+ * frame's solve and its lc_record_motion it is the update that solve made
+ * from the frame's start: the warm start's training target.  LC_ERR_STATE
+ * if nothing was recorded for the current graph.  Synchronises. */
+lc_status lc_read_motion(lc_ctx *ctx, float *u);
 /* Warm start at the current node parameters (normally the previous frame's
  * result): visibility, linearisation and features there; the network's
  * update applied to every node (R <- Exp(d_omega) R, t += d_t); kept iff

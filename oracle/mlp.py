@@ -14,10 +14,17 @@ x = (f - mu) / sigma:
 
     h1 = relu(x W1 + b1)        W1: 64 x 256
     h2 = relu(h1 W2 + b2)       W2: 256 x 256
-    y  = h2 W3 + b3             W3: 256 x 6      y = (d_omega, d_t)
+    y  = (h2 W3 + b3) * s_out   W3: 256 x 6      y = (d_omega, d_t)
+
+s_out is a fixed per-output scale (not trained), and mu / sigma / s_out are
+fitted to the training rows (``fit_scaling``): column mean and population
+standard deviation of the features, root mean square of the targets.
 
 Loss over M rows: L = (1/M) sum_rows ||y - t||^2.  Gradients by the chain
 rule; Adam with bias correction (Kingma and Ba, 2015).
+
+The training target of a frame is the update its solve made to each node
+(``node_motion``): Log(R_end R_start^T) and t_end - t_start.
 
 Parameter vector order (flat, float): W1 (row-major 64 x 256), b1, W2
 (256 x 256), b2, W3 (256 x 6), b3.
@@ -65,16 +72,18 @@ def pack(parts) -> np.ndarray:
     return np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in parts])
 
 
-def forward(theta, x):
-    """x: M x 64 (normalised features).  Returns (y, cache)."""
+def forward(theta, x, s_out=None):
+    """x: M x 64 (normalised features); s_out: 6 output scales (None = 1).
+    Returns (y, cache)."""
     W1, b1, W2, b2, W3, b3 = unpack(theta)
     x = np.asarray(x, dtype=np.float64)
+    s = np.ones(D_OUT) if s_out is None else np.asarray(s_out, dtype=np.float64)
     z1 = x @ W1 + b1
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W2 + b2
     h2 = np.maximum(z2, 0.0)
-    y = h2 @ W3 + b3
-    return y, (x, z1, h1, z2, h2)
+    y = (h2 @ W3 + b3) * s
+    return y, (x, z1, h1, z2, h2, s)
 
 
 def loss(y, t):
@@ -87,10 +96,11 @@ def loss(y, t):
 def backward(theta, cache, dy):
     """Gradient of L with respect to the flat parameters, given dL/dy."""
     W1, b1, W2, b2, W3, b3 = unpack(theta)
-    x, z1, h1, z2, h2 = cache
-    dW3 = h2.T @ dy
-    db3 = dy.sum(0)
-    dh2 = (dy @ W3.T) * (z2 > 0.0)
+    x, z1, h1, z2, h2, s = cache
+    dz3 = np.asarray(dy, dtype=np.float64) * s        # through y = z3 * s_out
+    dW3 = h2.T @ dz3
+    db3 = dz3.sum(0)
+    dh2 = (dz3 @ W3.T) * (z2 > 0.0)
     dW2 = h1.T @ dh2
     db2 = dh2.sum(0)
     dh1 = (dh2 @ W2.T) * (z1 > 0.0)
@@ -106,6 +116,31 @@ def adam_step(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** step)
     vh = v / (1.0 - beta2 ** step)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def fit_scaling(F, T):
+    """(mu, sigma, s_out) of training rows F (rows x 64), T (rows x 6):
+    column mean and population standard deviation of F (sigma 1 where below
+    1e-12; the constant feature 63 keeps mu 0, sigma 1), root mean square of
+    each column of T (1 where below 1e-12)."""
+    F = np.asarray(F, dtype=np.float64).reshape(-1, D_IN)
+    T = np.asarray(T, dtype=np.float64).reshape(-1, D_OUT)
+    mu = F.mean(0)
+    sigma = F.std(0)
+    sigma[sigma < 1e-12] = 1.0
+    mu[D_IN - 1], sigma[D_IN - 1] = 0.0, 1.0
+    s_out = np.sqrt((T * T).mean(0))
+    s_out[s_out < 1e-12] = 1.0
+    return mu, sigma, s_out
+
+
+def node_motion(R_start, t_start, R_end, t_end) -> np.ndarray:
+    """Per node (Log(R_end R_start^T), t_end - t_start), n x 6."""
+    Rs = np.asarray(R_start, dtype=np.float64).reshape(-1, 3, 3)
+    Re = np.asarray(R_end, dtype=np.float64).reshape(-1, 3, 3)
+    D = np.einsum("nij,nkj->nik", Re, Rs)
+    return np.concatenate([rot_log(D), np.asarray(t_end, dtype=np.float64).reshape(-1, 3)
+                           - np.asarray(t_start, dtype=np.float64).reshape(-1, 3)], 1)
 
 
 # ----------------------------------------------------------------------------

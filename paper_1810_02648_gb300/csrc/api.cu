@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <functional>
 
 #include "lc_context.h"
 
@@ -16,14 +17,12 @@ using namespace lc;
 // error helpers
 // ---------------------------------------------------------------------------
 lc_status lc_ctx::fail(lc_status st, const char* fmt, ...) {
-    if (err.empty()) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof(buf), fmt, ap);
-        va_end(ap);
-        err = buf;
-    }
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
     return st;
 }
 
@@ -37,6 +36,7 @@ void* lc_ctx::alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
+        ++alloc_failures;
         cuda(e, "cudaMalloc");
         return nullptr;
     }
@@ -295,6 +295,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
     if (!V || !tris || !albedo || !material || N < 1 || F < 1)
         return ctx->fail(LC_ERR_ARG, "lc_upload_template: null array or empty mesh");
     cudaSetDevice(ctx->device);
+    const int af0 = ctx->alloc_failures;
     std::vector<float> hv, ha, hm;
     std::vector<int32_t> ht;
     lc_status s;
@@ -362,7 +363,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
     C.ev = (float4*)ctx->alloc(sizeof(float4) * N);
     C.q = (float4*)ctx->alloc(sizeof(float4) * N);
     C.q_lo = (float4*)ctx->alloc(sizeof(float4) * N);
-    if (!ctx->err.empty()) return LC_ERR_OOM;
+    if (ctx->alloc_failures != af0) return LC_ERR_OOM;
     C.base = ctx->base_buf;
     cudaStream_t st = ctx->stream;
     if ((s = ctx->cuda(cudaMemcpyAsync(ctx->tpl, v4.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st), "upload")) ||
@@ -506,16 +507,11 @@ lc_status lc_ctx::plan_pcg() {
     return LC_OK;
 }
 
-extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
-    if (!ctx) return LC_ERR_ARG;
-    if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_build_graph: no template");
+// device arrays of a graph of n nodes and K bindings per vertex, edges apart
+static void graph_alloc(lc_ctx* ctx, int n, int K) {
     CapDesc& C = ctx->hC;
-    if (K < 1 || K > kMaxK || n_nodes < K + 1 || n_nodes > C.N)
-        return ctx->fail(LC_ERR_ARG, "lc_build_graph: need 1 <= K <= %d and K+1 <= n_nodes <= N", kMaxK);
-    cudaSetDevice(ctx->device);
+    const int N = C.N;
     ctx->free_graph();
-    const int n = n_nodes, N = C.N;
-    cudaStream_t st = ctx->stream;
     C.n = n;
     C.K = K;
     C.node_tiles = (n + kNodeTile - 1) / kNodeTile;
@@ -531,6 +527,51 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     float4** vecs[] = {&C.b, &C.minv, &C.diag, &C.x, &C.r, &C.z, &C.p, &C.Ap, &ctx->tmp_vec, &ctx->tmp_vec2,
                        &C.x_lo, &C.r_lo, &C.z_lo, &C.p_lo, &C.Ap_lo};
     for (float4** v : vecs) *v = (float4*)ctx->alloc(sizeof(float4) * 2 * n);
+}
+
+// the E edge arrays and the per-binding / per-edge staging of the solver
+static void graph_alloc_edges(lc_ctx* ctx, int E) {
+    CapDesc& C = ctx->hC;
+    const size_t NK = (size_t)C.N * C.K;
+    C.E = E;
+    C.edge_dst = (const int*)ctx->alloc(sizeof(int) * std::max(E, 1));
+    C.edge_s = (const float*)ctx->alloc(sizeof(float) * std::max(E, 1));
+    C.vA = (float4*)ctx->alloc(sizeof(float4) * NK);
+    C.eA = (float4*)ctx->alloc(sizeof(float4) * NK);
+    C.dB = (float4*)ctx->alloc(sizeof(float4) * 2 * (size_t)std::max(E, 1));
+}
+
+// after the bindings and edges are in place: the node -> vertex entries,
+// node positions of the current rest geometry, identity parameters, the PCG
+// plan; the captured solves are dropped
+static lc_status graph_finish(lc_ctx* ctx, GraphScratch& gs, const std::function<void()>& cleanup) {
+    CapDesc& C = ctx->hC;
+    cudaStream_t st = ctx->stream;
+    launch_entries(C.bind_idx, C.bind_w, C.N, C.K, C.n, gs, (int*)C.ent_off, (int2*)C.ent, st);
+    launch_gather_nodes(C.base, C.node_vid, C.n, (float4*)C.node_g, st);
+    launch_identity_params(C.node_R, C.node_t, C.n, st);
+    lc_status s = ctx->cuda(cudaStreamSynchronize(st), "graph build");
+    cleanup();
+    if (s != LC_OK) return s;
+    if ((s = ctx->plan_pcg())) return s;
+    ctx->ensure_partials();
+    ctx->has_graph = true;
+    ctx->drop_graph();
+    ctx->pose_drop_graph();   // the pose solve moves the graph nodes
+    return ctx->sync_desc();
+}
+
+extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
+    if (!ctx) return LC_ERR_ARG;
+    if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_build_graph: no template");
+    CapDesc& C = ctx->hC;
+    if (K < 1 || K > kMaxK || n_nodes < K + 1 || n_nodes > C.N)
+        return ctx->fail(LC_ERR_ARG, "lc_build_graph: need 1 <= K <= %d and K+1 <= n_nodes <= N", kMaxK);
+    cudaSetDevice(ctx->device);
+    const int af0 = ctx->alloc_failures;
+    const int n = n_nodes, N = C.N;
+    cudaStream_t st = ctx->stream;
+    graph_alloc(ctx, n, K);
     GraphScratch gs;
     std::vector<void*> scratch;
     auto salloc = [&](size_t b) {
@@ -549,14 +590,14 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
     auto cleanup = [&]() {
         for (void* p : scratch) ctx->release(p);
     };
-    if (!ctx->err.empty()) {
+    if (ctx->alloc_failures != af0) {
         cleanup();
         return LC_ERR_OOM;
     }
     constexpr int kFpsMaxCtas = 4096;
     double* fps_val = (double*)salloc(sizeof(double) * 2 * kFpsMaxCtas);
     int* fps_idx = (int*)salloc(sizeof(int) * 2 * kFpsMaxCtas);
-    if (!ctx->err.empty()) {
+    if (ctx->alloc_failures != af0) {
         cleanup();
         return LC_ERR_OOM;
     }
@@ -583,26 +624,104 @@ extern "C" lc_status lc_build_graph(lc_ctx* ctx, int n_nodes, int K) {
         cleanup();
         return ctx->fail(LC_ERR_NUMERIC, "lc_build_graph: a node has more than %d incoming edges", kMaxExtraEdges);
     }
-    C.E = E;
-    C.edge_dst = (const int*)ctx->alloc(sizeof(int) * std::max(E, 1));
-    C.edge_s = (const float*)ctx->alloc(sizeof(float) * std::max(E, 1));
-    C.vA = (float4*)ctx->alloc(sizeof(float4) * (size_t)N * K);
-    C.eA = (float4*)ctx->alloc(sizeof(float4) * (size_t)N * K);
-    C.dB = (float4*)ctx->alloc(sizeof(float4) * 2 * (size_t)std::max(E, 1));
+    graph_alloc_edges(ctx, E);
+    if (ctx->alloc_failures != af0) {
+        cleanup();
+        return LC_ERR_OOM;
+    }
     launch_node_edges_fill(G_tpl, n, ctx->material, C.node_vid, gs, C.edge_off, (int*)C.edge_dst, (float*)C.edge_s, st);
-    launch_entries(C.bind_idx, C.bind_w, N, K, n, gs, (int*)C.ent_off, (int2*)C.ent, st);
-    // node positions of the current rest geometry
-    launch_gather_nodes(C.base, C.node_vid, n, (float4*)C.node_g, st);
-    launch_identity_params(C.node_R, C.node_t, n, st);
-    s = ctx->cuda(cudaStreamSynchronize(st), "graph build");
-    cleanup();
-    if (s != LC_OK) return s;
-    if ((s = ctx->plan_pcg())) return s;
-    ctx->ensure_partials();
-    ctx->has_graph = true;
-    ctx->drop_graph();
-    ctx->pose_drop_graph();   // the pose solve moves the graph nodes
-    return ctx->sync_desc();
+    return graph_finish(ctx, gs, cleanup);
+}
+
+extern "C" lc_status lc_upload_graph(lc_ctx* ctx, int n_nodes, int K, const int32_t* node_vid, const int32_t* bind_idx,
+                                     const float* bind_w, const int32_t* edge_off, const int32_t* edge_dst,
+                                     const float* edge_s) {
+    if (!ctx || !node_vid || !bind_idx || !bind_w || !edge_off) return LC_ERR_ARG;
+    if (!ctx->has_template) return ctx->fail(LC_ERR_STATE, "lc_upload_graph: no template");
+    CapDesc& C = ctx->hC;
+    if (K < 1 || K > kMaxK || n_nodes < 1 || n_nodes > C.N)
+        return ctx->fail(LC_ERR_ARG, "lc_upload_graph: need 1 <= K <= %d and 1 <= n_nodes <= N", kMaxK);
+    cudaSetDevice(ctx->device);
+    const int af0 = ctx->alloc_failures;
+    const int n = n_nodes, N = C.N;
+    const size_t NK = (size_t)N * K;
+    // host copies (the arguments may be host or device memory) for the checks
+    std::vector<int32_t> vid(n), bi(NK), eo(n + 1);
+    std::vector<float> bw(NK);
+    auto get = [&](void* dst, const void* src, size_t bytes) {
+        return ctx->cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault), "lc_upload_graph: read arguments");
+    };
+    lc_status s;
+    if ((s = get(vid.data(), node_vid, sizeof(int32_t) * n)) || (s = get(bi.data(), bind_idx, sizeof(int32_t) * NK)) ||
+        (s = get(bw.data(), bind_w, sizeof(float) * NK)) || (s = get(eo.data(), edge_off, sizeof(int32_t) * (n + 1))))
+        return s;
+    for (int k = 0; k < n; ++k)
+        if (vid[k] < 0 || vid[k] >= N) return ctx->fail(LC_ERR_ARG, "lc_upload_graph: node_vid[%d] out of range", k);
+    for (size_t j = 0; j < NK; ++j) {
+        if (bi[j] < 0 || bi[j] >= n) return ctx->fail(LC_ERR_ARG, "lc_upload_graph: bind_idx[%zu] out of range", j);
+        if (!(bw[j] >= 0.f) || !std::isfinite(bw[j]))
+            return ctx->fail(LC_ERR_ARG, "lc_upload_graph: bind_w[%zu] must be finite and >= 0", j);
+    }
+    if (eo[0] != 0) return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edge_off[0] must be 0");
+    for (int k = 0; k < n; ++k)
+        if (eo[k + 1] < eo[k]) return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edge_off must not decrease");
+    const int E = eo[n];
+    std::vector<int32_t> ed(std::max(E, 1));
+    std::vector<float> es(std::max(E, 1));
+    if (E > 0) {
+        if (!edge_dst || !edge_s) return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edges without edge_dst / edge_s");
+        if ((s = get(ed.data(), edge_dst, sizeof(int32_t) * E)) || (s = get(es.data(), edge_s, sizeof(float) * E)))
+            return s;
+    }
+    // the solver evaluates both residuals of a node pair from either node's
+    // out-edges, so the edge set must be symmetric with equal weights
+    std::vector<std::pair<long long, float>> key(E);
+    for (int k = 0; k < n; ++k)
+        for (int e = eo[k]; e < eo[k + 1]; ++e) {
+            const int l = ed[e];
+            if (l < 0 || l >= n || l == k)
+                return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edge %d (%d -> %d) invalid", e, k, l);
+            if (!(es[e] >= 0.f) || !std::isfinite(es[e]))
+                return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edge_s[%d] must be finite and >= 0", e);
+            key[e] = {(long long)k * n + l, es[e]};
+        }
+    std::sort(key.begin(), key.end());
+    for (int e = 0; e < E; ++e) {
+        if (e > 0 && key[e].first == key[e - 1].first)
+            return ctx->fail(LC_ERR_ARG, "lc_upload_graph: duplicate edge");
+        const long long k = key[e].first / n, l = key[e].first % n;
+        auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(l * n + k, -INFINITY));
+        if (it == key.end() || it->first != l * n + k || it->second != key[e].second)
+            return ctx->fail(LC_ERR_ARG, "lc_upload_graph: edge %lld -> %lld has no reverse edge of equal weight", k, l);
+    }
+    cudaStream_t st = ctx->stream;
+    graph_alloc(ctx, n, K);
+    graph_alloc_edges(ctx, E);
+    GraphScratch gs{};
+    std::vector<void*> scratch;
+    auto salloc = [&](size_t b) {
+        void* p = ctx->alloc(b);
+        scratch.push_back(p);
+        return p;
+    };
+    gs.ent_cnt = (int*)salloc(sizeof(int) * (n + 1));
+    gs.ent_fill = (int*)salloc(sizeof(int) * n);
+    auto cleanup = [&]() {
+        for (void* p : scratch) ctx->release(p);
+    };
+    if (ctx->alloc_failures != af0) {
+        cleanup();
+        return LC_ERR_OOM;
+    }
+    cudaMemcpyAsync((void*)C.node_vid, vid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync((void*)C.bind_idx, bi.data(), sizeof(int) * NK, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync((void*)C.bind_w, bw.data(), sizeof(float) * NK, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync((void*)C.edge_off, eo.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (E > 0) {
+        cudaMemcpyAsync((void*)C.edge_dst, ed.data(), sizeof(int) * E, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync((void*)C.edge_s, es.data(), sizeof(float) * E, cudaMemcpyHostToDevice, st);
+    }
+    return graph_finish(ctx, gs, cleanup);
 }
 
 extern "C" lc_status lc_read_graph(lc_ctx* ctx, int32_t* node_vid, int32_t* bind_idx, float* bind_w, int32_t* edge_off,

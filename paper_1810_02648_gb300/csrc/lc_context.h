@@ -84,6 +84,9 @@ struct lc_ctx {
     lc_status accumulate_profile(const ProfRange& r);
 
     lc_status fail(lc_status st, const char* fmt, ...);
+    // device allocations that failed since creation: a setup sequence
+    // compares it with its value at the start
+    int alloc_failures = 0;
     lc_status cuda(cudaError_t e, const char* what);
     void* alloc(size_t bytes);
     void release(void* p);

@@ -163,6 +163,7 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     if (J < 1 || J > kMaxJoints || !parents || !joints_rest || !dof || !skin_idx || !skin_w)
         return ctx->fail(LC_ERR_ARG, "lc_upload_skeleton: 1 <= J <= %d and non-null arrays required", kMaxJoints);
     cudaSetDevice(ctx->device);
+    const int af0 = ctx->alloc_failures;
     const int N = ctx->hC.N;
     std::vector<int32_t> par(J), sidx((size_t)4 * N);
     std::vector<float> rest((size_t)3 * J), sw((size_t)4 * N);
@@ -240,7 +241,7 @@ extern "C" lc_status lc_upload_skeleton(lc_ctx* ctx, int J, const int32_t* paren
     P.n_hist = 0;
     S.d = (PoseDesc*)ctx->alloc(sizeof(PoseDesc));
     S.pose_set = (float*)ctx->alloc(sizeof(float) * (kMaxDof + 9));
-    if (!ctx->err.empty()) return LC_ERR_OOM;
+    if (ctx->alloc_failures != af0) return LC_ERR_OOM;
     std::vector<float4> r4(J), w4(N);
     std::vector<int4> i4(N);
     for (int j = 0; j < J; ++j) r4[j] = make_float4(rest[3 * j], rest[3 * j + 1], rest[3 * j + 2], 0.f);

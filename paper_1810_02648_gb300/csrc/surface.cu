@@ -534,6 +534,7 @@ using namespace lc;
 // ---------------------------------------------------------------------------
 lc_status lc_ctx::surface_setup(const float* V, const float* mat, const std::vector<int4>& medges) {
     const int N = hC.N;
+    const int af0 = alloc_failures;
     // one-ring CSR from the unique mesh edges, neighbours ascending
     std::vector<int> off(N + 1, 0);
     for (const int4& e : medges) {
@@ -573,7 +574,7 @@ lc_status lc_ctx::surface_setup(const float* V, const float* mat, const std::vec
     float4** vecs[] = {&C.sV, &C.sH1, &C.sH2, &C.sD, &C.sb, &C.sminv, &C.sx, &C.sr, &C.sz, &C.sp[0], &C.sp[1],
                        &C.sAp, &surf_diag};
     for (float4** v : vecs) *v = (float4*)alloc(sizeof(float4) * N);
-    if (!err.empty()) return LC_ERR_OOM;
+    if (alloc_failures != af0) return LC_ERR_OOM;
     cudaStream_t st = stream;
     lc_status s;
     if ((s = cuda(cudaMemcpyAsync((void*)C.adj_off, off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st),

@@ -147,24 +147,26 @@ __global__ void bias_relu_kernel(const float* __restrict__ Z, const float* __res
     H[e] = __float2bfloat16(fmaxf(Z[e] + b[e % N], 0.f));
 }
 
-__global__ void out_bias_kernel(const float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ Y,
-                                int M) {
+// Y = (Z + b) * s_out, per output column
+__global__ void out_bias_kernel(const float* __restrict__ Z, const float* __restrict__ b,
+                                const float* __restrict__ s_out, float* __restrict__ Y, int M) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * kDOut) return;
-    Y[e] = Z[e] + b[e % kDOut];
+    Y[e] = (Z[e] + b[e % kDOut]) * s_out[e % kDOut];
 }
 
-// dY = 2 (Y - T) / M (FP32 and BF16) and per-block FP64 partial sums of
-// ||Y - T||^2 (a fixed-order second pass adds them)
+// gradient with respect to the last layer's pre-scale output,
+// dZ3 = 2 (Y - T) s_out / M (FP32 and BF16), and per-block FP64 partial sums
+// of ||Y - T||^2 (a fixed-order second pass adds them)
 __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ Y, const float* __restrict__ T,
-                                                   float* __restrict__ dY, bf16* __restrict__ dYb,
-                                                   double* __restrict__ part, int M) {
+                                                   const float* __restrict__ s_out, float* __restrict__ dY,
+                                                   bf16* __restrict__ dYb, double* __restrict__ part, int M) {
     __shared__ double sh[8];
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     double s = 0.0;
     if (e < M * kDOut) {
         const float d = Y[e] - T[e];
-        const float gy = 2.f * d / (float)M;
+        const float gy = 2.f * d / (float)M * s_out[e % kDOut];
         dY[e] = gy;
         dYb[e] = __float2bfloat16(gy);
         s = (double)d * d;
@@ -239,6 +241,80 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
     m[e] = mm;
     v[e] = vv;
     theta[e] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+}
+
+// Column sums and sums of squares in FP64 of a rows x cols array (cols <=
+// 256), shifted by the column's first value (sums of x - x_0 and
+// (x - x_0)^2: no cancellation when the mean is large against the spread,
+// and exactly zero for a constant column): thread j of a block takes column
+// j % cols of rows j / cols, + 256 / cols, ...; grid-stride over row groups,
+// fixed order.  part[block][2 cols].
+__global__ void __launch_bounds__(256) column_moments_kernel(const float* __restrict__ X, long long rows, int cols,
+                                                             double* __restrict__ part) {
+    __shared__ double sh[2][256];
+    const int per = 256 / cols;            // rows per pass of a block
+    const int j = threadIdx.x;
+    const bool on = j < per * cols;
+    const int c = j % cols, r0 = j / cols;
+    double s = 0.0, q = 0.0;
+    if (on) {
+        const double x0 = X[c];
+        for (long long r = (long long)blockIdx.x * per + r0; r < rows; r += (long long)gridDim.x * per) {
+            const double x = (double)X[r * cols + c] - x0;
+            s += x;
+            q += x * x;
+        }
+    }
+    sh[0][j] = on ? s : 0.0;
+    sh[1][j] = on ? q : 0.0;
+    __syncthreads();
+    if (j < cols) {
+        double ts = 0.0, tq = 0.0;
+        for (int k = j; k < per * cols; k += cols) {
+            ts += sh[0][k];
+            tq += sh[1][k];
+        }
+        part[(size_t)blockIdx.x * 2 * cols + j] = ts;
+        part[(size_t)blockIdx.x * 2 * cols + cols + j] = tq;
+    }
+}
+
+// input normalisation and output scale from the shifted column moments of
+// the features (partF, 64 columns, first row F0) and of the targets (partT,
+// 6 columns, first row T0): mu = mean, sigma = population standard
+// deviation (1 where below 1e-12; the constant feature 63 keeps mu 0,
+// sigma 1), s_out = root mean square of each target column (1 where below
+// 1e-12).  With d = x - x_0: mean = x_0 + S/n, variance = Q/n - (S/n)^2,
+// mean square = x_0^2 + 2 x_0 S/n + Q/n.
+__global__ void __launch_bounds__(128) fit_scaling_kernel(const double* __restrict__ partF,
+                                                          const double* __restrict__ partT,
+                                                          const float* __restrict__ F0, const float* __restrict__ T0,
+                                                          int nblocks, long long rows, float* __restrict__ mu,
+                                                          float* __restrict__ sigma, float* __restrict__ s_out) {
+    const int j = threadIdx.x;
+    const double n = (double)rows;
+    if (j < kDIn) {
+        double s = 0.0, q = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            s += partF[(size_t)b * 2 * kDIn + j];
+            q += partF[(size_t)b * 2 * kDIn + kDIn + j];
+        }
+        const double d = s / n;
+        const double sd = sqrt(fmax(q / n - d * d, 0.0));
+        const bool constant = j == kDIn - 1;
+        mu[j] = constant ? 0.f : (float)((double)F0[j] + d);
+        sigma[j] = (constant || sd < 1e-12) ? 1.f : (float)sd;
+    } else if (j < kDIn + kDOut) {
+        const int c = j - kDIn;
+        double s = 0.0, q = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            s += partT[(size_t)b * 2 * kDOut + c];
+            q += partT[(size_t)b * 2 * kDOut + kDOut + c];
+        }
+        const double x0 = T0[c];
+        const double rms = sqrt(fmax(x0 * x0 + 2.0 * x0 * (s / n) + q / n, 0.0));
+        s_out[c] = rms < 1e-12 ? 1.f : (float)rms;
+    }
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ F, const float* __restrict__ T,
@@ -438,6 +514,7 @@ struct lc_mlp {
     float* vel = nullptr;
     float* mu = nullptr;
     float* sigma = nullptr;
+    float* s_out = nullptr;   // output scale (6), 1 unless set or fitted
     bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr;
     int step = 0;
     // activations, sized for `cap` rows
@@ -501,12 +578,12 @@ struct lc_mlp {
         gemm_bf16(false, false, H1, kDH, W2, kDH, Z, kDH, M, kDH, kDH, st);
         bias_relu_kernel<<<(unsigned)(((size_t)M * kDH + 255) / 256), 256, 0, st>>>(Z, theta + kOffB2, H2, M, kDH);
         gemm_bf16(false, false, H2, kDH, W3, kDOut, Z, kDOut, M, kDOut, kDH, st);
-        out_bias_kernel<<<(M * kDOut + 255) / 256, 256, 0, st>>>(Z, theta + kOffB3, Y, M);
+        out_bias_kernel<<<(M * kDOut + 255) / 256, 256, 0, st>>>(Z, theta + kOffB3, s_out, Y, M);
     }
     // loss and parameter gradient for targets T (FP32, M x 6) after forward
     void backward(const float* T, int M, cudaStream_t st) {
         const int lb = (M * kDOut + 255) / 256;
-        loss_kernel<<<lb, 256, 0, st>>>(Y, T, dY, dYb, part, M);
+        loss_kernel<<<lb, 256, 0, st>>>(Y, T, s_out, dY, dYb, part, M);
         loss_total_kernel<<<1, 32, 0, st>>>(part, lb, M, loss);
         const size_t nh = (size_t)M * kDH;
         // layer 3
@@ -582,11 +659,12 @@ extern "C" lc_status lc_mlp_create(lc_mlp** out, int device, const float* params
     m->vel = (float*)m->alloc(sizeof(float) * kNParams);
     m->mu = (float*)m->alloc(sizeof(float) * kDIn);
     m->sigma = (float*)m->alloc(sizeof(float) * kDIn);
+    m->s_out = (float*)m->alloc(sizeof(float) * kDOut);
     m->W1 = (bf16*)m->alloc(sizeof(bf16) * kDIn * kDH);
     m->W2 = (bf16*)m->alloc(sizeof(bf16) * kDH * kDH);
     m->W3 = (bf16*)m->alloc(sizeof(bf16) * kDH * kDOut);
     m->loss = (double*)m->alloc(sizeof(double));
-    if (!m->theta || !m->grad || !m->mom || !m->vel || !m->mu || !m->sigma || !m->W1 || !m->W2 || !m->W3 || !m->loss) {
+    if (!m->theta || !m->grad || !m->mom || !m->vel || !m->mu || !m->sigma || !m->s_out || !m->W1 || !m->W2 || !m->W3 || !m->loss) {
         lc_mlp_destroy(m);
         return LC_ERR_OOM;
     }
@@ -594,6 +672,7 @@ extern "C" lc_status lc_mlp_create(lc_mlp** out, int device, const float* params
     cudaMemcpy(m->theta, params ? params : zeros.data(), sizeof(float) * kNParams, cudaMemcpyDefault);
     cudaMemcpy(m->mu, mu ? mu : zeros.data(), sizeof(float) * kDIn, cudaMemcpyDefault);
     cudaMemcpy(m->sigma, sigma ? sigma : ones.data(), sizeof(float) * kDIn, cudaMemcpyDefault);
+    cudaMemcpy(m->s_out, ones.data(), sizeof(float) * kDOut, cudaMemcpyDefault);
     cudaMemset(m->mom, 0, sizeof(float) * kNParams);
     cudaMemset(m->vel, 0, sizeof(float) * kNParams);
     m->refresh_weights(m->stream);
@@ -623,6 +702,49 @@ extern "C" lc_status lc_mlp_get_params(lc_mlp* m, float* params) {
     cudaSetDevice(m->device);
     cudaStreamSynchronize(m->stream);
     return mlp_cuda(m, cudaMemcpy(params, m->theta, sizeof(float) * kNParams, cudaMemcpyDefault), "lc_mlp_get_params");
+}
+
+extern "C" lc_status lc_mlp_set_scaling(lc_mlp* m, const float* mu, const float* sigma, const float* s_out) {
+    if (!m) return LC_ERR_ARG;
+    cudaSetDevice(m->device);
+    cudaStream_t st = m->stream;
+    if (mu) cudaMemcpyAsync(m->mu, mu, sizeof(float) * kDIn, cudaMemcpyDefault, st);
+    if (sigma) cudaMemcpyAsync(m->sigma, sigma, sizeof(float) * kDIn, cudaMemcpyDefault, st);
+    if (s_out) cudaMemcpyAsync(m->s_out, s_out, sizeof(float) * kDOut, cudaMemcpyDefault, st);
+    return mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_set_scaling");
+}
+
+extern "C" lc_status lc_mlp_get_scaling(lc_mlp* m, float* mu, float* sigma, float* s_out) {
+    if (!m) return LC_ERR_ARG;
+    cudaSetDevice(m->device);
+    cudaStream_t st = m->stream;
+    if (mu) cudaMemcpyAsync(mu, m->mu, sizeof(float) * kDIn, cudaMemcpyDefault, st);
+    if (sigma) cudaMemcpyAsync(sigma, m->sigma, sizeof(float) * kDIn, cudaMemcpyDefault, st);
+    if (s_out) cudaMemcpyAsync(s_out, m->s_out, sizeof(float) * kDOut, cudaMemcpyDefault, st);
+    return mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_get_scaling");
+}
+
+// mu / sigma / s_out from the training rows, on the device
+extern "C" lc_status lc_mlp_fit_scaling(lc_mlp* m, const float* F, const float* T, long long rows) {
+    if (!m || !F || !T || rows < 1) return LC_ERR_ARG;
+    if (!is_dev(F) || !is_dev(T)) return m->fail(LC_ERR_ARG, "lc_mlp_fit_scaling: F and T must be device arrays");
+    cudaSetDevice(m->device);
+    cudaStream_t st = m->stream;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    const int nb = 4 * (sms > 0 ? sms : 1);
+    double* part = nullptr;
+    if (cudaMalloc(&part, sizeof(double) * (size_t)nb * 2 * (kDIn + kDOut)) != cudaSuccess) {
+        cudaGetLastError();
+        return m->fail(LC_ERR_OOM, "lc_mlp_fit_scaling: device memory");
+    }
+    double* partT = part + (size_t)nb * 2 * kDIn;
+    column_moments_kernel<<<nb, 256, 0, st>>>(F, rows, kDIn, part);
+    column_moments_kernel<<<nb, 256, 0, st>>>(T, rows, kDOut, partT);
+    fit_scaling_kernel<<<1, 128, 0, st>>>(part, partT, F, T, nb, rows, m->mu, m->sigma, m->s_out);
+    lc_status s = mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_fit_scaling");
+    cudaFree(part);
+    return s;
 }
 
 // F (M x 64 raw features) -> Y (M x 6)
@@ -752,6 +874,20 @@ extern "C" lc_status lc_record_motion(lc_ctx* ctx) {
     WarmState& w = *ctx->warm;
     record_motion_kernel<<<(w.n + 127) / 128, 128, 0, ctx->stream>>>(ctx->dC, w.Rprev, w.tprev, w.motion);
     return ctx->cuda(cudaGetLastError(), "record motion");
+}
+
+extern "C" lc_status lc_read_motion(lc_ctx* ctx, float* u) {
+    if (!ctx || !u) return LC_ERR_ARG;
+    if (!ctx->warm || ctx->warm->n != ctx->hC.n)
+        return ctx->fail(LC_ERR_STATE, "lc_read_motion: no motion recorded for this graph");
+    cudaSetDevice(ctx->device);
+    // float4 rows (x, y, z, 0) -> three floats each: n x (d_omega, d_t)
+    lc_status s = ctx->cuda(cudaMemcpy2DAsync(u, 3 * sizeof(float), ctx->warm->motion, sizeof(float4),
+                                              3 * sizeof(float), 2 * (size_t)ctx->warm->n, cudaMemcpyDefault,
+                                              ctx->stream),
+                            "copy out");
+    if (s) return s;
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "synchronize");
 }
 
 // the warm-start sequence on the context's stream (captured once per network)

@@ -66,6 +66,7 @@ _SIGS = {
     "lc_set_camera": [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int],
     "lc_upload_template": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P],
     "lc_build_graph": [_P, ctypes.c_int, ctypes.c_int],
+    "lc_upload_graph": [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P],
     "lc_read_graph": [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)],
     "lc_set_node_params": [_P, _P, _P],
     "lc_upload_frame": [_P, _P, _P, _P, _P, _P],
@@ -92,12 +93,16 @@ _SIGS = {
     "lc_mlp_destroy": [_P],
     "lc_mlp_last_error": [_P],
     "lc_mlp_get_params": [_P, _P],
+    "lc_mlp_set_scaling": [_P, _P, _P, _P],
+    "lc_mlp_get_scaling": [_P, _P, _P, _P],
+    "lc_mlp_fit_scaling": [_P, _P, _P, ctypes.c_longlong],
     "lc_mlp_forward": [_P, _P, ctypes.c_int, _P],
     "lc_mlp_gradient": [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)],
     "lc_mlp_train_step": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
     "lc_node_features": [_P, _P],
     "lc_read_stats": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_record_motion": [_P],
+    "lc_read_motion": [_P, _P],
     "lc_warm_start": [_P, _P, ctypes.POINTER(ctypes.c_int), _P],
     "lc_solve_pose": [_P, ctypes.POINTER(lc_solve_stats)],
     "lc_eval_pose": [_P, _P, _P, _P, _P],
@@ -199,6 +204,7 @@ class Context:
             st = getattr(stream, "cuda_stream", stream)
         self._check(self._lib.lc_create(ctypes.byref(h), device, st), None)
         self.h = h
+        self.device = device
         self.N = self.n = self.K = 0
         self.W = self.H = 0
         self.n_dof = 0
@@ -256,6 +262,19 @@ class Context:
     def build_graph(self, n_nodes: int, K: int):
         self._check(self._lib.lc_build_graph(self.h, int(n_nodes), int(K)))
         self.n, self.K = int(n_nodes), int(K)
+
+    def upload_graph(self, node_vid, bind_idx, bind_w, edge_off, edge_dst, edge_s):
+        """A caller-built graph (the layout of read_graph)."""
+        node_vid = _arr(node_vid, np.int32)
+        bind_idx = _arr(bind_idx, np.int32)
+        bind_w = _arr(bind_w, np.float32)
+        edge_off = _arr(edge_off, np.int32)
+        edge_dst = _arr(edge_dst, np.int32)
+        edge_s = _arr(edge_s, np.float32)
+        n, K = int(node_vid.shape[0]), int(bind_idx.shape[1])
+        self._check(self._lib.lc_upload_graph(self.h, n, K, _ptr(node_vid), _ptr(bind_idx), _ptr(bind_w),
+                                              _ptr(edge_off), _ptr(edge_dst), _ptr(edge_s)))
+        self.n, self.K = n, K
 
     def read_graph(self) -> dict:
         ne = ctypes.c_int(0)
@@ -345,13 +364,21 @@ class Context:
         return out
 
     # ---- learned warm start
-    def node_features(self) -> np.ndarray:
-        F = np.zeros((self.n, 64), np.float32)
+    def node_features(self, out=None) -> np.ndarray:
+        """Features n x 64 (host array, or ``out``: a device tensor)."""
+        F = np.zeros((self.n, 64), np.float32) if out is None else out
         self._check(self._lib.lc_node_features(self.h, _ptr(F)))
         return F
 
     def record_motion(self):
         self._check(self._lib.lc_record_motion(self.h))
+
+    def read_motion(self, out=None) -> np.ndarray:
+        """Motion of the last record_motion, n x 6 (host array, or ``out``:
+        a device tensor / pointer-bearing array of n x 6 floats)."""
+        u = np.zeros((self.n, 6), np.float32) if out is None else out
+        self._check(self._lib.lc_read_motion(self.h, _ptr(u)))
+        return u
 
     def warm_start(self, mlp, sync: bool = True):
         if not sync:
@@ -549,6 +576,20 @@ class MLP:
         out = np.zeros(MLP_PARAMS, np.float32)
         self._check(self._lib.lc_mlp_get_params(self.h, _ptr(out)))
         return out
+
+    def set_scaling(self, mu=None, sigma=None, s_out=None):
+        keep = [_arr(a, np.float32) for a in (mu, sigma, s_out)]
+        self._check(self._lib.lc_mlp_set_scaling(self.h, *[_ptr(a) for a in keep]))
+
+    def scaling(self):
+        """(mu, sigma, s_out) as host arrays."""
+        mu, sigma, s_out = np.zeros(64, np.float32), np.zeros(64, np.float32), np.zeros(6, np.float32)
+        self._check(self._lib.lc_mlp_get_scaling(self.h, _ptr(mu), _ptr(sigma), _ptr(s_out)))
+        return mu, sigma, s_out
+
+    def fit_scaling(self, F_dev, T_dev):
+        """mu / sigma / s_out from device arrays F (rows x 64), T (rows x 6)."""
+        self._check(self._lib.lc_mlp_fit_scaling(self.h, _ptr(F_dev), _ptr(T_dev), int(F_dev.shape[0])))
 
     def forward(self, F) -> np.ndarray:
         F = _arr(F, np.float32)

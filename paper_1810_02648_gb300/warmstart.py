@@ -1,18 +1,20 @@
 """Training and evaluation of the learned warm start (host-side driver).
 
 Every computation runs in the library's kernels (lc_node_features,
-lc_solve_nonrigid, lc_mlp_*, lc_warm_start); this module only sequences
-them over a capture's frames:
+lc_solve_nonrigid, lc_record_motion / lc_read_motion, lc_mlp_*,
+lc_warm_start); this module only sequences them over a capture's frames and
+keeps the results in device memory:
 
 * ``collect``: track a sequence with the plain method (each frame solved from
   the previous frame's result) and record, per frame and node, the features
-  at the start and the update the solve converged to: Log(R_end R_start^T)
-  and t_end - t_start.
-* ``train``: Adam on (features, update) pairs with per-feature
-  normalisation, minibatches drawn by a seeded generator.
-* ``evaluate``: per frame, the plain solve (n_gn steps) and the warm-started
-  solve that stops once it reaches the plain solve's final energy (within a
-  relative tolerance), both timed with CUDA events.
+  at the start and the update the solve made (the motion recorded after it:
+  Log(R_end R_start^T), t_end - t_start).
+* ``train``: the network's input normalisation and output scale fitted to the
+  rows on the device, then Adam on minibatches drawn by a seeded generator.
+* ``evaluate``: per frame, the plain method's energy after its full step
+  budget is the target; the plain solve from the previous frame's result and
+  the warm-started solve then both run with the same target-energy stop, and
+  both are timed with CUDA events.
 """
 from __future__ import annotations
 
@@ -21,43 +23,37 @@ import numpy as np
 from .livecap import MLP, MLP_PARAMS
 
 
-def _rot_log(R):
-    R = np.asarray(R, dtype=np.float64)
-    c = np.clip(0.5 * (np.trace(R, axis1=-2, axis2=-1) - 1.0), -1.0, 1.0)
-    th = np.arccos(c)
-    v = np.stack([R[..., 2, 1] - R[..., 1, 2], R[..., 0, 2] - R[..., 2, 0], R[..., 1, 0] - R[..., 0, 1]], -1)
-    s = np.sin(th)
-    f = np.where(th < 1e-7, 0.5, th / (2.0 * np.where(s == 0.0, 1.0, s)))
-    return v * f[..., None]
-
-
-def node_update(start: dict, end: dict) -> np.ndarray:
-    """(Log(R_end R_start^T), t_end - t_start) per node, n x 6."""
-    Rd = np.einsum("nij,nkj->nik", end["R"].astype(np.float64), start["R"].astype(np.float64))
-    return np.concatenate([_rot_log(Rd), end["t"].astype(np.float64) - start["t"]], 1)
-
-
 def _upload(ctx, frame):
     rgb, dt, mask = frame
     ctx.upload_frame(rgb, dt, np.asarray(mask, dtype=np.uint8), None, None)
 
 
-def collect(ctx, frames):
-    """Plain tracking of ``frames`` (list of (rgb, dt, mask)) from the
-    context's current node parameters.  Returns features (T, n, 64),
-    targets (T, n, 6) and the plain final energies (T)."""
+def collect(ctx, frames, skip: int = 0):
+    """Plain tracking of ``frames`` (an iterable of (rgb, dt, mask)) from the
+    context's current node parameters.  Returns features (T, n, 64) and
+    targets (T, n, 6) as device tensors and the plain final energies (T) of
+    the frames after the first ``skip`` (those are tracked but not kept)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
     F, Tg, E = [], [], []
-    for fr in frames:
+    for i, fr in enumerate(frames):
         _upload(ctx, fr)
-        start = ctx.read_back(V=False, flags=False)
-        ctx.compute_visibility()
-        F.append(ctx.node_features())
+        keep = i >= skip
+        if keep:
+            ctx.compute_visibility()
+            f = torch.empty((ctx.n, 64), dtype=torch.float32, device=dev)
+            ctx.node_features(out=f)
         st = ctx.solve_nonrigid()
-        end = ctx.read_back(V=False, flags=False)
-        Tg.append(node_update(start, end))
-        E.append(st["e_total"])
         ctx.record_motion()
-    return np.stack(F), np.stack(Tg).astype(np.float32), np.array(E)
+        if keep:
+            u = torch.empty((ctx.n, 6), dtype=torch.float32, device=dev)
+            ctx.read_motion(out=u)
+            F.append(f)
+            Tg.append(u)
+            E.append(st["e_total"])
+    if not F:
+        return (torch.empty((0, ctx.n, 64), device=dev), torch.empty((0, ctx.n, 6), device=dev), np.zeros(0))
+    return torch.stack(F), torch.stack(Tg), np.array(E)
 
 
 def init_params(seed: int) -> np.ndarray:
@@ -72,94 +68,105 @@ def init_params(seed: int) -> np.ndarray:
 
 
 def train(F, T, steps: int, batch: int = 1024, lr: float = 1e-3, seed: int = 0, device: int = 0,
-          target_scale: float | None = None, log_every: int = 0):
-    """Adam on rows of F (rows x 64) / T (rows x 6).  Targets are scaled by
-    1 / target_scale inside the loss (the network's output is scaled back by
-    the caller through ``Predictor``).  Returns (Predictor, losses)."""
-    import torch
-    F = np.asarray(F, dtype=np.float32).reshape(-1, 64)
-    T = np.asarray(T, dtype=np.float32).reshape(-1, 6)
-    mu = F.mean(0)
-    sigma = F.std(0)
-    sigma[sigma < 1e-12] = 1.0
-    mu[63], sigma[63] = 0.0, 1.0                      # keep the constant feature as is
-    s = float(target_scale) if target_scale else float(np.abs(T).std() + 1e-12)
-    net = MLP(device, init_params(seed), mu, sigma)
-    Fd = torch.from_numpy(F).to(f"cuda:{device}")
-    Td = torch.from_numpy(T / s).to(f"cuda:{device}")
+          log_every: int = 0):
+    """Adam on the rows of F (device, rows x 64) / T (device, rows x 6) after
+    fitting the network's scaling to them (lc_mlp_fit_scaling).  Returns
+    (network, losses)."""
+    F = F.reshape(-1, 64).contiguous()
+    T = T.reshape(-1, 6).contiguous()
+    net = MLP(device, init_params(seed))
+    net.fit_scaling(F, T)
     rng = np.random.default_rng(seed + 1)
     losses = []
     rows = F.shape[0]
     for k in range(steps):
         idx = rng.integers(0, rows, size=min(batch, rows)).astype(np.int32)
         want = log_every and (k % log_every == 0 or k == steps - 1)
-        L = net.train_step(Fd, Td, idx, lr, want_loss=bool(want))
+        L = net.train_step(F, T, idx, lr, want_loss=bool(want))
         if want:
             losses.append((k, L))
-    return Predictor(net, s), losses
+    return net, losses
 
 
-class Predictor:
-    """The trained network plus the scale of its targets: the output layer is
-    rescaled in place so that the network predicts the update directly."""
+def evaluate(plain_ctx, warm_ctx, net: MLP, frames, streams, rel_tol: float = 1e-4):
+    """Plain vs warm-started solves along the plain trajectory, with one
+    stopping rule for both.
 
-    def __init__(self, net: MLP, scale: float):
-        theta = net.params()
-        theta[-6 - 256 * 6:] *= scale                  # W3 and b3
-        self.net = MLP(net.device, theta, *self._norm(net))
-        self.scale = scale
-        net.close()
-
-    @staticmethod
-    def _norm(net):
-        return net._keep[1], net._keep[2]
-
-    def close(self):
-        self.net.close()
-
-
-def evaluate(plain_ctx, warm_ctx, pred: Predictor, frames, streams, rel_tol: float = 1e-4):
-    """Plain vs warm-started solves along the plain trajectory.
-
-    ``plain_ctx`` runs its n_gn steps from the previous frame's result;
-    ``warm_ctx`` (same capture, normally a larger n_gn budget) starts from
-    the same parameters, applies the network's prediction (kept only if it
-    does not raise the energy) and runs Gauss-Newton until its energy is
-    within rel_tol of the plain solve's final energy (the solve's
-    target-energy stop).  Both are timed with CUDA events on their streams
-    (``streams`` = (plain, warm) torch streams).  Returns per-frame records."""
+    Per frame: an untimed reference solve of ``plain_ctx`` (its full n_gn
+    steps from the previous frame's result: a target below every energy)
+    gives the energy E* that the plain method reaches.  Then, from the same
+    start and with the target-energy stop at E* (1 + rel_tol): the plain
+    solve (``plain_ctx``) and the warm-started one (``warm_ctx``, normally a
+    larger step budget: the network's prediction, kept only if it does not
+    raise the energy, then Gauss-Newton), each timed with CUDA events on its
+    stream (``streams`` = (plain, warm) torch streams).  Every solve runs
+    with a target, so the captured graphs are reused (only the target's
+    value changes); the warm arm runs once untimed on the first frame to
+    capture its graphs.  Both contexts continue from the reference solve's
+    result.  Returns per-frame records."""
     import torch
     out = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     sp, sw = streams
-    for fr in frames:
+    never = 1e-30
+    for k, fr in enumerate(frames):
         _upload(plain_ctx, fr)
         _upload(warm_ctx, fr)
         start = plain_ctx.read_back(V=False, flags=False)
         n = start["R"].shape[0]
+        if k == 0:
+            warm_ctx.set_params(target_energy=never)
+            warm_ctx.set_node_params(start["R"].reshape(n, 9), start["t"])
+            warm_ctx.warm_start(net, sync=False)
+            warm_ctx.solve_nonrigid(stats=False)
+        plain_ctx.set_params(target_energy=never)
+        ref = plain_ctx.solve_nonrigid()
+        end = plain_ctx.read_back(V=False, flags=False)
+        e_star = float(ref["e_total"])
+        target = e_star * (1.0 + rel_tol)
+        # plain, same start, target stop
+        plain_ctx.set_node_params(start["R"].reshape(n, 9), start["t"])
+        plain_ctx.set_params(target_energy=target)
         torch.cuda.synchronize()
         ev[0].record(sp)
         plain_ctx.solve_nonrigid(stats=False)
         ev[1].record(sp)
         torch.cuda.synchronize()
-        plain_stats = plain_ctx.read_stats()
-        plain = plain_ctx.read_back(V=False, flags=False)
-        e_plain = plain_stats["e_total"]
+        ps = plain_ctx.read_stats()
+        # warm start + Gauss-Newton, same start, same target stop
         warm_ctx.set_node_params(start["R"].reshape(n, 9), start["t"])
-        warm_ctx.set_params(target_energy=float(e_plain) * (1.0 + rel_tol))
+        warm_ctx.set_params(target_energy=target)
         torch.cuda.synchronize()
         ev[2].record(sw)
-        warm_ctx.warm_start(pred.net, sync=False)
+        warm_ctx.warm_start(net, sync=False)
         warm_ctx.solve_nonrigid(stats=False)
         ev[3].record(sw)
         torch.cuda.synchronize()
-        st = warm_ctx.read_stats()
+        ws = warm_ctx.read_stats()
+        e0_plain, e0_warm = ps["e_gn_all"][0], ws["e_gn_all"][0]
         out.append(dict(plain_ms=ev[0].elapsed_time(ev[1]), warm_ms=ev[2].elapsed_time(ev[3]),
-                        e_plain=e_plain, e_warm=st["e_total"], steps_plain=plain_stats["n_gn_done"],
-                        steps_warm=st["n_gn_done"],
-                        reached=bool(st["e_total"] <= e_plain * (1.0 + rel_tol))))
+                        e_star=e_star, e_plain=ps["e_total"], e_warm=ws["e_total"],
+                        steps_ref=ref["n_gn_done"], steps_plain=ps["n_gn_done"], steps_warm=ws["n_gn_done"],
+                        e_start=e0_plain, e_predicted=e0_warm, kept=bool(e0_warm < e0_plain),
+                        reached_plain=bool(ps["e_total"] <= target), reached_warm=bool(ws["e_total"] <= target)))
         # both continue along the plain trajectory
-        warm_ctx.set_node_params(plain["R"].reshape(n, 9), plain["t"])
-        plain_ctx.record_motion()
-        warm_ctx.record_motion()
+        for c in (plain_ctx, warm_ctx):
+            c.set_node_params(end["R"].reshape(n, 9), end["t"])
+            c.record_motion()
     return out
+
+
+def summary(res) -> dict:
+    """Frames/s of both arms over the records of ``evaluate`` and the
+    step counts (the warm arm's unreached frames count with their time)."""
+    plain_ms = float(np.sum([r["plain_ms"] for r in res]))
+    warm_ms = float(np.sum([r["warm_ms"] for r in res]))
+    return dict(frames=len(res), plain_frames_per_s=len(res) / (plain_ms / 1e3),
+                warm_frames_per_s=len(res) / (warm_ms / 1e3), gain=plain_ms / warm_ms,
+                reached_plain=float(np.mean([r["reached_plain"] for r in res])),
+                reached_warm=float(np.mean([r["reached_warm"] for r in res])),
+                kept=float(np.mean([r["kept"] for r in res])),
+                steps_plain_mean=float(np.mean([r["steps_plain"] for r in res])),
+                steps_warm_mean=float(np.mean([r["steps_warm"] for r in res])),
+                steps_warm_median=float(np.median([r["steps_warm"] for r in res])),
+                start_energy_ratio_median=float(np.median([r["e_predicted"] / r["e_start"] for r in res])))

@@ -20,7 +20,10 @@ from .scenes import (  # noqa: F401
     half_split_material,
     smooth_deformation,
     rbf_field,
+    rbf_field_linear,
+    ar1_draws,
     ar1_sequence,
+    ar1_frame,
     render_frame,
     render,
     contour_distance_transform,

@@ -415,11 +415,35 @@ def smooth_deformation(V: np.ndarray, n_ctrl: int, sigma_rot: float,
     return dict(V=rbf_field(V, c, aa, tt, rho), ctrl_ids=ids, aa=aa, t=tt, rho=rho)
 
 
-def ar1_sequence(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma_t: float,
-                 seed: int, rho_ar: float = 0.9) -> List[np.ndarray]:
-    """Deformed vertex positions of a sequence whose control-point rotations
-    and translations follow AR(1): x_t = rho x_{t-1} + sqrt(1 - rho^2) sigma
-    eps_t, started from the stationary distribution."""
+def rbf_field_linear(V: np.ndarray, ctrl: np.ndarray, aa: np.ndarray, tt: np.ndarray, rho: float) -> np.ndarray:
+    """The field of ``rbf_field`` written as one blended 3x3 matrix and
+    offset per vertex (the blend of rigid motions is linear in the vertex):
+    sum_m phi_m (R_m (v - c_m) + c_m + t_m) = (sum_m phi_m R_m) v
+    + sum_m phi_m (c_m + t_m - R_m c_m).  Equal to ``rbf_field`` up to
+    rounding and several times faster; used for long sequences."""
+    V = np.asarray(V, dtype=np.float64)
+    ctrl = np.asarray(ctrl, dtype=np.float64)
+    R = _rodrigues(aa)
+    off = ctrl + tt - np.einsum("mij,mj->mi", R, ctrl)
+    out = np.empty_like(V)
+    chunk = 8192
+    for s in range(0, len(V), chunk):
+        v = V[s:s + chunk]
+        d2 = ((v[:, None, :] - ctrl[None, :, :]) ** 2).sum(-1)
+        lw = -d2 / (2.0 * rho * rho)
+        lw -= lw.max(axis=1, keepdims=True)
+        phi = np.exp(lw)
+        phi /= phi.sum(axis=1, keepdims=True)
+        A = (phi @ R.reshape(-1, 9)).reshape(-1, 3, 3)
+        out[s:s + chunk] = np.einsum("nij,nj->ni", A, v) + phi @ off
+    return out
+
+
+def ar1_draws(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma_t: float,
+              seed: int, rho_ar: float = 0.9):
+    """Control points, RBF width and the per-frame control-point rotations
+    and translations (aa, tt) of an AR(1) sequence: x_t = rho x_{t-1} +
+    sqrt(1 - rho^2) sigma eps_t, started from the stationary distribution."""
     rng = np.random.default_rng(seed + 3000)
     V = np.asarray(V, dtype=np.float64)
     ids = np.sort(rng.choice(len(V), size=n_ctrl, replace=False))
@@ -428,12 +452,30 @@ def ar1_sequence(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, si
     aa = rng.normal(0.0, sigma_rot, size=(n_ctrl, 3))
     tt = rng.normal(0.0, sigma_t, size=(n_ctrl, 3))
     k = math.sqrt(1.0 - rho_ar * rho_ar)
-    out = []
+    draws = []
     for _ in range(n_frames):
-        out.append(rbf_field(V, c, aa, tt, rho))
+        draws.append((aa, tt))
         aa = rho_ar * aa + k * rng.normal(0.0, sigma_rot, size=aa.shape)
         tt = rho_ar * tt + k * rng.normal(0.0, sigma_t, size=tt.shape)
-    return out
+    return c, rho, draws
+
+
+def ar1_sequence(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma_t: float,
+                 seed: int, rho_ar: float = 0.9) -> List[np.ndarray]:
+    """Deformed vertex positions of a sequence whose control-point rotations
+    and translations follow AR(1) (``ar1_draws``)."""
+    c, rho, draws = ar1_draws(V, n_frames, n_ctrl, sigma_rot, sigma_t, seed, rho_ar)
+    return [rbf_field(V, c, aa, tt, rho) for aa, tt in draws]
+
+
+def ar1_frame(V: np.ndarray, n_ctrl: int, sigma_rot: float, sigma_t: float, seed: int, i: int,
+              rho_ar: float = 0.9) -> np.ndarray:
+    """Frame i of the AR(1) sequence of ``seed`` on its own (the draws up to
+    i are repeated, the field is ``rbf_field_linear``): lets a pool
+    generate one long sequence's frames in parallel."""
+    c, rho, draws = ar1_draws(V, i + 1, n_ctrl, sigma_rot, sigma_t, seed, rho_ar)
+    aa, tt = draws[i]
+    return rbf_field_linear(V, c, aa, tt, rho)
 
 
 def render_frame(V_target: np.ndarray, F: np.ndarray, albedo: np.ndarray, cam: Camera, seed: int,

@@ -21,12 +21,14 @@ def test_parameter_count():
     assert np.array_equal(mlp.pack(parts), np.arange(mlp.N_PARAMS))
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("scaled", [False, True])
+def test_backward_matches_finite_differences(scaled):
     rng = np.random.default_rng(1)
     theta = _theta(2)
     x = rng.normal(size=(7, 64))
     t = rng.normal(size=(7, 6))
-    y, cache = mlp.forward(theta, x)
+    s_out = rng.uniform(0.01, 3.0, size=6) if scaled else None
+    y, cache = mlp.forward(theta, x, s_out)
     # keep every pre-activation away from the ReLU kink for the FD step
     assert min(np.abs(cache[1]).min(), np.abs(cache[3]).min()) > 1e-5
     L, dy = mlp.loss(y, t)
@@ -42,7 +44,7 @@ def test_backward_matches_finite_differences():
         tp, tm = theta.copy(), theta.copy()
         tp[j] += h
         tm[j] -= h
-        fd = (mlp.loss(mlp.forward(tp, x)[0], t)[0] - mlp.loss(mlp.forward(tm, x)[0], t)[0]) / (2 * h)
+        fd = (mlp.loss(mlp.forward(tp, x, s_out)[0], t)[0] - mlp.loss(mlp.forward(tm, x, s_out)[0], t)[0]) / (2 * h)
         assert abs(fd - g[j]) <= 1e-6 * max(1.0, abs(g[j])), (j, fd, g[j])
 
 
@@ -114,3 +116,50 @@ def test_node_features_hand_example():
     assert np.allclose(f[57:63], u_prev[1]) and f[63] == 1.0
     # node 1: its only vertex is inactive (zero residuals, no flags)
     assert np.allclose(F[1, 24:47], 0.0) and F[1, 47] == 1.0 and np.allclose(F[1, 57:63], u_prev[0])
+
+
+def test_output_scale_multiplies_each_output():
+    rng = np.random.default_rng(6)
+    theta = _theta(7)
+    x = rng.normal(size=(4, 64))
+    s_out = np.array([0.5, 2.0, 1.0, 1e-3, 7.0, 1.0])
+    y1, _ = mlp.forward(theta, x)
+    y2, _ = mlp.forward(theta, x, s_out)
+    assert np.allclose(y2, y1 * s_out, rtol=1e-14, atol=0)
+
+
+def test_fit_scaling_normalises_the_training_rows():
+    """After fitting, the normalised features have zero mean and unit
+    population variance per column (the constant column and a constant
+    feature excepted) and the scaled targets unit root mean square."""
+    rng = np.random.default_rng(8)
+    F = rng.normal(size=(500, 64)) * rng.uniform(1e-3, 50.0, size=64) + rng.normal(scale=20.0, size=64)
+    F[:, 63] = 1.0
+    F[:, 10] = 4.25                       # a constant feature
+    T = rng.normal(size=(500, 6)) * np.array([0.02, 0.03, 0.01, 2e-3, 1e-3, 5e-3]) + 1e-3
+    T[:, 5] = 0.0                         # an all-zero target column
+    mu, sigma, s_out = mlp.fit_scaling(F, T)
+    X = (F - mu) / sigma
+    live = [j for j in range(63) if j != 10]
+    assert np.allclose(X[:, live].mean(0), 0.0, atol=1e-9)     # rounding of a mean ~20 over sigma ~1e-3
+    assert np.allclose(X[:, live].std(0), 1.0, rtol=1e-9)
+    assert mu[63] == 0.0 and sigma[63] == 1.0 and np.all(X[:, 63] == 1.0)
+    assert sigma[10] == 1.0 and np.all(X[:, 10] == 0.0)
+    Ts = T[:, :5] / s_out[:5]
+    assert np.allclose(np.sqrt((Ts * Ts).mean(0)), 1.0, rtol=1e-12)
+    assert s_out[5] == 1.0
+
+
+def test_node_motion_recovers_the_applied_rotation():
+    """R_end = Exp(w) R_start (library exponential) gives back w; the
+    translation part is the plain difference."""
+    rng = np.random.default_rng(9)
+    n = 50
+    Rs = Rotation.from_rotvec(rng.normal(scale=0.8, size=(n, 3))).as_matrix()
+    w = rng.normal(size=(n, 3))
+    w *= (rng.uniform(1e-4, 2.5, size=n) / np.linalg.norm(w, axis=1))[:, None]
+    Re = np.einsum("nij,njk->nik", Rotation.from_rotvec(w).as_matrix(), Rs)
+    ts, te = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    u = mlp.node_motion(Rs.reshape(n, 9), ts, Re.reshape(n, 9), te)
+    assert np.allclose(u[:, :3], w, atol=1e-9)
+    assert np.array_equal(u[:, 3:], te - ts)

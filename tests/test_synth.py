@@ -108,3 +108,20 @@ def test_splitmix64_reference_values():
     assert got[0] == 0xE220A8397B1DCDAF
     assert got[1] == 0x6E789E6AA1B965F4
     assert got[2] == 0x06C45D188009454F
+
+
+def test_ar1_frame_matches_the_sequence():
+    """A frame generated on its own (blended-matrix field) equals the same
+    frame of the serial sequence (per-control blend) up to rounding, and the
+    AR(1) draws keep their stationary scale."""
+    V, _ = synth.capsule_mesh(0.3, 1.0, 12, 10)
+    seq = synth.ar1_sequence(V, 6, 20, 0.05, 0.01, seed=4)
+    for i in (0, 3, 5):
+        one = synth.ar1_frame(V, 20, 0.05, 0.01, seed=4, i=i)
+        assert np.abs(one - seq[i]).max() <= 1e-12
+    _, _, draws = synth.ar1_draws(V, 400, 50, 0.05, 0.01, seed=5)
+    aa = np.stack([d[0] for d in draws])
+    assert 0.045 < aa.std() < 0.055
+    # lag-one correlation of the rotations: rho = 0.9
+    r = (aa[1:] * aa[:-1]).mean() / (aa * aa).mean()
+    assert 0.85 < r < 0.95
