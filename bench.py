@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["body", "tiny", "stress", "batch", "warmstart", "surface",
+    ap.add_argument("--workload", choices=["body", "tiny", "stress", "stream", "batch", "warmstart", "surface",
                                            "surface-stress"], default="body",
                     help="surface*: the per-vertex surface stage (the paper's own unknowns) in place of the "
                          "embedded graph, on the body / stress capture")
@@ -56,6 +56,17 @@ def parse():
     ap.add_argument("--ws-adam-steps", type=int, default=20000, help="warm start: Adam steps")
     ap.add_argument("--ws-gn-block", type=int, default=2,
                     help="warm start: Gauss-Newton steps per conditional graph block, both arms")
+    ap.add_argument("--streams", type=int, default=8, help="stream: tracked sequences solved together")
+    ap.add_argument("--stream-frames", type=int, default=40, help="stream: frames per sequence")
+    ap.add_argument("--stream-scene", choices=["stress", "body"], default="stress", help="stream: the capture")
+    ap.add_argument("--stream-train-seqs", type=int, default=4, help="stream: warm-start training sequences")
+    ap.add_argument("--stream-train-len", type=int, default=8, help="stream: frames per training sequence")
+    ap.add_argument("--no-warm-start", action="store_true", help="stream: without the learned warm start")
+    ap.add_argument("--euler-start", action="store_true",
+                    help="stream: the pose stage starts from the explicit Euler step (default: the last solved pose)")
+    ap.add_argument("--carry-graph", action="store_true",
+                    help="stream: the non-rigid stage starts from the previous frame's node parameters, carried with "
+                         "the bones (default: the identity over the new skinned surface)")
     ap.add_argument("--batch-count", type=int, default=64, help="captures of the batch workload")
     ap.add_argument("--pcg-mode", type=int, default=-1, help="batch PCG strategy (-1: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample length")
@@ -1170,6 +1181,214 @@ def run_warmstart(a):
     warm.close()
 
 
+# ---------------------------------------------------------------------------
+# tracked streams: both stages per frame, warm start, one graph per frame step
+# ---------------------------------------------------------------------------
+def _stream_init(name):
+    """Pool initialiser: the capture (without its own target frame) per worker."""
+    sys.path.insert(0, ROOT)
+    import synth
+    _WS["synth"] = synth
+    _WS["sc"] = synth.make_scene(name, frame=False)
+
+
+def _stream_frame(args):
+    """Frame i of stream ``seed`` of the capture: (rgb, dt, mask, joints2d, joints3d)."""
+    seed, i = args
+    return _WS["synth"].stream_frame(_WS["sc"], seed, i)
+
+
+def run_stream(a):
+    """Tracked streams of one capture (default: the 100k-vertex, 4,000-node,
+    K = 8, 2048^2 stress capture), all solved together.  Frames are rendered
+    by a spawned pool (host cores) in step order while the GPU tracks them.
+    Per stream the first two frames go through the per-call API (pose stage,
+    non-rigid stage, motion and pose bookkeeping); from the third on, every
+    frame step is one CUDA graph over all streams (lc_batch_step: pose
+    stages, warm starts, the batched non-rigid stage, bookkeeping).  value =
+    frames of all streams per second of device time of the step graphs; e2e
+    adds the frames' upload from pinned host memory and the statistics'
+    read-back."""
+    import numpy as np
+    import torch
+
+    import synth
+    import ctypes
+
+    from paper_1810_02648_gb300 import Batch, Context
+    from paper_1810_02648_gb300 import warmstart as ws
+    from paper_1810_02648_gb300.livecap import lc_solve_stats
+    from synth import setup_scene
+
+    name, S, L = a.stream_scene, a.streams, a.stream_frames
+    sc = synth.make_scene(name, frame=False)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    use_net = not a.no_warm_start
+    train_seeds = [900 + k for k in range(a.stream_train_seqs)] if use_net else []
+    seeds = [100 + k for k in range(S)]
+    procs = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    t_start = time.perf_counter()
+    pool = mp.get_context("spawn").Pool(procs, initializer=_stream_init, initargs=(name,))
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    tasks = [(s_, i) for s_ in train_seeds for i in range(a.stream_train_len)]
+    tasks += [(seeds[j], i) for i in range(L) for j in range(S)]
+    it = pool.imap(_stream_frame, tasks, chunksize=1)
+    parts = not a.no_body_parts
+    ctxs = []
+    for j in range(S):
+        c = Context(0)
+        setup_scene(c, sc, with_frame=False)
+        c.set_params(graph_warp=1 if a.carry_graph else 0)
+        if parts:
+            c.set_body_parts(sc.skeleton["bone_part"], sc.skeleton["torso_part"], 10)
+        ctxs.append(c)
+    net, losses, t_train = None, [], 0.0
+    if use_net:
+        t0 = time.perf_counter()
+        Fs, Ts = [], []
+        for s_ in train_seeds:
+            ws.restart(ctxs[0], pose=True)
+            F, T, _ = ws.collect(ctxs[0], (next(it) for _ in range(a.stream_train_len)), skip=1, pose=True,
+                                 euler=a.euler_start, from_identity=not a.carry_graph)
+            Fs.append(F)
+            Ts.append(T)
+        net, losses = ws.train(torch.cat(Fs), torch.cat(Ts), steps=2000, batch=4096, lr=1e-3, seed=0,
+                               log_every=500)
+        rows = int(sum(f.shape[0] for f in Fs) * sc.n_nodes)
+        del Fs, Ts
+        torch.cuda.synchronize(dev)
+        t_train = time.perf_counter() - t0
+        ws.restart(ctxs[0], pose=True)
+    # the first two frames per stream through the per-call API
+    for i in range(2):
+        for j in range(S):
+            c = ctxs[j]
+            ws._upload(c, next(it))
+            if i > 0 and a.euler_start:
+                c.pose_extrapolate()
+            c.solve_pose(stats=False)
+            if not a.carry_graph:
+                c.set_node_params(None, None)
+                c.record_motion()
+            if i > 0 and net is not None:
+                c.warm_start(net, sync=False)
+            c.solve_nonrigid(stats=False)
+            c.record_motion()
+            c.pose_advance()
+    torch.cuda.synchronize(dev)
+    batch = Batch(ctxs)
+    ext = torch.cuda.ExternalStream(batch.stream_handle, device=dev)
+    steps = L - 2
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e2e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e2e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    W, H = sc.cam.W, sc.cam.H
+    pin = [dict(rgb=torch.empty((H, W, 3), dtype=torch.float32).pin_memory(),
+                dt=torch.empty((H, W), dtype=torch.float32).pin_memory(),
+                mask=torch.empty((H, W), dtype=torch.uint8).pin_memory(),
+                j2=torch.empty((23, 2), dtype=torch.float32).pin_memory(),
+                j3=torch.empty((23, 3), dtype=torch.float32).pin_memory()) for _ in range(S)]
+    stats_all, e_totals = [], []
+
+    clk = ClockSampler(0)
+    clk.__enter__()
+    wall = []
+    for k in range(steps):
+        frames = [next(it) for _ in range(S)]
+        for j, fr in enumerate(frames):
+            for key, arr in zip(("rgb", "dt", "mask", "j2", "j3"), fr):
+                pin[j][key].numpy()[...] = arr
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for j in range(S):
+            P = pin[j]
+            ctxs[j].upload_frame(P["rgb"], P["dt"], P["mask"], P["j2"], P["j3"])
+        torch.cuda.synchronize(dev)
+        ev0[k].record(ext)
+        batch.step(net, euler_start=a.euler_start, carry_graph=a.carry_graph, stats=False)
+        ev1[k].record(ext)
+        st = [c.read_stats() for c in ctxs]
+        wall.append(time.perf_counter() - t0)
+        e_totals.append([x["e_total"] for x in st])
+    torch.cuda.synchronize(dev)
+    clk.__exit__(None, None, None)
+    pool.close()
+    pool.join()
+    total_ms = sum(x.elapsed_time(y) for x, y in zip(ev0, ev1))
+    value = S * steps / (total_ms / 1e3)
+    e2e_value = S * steps / sum(wall)
+    # the batched J^T J p over all streams, L2 flushed before each call
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    reps = 20
+    batch.apply_jtj(stage=True)
+    j0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    j1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for r in range(reps):
+        with torch.cuda.stream(ext):
+            flush.zero_()
+        j0[r].record(ext)
+        batch.apply_jtj()
+        j1[r].record(ext)
+    torch.cuda.synchronize(dev)
+    jtj_ms = sum(x.elapsed_time(y) for x, y in zip(j0, j1)) / reps
+    last = [c.read_stats() for c in ctxs]
+    E = len(ctxs[0].read_graph()["edge_dst"])
+    jtj_bytes = sum(jtj_algorithmic_bytes(sc, x["n_visible"], E) for x in last)
+    peak, peak_kind = measured_peaks()
+    achieved = jtj_bytes / (jtj_ms * 1e-3) / 1e9
+    n_kernels = int(last[0]["n_kernels"])
+    h2d = S * (W * H * (12 + 4 + 1) + 23 * 5 * 4)
+    et = np.array(e_totals)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 2,
+        "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 solver (compensated-pair PCG)" + (", bf16 network" if use_net else ""), "data": "synthetic",
+        "config": {"workload": f"streams: {S} tracked {L}-frame sequences of the {name} capture ({sc.N} vertices, "
+                               f"{sc.n_nodes} nodes, K={sc.K}, {W}x{H}); smooth joint and root motion (sinusoids, "
+                               f"0.3-1 Hz at 25 frames/s, amplitudes 0.1 rad per angle, 0.05 rad / 3 cm at the root), AR(1) "
+                               f"control-point field (0.05 rad, 1 cm, rho 0.9); per frame the "
+                               f"pose stage ({sc.n_gn_pose} GN from "
+                               + ("the explicit Euler step), " if a.euler_start else "the last solved pose), ")
+                               + ("the learned warm start, " if use_net else "")
+                               + f"the non-rigid stage {sc.n_gn} GN x {sc.n_pcg} PCG from "
+                               + ("the previous frame's node parameters carried with the bones" if a.carry_graph
+                                  else "the identity over the new skinned surface") + "; "
+                               f"frames 3..{L} of all streams: one CUDA graph per frame step",
+                   "streams": S, "frames_per_stream": L, "timed_frame_steps": steps, "body_parts": parts,
+                   "euler_start": a.euler_start, "carry_graph": a.carry_graph,
+                   "warm_start": use_net, "warm_start_training_rows": rows if use_net else 0,
+                   "l2": "each step uploads new frames (17 MB per 2048^2 frame); no flush"},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(S * ctypes.sizeof(lc_solve_stats))},
+        "gpu_launches": n_kernels * steps,
+        "roofline": {"kernel": "jtj_vertex_kernel + jtj_node_kernel over all streams (one J^T J p each)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": jtj_bytes,
+                     "avg_launch_us": 1e3 * jtj_ms, "l2": "flushed before each timed call"},
+        "solve": {"e_total_median": float(np.median(et)), "e_total_max": float(et.max()),
+                  "e_total_last_step": [float(x) for x in et[-1]],
+                  "network_loss": [float(losses[0][1]), float(losses[-1][1])] if losses else None,
+                  "train_s": t_train, "wall_s": time.perf_counter() - t_start},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    if net is not None:
+        net.close()
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -1178,6 +1397,8 @@ def main():
         run_batch(a)
     elif a.workload == "warmstart":
         run_warmstart(a)
+    elif a.workload == "stream":
+        run_stream(a)
     elif a.workload in ("body", "tiny") and not path_options(a):
         run_frames(a)
     else:

@@ -5,9 +5,9 @@
  *
  * Conventions for every call
  * --------------------------
- *  - Every call returns an lc_status.  The first error is kept in the context
- *    and its message is returned by lc_last_error(); later calls keep
- *    returning their own status.  Device-side failures (a pivot <= 0 in the
+ *  - Every call returns an lc_status.  The message of the most recent failed
+ *    call on a context is returned by lc_last_error(); a failure leaves the
+ *    context usable for later calls, which return their own status.  Device-side failures (a pivot <= 0 in the
  *    pose Cholesky, a non-finite input) are reported through a status word
  *    that the next synchronising call reads.
  *  - Array arguments are plain pointers that may point to host memory or to
@@ -129,6 +129,15 @@ typedef struct {
                                is a conditional graph node that runs only while the target is
                                not reached (the steps after the target inside a block return at
                                once).  0 (default): all n_gn steps unrolled */
+    int graph_warp;         /* 1: displacement warping of the graph stage (the graph counterpart of
+                               Sec. 3.4's warping) with a skeleton: lc_pose_advance records every
+                               node's parameters in the rest pose through the dual-quaternion blend
+                               rotation Q_k of its node vertex at the frame's final pose
+                               (R^rest = Q^T R Q, t^rest = Q^T t), and the next pose solve ends by
+                               posing them with the solved pose (R = Q R^rest Q^T, t = Q t^rest),
+                               so the non-rigid stage starts from the previous frame's deformation
+                               carried along with the bones; a record is dropped by
+                               lc_pose_clear_history and by a new graph.  0 (default): off */
 } lc_params;
 
 #define LC_MAX_GN 64
@@ -354,7 +363,8 @@ lc_status lc_upload_skeleton(lc_ctx *ctx, int J, const int32_t *parents, const f
  * silhouette residual switched off (b_i = 0, LC_FLAG_MASKED).  bone_part
  * NULL switches the mask off.  Needs a skeleton (LC_ERR_STATE); labels above
  * 254, torso_part outside -1..254 or dilate_px outside 0..32: LC_ERR_ARG.
- * Contexts with a mask cannot join an lc_batch solve.  Synchronises. */
+ * In an lc_batch solve each member with a mask builds it in the same way.
+ * Synchronises. */
 lc_status lc_set_body_parts(lc_ctx *ctx, const int32_t *bone_part, int torso_part, int dilate_px);
 /* Inspection of the mask of the last frame decisions (synchronises): mask
  * H x W labels (255 = no part) and vertex_part N; either may be NULL. */
@@ -426,6 +436,7 @@ lc_status lc_eval_pose(lc_ctx *ctx, float *V_skinned, double *A, double *g, doub
  * reallocated makes the next solve rebuild the plan).  The pose stage is not
  * batched: run lc_solve_pose per context first. */
 typedef struct lc_batch lc_batch;
+typedef struct lc_mlp lc_mlp;   /* the warm-start network, below */
 
 /* PCG strategy of a batch: */
 #define LC_BATCH_PCG_AUTO 0           /* each capture as on its own (smallest cluster that fits,
@@ -464,6 +475,29 @@ void *lc_batch_stream(const lc_batch *batch);
  * previous lc_batch_solve.  Enqueue only. */
 lc_status lc_batch_apply_jtj(lc_batch *batch, int stage);
 
+/* One frame step of every member as one CUDA graph (Sec. 3.3-3.4, the
+ * per-frame sequence of a tracked stream): per member the pose solve
+ * (lc_solve_pose), started from the explicit Euler step (lc_pose_extrapolate)
+ * with LC_STEP_EULER_START, else from the member's last solved pose; unless
+ * LC_STEP_CARRY_GRAPH, the node parameters reset to the identity over the new
+ * skinned surface followed by lc_record_motion (so that the motion recorded
+ * after the solve is the frame's update from that start); with a network
+ * (non-null), the warm start (lc_warm_start: prediction kept iff the energy
+ * does not rise, frame decisions of the start kept); then the non-rigid
+ * stage of all members in one launch per phase from their current
+ * parameters (lc_batch_solve with from_identity = 0); then per member
+ * lc_record_motion and lc_pose_advance.
+ * Each member must have a skeleton, a frame uploaded for this step and two
+ * recorded frames (two lc_pose_advance calls, so that the pose history no
+ * longer changes on the host), else LC_ERR_STATE; profiling must be off.
+ * Other flag bits: LC_ERR_ARG.  The graph is captured on the first call and
+ * again when the members' descriptors, the network or the flags change; the result is that of the calls above
+ * made one after the other.  stats (nullable, one per member in caller
+ * order: the non-rigid stage's statistics) makes the call synchronise. */
+#define LC_STEP_EULER_START 1u
+#define LC_STEP_CARRY_GRAPH 2u
+lc_status lc_batch_step(lc_batch *batch, lc_mlp *mlp, unsigned flags, lc_solve_stats *stats);
+
 /* ---- learned warm start (the project's addition to the paper's solver) ---- */
 
 /* The paper starts each frame's non-rigid solve from the previous frame's
@@ -493,7 +527,6 @@ lc_status lc_batch_apply_jtj(lc_batch *batch, int stage);
  *   48-50 g_k   51-56 u_k: the node's motion over the last frame (lc_record_motion)
  *   57-62 mean u_l over the node's graph neighbours   63 1 */
 #define LC_MLP_PARAMS 83974
-typedef struct lc_mlp lc_mlp;
 
 /* params (LC_MLP_PARAMS, null = zeros), mu / sigma (64 each, null = 0 / 1;
  * sigma <= 0 is treated as 1): host or device. */

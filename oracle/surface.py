@@ -324,6 +324,25 @@ def warped_start(VS: np.ndarray, Q: np.ndarray, dh: np.ndarray) -> np.ndarray:
     return np.asarray(VS, np.float64) + np.einsum("nij,nj->ni", Q, dh)
 
 
+def graph_rest_params(R: np.ndarray, t: np.ndarray, node_vid: np.ndarray, Q: np.ndarray):
+    """The graph counterpart of the displacement warping: node k's
+    parameters carried to the rest pose through the blend rotation
+    Q_k = Q[node_vid[k]] of its node vertex, R^rest = Q_k^T R_k Q_k and
+    t^rest = Q_k^T t_k.  R (n,3,3) or (n,9), t (n,3)."""
+    Qk = np.asarray(Q, dtype=np.float64)[np.asarray(node_vid, dtype=np.int64)]
+    Rn = np.asarray(R, dtype=np.float64).reshape(-1, 3, 3)
+    return (np.einsum("nji,njk,nkl->nil", Qk, Rn, Qk),
+            np.einsum("nji,nj->ni", Qk, np.asarray(t, dtype=np.float64).reshape(-1, 3)))
+
+
+def graph_posed_params(R_rest: np.ndarray, t_rest: np.ndarray, node_vid: np.ndarray, Q: np.ndarray):
+    """Rest-pose node parameters posed with the blend rotations Q of a new
+    pose: R_k = Q_k R^rest_k Q_k^T, t_k = Q_k t^rest_k."""
+    Qk = np.asarray(Q, dtype=np.float64)[np.asarray(node_vid, dtype=np.int64)]
+    return (np.einsum("nij,njk,nlk->nil", Qk, np.asarray(R_rest, dtype=np.float64), Qk),
+            np.einsum("nij,nj->ni", Qk, np.asarray(t_rest, dtype=np.float64)))
+
+
 # ----------------------------------------------------------------------------
 # Assembling a problem from scene data
 # ----------------------------------------------------------------------------

@@ -212,7 +212,7 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
         p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
         !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3 || p->pose_displacement < 0 ||
-        p->pose_displacement > 1 || p->gn_block < 0)
+        p->pose_displacement > 1 || p->gn_block < 0 || p->graph_warp < 0 || p->graph_warp > 1)
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     for (int j = 0; j < 3; ++j)
         if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)
@@ -225,7 +225,7 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
         p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
-    if (p->n_gn_pose != ctx->params.n_gn_pose) ctx->pose_drop_graph();
+    if (p->n_gn_pose != ctx->params.n_gn_pose || p->graph_warp != ctx->params.graph_warp) ctx->pose_drop_graph();
     const bool pyr_changed = p->pyr_levels != ctx->params.pyr_levels ||
                              memcmp(p->pyr_ksize, ctx->params.pyr_ksize, sizeof(p->pyr_ksize)) != 0;
     ctx->params = *p;
@@ -558,6 +558,7 @@ static lc_status graph_finish(lc_ctx* ctx, GraphScratch& gs, const std::function
     ctx->has_graph = true;
     ctx->drop_graph();
     ctx->pose_drop_graph();   // the pose solve moves the graph nodes
+    ctx->pose_graph_changed();
     return ctx->sync_desc();
 }
 

@@ -25,29 +25,37 @@ namespace lc {
 
 constexpr int kPixTile = 2048;   // z-buffer pixels cleared per block (256 threads x 8)
 
-// Frame reset of every capture: z-buffer cleared, visibility counters and
-// the per-step history zeroed (tile 0 of each capture).
+// Frame reset of every capture: the per-step history zeroed (tile 0 of each
+// capture); the z-buffer cleared and the visibility counters zeroed unless
+// the capture's frame decisions are frozen (a warm start kept those of its
+// start: the visibility kernels then skip the capture).
 __global__ void __launch_bounds__(256) batch_reset_kernel(const CapDesc* __restrict__ caps,
                                                           const WorkItem* __restrict__ items) {
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
+    const bool frozen = C.sc->vis_frozen != 0;
     const size_t P = (size_t)C.W * C.H;
     const size_t p0 = (size_t)tile * kPixTile;
-    for (int j = threadIdx.x; j < kPixTile; j += blockDim.x) {
-        const size_t p = p0 + j;
-        if (p < P) C.zbuf[p] = ~0ULL;
-    }
+    if (!frozen)
+        for (int j = threadIdx.x; j < kPixTile; j += blockDim.x) {
+            const size_t p = p0 + j;
+            if (p < P) C.zbuf[p] = ~0ULL;
+        }
     if (tile == 0) {
         for (int j = threadIdx.x; j < 2 * (LC_MAX_GN + 1); j += blockDim.x) C.hist[j] = 0.0;
         for (int j = threadIdx.x; j < LC_MAX_GN + 2; j += blockDim.x) C.hist_iters[j] = 0;
-        if (threadIdx.x < 3) C.sc->counts[threadIdx.x] = 0;
+        if (!frozen && threadIdx.x < 3) C.sc->counts[threadIdx.x] = 0;
         if (threadIdx.x == 0) {
             C.sc->gn_stop = 0;
             C.sc->gn_done = 0;
-            C.sc->vis_frozen = 0;
         }
     }
+}
+
+// End of a batched solve: the next visibility pass of every capture runs again.
+__global__ void __launch_bounds__(256) batch_unfreeze_kernel(const CapDesc* __restrict__ caps, int count) {
+    for (int c = threadIdx.x; c < count; c += blockDim.x) caps[c].sc->vis_frozen = 0;
 }
 
 // Node parameters of every capture back to the identity.
@@ -90,6 +98,11 @@ struct lc_batch {
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
     bool gexec_identity = false;
+    // the frame-step graph (lc_batch_step) and the network it was captured for
+    cudaGraphExec_t step_gexec = nullptr;
+    unsigned long long step_uid = 0, step_gen = 0;
+    unsigned step_flags = 0;
+    int step_kernels = 0;
     bool solved = false;              // a solve has run: linearisations and directions exist
     std::vector<cudaEvent_t> ev;      // per member: its stream's work before the solve
     cudaEvent_t done = nullptr;       // the batch solve, awaited by every member's stream
@@ -103,6 +116,8 @@ struct lc_batch {
     void free_plan() {
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
+        if (step_gexec) cudaGraphExecDestroy(step_gexec);
+        step_gexec = nullptr;
         if (items) cudaFree(items);
         items = nullptr;
         if (dC) cudaFree(dC);
@@ -233,6 +248,10 @@ lc_status lc_batch::build() {
 
 void lc_batch::enqueue(bool from_identity) {
     cudaStream_t st = stream;
+    // body-part masks of the members that have one, from their rest geometry
+    // (each rasterises into its own z-buffer, which the reset clears again)
+    for (size_t j = 0; j < snap.size(); ++j)
+        if (snap[j].part_on) launch_part_mask(dC + j, snap[j], st);
     if (from_identity && all.vec) batch_identity_kernel<<<all.vec, kVecThreads, 0, st>>>(dC, all.vec_items);
     if (pix_blocks) batch_reset_kernel<<<pix_blocks, 256, 0, st>>>(dC, pix_items);
     launch_warp(dC, all, st);
@@ -256,6 +275,7 @@ void lc_batch::enqueue(bool from_identity) {
     launch_warp(dC, all, st);
     launch_linearize(dC, all, false, LC_MAX_GN, st);
     launch_rhs(dC, all, n_gn, true, st);
+    batch_unfreeze_kernel<<<1, 256, 0, st>>>(dC, (int)snap.size());
 }
 
 static lc_status batch_check(lc_batch* b) {
@@ -265,8 +285,6 @@ static lc_status batch_check(lc_batch* b) {
         if (c->device != b->device) return b->fail(LC_ERR_ARG, "lc_batch: contexts on different devices");
         if (c->params.n_gn != b->n_gn || c->params.n_pcg != b->n_pcg)
             return b->fail(LC_ERR_ARG, "lc_batch: contexts differ in n_gn / n_pcg");
-        if (c->hC.part_on)
-            return b->fail(LC_ERR_STATE, "lc_batch: body-part masks are built by per-context solves only");
     }
     return LC_OK;
 }
@@ -406,6 +424,116 @@ extern "C" lc_status lc_batch_solve(lc_batch* b, int from_identity, lc_solve_sta
         for (const BatchGroup& g : b->groups)
             if (slot >= g.first && slot < g.first + g.count) cl = g.plan.cl;
         stats[i].pcg_cluster_size = cl;
+    }
+    return LC_OK;
+}
+
+// One frame step of every member as one CUDA graph: per member the pose
+// stage (from its Euler start or its last solved pose), the identity start of
+// the non-rigid stage unless the graph parameters are carried, the warm
+// start (with a network), then the batched non-rigid stage of all members,
+// then per member the motion record and the end of the pose frame.  Captured
+// on the first call (and again when the plan or the network changes) by
+// routing every member's enqueue sequence into the batch's stream.
+extern "C" lc_status lc_batch_step(lc_batch* b, lc_mlp* net, unsigned flags, lc_solve_stats* stats) {
+    if (!b) return LC_ERR_ARG;
+    if (flags & ~(LC_STEP_EULER_START | LC_STEP_CARRY_GRAPH)) return b->fail(LC_ERR_ARG, "lc_batch_step: unknown flags");
+    cudaSetDevice(b->device);
+    lc_status s;
+    if ((s = batch_check(b))) return s;
+    bool changed = false;
+    for (size_t j = 0; j < b->snap.size(); ++j)
+        if (memcmp(&b->snap[j], &b->ctxs[b->ctx_of[j]]->hC, sizeof(CapDesc)) != 0) changed = true;
+    if (changed && (s = b->build())) return s;
+    for (lc_ctx* c : b->ctxs) {
+        if (c->profiling) return b->fail(LC_ERR_STATE, "lc_batch_step: profiling is on for a member");
+        if ((s = pose_step_prepare(c))) return b->fail(s, c->err.c_str());
+        if ((s = warm_step_prepare(c, net))) return b->fail(s, c->err.c_str());
+    }
+    unsigned long long uid = 0, gen = 0;
+    mlp_identity(net, &uid, &gen);
+    if (b->step_gexec && (b->step_uid != uid || b->step_gen != gen || b->step_flags != flags)) {
+        cudaGraphExecDestroy(b->step_gexec);
+        b->step_gexec = nullptr;
+    }
+    if (!b->step_gexec) {
+        // every member's stream is the batch's while its sequences are captured
+        std::vector<cudaStream_t> saved(b->ctxs.size());
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return b->fail(LC_ERR_CUDA, "lc_batch_step: begin capture");
+        for (size_t i = 0; i < b->ctxs.size(); ++i) {
+            lc_ctx* c = b->ctxs[i];
+            saved[i] = c->stream;
+            c->stream = b->stream;
+            pose_step_begin(c, (flags & LC_STEP_EULER_START) != 0);
+            if (!(flags & LC_STEP_CARRY_GRAPH)) {
+                // the non-rigid stage starts from the identity over the new skinned
+                // surface; the motion record then measures the frame's update from it
+                launch_identity_params(c->hC.node_R, c->hC.node_t, c->hC.n, c->stream);
+                motion_step_enqueue(c);
+            }
+            if (net) warm_step_enqueue(c, net);
+        }
+        b->enqueue(false);
+        for (lc_ctx* c : b->ctxs) {
+            motion_step_enqueue(c);
+            pose_step_end(c);
+        }
+        for (size_t i = 0; i < b->ctxs.size(); ++i) b->ctxs[i]->stream = saved[i];
+        if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess || !g) {
+            cudaGetLastError();
+            return b->fail(LC_ERR_CUDA, "lc_batch_step: capture failed");
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int k = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nd, &ty);
+            if (ty == cudaGraphNodeTypeKernel) ++k;
+        }
+        const cudaError_t e = cudaGraphInstantiate(&b->step_gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->step_gexec = nullptr;
+            return b->fail(LC_ERR_CUDA, "lc_batch_step: graph instantiation");
+        }
+        b->step_kernels = k;
+        b->step_uid = uid;
+        b->step_gen = gen;
+        b->step_flags = flags;
+    }
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        cudaEventRecord(b->ev[i], b->ctxs[i]->stream);
+        cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+    }
+    if (net) mlp_before(net, b->stream);
+    if (cudaGraphLaunch(b->step_gexec, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return b->fail(LC_ERR_CUDA, "lc_batch_step: graph launch");
+    }
+    if (net) mlp_after(net, b->stream);
+    cudaEventRecord(b->done, b->stream);
+    for (lc_ctx* c : b->ctxs) {
+        cudaStreamWaitEvent(c->stream, b->done, 0);
+        c->has_vis = true;
+        c->has_lin = true;
+        c->surf_has_lin = false;
+        c->last_surface = false;
+    }
+    b->solved = true;
+    if (!stats) return LC_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return b->fail(LC_ERR_CUDA, "lc_batch_step: execution failed");
+    }
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if ((s = b->ctxs[i]->read_stats(&stats[i], b->n_gn))) return b->fail(s, "lc_batch_step: reading statistics");
+        stats[i].n_kernels = b->step_kernels;
     }
     return LC_OK;
 }

@@ -127,6 +127,20 @@ struct lc_ctx {
     void enqueue_pose();
     void pose_release();
     void pose_drop_graph();
+    void pose_graph_changed();   // a new graph: no recorded rest-pose node parameters
     lc_status pose_frame(const float* joints2d, const float* joints3d);
     lc_status pose_read(float* pose_out);
 };
+
+// Pieces of a frame step that lc_batch_step captures into one graph
+// (pose_api.cu, warmstart.cu): *_prepare run on the host before the capture
+// (descriptor uploads, allocations); the others enqueue on ctx->stream.
+lc_status pose_step_prepare(lc_ctx* ctx);
+void pose_step_begin(lc_ctx* ctx, bool euler_start);
+void pose_step_end(lc_ctx* ctx);
+lc_status warm_step_prepare(lc_ctx* ctx, lc_mlp* m);   // m may be null: motion bookkeeping only
+void warm_step_enqueue(lc_ctx* ctx, lc_mlp* m);
+void motion_step_enqueue(lc_ctx* ctx);
+void mlp_identity(const lc_mlp* m, unsigned long long* uid, unsigned long long* gen);
+void mlp_before(lc_mlp* m, cudaStream_t st);   // st waits for the network's earlier work
+void mlp_after(lc_mlp* m, cudaStream_t st);    // the network's later work waits for st

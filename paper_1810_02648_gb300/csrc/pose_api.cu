@@ -21,6 +21,12 @@ struct PoseState {
     PoseDesc last{};                // the descriptor as last copied to the device
     bool synced = false;
     int graph_disp = 0;             // use_disp when the graph was captured
+    // the graph stage's displacement warping: node parameters in the rest
+    // pose (4n float4) and whether they hold a record
+    float4* g_rest = nullptr;
+    int* g_valid = nullptr;
+    int g_rest_n = 0;
+    int graph_warp = 0;             // graph_warp when the pose graph was captured
 };
 
 static void rodrigues(const double* w, double* R) {
@@ -76,7 +82,7 @@ void lc_ctx::pose_release() {
                     pose->h.pose, pose->h.pose_start, pose->h.Rroot, pose->h.blist,
                     pose->h.bcount, pose->h.hist, pose->h.info, pose->h.expA, pose->h.status, pose->d,
                     pose->pose_set, (void*)pose->h.temporal_w, (void*)pose->h.th_lo, (void*)pose->h.th_hi,
-                    pose->h.prev_joints, pose->h.pose_hist, pose->h.disp};
+                    pose->h.prev_joints, pose->h.pose_hist, pose->h.disp, pose->g_rest, pose->g_valid};
     for (void* p : bufs) release(p);
     delete pose;
     pose = nullptr;
@@ -85,6 +91,33 @@ void lc_ctx::pose_release() {
         hC.part_on = 0;
         drop_graph();
     }
+}
+
+// buffers of the graph stage's displacement warping for the current graph
+// (a new graph size reallocates them and drops the captured pose graph,
+// which holds their addresses); no record is valid after a reallocation
+static lc_status graph_warp_ensure(lc_ctx* ctx) {
+    PoseState& S = *ctx->pose;
+    if (!ctx->params.graph_warp || !ctx->has_graph || S.g_rest_n == ctx->hC.n) return LC_OK;
+    ctx->release(S.g_rest);
+    ctx->release(S.g_valid);
+    S.g_rest = (float4*)ctx->alloc(sizeof(float4) * 4 * (size_t)ctx->hC.n);
+    S.g_valid = (int*)ctx->alloc(sizeof(int));
+    S.g_rest_n = 0;
+    if (!S.g_rest || !S.g_valid) return LC_ERR_OOM;
+    S.g_rest_n = ctx->hC.n;
+    ctx->pose_drop_graph();
+    return ctx->cuda(cudaMemsetAsync(S.g_valid, 0, sizeof(int), ctx->stream), "graph warp");
+}
+
+static bool graph_warp_active(const lc_ctx* ctx) {
+    return ctx->pose && ctx->params.graph_warp && ctx->has_graph && ctx->pose->g_rest &&
+           ctx->pose->g_rest_n == ctx->hC.n;
+}
+
+// a new graph: the recorded rest-pose node parameters no longer apply
+void lc_ctx::pose_graph_changed() {
+    if (pose && pose->g_valid) cudaMemsetAsync(pose->g_valid, 0, sizeof(int), stream);
 }
 
 static lc_status pose_sync(lc_ctx* ctx) {
@@ -349,8 +382,11 @@ extern "C" lc_status lc_pose_advance(lc_ctx* ctx) {
     if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_pose_advance: no skeleton");
     cudaSetDevice(ctx->device);
     PoseState& S = *ctx->pose;
+    lc_status s;
+    if ((s = graph_warp_ensure(ctx))) return s;
     launch_pose_advance(S.d, ctx->stream);
-    lc_status s = ctx->cuda(cudaGetLastError(), "lc_pose_advance");
+    if (graph_warp_active(ctx)) launch_graph_warp(ctx->dC, ctx->hC, S.d, S.g_rest, S.g_valid, 0, ctx->stream);
+    s = ctx->cuda(cudaGetLastError(), "lc_pose_advance");
     if (s) return s;
     if (S.h.has_prev && S.h.n_hist >= 2) return LC_OK;   // the descriptor is unchanged
     S.h.has_prev = 1;
@@ -373,6 +409,7 @@ extern "C" lc_status lc_pose_clear_history(lc_ctx* ctx) {
     cudaSetDevice(ctx->device);
     ctx->pose->h.has_prev = 0;
     ctx->pose->h.n_hist = 0;
+    if (ctx->pose->g_valid) cudaMemsetAsync(ctx->pose->g_valid, 0, sizeof(int), ctx->stream);
     return pose_sync(ctx);
 }
 
@@ -390,6 +427,36 @@ extern "C" lc_status lc_reset_pose(lc_ctx* ctx) {
                        "pose reset")))
         return s;
     return LC_OK;
+}
+
+// A frame step captured once and replayed (lc_batch_step): the host state
+// that lc_solve_pose and lc_pose_advance keep must not change between
+// replays, so the pose history must be full (two recorded frames) and the
+// descriptor is brought to the device here, before the capture.
+lc_status pose_step_prepare(lc_ctx* ctx) {
+    if (!ctx->pose) return ctx->fail(LC_ERR_STATE, "lc_batch_step: a member has no skeleton");
+    PoseState& S = *ctx->pose;
+    if (!S.h.has_prev || S.h.n_hist < 2)
+        return ctx->fail(LC_ERR_STATE, "lc_batch_step: a member has fewer than two recorded frames (lc_pose_advance)");
+    if (!ctx->has_camera || !ctx->has_frame) return ctx->fail(LC_ERR_STATE, "lc_batch_step: camera and frame required");
+    apply_pose_params(ctx);
+    lc_status s;
+    if ((s = graph_warp_ensure(ctx))) return s;
+    if (!S.synced || memcmp(&S.h, &S.last, sizeof(PoseDesc)) != 0) return pose_sync(ctx);
+    return LC_OK;
+}
+
+// the frame's start and pose stage, then (after the non-rigid stage) its end,
+// enqueued on ctx->stream
+void pose_step_begin(lc_ctx* ctx, bool euler_start) {
+    if (euler_start) launch_pose_extrapolate(ctx->pose->d, ctx->stream);
+    ctx->enqueue_pose();
+}
+
+void pose_step_end(lc_ctx* ctx) {
+    PoseState& S = *ctx->pose;
+    launch_pose_advance(S.d, ctx->stream);
+    if (graph_warp_active(ctx)) launch_graph_warp(ctx->dC, ctx->hC, S.d, S.g_rest, S.g_valid, 0, ctx->stream);
 }
 
 void lc_ctx::enqueue_pose() {
@@ -426,6 +493,9 @@ void lc_ctx::enqueue_pose() {
     mark(LC_PH_POSE);
     launch_pose_skin(dC, hC, S.d, base_buf, 1, st);
     if (has_graph) launch_gather_nodes(base_buf, hC.node_vid, hC.n, (float4*)hC.node_g, st);
+    // the node parameters recorded in the rest pose at the end of the last
+    // frame, carried into the solved pose
+    if (graph_warp_active(this)) launch_graph_warp(dC, hC, S.d, S.g_rest, S.g_valid, 1, st);
     mark_end();
     prof_pose.end = prof_used;
 }
@@ -443,11 +513,15 @@ extern "C" lc_status lc_solve_pose(lc_ctx* ctx, lc_solve_stats* stats) {
     if (!S.synced || memcmp(&S.h, &S.last, sizeof(PoseDesc)) != 0) {
         if ((s = pose_sync(ctx))) return s;
     }
-    if (S.gexec && (S.graph_n_gn != ctx->params.n_gn_pose || S.graph_disp != S.h.use_disp)) ctx->pose_drop_graph();
+    if ((s = graph_warp_ensure(ctx))) return s;
+    const int warp_on = graph_warp_active(ctx) ? 1 : 0;
+    if (S.gexec && (S.graph_n_gn != ctx->params.n_gn_pose || S.graph_disp != S.h.use_disp || S.graph_warp != warp_on))
+        ctx->pose_drop_graph();
     if (!S.gexec) {
         if ((s = ctx->capture(&S.gexec, &S.graph_kernels, &lc_ctx::enqueue_pose))) return s;
         S.graph_n_gn = ctx->params.n_gn_pose;
         S.graph_disp = S.h.use_disp;   // the displacement kernel is in the graph or not
+        S.graph_warp = warp_on;        // and the graph warping kernel
     }
     if ((s = ctx->cuda(cudaGraphLaunch(S.gexec, ctx->stream), "graph launch"))) return s;
     if ((s = ctx->accumulate_profile(ctx->prof_pose))) return s;

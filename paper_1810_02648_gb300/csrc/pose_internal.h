@@ -68,6 +68,10 @@ void launch_pose_dirs(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, 
 void launch_pose_advance(const PoseDesc* dP, cudaStream_t st);
 // the pose <- the explicit Euler step from the pose history (n_hist >= 1)
 void launch_pose_extrapolate(const PoseDesc* dP, cudaStream_t st);
+// the graph stage's displacement warping: mode 0 records the node parameters in the rest pose,
+// mode 1 poses a valid record with the current pose (rest: 4n float4)
+void launch_graph_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* rest, int* valid, int mode,
+                       cudaStream_t st);
 // displacement warping of the surface stage (dP null: no skeleton, Q_i = I);
 // mode 0 records sD from sV, mode 1 sets sV from sD, mode 2 writes Q_i sD_i
 // into the pose stage's dP->disp

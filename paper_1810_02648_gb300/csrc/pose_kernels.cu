@@ -832,6 +832,31 @@ __device__ __forceinline__ float4 quat_of(const float* G) {
     return q;
 }
 
+// the blend rotation of vertex i from the bones' quaternions qb (row-major;
+// the identity where the weighted sum vanishes)
+__device__ __forceinline__ void blend_rotation(const PoseDesc& P, const float4* qb, int i, float* R) {
+    const int4 bi = P.skin_idx[i];
+    const float4 bw = P.skin_w[i];
+    const int bones[4] = {bi.x, bi.y, bi.z, bi.w};
+    const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
+    const float4 q0 = qb[bones[0]];
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 q = qb[bones[k]];
+        const float w = (q.x * q0.x + q.y * q0.y + q.z * q0.z + q.w * q0.w) < 0.f ? -ws[k] : ws[k];
+        s.x += w * q.x; s.y += w * q.y; s.z += w * q.z; s.w += w * q.w;
+    }
+    const float n2 = s.x * s.x + s.y * s.y + s.z * s.z + s.w * s.w;
+    if (n2 > 0.f) {
+        const float inv = rsqrtf(n2);
+        const float x = s.x * inv, y = s.y * inv, z = s.z * inv, w = s.w * inv;
+        R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
+        R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
+        R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
+    }
+}
+
 __global__ void __launch_bounds__(256) surface_warp_kernel(const CapDesc* __restrict__ caps,
                                                            const PoseDesc* __restrict__ pd, int mode) {
     __shared__ float4 qb[kMaxJoints];
@@ -842,28 +867,7 @@ __global__ void __launch_bounds__(256) surface_warp_kernel(const CapDesc* __rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.N) return;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-    if (pd) {
-        const int4 bi = pd->skin_idx[i];
-        const float4 bw = pd->skin_w[i];
-        const int bones[4] = {bi.x, bi.y, bi.z, bi.w};
-        const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
-        const float4 q0 = qb[bones[0]];
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4 q = qb[bones[k]];
-            const float w = (q.x * q0.x + q.y * q0.y + q.z * q0.z + q.w * q0.w) < 0.f ? -ws[k] : ws[k];
-            s.x += w * q.x; s.y += w * q.y; s.z += w * q.z; s.w += w * q.w;
-        }
-        const float n2 = s.x * s.x + s.y * s.y + s.z * s.z + s.w * s.w;
-        if (n2 > 0.f) {
-            const float inv = rsqrtf(n2);
-            const float x = s.x * inv, y = s.y * inv, z = s.z * inv, w = s.w * inv;
-            R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
-            R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
-            R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
-        }
-    }
+    if (pd) blend_rotation(*pd, qb, i, R);
     if (mode == 2) {
         const float4 d = C.sD[i];
         pd->disp[i] = make_float4(R[0] * d.x + R[1] * d.y + R[2] * d.z, R[3] * d.x + R[4] * d.y + R[5] * d.z,
@@ -881,6 +885,61 @@ __global__ void __launch_bounds__(256) surface_warp_kernel(const CapDesc* __rest
         C.sV[i] = make_float4(S.x + (R[0] * d.x + R[1] * d.y + R[2] * d.z), S.y + (R[3] * d.x + R[4] * d.y + R[5] * d.z),
                               S.z + (R[6] * d.x + R[7] * d.y + R[8] * d.z), 0.f);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Displacement warping of the graph stage (the graph counterpart of Sec. 3.4's
+// warping): node k's parameters are carried in the rest pose through the
+// blend rotation Q_k of its node vertex.  mode 0 (end of a frame, final pose)
+// records R^rest = Q^T R Q, t^rest = Q^T t and marks them valid; mode 1
+// (start of a frame, after the pose solve) sets R = Q R^rest Q^T,
+// t = Q t^rest when a record is valid.  Under a common rigid motion of a
+// node's bones this moves the deformed surface rigidly with them.
+// rest: 4n float4 (rows of R^rest, then t^rest).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) graph_warp_kernel(const CapDesc* __restrict__ caps,
+                                                         const PoseDesc* __restrict__ pd, float4* __restrict__ rest,
+                                                         int* __restrict__ valid, int mode) {
+    __shared__ float4 qb[kMaxJoints];
+    const CapDesc& C = caps[0];
+    if (mode == 1 && *valid == 0) return;
+    for (int b = threadIdx.x; b < pd->J; b += blockDim.x) qb[b] = quat_of(&pd->fk->G[b][0]);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= C.n) return;
+    float Q[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    blend_rotation(*pd, qb, C.node_vid[k], Q);
+    // A = Q^T, B = Q (mode 0) or A = Q, B = Q^T (mode 1): out = A M B, t' = A t
+    float A[9], B[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            A[3 * r + c] = mode == 0 ? Q[3 * c + r] : Q[3 * r + c];
+            B[3 * r + c] = mode == 0 ? Q[3 * r + c] : Q[3 * c + r];
+        }
+    const float4* src_R = mode == 0 ? C.node_R : rest;
+    const float4 s0 = src_R[3 * k], s1 = src_R[3 * k + 1], s2 = src_R[3 * k + 2];
+    const float4 st = mode == 0 ? C.node_t[k] : rest[3 * C.n + k];
+    const float M[9] = {s0.x, s0.y, s0.z, s1.x, s1.y, s1.z, s2.x, s2.y, s2.z};
+    float AM[9], O[9];
+    mat3mul(A, M, AM);
+    mat3mul(AM, B, O);
+    const float4 r0 = make_float4(O[0], O[1], O[2], 0.f), r1 = make_float4(O[3], O[4], O[5], 0.f),
+                 r2 = make_float4(O[6], O[7], O[8], 0.f);
+    const float4 t = make_float4(A[0] * st.x + A[1] * st.y + A[2] * st.z, A[3] * st.x + A[4] * st.y + A[5] * st.z,
+                                 A[6] * st.x + A[7] * st.y + A[8] * st.z, 0.f);
+    if (mode == 0) {
+        rest[3 * k] = r0; rest[3 * k + 1] = r1; rest[3 * k + 2] = r2;
+        rest[3 * C.n + k] = t;
+        if (k == 0) *valid = 1;
+    } else {
+        C.node_R[3 * k] = r0; C.node_R[3 * k + 1] = r1; C.node_R[3 * k + 2] = r2;
+        C.node_t[k] = t;
+    }
+}
+
+void launch_graph_warp(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* rest, int* valid, int mode,
+                       cudaStream_t st) {
+    graph_warp_kernel<<<(hC.n + 255) / 256, 256, 0, st>>>(dC, dP, rest, valid, mode);
 }
 
 void launch_pose_skin(const CapDesc* dC, const CapDesc& hC, const PoseDesc* dP, float4* out_base, int mode,

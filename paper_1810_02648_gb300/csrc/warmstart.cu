@@ -917,6 +917,47 @@ static void enqueue_warm(lc_ctx* ctx, lc_mlp* m) {
     accept_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctx->dC, w.e, w.R0, w.t0, w.accepted);
 }
 
+// Parts of a frame step captured once and replayed (lc_batch_step): the
+// allocations first, then the enqueued sequences on ctx->stream.
+lc_status warm_step_prepare(lc_ctx* ctx, lc_mlp* m) {
+    lc_status s;
+    if ((s = warm_ensure(ctx))) return s;
+    if (!m) return LC_OK;
+    if (m->device != ctx->device) return ctx->fail(LC_ERR_ARG, "lc_batch_step: network on another device");
+    if ((s = m->ensure(ctx->hC.n))) return ctx->fail(s, "lc_batch_step: network scratch");
+    return LC_OK;
+}
+
+void warm_step_enqueue(lc_ctx* ctx, lc_mlp* m) { enqueue_warm(ctx, m); }
+
+void motion_step_enqueue(lc_ctx* ctx) {
+    WarmState& w = *ctx->warm;
+    record_motion_kernel<<<(w.n + 127) / 128, 128, 0, ctx->stream>>>(ctx->dC, w.Rprev, w.tprev, w.motion);
+}
+
+// order a use of the network's buffers on stream st after its earlier work
+// (training, other warm starts), and its later work after this use
+void mlp_before(lc_mlp* m, cudaStream_t st) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, m->stream);
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+}
+
+void mlp_after(lc_mlp* m, cudaStream_t st) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(m->stream, ev, 0);
+    cudaEventDestroy(ev);
+}
+
+void mlp_identity(const lc_mlp* m, unsigned long long* uid, unsigned long long* gen) {
+    *uid = m ? m->uid : 0;
+    *gen = m ? m->gen : 0;
+}
+
 extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double* energies) {
     if (!ctx || !m) return LC_ERR_ARG;
     lc_status s;
@@ -947,21 +988,13 @@ extern "C" lc_status lc_warm_start(lc_ctx* ctx, lc_mlp* m, int* accepted, double
         w.g_uid = m->uid;
         w.g_gen = m->gen;
     }
-    // the network's previous work (training) before its buffers are reused here
-    cudaEvent_t ev;
-    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    cudaEventRecord(ev, m->stream);
-    cudaStreamWaitEvent(st, ev, 0);
-    cudaEventDestroy(ev);
+    // the network's previous work (training, other contexts' warm starts)
+    // before its buffers are reused here, its later work after
+    mlp_before(m, st);
     if ((s = ctx->cuda(cudaGraphLaunch(w.gexec, st), "warm-start graph launch"))) return s;
     ctx->has_vis = true;
     ctx->has_lin = false;
-    // the network's later work waits for this use of its buffers
-    cudaEvent_t ev2;
-    cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming);
-    cudaEventRecord(ev2, st);
-    cudaStreamWaitEvent(m->stream, ev2, 0);
-    cudaEventDestroy(ev2);
+    mlp_after(m, st);
     if (!accepted && !energies) return LC_OK;
     if (accepted && (s = ctx->copy_to_host(accepted, w.accepted, sizeof(int)))) return s;
     if (energies && (s = ctx->copy_to_host(energies, w.e, 2 * sizeof(double)))) return s;

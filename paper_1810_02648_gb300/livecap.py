@@ -30,7 +30,8 @@ class lc_params(ctypes.Structure):
                 ("n_gn_surface", ctypes.c_int), ("n_pcg_surface", ctypes.c_int), ("pose_solver", ctypes.c_int),
                 ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float),
                 ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3), ("pose_displacement", ctypes.c_int),
-                ("gn_block", ctypes.c_int)]
+                ("gn_block", ctypes.c_int),
+                ("graph_warp", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):
@@ -89,6 +90,7 @@ _SIGS = {
     "lc_batch_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P],
     "lc_batch_stream": [_P],
     "lc_batch_apply_jtj": [_P, ctypes.c_int],
+    "lc_batch_step": [_P, _P, ctypes.c_uint, _P],
     "lc_mlp_create": [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P],
     "lc_mlp_destroy": [_P],
     "lc_mlp_last_error": [_P],
@@ -613,6 +615,7 @@ class MLP:
         return loss.value if want_loss else None
 
 
+STEP_EULER_START, STEP_CARRY_GRAPH = 1, 2
 BATCH_PCG_AUTO, BATCH_PCG_CLUSTER8, BATCH_PCG_CLUSTER16, BATCH_PCG_PER_ITERATION = 0, 1, 2, 3
 
 
@@ -660,6 +663,20 @@ class Batch:
     def stream_handle(self) -> int:
         """The batch's cudaStream_t as an integer."""
         return self._lib.lc_batch_stream(self.h) or 0
+
+    def step(self, mlp=None, euler_start: bool = True, carry_graph: bool = True, stats: bool = True):
+        """One frame step of every member as one CUDA graph (lc_batch_step):
+        pose stage, identity start of the non-rigid stage unless
+        ``carry_graph``, warm start (with ``mlp``), batched non-rigid stage,
+        motion and pose bookkeeping.  Returns per-member non-rigid statistics."""
+        flags = (STEP_EULER_START if euler_start else 0) | (STEP_CARRY_GRAPH if carry_graph else 0)
+        h = mlp.h if mlp is not None else None
+        if not stats:
+            self._check(self._lib.lc_batch_step(self.h, h, flags, None))
+            return None
+        arr = (lc_solve_stats * len(self.contexts))()
+        self._check(self._lib.lc_batch_step(self.h, h, flags, arr))
+        return [a.to_dict() for a in arr]
 
     def apply_jtj(self, stage: bool = False):
         """Enqueue one J^T J p of every member (measurement entry); stage

@@ -24,20 +24,47 @@ from .livecap import MLP, MLP_PARAMS
 
 
 def _upload(ctx, frame):
-    rgb, dt, mask = frame
-    ctx.upload_frame(rgb, dt, np.asarray(mask, dtype=np.uint8), None, None)
+    """frame: (rgb, dt, mask) or (rgb, dt, mask, joints2d, joints3d)."""
+    rgb, dt, mask = frame[:3]
+    j2, j3 = (frame[3], frame[4]) if len(frame) > 3 else (None, None)
+    ctx.upload_frame(rgb, dt, np.asarray(mask, dtype=np.uint8), j2, j3)
 
 
-def collect(ctx, frames, skip: int = 0):
-    """Plain tracking of ``frames`` (an iterable of (rgb, dt, mask)) from the
-    context's current node parameters.  Returns features (T, n, 64) and
-    targets (T, n, 6) as device tensors and the plain final energies (T) of
-    the frames after the first ``skip`` (those are tracked but not kept)."""
+def restart(ctx, pose: bool = False):
+    """Start a new sequence: identity node parameters and zero motion; with
+    ``pose``, the pose stage restarts from the pose last set and forgets its
+    recorded frames."""
+    ctx.set_node_params(None, None)
+    ctx.record_motion()
+    ctx.record_motion()
+    if pose:
+        ctx.reset_pose()
+        ctx.pose_clear_history()
+
+
+def collect(ctx, frames, skip: int = 0, pose: bool = False, euler: bool = True, from_identity: bool = False):
+    """Plain tracking of ``frames`` (an iterable of (rgb, dt, mask), with
+    joints when ``pose``) from the context's current state.  With ``pose``
+    every frame first runs the pose stage (from the explicit Euler start once
+    a frame is recorded, with ``euler``, else from the last solved pose) and
+    ends with lc_pose_advance.  With ``from_identity`` the non-rigid stage of
+    every frame starts from the identity (the motion is recorded there, so
+    the target is the update from that start).
+    Returns features (T, n, 64) and targets (T, n, 6) as device tensors and
+    the plain final energies (T) of the frames after the first ``skip``
+    (those are tracked but not kept)."""
     import torch
     dev = torch.device("cuda", ctx.device)
     F, Tg, E = [], [], []
     for i, fr in enumerate(frames):
         _upload(ctx, fr)
+        if pose:
+            if euler and i > 0:
+                ctx.pose_extrapolate()
+            ctx.solve_pose(stats=False)
+        if from_identity:
+            ctx.set_node_params(None, None)
+            ctx.record_motion()
         keep = i >= skip
         if keep:
             ctx.compute_visibility()
@@ -45,6 +72,8 @@ def collect(ctx, frames, skip: int = 0):
             ctx.node_features(out=f)
         st = ctx.solve_nonrigid()
         ctx.record_motion()
+        if pose:
+            ctx.pose_advance()
         if keep:
             u = torch.empty((ctx.n, 6), dtype=torch.float32, device=dev)
             ctx.read_motion(out=u)

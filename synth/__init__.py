@@ -24,6 +24,7 @@ from .scenes import (  # noqa: F401
     ar1_draws,
     ar1_sequence,
     ar1_frame,
+    stream_frame,
     render_frame,
     render,
     contour_distance_transform,

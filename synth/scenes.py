@@ -444,11 +444,15 @@ def ar1_draws(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma
     """Control points, RBF width and the per-frame control-point rotations
     and translations (aa, tt) of an AR(1) sequence: x_t = rho x_{t-1} +
     sqrt(1 - rho^2) sigma eps_t, started from the stationary distribution."""
+    ids, rho, draws = _ar1_state(V, n_frames, n_ctrl, sigma_rot, sigma_t, seed, rho_ar)
+    return np.asarray(V, dtype=np.float64)[ids], rho, draws
+
+
+def _ar1_state(V, n_frames, n_ctrl, sigma_rot, sigma_t, seed, rho_ar):
     rng = np.random.default_rng(seed + 3000)
     V = np.asarray(V, dtype=np.float64)
     ids = np.sort(rng.choice(len(V), size=n_ctrl, replace=False))
-    c = V[ids]
-    rho = _rbf_width(c)
+    rho = _rbf_width(V[ids])
     aa = rng.normal(0.0, sigma_rot, size=(n_ctrl, 3))
     tt = rng.normal(0.0, sigma_t, size=(n_ctrl, 3))
     k = math.sqrt(1.0 - rho_ar * rho_ar)
@@ -457,7 +461,7 @@ def ar1_draws(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma
         draws.append((aa, tt))
         aa = rho_ar * aa + k * rng.normal(0.0, sigma_rot, size=aa.shape)
         tt = rho_ar * tt + k * rng.normal(0.0, sigma_t, size=tt.shape)
-    return c, rho, draws
+    return ids, rho, draws
 
 
 def ar1_sequence(V: np.ndarray, n_frames: int, n_ctrl: int, sigma_rot: float, sigma_t: float,
@@ -476,6 +480,51 @@ def ar1_frame(V: np.ndarray, n_ctrl: int, sigma_rot: float, sigma_t: float, seed
     c, rho, draws = ar1_draws(V, i + 1, n_ctrl, sigma_rot, sigma_t, seed, rho_ar)
     aa, tt = draws[i]
     return rbf_field_linear(V, c, aa, tt, rho)
+
+
+def stream_frame(scene, seed: int, i: int, n_ctrl: int = 500, sigma_pose: float = 0.1, sigma_root: float = 0.05,
+                 sigma_root_t: float = 0.03, sigma_rot: float = 0.05, sigma_t: float = 0.01, rho_ar: float = 0.9,
+                 noise: float = 0.01, fps: float = 25.0):
+    """Frame i of a tracked stream of a body capture ``scene`` (a Scene with
+    a skeleton).  Articulated motion is smooth, as a performer's: every
+    joint angle and the root's rotation and translation move from the
+    capture's ground-truth pose along a sinusoid, a (sin(w t + phi) -
+    sin(phi)), with amplitude a ~ N(0, sigma_pose) rad per angle
+    (sigma_root rad, sigma_root_t m at the root), frequency w / 2 pi
+    uniform in [0.3, 1] Hz at ``fps`` frames per second and a uniform phase,
+    so that frame 0 has the capture's own pose (from which its pose_init
+    starts).  The posed surface is deformed by the AR(1) control-point field
+    of ``ar1_draws`` (n_ctrl control points, sigma_rot rad / sigma_t m,
+    rho_ar), and the frame is rendered with N(0, noise) colour noise.
+    Returns (rgb, dt, mask, joints2d, joints3d) with 2 px / 1 cm detection
+    noise."""
+    sk, meta = scene.skeleton, scene.meta
+    tpl = dict(V=np.asarray(scene.V, dtype=np.float64), joints_rest=np.asarray(sk["joints_rest"], dtype=np.float64),
+               parents=sk["parents"], skin_idx=sk["skin_idx"], skin_w=sk["skin_w"])
+    dof_joints = [j for j in range(1, 23) if j not in set(SKELETON_SITES.tolist())]
+    rng = np.random.default_rng(seed + 7000)
+    n_ang = 3 * len(dof_joints)
+    amp = np.concatenate([rng.normal(0.0, sigma_pose, size=n_ang), rng.normal(0.0, sigma_root, size=3),
+                          rng.normal(0.0, sigma_root_t, size=3)])
+    w = 2.0 * math.pi * rng.uniform(0.3, 1.0, size=amp.size) / fps
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=amp.size)
+    dev = amp * (np.sin(w * i + phi) - np.sin(phi))
+    angles = np.zeros((23, 3))
+    angles[dof_joints] = np.asarray(meta["pose_gt"][6:], dtype=np.float64).reshape(-1, 3) + dev[:n_ang].reshape(-1, 3)
+    root_aa = np.asarray(meta["root_aa"], dtype=np.float64) + dev[n_ang:n_ang + 3]
+    root_t = np.asarray(meta["root_t"], dtype=np.float64) + dev[n_ang + 3:]
+    Vp, joints = pose_body(tpl, _rodrigues(root_aa)[0], root_t, _euler_xyz(angles))
+    ids, rho, draws = _ar1_state(scene.V, i + 1, n_ctrl, sigma_rot, sigma_t, seed, rho_ar)
+    aa, tt = draws[i]
+    V = rbf_field_linear(Vp, Vp[ids], aa, tt, rho)
+    frng = np.random.default_rng([seed, i, 11])
+    rgb, dt, mask = _finish_frame(V, scene.F, scene.albedo, scene.cam, frng, noise)
+    cam = scene.cam
+    j3 = joints + frng.normal(0.0, 0.01, size=joints.shape)
+    u = cam.f * joints[:, 0] / joints[:, 2] + cam.cx
+    v = cam.f * joints[:, 1] / joints[:, 2] + cam.cy
+    j2 = np.stack([u, v], 1) + frng.normal(0.0, 2.0, size=(len(joints), 2))
+    return rgb, dt, mask, j2.astype(np.float32), j3.astype(np.float32)
 
 
 def render_frame(V_target: np.ndarray, F: np.ndarray, albedo: np.ndarray, cam: Camera, seed: int,
@@ -670,7 +719,8 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
                2D joints with 2 px noise, 3D joints with 1 cm noise,
                10 GN x 40 PCG after a 5-step pose fit.
     ``stress`` body of ~100k vertices, 4,000 nodes, K=8, 2048^2, f=2400.
-    Keyword overrides: rings, segments, n_nodes, K, side, n_gn, n_pcg.
+    Keyword overrides: rings, segments, n_nodes, K, side, n_gn, n_pcg; frame=False
+    (body and stress) skips the target frame (rgb, dt and mask are None).
     """
     if name == "tiny":
         seed = 0 if seed is None else seed
@@ -716,8 +766,15 @@ def make_scene(name: str, seed: Optional[int] = None, **over) -> Scene:
         local = _euler_xyz(angles)
         Vp, joints_gt = pose_body(dict(tpl, V=V32.astype(np.float64)),
                                   _rodrigues(root_aa)[0], root_t, local)
-        gt = smooth_deformation(Vp, n_nodes, over.get("sigma_nonrigid", 0.1), 0.01, seed)
-        rgb, dt, mask = _finish_frame(gt["V"], F, albedo, cam, rng)
+        if over.get("frame", True):
+            gt = smooth_deformation(Vp, n_nodes, over.get("sigma_nonrigid", 0.1), 0.01, seed)
+            rgb, dt, mask = _finish_frame(gt["V"], F, albedo, cam, rng)
+        else:
+            # no target frame (streams render their own): the generator's
+            # draws stay those of the full scene
+            gt = dict(V=Vp)
+            rgb = dt = mask = None
+            rng.normal(0.0, 0.01, size=(side, side, 3))
         j3 = joints_gt + rng.normal(0.0, 0.01, size=joints_gt.shape)
         u = cam.f * joints_gt[:, 0] / joints_gt[:, 2] + cam.cx
         v = cam.f * joints_gt[:, 1] / joints_gt[:, 2] + cam.cy

@@ -133,3 +133,35 @@ def test_batch_autotune_and_errors(scenes):
     bare.close()
     for c in ctxs:
         c.close()
+
+
+def test_batch_members_with_body_part_masks():
+    """Members with a body-part mask (body captures with a skeleton) beside
+    one without: each batched result equals its own single solve, and the
+    masked members' silhouette rows were masked."""
+    from paper_1810_02648_gb300 import Batch, Context
+    from synth import setup_scene
+    scs = [synth.make_scene("body", seed=s, rings=8, segments=14, side=256, n_nodes=80) for s in (3, 4)]
+    scs.append(synth.make_scene("tiny"))
+    ctxs = []
+    for k, sc in enumerate(scs):
+        c = Context(0)
+        setup_scene(c, sc)
+        c.set_params(n_gn=N_GN, n_pcg=N_PCG)
+        if sc.skeleton is not None:
+            c.solve_pose(stats=False)
+            c.set_body_parts(sc.skeleton["bone_part"], sc.skeleton["torso_part"], 10)
+        ctxs.append(c)
+    ref = _single(ctxs)
+    b = Batch(ctxs)
+    stats = b.solve(from_identity=True)
+    for i, c in enumerate(ctxs):
+        out = c.read_back()
+        st_ref, out_ref = ref[i]
+        assert _same(out, out_ref), f"capture {i}"
+        assert stats[i]["e_total"] == st_ref["e_total"] and stats[i]["e_gn"] == st_ref["e_gn"]
+    masked = [int(((ref[i][1]["flags"] & 32) != 0).sum()) for i in range(2)]
+    report("batch_body_parts", masked=masked, e=[s["e_total"] for s in stats])
+    b.close()
+    for c in ctxs:
+        c.close()
