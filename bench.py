@@ -986,10 +986,12 @@ def run_batch(a):
         setup_scene(c, sc)
         ctxs.append(c)
     batch = Batch(ctxs)
+    tune = None
     if a.pcg_mode < 0:
-        mode, mode_ms = batch.autotune(reps=2)
+        tune = batch.autotune_shapes(reps=2, use_cache=False)
+        mode = tune["shape"]["pcg_mode"]
     else:
-        mode, mode_ms = a.pcg_mode, []
+        mode = a.pcg_mode
         batch.set_pcg_mode(mode)
     ext = torch.cuda.ExternalStream(batch.stream_handle, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -1040,7 +1042,8 @@ def run_batch(a):
                                f"{scenes[0].n_gn} GN x {scenes[0].n_pcg} PCG, one launch per phase",
                    "captures": count, "vertices_total": int(verts),
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)",
-                   "pcg_mode": int(mode), "autotune_ms": [float(x) for x in mode_ms]},
+                   "pcg_mode": int(mode), "shape": batch.shape(), "size_class": batch.size_class(),
+                   "autotune": tune},
         "clocks": clk.summary(),
         "gpu_launches": int(stats[0]["n_kernels"]) * a.steps,
         "roofline": {"kernel": "jtj_vertex_kernel + jtj_node_kernel over all captures (one J^T J p each)",

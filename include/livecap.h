@@ -465,6 +465,47 @@ lc_status lc_batch_solve(lc_batch *batch, int from_identity, lc_solve_stats *sta
  * *mode_out; ms_out (nullable, 4 entries indexed by LC_BATCH_PCG_*) receives
  * the mean milliseconds per solve of each.  Synchronises. */
 lc_status lc_batch_autotune(lc_batch *batch, int reps, int *mode_out, float *ms_out);
+
+/* Launch shape of a batch: the PCG strategy (LC_BATCH_PCG_*) and, for the
+ * captures that run the per-iteration J^T J p (not on a cluster), its
+ * vertex-phase block (vert_block: 128, 256 or 512 vertices), its node-phase
+ * block (node_warps: 8 or 16 nodes, one warp each) and the node phase's
+ * entry rounds in flight per lane (node_unroll: 2, 4 or 8).  Under one PCG
+ * strategy every shape gives bit-identical results: the vertex phase is
+ * per vertex, each lane takes a node's entries in the same order, and p.A p
+ * is summed per group of 8 nodes in the same tree.  lc_batch_set_shape
+ * rebuilds the plan (LC_ERR_ARG for another value); lc_batch_get_shape
+ * reads it. */
+typedef struct {
+    int pcg_mode;
+    int vert_block;
+    int node_warps;
+    int node_unroll;
+} lc_batch_shape;
+lc_status lc_batch_set_shape(lc_batch *batch, const lc_batch_shape *shape);
+lc_status lc_batch_get_shape(const lc_batch *batch, lc_batch_shape *shape);
+/* The autotuner over shapes: for every PCG strategy, every shape where any
+ * capture runs the per-iteration J^T J p (else the one default shape): a
+ * solve from the identity, its members' node parameters and energy
+ * histories compared with the strategy's first shape (a shape whose bits
+ * differ is rejected and counted), then reps timed solves from the identity.
+ * The fastest shape is set and stored in a process-wide table under the
+ * batch's size class (lc_batch_size_class); with use_cache and an entry for
+ * the class, that entry is set without timing (*from_cache = 1).  Outputs
+ * are nullable.  The members' node parameters are left at a solve from the
+ * identity. */
+lc_status lc_batch_autotune_shapes(lc_batch *batch, int reps, int use_cache, lc_batch_shape *best, float *best_ms,
+                                   int *from_cache, int *n_tried, int *n_rejected);
+/* Size class of a batch: per member (K, ceil log2 of its vertices, ceil
+ * log2 of its nodes), sorted with multiplicities ("K4.N12.n9x3,...");
+ * LC_ERR_ARG if it does not fit in len bytes. */
+lc_status lc_batch_size_class(const lc_batch *batch, char *key, int len);
+/* The table as text, one line per size class: "class<TAB>pcg_mode vert_block
+ * node_warps node_unroll ms"; *needed receives the size with the final NUL
+ * (text may be null to ask for it).  _load merges such text into the table
+ * (LC_ERR_ARG for a malformed line; nothing is merged then). */
+lc_status lc_autotune_table(char *text, int len, int *needed);
+lc_status lc_autotune_table_load(const char *text);
 /* The batch's CUDA stream (a cudaStream_t), for ordering and timing. */
 void *lc_batch_stream(const lc_batch *batch);
 /* One matrix-free J^T J p of every member in one launch pair (vertex phase,

@@ -13,8 +13,13 @@
 // kernel and cluster size.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "lc_context.h"
@@ -94,6 +99,8 @@ struct lc_batch {
     int pix_blocks = 0;
     std::vector<BatchGroup> groups;   // captures on the cluster PCG
     int mode = LC_BATCH_PCG_AUTO;
+    // launch shape of the per-iteration J^T J p (captures not on a cluster)
+    int jv_block = kVertTile, jn_warps = kNodeWarps, jn_unroll = 4;
     int first_multi = 0;              // first slot on the per-iteration / grid PCG
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -223,6 +230,12 @@ lc_status lc_batch::build() {
                        family(0, count, node), family(0, count, vec), family(0, count, pix)};
     const Fam fm[3] = {family(first_multi, count, vert), family(first_multi, count, node),
                        family(first_multi, count, vec)};
+    // the J^T J p's own blocks at the batch's launch shape
+    const int vb = jv_block, nw = jn_warps;
+    auto jvert = [vb](const CapDesc& C) { return (C.N + vb - 1) / vb; };
+    auto jnode = [nw](const CapDesc& C) { return (C.n + nw - 1) / nw; };
+    const Fam fj[4] = {family(0, count, jvert), family(0, count, jnode), family(first_multi, count, jvert),
+                       family(first_multi, count, jnode)};
     if (cudaMalloc(&items, sizeof(WorkItem) * std::max<size_t>(w.size(), 1)) != cudaSuccess ||
         cudaMalloc(&dC, sizeof(CapDesc) * count) != cudaSuccess) {
         cudaGetLastError();
@@ -242,6 +255,15 @@ lc_status lc_batch::build() {
     multi.vert = fm[0].n, multi.vert_items = at(fm[0]);
     multi.node = fm[1].n, multi.node_items = at(fm[1]);
     multi.vec = fm[2].n, multi.vec_items = at(fm[2]);
+    for (Tiles* T : {&all, &multi}) {
+        T->jv_block = jv_block;
+        T->jn_warps = jn_warps;
+        T->jn_unroll = jn_unroll;
+    }
+    all.jv = fj[0].n, all.jv_items = at(fj[0]);
+    all.jn = fj[1].n, all.jn_items = at(fj[1]);
+    multi.jv = fj[2].n, multi.jv_items = at(fj[2]);
+    multi.jn = fj[3].n, multi.jn_items = at(fj[3]);
     if (cudaGetLastError() != cudaSuccess) return fail(LC_ERR_CUDA, "lc_batch: uploading the work lists");
     return LC_OK;
 }
@@ -584,5 +606,224 @@ extern "C" lc_status lc_batch_apply_jtj(lc_batch* b, int stage) {
     if (stage) launch_jtj_stage(b->dC, b->all, b->stream);
     launch_jtj(b->dC, b->all, nullptr, nullptr, nullptr, nullptr, false, b->stream);
     if (cudaGetLastError() != cudaSuccess) return b->fail(LC_ERR_CUDA, "lc_batch_apply_jtj: launch");
+    return LC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch shapes of the per-iteration J^T J p and the shape autotuner with its
+// per-size-class table (process-wide).
+// ---------------------------------------------------------------------------
+extern "C" lc_status lc_batch_set_shape(lc_batch* b, const lc_batch_shape* s) {
+    if (!b || !s) return LC_ERR_ARG;
+    if (s->pcg_mode < LC_BATCH_PCG_AUTO || s->pcg_mode > LC_BATCH_PCG_PER_ITERATION ||
+        !jtj_shape_valid(s->vert_block, s->node_warps, s->node_unroll))
+        return b->fail(LC_ERR_ARG, "lc_batch_set_shape: unknown mode or shape");
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->mode = s->pcg_mode;
+    b->jv_block = s->vert_block;
+    b->jn_warps = s->node_warps;
+    b->jn_unroll = s->node_unroll;
+    return b->build();
+}
+
+extern "C" lc_status lc_batch_get_shape(const lc_batch* b, lc_batch_shape* s) {
+    if (!b || !s) return LC_ERR_ARG;
+    s->pcg_mode = b->mode;
+    s->vert_block = b->jv_block;
+    s->node_warps = b->jn_warps;
+    s->node_unroll = b->jn_unroll;
+    return LC_OK;
+}
+
+// per member (K, ceil log2 of the vertices, ceil log2 of the nodes), sorted,
+// with multiplicities: "K4.N12.n9x3,K8.N17.n12x1"
+static std::string size_class(const lc_batch* b) {
+    std::map<std::string, int> cnt;
+    for (const lc_ctx* c : b->ctxs) {
+        char k[64];
+        snprintf(k, sizeof(k), "K%d.N%d.n%d", c->hC.K, (int)std::ceil(std::log2((double)std::max(c->hC.N, 1))),
+                 (int)std::ceil(std::log2((double)std::max(c->hC.n, 1))));
+        ++cnt[k];
+    }
+    std::string out;
+    for (const auto& kv : cnt) {
+        if (!out.empty()) out += ",";
+        out += kv.first + "x" + std::to_string(kv.second);
+    }
+    return out;
+}
+
+extern "C" lc_status lc_batch_size_class(const lc_batch* b, char* key, int len) {
+    if (!b || !key || len < 1) return LC_ERR_ARG;
+    const std::string k = size_class(b);
+    if ((int)k.size() + 1 > len) return LC_ERR_ARG;
+    memcpy(key, k.c_str(), k.size() + 1);
+    return LC_OK;
+}
+
+struct TuneEntry {
+    lc_batch_shape shape;
+    float ms;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneEntry> g_tune;
+
+// every member's node parameters and per-step energy history, as bytes
+static lc_status batch_snapshot(lc_batch* b, std::vector<unsigned char>& out) {
+    out.clear();
+    for (lc_ctx* c : b->ctxs) {
+        const CapDesc& C = c->hC;
+        const size_t off = out.size();
+        const size_t nb = sizeof(float4) * 4 * (size_t)C.n + sizeof(double) * 2 * (LC_MAX_GN + 1);
+        out.resize(off + nb);
+        if (cudaMemcpy(out.data() + off, C.node_R, sizeof(float4) * 3 * (size_t)C.n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(out.data() + off + sizeof(float4) * 3 * (size_t)C.n, C.node_t, sizeof(float4) * (size_t)C.n,
+                       cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(out.data() + off + sizeof(float4) * 4 * (size_t)C.n, C.hist, sizeof(double) * 2 * (LC_MAX_GN + 1),
+                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return b->fail(LC_ERR_CUDA, "lc_batch_autotune_shapes: reading results");
+        }
+    }
+    return LC_OK;
+}
+
+extern "C" lc_status lc_batch_autotune_shapes(lc_batch* b, int reps, int use_cache, lc_batch_shape* best_out,
+                                              float* best_ms, int* from_cache, int* n_tried, int* n_rejected) {
+    if (!b || reps < 1) return LC_ERR_ARG;
+    cudaSetDevice(b->device);
+    const std::string key = size_class(b);
+    if (from_cache) *from_cache = 0;
+    if (n_tried) *n_tried = 0;
+    if (n_rejected) *n_rejected = 0;
+    if (use_cache) {
+        TuneEntry e{};
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                e = it->second;
+                hit = true;
+            }
+        }
+        if (hit) {
+            if (from_cache) *from_cache = 1;
+            if (best_out) *best_out = e.shape;
+            if (best_ms) *best_ms = e.ms;
+            return lc_batch_set_shape(b, &e.shape);
+        }
+    }
+    const int modes[4] = {LC_BATCH_PCG_AUTO, LC_BATCH_PCG_CLUSTER8, LC_BATCH_PCG_CLUSTER16,
+                          LC_BATCH_PCG_PER_ITERATION};
+    const int vbs[3] = {128, 256, 512}, nws[2] = {kNodeWarps, 2 * kNodeWarps}, nus[3] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    lc_status s = LC_OK;
+    lc_batch_shape best{};
+    float best_t = -1.f;
+    int tried = 0, rejected = 0;
+    std::vector<unsigned char> ref, cur;
+    for (int m : modes) {
+        lc_batch_shape sh{m, kVertTile, kNodeWarps, 4};
+        if ((s = lc_batch_set_shape(b, &sh))) break;
+        // shapes matter only where captures run the per-iteration J^T J p
+        const bool any_multi = b->first_multi < (int)b->ctxs.size();
+        std::vector<lc_batch_shape> cands;
+        if (!any_multi)
+            cands.push_back(sh);
+        else
+            for (int vb : vbs)
+                for (int nw : nws)
+                    for (int nu : nus) cands.push_back(lc_batch_shape{m, vb, nw, nu});
+        ref.clear();
+        for (const lc_batch_shape& c : cands) {
+            if ((s = lc_batch_set_shape(b, &c))) break;
+            // capture and one run, then the bit-identity check against the
+            // mode's first shape, then reps timed solves from the identity
+            if ((s = lc_batch_solve(b, 1, nullptr))) break;
+            cudaStreamSynchronize(b->stream);
+            if ((s = batch_snapshot(b, ref.empty() ? ref : cur))) break;
+            ++tried;
+            if (&c != &cands[0] && cur != ref) {
+                ++rejected;
+                continue;
+            }
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && !s; ++r) s = lc_batch_solve(b, 1, nullptr);
+            if (s) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (best_t < 0.f || ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
+        if (s) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if (n_tried) *n_tried = tried;
+    if (n_rejected) *n_rejected = rejected;
+    if (best_out) *best_out = best;
+    if (best_ms) *best_ms = best_t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = TuneEntry{best, best_t};
+    }
+    return lc_batch_set_shape(b, &best);
+}
+
+// the table as text: one line per size class, "key<TAB>mode vert_block
+// node_warps node_unroll ms"
+extern "C" lc_status lc_autotune_table(char* text, int len, int* needed) {
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& kv : g_tune) {
+            char line[96];
+            const lc_batch_shape& s = kv.second.shape;
+            snprintf(line, sizeof(line), "\t%d %d %d %d %.6g\n", s.pcg_mode, s.vert_block, s.node_warps,
+                     s.node_unroll, (double)kv.second.ms);
+            out += kv.first + line;
+        }
+    }
+    if (needed) *needed = (int)out.size() + 1;
+    if (!text) return LC_OK;
+    if (len < (int)out.size() + 1) return LC_ERR_ARG;
+    memcpy(text, out.c_str(), out.size() + 1);
+    return LC_OK;
+}
+
+extern "C" lc_status lc_autotune_table_load(const char* text) {
+    if (!text) return LC_ERR_ARG;
+    std::map<std::string, TuneEntry> add;
+    const char* p = text;
+    while (*p) {
+        const char* nl = strchr(p, '\n');
+        const std::string line(p, nl ? (size_t)(nl - p) : strlen(p));
+        p = nl ? nl + 1 : p + line.size();
+        if (line.empty()) continue;
+        const size_t tab = line.find('\t');
+        if (tab == std::string::npos || tab == 0) return LC_ERR_ARG;
+        TuneEntry e{};
+        double ms = 0.0;
+        if (sscanf(line.c_str() + tab + 1, "%d %d %d %d %lf", &e.shape.pcg_mode, &e.shape.vert_block,
+                   &e.shape.node_warps, &e.shape.node_unroll, &ms) != 5)
+            return LC_ERR_ARG;
+        if (e.shape.pcg_mode < LC_BATCH_PCG_AUTO || e.shape.pcg_mode > LC_BATCH_PCG_PER_ITERATION ||
+            !jtj_shape_valid(e.shape.vert_block, e.shape.node_warps, e.shape.node_unroll))
+            return LC_ERR_ARG;
+        e.ms = (float)ms;
+        add[line.substr(0, tab)] = e;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : add) g_tune[kv.first] = kv.second;
     return LC_OK;
 }

@@ -331,6 +331,28 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NV], double (&out)[NV], f
 
 // Write this tile's partials; returns true (in every thread) in the block
 // that finished last for this capture and counter.
+// m consecutive tiles' partials (tile0 .. tile0 + m - 1) from one block;
+// returns true (in every thread) in the block that finished last.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const CapDesc& C, int counter, int tile0, int m, int ntiles,
+                                                 const double (*v)[NV], double* part_base) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        for (int g = 0; g < m; ++g)
+#pragma unroll
+            for (int j = 0; j < NV; ++j) part_base[(tile0 + g) * NV + j] = v[g][j];
+        __threadfence();
+        unsigned done = atomicAdd(&C.counters[counter], (unsigned)m);
+        last = (done + (unsigned)m == (unsigned)ntiles);
+        if (last) {
+            __threadfence();
+            C.counters[counter] = 0u;   // re-arm for the next launch
+        }
+    }
+    __syncthreads();
+    return last;
+}
+
 template <int NV>
 __device__ __forceinline__ bool publish_partial(const CapDesc& C, int counter, int tile, int ntiles,
                                                 const double (&v)[NV], double* part_base) {
@@ -390,6 +412,14 @@ struct Tiles {
     const WorkItem* medge_items = nullptr;
     const WorkItem* node_items = nullptr;
     const WorkItem* vec_items = nullptr;
+    // launch shape of the per-iteration J^T J p (launch_jtj): vertices per
+    // vertex-phase block, nodes (warps) per node-phase block and the node
+    // phase's entry rounds in flight, with their own work lists (jv / jn
+    // blocks); every shape gives bit-identical results
+    int jv = 0, jn = 0;
+    const WorkItem* jv_items = nullptr;
+    const WorkItem* jn_items = nullptr;
+    int jv_block = kVertTile, jn_warps = kNodeWarps, jn_unroll = 4;
 };
 
 inline Tiles single_tiles(const CapDesc& C) {
@@ -399,6 +429,8 @@ inline Tiles single_tiles(const CapDesc& C) {
     t.medge = C.medge_tiles;
     t.node = C.node_tiles;
     t.vec = (C.n + kVecThreads - 1) / kVecThreads;
+    t.jv = C.vert_tiles;
+    t.jn = C.node_tiles;
     return t;
 }
 
@@ -451,6 +483,8 @@ void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const flo
 // K: the captures' common K selects an unrolled vertex phase (0: any K)
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
                 float4* out_lo, bool dot, cudaStream_t st, int K = 0);
+// the launch shapes launch_jtj has kernels for
+bool jtj_shape_valid(int vert_block, int node_warps, int node_unroll);
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);

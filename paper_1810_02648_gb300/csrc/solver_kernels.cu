@@ -370,11 +370,11 @@ void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st) {
 }
 void launch_jtj_stage(const CapDesc* dC, const CapDesc& hC, cudaStream_t st) { launch_jtj_stage(dC, single_tiles(hC), st); }
 
-template <int KT>
-__global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
-                                                                const WorkItem* __restrict__ items,
-                                                                const float4* __restrict__ p_in,
-                                                                const float4* __restrict__ p_lo_in, int check_stop) {
+template <int KT, int VB>
+__global__ void __launch_bounds__(VB) jtj_vertex_kernel(const CapDesc* __restrict__ caps,
+                                                         const WorkItem* __restrict__ items,
+                                                         const float4* __restrict__ p_in,
+                                                         const float4* __restrict__ p_lo_in, int check_stop) {
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
     // null: the capture's PCG direction (both parts)
     const float4* __restrict__ p = p_in ? p_in : C.p;
     const float4* __restrict__ p_lo = p_in ? p_lo_in : C.p_lo;
-    const int i = tile * kVertTile + threadIdx.x;
+    const int i = tile * VB + threadIdx.x;
     if (i >= C.N) return;
     const int K = C.K;
     const float4* __restrict__ A = C.vA + (size_t)i * K;
@@ -412,13 +412,33 @@ __global__ void __launch_bounds__(kVertTile) jtj_vertex_kernel(const CapDesc* __
     C.q_lo[i] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
 }
 
-__global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
-                                                                    const WorkItem* __restrict__ items,
-                                                                    const float4* __restrict__ p_in,
-                                                                    const float4* __restrict__ p_lo_in,
-                                                                    float4* __restrict__ out_in,
-                                                                    float4* __restrict__ out_lo_in, int dot) {
-    __shared__ float2 sh[kNodeWarps];
+// the p . A p total of a capture: alpha = r.z / p.A p as a pair division, or
+// a breakdown stop
+__device__ __forceinline__ void dot_alpha(const CapDesc& C, double pAp) {
+    Scalars* sc = C.sc;
+    sc->pAp = pAp;
+    if (!(pAp > 0.0)) {
+        sc->stop = 1;
+        sc->breakdown = 1;
+    } else {
+        const fp2 alpha = fp2_div(fp2_from_double(sc->rz), fp2_from_double(pAp));
+        sc->alpha_h = alpha.h;
+        sc->alpha_l = alpha.l;
+    }
+}
+
+// W warps (nodes) per block, U rounds of a node's entries in flight per lane.
+// p . A p is summed per group of kNodeWarps nodes in the same tree for any W
+// (W = kNodeWarps or 2 kNodeWarps), so every shape gives the same bits.
+template <int W, int U>
+__global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
+                                                          const WorkItem* __restrict__ items,
+                                                          const float4* __restrict__ p_in,
+                                                          const float4* __restrict__ p_lo_in,
+                                                          float4* __restrict__ out_in,
+                                                          float4* __restrict__ out_lo_in, int dot) {
+    static_assert(W == kNodeWarps || W == 2 * kNodeWarps, "node block of one or two partial groups");
+    __shared__ float2 sh[W];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
@@ -429,13 +449,13 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
     float4* __restrict__ out = out_in ? out_in : C.Ap;
     float4* __restrict__ out_lo = out_in ? out_lo_in : C.Ap_lo;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int k = tile * kNodeTile + w;
+    const int k = tile * W + w;
     fp2acc pap;
     if (k < C.n) {
         fp2acc acc[6];
-        // four rounds of the node's entries at a time: their loads are issued
-        // together before any result is used
-        constexpr int U = 4;
+        // U rounds of the node's entries at a time: their loads are issued
+        // together before any result is used (each lane still takes entries
+        // lane, lane + 32, ... in order)
         const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
         for (int jb = e0 + lane; jb < e1; jb += 32 * U) {
             float4 a[U];
@@ -480,31 +500,76 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_node_kernel(const CapDesc
         }
     }
     if (!dot) return;
-    const fp2 tot = block_sum_fp2<kNodeWarps>(pap.get(), sh);
-    const double part[1] = {fp2_to_double(tot)};
-    reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, part, [&](const double (&sum)[1]) {
-        Scalars* sc = C.sc;
-        sc->pAp = sum[0];
-        if (!(sum[0] > 0.0)) {
-            sc->stop = 1;
-            sc->breakdown = 1;
-        } else {
-            const fp2 alpha = fp2_div(fp2_from_double(sc->rz), fp2_from_double(sum[0]));
-            sc->alpha_h = alpha.h;
-            sc->alpha_l = alpha.l;
+    if constexpr (W == kNodeWarps) {
+        const fp2 tot = block_sum_fp2<kNodeWarps>(pap.get(), sh);
+        const double part[1] = {fp2_to_double(tot)};
+        reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, part,
+                           [&](const double (&sum)[1]) { dot_alpha(C, sum[0]); });
+    } else {
+        // two groups of kNodeWarps nodes: warp g sums group g's warp totals
+        // in its first kNodeWarps lanes, the tree block_sum_fp2 uses
+        __shared__ float2 gs[2];
+        const fp2 v = fp2_warp_sum(pap.get());
+        if (lane == 0) sh[w] = make_float2(v.h, v.l);
+        __syncthreads();
+        if (w < 2) {
+            const float2 a = lane < kNodeWarps ? sh[w * kNodeWarps + lane] : make_float2(0.f, 0.f);
+            const fp2 g = fp2_warp_sum(fp2{a.x, a.y});
+            if (lane == 0) gs[w] = make_float2(g.h, g.l);
         }
-    });
+        __syncthreads();
+        const int t0 = 2 * tile;
+        const int m = min(2, C.node_tiles - t0);
+        const double part[2][1] = {{fp2_to_double(fp2{gs[0].x, gs[0].y})}, {fp2_to_double(fp2{gs[1].x, gs[1].y})}};
+        if (!publish_partials<1>(C, CNT_DOT, t0, m, C.node_tiles, part, C.part)) return;
+        if (threadIdx.x >= 32) return;
+        double tot[1];
+        sum_partials_warp<1>(C.part, C.node_tiles, tot);
+        if (threadIdx.x == 0) dot_alpha(C, tot[0]);
+    }
+}
+
+template <int VB>
+static void launch_jtj_vertex(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, bool dot,
+                              cudaStream_t st, int K) {
+    if (K == 4)
+        jtj_vertex_kernel<4, VB><<<T.jv, VB, 0, st>>>(dC, T.jv_items, p, p_lo, dot ? 1 : 0);
+    else if (K == 8)
+        jtj_vertex_kernel<8, VB><<<T.jv, VB, 0, st>>>(dC, T.jv_items, p, p_lo, dot ? 1 : 0);
+    else
+        jtj_vertex_kernel<0, VB><<<T.jv, VB, 0, st>>>(dC, T.jv_items, p, p_lo, dot ? 1 : 0);
+}
+
+template <int W>
+static void launch_jtj_node(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
+                            float4* out_lo, bool dot, cudaStream_t st) {
+    const int d = dot ? 1 : 0;
+    if (T.jn_unroll == 2)
+        jtj_node_kernel<W, 2><<<T.jn, W * 32, 0, st>>>(dC, T.jn_items, p, p_lo, out, out_lo, d);
+    else if (T.jn_unroll == 8)
+        jtj_node_kernel<W, 8><<<T.jn, W * 32, 0, st>>>(dC, T.jn_items, p, p_lo, out, out_lo, d);
+    else
+        jtj_node_kernel<W, 4><<<T.jn, W * 32, 0, st>>>(dC, T.jn_items, p, p_lo, out, out_lo, d);
+}
+
+bool jtj_shape_valid(int vert_block, int node_warps, int node_unroll) {
+    return (vert_block == 128 || vert_block == 256 || vert_block == 512) &&
+           (node_warps == kNodeWarps || node_warps == 2 * kNodeWarps) &&
+           (node_unroll == 2 || node_unroll == 4 || node_unroll == 8);
 }
 
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
                 float4* out_lo, bool dot, cudaStream_t st, int K) {
-    if (K == 4)
-        jtj_vertex_kernel<4><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
-    else if (K == 8)
-        jtj_vertex_kernel<8><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
+    if (T.jv_block == 128)
+        launch_jtj_vertex<128>(dC, T, p, p_lo, dot, st, K);
+    else if (T.jv_block == 512)
+        launch_jtj_vertex<512>(dC, T, p, p_lo, dot, st, K);
     else
-        jtj_vertex_kernel<0><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, p, p_lo, dot ? 1 : 0);
-    jtj_node_kernel<<<T.node, kNodeWarps * 32, 0, st>>>(dC, T.node_items, p, p_lo, out, out_lo, dot ? 1 : 0);
+        launch_jtj_vertex<256>(dC, T, p, p_lo, dot, st, K);
+    if (T.jn_warps == 2 * kNodeWarps)
+        launch_jtj_node<2 * kNodeWarps>(dC, T, p, p_lo, out, out_lo, dot, st);
+    else
+        launch_jtj_node<kNodeWarps>(dC, T, p, p_lo, out, out_lo, dot, st);
 }
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const float4* p_lo, float4* out,
                 float4* out_lo, bool dot, cudaStream_t st) {

@@ -91,6 +91,14 @@ _SIGS = {
     "lc_batch_stream": [_P],
     "lc_batch_apply_jtj": [_P, ctypes.c_int],
     "lc_batch_step": [_P, _P, ctypes.c_uint, _P],
+    "lc_batch_set_shape": [_P, _P],
+    "lc_batch_get_shape": [_P, _P],
+    "lc_batch_autotune_shapes": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)],
+    "lc_batch_size_class": [_P, ctypes.c_char_p, ctypes.c_int],
+    "lc_autotune_table": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "lc_autotune_table_load": [ctypes.c_char_p],
     "lc_mlp_create": [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P],
     "lc_mlp_destroy": [_P],
     "lc_mlp_last_error": [_P],
@@ -619,6 +627,32 @@ STEP_EULER_START, STEP_CARRY_GRAPH = 1, 2
 BATCH_PCG_AUTO, BATCH_PCG_CLUSTER8, BATCH_PCG_CLUSTER16, BATCH_PCG_PER_ITERATION = 0, 1, 2, 3
 
 
+class lc_batch_shape(ctypes.Structure):
+    _fields_ = [("pcg_mode", ctypes.c_int), ("vert_block", ctypes.c_int), ("node_warps", ctypes.c_int),
+                ("node_unroll", ctypes.c_int)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def autotune_table() -> str:
+    """The process-wide shape table (lc_autotune_table) as text."""
+    lib = load()
+    need = ctypes.c_int(0)
+    if lib.lc_autotune_table(None, 0, ctypes.byref(need)) != LC_OK:
+        raise LivecapError(LC_ERR_ARG, "lc_autotune_table failed")
+    buf = ctypes.create_string_buffer(max(need.value, 1))
+    if lib.lc_autotune_table(buf, len(buf), None) != LC_OK:
+        raise LivecapError(LC_ERR_ARG, "lc_autotune_table failed")
+    return buf.value.decode()
+
+
+def autotune_table_load(text: str):
+    st = load().lc_autotune_table_load(text.encode())
+    if st != LC_OK:
+        raise LivecapError(st, "lc_autotune_table_load: malformed table")
+
+
 class Batch:
     """Several contexts solved together (lc_batch_*): one launch per phase
     for all captures, the whole non-rigid loop in one CUDA graph."""
@@ -677,6 +711,33 @@ class Batch:
         arr = (lc_solve_stats * len(self.contexts))()
         self._check(self._lib.lc_batch_step(self.h, h, flags, arr))
         return [a.to_dict() for a in arr]
+
+    def set_shape(self, pcg_mode: int, vert_block: int = 256, node_warps: int = 8, node_unroll: int = 4):
+        sh = lc_batch_shape(pcg_mode, vert_block, node_warps, node_unroll)
+        self._check(self._lib.lc_batch_set_shape(self.h, ctypes.byref(sh)))
+
+    def shape(self) -> dict:
+        sh = lc_batch_shape()
+        self._check(self._lib.lc_batch_get_shape(self.h, ctypes.byref(sh)))
+        return sh.to_dict()
+
+    def size_class(self) -> str:
+        buf = ctypes.create_string_buffer(4096)
+        self._check(self._lib.lc_batch_size_class(self.h, buf, len(buf)))
+        return buf.value.decode()
+
+    def autotune_shapes(self, reps: int = 2, use_cache: bool = True) -> dict:
+        """lc_batch_autotune_shapes: returns the chosen shape, its time and
+        whether it came from the table, with the counts of shapes tried and
+        rejected by the bit-identity check."""
+        sh = lc_batch_shape()
+        ms = ctypes.c_float(0.0)
+        hit, tried, rej = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._lib.lc_batch_autotune_shapes(self.h, int(reps), int(use_cache), ctypes.byref(sh),
+                                                       ctypes.byref(ms), ctypes.byref(hit), ctypes.byref(tried),
+                                                       ctypes.byref(rej)))
+        return dict(shape=sh.to_dict(), ms=ms.value, from_cache=bool(hit.value), tried=tried.value,
+                    rejected=rej.value)
 
     def apply_jtj(self, stage: bool = False):
         """Enqueue one J^T J p of every member (measurement entry); stage

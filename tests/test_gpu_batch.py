@@ -165,3 +165,53 @@ def test_batch_members_with_body_part_masks():
     b.close()
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("shape", [(128, 8, 2), (512, 16, 8), (256, 16, 4), (128, 16, 2)])
+def test_jtj_launch_shapes_are_bit_identical(scenes, shape):
+    """The per-iteration J^T J p at another launch shape (vertex block,
+    nodes per node block, entry rounds in flight) gives the same bits as the
+    default shape: node parameters, vertices, flags, energies."""
+    from paper_1810_02648_gb300 import Batch
+    from paper_1810_02648_gb300.livecap import BATCH_PCG_PER_ITERATION
+    ctxs = _contexts(scenes, 1)
+    b = Batch(ctxs)
+    b.set_shape(BATCH_PCG_PER_ITERATION)
+    ref_stats = b.solve(from_identity=True)
+    ref = [c.read_back() for c in ctxs]
+    vb, nw, nu = shape
+    b.set_shape(BATCH_PCG_PER_ITERATION, vb, nw, nu)
+    assert b.shape() == dict(pcg_mode=BATCH_PCG_PER_ITERATION, vert_block=vb, node_warps=nw, node_unroll=nu)
+    stats = b.solve(from_identity=True)
+    for i, c in enumerate(ctxs):
+        assert _same(c.read_back(), ref[i]), f"capture {i}"
+        assert stats[i]["e_gn"] == ref_stats[i]["e_gn"] and stats[i]["e_total"] == ref_stats[i]["e_total"]
+        assert stats[i]["pcg_iters"] == ref_stats[i]["pcg_iters"]
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_shape_autotuner_and_its_table(scenes):
+    """The autotuner tries every shape of the strategies that use the
+    per-iteration product, rejects none (all bit-identical), sets the
+    fastest, stores it under the batch's size class, and a second batch of
+    the same class takes it from the table without timing."""
+    from paper_1810_02648_gb300 import Batch
+    from paper_1810_02648_gb300.livecap import autotune_table
+    ctxs = _contexts(scenes, 0)
+    b = Batch(ctxs)
+    r = b.autotune_shapes(reps=1, use_cache=False)
+    report("shape_autotune", tried=r["tried"], rejected=r["rejected"], ms=r["ms"], **r["shape"])
+    assert r["tried"] > 4 and r["rejected"] == 0 and not r["from_cache"]
+    assert b.shape() == r["shape"]
+    key = b.size_class()
+    table = autotune_table()
+    assert any(line.split("\t")[0] == key for line in table.splitlines())
+    b2 = Batch(ctxs)
+    r2 = b2.autotune_shapes(reps=1, use_cache=True)
+    assert r2["from_cache"] and r2["shape"] == r["shape"] and r2["tried"] == 0
+    for bt in (b, b2):
+        bt.close()
+    for c in ctxs:
+        c.close()
