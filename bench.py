@@ -76,6 +76,8 @@ def parse():
                     help="body / tiny: Gauss-Newton steps at most while a frame works toward the oracle's energy")
     ap.add_argument("--gn-block", type=int, default=10,
                     help="body / tiny: Gauss-Newton steps per conditional graph block (0: unrolled)")
+    ap.add_argument("--tma-taps", action="store_true",
+                    help="body / tiny: stage each vertex's image taps with a TMA bulk-tensor copy")
     ap.add_argument("--profile-region", action="store_true",
                     help="start / stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--no-body-parts", action="store_true",
@@ -733,7 +735,7 @@ def run_frames(a):
         if body_parts:
             c.set_body_parts(sc.skeleton["bone_part"], sc.skeleton["torso_part"], 10)
         fr["target"] = fr["e_star"] * (1.0 + TARGET_TOL)
-        c.set_params(n_gn=a.gn_cap, target_energy=fr["target"], gn_block=a.gn_block)
+        c.set_params(n_gn=a.gn_cap, target_energy=fr["target"], gn_block=a.gn_block, tma_taps=1 if a.tma_taps else 0)
         ctxs.append(c)
     scene = frames[0]["scene"]
     has_pose = scene.skeleton is not None
@@ -892,7 +894,8 @@ def run_frames(a):
                        f"frames/s until the non-rigid energy reaches the FP64 oracle's final energy "
                        f"({scene.n_gn} GN x {scene.n_pcg} PCG) within {TARGET_TOL:g}, at most {a.gn_cap} GN steps"
                        + ("; body-part mask of the silhouette term" if body_parts else ""))
-    cfg.update(frames=len(frames), gn_cap=a.gn_cap, gn_block=a.gn_block, target_tol=TARGET_TOL, body_parts=body_parts)
+    cfg.update(frames=len(frames), gn_cap=a.gn_cap, gn_block=a.gn_block, target_tol=TARGET_TOL, body_parts=body_parts,
+               tma_taps=bool(a.tma_taps))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,

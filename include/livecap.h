@@ -138,6 +138,14 @@ typedef struct {
                                so the non-rigid stage starts from the previous frame's deformation
                                carried along with the bones; a record is dropped by
                                lc_pose_clear_history and by a new graph.  0 (default): off */
+    int tma_taps;           /* 1: the linearisation of a single capture stages every vertex's 4 x 4
+                               pixel patch of the frame (its bilinear taps and central differences,
+                               Sec. 3.4 E_photo / E_silhouette) into shared memory with one TMA
+                               bulk-tensor copy per vertex (cp.async.bulk.tensor, one mbarrier per
+                               CTA, a bounded wait; LC_ERR_TIMEOUT from the next statistics read if
+                               a wait ran out, the global loads being used then); vertices whose
+                               patch leaves the frame, batched solves and pyramid levels use global
+                               loads.  The same bits either way.  Default 1; 0: global loads */
 } lc_params;
 
 #define LC_MAX_GN 64

@@ -129,6 +129,7 @@ extern "C" lc_status lc_params_default(lc_params* p) {
     p->pyr_ksize[0] = 15;
     p->pyr_ksize[1] = 9;
     p->pyr_ksize[2] = 3;
+    p->tma_taps = 1;   // measured faster than the global loads on the body capture, same bits
     return LC_OK;
 }
 
@@ -200,6 +201,7 @@ void lc_ctx::apply_params() {
     hC.eps_vis = params.eps_vis;
     hC.target_energy = params.target_energy;
     hC.sigma_c = params.sigma_c;
+    hC.tma_taps = params.tma_taps;
     surface_weights();
 }
 
@@ -212,7 +214,8 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         !(p->w_smooth >= 0.f) || !(p->w_edge >= 0.f) || !(p->w_velocity >= 0.f) || !(p->w_acceleration >= 0.f) ||
         p->pose_solver < 0 || p->pose_solver > 1 || !(p->lambda_temporal >= 0.f) || !(p->lambda_anatomic >= 0.f) ||
         !(p->sigma_c >= 0.f) || p->pyr_levels < 0 || p->pyr_levels > 3 || p->pose_displacement < 0 ||
-        p->pose_displacement > 1 || p->gn_block < 0 || p->graph_warp < 0 || p->graph_warp > 1)
+        p->pose_displacement > 1 || p->gn_block < 0 || p->graph_warp < 0 || p->graph_warp > 1 ||
+        p->tma_taps < 0 || p->tma_taps > 1)
         return ctx->fail(LC_ERR_ARG, "lc_set_params: out of range");
     for (int j = 0; j < 3; ++j)
         if (p->pyr_ksize[j] < 1 || p->pyr_ksize[j] > kPyrMaxTaps || p->pyr_ksize[j] % 2 == 0)
@@ -222,6 +225,10 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
     // a target energy switches the captured solve to conditional blocks of steps
     if ((p->target_energy > 0.f) != (ctx->params.target_energy > 0.f) || p->gn_block != ctx->params.gn_block)
         ctx->drop_graph();
+    if (p->tma_taps != ctx->params.tma_taps) {   // the captured linearisations change kernel
+        ctx->drop_graph();
+        ctx->pose_drop_graph();
+    }
     if (p->n_gn != ctx->params.n_gn || p->n_pcg != ctx->params.n_pcg || p->pcg_kernel != ctx->params.pcg_kernel ||
         p->n_gn_surface != ctx->params.n_gn_surface || p->n_pcg_surface != ctx->params.n_pcg_surface)
         ctx->drop_graph();
@@ -235,6 +242,46 @@ extern "C" lc_status lc_set_params(lc_ctx* ctx, const lc_params* p) {
         if (s) return s;
     }
     return ctx->sync_desc();
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+// the frame as a 2D tensor of 4W x H floats, boxes of 16 x 4 (a 4 x 4 pixel
+// patch) for the TMA-staged taps; tma_ok = 0 where it cannot be made
+static void encode_image_map(lc_ctx* ctx) {
+    CapDesc& C = ctx->hC;
+    C.tma_ok = 0;
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || !C.img || C.W < 4 || C.H < 4) return;
+    if (linearize_tma_init() != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const cuuint64_t dims[2] = {4ull * (cuuint64_t)C.W, (cuuint64_t)C.H};
+    const cuuint64_t strides[1] = {16ull * (cuuint64_t)C.W};
+    const cuuint32_t box[2] = {16, 4}, elem[2] = {1, 1};
+    if (fn(&C.tmap_img, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)C.img, dims, strides, box, elem,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        C.tma_ok = 1;
 }
 
 extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int W, int H) {
@@ -276,6 +323,7 @@ extern "C" lc_status lc_set_camera(lc_ctx* ctx, float f, float cx, float cy, int
     ctx->hC.cy = cy;
     ctx->hC.W = W;
     ctx->hC.H = H;
+    encode_image_map(ctx);
     ctx->has_camera = true;
     return ctx->sync_desc();
 }
@@ -1161,6 +1209,10 @@ lc_status lc_ctx::read_stats(lc_solve_stats* stats, int n_gn, bool surface) {
     if (sc.status & kDevErrCapacity) {
         cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, status), 0, sizeof(int), stream);
         return fail(LC_ERR_NUMERIC, "internal: the cluster PCG's staging exceeded its planned capacity");
+    }
+    if (sc.status & kDevErrWait) {
+        cudaMemsetAsync((char*)hC.sc + offsetof(Scalars, status), 0, sizeof(int), stream);
+        return fail(LC_ERR_TIMEOUT, "a bounded wait for the TMA-staged image taps ran out (the global loads were used)");
     }
     memset(stats, 0, sizeof(*stats));
     stats->e_photo = sc.e_lin[0];

@@ -9,6 +9,7 @@
 
 #include <cstdint>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "livecap.h"
@@ -56,6 +57,7 @@ struct Scalars {
 
 // Bits of Scalars::status.
 constexpr int kDevErrCapacity = 1;   // the cluster PCG's staging exceeded its planned capacity
+constexpr int kDevErrWait = 2;       // a bounded wait (TMA staging of the image taps) ran out
 
 // Reduction counters: the last tile of a capture to finish a phase reduces
 // the per-tile partials in a fixed order (deterministic, no float atomics).
@@ -176,6 +178,12 @@ struct CapDesc {
     Scalars* sc;
     double* hist;            // 2 * (LC_MAX_GN + 1): [2 gn] energy, [2 gn + 1] step norm
     int* hist_iters;         // LC_MAX_GN + 2: PCG iterations per step, [LC_MAX_GN + 1] breakdowns
+    // TMA staging of the image taps (lc_params.tma_taps) in single-capture
+    // launches: img as a 2D tensor of 4W x H floats, passed to the kernel by
+    // value (valid when tma_ok)
+    int tma_taps;
+    int tma_ok;
+    CUtensorMap tmap_img;
 };
 
 struct WorkItem {
@@ -420,6 +428,9 @@ struct Tiles {
     const WorkItem* jv_items = nullptr;
     const WorkItem* jn_items = nullptr;
     int jv_block = kVertTile, jn_warps = kNodeWarps, jn_unroll = 4;
+    // linearisation with TMA-staged image taps (single-capture launches only:
+    // the tensor map is a kernel parameter)
+    bool tma = false;
 };
 
 inline Tiles single_tiles(const CapDesc& C) {
@@ -431,6 +442,7 @@ inline Tiles single_tiles(const CapDesc& C) {
     t.vec = (C.n + kVecThreads - 1) / kVecThreads;
     t.jv = C.vert_tiles;
     t.jn = C.node_tiles;
+    t.tma = C.tma_taps && C.tma_ok;
     return t;
 }
 
@@ -485,6 +497,8 @@ void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4
                 float4* out_lo, bool dot, cudaStream_t st, int K = 0);
 // the launch shapes launch_jtj has kernels for
 bool jtj_shape_valid(int vert_block, int node_warps, int node_unroll);
+// dynamic shared memory of the TMA-staged linearisation (once per process)
+cudaError_t linearize_tma_init();
 void launch_pcg_init(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);
 void launch_pcg_init(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 void launch_pcg_vectors(const CapDesc* dC, const CapDesc& hC, cudaStream_t st);

@@ -91,12 +91,70 @@ __device__ __forceinline__ void sample_image(const float4* img, int W, int H, fl
                lerp4(grad_y(img, W, H, x0, y1), grad_y(img, W, H, x1, y1), fx), fy);
 }
 
+// The same bilinear sample from a staged 4 x 4 patch P (row-major, its
+// origin at pixel (x0 - 1, y0 - 1)) when every tap lies inside the image:
+// the same operations in the same order as sample_image.
+__device__ __forceinline__ void sample_patch(const float4* P, float fx, float fy, float4& I, float4& Gx, float4& Gy) {
+    auto p = [&](int x, int y) { return P[4 * y + x]; };
+    auto gx = [&](int x, int y) { return scale4(sub4(p(x + 1, y), p(x - 1, y)), 0.5f); };
+    auto gy = [&](int x, int y) { return scale4(sub4(p(x, y + 1), p(x, y - 1)), 0.5f); };
+    I = lerp4(lerp4(p(1, 1), p(2, 1), fx), lerp4(p(1, 2), p(2, 2), fx), fy);
+    Gx = lerp4(lerp4(gx(1, 1), gx(2, 1), fx), lerp4(gx(1, 2), gx(2, 2), fx), fy);
+    Gy = lerp4(lerp4(gy(1, 1), gy(2, 1), fx), lerp4(gy(1, 2), gy(2, 2), fx), fy);
+}
+
+// mbarrier and bulk-tensor copy primitives (one CTA)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((unsigned)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// bounded wait for phase `parity`; false if it did not complete in time
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int max_tries) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    for (int t = 0; t < max_tries; ++t) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// a box of the 2D tensor map at element coordinates (x, y) into shared memory
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tmap, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            (unsigned)__cvta_generic_to_shared(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"((unsigned)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
+constexpr int kTmaPatchBytes = 16 * (int)sizeof(float4);        // 4 x 4 pixels
+constexpr int kTmaSmem = kVertTile * kTmaPatchBytes + 128;      // + alignment slack
+constexpr int kTmaMaxTries = 1 << 20;
+
 // ---------------------------------------------------------------------------
-// Linearisation: residuals, H_i, e_i and the data energy.
+// Linearisation: residuals, H_i, e_i and the data energy.  With TMA, every
+// vertex whose 4 x 4 tap patch lies inside the frame gets it by one
+// bulk-tensor copy into its own shared-memory slot (one mbarrier per CTA,
+// a bounded wait); the others, and a wait that runs out (flagged in the
+// capture's status word), take the global loads.  Both give the same bits.
 // ---------------------------------------------------------------------------
+template <bool TMA>
 __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __restrict__ caps,
                                                                const WorkItem* __restrict__ items, int update_b,
-                                                               int gn) {
+                                                               int gn, const __grid_constant__ CUtensorMap tmap) {
     __shared__ float sh[kVertTile / 32][2];
     int cap, tile;
     decode(items, cap, tile);
@@ -104,20 +162,23 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     if (update_b && C.sc->gn_stop) return;   // a GN step after the solve reached its target
     const int i = tile * kVertTile + threadIdx.x;
     float enf[2] = {0.f, 0.f};
+    uint32_t fl = 0;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 uv = make_float2(0.f, 0.f);
+    bool ok = false, ph = false, si = false, masked = false;
     if (i < C.N) {
-        uint32_t fl = C.flags[i];
-        const float4 v = C.vw[i];
-        const float2 uv = C.uv[i];
-        const bool ok = v.w > 0.f && in_image(uv, C.W, C.H);
-        bool ph = ok && (fl & LC_VIS_BIT);
-        bool si = ok && (fl & LC_INB_BIT);
+        fl = C.flags[i];
+        v = C.vw[i];
+        uv = C.uv[i];
+        ok = v.w > 0.f && in_image(uv, C.W, C.H);
+        ph = ok && (fl & LC_VIS_BIT);
+        si = ok && (fl & LC_INB_BIT);
         if (update_b && si) {
             // b_i follows the current surface; the contour set stays the frame's
             const uint32_t nf = direction_neg(C, i) ? (fl | LC_BNEG_BIT) : (fl & ~LC_BNEG_BIT);
             if (nf != fl) C.flags[i] = nf;
             fl = nf;
         }
-        bool masked = false;
         if (si && C.part_on) {
             // body-part mask: the silhouette term is off on another part's region
             const int px = min((int)floorf(uv.x + 0.5f), C.W - 1), py = min((int)floorf(uv.y + 0.5f), C.H - 1);
@@ -125,12 +186,54 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
             masked = lab != 255 && lab != (int)C.vpart[i];
             si = !masked;
         }
+    }
+    const bool need = i < C.N && (ph || si);
+    float4 I = make_float4(0.f, 0.f, 0.f, 0.f), Gx = I, Gy = I;
+    if constexpr (TMA) {
+        extern __shared__ unsigned char tma_raw[];
+        __shared__ __align__(8) uint64_t bar;
+        float4* patch = reinterpret_cast<float4*>(((uintptr_t)tma_raw + 127) & ~(uintptr_t)127);
+        float fx = 0.f, fy = 0.f;
+        int x0 = 0, y0 = 0;
+        bool staged = false;
+        if (need) {
+            const float u = fminf(fmaxf(uv.x, 0.f), (float)(C.W - 1));
+            const float w = fminf(fmaxf(uv.y, 0.f), (float)(C.H - 1));
+            x0 = (int)floorf(u);
+            y0 = (int)floorf(w);
+            fx = u - (float)x0;
+            fy = w - (float)y0;
+            staged = x0 >= 1 && y0 >= 1 && x0 + 2 <= C.W - 1 && y0 + 2 <= C.H - 1;
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, blockDim.x);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        float4* slot = patch + 16 * threadIdx.x;
+        if (staged) {
+            mbar_arrive_expect_tx(&bar, kTmaPatchBytes);
+            // x in floats: 4 per pixel, so the start is 16-byte aligned
+            tma_load_2d(slot, &tmap, 4 * (x0 - 1), y0 - 1, &bar);
+        } else {
+            mbar_arrive(&bar);
+        }
+        bool done = mbar_wait(&bar, 0, kTmaMaxTries);
+        if (!done) atomicOr(&C.sc->status, kDevErrWait);
+        if (staged && done)
+            sample_patch(slot, fx, fy, I, Gx, Gy);
+        else if (need)
+            sample_image(C.img, C.W, C.H, uv.x, uv.y, I, Gx, Gy);
+        // no copy may land after the CTA is gone
+        if (!done) done = mbar_wait(&bar, 0, kTmaMaxTries);
+    } else {
+        if (need) sample_image(C.img, C.W, C.H, uv.x, uv.y, I, Gx, Gy);
+    }
+    if (i < C.N) {
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         if (ph || si) {
-            float4 I, Gx, Gy;
-            sample_image(C.img, C.W, C.H, uv.x, uv.y, I, Gx, Gy);
             if (ph && C.pyr_levels > 0) {
                 // E_photo samples pyramid level j at u_j = (u - (d-1)/2) / d,
                 // its gradient scaled by 1/d to full-resolution pixels
@@ -199,11 +302,21 @@ __global__ void __launch_bounds__(kVertTile) linearize_kernel(const CapDesc* __r
     });
 }
 
+cudaError_t linearize_tma_init() {
+    return cudaFuncSetAttribute(linearize_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
+}
+
 void launch_linearize(const CapDesc* dC, const Tiles& T, bool update_b, int gn, cudaStream_t st) {
-    linearize_kernel<<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, update_b ? 1 : 0, gn);
+    // work lists span several captures: global loads (the tensor map is per capture)
+    static const CUtensorMap none{};
+    linearize_kernel<false><<<T.vert, kVertTile, 0, st>>>(dC, T.vert_items, update_b ? 1 : 0, gn, none);
 }
 void launch_linearize(const CapDesc* dC, const CapDesc& hC, bool update_b, int gn, cudaStream_t st) {
-    launch_linearize(dC, single_tiles(hC), update_b, gn, st);
+    const Tiles T = single_tiles(hC);
+    if (T.tma)
+        linearize_kernel<true><<<T.vert, kVertTile, kTmaSmem, st>>>(dC, nullptr, update_b ? 1 : 0, gn, hC.tmap_img);
+    else
+        launch_linearize(dC, T, update_b, gn, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,7 +31,8 @@ class lc_params(ctypes.Structure):
                 ("lambda_temporal", ctypes.c_float), ("lambda_anatomic", ctypes.c_float), ("sigma_c", ctypes.c_float),
                 ("pyr_levels", ctypes.c_int), ("pyr_ksize", ctypes.c_int * 3), ("pose_displacement", ctypes.c_int),
                 ("gn_block", ctypes.c_int),
-                ("graph_warp", ctypes.c_int)]
+                ("graph_warp", ctypes.c_int),
+                ("tma_taps", ctypes.c_int)]
 
 
 class lc_solve_stats(ctypes.Structure):

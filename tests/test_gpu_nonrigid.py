@@ -294,3 +294,33 @@ def test_empty_frame(tiny):
     s.mask = np.zeros_like(s.mask)
     stats = _e2e(s, "empty")
     assert stats["n_boundary_neg"] == 0
+
+
+@pytest.mark.parametrize("name", ["tiny", "body", "ragged"])
+def test_tma_staged_taps_are_bit_identical(name, tiny, body):
+    """The linearisation with TMA-staged image taps (lc_params.tma_taps)
+    against the global loads: residuals, per-vertex blocks and flags of one
+    linearisation at random parameters, and a whole solve, bit for bit
+    (the ragged capture leaves the image: its border vertices take the
+    global loads inside the staged kernel)."""
+    scene = {"tiny": tiny, "body": body}.get(name) or _ragged_scene(15, 13, 41, 4, side=90, shift=0.2)
+    ctxs = [_ctx(scene, tma_taps=0), _ctx(scene, tma_taps=1)]
+    n = scene.n_nodes
+    R, t = random_params(n, 91)
+    lins = []
+    for c in ctxs:
+        c.set_node_params(R.reshape(n, 9), t)
+        c.compute_visibility()
+        lins.append(c.eval_linearization())
+    for k in lins[0]:
+        assert np.array_equal(np.asarray(lins[0][k]), np.asarray(lins[1][k])), k
+    if name != "body":
+        outs = []
+        for c in ctxs:
+            c.set_node_params(None, None)
+            st = c.solve_nonrigid()
+            outs.append((st["e_total"], st["e_gn"], c.read_back()))
+        assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1]
+        assert np.array_equal(outs[0][2]["V"], outs[1][2]["V"])
+    for c in ctxs:
+        c.close()
