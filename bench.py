@@ -76,8 +76,8 @@ def parse():
                     help="body / tiny: Gauss-Newton steps at most while a frame works toward the oracle's energy")
     ap.add_argument("--gn-block", type=int, default=10,
                     help="body / tiny: Gauss-Newton steps per conditional graph block (0: unrolled)")
-    ap.add_argument("--tma-taps", action="store_true",
-                    help="body / tiny: stage each vertex's image taps with a TMA bulk-tensor copy")
+    ap.add_argument("--no-tma-taps", action="store_true",
+                    help="body / tiny: image taps by global loads instead of one TMA bulk-tensor copy per vertex")
     ap.add_argument("--profile-region", action="store_true",
                     help="start / stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--no-body-parts", action="store_true",
@@ -702,6 +702,45 @@ def oracle_targets(name, seeds, body_parts, procs):
         return pool.map(_frame_target_worker, [(name, s, body_parts) for s in seeds])
 
 
+def batched_jtj_roofline(ctxs, scenes, n_visible, dev, shape=None):
+    """The per-iteration J^T J p of several captures batched into one launch
+    pair (lc_batch_apply_jtj), L2 flushed before each of 20 timed calls:
+    algorithmic bytes over CUDA-event time against the measured HBM peak.
+    Runs one untimed batched solve first (its operands), which moves the
+    captures' node parameters."""
+    import torch
+    from paper_1810_02648_gb300 import Batch
+    b = Batch(ctxs)
+    if shape is not None:
+        b.set_shape(*shape)
+    b.solve(False, stats=False)
+    ext = torch.cuda.ExternalStream(b.stream_handle, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    b.apply_jtj(stage=True)
+    reps = 20
+    j0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    j1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for r in range(reps):
+        with torch.cuda.stream(ext):
+            flush.zero_()
+        j0[r].record(ext)
+        b.apply_jtj()
+        j1[r].record(ext)
+    torch.cuda.synchronize(dev)
+    ms = sum(x.elapsed_time(y) for x, y in zip(j0, j1)) / reps
+    nbytes = sum(jtj_algorithmic_bytes(sc, nv, len(c.read_graph()["edge_dst"]))
+                 for c, sc, nv in zip(ctxs, scenes, n_visible))
+    peak, peak_kind = measured_peaks()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    shp = b.shape()
+    b.close()
+    return {"kernel": f"jtj_vertex_kernel + jtj_node_kernel over {len(ctxs)} captures in one launch pair "
+                      f"(vertex block {shp['vert_block']}, {shp['node_warps']} nodes per block)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
+            "avg_launch_us": 1e3 * ms, "l2": "flushed before each timed call"}
+
+
 def run_frames(a):
     import numpy as np
     import torch
@@ -735,7 +774,7 @@ def run_frames(a):
         if body_parts:
             c.set_body_parts(sc.skeleton["bone_part"], sc.skeleton["torso_part"], 10)
         fr["target"] = fr["e_star"] * (1.0 + TARGET_TOL)
-        c.set_params(n_gn=a.gn_cap, target_energy=fr["target"], gn_block=a.gn_block, tma_taps=1 if a.tma_taps else 0)
+        c.set_params(n_gn=a.gn_cap, target_energy=fr["target"], gn_block=a.gn_block, tma_taps=0 if a.no_tma_taps else 1)
         ctxs.append(c)
     scene = frames[0]["scene"]
     has_pose = scene.skeleton is not None
@@ -875,6 +914,9 @@ def run_frames(a):
            + ((h0["j2"].numel() + h0["j3"].numel()) * 4 if has_pose else 0))
     d2h = (h0["R"].numel() + h0["t"].numel() + h0["V"].numel() + (h0["P"].numel() if has_pose else 0)) * 4
 
+    # the same captures' J^T J p batched into one launch pair (the batched
+    # product of the scope; untimed solve first, after the timed region)
+    roof_batched = batched_jtj_roofline(ctxs, [fr["scene"] for fr in frames], [p["n_visible"] for p in per], dev)
     if rank != 0:
         for c in ctxs:
             c.close()
@@ -895,7 +937,7 @@ def run_frames(a):
                        f"({scene.n_gn} GN x {scene.n_pcg} PCG) within {TARGET_TOL:g}, at most {a.gn_cap} GN steps"
                        + ("; body-part mask of the silhouette term" if body_parts else ""))
     cfg.update(frames=len(frames), gn_cap=a.gn_cap, gn_block=a.gn_block, target_tol=TARGET_TOL, body_parts=body_parts,
-               tma_taps=bool(a.tma_taps))
+               tma_taps=not a.no_tma_taps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
@@ -916,6 +958,7 @@ def run_frames(a):
                      "note": "the capture's working set (~0.3 MB per J^T J p) stays on chip across the PCG "
                              "iterations; the kernel is bound by its per-iteration synchronisation and the "
                              "compensated-pair arithmetic, so the HBM fraction is low by construction"},
+        "roofline_batched": roof_batched,
         "phases": phases,
         "solve": {"frames_reached": n_reached, "frames": len(per),
                   "gn_steps_mean": statistics.mean(p["gn_steps"] for p in per),
