@@ -557,7 +557,11 @@ lc_status lc_batch_step(lc_batch *batch, lc_mlp *mlp, unsigned flags, lc_solve_s
  *
  * Network: x = (f - mu) / sigma (per feature), h1 = relu(x W1 + b1),
  * h2 = relu(h1 W2 + b2), y = (h2 W3 + b3) * s_out (per output), sizes
- * 64 -> 256 -> 256 -> 6;
+ * 64 -> 256 -> 256 -> 6; the contractions run on the tcgen05 tensor cores
+ * (one CTA per 128 x 256 tile, shared-memory operands, tensor-memory
+ * accumulator; a bounded wait that runs out is reported as LC_ERR_TIMEOUT by
+ * the next synchronising lc_mlp_* call) or, selected by lc_mlp_set_gemm, on
+ * mma.sync;
  * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
  * master parameters.  Parameter vector (LC_MLP_PARAMS floats): W1 row-major
  * 64 x 256, b1 256, W2 256 x 256, b2 256, W3 256 x 6, b3 6.  Loss over M
@@ -584,6 +588,12 @@ lc_status lc_mlp_destroy(lc_mlp *mlp);
 const char *lc_mlp_last_error(const lc_mlp *mlp);
 /* Current FP32 parameters (LC_MLP_PARAMS).  Synchronises. */
 lc_status lc_mlp_get_params(lc_mlp *mlp, float *params);
+/* Tensor-core path of the network's contractions: LC_GEMM_TCGEN05 (default)
+ * or LC_GEMM_MMA_SYNC; both accumulate in FP32 (the order of the sums
+ * differs).  Synchronises. */
+#define LC_GEMM_TCGEN05 0
+#define LC_GEMM_MMA_SYNC 1
+lc_status lc_mlp_set_gemm(lc_mlp *mlp, int kind);
 /* The network's input normalisation mu / sigma (64 each) and output scale
  * s_out (6; 1 after lc_mlp_create).  Each pointer is nullable (that part is
  * left as is or not read) and may be host or device.  Synchronises. */

@@ -118,6 +118,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const bf16* __restrict__
         }
 }
 
+// tcgen05 GEMM (gemm_tc05.cu)
+cudaError_t gemm_bf16_tc05(bool at, bool bt, const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, int M,
+                           int N, int K, float* ws, size_t ws_floats, int* err, cudaStream_t st);
+
 void gemm_bf16(bool at, bool bt, const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, int M, int N,
                int K, cudaStream_t st) {
     const dim3 grid((N + kGN - 1) / kGN, (M + kGM - 1) / kGM);
@@ -523,6 +527,11 @@ struct lc_mlp {
     float *Z = nullptr, *Y = nullptr, *dY = nullptr, *Fin = nullptr, *Tin = nullptr;
     double *part = nullptr, *loss = nullptr;
     int* idx = nullptr;
+    // contractions on tcgen05 (0) or mma.sync (1); gerr: a tcgen05 wait ran out
+    int gemm_kind = 0;
+    int* gerr = nullptr;
+    float* ws = nullptr;                       // split-K slices of the tcgen05 GEMM
+    static constexpr size_t kWsFloats = size_t(1) << 20;
     std::vector<void*> owned;
 
     lc_status fail(lc_status s, const char* m) {
@@ -570,14 +579,21 @@ struct lc_mlp {
         ++gen;
         return LC_OK;
     }
+    void gemm(bool at, bool bt, const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, int M, int N, int K,
+              cudaStream_t st) {
+        if (gemm_kind == 0)
+            gemm_bf16_tc05(at, bt, A, lda, B, ldb, C, ldc, M, N, K, ws, kWsFloats, gerr, st);
+        else
+            gemm_bf16(at, bt, A, lda, B, ldb, C, ldc, M, N, K, st);
+    }
     void refresh_weights(cudaStream_t st) { weights_bf16_kernel<<<(kDH * kDH + 255) / 256, 256, 0, st>>>(theta, W1, W2, W3); }
     // forward on rows already normalised into X; output Y (FP32, M x 6)
     void forward(int M, cudaStream_t st) {
-        gemm_bf16(false, false, X, kDIn, W1, kDH, Z, kDH, M, kDH, kDIn, st);
+        gemm(false, false, X, kDIn, W1, kDH, Z, kDH, M, kDH, kDIn, st);
         bias_relu_kernel<<<(unsigned)(((size_t)M * kDH + 255) / 256), 256, 0, st>>>(Z, theta + kOffB1, H1, M, kDH);
-        gemm_bf16(false, false, H1, kDH, W2, kDH, Z, kDH, M, kDH, kDH, st);
+        gemm(false, false, H1, kDH, W2, kDH, Z, kDH, M, kDH, kDH, st);
         bias_relu_kernel<<<(unsigned)(((size_t)M * kDH + 255) / 256), 256, 0, st>>>(Z, theta + kOffB2, H2, M, kDH);
-        gemm_bf16(false, false, H2, kDH, W3, kDOut, Z, kDOut, M, kDOut, kDH, st);
+        gemm(false, false, H2, kDH, W3, kDOut, Z, kDOut, M, kDOut, kDH, st);
         out_bias_kernel<<<(M * kDOut + 255) / 256, 256, 0, st>>>(Z, theta + kOffB3, s_out, Y, M);
     }
     // loss and parameter gradient for targets T (FP32, M x 6) after forward
@@ -587,17 +603,17 @@ struct lc_mlp {
         loss_total_kernel<<<1, 32, 0, st>>>(part, lb, M, loss);
         const size_t nh = (size_t)M * kDH;
         // layer 3
-        gemm_bf16(true, false, H2, kDH, dYb, kDOut, grad + kOffW3, kDOut, kDH, kDOut, M, st);
+        gemm(true, false, H2, kDH, dYb, kDOut, grad + kOffW3, kDOut, kDH, kDOut, M, st);
         colsum_kernel<float><<<kDOut, 256, 0, st>>>(dY, M, kDOut, grad + kOffB3);
-        gemm_bf16(false, true, dYb, kDOut, W3, kDOut, Z, kDH, M, kDH, kDOut, st);   // dH2 = dY W3^T
+        gemm(false, true, dYb, kDOut, W3, kDOut, Z, kDH, M, kDH, kDOut, st);   // dH2 = dY W3^T
         relu_back_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, st>>>(Z, H2, dZ2, nh);
         // layer 2
-        gemm_bf16(true, false, H1, kDH, dZ2, kDH, grad + kOffW2, kDH, kDH, kDH, M, st);
+        gemm(true, false, H1, kDH, dZ2, kDH, grad + kOffW2, kDH, kDH, kDH, M, st);
         colsum_kernel<bf16><<<kDH, 256, 0, st>>>(dZ2, M, kDH, grad + kOffB2);
-        gemm_bf16(false, true, dZ2, kDH, W2, kDH, Z, kDH, M, kDH, kDH, st);        // dH1 = dZ2 W2^T
+        gemm(false, true, dZ2, kDH, W2, kDH, Z, kDH, M, kDH, kDH, st);        // dH1 = dZ2 W2^T
         relu_back_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, st>>>(Z, H1, dZ1, nh);
         // layer 1
-        gemm_bf16(true, false, X, kDIn, dZ1, kDH, grad + kOffW1, kDH, kDIn, kDH, M, st);
+        gemm(true, false, X, kDIn, dZ1, kDH, grad + kOffW1, kDH, kDIn, kDH, M, st);
         colsum_kernel<bf16><<<kDH, 256, 0, st>>>(dZ1, M, kDH, grad + kOffB1);
     }
 };
@@ -632,6 +648,20 @@ static lc_status mlp_cuda(lc_mlp* m, cudaError_t e, const char* what) {
     return LC_ERR_CUDA;
 }
 
+// synchronise the network's stream; a tcgen05 wait that ran out since the
+// last check is reported (once) as LC_ERR_TIMEOUT
+static lc_status mlp_sync(lc_mlp* m, cudaStream_t st, const char* what) {
+    lc_status s = mlp_cuda(m, cudaStreamSynchronize(st), what);
+    if (s) return s;
+    int ge = 0;
+    if (m->gerr && cudaMemcpy(&ge, m->gerr, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && ge) {
+        cudaMemset(m->gerr, 0, sizeof(int));
+        m->err = std::string(what) + ": a bounded tensor-core wait ran out";
+        return LC_ERR_TIMEOUT;
+    }
+    return LC_OK;
+}
+
 static bool is_dev(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -664,7 +694,9 @@ extern "C" lc_status lc_mlp_create(lc_mlp** out, int device, const float* params
     m->W2 = (bf16*)m->alloc(sizeof(bf16) * kDH * kDH);
     m->W3 = (bf16*)m->alloc(sizeof(bf16) * kDH * kDOut);
     m->loss = (double*)m->alloc(sizeof(double));
-    if (!m->theta || !m->grad || !m->mom || !m->vel || !m->mu || !m->sigma || !m->s_out || !m->W1 || !m->W2 || !m->W3 || !m->loss) {
+    m->gerr = (int*)m->alloc(sizeof(int));
+    m->ws = (float*)m->alloc(sizeof(float) * lc_mlp::kWsFloats);
+    if (!m->theta || !m->grad || !m->mom || !m->vel || !m->mu || !m->sigma || !m->s_out || !m->W1 || !m->W2 || !m->W3 || !m->loss || !m->gerr || !m->ws) {
         lc_mlp_destroy(m);
         return LC_ERR_OOM;
     }
@@ -673,6 +705,7 @@ extern "C" lc_status lc_mlp_create(lc_mlp** out, int device, const float* params
     cudaMemcpy(m->mu, mu ? mu : zeros.data(), sizeof(float) * kDIn, cudaMemcpyDefault);
     cudaMemcpy(m->sigma, sigma ? sigma : ones.data(), sizeof(float) * kDIn, cudaMemcpyDefault);
     cudaMemcpy(m->s_out, ones.data(), sizeof(float) * kDOut, cudaMemcpyDefault);
+    cudaMemset(m->gerr, 0, sizeof(int));
     cudaMemset(m->mom, 0, sizeof(float) * kNParams);
     cudaMemset(m->vel, 0, sizeof(float) * kNParams);
     m->refresh_weights(m->stream);
@@ -702,6 +735,15 @@ extern "C" lc_status lc_mlp_get_params(lc_mlp* m, float* params) {
     cudaSetDevice(m->device);
     cudaStreamSynchronize(m->stream);
     return mlp_cuda(m, cudaMemcpy(params, m->theta, sizeof(float) * kNParams, cudaMemcpyDefault), "lc_mlp_get_params");
+}
+
+extern "C" lc_status lc_mlp_set_gemm(lc_mlp* m, int kind) {
+    if (!m || kind < LC_GEMM_TCGEN05 || kind > LC_GEMM_MMA_SYNC) return LC_ERR_ARG;
+    cudaSetDevice(m->device);
+    cudaStreamSynchronize(m->stream);
+    m->gemm_kind = kind;
+    ++m->gen;   // captured warm-start graphs hold the other kernels
+    return LC_OK;
 }
 
 extern "C" lc_status lc_mlp_set_scaling(lc_mlp* m, const float* mu, const float* sigma, const float* s_out) {
@@ -742,7 +784,7 @@ extern "C" lc_status lc_mlp_fit_scaling(lc_mlp* m, const float* F, const float* 
     column_moments_kernel<<<nb, 256, 0, st>>>(F, rows, kDIn, part);
     column_moments_kernel<<<nb, 256, 0, st>>>(T, rows, kDOut, partT);
     fit_scaling_kernel<<<1, 128, 0, st>>>(part, partT, F, T, nb, rows, m->mu, m->sigma, m->s_out);
-    lc_status s = mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_fit_scaling");
+    lc_status s = mlp_sync(m, st, "lc_mlp_fit_scaling");
     cudaFree(part);
     return s;
 }
@@ -762,7 +804,7 @@ extern "C" lc_status lc_mlp_forward(lc_mlp* m, const float* F, int M, float* Y) 
     normalise_kernel<<<(unsigned)(((size_t)M * kDIn + 255) / 256), 256, 0, st>>>(Fd, m->mu, m->sigma, m->X, M);
     m->forward(M, st);
     cudaMemcpyAsync(Y, m->Y, sizeof(float) * (size_t)M * kDOut, cudaMemcpyDefault, st);
-    return mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_forward");
+    return mlp_sync(m, st, "lc_mlp_forward");
 }
 
 // loss (1/M) sum ||y - t||^2 and its gradient with respect to the parameters
@@ -779,7 +821,7 @@ extern "C" lc_status lc_mlp_gradient(lc_mlp* m, const float* F, const float* T, 
     m->backward(m->Tin, M, st);
     if (grad) cudaMemcpyAsync(grad, m->grad, sizeof(float) * kNParams, cudaMemcpyDefault, st);
     if (loss) cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDefault, st);
-    return mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_gradient");
+    return mlp_sync(m, st, "lc_mlp_gradient");
 }
 
 // one Adam step on the rows idx[0..B) of (F, T), both device arrays
@@ -803,7 +845,7 @@ extern "C" lc_status lc_mlp_train_step(lc_mlp* m, const float* F, const float* T
     m->refresh_weights(st);
     if (loss) {
         cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDefault, st);
-        return mlp_cuda(m, cudaStreamSynchronize(st), "lc_mlp_train_step");
+        return mlp_sync(m, st, "lc_mlp_train_step");
     }
     return mlp_cuda(m, cudaGetLastError(), "lc_mlp_train_step");
 }

@@ -105,6 +105,7 @@ _SIGS = {
     "lc_mlp_last_error": [_P],
     "lc_mlp_get_params": [_P, _P],
     "lc_mlp_set_scaling": [_P, _P, _P, _P],
+    "lc_mlp_set_gemm": [_P, ctypes.c_int],
     "lc_mlp_get_scaling": [_P, _P, _P, _P],
     "lc_mlp_fit_scaling": [_P, _P, _P, ctypes.c_longlong],
     "lc_mlp_forward": [_P, _P, ctypes.c_int, _P],
@@ -588,6 +589,10 @@ class MLP:
         self._check(self._lib.lc_mlp_get_params(self.h, _ptr(out)))
         return out
 
+    def set_gemm(self, kind: int):
+        """GEMM_TCGEN05 (default) or GEMM_MMA_SYNC."""
+        self._check(self._lib.lc_mlp_set_gemm(self.h, int(kind)))
+
     def set_scaling(self, mu=None, sigma=None, s_out=None):
         keep = [_arr(a, np.float32) for a in (mu, sigma, s_out)]
         self._check(self._lib.lc_mlp_set_scaling(self.h, *[_ptr(a) for a in keep]))
@@ -625,6 +630,7 @@ class MLP:
 
 
 STEP_EULER_START, STEP_CARRY_GRAPH = 1, 2
+GEMM_TCGEN05, GEMM_MMA_SYNC = 0, 1
 BATCH_PCG_AUTO, BATCH_PCG_CLUSTER8, BATCH_PCG_CLUSTER16, BATCH_PCG_PER_ITERATION = 0, 1, 2, 3
 
 

@@ -71,11 +71,13 @@ def _blocks(v):
 S_OUT = np.array([0.02, 0.5, 1.0, 3e-3, 2.0, 7e-4], np.float32)
 
 
+@pytest.mark.parametrize("gemm", [0, 1], ids=["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("M,scaled", [(1, False), (37, False), (500, False), (2053, False), (500, True)])
-def test_forward_matches_oracle(M, scaled):
+def test_forward_matches_oracle(M, scaled, gemm):
     from paper_1810_02648_gb300 import MLP
     theta, mu, sigma, F, T = _net(1, M)
     net = MLP(0, theta, mu, sigma)
+    net.set_gemm(gemm)
     s_out = S_OUT if scaled else None
     if scaled:
         net.set_scaling(s_out=s_out)
@@ -87,20 +89,22 @@ def test_forward_matches_oracle(M, scaled):
     scale = np.abs(y64).max(0)
     d_em = (np.abs(y - y_em) / scale).max()
     d_64 = (np.abs(y_em - y64) / scale).max()
-    report(f"mlp_forward_{M}{'_scaled' if scaled else ''}", vs_emulation=d_em, emulation_vs_fp64=d_64)
+    report(f"mlp_forward_{M}{'_scaled' if scaled else ''}_g{gemm}", vs_emulation=d_em, emulation_vs_fp64=d_64)
     assert d_em <= 2e-3       # FP32 accumulation; rare BF16 tie flips
     assert d_64 <= 4e-2       # two BF16 activation layers + BF16 weights
     net.close()
 
 
-@pytest.mark.parametrize("M,scaled", [(64, False), (1000, False), (1000, True)])
-def test_gradient_matches_oracle(M, scaled):
+@pytest.mark.parametrize("gemm", [0, 1], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("M,scaled", [(64, False), (1000, False), (1000, True), (4096, False)])
+def test_gradient_matches_oracle(M, scaled, gemm):
     from paper_1810_02648_gb300 import MLP
     theta, mu, sigma, F, T = _net(2, M)
     s_out = S_OUT if scaled else None
     if scaled:
         T = (T * S_OUT).astype(np.float32)           # targets on the outputs' scales
     net = MLP(0, theta, mu, sigma)
+    net.set_gemm(gemm)
     if scaled:
         net.set_scaling(s_out=s_out)
     g, L = net.gradient(F, T)
@@ -112,7 +116,7 @@ def test_gradient_matches_oracle(M, scaled):
     errs = {}
     for name, a, b, c in zip(["W1", "b1", "W2", "b2", "W3", "b3"], _blocks(g), _blocks(g_em), _blocks(g64)):
         errs[name] = (np.linalg.norm(a - b) / np.linalg.norm(b), np.linalg.norm(b - c) / np.linalg.norm(c))
-    report(f"mlp_gradient_{M}{'_scaled' if scaled else ''}", loss_rel=abs(L - L_em) / L_em,
+    report(f"mlp_gradient_{M}{'_scaled' if scaled else ''}_g{gemm}", loss_rel=abs(L - L_em) / L_em,
            **{f"{k}_vs_em": v[0] for k, v in errs.items()}, **{f"{k}_em_vs_fp64": v[1] for k, v in errs.items()})
     assert abs(L - L_em) <= 1e-4 * L_em and abs(L_em - L64) <= 5e-2 * L64
     for name, (e_em, e_64) in errs.items():
