@@ -841,6 +841,50 @@ def run_frames(a):
         reached_steps *= world
     value = reached_steps / (total_ms * 1e-3)
 
+    # the same frames with every capture in flight at once: one context and
+    # stream per capture, each frame's solves enqueued round-robin (the
+    # GPU's throughput when independent captures share it)
+    concurrent = None
+    if not a.profile_region:
+        cstreams = [torch.cuda.Stream(device=dev) for _ in frames]
+        cctxs = []
+        for fr, cs in zip(frames, cstreams):
+            sc = fr["scene"]
+            c = Context(local, stream=cs)
+            setup_scene(c, sc)
+            if body_parts:
+                c.set_body_parts(sc.skeleton["bone_part"], sc.skeleton["torso_part"], 10)
+            c.set_params(n_gn=a.gn_cap, target_energy=fr["target"], gn_block=a.gn_block,
+                         tma_taps=0 if a.no_tma_taps else 1)
+            cctxs.append(c)
+        for c in cctxs:
+            step(c)
+        torch.cuda.synchronize(dev)
+        rounds = max(1, a.steps // len(cctxs))
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            c0.record(stream)
+        for cs in cstreams:
+            cs.wait_event(c0)
+        for r in range(rounds):
+            for c in cctxs:
+                step(c)
+        for cs in cstreams:
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            stream.wait_event(ev)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        c_ms = c0.elapsed_time(c1)
+        c_reached = rounds * sum(p["reached"] for p in per)
+        concurrent = {"value": c_reached / (c_ms * 1e-3), "unit": UNIT, "captures_in_flight": len(cctxs),
+                      "rounds": rounds, "ms": c_ms,
+                      "note": "the same frames, every capture on its own context and stream, all in flight at "
+                              "once (a 16-CTA cluster PCG per capture); one L2 flush before the timed region"}
+        for c in cctxs:
+            c.close()
+
     # per-phase device time of one pass over the frames
     for c in ctxs:
         c.set_profiling(True)
@@ -959,6 +1003,7 @@ def run_frames(a):
                              "iterations; the kernel is bound by its per-iteration synchronisation and the "
                              "compensated-pair arithmetic, so the HBM fraction is low by construction"},
         "roofline_batched": roof_batched,
+        "concurrent": concurrent,
         "phases": phases,
         "solve": {"frames_reached": n_reached, "frames": len(per),
                   "gn_steps_mean": statistics.mean(p["gn_steps"] for p in per),
