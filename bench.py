@@ -79,7 +79,8 @@ def parse():
     ap.add_argument("--no-tma-taps", action="store_true",
                     help="body / tiny: image taps by global loads instead of one TMA bulk-tensor copy per vertex")
     ap.add_argument("--profile-region", action="store_true",
-                    help="start / stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
+                    help="start / stop the CUDA profiler around the timed steps (batch: around the J^T J p timing) "
+                         "for ncu --profile-from-start off")
     ap.add_argument("--no-body-parts", action="store_true",
                     help="body: solve without the body-part mask of the silhouette term")
     # options of the per-frame path (Sec. 3.2-3.4), off in the default line
@@ -735,7 +736,7 @@ def batched_jtj_roofline(ctxs, scenes, n_visible, dev, shape=None):
     shp = b.shape()
     b.close()
     return {"kernel": f"jtj_vertex_kernel + jtj_node_kernel over {len(ctxs)} captures in one launch pair "
-                      f"(vertex block {shp['vert_block']}, {shp['node_warps']} nodes per block)",
+                      f"(vertex block {shp['vert_block']}, node block {shp['node_warps']} warps of 4 nodes)",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
             "avg_launch_us": 1e3 * ms, "l2": "flushed before each timed call"}
@@ -1108,6 +1109,9 @@ def run_batch(a):
     batch.apply_jtj(stage=True)      # operands of the final linearisation, untimed
     j0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     j1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    if a.profile_region:
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.start()
     for r in range(reps):
         with torch.cuda.stream(ext):
             flush.zero_()
@@ -1115,6 +1119,8 @@ def run_batch(a):
         batch.apply_jtj()
         j1[r].record(ext)
     torch.cuda.synchronize(dev)
+    if a.profile_region:
+        torch.cuda.profiler.stop()
     jtj_ms = sum(s.elapsed_time(e) for s, e in zip(j0, j1)) / reps
     jtj_bytes = 0
     verts = 0

@@ -477,11 +477,12 @@ lc_status lc_batch_autotune(lc_batch *batch, int reps, int *mode_out, float *ms_
 /* Launch shape of a batch: the PCG strategy (LC_BATCH_PCG_*) and, for the
  * captures that run the per-iteration J^T J p (not on a cluster), its
  * vertex-phase block (vert_block: 128, 256 or 512 vertices), its node-phase
- * block (node_warps: 8 or 16 nodes, one warp each) and the node phase's
- * entry rounds in flight per lane (node_unroll: 2, 4 or 8).  Under one PCG
- * strategy every shape gives bit-identical results: the vertex phase is
- * per vertex, each lane takes a node's entries in the same order, and p.A p
- * is summed per group of 8 nodes in the same tree.  lc_batch_set_shape
+ * block (node_warps: 4, 8 or 16 warps of 4 nodes, 8 lanes per node; default
+ * 4) and the node phase's entry rounds in flight per lane (node_unroll: 2, 4
+ * or 8).  Under one PCG strategy every shape gives bit-identical results:
+ * the vertex phase is per vertex, each lane of a node's group takes the
+ * node's entries in the same order, and p.A p is summed per group of 8
+ * nodes in the same tree.  lc_batch_set_shape
  * rebuilds the plan (LC_ERR_ARG for another value); lc_batch_get_shape
  * reads it. */
 typedef struct {

@@ -100,7 +100,7 @@ struct lc_batch {
     std::vector<BatchGroup> groups;   // captures on the cluster PCG
     int mode = LC_BATCH_PCG_AUTO;
     // launch shape of the per-iteration J^T J p (captures not on a cluster)
-    int jv_block = kVertTile, jn_warps = kNodeWarps, jn_unroll = 4;
+    int jv_block = kVertTile, jn_warps = kJtjNodeWarps, jn_unroll = 4;
     int first_multi = 0;              // first slot on the per-iteration / grid PCG
     int n_gn = 0, n_pcg = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -231,9 +231,9 @@ lc_status lc_batch::build() {
     const Fam fm[3] = {family(first_multi, count, vert), family(first_multi, count, node),
                        family(first_multi, count, vec)};
     // the J^T J p's own blocks at the batch's launch shape
-    const int vb = jv_block, nw = jn_warps;
+    const int vb = jv_block, nb = jn_warps * kJtjNodesPerWarp;
     auto jvert = [vb](const CapDesc& C) { return (C.N + vb - 1) / vb; };
-    auto jnode = [nw](const CapDesc& C) { return (C.n + nw - 1) / nw; };
+    auto jnode = [nb](const CapDesc& C) { return (C.n + nb - 1) / nb; };
     const Fam fj[4] = {family(0, count, jvert), family(0, count, jnode), family(first_multi, count, jvert),
                        family(first_multi, count, jnode)};
     if (cudaMalloc(&items, sizeof(WorkItem) * std::max<size_t>(w.size(), 1)) != cudaSuccess ||
@@ -260,6 +260,15 @@ lc_status lc_batch::build() {
         T->jn_warps = jn_warps;
         T->jn_unroll = jn_unroll;
     }
+    // the common K of a tile set's captures (0: mixed)
+    auto common_k = [&](int lo) {
+        int k = lo < count ? snap[lo].K : 0;
+        for (int j = lo; j < count; ++j)
+            if (snap[j].K != k) k = 0;
+        return k;
+    };
+    all.jk = common_k(0);
+    multi.jk = common_k(first_multi);
     all.jv = fj[0].n, all.jv_items = at(fj[0]);
     all.jn = fj[1].n, all.jn_items = at(fj[1]);
     multi.jv = fj[2].n, multi.jv_items = at(fj[2]);
@@ -717,7 +726,7 @@ extern "C" lc_status lc_batch_autotune_shapes(lc_batch* b, int reps, int use_cac
     }
     const int modes[4] = {LC_BATCH_PCG_AUTO, LC_BATCH_PCG_CLUSTER8, LC_BATCH_PCG_CLUSTER16,
                           LC_BATCH_PCG_PER_ITERATION};
-    const int vbs[3] = {128, 256, 512}, nws[2] = {kNodeWarps, 2 * kNodeWarps}, nus[3] = {2, 4, 8};
+    const int vbs[3] = {128, 256, 512}, nws[3] = {4, 8, 16}, nus[3] = {2, 4, 8};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -727,7 +736,7 @@ extern "C" lc_status lc_batch_autotune_shapes(lc_batch* b, int reps, int use_cac
     int tried = 0, rejected = 0;
     std::vector<unsigned char> ref, cur;
     for (int m : modes) {
-        lc_batch_shape sh{m, kVertTile, kNodeWarps, 4};
+        lc_batch_shape sh{m, kVertTile, kJtjNodeWarps, 4};
         if ((s = lc_batch_set_shape(b, &sh))) break;
         // shapes matter only where captures run the per-iteration J^T J p
         const bool any_multi = b->first_multi < (int)b->ctxs.size();

@@ -22,6 +22,11 @@ constexpr int kNodeTile = kNodeWarps;
 constexpr int kTriTile = 128;       // triangles per raster tile
 constexpr int kEdgeTile = 256;      // mesh edges per tile
 constexpr int kMaxK = 8;            // nodes per vertex
+constexpr int kJChunk = 128;        // vertex ids per compaction chunk of the per-iteration J^T J p
+constexpr int kJtjNodeLanes = 8;       // lanes per node in the node phase of the per-iteration J^T J p
+constexpr int kJtjNodesPerWarp = 32 / kJtjNodeLanes;
+constexpr int kJtjNodeWarps = 4;    // default warps per node-phase block (16 nodes)
+static_assert(kVertTile % kJChunk == 0, "vertex tiles hold whole compaction chunks");
 constexpr int kEdgeNN = 4;          // node-graph neighbours before symmetrising
 constexpr int kMaxExtraEdges = 60;  // symmetrised extra in-edges per node
 constexpr int kVecThreads = 256;    // nodes per PCG vector tile
@@ -130,7 +135,7 @@ struct CapDesc {
     float4* z_lo;
     float4* p_lo;
     float4* Ap_lo;
-    float4* q;               // per-vertex H_i dv_i scratch (N), high part
+    float4* q;               // per active vertex H_i dv_i scratch (N, by compact position), high part
     float4* q_lo;            // its low part
     // spatial node partition of the cluster PCG (kPcgLeaves leaves; a
     // cluster of cl CTAs gives CTA r the leaves r*L/cl .. (r+1)*L/cl - 1)
@@ -150,8 +155,18 @@ struct CapDesc {
     // local vertex of it binds to the node, or an owned edge ends there)
     const unsigned short* pcg_zdst[2];
     // operands of the per-iteration J^T J p, staged once per linearisation
-    float4* vA;              // N*K: (w_is R_k (v_i - g_k), w_is) per binding, zero for inactive vertices
-    float4* eA;              // N*K: the same per node -> vertex CSR entry
+    // with the inactive vertices left out: the active vertices of each chunk
+    // of kJChunk ids are packed, in id order, at the chunk's start (their
+    // compact positions), and the active entries of each node at the start
+    // of its CSR range
+    float4* vA;              // N*K: (w_is R_k (v_i - g_k), w_is) of compact position pos, slot s, at pos*K + s
+    int* vK;                 // N*K: the node of that binding
+    float4* vH;              // 2N: (h00, h01, h02, h11), (h12, h22, 0, 0) of compact position pos
+    int* vpos;               // N: compact position of vertex i, -1 when inactive
+    int* vcnt;               // ceil(N / kJChunk): active vertices per chunk
+    float4* eA;              // N*K: (c, w) of the node's active entries, vertex ascending
+    int* eV;                 // N*K: the compact positions of their vertices
+    int* ecnt;               // n: active entries per node
     float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)
     // per-vertex surface stage (unknowns V)
     int n_adj;               // directed one-ring pairs
@@ -421,13 +436,14 @@ struct Tiles {
     const WorkItem* node_items = nullptr;
     const WorkItem* vec_items = nullptr;
     // launch shape of the per-iteration J^T J p (launch_jtj): vertices per
-    // vertex-phase block, nodes (warps) per node-phase block and the node
-    // phase's entry rounds in flight, with their own work lists (jv / jn
-    // blocks); every shape gives bit-identical results
+    // vertex-phase block, warps per node-phase block (kJtjNodesPerWarp nodes
+    // each) and the node phase's entry rounds in flight, with their own work
+    // lists (jv / jn blocks); every shape gives bit-identical results
     int jv = 0, jn = 0;
     const WorkItem* jv_items = nullptr;
     const WorkItem* jn_items = nullptr;
-    int jv_block = kVertTile, jn_warps = kNodeWarps, jn_unroll = 4;
+    int jv_block = kVertTile, jn_warps = kJtjNodeWarps, jn_unroll = 4;
+    int jk = 0;   // the captures' common K (0: mixed), selects an unrolled vertex phase
     // linearisation with TMA-staged image taps (single-capture launches only:
     // the tensor map is a kernel parameter)
     bool tma = false;
@@ -441,7 +457,8 @@ inline Tiles single_tiles(const CapDesc& C) {
     t.node = C.node_tiles;
     t.vec = (C.n + kVecThreads - 1) / kVecThreads;
     t.jv = C.vert_tiles;
-    t.jn = C.node_tiles;
+    t.jn = (C.n + kJtjNodeWarps * kJtjNodesPerWarp - 1) / (kJtjNodeWarps * kJtjNodesPerWarp);
+    t.jk = C.K;
     t.tma = C.tma_taps && C.tma_ok;
     return t;
 }
@@ -492,9 +509,9 @@ void launch_jtj_stage(const CapDesc* dC, const Tiles& T, cudaStream_t st);
 // nullable: the low part is dropped); p / out null: each capture's own p and Ap
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const float4* p_lo, float4* out,
                 float4* out_lo, bool dot, cudaStream_t st);
-// K: the captures' common K selects an unrolled vertex phase (0: any K)
+// T.jk: the captures' common K selects an unrolled vertex phase (0: any K)
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
-                float4* out_lo, bool dot, cudaStream_t st, int K = 0);
+                float4* out_lo, bool dot, cudaStream_t st);
 // the launch shapes launch_jtj has kernels for
 bool jtj_shape_valid(int vert_block, int node_warps, int node_unroll);
 // dynamic shared memory of the TMA-staged linearisation (once per process)

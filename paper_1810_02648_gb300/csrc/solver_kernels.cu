@@ -428,27 +428,54 @@ void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only
 // binding, of every node -> vertex entry, and the rotated offsets of every
 // node edge do not change during the PCG, so they are staged once per
 // linearisation (the kernels below); the PCG's J^T J p then reads them
-// coalesced instead of gathering node rotations and positions, and skips
-// inactive vertices without touching them.  Bindings and entries are staged
-// by the same function, so the forward and transposed products use the same
-// bits.
+// coalesced instead of gathering node rotations and positions.  Only active
+// vertices (those with a data row) enter the product, so the staging packs
+// them: per chunk of kJChunk vertex ids, the active ones in id order at the
+// chunk's start with their coefficients, nodes and H block side by side, and
+// per node its active entries at the start of its CSR range, in vertex
+// order, with the vertex's compact position.  The product then reads no byte
+// of an inactive vertex.  Bindings and entries are staged by the same
+// function, so the forward and transposed products use the same bits.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) jtj_stage_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                       const WorkItem* __restrict__ items) {
+    constexpr int kWarps = kVertTile / 32, kChunkWarps = kJChunk / 32;
+    __shared__ int wcount[kWarps];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
     if (C.sc->gn_stop) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = tile * kVertTile + threadIdx.x;
+    const bool active = i < C.N && C.ev[i].w != 0.f;
+    const unsigned bal = __ballot_sync(0xffffffffu, active);
+    if (lane == 0) wcount[w] = __popc(bal);
+    __syncthreads();
+    // rank among the chunk's active vertices: earlier warps of the chunk,
+    // then earlier lanes of this warp
+    const int w0 = w - w % kChunkWarps;
+    int rank = __popc(bal & ((1u << lane) - 1u));
+    for (int u = w0; u < w; ++u) rank += wcount[u];
+    const int chunk = i / kJChunk;
+    if (w == w0 && lane == 0 && chunk * kJChunk < C.N) {
+        int total = 0;
+        for (int u = w0; u < w0 + kChunkWarps; ++u) total += wcount[u];
+        C.vcnt[chunk] = total;
+    }
     if (i >= C.N) return;
-    const bool active = C.ev[i].w != 0.f;
+    const int pos = chunk * kJChunk + rank;
+    C.vpos[i] = active ? pos : -1;
+    if (!active) return;
     const float4 v = C.base[i];
     const int K = C.K;
     for (int s = 0; s < K; ++s) {
         const size_t e = (size_t)i * K + s;
         const int k = C.bind_idx[e];
-        C.vA[e] = active ? staged_coef(C.node_R, k, v, C.node_g[k], C.bind_w[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        C.vA[(size_t)pos * K + s] = staged_coef(C.node_R, k, v, C.node_g[k], C.bind_w[e]);
+        C.vK[(size_t)pos * K + s] = k;
     }
+    C.vH[2 * pos] = C.HA[i];
+    C.vH[2 * pos + 1] = C.HB[i];
 }
 
 __global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const CapDesc* __restrict__ caps,
@@ -461,12 +488,27 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const C
     const int k = tile * kNodeTile + (threadIdx.x >> 5);
     if (k >= C.n) return;
     const float4 g = C.node_g[k];
-    for (int j = C.ent_off[k] + lane; j < C.ent_off[k + 1]; j += 32) {
-        const int2 en = C.ent[j];
-        const bool active = C.ev[en.x].w != 0.f;
-        C.eA[j] = active ? staged_coef(C.node_R, k, C.base[en.x], g, __int_as_float(en.y))
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the node's active entries packed in CSR order (runs after the vertex
+    // stage, whose compact positions it reads)
+    const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
+    int cnt = 0;
+    for (int jb = e0; jb < e1; jb += 32) {
+        const int j = jb + lane;
+        int2 en = make_int2(0, 0);
+        int pos = -1;
+        if (j < e1) {
+            en = C.ent[j];
+            pos = C.vpos[en.x];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pos >= 0);
+        if (pos >= 0) {
+            const int d = e0 + cnt + __popc(bal & ((1u << lane) - 1u));
+            C.eA[d] = staged_coef(C.node_R, k, C.base[en.x], g, __int_as_float(en.y));
+            C.eV[d] = pos;
+        }
+        cnt += __popc(bal);
     }
+    if (lane == 0) C.ecnt[k] = cnt;
     for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32) {
         const int l = C.edge_dst[j];
         const float4 gl = C.node_g[l];
@@ -495,34 +537,50 @@ __global__ void __launch_bounds__(VB) jtj_vertex_kernel(const CapDesc* __restric
     // null: the capture's PCG direction (both parts)
     const float4* __restrict__ p = p_in ? p_in : C.p;
     const float4* __restrict__ p_lo = p_in ? p_lo_in : C.p_lo;
-    const int i = tile * VB + threadIdx.x;
-    if (i >= C.N) return;
+    // thread -> (chunk, rank): a block covers VB / kJChunk whole chunks, and
+    // only the chunk's active vertices (packed at its start) have work
+    static_assert(VB % kJChunk == 0, "vertex blocks hold whole compaction chunks");
+    const int chunk = tile * (VB / kJChunk) + threadIdx.x / kJChunk;
+    if (chunk * kJChunk >= C.N) return;
+    const int r = threadIdx.x % kJChunk;
+    if (r >= C.vcnt[chunk]) return;
+    const int pos = chunk * kJChunk + r;
     const int K = C.K;
-    const float4* __restrict__ A = C.vA + (size_t)i * K;
-    if (A[0].w == 0.f) return;   // inactive vertex: no entry of the node phase reads its q
+    const float4* __restrict__ A = C.vA + (size_t)pos * K;
+    const int* __restrict__ nk = C.vK + (size_t)pos * K;
     constexpr int KM = KT > 0 ? KT : kMaxK;
     const int kk = KT > 0 ? KT : K;
     // all K (coefficient, node) pairs loaded before the p gathers, so the
     // loads of the slots are in flight together
     float4 a[KM];
     int k[KM];
+    if constexpr (KT == 4 || KT == 8) {
 #pragma unroll
-    for (int s = 0; s < KM; ++s)
-        if (s < kk) {
-            a[s] = A[s];
-            k[s] = C.bind_idx[(size_t)i * K + s];
+        for (int s = 0; s < KT; s += 4) {
+            const int4 k4 = *reinterpret_cast<const int4*>(nk + s);
+            k[s] = k4.x; k[s + 1] = k4.y; k[s + 2] = k4.z; k[s + 3] = k4.w;
         }
+#pragma unroll
+        for (int s = 0; s < KT; ++s) a[s] = A[s];
+    } else {
+#pragma unroll
+        for (int s = 0; s < KM; ++s)
+            if (s < kk) {
+                a[s] = A[s];
+                k[s] = nk[s];
+            }
+    }
+    const float4 HA = C.vH[2 * pos], HB = C.vH[2 * pos + 1];
     fp2acc dv[3];
 #pragma unroll
     for (int s = 0; s < KM; ++s)
         if (s < kk) jtj_slot(a[s], node_pair44(p, p_lo, k[s]), dv);
-    const float4 HA = C.HA[i], HB = C.HB[i];
     const float h[6] = {HA.x, HA.y, HA.z, HA.w, HB.x, HB.y};
     const fp2 d[3] = {dv[0].get(), dv[1].get(), dv[2].get()};
     fp2 q[3];
     jtj_block(h, d, q);
-    C.q[i] = make_float4(q[0].h, q[1].h, q[2].h, 1.f);
-    C.q_lo[i] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
+    C.q[pos] = make_float4(q[0].h, q[1].h, q[2].h, 1.f);
+    C.q_lo[pos] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
 }
 
 // the p . A p total of a capture: alpha = r.z / p.A p as a pair division, or
@@ -540,9 +598,26 @@ __device__ __forceinline__ void dot_alpha(const CapDesc& C, double pAp) {
     }
 }
 
-// W warps (nodes) per block, U rounds of a node's entries in flight per lane.
-// p . A p is summed per group of kNodeWarps nodes in the same tree for any W
-// (W = kNodeWarps or 2 kNodeWarps), so every shape gives the same bits.
+// Sum of a pair over an aligned group of G lanes (fixed xor-shuffle tree;
+// every lane of the group gets the total).  Called by all 32 lanes.
+template <int G>
+__device__ __forceinline__ fp2 fp2_group_sum(fp2 v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        fp2 w;
+        w.h = __shfl_xor_sync(0xffffffffu, v.h, o);
+        w.l = __shfl_xor_sync(0xffffffffu, v.l, o);
+        v = fp2_add(v, w);
+    }
+    return v;
+}
+
+// W warps per block, kJtjNodeLanes lanes per node (kJtjNodesPerWarp nodes per
+// warp), U rounds of a node's entries in flight per lane.  Lane l of a
+// node's group takes its active entries l, l + kJtjNodeLanes, ... and edges
+// likewise; the group's sums use a fixed shuffle tree, and p . A p is summed
+// per group of kNodeTile consecutive nodes in one fixed tree, so every
+// launch shape gives the same bits.
 template <int W, int U>
 __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
                                                           const WorkItem* __restrict__ items,
@@ -550,8 +625,11 @@ __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restr
                                                           const float4* __restrict__ p_lo_in,
                                                           float4* __restrict__ out_in,
                                                           float4* __restrict__ out_lo_in, int dot) {
-    static_assert(W == kNodeWarps || W == 2 * kNodeWarps, "node block of one or two partial groups");
-    __shared__ float2 sh[W];
+    constexpr int NPB = W * kJtjNodesPerWarp;   // nodes per block
+    constexpr int NG = NPB / kNodeTile;      // p . A p partial groups per block
+    static_assert(NPB % kNodeTile == 0 && NG <= W, "whole partial groups, one warp to sum each");
+    __shared__ float2 sh[NPB];
+    __shared__ float2 gs[NG];
     int cap, tile;
     decode(items, cap, tile);
     const CapDesc& C = caps[cap];
@@ -561,85 +639,87 @@ __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restr
     const float4* __restrict__ p_lo = p_in ? p_lo_in : C.p_lo;
     float4* __restrict__ out = out_in ? out_in : C.Ap;
     float4* __restrict__ out_lo = out_in ? out_lo_in : C.Ap_lo;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int k = tile * W + w;
-    fp2acc pap;
-    if (k < C.n) {
-        fp2acc acc[6];
-        // U rounds of the node's entries at a time: their loads are issued
-        // together before any result is used (each lane still takes entries
-        // lane, lane + 32, ... in order)
-        const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
-        for (int jb = e0 + lane; jb < e1; jb += 32 * U) {
-            float4 a[U];
-            int vi[U];
+    const int g = threadIdx.x / kJtjNodeLanes, sl = threadIdx.x % kJtjNodeLanes;
+    const int k = tile * NPB + g;
+    const bool has = k < C.n;
+    // every lane runs the group sums below; a node past the end has no work
+    int e0 = 0, e1 = 0, d0 = 0, d1 = 0;
+    if (has) {
+        e0 = C.ent_off[k];
+        e1 = e0 + C.ecnt[k];   // the node's active entries only (packed at the start of its range)
+        d0 = C.edge_off[k];
+        d1 = C.edge_off[k + 1];
+    }
+    fp2acc acc[6];
+    // U rounds of the node's entries at a time: their loads are issued
+    // together before any result is used
+    for (int jb = e0 + sl; jb < e1; jb += kJtjNodeLanes * U) {
+        float4 a[U];
+        int vi[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = jb + 32 * u;
-                a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                vi[u] = j < e1 ? C.ent[j].x : 0;
-            }
-            float4 qh[U], ql[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool on = a[u].w != 0.f;
-                qh[u] = on ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-                ql[u] = on ? C.q_lo[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (a[u].w == 0.f) continue;
-                const fp2 q[3] = {{qh[u].x, ql[u].x}, {qh[u].y, ql[u].y}, {qh[u].z, ql[u].z}};
-                jtj_entry(a[u], q, acc);
-            }
+        for (int u = 0; u < U; ++u) {
+            const int j = jb + kJtjNodeLanes * u;
+            a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            vi[u] = j < e1 ? C.eV[j] : -1;
         }
-        const NodeP pk = node_pair44(p, p_lo, k);
-        for (int j = C.edge_off[k] + lane; j < C.edge_off[k + 1]; j += 32)
-            jtj_edge(C.dB[2 * j], C.dB[2 * j + 1], pk, node_pair44(p, p_lo, C.edge_dst[j]), acc);
-        fp2 t[6];
+        float4 qh[U], ql[U];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) t[c] = fp2_warp_sum(acc[c].get());
-        if (lane == 0) {
-            out[2 * k] = make_float4(t[0].h, t[1].h, t[2].h, 0.f);
-            out[2 * k + 1] = make_float4(t[3].h, t[4].h, t[5].h, 0.f);
-            if (out_lo) {
-                out_lo[2 * k] = make_float4(t[0].l, t[1].l, t[2].l, 0.f);
-                out_lo[2 * k + 1] = make_float4(t[3].l, t[4].l, t[5].l, 0.f);
-            }
-            if (dot) {
-                pap.mac(pk.w[0], t[0]); pap.mac(pk.w[1], t[1]); pap.mac(pk.w[2], t[2]);
-                pap.mac(pk.t[0], t[3]); pap.mac(pk.t[1], t[4]); pap.mac(pk.t[2], t[5]);
-            }
+        for (int u = 0; u < U; ++u) {
+            const bool on = vi[u] >= 0;
+            qh[u] = on ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ql[u] = on ? C.q_lo[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (vi[u] < 0) continue;
+            const fp2 q[3] = {{qh[u].x, ql[u].x}, {qh[u].y, ql[u].y}, {qh[u].z, ql[u].z}};
+            jtj_entry(a[u], q, acc);
+        }
+    }
+    NodeP pk{};
+    if (has) pk = node_pair44(p, p_lo, k);
+    for (int j = d0 + sl; j < d1; j += kJtjNodeLanes)
+        jtj_edge(C.dB[2 * j], C.dB[2 * j + 1], pk, node_pair44(p, p_lo, C.edge_dst[j]), acc);
+    fp2 t[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = fp2_group_sum<kJtjNodeLanes>(acc[c].get());
+    fp2 pap_k = {0.f, 0.f};
+    if (has && sl == 0) {
+        out[2 * k] = make_float4(t[0].h, t[1].h, t[2].h, 0.f);
+        out[2 * k + 1] = make_float4(t[3].h, t[4].h, t[5].h, 0.f);
+        if (out_lo) {
+            out_lo[2 * k] = make_float4(t[0].l, t[1].l, t[2].l, 0.f);
+            out_lo[2 * k + 1] = make_float4(t[3].l, t[4].l, t[5].l, 0.f);
+        }
+        if (dot) {
+            fp2acc pap;
+            pap.mac(pk.w[0], t[0]); pap.mac(pk.w[1], t[1]); pap.mac(pk.w[2], t[2]);
+            pap.mac(pk.t[0], t[3]); pap.mac(pk.t[1], t[4]); pap.mac(pk.t[2], t[5]);
+            pap_k = pap.get();
         }
     }
     if (!dot) return;
-    if constexpr (W == kNodeWarps) {
-        const fp2 tot = block_sum_fp2<kNodeWarps>(pap.get(), sh);
-        const double part[1] = {fp2_to_double(tot)};
-        reduce_partials<1>(C, CNT_DOT, tile, C.node_tiles, part,
-                           [&](const double (&sum)[1]) { dot_alpha(C, sum[0]); });
-    } else {
-        // two groups of kNodeWarps nodes: warp g sums group g's warp totals
-        // in its first kNodeWarps lanes, the tree block_sum_fp2 uses
-        __shared__ float2 gs[2];
-        const fp2 v = fp2_warp_sum(pap.get());
-        if (lane == 0) sh[w] = make_float2(v.h, v.l);
-        __syncthreads();
-        if (w < 2) {
-            const float2 a = lane < kNodeWarps ? sh[w * kNodeWarps + lane] : make_float2(0.f, 0.f);
-            const fp2 g = fp2_warp_sum(fp2{a.x, a.y});
-            if (lane == 0) gs[w] = make_float2(g.h, g.l);
-        }
-        __syncthreads();
-        const int t0 = 2 * tile;
-        const int m = min(2, C.node_tiles - t0);
-        const double part[2][1] = {{fp2_to_double(fp2{gs[0].x, gs[0].y})}, {fp2_to_double(fp2{gs[1].x, gs[1].y})}};
-        if (!publish_partials<1>(C, CNT_DOT, t0, m, C.node_tiles, part, C.part)) return;
-        if (threadIdx.x >= 32) return;
-        double tot[1];
-        sum_partials_warp<1>(C.part, C.node_tiles, tot);
-        if (threadIdx.x == 0) dot_alpha(C, tot[0]);
+    // per group of kNodeTile nodes: warp r sums group r's node terms in its
+    // first kNodeTile lanes
+    if (sl == 0) sh[g] = make_float2(pap_k.h, pap_k.l);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < NG) {
+        const float2 v = lane < kNodeTile ? sh[w * kNodeTile + lane] : make_float2(0.f, 0.f);
+        const fp2 s = fp2_warp_sum(fp2{v.x, v.y});
+        if (lane == 0) gs[w] = make_float2(s.h, s.l);
     }
+    __syncthreads();
+    const int t0 = tile * NG;
+    const int m = min(NG, C.node_tiles - t0);
+    double part[NG][1];
+#pragma unroll
+    for (int r = 0; r < NG; ++r) part[r][0] = fp2_to_double(fp2{gs[r].x, gs[r].y});
+    if (!publish_partials<1>(C, CNT_DOT, t0, m, C.node_tiles, part, C.part)) return;
+    if (threadIdx.x >= 32) return;
+    double tot[1];
+    sum_partials_warp<1>(C.part, C.node_tiles, tot);
+    if (threadIdx.x == 0) dot_alpha(C, tot[0]);
 }
 
 template <int VB>
@@ -667,26 +747,28 @@ static void launch_jtj_node(const CapDesc* dC, const Tiles& T, const float4* p, 
 
 bool jtj_shape_valid(int vert_block, int node_warps, int node_unroll) {
     return (vert_block == 128 || vert_block == 256 || vert_block == 512) &&
-           (node_warps == kNodeWarps || node_warps == 2 * kNodeWarps) &&
+           (node_warps == 4 || node_warps == 8 || node_warps == 16) &&
            (node_unroll == 2 || node_unroll == 4 || node_unroll == 8);
 }
 
 void launch_jtj(const CapDesc* dC, const Tiles& T, const float4* p, const float4* p_lo, float4* out,
-                float4* out_lo, bool dot, cudaStream_t st, int K) {
+                float4* out_lo, bool dot, cudaStream_t st) {
     if (T.jv_block == 128)
-        launch_jtj_vertex<128>(dC, T, p, p_lo, dot, st, K);
+        launch_jtj_vertex<128>(dC, T, p, p_lo, dot, st, T.jk);
     else if (T.jv_block == 512)
-        launch_jtj_vertex<512>(dC, T, p, p_lo, dot, st, K);
+        launch_jtj_vertex<512>(dC, T, p, p_lo, dot, st, T.jk);
     else
-        launch_jtj_vertex<256>(dC, T, p, p_lo, dot, st, K);
-    if (T.jn_warps == 2 * kNodeWarps)
-        launch_jtj_node<2 * kNodeWarps>(dC, T, p, p_lo, out, out_lo, dot, st);
+        launch_jtj_vertex<256>(dC, T, p, p_lo, dot, st, T.jk);
+    if (T.jn_warps == 16)
+        launch_jtj_node<16>(dC, T, p, p_lo, out, out_lo, dot, st);
+    else if (T.jn_warps == 8)
+        launch_jtj_node<8>(dC, T, p, p_lo, out, out_lo, dot, st);
     else
-        launch_jtj_node<kNodeWarps>(dC, T, p, p_lo, out, out_lo, dot, st);
+        launch_jtj_node<4>(dC, T, p, p_lo, out, out_lo, dot, st);
 }
 void launch_jtj(const CapDesc* dC, const CapDesc& hC, const float4* p, const float4* p_lo, float4* out,
                 float4* out_lo, bool dot, cudaStream_t st) {
-    launch_jtj(dC, single_tiles(hC), p, p_lo, out, out_lo, dot, st, hC.K);
+    launch_jtj(dC, single_tiles(hC), p, p_lo, out, out_lo, dot, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -719,7 +719,7 @@ class Batch:
         self._check(self._lib.lc_batch_step(self.h, h, flags, arr))
         return [a.to_dict() for a in arr]
 
-    def set_shape(self, pcg_mode: int, vert_block: int = 256, node_warps: int = 8, node_unroll: int = 4):
+    def set_shape(self, pcg_mode: int, vert_block: int = 256, node_warps: int = 4, node_unroll: int = 4):
         sh = lc_batch_shape(pcg_mode, vert_block, node_warps, node_unroll)
         self._check(self._lib.lc_batch_set_shape(self.h, ctypes.byref(sh)))
 

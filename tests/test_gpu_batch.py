@@ -170,7 +170,7 @@ def test_batch_members_with_body_part_masks():
 @pytest.mark.parametrize("shape", [(128, 8, 2), (512, 16, 8), (256, 16, 4), (128, 16, 2)])
 def test_jtj_launch_shapes_are_bit_identical(scenes, shape):
     """The per-iteration J^T J p at another launch shape (vertex block,
-    nodes per node block, entry rounds in flight) gives the same bits as the
+    warps of four nodes per node block, entry rounds in flight) gives the same bits as the
     default shape: node parameters, vertices, flags, energies."""
     from paper_1810_02648_gb300 import Batch
     from paper_1810_02648_gb300.livecap import BATCH_PCG_PER_ITERATION
