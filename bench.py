@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--no-tma-taps", action="store_true",
                     help="body / tiny: image taps by global loads instead of one TMA bulk-tensor copy per vertex")
     ap.add_argument("--profile-region", action="store_true",
-                    help="start / stop the CUDA profiler around the timed steps (batch: around the J^T J p timing) "
+                    help="start / stop the CUDA profiler around the timed steps (batch, stream: around the J^T J p timing) "
                          "for ncu --profile-from-start off")
     ap.add_argument("--no-body-parts", action="store_true",
                     help="body: solve without the body-part mask of the silhouette term")
@@ -1432,6 +1432,9 @@ def run_stream(a):
     batch.apply_jtj(stage=True)
     j0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     j1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    if a.profile_region:
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.start()
     for r in range(reps):
         with torch.cuda.stream(ext):
             flush.zero_()
@@ -1439,6 +1442,8 @@ def run_stream(a):
         batch.apply_jtj()
         j1[r].record(ext)
     torch.cuda.synchronize(dev)
+    if a.profile_region:
+        torch.cuda.profiler.stop()
     jtj_ms = sum(x.elapsed_time(y) for x, y in zip(j0, j1)) / reps
     last = [c.read_stats() for c in ctxs]
     E = len(ctxs[0].read_graph()["edge_dst"])

@@ -498,12 +498,13 @@ void lc_ctx::free_template() {
 // graph
 // ---------------------------------------------------------------------------
 void lc_ctx::release_pcg_tables() {
-    void* bufs[] = {(void*)hC.pcg_perm, (void*)hC.pcg_leaf_off, (void*)hC.pcg_leaf,
+    void* bufs[] = {(void*)hC.pcg_perm, (void*)hC.pcg_leaf_off, (void*)hC.pcg_leaf, (void*)hC.jn_perm,
                     (void*)hC.pcg_loc_off[0], (void*)hC.pcg_loc_vid[0], (void*)hC.pcg_eus_off[0], (void*)hC.pcg_ent_us[0],
                     (void*)hC.pcg_loc_off[1], (void*)hC.pcg_loc_vid[1], (void*)hC.pcg_eus_off[1], (void*)hC.pcg_ent_us[1],
                     (void*)hC.pcg_zdst[0], (void*)hC.pcg_zdst[1]};
     for (void* p : bufs) release(p);
     hC.pcg_perm = nullptr;
+    hC.jn_perm = nullptr;
     hC.pcg_leaf_off = nullptr;
     hC.pcg_leaf = nullptr;
     for (int ti = 0; ti < 2; ++ti) {
@@ -545,7 +546,8 @@ lc_status lc_ctx::plan_pcg() {
     C.pcg_perm = (const int*)put(pcg_part.perm.data(), sizeof(int) * n);
     C.pcg_leaf_off = (const int*)put(pcg_part.leaf_off.data(), sizeof(int) * (kPcgLeaves + 1));
     C.pcg_leaf = (const uint8_t*)put(pcg_part.leaf.data(), n);
-    bool ok = C.pcg_perm && C.pcg_leaf_off && C.pcg_leaf;
+    C.jn_perm = (const int*)put(pcg_part.zorder.data(), sizeof(int) * n);
+    bool ok = C.pcg_perm && C.pcg_leaf_off && C.pcg_leaf && C.jn_perm;
     for (int ti = 0; ti < 2; ++ti) {
         C.pcg_loc_off[ti] = (const int*)put(pcg_part.loc_off[ti].data(), sizeof(int) * pcg_part.loc_off[ti].size());
         C.pcg_loc_vid[ti] = (const int*)put(pcg_part.loc_vid[ti].data(), sizeof(int) * pcg_part.loc_vid[ti].size());

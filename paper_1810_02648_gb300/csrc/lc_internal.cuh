@@ -167,6 +167,7 @@ struct CapDesc {
     float4* eA;              // N*K: (c, w) of the node's active entries, vertex ascending
     int* eV;                 // N*K: the compact positions of their vertices
     int* ecnt;               // n: active entries per node
+    const int* jn_perm;      // n: node of each node-phase slot (Morton order of the node positions)
     float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)
     // per-vertex surface stage (unknowns V)
     int n_adj;               // directed one-ring pairs
@@ -556,6 +557,9 @@ struct PcgPartition {
     std::vector<int> perm;
     std::vector<int> leaf_off;
     std::vector<uint8_t> leaf;
+    // all nodes in Morton (Z) order of their positions, ties by id: the node
+    // order of the per-iteration J^T J p's node phase
+    std::vector<int> zorder;
     // clusters of 8 and 16 CTAs (index 0, 1): local vertex lists and entry
     // tables (CapDesc::pcg_loc_* / pcg_ent_us)
     std::vector<int> loc_off[2], loc_vid[2], eus_off[2];

@@ -613,11 +613,14 @@ __device__ __forceinline__ fp2 fp2_group_sum(fp2 v) {
 }
 
 // W warps per block, kJtjNodeLanes lanes per node (kJtjNodesPerWarp nodes per
-// warp), U rounds of a node's entries in flight per lane.  Lane l of a
-// node's group takes its active entries l, l + kJtjNodeLanes, ... and edges
-// likewise; the group's sums use a fixed shuffle tree, and p . A p is summed
-// per group of kNodeTile consecutive nodes in one fixed tree, so every
-// launch shape gives the same bits.
+// warp), U rounds of a node's entries in flight per lane.  Slots walk the
+// nodes in the Morton order of their positions (jn_perm), so the nodes of a
+// warp are neighbours: similar numbers of active entries (visibility is
+// spatially coherent) and shared vertices.  Lane l of a node's group takes
+// its active entries l, l + kJtjNodeLanes, ... and edges likewise; the
+// group's sums use a fixed shuffle tree, and p . A p is summed per group of
+// kNodeTile consecutive slots in one fixed tree, so every launch shape gives
+// the same bits.
 template <int W, int U>
 __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restrict__ caps,
                                                           const WorkItem* __restrict__ items,
@@ -640,8 +643,9 @@ __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restr
     float4* __restrict__ out = out_in ? out_in : C.Ap;
     float4* __restrict__ out_lo = out_in ? out_lo_in : C.Ap_lo;
     const int g = threadIdx.x / kJtjNodeLanes, sl = threadIdx.x % kJtjNodeLanes;
-    const int k = tile * NPB + g;
-    const bool has = k < C.n;
+    const int slot = tile * NPB + g;
+    const bool has = slot < C.n;
+    const int k = has ? C.jn_perm[slot] : 0;
     // every lane runs the group sums below; a node past the end has no work
     int e0 = 0, e1 = 0, d0 = 0, d1 = 0;
     if (has) {
