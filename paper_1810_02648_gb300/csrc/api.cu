@@ -409,8 +409,7 @@ extern "C" lc_status lc_upload_template(lc_ctx* ctx, const float* V, int N, cons
     C.HA = (float4*)ctx->alloc(sizeof(float4) * N);
     C.HB = (float4*)ctx->alloc(sizeof(float4) * N);
     C.ev = (float4*)ctx->alloc(sizeof(float4) * N);
-    C.q = (float4*)ctx->alloc(sizeof(float4) * N);
-    C.q_lo = (float4*)ctx->alloc(sizeof(float4) * N);
+    C.q = (float4*)ctx->alloc(sizeof(float4) * 2 * N);
     C.vH = (float4*)ctx->alloc(sizeof(float4) * 2 * N);
     C.vpos = (int*)ctx->alloc(sizeof(int) * N);
     C.vcnt = (int*)ctx->alloc(sizeof(int) * ((N + kJChunk - 1) / kJChunk));
@@ -452,7 +451,7 @@ void lc_ctx::free_graph() {
     warm_release();
     void* bufs[] = {(void*)hC.node_vid, (void*)hC.bind_idx, (void*)hC.bind_w, (void*)hC.node_g, (void*)hC.ent_off,
                     (void*)hC.ent, (void*)hC.edge_off, (void*)hC.edge_dst, (void*)hC.edge_s, hC.node_R, hC.node_t,
-                    hC.vA, hC.vK, hC.eA, hC.eV, hC.ecnt, hC.dB,
+                    hC.vA, hC.vK, hC.eV, hC.ecnt, hC.dB,
                     hC.b, hC.minv, hC.diag, hC.x, hC.r, hC.z, hC.p, hC.Ap, tmp_vec, tmp_vec2,
                     hC.x_lo, hC.r_lo, hC.z_lo, hC.p_lo, hC.Ap_lo};
     release_pcg_tables();
@@ -460,7 +459,7 @@ void lc_ctx::free_graph() {
     hC.node_vid = nullptr; hC.bind_idx = nullptr; hC.bind_w = nullptr; hC.node_g = nullptr;
     hC.ent_off = nullptr; hC.ent = nullptr; hC.edge_off = nullptr; hC.edge_dst = nullptr; hC.edge_s = nullptr;
     hC.node_R = nullptr; hC.node_t = nullptr;
-    hC.vA = hC.eA = hC.dB = nullptr;
+    hC.vA = hC.dB = nullptr;
     hC.vK = hC.eV = hC.ecnt = nullptr;
     hC.b = hC.minv = hC.diag = hC.x = hC.r = hC.z = hC.p = hC.Ap = nullptr;
     hC.x_lo = hC.r_lo = hC.z_lo = hC.p_lo = hC.Ap_lo = nullptr;
@@ -481,14 +480,14 @@ void lc_ctx::free_template() {
     pose_release();
     surface_release();
     void* bufs[] = {tpl, base_buf, (void*)hC.albedo, (void*)hC.tris, (void*)hC.vt_off, (void*)hC.vt_tri,
-                    (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q, hC.q_lo,
+                    (void*)hC.medges, material, hC.flags, hC.vw, hC.uv, hC.res, hC.HA, hC.HB, hC.ev, hC.q,
                     hC.vH, hC.vpos, hC.vcnt};
     for (void* p : bufs) release(p);
     tpl = base_buf = nullptr;
     material = nullptr;
     hC.base = nullptr; hC.albedo = nullptr; hC.tris = nullptr; hC.vt_off = nullptr; hC.vt_tri = nullptr;
     hC.medges = nullptr; hC.flags = nullptr; hC.vw = nullptr; hC.uv = nullptr; hC.res = nullptr;
-    hC.HA = hC.HB = hC.ev = hC.q = hC.q_lo = hC.vH = nullptr;
+    hC.HA = hC.HB = hC.ev = hC.q = hC.vH = nullptr;
     hC.vpos = hC.vcnt = nullptr;
     hC.N = hC.F = hC.n_medges = 0;
     has_template = false;
@@ -595,7 +594,6 @@ static void graph_alloc_edges(lc_ctx* ctx, int E) {
     C.edge_s = (const float*)ctx->alloc(sizeof(float) * std::max(E, 1));
     C.vA = (float4*)ctx->alloc(sizeof(float4) * NK);
     C.vK = (int*)ctx->alloc(sizeof(int) * NK);
-    C.eA = (float4*)ctx->alloc(sizeof(float4) * NK);
     C.eV = (int*)ctx->alloc(sizeof(int) * NK);
     C.dB = (float4*)ctx->alloc(sizeof(float4) * 2 * (size_t)std::max(E, 1));
 }

@@ -135,8 +135,7 @@ struct CapDesc {
     float4* z_lo;
     float4* p_lo;
     float4* Ap_lo;
-    float4* q;               // per active vertex H_i dv_i scratch (N, by compact position), high part
-    float4* q_lo;            // its low part
+    float4* q;               // 2N: per active vertex H_i dv_i scratch by compact position, (high, low) parts
     // spatial node partition of the cluster PCG (kPcgLeaves leaves; a
     // cluster of cl CTAs gives CTA r the leaves r*L/cl .. (r+1)*L/cl - 1)
     const int* pcg_perm;      // n nodes in leaf order
@@ -164,8 +163,7 @@ struct CapDesc {
     float4* vH;              // 2N: (h00, h01, h02, h11), (h12, h22, 0, 0) of compact position pos
     int* vpos;               // N: compact position of vertex i, -1 when inactive
     int* vcnt;               // ceil(N / kJChunk): active vertices per chunk
-    float4* eA;              // N*K: (c, w) of the node's active entries, vertex ascending
-    int* eV;                 // N*K: the compact positions of their vertices
+    int* eV;                 // N*K: per active entry of a node, vertex ascending: (compact position << 3) | slot
     int* ecnt;               // n: active entries per node
     const int* jn_perm;      // n: node of each node-phase slot (Morton order of the node positions)
     float4* dB;              // 2 per directed node edge: (R_k (g_l - g_k), w_a s_kl), (R_l (g_k - g_l), 0)

@@ -433,9 +433,9 @@ void launch_rhs(const CapDesc* dC, const CapDesc& hC, int slot, bool energy_only
 // them: per chunk of kJChunk vertex ids, the active ones in id order at the
 // chunk's start with their coefficients, nodes and H block side by side, and
 // per node its active entries at the start of its CSR range, in vertex
-// order, with the vertex's compact position.  The product then reads no byte
-// of an inactive vertex.  Bindings and entries are staged by the same
-// function, so the forward and transposed products use the same bits.
+// order, as the vertex's compact position and the slot of the binding.  The
+// product then reads no byte of an inactive vertex, and the transposed
+// product reads the same staged coefficients as the forward one.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVertTile) jtj_stage_vertex_kernel(const CapDesc* __restrict__ caps,
                                                                       const WorkItem* __restrict__ items) {
@@ -489,8 +489,10 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const C
     if (k >= C.n) return;
     const float4 g = C.node_g[k];
     // the node's active entries packed in CSR order (runs after the vertex
-    // stage, whose compact positions it reads)
+    // stage, whose compact positions it reads); the slot is the vertex's
+    // binding to k with the entry's weight
     const int e0 = C.ent_off[k], e1 = C.ent_off[k + 1];
+    const int K = C.K;
     int cnt = 0;
     for (int jb = e0; jb < e1; jb += 32) {
         const int j = jb + lane;
@@ -502,9 +504,12 @@ __global__ void __launch_bounds__(kNodeWarps * 32) jtj_stage_node_kernel(const C
         }
         const unsigned bal = __ballot_sync(0xffffffffu, pos >= 0);
         if (pos >= 0) {
-            const int d = e0 + cnt + __popc(bal & ((1u << lane) - 1u));
-            C.eA[d] = staged_coef(C.node_R, k, C.base[en.x], g, __int_as_float(en.y));
-            C.eV[d] = pos;
+            int slot = 0;
+            for (int s = K - 1; s >= 0; --s) {
+                const size_t b = (size_t)en.x * K + s;
+                if (C.bind_idx[b] == k && __float_as_int(C.bind_w[b]) == en.y) slot = s;
+            }
+            C.eV[e0 + cnt + __popc(bal & ((1u << lane) - 1u))] = (pos << 3) | slot;
         }
         cnt += __popc(bal);
     }
@@ -579,8 +584,8 @@ __global__ void __launch_bounds__(VB) jtj_vertex_kernel(const CapDesc* __restric
     const fp2 d[3] = {dv[0].get(), dv[1].get(), dv[2].get()};
     fp2 q[3];
     jtj_block(h, d, q);
-    C.q[pos] = make_float4(q[0].h, q[1].h, q[2].h, 1.f);
-    C.q_lo[pos] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
+    C.q[2 * pos] = make_float4(q[0].h, q[1].h, q[2].h, 1.f);
+    C.q[2 * pos + 1] = make_float4(q[0].l, q[1].l, q[2].l, 0.f);
 }
 
 // the p . A p total of a capture: alpha = r.z / p.A p as a pair division, or
@@ -655,23 +660,25 @@ __global__ void __launch_bounds__(W * 32) jtj_node_kernel(const CapDesc* __restr
         d1 = C.edge_off[k + 1];
     }
     fp2acc acc[6];
+    const int K = C.K;
     // U rounds of the node's entries at a time: their loads are issued
-    // together before any result is used
+    // together before any result is used; an entry's coefficient is its
+    // vertex's staged binding (compact position, slot)
     for (int jb = e0 + sl; jb < e1; jb += kJtjNodeLanes * U) {
-        float4 a[U];
         int vi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = jb + kJtjNodeLanes * u;
-            a[u] = j < e1 ? C.eA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             vi[u] = j < e1 ? C.eV[j] : -1;
         }
-        float4 qh[U], ql[U];
+        float4 a[U], qh[U], ql[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool on = vi[u] >= 0;
-            qh[u] = on ? C.q[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-            ql[u] = on ? C.q_lo[vi[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int pos = vi[u] >> 3;
+            a[u] = on ? C.vA[(size_t)pos * K + (vi[u] & 7)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            qh[u] = on ? C.q[2 * pos] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ql[u] = on ? C.q[2 * pos + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
