@@ -1385,6 +1385,10 @@ def run_stream(a):
             c.pose_advance()
     torch.cuda.synchronize(dev)
     batch = Batch(ctxs)
+    # launch shape of the batched product, tuned on the streams' current
+    # frames (the tuner's solves start from the identity, as every frame
+    # step's non-rigid stage does)
+    tune = batch.autotune_shapes(reps=2, use_cache=False)
     ext = torch.cuda.ExternalStream(batch.stream_handle, device=dev)
     steps = L - 2
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -1471,6 +1475,7 @@ def run_stream(a):
                    "streams": S, "frames_per_stream": L, "timed_frame_steps": steps, "body_parts": parts,
                    "euler_start": a.euler_start, "carry_graph": a.carry_graph,
                    "warm_start": use_net, "warm_start_training_rows": rows if use_net else 0,
+                   "shape": tune["shape"], "autotune": {k: tune[k] for k in ("ms", "tried", "rejected")},
                    "l2": "each step uploads new frames (17 MB per 2048^2 frame); no flush"},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
