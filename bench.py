@@ -644,13 +644,31 @@ PCG_TRAFFIC = {"sources": ("pcg_cluster.cu", "jtj_pair.cuh", "fpair.cuh"), "sha2
                "bytes": 709632 + 0}
 
 
-def pcg_traffic():
+def _sources_hash(sources):
     import hashlib
     h = hashlib.sha256()
-    for f in PCG_TRAFFIC["sources"]:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_1810_02648_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return PCG_TRAFFIC["bytes"] if h.hexdigest()[:16] == PCG_TRAFFIC["sha256_16"] else None
+    return h.hexdigest()[:16]
+
+
+def pcg_traffic():
+    return PCG_TRAFFIC["bytes"] if _sources_hash(PCG_TRAFFIC["sources"]) == PCG_TRAFFIC["sha256_16"] else None
+
+
+# DRAM bytes (read + write) of the batch workload's J^T J p launch pair
+# (jtj_vertex_kernel + jtj_node_kernel over the 64 captures), from one ncu
+# capture of these kernel sources with ncu's cache flush before each kernel
+# (profiles/jtj_batched_batch_streams.md); reported only while the sources
+# still hash to the captured version, else null.
+BATCH_JTJ_TRAFFIC = {"sources": ("solver_kernels.cu", "jtj_pair.cuh", "fpair.cuh", "lc_internal.cuh"),
+                     "sha256_16": "bc1a4118eb5951f9", "bytes": 26465536 + 18432 + 36380160 + 232704}
+
+
+def batch_jtj_traffic():
+    return (BATCH_JTJ_TRAFFIC["bytes"]
+            if _sources_hash(BATCH_JTJ_TRAFFIC["sources"]) == BATCH_JTJ_TRAFFIC["sha256_16"] else None)
 
 
 def frame_seeds(a, rank=0):
@@ -1145,7 +1163,7 @@ def run_batch(a):
         "gpu_launches": int(stats[0]["n_kernels"]) * a.steps,
         "roofline": {"kernel": "jtj_vertex_kernel + jtj_node_kernel over all captures (one J^T J p each)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": jtj_bytes,
+                     "peak_source": peak_kind, "traffic": batch_jtj_traffic(), "algorithmic_bytes_per_launch": jtj_bytes,
                      "avg_launch_us": 1e3 * jtj_ms, "l2": "flushed before each timed call"},
         "solve": {"e_total_sum": float(sum(s["e_total"] for s in stats)),
                   "cluster_sizes": sorted(set(int(s["pcg_cluster_size"]) for s in stats))},
@@ -1224,16 +1242,16 @@ def run_warmstart(a):
         it = pool.imap(_ws_frame, [(s, i) for s in train_seeds for i in range(L + 1)], chunksize=2)
         ev_async = pool.map_async(_ws_frame, [(s, i) for s in eval_seeds for i in range(a.ws_eval_frames)],
                                   chunksize=2)
-        Fs, Ts = [], []
+        Fs, Ts, Es = [], [], []
         for s in train_seeds:
             _ws_restart(plain)
-            F, T, _ = ws.collect(plain, (next(it) for _ in range(L + 1)), skip=1)
+            F, T, E = ws.collect(plain, (next(it) for _ in range(L + 1)), skip=1)
             Fs.append(F)
             Ts.append(T)
+            Es.append(E)
         torch.cuda.synchronize(dev)
         t_collect = time.perf_counter() - t_start
-        F = torch.cat(Fs)
-        T = torch.cat(Ts)
+        F, T, kept = ws.keep_converged(torch.cat(Fs), torch.cat(Ts), np.concatenate(Es))
         del Fs, Ts
         t0 = time.perf_counter()
         net, losses = ws.train(F, T, steps=a.ws_adam_steps, batch=4096, lr=1e-3, seed=0,
@@ -1269,7 +1287,8 @@ def run_warmstart(a):
                                f"up to {2 * sc.n_gn} GN, both stopping at the plain method's own final energy "
                                f"(1e-4), conditional blocks of {a.ws_gn_block} steps",
                    "train_frames": n_seq * L, "train_sequences": n_seq, "frames_per_sequence": L,
-                   "train_rows": rows, "adam_steps": a.ws_adam_steps, "adam_batch": 4096,
+                   "train_rows": rows, "train_frames": int(len(kept)), "train_frames_kept": int(kept.sum()),
+                   "adam_steps": a.ws_adam_steps, "adam_batch": 4096,
                    "eval_sequences": len(eval_seeds), "eval_frames_per_sequence": a.ws_eval_frames,
                    "l2": "inputs of one frame < L2; no flush (every frame uploads a new image)"},
         "warm_start": dict(sm, loss_first=losses[0][1], loss_last=losses[-1][1], collect_s=t_collect,
@@ -1353,17 +1372,19 @@ def run_stream(a):
     net, losses, t_train = None, [], 0.0
     if use_net:
         t0 = time.perf_counter()
-        Fs, Ts = [], []
+        Fs, Ts, Es = [], [], []
         for s_ in train_seeds:
             ws.restart(ctxs[0], pose=True)
-            F, T, _ = ws.collect(ctxs[0], (next(it) for _ in range(a.stream_train_len)), skip=1, pose=True,
+            F, T, E = ws.collect(ctxs[0], (next(it) for _ in range(a.stream_train_len)), skip=1, pose=True,
                                  euler=a.euler_start, from_identity=not a.carry_graph)
             Fs.append(F)
             Ts.append(T)
-        net, losses = ws.train(torch.cat(Fs), torch.cat(Ts), steps=2000, batch=4096, lr=1e-3, seed=0,
-                               log_every=500)
-        rows = int(sum(f.shape[0] for f in Fs) * sc.n_nodes)
-        del Fs, Ts
+            Es.append(E)
+        train_e = np.concatenate(Es)
+        F, T, kept = ws.keep_converged(torch.cat(Fs), torch.cat(Ts), train_e)
+        net, losses = ws.train(F, T, steps=2000, batch=4096, lr=1e-3, seed=0, log_every=500)
+        rows = int(F.shape[0] * sc.n_nodes)
+        del Fs, Ts, F, T
         torch.cuda.synchronize(dev)
         t_train = time.perf_counter() - t0
         ws.restart(ctxs[0], pose=True)
@@ -1488,6 +1509,9 @@ def run_stream(a):
         "solve": {"e_total_median": float(np.median(et)), "e_total_max": float(et.max()),
                   "e_total_last_step": [float(x) for x in et[-1]],
                   "network_loss": [float(losses[0][1]), float(losses[-1][1])] if losses else None,
+                  "training_frames": int(len(train_e)) if use_net else 0,
+                  "training_frames_kept": int(kept.sum()) if use_net else 0,
+                  "training_e_final": [float(x) for x in train_e] if use_net else [],
                   "train_s": t_train, "wall_s": time.perf_counter() - t_start},
         "cpu_baseline": None,
     }

@@ -515,6 +515,40 @@ void lc_ctx::release_pcg_tables() {
     }
 }
 
+// Morton order of the node positions: each coordinate quantised to 10 bits
+// over the nodes' bounding box, the bits interleaved (x lowest), nodes
+// sorted by code and then by id.
+static void morton_order(int n, const float4* g, std::vector<int>& order) {
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < n; ++k) {
+        const float v[3] = {g[k].x, g[k].y, g[k].z};
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = k ? std::min(lo[d], v[d]) : v[d];
+            hi[d] = k ? std::max(hi[d], v[d]) : v[d];
+        }
+    }
+    auto spread = [](uint32_t x) {   // 10 bits -> every third bit of 30
+        uint32_t r = 0;
+        for (int b = 0; b < 10; ++b) r |= ((x >> b) & 1u) << (3 * b);
+        return r;
+    };
+    std::vector<std::pair<uint32_t, int>> key(n);
+    for (int k = 0; k < n; ++k) {
+        const float v[3] = {g[k].x, g[k].y, g[k].z};
+        uint32_t code = 0;
+        for (int d = 0; d < 3; ++d) {
+            const float ext = hi[d] - lo[d];
+            const float u = ext > 0.f ? (v[d] - lo[d]) / ext : 0.f;
+            const uint32_t q = (uint32_t)std::min(1023.f, std::max(0.f, u * 1023.f));
+            code |= spread(q) << d;
+        }
+        key[k] = {code, k};
+    }
+    std::sort(key.begin(), key.end());
+    order.resize(n);
+    for (int k = 0; k < n; ++k) order[k] = key[k].second;
+}
+
 // Spatial partition of the graph's nodes (host, from the node positions,
 // bindings and CSR), its per-CTA tables uploaded to the device, and the
 // cluster PCG plan.
@@ -535,6 +569,7 @@ lc_status lc_ctx::plan_pcg() {
         (s = copy_to_host(ed.data(), C.edge_dst, sizeof(int) * (size_t)go[n])))
         return s;
     spatial_partition(n, N, K, g.data(), eo.data(), en.data(), go.data(), ed.data(), bi.data(), pcg_part);
+    morton_order(n, g.data(), pcg_part.zorder);
     release_pcg_tables();
     // upload one host array into a fresh device buffer
     auto put = [&](const void* src, size_t bytes) -> void* {

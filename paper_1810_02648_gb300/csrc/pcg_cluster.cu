@@ -625,43 +625,8 @@ static void rcb(std::vector<int>& idx, int a, int b, int levels, int leaf0, cons
     rcb(idx, s, b, levels - 1, leaf0 + half, g, leaf_off);
 }
 
-// Morton order of the node positions: each coordinate quantised to 10 bits
-// over the nodes' bounding box, the bits interleaved (x lowest), nodes
-// sorted by code and then by id.
-static void morton_order(int n, const float4* g, std::vector<int>& order) {
-    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < n; ++k) {
-        const float v[3] = {g[k].x, g[k].y, g[k].z};
-        for (int d = 0; d < 3; ++d) {
-            lo[d] = k ? std::min(lo[d], v[d]) : v[d];
-            hi[d] = k ? std::max(hi[d], v[d]) : v[d];
-        }
-    }
-    auto spread = [](uint32_t x) {   // 10 bits -> every third bit of 30
-        uint32_t r = 0;
-        for (int b = 0; b < 10; ++b) r |= ((x >> b) & 1u) << (3 * b);
-        return r;
-    };
-    std::vector<std::pair<uint32_t, int>> key(n);
-    for (int k = 0; k < n; ++k) {
-        const float v[3] = {g[k].x, g[k].y, g[k].z};
-        uint32_t code = 0;
-        for (int d = 0; d < 3; ++d) {
-            const float ext = hi[d] - lo[d];
-            const float u = ext > 0.f ? (v[d] - lo[d]) / ext : 0.f;
-            const uint32_t q = (uint32_t)std::min(1023.f, std::max(0.f, u * 1023.f));
-            code |= spread(q) << d;
-        }
-        key[k] = {code, k};
-    }
-    std::sort(key.begin(), key.end());
-    order.resize(n);
-    for (int k = 0; k < n; ++k) order[k] = key[k].second;
-}
-
 void spatial_partition(int n, int N, int K, const float4* g, const int* ent_off, const int2* ent,
                        const int* edge_off, const int* edge_dst, const int* bind_idx, PcgPartition& out) {
-    morton_order(n, g, out.zorder);
     out.perm.resize(n);
     std::iota(out.perm.begin(), out.perm.end(), 0);
     out.leaf_off.assign(kPcgLeaves + 1, 0);

@@ -85,6 +85,24 @@ def collect(ctx, frames, skip: int = 0, pose: bool = False, euler: bool = True, 
     return torch.stack(F), torch.stack(Tg), np.array(E)
 
 
+def keep_converged(F, T, E, factor: float = 100.0):
+    """The training frames whose plain solve converged: final energy finite
+    and at most ``factor`` times the median final energy of the set, targets
+    finite.  A tracked solve that ran away from the capture (Gauss-Newton
+    without step control can, on a rare frame) would otherwise put its
+    motion, orders of magnitude off, among the targets.  Returns (F, T,
+    kept mask over the frames)."""
+    import torch
+    E = np.asarray(E, dtype=np.float64)
+    ok = np.isfinite(E)
+    if ok.any():
+        ok &= E <= factor * np.median(E[ok])
+    fin = torch.isfinite(T.reshape(T.shape[0], -1)).all(1).cpu().numpy()
+    keep = ok & fin
+    idx = torch.as_tensor(np.nonzero(keep)[0], device=F.device)
+    return F.index_select(0, idx), T.index_select(0, idx), keep
+
+
 def init_params(seed: int) -> np.ndarray:
     """He-normal weights, zero biases (flat layout of LC_MLP_PARAMS)."""
     rng = np.random.default_rng(seed)
