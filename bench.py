@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--stream-scene", choices=["stress", "body"], default="stress", help="stream: the capture")
     ap.add_argument("--stream-train-seqs", type=int, default=4, help="stream: warm-start training sequences")
     ap.add_argument("--stream-train-len", type=int, default=8, help="stream: frames per training sequence")
+    ap.add_argument("--stream-train-counts", default="3x4",
+                    help="stream: GN x PCG counts of the solves that give the warm start's targets (default 3x4, "
+                         "the paper's counts for the stage: a stable function of the data; '' = the streams' own)")
     ap.add_argument("--no-warm-start", action="store_true", help="stream: without the learned warm start")
     ap.add_argument("--euler-start", action="store_true",
                     help="stream: the pose stage starts from the explicit Euler step (default: the last solved pose)")
@@ -1373,6 +1376,9 @@ def run_stream(a):
     if use_net:
         t0 = time.perf_counter()
         Fs, Ts, Es = [], [], []
+        if a.stream_train_counts:
+            tg, tp = (int(x) for x in a.stream_train_counts.lower().split("x"))
+            ctxs[0].set_params(n_gn=tg, n_pcg=tp)
         for s_ in train_seeds:
             ws.restart(ctxs[0], pose=True)
             F, T, E = ws.collect(ctxs[0], (next(it) for _ in range(a.stream_train_len)), skip=1, pose=True,
@@ -1385,6 +1391,8 @@ def run_stream(a):
         net, losses = ws.train(F, T, steps=2000, batch=4096, lr=1e-3, seed=0, log_every=500)
         rows = int(F.shape[0] * sc.n_nodes)
         del Fs, Ts, F, T
+        if a.stream_train_counts:
+            ctxs[0].set_params(n_gn=sc.n_gn, n_pcg=sc.n_pcg)
         torch.cuda.synchronize(dev)
         t_train = time.perf_counter() - t0
         ws.restart(ctxs[0], pose=True)
@@ -1496,6 +1504,7 @@ def run_stream(a):
                    "streams": S, "frames_per_stream": L, "timed_frame_steps": steps, "body_parts": parts,
                    "euler_start": a.euler_start, "carry_graph": a.carry_graph,
                    "warm_start": use_net, "warm_start_training_rows": rows if use_net else 0,
+                   "warm_start_target_counts": a.stream_train_counts or f"{sc.n_gn}x{sc.n_pcg}",
                    "shape": tune["shape"], "autotune": {k: tune[k] for k in ("ms", "tried", "rejected")},
                    "l2": "each step uploads new frames (17 MB per 2048^2 frame); no flush"},
         "clocks": clk.summary(),
