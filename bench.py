@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--ws-eval-seqs", type=int, default=2, help="warm start: held-out sequences")
     ap.add_argument("--ws-eval-frames", type=int, default=300, help="warm start: frames per held-out sequence")
     ap.add_argument("--ws-adam-steps", type=int, default=20000, help="warm start: Adam steps")
+    ap.add_argument("--ws-train-counts", default="",
+                    help="warm start: GN x PCG counts of the solves that give the targets, e.g. 3x4 "
+                         "(default: the capture's own counts)")
     ap.add_argument("--ws-gn-block", type=int, default=2,
                     help="warm start: Gauss-Newton steps per conditional graph block, both arms")
     ap.add_argument("--streams", type=int, default=8, help="stream: tracked sequences solved together")
@@ -1246,12 +1249,17 @@ def run_warmstart(a):
         ev_async = pool.map_async(_ws_frame, [(s, i) for s in eval_seeds for i in range(a.ws_eval_frames)],
                                   chunksize=2)
         Fs, Ts, Es = [], [], []
+        if a.ws_train_counts:
+            tg, tp = (int(x) for x in a.ws_train_counts.lower().split("x"))
+            plain.set_params(n_gn=tg, n_pcg=tp)
         for s in train_seeds:
             _ws_restart(plain)
             F, T, E = ws.collect(plain, (next(it) for _ in range(L + 1)), skip=1)
             Fs.append(F)
             Ts.append(T)
             Es.append(E)
+        if a.ws_train_counts:
+            plain.set_params(n_gn=sc.n_gn, n_pcg=sc.n_pcg)
         torch.cuda.synchronize(dev)
         t_collect = time.perf_counter() - t_start
         F, T, kept = ws.keep_converged(torch.cat(Fs), torch.cat(Ts), np.concatenate(Es))
@@ -1291,6 +1299,7 @@ def run_warmstart(a):
                                f"(1e-4), conditional blocks of {a.ws_gn_block} steps",
                    "train_frames": n_seq * L, "train_sequences": n_seq, "frames_per_sequence": L,
                    "train_rows": rows, "train_frames": int(len(kept)), "train_frames_kept": int(kept.sum()),
+                   "target_counts": a.ws_train_counts or f"{sc.n_gn}x{sc.n_pcg}",
                    "adam_steps": a.ws_adam_steps, "adam_batch": 4096,
                    "eval_sequences": len(eval_seeds), "eval_frames_per_sequence": a.ws_eval_frames,
                    "l2": "inputs of one frame < L2; no flush (every frame uploads a new image)"},

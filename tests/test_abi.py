@@ -91,11 +91,12 @@ def test_autotune_table_text_round_trip():
     """The shape table's text form (host only): a valid line is merged and
     exported again; a malformed line or an unknown shape is refused."""
     from paper_1810_02648_gb300.livecap import LivecapError, autotune_table, autotune_table_load
-    autotune_table_load("K4.N12.n9x2,K8.N17.n12x1\t3 512 16 2 1.25\n")
+    autotune_table_load("K4.N12.n9x2,K8.N17.n12x1\t3 512 16 2 1.25\nK4.N11.n8x5\t0 128 4 8 0.5\n")
     lines = dict(line.split("\t") for line in autotune_table().splitlines())
     assert lines["K4.N12.n9x2,K8.N17.n12x1"].split()[:4] == ["3", "512", "16", "2"]
+    assert lines["K4.N11.n8x5"].split()[:4] == ["0", "128", "4", "8"]
     for bad in ("no tab here 3 256 8 4 1\n", "K4.N1.n1x1\t3 300 8 4 1\n", "K4.N1.n1x1\t3 256 12 4 1\n",
-                "K4.N1.n1x1\t9 256 8 4 1\n", "K4.N1.n1x1\t3 256 8\n"):
+                "K4.N1.n1x1\t3 256 2 4 1\n", "K4.N1.n1x1\t9 256 8 4 1\n", "K4.N1.n1x1\t3 256 8\n"):
         with pytest.raises(LivecapError):
             autotune_table_load(bad)
     assert "K4.N1.n1x1" not in autotune_table()
